@@ -1,0 +1,223 @@
+/*
+ * gao.h - C ABI of the GA-driven GPU-offload loop-program library (libgao.so).
+ *
+ * The method (Yamato et al., "Study of Automatic GPU Offloading Technology for
+ * Open IoT", Sec. 3.3 and Sec. 4) takes a program whose parallelisable `for`
+ * loops are numbered 0..a-1, encodes an offload pattern as a gene of a bits
+ * (bit i = 1: loop i runs on the GPU; 0: it stays on the CPU), measures the
+ * program's processing time under that gene, and searches the genes with a
+ * Simple GA whose fitness is (processing time)^(-1/2) (Sec. 5.1.2).
+ *
+ * This library runs such a program on one GPU (sm_103a) and its host CPU:
+ *   prog_create  declares the buffers and loops (Sec. 4: the loop list and its
+ *                gene length a),
+ *   prog_run     executes the program under one gene and returns its time
+ *                (Sec. 3.3 "evaluation": run the pattern and measure it),
+ *   ga_evaluate  scores a population, reusing the time of any gene measured
+ *                before (Sec. 4: repeated patterns are not re-measured),
+ *   ga_run       runs the whole Simple GA (Sec. 3.3, parameters of Sec. 5.1.2).
+ *
+ * Conventions for every entry point:
+ *   - Return value is a gao_status; GAO_OK = 0.  On error, gao_last_error()
+ *     returns a message for the calling thread.  Nothing aborts or traps.
+ *   - Arrays passed in are borrowed for the duration of the call only.
+ *   - Matrices are row-major binary32; scalars produced by FROBENIUS and SUM
+ *     are binary64 (a 1 x 1 buffer of dtype GAO_F64).
+ *   - Gene bit i (bit 0 = least significant) places loop i; bits at or above
+ *     the loop count must be zero (GAO_EINVAL otherwise).  At most 64 loops.
+ *   - A program is not thread-safe: one call at a time per gao_prog.
+ */
+#ifndef GAO_H
+#define GAO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gao_status {
+    GAO_OK = 0,
+    GAO_EINVAL = 1,   /* invalid argument: null pointer, bad shape, bad gene bits   */
+    GAO_ENOMEM = 2,   /* device, pinned-host or arena space exhausted               */
+    GAO_ECUDA = 3,    /* a CUDA runtime call failed                                 */
+    GAO_ETIMEOUT = 4, /* the run exceeded its time budget (Sec. 5.2: trials time out) */
+    GAO_EDEVICE = 5,  /* a kernel raised its error word (bounded wait expired)      */
+    GAO_ENODEV = 6,   /* no usable CUDA device of compute capability 10.3           */
+    GAO_ECPU = 7      /* a CPU loop failed                                          */
+} gao_status;
+
+/* Loop kinds.  The paper's benchmark is a matrix-product program (Sec. 5.1.1)
+ * whose loops it does not list; these are the loop bodies the library offers. */
+typedef enum gao_loop_kind {
+    GAO_LOOP_INIT = 0,      /* outs[t][i,j] = U[-1,1) value of (seed, buffer id outs[t], i*cols+j);
+                               flags bit t: multiply row i by its power-of-two factor          */
+    GAO_LOOP_GEMM = 1,      /* outs[0] = alpha * ins[0] @ ins[1] + beta * ins[2]; outs[0] may be ins[2] */
+    GAO_LOOP_AXPY = 2,      /* outs[0] = ins[0] + alpha * ins[1]   (scale-add D = C + 2A)         */
+    GAO_LOOP_TRANSPOSE = 3, /* outs[0] = ins[0]^T                                                */
+    GAO_LOOP_ROWSUM = 4,    /* outs[0][i] = sum_j ins[0][i,j]   (rows x 1, binary32)             */
+    GAO_LOOP_FROBENIUS = 5, /* outs[0] = sqrt(sum ins[0]^2)     (1 x 1, binary64)                */
+    GAO_LOOP_RELU = 6,      /* outs[0] = max(ins[0], 0)                                          */
+    GAO_LOOP_SQUARE = 7,    /* outs[0] = ins[0] (.) ins[0]                                       */
+    GAO_LOOP_COLMAX = 8,    /* outs[0][j] = max_i ins[0][i,j]   (1 x cols, binary32)             */
+    GAO_LOOP_SUM = 9        /* outs[0] = sum ins[0]             (1 x 1, binary64)                */
+} gao_loop_kind;
+
+typedef enum gao_dtype { GAO_F32 = 0, GAO_F64 = 1 } gao_dtype;
+
+typedef enum gao_buf_role {
+    GAO_BUF_TEMP = 0,   /* produced and consumed inside the program                               */
+    GAO_BUF_INPUT = 1,  /* host data set by prog_set_input; valid on the host at the start of a run */
+    GAO_BUF_OUTPUT = 2  /* copied to the host at the end of every run (unless GAO_RUN_KEEP_DEVICE) */
+} gao_buf_role;
+
+typedef struct gao_buffer {
+    int64_t rows, cols;
+    int32_t dtype; /* gao_dtype    */
+    int32_t role;  /* gao_buf_role */
+} gao_buffer;
+
+#define GAO_MAX_IO 4
+typedef struct gao_loop {
+    int32_t kind;            /* gao_loop_kind                          */
+    int32_t ins[GAO_MAX_IO]; /* buffer indices, -1 for unused slots    */
+    int32_t outs[GAO_MAX_IO];
+    double alpha, beta;
+    uint64_t flags;
+} gao_loop;
+
+/* GEMM arithmetic.  Every variant takes binary32 A, B, C and accumulates in binary32. */
+typedef enum gao_gemm_prec {
+    GAO_GEMM_FP32_SIMT = 0, /* FFMA on the CUDA cores                                      */
+    GAO_GEMM_BF16 = 1,      /* A, B rounded to bfloat16, tcgen05 tensor cores              */
+    GAO_GEMM_BF16X3 = 2,    /* two-term bfloat16 split, 3 products (hi.hi + hi.lo + lo.hi) */
+    GAO_GEMM_BF16X6 = 3,    /* three-term split, 6 products                               */
+    GAO_GEMM_FP8 = 4        /* e4m3 with one scale per 128-element K block                */
+} gao_gemm_prec;
+
+typedef struct gao_opts {
+    int32_t gemm_prec;       /* gao_gemm_prec                                               */
+    int32_t kchunk;          /* K elements per binary32 partial sum (0: library default)    */
+    int32_t tile_cfg;        /* tensor-core tile configuration id (0: default)              */
+    int32_t cpu_threads;     /* OpenMP threads for CPU loops (0: all)                       */
+    uint64_t seed;           /* seed of the INIT loop's counter hash                        */
+    double timeout_s;        /* wall-clock budget of one prog_run (0: none)                 */
+    void *stream;            /* cudaStream_t the program runs on (NULL: a library stream)   */
+    void *dev_arena;         /* caller-owned device memory for every buffer and all scratch
+                                (NULL: the library allocates it); must outlive the program */
+    uint64_t dev_arena_bytes;
+} gao_opts;
+
+typedef struct gao_prog gao_prog;
+
+/* Device bytes a program needs (buffers + scratch), for callers that supply dev_arena. */
+gao_status prog_device_bytes(const gao_loop *loops, int n_loops, const gao_buffer *bufs, int n_bufs,
+                             const gao_opts *opts, uint64_t *bytes_out);
+
+/* Declare a program: its buffers and its loops in program order (gene length = n_loops).
+ * Validates shapes and the dataflow (every input is produced earlier or is an INPUT buffer).
+ * On success *out owns device memory (or uses opts->dev_arena) and pinned host mirrors. */
+gao_status prog_create(const gao_loop *loops, int n_loops, const gao_buffer *bufs, int n_bufs,
+                       const gao_opts *opts, gao_prog **out);
+
+/* Copy `bytes` of host data into INPUT buffer `buf` (its pinned host mirror). */
+gao_status prog_set_input(gao_prog *p, int buf, const void *host_src, uint64_t bytes);
+
+#define GAO_RUN_KEEP_DEVICE 1u /* leave OUTPUT buffers on the device (no final copy) */
+
+/* Run every loop in program order, loop i on the GPU iff gene bit i is 1.  Data moves
+ * between host and device only where a loop needs a buffer last written on the other
+ * side (Sec. 3.3: CPU-GPU transfers decide which loop combinations are fast).
+ * *seconds_out = wall time from the first loop until the outputs are on the host. */
+gao_status prog_run(gao_prog *p, uint64_t gene_mask, uint32_t flags, double *seconds_out);
+
+/* Borrowed pointer to buffer `buf`'s host copy after a run (valid until the next
+ * run or destroy); *shape_out receives its shape.  GAO_EINVAL if not on the host. */
+gao_status prog_output(gao_prog *p, int buf, const void **host_ptr, gao_buffer *shape_out);
+
+/* Device pointer of buffer `buf` (for callers that keep data on the GPU). */
+gao_status prog_device_ptr(gao_prog *p, int buf, void **dev_ptr);
+
+typedef struct gao_loop_stat {
+    int32_t placement;  /* 1: ran on the GPU, 0: on the CPU                           */
+    int32_t _pad;
+    double device_ms;   /* GPU time of the loop's kernels (CUDA events)                */
+    double kernel_ms;   /* GPU time of its main kernel only (GEMM: without the split)  */
+    double cpu_ms;      /* host wall time of the CPU loop                              */
+    double copy_ms;     /* wall time of the copies issued before the loop              */
+    uint64_t h2d_bytes; /* bytes copied host->device before the loop                   */
+    uint64_t d2h_bytes; /* bytes copied device->host before the loop                   */
+} gao_loop_stat;
+
+/* Per-loop statistics of the last prog_run (n >= loop count). */
+gao_status prog_stats(gao_prog *p, gao_loop_stat *out, int n);
+
+/* Forget every cached gene time of this program. */
+gao_status prog_cache_clear(gao_prog *p);
+
+void prog_destroy(gao_prog *p);
+
+/* ---- GA (Sec. 3.3 / Sec. 4 / Sec. 5.1.2) ---------------------------------- */
+
+typedef struct gao_ga_params {
+    int32_t pop;         /* M, individuals per generation                              */
+    int32_t generations; /* T, populations evaluated                                   */
+    double pc;           /* crossover rate Pc                                          */
+    double pm;           /* mutation rate Pm (per gene)                                */
+    int32_t elite;       /* 1: best gene passes unchanged to the next generation       */
+    int32_t mutation;    /* 0: flip each gene with prob. pm; 1: flip one gene w.p. pm  */
+    uint64_t seed;       /* SplitMix64 seed of all GA draws                            */
+    double timeout_s;    /* per-evaluation budget: >0 value, 0 program's own,
+                            <0 automatic (10 x the all-GPU time, capped at 60 s)      */
+} gao_ga_params;
+
+typedef struct gao_ga_gen {
+    uint64_t best_mask; /* best gene of this generation                                 */
+    double best_s;      /* its time                                                     */
+    double mean_s;      /* mean time over the generation's successful individuals       */
+    int32_t evaluated;  /* genes measured for the first time in this generation         */
+    int32_t cache_hits; /* individuals whose time came from the cache                   */
+} gao_ga_gen;
+
+typedef struct gao_ga_result {
+    uint64_t best_mask;   /* best gene found (lowest time; first found on ties)         */
+    double best_s;
+    int32_t evaluations;  /* distinct genes measured                                    */
+    int32_t cache_hits;
+    gao_ga_gen *history;  /* optional, caller array of `generations` entries            */
+    uint64_t *populations;/* optional, caller array of generations * pop genes          */
+} gao_ga_result;
+
+/* Score a population: seconds_out[i] = sum over programs of prog_run time of gene i
+ * (from the cache when measured before), fitness_out[i] = seconds^(-1/2), 0 when
+ * the gene failed.  *cache_hits_out counts individuals served from the cache. */
+gao_status ga_evaluate(gao_prog *const *progs, int n_progs, const uint64_t *population, int pop,
+                       double *fitness_out, double *seconds_out, int *cache_hits_out);
+
+/* Run the Simple GA over the programs' common gene length. */
+gao_status ga_run(gao_prog *const *progs, int n_progs, const gao_ga_params *params, gao_ga_result *result);
+
+/* Run the same GA against a fixed time table instead of measurements:
+ * times[mask] for every mask < 2^n_genes (n_genes <= 24); a negative or
+ * non-finite time marks a failed gene (fitness 0).  Host only, no GPU. */
+gao_status ga_run_table(const double *times, int n_genes, const gao_ga_params *params, gao_ga_result *result);
+
+/* ---- misc ------------------------------------------------------------------ */
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *gao_last_error(void);
+
+/* Library version string. */
+const char *gao_version(void);
+
+/* Device-side wait self-test: launches one kernel that waits for a flag nothing
+ * sets, with a wall-clock limit of limit_s; the kernel records the expiry in the
+ * library's error word and returns.  Returns GAO_ETIMEOUT when the limit was
+ * observed (the expected outcome), GAO_OK never.  stream may be NULL. */
+gao_status gao_selftest_device_wait(double limit_s, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAO_H */
