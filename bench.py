@@ -1,0 +1,369 @@
+"""Benchmark of the loop-program hot path on GB300.
+
+One step = one run of the six-loop program (init, GEMM, scale-add, transpose, row
+sums, Frobenius norm) on n x n binary32 matrices under the all-GPU gene, through
+the C ABI (prog_run).  Default workload: n = 4096 (the size of the all-64-genes
+configuration), GEMM as the three-term split-bfloat16 product with binary32
+accumulation (the path that meets 1e-6).  value = 2 n^3 / step time (TFLOP/s of
+the whole program).  Inputs never leave the device inside the timed region for
+`value`; `e2e` repeats the measurement with A, B, C0 coming from pinned host
+memory and the results (row sums, norm) read back every step.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, each rank runs its own replica on its own GPU (replicas
+only: the path has no exchange step); value sums the ranks' work over the max
+time.  --impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+PREC = {"fp32_simt": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "fp8": 4}
+PRODUCTS = {"fp32_simt": 1, "bf16": 1, "bf16x3": 3, "bf16x6": 6, "fp8": 1}
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["source"] = "measured"
+        return d
+    d = dict(FALLBACK)
+    d["source"] = "fallback"
+    return d
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def profile_traffic(kernel_file: str, name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    src = os.path.join(ROOT, "paper_1806_01430_gb300", "csrc", kernel_file)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m and t):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != m.group(1):
+        return None
+    return float(t.group(1))
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---- CPU oracle baseline -------------------------------------------------------------------
+
+def oracle_sample(n: int, seed: int, target_s: float):
+    """Time the FP64 oracle on rows [0, r) of the program (GEMM rows, their scale-add,
+    transpose, row sums and norm contributions), r grown until ~target_s of work.
+    Returns (flops_equivalent_per_s, rows, seconds, threads)."""
+    import oracle
+    B = oracle.init_matrix(seed, 1, n, n)
+    r = 16
+    while True:
+        t0 = time.perf_counter()
+        A = oracle.init_matrix(seed, 0, n, n)[:r]
+        C0 = oracle.init_matrix(seed, 2, n, n)[:r]
+        C = oracle.gemm(A, B, C0, 1.5, 0.5)
+        D = oracle.axpy(C, 2.0, A)
+        E = oracle.transpose(D)
+        oracle.rowsum(E)
+        oracle.frobenius(E)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or r >= n:
+            return 2.0 * r * n * n / dt, r, dt, oracle.num_threads()
+        r = min(n, max(r * 2, int(r * target_s / max(dt, 1e-3) * 0.9)))
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    n = args.n
+    vals = []
+    rows = secs = thr = None
+    for i in range(args.warmup + args.steps):
+        v, rows, secs, thr = oracle_sample(n, W.SEED_CONFIG1, args.ref_target_s)
+        if i >= args.warmup:
+            vals.append(v)
+    val = statistics.median(vals) / 1e12
+    sample = f"rows 0..{rows - 1} of the n={n} six-loop program (GEMM rows + their scale-add/transpose/row-sum/norm)"
+    line = {"impl": "reference", "metric": "gemm_program_tflops", "value": val, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded counter hash)",
+            "config": {"workload": f"six_loop_n{n}_all_gpu", "n": n, "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": thr, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our arm --------------------------------------------------------------------------------------
+
+def our_arm(args, world, rank, local):
+    import torch
+
+    import paper_1806_01430_gb300 as gao
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    n, prec = args.n, args.prec
+    flops = 2.0 * n ** 3
+    prog = W.six_loop(n, W.SEED_CONFIG1 + rank, outputs=("C", "r", "f"))
+    p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream)
+    mask = (1 << prog.n_loops) - 1
+    gemm_loop = 1
+    for _ in range(args.warmup):
+        gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
+    torch.cuda.synchronize()
+    kern_ms, launches = [], 0
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
+            st = gao.prog_stats(p)
+            kern_ms.append(st[gemm_loop]["kernel_ms"])
+            launches += sum(s["launches"] for s in st)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = allmax(world, ms)
+    total_flops = allsum(world, flops)
+    value = total_flops / (ms / 1e3) / 1e12
+    clocks = clk.summary()
+
+    # accuracy of this run's GEMM against the oracle on sampled entries (no timing)
+    err = None
+    if rank == 0 and args.check:
+        import oracle
+        gao.prog_run(p, mask)
+        C = gao.prog_output(p, prog.index("C"))
+        rng = np.random.default_rng(1)
+        ii, jj = rng.integers(0, n, 128), rng.integers(0, n, 128)
+        want = oracle.gemm_init_entries(prog.seed, (0, 1, 2), False, n, n, n, 1.5, 0.5, ii, jj)
+        got = C[ii, jj].astype(np.float64)
+        err = math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
+    gao.prog_destroy(p)
+
+    # FP32 SIMT comparison (same program, same n)
+    simt = None
+    if args.compare_simt and prec != "fp32_simt":
+        q = gao.prog_from_workload(prog, gemm_prec=PREC["fp32_simt"], stream=stream)
+        for _ in range(2):
+            gao.prog_run(q, mask, gao.RUN_KEEP_DEVICE)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(3, args.steps // 4)
+        ks = []
+        e0.record(stream)
+        for _ in range(k):
+            gao.prog_run(q, mask, gao.RUN_KEEP_DEVICE)
+            ks.append(gao.prog_stats(q)[gemm_loop]["kernel_ms"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sms = e0.elapsed_time(e1) / k
+        simt = {"value": flops / (sms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": sms,
+                "gemm_kernel_tflops": flops / (statistics.mean(ks) / 1e3) / 1e12}
+        gao.prog_destroy(q)
+
+    # end to end: inputs from pinned host memory, results read back, every step
+    e2e = None
+    if args.e2e:
+        hp = W.host_input_program(n, prog.seed, outputs=("r", "f"))
+        q = gao.prog_from_workload(hp, gemm_prec=PREC[prec], stream=stream)
+        import oracle  # input generation only (seeded counter hash); not on the timed path
+        for nm, b in (("A", 0), ("B", 1), ("C0", 2)):
+            gao.prog_set_input(q, hp.index(nm), oracle.init_matrix(prog.seed, b, n, n).astype(np.float32))
+        m5 = (1 << hp.n_loops) - 1
+        for _ in range(2):
+            gao.prog_run(q, m5)
+        k = max(3, args.steps // 2)
+        walls = []
+        for _ in range(k):
+            walls.append(gao.prog_run(q, m5))
+        st = gao.prog_stats(q)
+        h2d = sum(s["h2d_bytes"] for s in st)
+        d2h = sum(s["d2h_bytes"] for s in st)
+        ew = statistics.median(walls)
+        e2e = {"value": allsum(world, flops) / allmax(world, ew) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ew * 1e3}
+        gao.prog_destroy(q)
+
+    if rank != 0:
+        return
+    pk = peaks()
+    gemm_ms = statistics.mean(kern_ms)
+    tc = prec != "fp32_simt"
+    if tc:
+        peak = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        if prec == "fp8":
+            peak *= 2.0
+        achieved = flops / (gemm_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_{prec}_n{n}.md"),
+                "kernel": f"gemm_tc ({prec})", "products": PRODUCTS[prec],
+                "hw_tflops": achieved * PRODUCTS[prec], "hw_frac": achieved * PRODUCTS[prec] / peak,
+                "peak_source": f"{pk['source']} bf16 sustained" + (" x2 (fp8 nominal ratio)" if prec == "fp8" else "")}
+    else:
+        mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        achieved = flops / (gemm_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": profile_traffic("gemm_simt.cu", f"gemm_simt_n{n}.md"), "kernel": "gemm_simt",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    cpu = None
+    if args.cpu_baseline:
+        v, rows, secs, thr = oracle_sample(n, W.SEED_CONFIG1, args.ref_target_s)
+        cpu = {"value": v / 1e12, "unit": "TFLOP/s", "cores": thr, "kind": "oracle",
+               "sample": f"rows 0..{rows - 1} of the n={n} program in FP64 ({secs:.1f} s)"}
+    line = {"metric": "gemm_program_tflops", "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x6->f32" if prec == "bf16x6" else prec,
+            "data": "synthetic (seeded counter hash, U[-1,1))",
+            "config": {"workload": f"six_loop_n{n}_all_gpu_{prec}", "n": n, "gene": f"{mask:06b}",
+                       "gemm": prec, "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "working set 7 x 64 MiB + split planes > 129 MB L2"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "gemm_rel_err_sampled": err, "fp32_simt": simt}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--prec", default="bf16x6", choices=list(PREC))
+    ap.add_argument("--no-check", dest="check", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-simt", dest="compare_simt", action="store_false")
+    ap.add_argument("--no-cpu", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--ref-target-s", type=float, default=8.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+    else:
+        our_arm(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -141,7 +141,7 @@ gao_status prog_device_ptr(gao_prog *p, int buf, void **dev_ptr);
 
 typedef struct gao_loop_stat {
     int32_t placement;  /* 1: ran on the GPU, 0: on the CPU                           */
-    int32_t _pad;
+    int32_t launches;   /* kernels of this library launched for the loop              */
     double device_ms;   /* GPU time of the loop's kernels (CUDA events)                */
     double kernel_ms;   /* GPU time of its main kernel only (GEMM: without the split)  */
     double cpu_ms;      /* host wall time of the CPU loop                              */

@@ -137,7 +137,11 @@ def run(time_of: Callable[[int], float], n_genes: int, pop: int, generations: in
         res.evaluations += ev
         res.cache_hits += hits
         res.populations.append(list(population))
-        ok = [t for t, f in zip(times, fit) if f > 0.0]
+        ok_sum, ok_n = 0.0, 0
+        for t, f in zip(times, fit):
+            if f > 0.0:  # plain left-to-right sum (Python's sum() is compensated)
+                ok_sum += t
+                ok_n += 1
         gbest_i = -1
         for i, (t, f) in enumerate(zip(times, fit)):
             if f > 0.0 and (gbest_i < 0 or t < times[gbest_i]):
@@ -147,7 +151,7 @@ def run(time_of: Callable[[int], float], n_genes: int, pop: int, generations: in
         res.history.append(GenRecord(
             best_mask=population[gbest_i] if gbest_i >= 0 else population[0],
             best_s=times[gbest_i] if gbest_i >= 0 else math.inf,
-            mean_s=(sum(ok) / len(ok)) if ok else math.inf,
+            mean_s=(ok_sum / ok_n) if ok_n else math.inf,
             evaluated=ev, cache_hits=hits))
         if g == generations - 1:
             break

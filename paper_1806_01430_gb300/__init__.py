@@ -1,0 +1,349 @@
+"""Python binding of libgao.so (include/gao.h): argument marshalling only.
+
+Every step of a program runs inside the C library (CUDA kernels for gene bits set
+to 1, the library's own OpenMP loops for bits set to 0).  There is no Python or
+CPU fallback: if the shared library is missing, importing the binding's entry
+points raises.  PyTorch is optional plumbing: ``prog_create`` accepts a
+``torch.cuda.Stream`` (or raw handle) and a device arena tensor.
+
+Names follow the C ABI: prog_create, prog_run, prog_output, prog_stats,
+ga_evaluate, ga_run, ga_run_table, prog_destroy, gao_last_error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgao.so")
+
+# enums (include/gao.h)
+GAO_OK, GAO_EINVAL, GAO_ENOMEM, GAO_ECUDA, GAO_ETIMEOUT, GAO_EDEVICE, GAO_ENODEV, GAO_ECPU = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EDEVICE", "ENODEV", "ECPU"]
+INIT, GEMM, AXPY, TRANSPOSE, ROWSUM, FROBENIUS, RELU, SQUARE, COLMAX, SUM = range(10)
+F32, F64 = 0, 1
+TEMP, INPUT, OUTPUT = 0, 1, 2
+FP32_SIMT, BF16, BF16X3, BF16X6, FP8 = range(5)
+PREC_NAMES = ["fp32_simt", "bf16", "bf16x3", "bf16x6", "fp8"]
+RUN_KEEP_DEVICE = 1
+MAX_IO = 4
+
+
+class gao_buffer(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("role", ctypes.c_int32)]
+
+
+class gao_loop(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("ins", ctypes.c_int32 * MAX_IO), ("outs", ctypes.c_int32 * MAX_IO),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("flags", ctypes.c_uint64)]
+
+
+class gao_opts(ctypes.Structure):
+    _fields_ = [("gemm_prec", ctypes.c_int32), ("kchunk", ctypes.c_int32), ("tile_cfg", ctypes.c_int32),
+                ("cpu_threads", ctypes.c_int32), ("seed", ctypes.c_uint64), ("timeout_s", ctypes.c_double),
+                ("stream", ctypes.c_void_p), ("dev_arena", ctypes.c_void_p), ("dev_arena_bytes", ctypes.c_uint64)]
+
+
+class gao_loop_stat(ctypes.Structure):
+    _fields_ = [("placement", ctypes.c_int32), ("launches", ctypes.c_int32), ("device_ms", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double), ("cpu_ms", ctypes.c_double), ("copy_ms", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64)]
+
+
+class gao_ga_params(ctypes.Structure):
+    _fields_ = [("pop", ctypes.c_int32), ("generations", ctypes.c_int32), ("pc", ctypes.c_double),
+                ("pm", ctypes.c_double), ("elite", ctypes.c_int32), ("mutation", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("timeout_s", ctypes.c_double)]
+
+
+class gao_ga_gen(ctypes.Structure):
+    _fields_ = [("best_mask", ctypes.c_uint64), ("best_s", ctypes.c_double), ("mean_s", ctypes.c_double),
+                ("evaluated", ctypes.c_int32), ("cache_hits", ctypes.c_int32)]
+
+
+class gao_ga_result(ctypes.Structure):
+    _fields_ = [("best_mask", ctypes.c_uint64), ("best_s", ctypes.c_double), ("evaluations", ctypes.c_int32),
+                ("cache_hits", ctypes.c_int32), ("history", ctypes.POINTER(gao_ga_gen)),
+                ("populations", ctypes.POINTER(ctypes.c_uint64))]
+
+
+# every entry point of include/gao.h: name -> (restype, argtypes)
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "prog_device_bytes": (ctypes.c_int, [ctypes.POINTER(gao_loop), ctypes.c_int, ctypes.POINTER(gao_buffer),
+                                         ctypes.c_int, ctypes.POINTER(gao_opts), ctypes.POINTER(ctypes.c_uint64)]),
+    "prog_create": (ctypes.c_int, [ctypes.POINTER(gao_loop), ctypes.c_int, ctypes.POINTER(gao_buffer), ctypes.c_int,
+                                   ctypes.POINTER(gao_opts), ctypes.POINTER(_P)]),
+    "prog_set_input": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint64]),
+    "prog_run": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]),
+    "prog_output": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(gao_buffer)]),
+    "prog_device_ptr": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "prog_stats": (ctypes.c_int, [_P, ctypes.POINTER(gao_loop_stat), ctypes.c_int]),
+    "prog_cache_clear": (ctypes.c_int, [_P]),
+    "prog_destroy": (None, [_P]),
+    "ga_evaluate": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int)]),
+    "ga_run": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(gao_ga_params),
+                              ctypes.POINTER(gao_ga_result)]),
+    "ga_run_table": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(gao_ga_params),
+                                    ctypes.POINTER(gao_ga_result)]),
+    "gao_last_error": (ctypes.c_char_p, []),
+    "gao_version": (ctypes.c_char_p, []),
+    "gao_selftest_device_wait": (ctypes.c_int, [ctypes.c_double, _P]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgao.so from the package directory (built by _build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no fallback implementation)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class GaoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().gao_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+
+
+def _check(st: int, where: str):
+    if st != GAO_OK:
+        raise GaoError(st, where)
+
+
+def gao_last_error() -> str:
+    return lib().gao_last_error().decode(errors="replace")
+
+
+def gao_version() -> str:
+    return lib().gao_version().decode()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _marshal(buffers, loops):
+    nb, nl = len(buffers), len(loops)
+    cb = (gao_buffer * nb)()
+    for i, b in enumerate(buffers):
+        cb[i].rows, cb[i].cols, cb[i].dtype, cb[i].role = int(b.rows), int(b.cols), int(b.dtype), int(b.role)
+    cl = (gao_loop * nl)()
+    for i, lp in enumerate(loops):
+        cl[i].kind = int(lp.kind)
+        ins = list(lp.ins) + [-1] * (MAX_IO - len(lp.ins))
+        outs = list(lp.outs) + [-1] * (MAX_IO - len(lp.outs))
+        for t in range(MAX_IO):
+            cl[i].ins[t] = ins[t]
+            cl[i].outs[t] = outs[t]
+        cl[i].alpha, cl[i].beta, cl[i].flags = float(lp.alpha), float(lp.beta), int(lp.flags)
+    return cb, nb, cl, nl
+
+
+def _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, arena_ptr, arena_bytes):
+    o = gao_opts()
+    o.gemm_prec, o.kchunk, o.tile_cfg, o.cpu_threads = int(gemm_prec), int(kchunk), int(tile_cfg), int(cpu_threads)
+    o.seed, o.timeout_s = int(seed), float(timeout_s)
+    o.stream = _stream_handle(stream)
+    o.dev_arena = arena_ptr
+    o.dev_arena_bytes = int(arena_bytes)
+    return o
+
+
+class Prog:
+    """Handle of a gao_prog (owning)."""
+
+    def __init__(self, handle, buffers, loops, arena=None):
+        self.handle = handle
+        self.buffers = list(buffers)
+        self.loops = list(loops)
+        self._arena = arena  # keeps a caller/torch arena alive
+
+    @property
+    def n_loops(self) -> int:
+        return len(self.loops)
+
+    def __del__(self):
+        try:
+            prog_destroy(self)
+        except Exception:
+            pass
+
+
+def prog_device_bytes(buffers, loops, seed=0, gemm_prec=FP32_SIMT, kchunk=0, tile_cfg=0) -> int:
+    cb, nb, cl, nl = _marshal(buffers, loops)
+    o = _opts(seed, gemm_prec, kchunk, tile_cfg, 0, 0.0, None, None, 0)
+    out = ctypes.c_uint64(0)
+    _check(lib().prog_device_bytes(cl, nl, cb, nb, ctypes.byref(o), ctypes.byref(out)), "prog_device_bytes")
+    return int(out.value)
+
+
+def prog_create(buffers, loops, seed: int = 0, gemm_prec: int = FP32_SIMT, kchunk: int = 0, tile_cfg: int = 0,
+                cpu_threads: int = 0, timeout_s: float = 0.0, stream=None, arena=None) -> Prog:
+    """Declare a program.  ``buffers``/``loops`` are sequences of objects with the
+    gao_buffer / gao_loop fields (e.g. workloads.Buffer / workloads.Loop).  ``arena``:
+    optional device memory (a torch uint8 CUDA tensor, or (ptr, bytes))."""
+    cb, nb, cl, nl = _marshal(buffers, loops)
+    ptr, nbytes, keep = None, 0, None
+    if arena is not None:
+        if isinstance(arena, tuple):
+            ptr, nbytes = int(arena[0]), int(arena[1])
+        else:
+            ptr, nbytes, keep = int(arena.data_ptr()), int(arena.numel() * arena.element_size()), arena
+    o = _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, ptr, nbytes)
+    h = ctypes.c_void_p(None)
+    _check(lib().prog_create(cl, nl, cb, nb, ctypes.byref(o), ctypes.byref(h)), "prog_create")
+    return Prog(h, buffers, loops, keep)
+
+
+def prog_from_workload(program, **kw) -> Prog:
+    """prog_create from a workloads.Program (uses its seed)."""
+    return prog_create(program.buffers, program.loops, seed=program.seed, **kw)
+
+
+def prog_set_input(p: Prog, buf: int, data: np.ndarray) -> None:
+    a = np.ascontiguousarray(data, dtype=np.float64 if p.buffers[buf].dtype == F64 else np.float32)
+    _check(lib().prog_set_input(p.handle, buf, a.ctypes.data_as(ctypes.c_void_p), a.nbytes), "prog_set_input")
+
+
+def prog_run(p: Prog, gene_mask: int, flags: int = 0) -> float:
+    """Run under a gene; returns the wall seconds of the run."""
+    s = ctypes.c_double(0.0)
+    _check(lib().prog_run(p.handle, ctypes.c_uint64(gene_mask), flags, ctypes.byref(s)), "prog_run")
+    return float(s.value)
+
+
+def prog_run_status(p: Prog, gene_mask: int, flags: int = 0):
+    """Like prog_run but returns (status, seconds) instead of raising."""
+    s = ctypes.c_double(0.0)
+    st = lib().prog_run(p.handle, ctypes.c_uint64(gene_mask), flags, ctypes.byref(s))
+    return int(st), float(s.value)
+
+
+def prog_output(p: Prog, buf: int) -> np.ndarray:
+    """Copy of buffer ``buf``'s host data after a run (float32 matrix or float64 scalar)."""
+    ptr = ctypes.c_void_p(None)
+    shp = gao_buffer()
+    _check(lib().prog_output(p.handle, buf, ctypes.byref(ptr), ctypes.byref(shp)), "prog_output")
+    n = shp.rows * shp.cols
+    ct = ctypes.c_double if shp.dtype == F64 else ctypes.c_float
+    arr = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ct)), shape=(max(n, 1),))[:n]
+    return arr.reshape(shp.rows, shp.cols).copy()
+
+
+def prog_device_ptr(p: Prog, buf: int) -> int:
+    ptr = ctypes.c_void_p(None)
+    _check(lib().prog_device_ptr(p.handle, buf, ctypes.byref(ptr)), "prog_device_ptr")
+    return int(ptr.value or 0)
+
+
+def prog_stats(p: Prog) -> List[Dict]:
+    arr = (gao_loop_stat * p.n_loops)()
+    _check(lib().prog_stats(p.handle, arr, p.n_loops), "prog_stats")
+    return [{k: getattr(s, k) for k, _ in gao_loop_stat._fields_} for s in arr]
+
+
+def prog_cache_clear(p: Prog) -> None:
+    _check(lib().prog_cache_clear(p.handle), "prog_cache_clear")
+
+
+def prog_destroy(p: Prog) -> None:
+    if p.handle is not None and p.handle.value:
+        lib().prog_destroy(p.handle)
+        p.handle = ctypes.c_void_p(None)
+
+
+def _handles(progs: Sequence[Prog]):
+    arr = (ctypes.c_void_p * len(progs))()
+    for i, p in enumerate(progs):
+        arr[i] = p.handle.value
+    return arr
+
+
+def ga_evaluate(progs: Sequence[Prog], population: Sequence[int]):
+    """Returns (fitness[pop], seconds[pop], cache_hits)."""
+    pop = len(population)
+    pa = (ctypes.c_uint64 * pop)(*[int(m) for m in population])
+    fit = (ctypes.c_double * pop)()
+    sec = (ctypes.c_double * pop)()
+    hits = ctypes.c_int(0)
+    _check(lib().ga_evaluate(_handles(progs), len(progs), pa, pop, fit, sec, ctypes.byref(hits)), "ga_evaluate")
+    return np.array(fit[:]), np.array(sec[:]), int(hits.value)
+
+
+@dataclass
+class GAResult:
+    best_mask: int
+    best_s: float
+    evaluations: int
+    cache_hits: int
+    history: List[dict]
+    populations: List[List[int]]
+
+
+def _params(pop, generations, pc, pm, seed, elite=1, mutation=0, timeout_s=0.0):
+    p = gao_ga_params()
+    p.pop, p.generations, p.pc, p.pm = int(pop), int(generations), float(pc), float(pm)
+    p.elite, p.mutation, p.seed, p.timeout_s = int(elite), int(mutation), int(seed), float(timeout_s)
+    return p
+
+
+def _result(params):
+    hist = (gao_ga_gen * params.generations)()
+    pops = (ctypes.c_uint64 * (params.generations * params.pop))()
+    r = gao_ga_result()
+    r.history = ctypes.cast(hist, ctypes.POINTER(gao_ga_gen))
+    r.populations = ctypes.cast(pops, ctypes.POINTER(ctypes.c_uint64))
+    return r, hist, pops
+
+
+def _unpack(r, hist, pops, params) -> GAResult:
+    h = [{k: getattr(g, k) for k, _ in gao_ga_gen._fields_} for g in hist]
+    P = [list(pops[g * params.pop:(g + 1) * params.pop]) for g in range(params.generations)]
+    return GAResult(int(r.best_mask), float(r.best_s), int(r.evaluations), int(r.cache_hits), h, P)
+
+
+def ga_run(progs: Sequence[Prog], pop=12, generations=12, pc=0.9, pm=0.05, seed=0, elite=1, mutation=0,
+           timeout_s=0.0) -> GAResult:
+    params = _params(pop, generations, pc, pm, seed, elite, mutation, timeout_s)
+    r, hist, pops = _result(params)
+    _check(lib().ga_run(_handles(progs), len(progs), ctypes.byref(params), ctypes.byref(r)), "ga_run")
+    return _unpack(r, hist, pops, params)
+
+
+def ga_run_table(times: np.ndarray, n_genes: int, pop=12, generations=12, pc=0.9, pm=0.05, seed=0, elite=1,
+                 mutation=0) -> GAResult:
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    assert t.size >= (1 << n_genes)
+    params = _params(pop, generations, pc, pm, seed, elite, mutation, 0.0)
+    r, hist, pops = _result(params)
+    _check(lib().ga_run_table(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n_genes, ctypes.byref(params),
+                              ctypes.byref(r)), "ga_run_table")
+    return _unpack(r, hist, pops, params)
+
+
+def gao_selftest_device_wait(limit_s: float = 0.2, stream=None) -> int:
+    """Returns the status (GAO_ETIMEOUT is the expected outcome)."""
+    return int(lib().gao_selftest_device_wait(float(limit_s), _stream_handle(stream)))

@@ -1,0 +1,226 @@
+// CPU side of every loop (gene bit 0): binary32, OpenMP over the host cores.
+//
+// These are the loops as a CPU program would run them when the gene leaves them on
+// the host.  Loops whose GPU version is exact (INIT, AXPY, TRANSPOSE, RELU, SQUARE,
+// COLMAX) produce bit-identical results here; the others agree within rounding.
+// Every loop polls a deadline between blocks of work so that a run over its time
+// budget stops early (the run then reports a timeout).
+#include <math.h>
+#include <omp.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <vector>
+
+#include "gao_internal.h"
+
+namespace gao {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+namespace {
+
+inline bool expired(CpuCtx& c) {
+    if (c.deadline > 0.0 && now_s() > c.deadline) {
+        __atomic_store_n(&c.timed_out, true, __ATOMIC_RELAXED);
+        return true;
+    }
+    return false;
+}
+
+inline int nthreads(const CpuCtx& c) { return c.threads > 0 ? c.threads : omp_get_max_threads(); }
+
+}  // namespace
+
+void cpu_init(float* out, int64_t rows, int64_t cols, uint64_t seed, uint32_t buf, bool rowscale, CpuCtx& c) {
+    std::atomic<bool> stop{false};
+#pragma omp parallel for schedule(static) num_threads(nthreads(c))
+    for (int64_t i = 0; i < rows; ++i) {
+        if (stop.load(std::memory_order_relaxed)) continue;
+        if ((i & 255) == 0 && expired(c)) stop = true;
+        const int e = rowscale ? row_exponent(seed, i) : 0;
+        float* o = out + i * cols;
+        for (int64_t j = 0; j < cols; ++j) {
+            float v = init_value(seed, buf, (uint64_t)(i * cols + j));
+            o[j] = rowscale ? ldexpf(v, e) : v;
+        }
+    }
+}
+
+// C = alpha*A@B + beta*C0.  Work is split into tasks of (up to 512 rows) x (up to
+// 256 columns); each task walks K in chunks of `kchunk`, keeping a 256 x kchunk
+// panel of B hot in cache while 16-row register/L1 blocks of the chunk sum are
+// formed and then added into the task's binary32 outer sum.
+void cpu_gemm(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K, float alpha,
+              float beta, int kchunk, CpuCtx& c) {
+    constexpr int64_t JT = 256, RB = 16, RS = 512;
+    const int64_t kc = kchunk > 0 ? kchunk : 256;
+    const int64_t ntj = (N + JT - 1) / JT, nts = (M + RS - 1) / RS;
+    std::atomic<bool> stop{false};
+#pragma omp parallel num_threads(nthreads(c))
+    {
+        std::vector<float> outer((size_t)RS * JT), acc((size_t)RB * JT);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t task = 0; task < ntj * nts; ++task) {
+            if (stop.load(std::memory_order_relaxed)) continue;
+            const int64_t j0 = (task % ntj) * JT, i0 = (task / ntj) * RS;
+            const int64_t jn = std::min(JT, N - j0), in = std::min(RS, M - i0);
+            std::fill(outer.begin(), outer.begin() + in * JT, 0.0f);
+            for (int64_t k0 = 0; k0 < K; k0 += kc) {
+                if (expired(c)) {
+                    stop = true;
+                    break;
+                }
+                const int64_t k1 = std::min(K, k0 + kc);
+                for (int64_t r0 = 0; r0 < in; r0 += RB) {
+                    const int64_t rn = std::min(RB, in - r0);
+                    std::fill(acc.begin(), acc.begin() + rn * JT, 0.0f);
+                    for (int64_t k = k0; k < k1; ++k) {
+                        const float* b = B + k * N + j0;
+                        for (int64_t r = 0; r < rn; ++r) {
+                            const float a = A[(i0 + r0 + r) * K + k];
+                            float* ar = acc.data() + r * JT;
+                            for (int64_t j = 0; j < jn; ++j) ar[j] = fmaf(a, b[j], ar[j]);
+                        }
+                    }
+                    for (int64_t r = 0; r < rn; ++r) {
+                        float* orow = outer.data() + (r0 + r) * JT;
+                        const float* ar = acc.data() + r * JT;
+                        for (int64_t j = 0; j < jn; ++j) orow[j] += ar[j];
+                    }
+                }
+            }
+            if (stop.load(std::memory_order_relaxed)) continue;
+            for (int64_t r = 0; r < in; ++r) {
+                const float* orow = outer.data() + r * JT;
+                const float* c0 = C0 + (i0 + r) * N + j0;
+                float* crow = C + (i0 + r) * N + j0;
+                for (int64_t j = 0; j < jn; ++j) {
+                    float v = alpha * orow[j];
+                    if (beta != 0.0f) v = fmaf(beta, c0[j], v);
+                    crow[j] = v;
+                }
+            }
+        }
+    }
+}
+
+void cpu_axpy(float* out, const float* x, float alpha, const float* y, int64_t n, CpuCtx& c) {
+    const int64_t blk = 1 << 20;
+    std::atomic<bool> stop{false};
+#pragma omp parallel for schedule(static) num_threads(nthreads(c))
+    for (int64_t b = 0; b < (n + blk - 1) / blk; ++b) {
+        if (stop.load(std::memory_order_relaxed)) continue;
+        if (expired(c)) {
+            stop = true;
+            continue;
+        }
+        const int64_t e = std::min(n, (b + 1) * blk);
+        for (int64_t i = b * blk; i < e; ++i) out[i] = fmaf(alpha, y[i], x[i]);
+    }
+}
+
+void cpu_transpose(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx& c) {
+    constexpr int64_t T = 64;
+    std::atomic<bool> stop{false};
+    const int64_t tr = (rows + T - 1) / T, tc = (cols + T - 1) / T;
+#pragma omp parallel for schedule(static) num_threads(nthreads(c))
+    for (int64_t t = 0; t < tr * tc; ++t) {
+        if (stop.load(std::memory_order_relaxed)) continue;
+        if ((t & 63) == 0 && expired(c)) {
+            stop = true;
+            continue;
+        }
+        const int64_t r0 = (t / tc) * T, c0 = (t % tc) * T;
+        const int64_t r1 = std::min(rows, r0 + T), c1 = std::min(cols, c0 + T);
+        for (int64_t i = r0; i < r1; ++i)
+            for (int64_t j = c0; j < c1; ++j) out[j * rows + i] = in[i * cols + j];
+    }
+}
+
+void cpu_rowsum(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx& c) {
+    std::atomic<bool> stop{false};
+#pragma omp parallel for schedule(static) num_threads(nthreads(c))
+    for (int64_t i = 0; i < rows; ++i) {
+        if (stop.load(std::memory_order_relaxed)) continue;
+        if ((i & 255) == 0 && expired(c)) {
+            stop = true;
+            continue;
+        }
+        float s = 0.0f;
+        const float* r = in + i * cols;
+        for (int64_t j = 0; j < cols; ++j) s += r[j];
+        out[i] = s;
+    }
+}
+
+namespace {
+template <bool SQUARES>
+double cpu_reduce64(const float* in, int64_t n, CpuCtx& c) {
+    const int nt = nthreads(c);
+    std::vector<double> part((size_t)nt, 0.0);
+    std::atomic<bool> stop{false};
+#pragma omp parallel num_threads(nt)
+    {
+        const int t = omp_get_thread_num(), T = omp_get_num_threads();
+        const int64_t b = n * t / T, e = n * (t + 1) / T;
+        double s = 0.0;
+        for (int64_t i0 = b; i0 < e && !stop.load(std::memory_order_relaxed); i0 += (1 << 20)) {
+            if (expired(c)) {
+                stop = true;
+                break;
+            }
+            const int64_t i1 = std::min(e, i0 + (int64_t)(1 << 20));
+            for (int64_t i = i0; i < i1; ++i) s += SQUARES ? (double)in[i] * (double)in[i] : (double)in[i];
+        }
+        part[(size_t)t] = s;
+    }
+    double s = 0.0;
+    for (double p : part) s += p;
+    return SQUARES ? sqrt(s) : s;
+}
+}  // namespace
+
+double cpu_frobenius(const float* in, int64_t n, CpuCtx& c) { return cpu_reduce64<true>(in, n, c); }
+double cpu_sum(const float* in, int64_t n, CpuCtx& c) { return cpu_reduce64<false>(in, n, c); }
+
+void cpu_relu(float* out, const float* in, int64_t n, CpuCtx& c) {
+    (void)c;
+#pragma omp parallel for schedule(static) num_threads(nthreads(c))
+    for (int64_t i = 0; i < n; ++i) out[i] = in[i] > 0.0f ? in[i] : 0.0f;
+}
+
+void cpu_square(float* out, const float* in, int64_t n, CpuCtx& c) {
+#pragma omp parallel for schedule(static) num_threads(nthreads(c))
+    for (int64_t i = 0; i < n; ++i) out[i] = in[i] * in[i];
+}
+
+void cpu_colmax(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx& c) {
+    const int nt = nthreads(c);
+    std::vector<uint32_t> keys((size_t)nt * (size_t)cols, 0u);
+#pragma omp parallel num_threads(nt)
+    {
+        const int t = omp_get_thread_num(), T = omp_get_num_threads();
+        uint32_t* k = keys.data() + (size_t)t * cols;
+        const int64_t b = rows * t / T, e = rows * (t + 1) / T;
+        for (int64_t i = b; i < e; ++i) {
+            const uint32_t* r = reinterpret_cast<const uint32_t*>(in + i * cols);
+            for (int64_t j = 0; j < cols; ++j) k[j] = std::max(k[j], fmax_key(r[j]));
+        }
+    }
+    for (int64_t j = 0; j < cols; ++j) {
+        uint32_t m = 0u;
+        for (int t = 0; t < nt; ++t) m = std::max(m, keys[(size_t)t * cols + j]);
+        uint32_t bits = fmax_unkey(m);
+        float v;
+        memcpy(&v, &bits, 4);
+        out[j] = rows > 0 ? v : -INFINITY;
+    }
+}
+
+}  // namespace gao

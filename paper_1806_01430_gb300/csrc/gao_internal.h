@@ -1,0 +1,129 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gao.h"
+
+namespace gao {
+
+// ---- error reporting --------------------------------------------------------
+void set_error(const std::string& msg);
+gao_status fail(gao_status st, const std::string& msg);
+gao_status cuda_fail(cudaError_t e, const char* what);
+
+#define GAO_CUDA_TRY(expr)                                             \
+    do {                                                               \
+        cudaError_t _e = (expr);                                       \
+        if (_e != cudaSuccess) return ::gao::cuda_fail(_e, #expr);     \
+    } while (0)
+
+// Device error word codes (written by kernels, read by the host after a run).
+enum : int {
+    DEV_OK = 0,
+    DEV_WAIT_TIMEOUT = 1,  // a bounded mbarrier / flag wait expired
+    DEV_BAD_SHAPE = 2,     // a kernel saw a shape it cannot handle
+};
+
+// ---- SplitMix64 counter hash (Steele, Lea & Flood 2014) -----------------------
+// gamma is the golden-ratio increment; the finaliser is the published
+// xor-shift-multiply mix (shifts 30, 27, 31).
+__host__ __device__ inline uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__host__ __device__ inline uint64_t sm64_hash(uint64_t state) { return sm64_mix(state + 0x9E3779B97F4A7C15ULL); }
+
+// Element key of the INIT loop: seed bits 40.., buffer id bits 36..39, index bits 0..35.
+__host__ __device__ inline uint64_t init_key(uint64_t seed, uint32_t buf, uint64_t idx) {
+    return (seed << 40) ^ ((uint64_t)buf << 36) ^ idx;
+}
+// U[-1,1) binary32 value: 24-bit integer times 2^-23, minus one (exact).
+__host__ __device__ inline float init_value(uint64_t seed, uint32_t buf, uint64_t idx) {
+    const int32_t u24 = (int32_t)(sm64_hash(init_key(seed, buf, idx)) >> 40);
+    return (float)(u24 - (1 << 23)) * (1.0f / 8388608.0f);
+}
+// Power-of-two exponent in [-10, 10] of row `row`'s factor for row-scaled inputs:
+// round((sum of twelve 24-bit uniforms / 2^24 - 6) * 10/3), in integer arithmetic.
+__host__ __device__ inline int row_exponent(uint64_t seed, int64_t row) {
+    int64_t s = 0;
+    for (int t = 0; t < 12; ++t) s += (int64_t)(sm64_hash(init_key(seed, 15u, (uint64_t)(row * 12 + t))) >> 40);
+    const int64_t two24 = 1LL << 24;
+    const int64_t num = (s - 6 * two24) * 10, den = 3 * two24;
+    int64_t a = 2 * num + den, b = 2 * den;
+    int64_t q = a / b;
+    if ((a % b != 0) && (a < 0)) q -= 1;  // floor division (b > 0)
+    return (int)(q < -10 ? -10 : (q > 10 ? 10 : q));
+}
+
+// Order-preserving key of a binary32 value for max reductions with integer atomics
+// (+0 above -0; NaN above +inf).  Used identically by the CPU loop.
+__host__ __device__ inline uint32_t fmax_key(uint32_t bits) {
+    return (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+}
+__host__ __device__ inline uint32_t fmax_unkey(uint32_t key) {
+    return (key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key;
+}
+
+// ---- device info -------------------------------------------------------------
+int sm_count();
+
+// ---- kernel launchers (all asynchronous on `st`) -------------------------------
+struct ReduceScratch {
+    double* partials;   // >= reduce_blocks() doubles
+    unsigned* counter;  // one zero-initialised word, reset by the kernel
+};
+int reduce_blocks();
+
+cudaError_t launch_row_exponents(int8_t* e, int64_t rows, uint64_t seed, cudaStream_t st);
+cudaError_t launch_init(float* out, int64_t rows, int64_t cols, uint64_t seed, uint32_t buf, const int8_t* rowexp,
+                        cudaStream_t st);
+cudaError_t launch_axpy(float* out, const float* x, float alpha, const float* y, int64_t n, cudaStream_t st);
+cudaError_t launch_transpose(float* out, const float* in, int64_t rows, int64_t cols, cudaStream_t st);
+cudaError_t launch_rowsum(float* out, const float* in, int64_t rows, int64_t cols, cudaStream_t st);
+cudaError_t launch_frobenius(double* out, const float* in, int64_t n, ReduceScratch rs, cudaStream_t st);
+cudaError_t launch_sum(double* out, const float* in, int64_t n, ReduceScratch rs, cudaStream_t st);
+cudaError_t launch_relu(float* out, const float* in, int64_t n, cudaStream_t st);
+cudaError_t launch_square(float* out, const float* in, int64_t n, cudaStream_t st);
+cudaError_t launch_colmax(float* out, const float* in, int64_t rows, int64_t cols, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_wait_selftest(int* flag, int* err, double limit_s, cudaStream_t st);
+
+// FP32 SIMT GEMM: C = alpha*A@B + beta*C0 (C may alias C0).  kchunk: K elements per
+// binary32 partial sum (<= 0: one sum over all of K).
+cudaError_t launch_gemm_simt(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
+                             int64_t K, float alpha, float beta, int kchunk, cudaStream_t st);
+
+// Tensor-core GEMM (split operands + tcgen05).  Scratch layout and size are given
+// by tc_scratch_bytes; `err` receives DEV_* codes.
+struct TcEvents {
+    cudaEvent_t k0 = nullptr, k1 = nullptr;  // recorded around the MMA kernel if non-null
+    int launches = 0;                         // out: kernels launched
+};
+size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K);
+cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M,
+                           int64_t N, int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
+                           size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why);
+
+// ---- CPU loops (binary32, OpenMP) ------------------------------------------------
+struct CpuCtx {
+    int threads;
+    double deadline;  // steady-clock seconds; 0 = none
+    bool timed_out;
+};
+double now_s();
+void cpu_init(float* out, int64_t rows, int64_t cols, uint64_t seed, uint32_t buf, bool rowscale, CpuCtx& c);
+void cpu_gemm(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K, float alpha,
+              float beta, int kchunk, CpuCtx& c);
+void cpu_axpy(float* out, const float* x, float alpha, const float* y, int64_t n, CpuCtx& c);
+void cpu_transpose(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx& c);
+void cpu_rowsum(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx& c);
+double cpu_frobenius(const float* in, int64_t n, CpuCtx& c);
+double cpu_sum(const float* in, int64_t n, CpuCtx& c);
+void cpu_relu(float* out, const float* in, int64_t n, CpuCtx& c);
+void cpu_square(float* out, const float* in, int64_t n, CpuCtx& c);
+void cpu_colmax(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx& c);
+
+}  // namespace gao

@@ -1,0 +1,434 @@
+// Memory-bound loops of the program on the GPU: INIT, AXPY (scale-add), TRANSPOSE,
+// ROWSUM, FROBENIUS, SUM, RELU, SQUARE, COLMAX.
+//
+// All kernels read and write row-major binary32 with 128-bit accesses where the
+// shape allows (element count or row length a multiple of 4), grid-stride over a
+// grid sized in multiples of the SM count, and keep every reduction in a fixed
+// order so that results are identical from run to run (no floating-point atomics).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gao_internal.h"
+
+namespace gao {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBlocksPerSm = 8;
+
+int grid_for(int64_t work_items) {
+    const int64_t cap = (int64_t)sm_count() * kBlocksPerSm;
+    int64_t g = (work_items + kThreads - 1) / kThreads;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ---- INIT ---------------------------------------------------------------------------
+
+__global__ void row_exponents_kernel(int8_t* e, int64_t rows, uint64_t seed) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
+        e[r] = (int8_t)row_exponent(seed, r);
+}
+
+// out[i] = init_value(seed, buf, i) (times 2^e_row).  Four consecutive elements per
+// thread and iteration, stored as one float4 when the row length is a multiple of 4.
+__global__ void init_kernel(float* __restrict__ out, int64_t rows, int64_t cols, uint64_t seed, uint32_t buf,
+                            const int8_t* __restrict__ rowexp) {
+    const int64_t n = rows * cols;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    const bool vec = (cols % 4 == 0) && aligned16(out);
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; i < n; i += stride) {
+        if (vec) {
+            float4 v;
+            v.x = init_value(seed, buf, (uint64_t)i);
+            v.y = init_value(seed, buf, (uint64_t)i + 1);
+            v.z = init_value(seed, buf, (uint64_t)i + 2);
+            v.w = init_value(seed, buf, (uint64_t)i + 3);
+            if (rowexp) {
+                const int e = rowexp[i / cols];
+                v.x = ldexpf(v.x, e);
+                v.y = ldexpf(v.y, e);
+                v.z = ldexpf(v.z, e);
+                v.w = ldexpf(v.w, e);
+            }
+            *reinterpret_cast<float4*>(out + i) = v;
+        } else {
+            for (int q = 0; q < 4 && i + q < n; ++q) {
+                float v = init_value(seed, buf, (uint64_t)(i + q));
+                if (rowexp) v = ldexpf(v, rowexp[(i + q) / cols]);
+                out[i + q] = v;
+            }
+        }
+    }
+}
+
+// ---- element-wise -------------------------------------------------------------------
+
+enum class Ew { Axpy, Relu, Square };
+
+template <Ew OP>
+__device__ __forceinline__ float ew_apply(float x, float y, float alpha) {
+    if constexpr (OP == Ew::Axpy) return fmaf(alpha, y, x);  // x + alpha*y, one rounding
+    else if constexpr (OP == Ew::Relu) return x > 0.0f ? x : 0.0f;
+    else return x * x;
+}
+
+template <Ew OP>
+__global__ void ew_kernel(float* __restrict__ out, const float* __restrict__ x, const float* __restrict__ y,
+                          float alpha, int64_t n) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const bool vec = aligned16(out) && aligned16(x) && (y == nullptr || aligned16(y));
+    int64_t nvec = vec ? n / 4 : 0;
+    if (vec) {
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        const float4* y4 = reinterpret_cast<const float4*>(y);
+        float4* o4 = reinterpret_cast<float4*>(out);
+        // two independent 16-byte loads per operand in flight per thread
+        int64_t i = tid;
+        for (; i + nthreads < nvec; i += 2 * nthreads) {
+            float4 a0 = x4[i], a1 = x4[i + nthreads];
+            float4 b0 = make_float4(0, 0, 0, 0), b1 = b0;
+            if (OP == Ew::Axpy) {
+                b0 = y4[i];
+                b1 = y4[i + nthreads];
+            }
+            float4 r0, r1;
+            r0.x = ew_apply<OP>(a0.x, b0.x, alpha);
+            r0.y = ew_apply<OP>(a0.y, b0.y, alpha);
+            r0.z = ew_apply<OP>(a0.z, b0.z, alpha);
+            r0.w = ew_apply<OP>(a0.w, b0.w, alpha);
+            r1.x = ew_apply<OP>(a1.x, b1.x, alpha);
+            r1.y = ew_apply<OP>(a1.y, b1.y, alpha);
+            r1.z = ew_apply<OP>(a1.z, b1.z, alpha);
+            r1.w = ew_apply<OP>(a1.w, b1.w, alpha);
+            o4[i] = r0;
+            o4[i + nthreads] = r1;
+        }
+        for (; i < nvec; i += nthreads) {
+            float4 a0 = x4[i];
+            float4 b0 = make_float4(0, 0, 0, 0);
+            if (OP == Ew::Axpy) b0 = y4[i];
+            float4 r0;
+            r0.x = ew_apply<OP>(a0.x, b0.x, alpha);
+            r0.y = ew_apply<OP>(a0.y, b0.y, alpha);
+            r0.z = ew_apply<OP>(a0.z, b0.z, alpha);
+            r0.w = ew_apply<OP>(a0.w, b0.w, alpha);
+            o4[i] = r0;
+        }
+    }
+    for (int64_t i = nvec * 4 + tid; i < n; i += nthreads)
+        out[i] = ew_apply<OP>(x[i], OP == Ew::Axpy ? y[i] : 0.0f, alpha);
+}
+
+// ---- TRANSPOSE -------------------------------------------------------------------------
+
+// 64x64 tile through shared memory; 16-byte loads along input rows and 16-byte
+// stores along output rows.  Needs rows % 4 == 0 and cols % 4 == 0.
+__global__ void __launch_bounds__(256) transpose_vec_kernel(float* __restrict__ out, const float* __restrict__ in,
+                                                            int64_t rows, int64_t cols) {
+    __shared__ float tile[64][65];
+    const int t = threadIdx.x;
+    const int c4 = t & 15, r = t >> 4;
+    const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t gr = r0 + r + 16 * k, gc = c0 + 4 * c4;
+        float4 v = make_float4(0, 0, 0, 0);
+        if (gr < rows && gc < cols) v = *reinterpret_cast<const float4*>(in + gr * cols + gc);
+        tile[r + 16 * k][4 * c4 + 0] = v.x;
+        tile[r + 16 * k][4 * c4 + 1] = v.y;
+        tile[r + 16 * k][4 * c4 + 2] = v.z;
+        tile[r + 16 * k][4 * c4 + 3] = v.w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int orow = r + 16 * k;  // output row = input column c0 + orow
+        const int64_t gr = c0 + orow, gc = r0 + 4 * c4;
+        if (gr < cols && gc < rows) {
+            float4 v;
+            v.x = tile[4 * c4 + 0][orow];
+            v.y = tile[4 * c4 + 1][orow];
+            v.z = tile[4 * c4 + 2][orow];
+            v.w = tile[4 * c4 + 3][orow];
+            *reinterpret_cast<float4*>(out + gr * rows + gc) = v;
+        }
+    }
+}
+
+// 32x32 tile, scalar accesses, any shape.
+__global__ void __launch_bounds__(256) transpose_scalar_kernel(float* __restrict__ out, const float* __restrict__ in,
+                                                               int64_t rows, int64_t cols) {
+    __shared__ float tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t gr = r0 + k, gc = c0 + tx;
+        if (gr < rows && gc < cols) tile[k][tx] = in[gr * cols + gc];
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t gr = c0 + k, gc = r0 + tx;  // output (cols x rows)
+        if (gr < cols && gc < rows) out[gr * rows + gc] = tile[tx][k];
+    }
+}
+
+// ---- ROWSUM ------------------------------------------------------------------------------
+
+// One warp per row.  Lane l adds the 4 entries of float4 l, l+32, ... in order; the
+// 32 lane sums are combined by a fixed butterfly.  Deterministic.
+__global__ void rowsum_kernel(float* __restrict__ out, const float* __restrict__ in, int64_t rows, int64_t cols) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool vec = (cols % 4 == 0) && aligned16(in);
+    for (int64_t r = warp; r < rows; r += nwarps) {
+        const float* row = in + r * cols;
+        float s = 0.0f;
+        if (vec) {
+            const float4* row4 = reinterpret_cast<const float4*>(row);
+            const int64_t n4 = cols / 4;
+            int64_t j = lane;
+            for (; j + 96 < n4; j += 128) {
+                const float4 a = row4[j], b = row4[j + 32], c = row4[j + 64], d = row4[j + 96];
+                s += ((a.x + a.y) + (a.z + a.w));
+                s += ((b.x + b.y) + (b.z + b.w));
+                s += ((c.x + c.y) + (c.z + c.w));
+                s += ((d.x + d.y) + (d.z + d.w));
+            }
+            for (; j < n4; j += 32) {
+                const float4 a = row4[j];
+                s += ((a.x + a.y) + (a.z + a.w));
+            }
+        } else {
+            for (int64_t j = lane; j < cols; j += 32) s += row[j];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) out[r] = s;
+    }
+}
+
+// ---- FROBENIUS / SUM -------------------------------------------------------------------------
+
+// Each thread forms a binary32 partial over one float4 (sum of squares, or sum),
+// widens it to binary64 and accumulates in binary64; blocks reduce in a fixed tree;
+// the last block to finish adds the block partials in index order.  Binary64 work is
+// one add per 4 elements, so the loop stays bound by HBM on a part with a low
+// binary64 rate.
+template <bool SQUARES>
+__global__ void __launch_bounds__(256) reduce64_kernel(double* __restrict__ out, const float* __restrict__ in,
+                                                       int64_t n, double* __restrict__ partials,
+                                                       unsigned* __restrict__ counter) {
+    __shared__ double wsum[8];
+    __shared__ bool last;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    double acc = 0.0;
+    const bool vec = aligned16(in);
+    const int64_t nvec = vec ? n / 4 : 0;
+    if (vec) {
+        const float4* in4 = reinterpret_cast<const float4*>(in);
+        int64_t i = tid;
+        for (; i + nthreads < nvec; i += 2 * nthreads) {
+            const float4 a = in4[i], b = in4[i + nthreads];
+            float pa, pb;
+            if (SQUARES) {
+                pa = fmaf(a.w, a.w, fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x)));
+                pb = fmaf(b.w, b.w, fmaf(b.z, b.z, fmaf(b.y, b.y, b.x * b.x)));
+            } else {
+                pa = (a.x + a.y) + (a.z + a.w);
+                pb = (b.x + b.y) + (b.z + b.w);
+            }
+            acc += (double)pa;
+            acc += (double)pb;
+        }
+        for (; i < nvec; i += nthreads) {
+            const float4 a = in4[i];
+            float pa = SQUARES ? fmaf(a.w, a.w, fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x))) : (a.x + a.y) + (a.z + a.w);
+            acc += (double)pa;
+        }
+    }
+    for (int64_t i = nvec * 4 + tid; i < n; i += nthreads) {
+        const float v = in[i];
+        acc += SQUARES ? (double)v * (double)v : (double)v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += wsum[w];
+        partials[blockIdx.x] = b;
+        __threadfence();
+        const unsigned ticket = atomicAdd(counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double*)partials)[b];
+        *out = SQUARES ? sqrt(s) : s;
+        *counter = 0u;  // ready for the next launch on this stream
+    }
+}
+
+// ---- COLMAX ------------------------------------------------------------------------------------
+
+// Column maxima via order-preserving integer keys and atomicMax (max is exact and
+// order-free, so the result is deterministic).  Thread = 4 consecutive columns of
+// a chunk of rows.
+__global__ void colmax_keys_kernel(uint32_t* __restrict__ keys, const float* __restrict__ in, int64_t rows,
+                                   int64_t cols, int64_t rows_per_chunk) {
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4;
+    if (c >= cols) return;
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+    const int64_t r1 = r0 + rows_per_chunk < rows ? r0 + rows_per_chunk : rows;
+    uint32_t m[4] = {0u, 0u, 0u, 0u};
+    const bool vec = (cols % 4 == 0) && aligned16(in);
+    for (int64_t r = r0; r < r1; ++r) {
+        if (vec) {
+            const float4 v = *reinterpret_cast<const float4*>(in + r * cols + c);
+            m[0] = max(m[0], fmax_key(__float_as_uint(v.x)));
+            m[1] = max(m[1], fmax_key(__float_as_uint(v.y)));
+            m[2] = max(m[2], fmax_key(__float_as_uint(v.z)));
+            m[3] = max(m[3], fmax_key(__float_as_uint(v.w)));
+        } else {
+            for (int q = 0; q < 4 && c + q < cols; ++q) m[q] = max(m[q], fmax_key(__float_as_uint(in[r * cols + c + q])));
+        }
+    }
+    for (int q = 0; q < 4 && c + q < cols; ++q)
+        if (r1 > r0) atomicMax(keys + c + q, m[q]);
+}
+
+__global__ void colmax_decode_kernel(float* __restrict__ out, const uint32_t* __restrict__ keys, int64_t cols,
+                                     int64_t rows) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cols; c += (int64_t)gridDim.x * blockDim.x)
+        out[c] = rows > 0 ? __uint_as_float(fmax_unkey(keys[c])) : -INFINITY;
+}
+
+// ---- device-wait self test --------------------------------------------------------------------
+
+__global__ void wait_selftest_kernel(volatile int* flag, int* err, unsigned long long limit_ns) {
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        if (*flag != 0) return;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns) {
+            atomicExch(err, DEV_WAIT_TIMEOUT);
+            return;
+        }
+        __nanosleep(1000);
+    }
+}
+
+}  // namespace
+
+int reduce_blocks() { return sm_count() * 4; }
+
+cudaError_t launch_row_exponents(int8_t* e, int64_t rows, uint64_t seed, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    row_exponents_kernel<<<grid_for(rows), kThreads, 0, st>>>(e, rows, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(float* out, int64_t rows, int64_t cols, uint64_t seed, uint32_t buf, const int8_t* rowexp,
+                        cudaStream_t st) {
+    const int64_t n = rows * cols;
+    if (n <= 0) return cudaSuccess;
+    init_kernel<<<grid_for((n + 3) / 4), kThreads, 0, st>>>(out, rows, cols, seed, buf, rowexp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(float* out, const float* x, float alpha, const float* y, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    ew_kernel<Ew::Axpy><<<grid_for((n + 7) / 8), kThreads, 0, st>>>(out, x, y, alpha, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relu(float* out, const float* in, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    ew_kernel<Ew::Relu><<<grid_for((n + 7) / 8), kThreads, 0, st>>>(out, in, nullptr, 0.0f, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_square(float* out, const float* in, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    ew_kernel<Ew::Square><<<grid_for((n + 7) / 8), kThreads, 0, st>>>(out, in, nullptr, 0.0f, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(float* out, const float* in, int64_t rows, int64_t cols, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const bool vec = (rows % 4 == 0) && (cols % 4 == 0) && (((uintptr_t)in | (uintptr_t)out) & 15u) == 0;
+    if (vec) {
+        dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
+        if (grid.y > 65535u) return cudaErrorInvalidValue;
+        transpose_vec_kernel<<<grid, 256, 0, st>>>(out, in, rows, cols);
+    } else {
+        dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+        if (grid.y > 65535u) return cudaErrorInvalidValue;
+        transpose_scalar_kernel<<<grid, 256, 0, st>>>(out, in, rows, cols);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowsum(float* out, const float* in, int64_t rows, int64_t cols, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    if (cols <= 0) return cudaMemsetAsync(out, 0, (size_t)rows * sizeof(float), st);
+    const int64_t threads = rows * 32;
+    int64_t g = (threads + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sm_count() * kBlocksPerSm;
+    if (g > cap) g = cap;
+    rowsum_kernel<<<(unsigned)g, kThreads, 0, st>>>(out, in, rows, cols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frobenius(double* out, const float* in, int64_t n, ReduceScratch rs, cudaStream_t st) {
+    reduce64_kernel<true><<<reduce_blocks(), 256, 0, st>>>(out, in, n < 0 ? 0 : n, rs.partials, rs.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum(double* out, const float* in, int64_t n, ReduceScratch rs, cudaStream_t st) {
+    reduce64_kernel<false><<<reduce_blocks(), 256, 0, st>>>(out, in, n < 0 ? 0 : n, rs.partials, rs.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colmax(float* out, const float* in, int64_t rows, int64_t cols, uint32_t* keys, cudaStream_t st) {
+    if (cols <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(keys, 0, (size_t)cols * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    if (rows > 0) {
+        const int64_t col_threads = (cols + 3) / 4;
+        const unsigned gx = (unsigned)((col_threads + 255) / 256);
+        // enough row chunks to put ~8 blocks on every SM
+        int64_t want = ((int64_t)sm_count() * kBlocksPerSm + gx - 1) / gx;
+        if (want > rows) want = rows;
+        if (want > 65535) want = 65535;
+        if (want < 1) want = 1;
+        const int64_t per = (rows + want - 1) / want;
+        const unsigned gy = (unsigned)((rows + per - 1) / per);
+        colmax_keys_kernel<<<dim3(gx, gy), 256, 0, st>>>(keys, in, rows, cols, per);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    colmax_decode_kernel<<<grid_for(cols), kThreads, 0, st>>>(out, keys, cols, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(int* flag, int* err, double limit_s, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 1, 0, st>>>(flag, err, (unsigned long long)(limit_s * 1e9));
+    return cudaGetLastError();
+}
+
+}  // namespace gao

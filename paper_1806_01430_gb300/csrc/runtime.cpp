@@ -1,0 +1,932 @@
+// Loop-program runtime and the C ABI (include/gao.h).
+//
+// A program is a list of buffers and loops (Sec. 4: the parallelisable loops of the
+// application, gene length a = loop count).  prog_run executes the loops in order,
+// loop i on the GPU when gene bit i is 1 and on the host otherwise, and moves a
+// buffer between host and device only when a loop needs it on the other side
+// (Sec. 3.3: transfers between CPU and GPU memory are what make some loop
+// combinations slower than others).  Residency is tracked per buffer with two bits
+// (valid on host, valid on device).  The time of a run is the wall time from the
+// first loop until every OUTPUT buffer is on the host; that is the benchmark time
+// the GA turns into fitness (Sec. 5.1.2).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ga_engine.h"
+#include "gao_internal.h"
+
+namespace gao {
+
+// ---- errors -------------------------------------------------------------------------
+
+namespace {
+thread_local std::string t_err;
+}
+
+void set_error(const std::string& msg) { t_err = msg; }
+
+gao_status fail(gao_status st, const std::string& msg) {
+    t_err = msg;
+    return st;
+}
+
+gao_status cuda_fail(cudaError_t e, const char* what) {
+    t_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return GAO_ENOMEM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver || e == cudaErrorNoKernelImageForDevice)
+        return GAO_ENODEV;
+    return GAO_ECUDA;
+}
+
+// ---- device ---------------------------------------------------------------------------
+
+namespace {
+std::mutex g_dev_mu;
+int g_sm_count = 0;
+
+gao_status check_device(int* dev_out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    if (!(prop.major == 10 && prop.minor == 3))
+        return fail(GAO_ENODEV, "device " + std::string(prop.name) + " is sm_" + std::to_string(prop.major) +
+                                    std::to_string(prop.minor) + "; this library is built for sm_103a only");
+    {
+        std::lock_guard<std::mutex> g(g_dev_mu);
+        g_sm_count = prop.multiProcessorCount;
+    }
+    if (dev_out) *dev_out = dev;
+    return GAO_OK;
+}
+}  // namespace
+
+int sm_count() {
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    if (g_sm_count == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            g_sm_count = n;
+        else
+            g_sm_count = 152;
+    }
+    return g_sm_count;
+}
+
+}  // namespace gao
+
+using namespace gao;
+
+// ---- program ------------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+struct BufState {
+    gao_buffer d;
+    size_t bytes = 0;
+    char* dev = nullptr;
+    void* host = nullptr;  // pinned mirror
+    bool vh = false, vd = false;
+    bool input_set = false;
+};
+
+struct CacheEntry {
+    double seconds;
+    gao_status status;
+};
+
+struct Layout {
+    std::vector<size_t> buf_off;
+    size_t err_off = 0, partial_off = 0, counter_off = 0, keys_off = 0, rowexp_off = 0, tc_off = 0;
+    size_t tc_bytes = 0, keys_bytes = 0, rowexp_bytes = 0;
+    size_t total = 0;
+};
+
+size_t elem_size(int32_t dtype) { return dtype == GAO_F64 ? 8 : 4; }
+
+}  // namespace
+
+struct gao_prog {
+    std::vector<gao_loop> loops;
+    std::vector<BufState> bufs;
+    gao_opts opts{};
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    char* arena = nullptr;
+    bool own_arena = false;
+    Layout lay;
+    int* h_err = nullptr;  // pinned
+    std::vector<gao_loop_stat> stats;
+    std::vector<cudaEvent_t> ev;  // 6 per loop: copy0, copy1, loop0, loop1, kern0, kern1
+    std::vector<uint8_t> ev_used; // bit 0 copies, bit 1 loop, bit 2 kernel
+    std::unordered_map<uint64_t, CacheEntry> cache;
+    bool dirty_stream = false;  // a previous run left work in flight
+};
+
+namespace {
+
+int default_kchunk(int prec) { return prec == GAO_GEMM_FP32_SIMT ? 256 : 0; }
+
+gao_status validate(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bufs, const gao_opts* opts) {
+    if (!loops || !bufs) return fail(GAO_EINVAL, "loops and buffers must be non-null");
+    if (n_loops < 1 || n_loops > 64) return fail(GAO_EINVAL, "loop count must be in [1, 64]");
+    if (n_bufs < 1 || n_bufs > 4096) return fail(GAO_EINVAL, "buffer count must be in [1, 4096]");
+    if (opts && (opts->gemm_prec < GAO_GEMM_FP32_SIMT || opts->gemm_prec > GAO_GEMM_FP8))
+        return fail(GAO_EINVAL, "unknown gemm_prec");
+    for (int b = 0; b < n_bufs; ++b) {
+        const gao_buffer& d = bufs[b];
+        if (d.rows < 0 || d.cols < 0) return fail(GAO_EINVAL, "buffer " + std::to_string(b) + ": negative shape");
+        if (d.dtype != GAO_F32 && d.dtype != GAO_F64)
+            return fail(GAO_EINVAL, "buffer " + std::to_string(b) + ": unknown dtype");
+        if (d.role < GAO_BUF_TEMP || d.role > GAO_BUF_OUTPUT)
+            return fail(GAO_EINVAL, "buffer " + std::to_string(b) + ": unknown role");
+        if (d.rows > (int64_t)1 << 31 || d.cols > (int64_t)1 << 31)
+            return fail(GAO_EINVAL, "buffer " + std::to_string(b) + ": dimension above 2^31");
+    }
+    std::vector<char> defined((size_t)n_bufs, 0);
+    for (int b = 0; b < n_bufs; ++b) defined[(size_t)b] = bufs[b].role == GAO_BUF_INPUT;
+    auto okbuf = [&](int i) { return i >= 0 && i < n_bufs; };
+    for (int li = 0; li < n_loops; ++li) {
+        const gao_loop& L = loops[li];
+        const std::string where = "loop " + std::to_string(li) + ": ";
+        auto need_in = [&](int slot) -> gao_status {
+            const int b = L.ins[slot];
+            if (!okbuf(b)) return fail(GAO_EINVAL, where + "input slot " + std::to_string(slot) + " is not a buffer");
+            if (!defined[(size_t)b])
+                return fail(GAO_EINVAL, where + "reads buffer " + std::to_string(b) + " before any loop writes it");
+            if (bufs[b].dtype != GAO_F32) return fail(GAO_EINVAL, where + "inputs must be binary32 matrices");
+            return GAO_OK;
+        };
+        auto need_out = [&](int slot, int64_t r, int64_t c, int32_t dt) -> gao_status {
+            const int b = L.outs[slot];
+            if (!okbuf(b)) return fail(GAO_EINVAL, where + "output slot " + std::to_string(slot) + " is not a buffer");
+            if (bufs[b].rows != r || bufs[b].cols != c || bufs[b].dtype != dt)
+                return fail(GAO_EINVAL, where + "output buffer " + std::to_string(b) + " has shape " +
+                                            std::to_string(bufs[b].rows) + "x" + std::to_string(bufs[b].cols) +
+                                            ", expected " + std::to_string(r) + "x" + std::to_string(c));
+            if (bufs[b].role == GAO_BUF_INPUT) return fail(GAO_EINVAL, where + "writes an INPUT buffer");
+            return GAO_OK;
+        };
+        gao_status s = GAO_OK;
+        switch (L.kind) {
+            case GAO_LOOP_INIT: {
+                int nout = 0;
+                for (int t = 0; t < GAO_MAX_IO; ++t) {
+                    if (L.outs[t] < 0) continue;
+                    const int b = L.outs[t];
+                    if (!okbuf(b)) return fail(GAO_EINVAL, where + "output is not a buffer");
+                    if (b > 14) return fail(GAO_EINVAL, where + "INIT writes buffer ids 0..14 only");
+                    if ((s = need_out(t, bufs[b].rows, bufs[b].cols, GAO_F32)) != GAO_OK) return s;
+                    defined[(size_t)b] = 1;
+                    ++nout;
+                }
+                if (nout == 0) return fail(GAO_EINVAL, where + "INIT has no output");
+                continue;
+            }
+            case GAO_LOOP_GEMM: {
+                if ((s = need_in(0)) || (s = need_in(1))) return s;
+                const gao_buffer &A = bufs[L.ins[0]], &B = bufs[L.ins[1]];
+                if (A.cols != B.rows) return fail(GAO_EINVAL, where + "inner dimensions of A and B differ");
+                if (L.ins[2] >= 0) {
+                    if ((s = need_in(2))) return s;
+                    const gao_buffer& C0 = bufs[L.ins[2]];
+                    if (C0.rows != A.rows || C0.cols != B.cols) return fail(GAO_EINVAL, where + "C0 shape mismatch");
+                } else if (L.beta != 0.0) {
+                    return fail(GAO_EINVAL, where + "beta != 0 needs a C0 input");
+                }
+                if ((s = need_out(0, A.rows, B.cols, GAO_F32))) return s;
+                if (L.outs[0] == L.ins[0] || L.outs[0] == L.ins[1])
+                    return fail(GAO_EINVAL, where + "GEMM output may alias C0 only");
+                break;
+            }
+            case GAO_LOOP_AXPY: {
+                if ((s = need_in(0)) || (s = need_in(1))) return s;
+                const gao_buffer &X = bufs[L.ins[0]], &Y = bufs[L.ins[1]];
+                if (X.rows != Y.rows || X.cols != Y.cols) return fail(GAO_EINVAL, where + "AXPY operand shapes differ");
+                if ((s = need_out(0, X.rows, X.cols, GAO_F32))) return s;
+                break;
+            }
+            case GAO_LOOP_TRANSPOSE: {
+                if ((s = need_in(0))) return s;
+                const gao_buffer& X = bufs[L.ins[0]];
+                if ((s = need_out(0, X.cols, X.rows, GAO_F32))) return s;
+                if (L.outs[0] == L.ins[0]) return fail(GAO_EINVAL, where + "TRANSPOSE cannot run in place");
+                break;
+            }
+            case GAO_LOOP_ROWSUM: {
+                if ((s = need_in(0))) return s;
+                if ((s = need_out(0, bufs[L.ins[0]].rows, 1, GAO_F32))) return s;
+                if (L.outs[0] == L.ins[0]) return fail(GAO_EINVAL, where + "ROWSUM cannot run in place");
+                break;
+            }
+            case GAO_LOOP_FROBENIUS:
+            case GAO_LOOP_SUM: {
+                if ((s = need_in(0))) return s;
+                if ((s = need_out(0, 1, 1, GAO_F64))) return s;
+                break;
+            }
+            case GAO_LOOP_RELU:
+            case GAO_LOOP_SQUARE: {
+                if ((s = need_in(0))) return s;
+                if ((s = need_out(0, bufs[L.ins[0]].rows, bufs[L.ins[0]].cols, GAO_F32))) return s;
+                break;
+            }
+            case GAO_LOOP_COLMAX: {
+                if ((s = need_in(0))) return s;
+                if ((s = need_out(0, 1, bufs[L.ins[0]].cols, GAO_F32))) return s;
+                if (L.outs[0] == L.ins[0]) return fail(GAO_EINVAL, where + "COLMAX cannot run in place");
+                break;
+            }
+            default:
+                return fail(GAO_EINVAL, where + "unknown loop kind " + std::to_string(L.kind));
+        }
+        defined[(size_t)L.outs[0]] = 1;
+    }
+    for (int b = 0; b < n_bufs; ++b)
+        if (bufs[b].role == GAO_BUF_OUTPUT && !defined[(size_t)b])
+            return fail(GAO_EINVAL, "OUTPUT buffer " + std::to_string(b) + " is never written");
+    return GAO_OK;
+}
+
+Layout plan(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bufs, const gao_opts& o) {
+    Layout L;
+    size_t off = 0;
+    L.buf_off.resize((size_t)n_bufs);
+    for (int b = 0; b < n_bufs; ++b) {
+        L.buf_off[(size_t)b] = off;
+        off += align_up(std::max<size_t>(1, (size_t)bufs[b].rows * (size_t)bufs[b].cols * elem_size(bufs[b].dtype)));
+    }
+    L.err_off = off;
+    off += kAlign;
+    L.partial_off = off;
+    off += align_up((size_t)reduce_blocks() * sizeof(double));
+    L.counter_off = off;
+    off += kAlign;
+    size_t keys = 1, rows = 1, tc = 0;
+    for (int i = 0; i < n_loops; ++i) {
+        const gao_loop& lp = loops[i];
+        if (lp.kind == GAO_LOOP_COLMAX) keys = std::max(keys, (size_t)bufs[lp.ins[0]].cols * 4);
+        if (lp.kind == GAO_LOOP_INIT)
+            for (int t = 0; t < GAO_MAX_IO; ++t)
+                if (lp.outs[t] >= 0 && ((lp.flags >> t) & 1)) rows = std::max(rows, (size_t)bufs[lp.outs[t]].rows);
+        if (lp.kind == GAO_LOOP_GEMM && o.gemm_prec != GAO_GEMM_FP32_SIMT) {
+            const gao_buffer &A = bufs[lp.ins[0]], &B = bufs[lp.ins[1]];
+            tc = std::max(tc, tc_scratch_bytes(o.gemm_prec, A.rows, B.cols, A.cols));
+        }
+    }
+    L.keys_off = off;
+    L.keys_bytes = keys;
+    off += align_up(keys);
+    L.rowexp_off = off;
+    L.rowexp_bytes = rows;
+    off += align_up(rows);
+    off = align_up(off, 1024);
+    L.tc_off = off;
+    L.tc_bytes = tc;
+    off += align_up(tc, 1024);
+    L.total = off;
+    return L;
+}
+
+// Wait for the stream; with a deadline, poll and report expiry.  Work already queued
+// always completes before returning (kernels bound their own waits), so the program
+// is reusable afterwards; hard_cap_s bounds the wait for a GPU that stopped answering.
+gao_status stream_wait(cudaStream_t st, double deadline, bool* timed_out, double hard_cap_s = 300.0) {
+    if (deadline <= 0.0) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        return e == cudaSuccess ? GAO_OK : cuda_fail(e, "cudaStreamSynchronize");
+    }
+    const double cap = now_s() + hard_cap_s;
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return GAO_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "cudaStreamQuery");
+        const double t = now_s();
+        if (t > deadline) *timed_out = true;
+        if (t > cap) return fail(GAO_ETIMEOUT, "stream did not drain within the hard cap");
+        std::this_thread::yield();
+    }
+}
+
+void free_prog(gao_prog* p) {
+    if (!p) return;
+    if (p->st) cudaStreamSynchronize(p->st);
+    for (auto& b : p->bufs)
+        if (b.host) cudaFreeHost(b.host);
+    if (p->h_err) cudaFreeHost(p->h_err);
+    for (auto e : p->ev)
+        if (e) cudaEventDestroy(e);
+    if (p->own_arena && p->arena) cudaFree(p->arena);
+    if (p->own_stream && p->st) cudaStreamDestroy(p->st);
+    delete p;
+}
+
+}  // namespace
+
+// ---- C ABI: programs -------------------------------------------------------------------
+
+extern "C" gao_status prog_device_bytes(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bufs,
+                                        const gao_opts* opts, uint64_t* bytes_out) {
+    gao_status s = validate(loops, n_loops, bufs, n_bufs, opts);
+    if (s != GAO_OK) return s;
+    if (!bytes_out) return fail(GAO_EINVAL, "bytes_out is null");
+    if ((s = check_device(nullptr)) != GAO_OK) return s;
+    gao_opts o{};
+    if (opts) o = *opts;
+    *bytes_out = plan(loops, n_loops, bufs, n_bufs, o).total;
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bufs,
+                                  const gao_opts* opts, gao_prog** out) {
+    if (!out) return fail(GAO_EINVAL, "out is null");
+    *out = nullptr;
+    gao_status s = validate(loops, n_loops, bufs, n_bufs, opts);
+    if (s != GAO_OK) return s;
+    int dev = 0;
+    if ((s = check_device(&dev)) != GAO_OK) return s;
+    gao_prog* p = new gao_prog();
+    p->device = dev;
+    if (opts) p->opts = *opts;
+    if (p->opts.kchunk <= 0) p->opts.kchunk = default_kchunk(p->opts.gemm_prec);
+    p->loops.assign(loops, loops + n_loops);
+    p->lay = plan(loops, n_loops, bufs, n_bufs, p->opts);
+    auto bail = [&](gao_status st) {
+        free_prog(p);
+        return st;
+    };
+    if (p->opts.stream) {
+        p->st = (cudaStream_t)p->opts.stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+        p->own_stream = true;
+    }
+    if (p->opts.dev_arena) {
+        if (p->opts.dev_arena_bytes < p->lay.total)
+            return bail(fail(GAO_ENOMEM, "dev_arena holds " + std::to_string(p->opts.dev_arena_bytes) +
+                                             " bytes; the program needs " + std::to_string(p->lay.total)));
+        if (((uintptr_t)p->opts.dev_arena) & 1023u) return bail(fail(GAO_EINVAL, "dev_arena must be 1024-byte aligned"));
+        p->arena = (char*)p->opts.dev_arena;
+    } else {
+        cudaError_t e = cudaMalloc((void**)&p->arena, p->lay.total);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(arena)"));
+        p->own_arena = true;
+    }
+    p->bufs.resize((size_t)n_bufs);
+    for (int b = 0; b < n_bufs; ++b) {
+        BufState& B = p->bufs[(size_t)b];
+        B.d = bufs[b];
+        B.bytes = (size_t)bufs[b].rows * (size_t)bufs[b].cols * elem_size(bufs[b].dtype);
+        B.dev = p->arena + p->lay.buf_off[(size_t)b];
+        cudaError_t e = cudaMallocHost(&B.host, std::max<size_t>(B.bytes, 16));
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost(buffer mirror)"));
+        memset(B.host, 0, std::max<size_t>(B.bytes, 16));
+    }
+    cudaError_t e = cudaMallocHost((void**)&p->h_err, 16);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost(err)"));
+    *p->h_err = 0;
+    // zero the scratch words the kernels expect zeroed (error word, reduction counter)
+    e = cudaMemsetAsync(p->arena + p->lay.err_off, 0, p->lay.rowexp_off - p->lay.err_off, p->st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync(scratch)"));
+    e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamSynchronize"));
+    p->ev.assign((size_t)n_loops * 6, nullptr);
+    for (auto& ev : p->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    }
+    p->ev_used.assign((size_t)n_loops, 0);
+    p->stats.assign((size_t)n_loops, gao_loop_stat{});
+    *out = p;
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_set_input(gao_prog* p, int buf, const void* host_src, uint64_t bytes) {
+    if (!p || !host_src) return fail(GAO_EINVAL, "null argument");
+    if (buf < 0 || buf >= (int)p->bufs.size()) return fail(GAO_EINVAL, "no such buffer");
+    BufState& B = p->bufs[(size_t)buf];
+    if (B.d.role != GAO_BUF_INPUT) return fail(GAO_EINVAL, "buffer is not an INPUT buffer");
+    if (bytes != B.bytes)
+        return fail(GAO_EINVAL, "buffer holds " + std::to_string(B.bytes) + " bytes, got " + std::to_string(bytes));
+    cudaError_t e = cudaStreamSynchronize(p->st);  // no copy may still be reading the mirror
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    memcpy(B.host, host_src, B.bytes);
+    B.input_set = true;
+    p->cache.clear();  // new data: earlier times no longer describe this program
+    return GAO_OK;
+}
+
+namespace {
+
+struct RunCtx {
+    gao_prog* p;
+    double deadline;
+    bool timed_out;
+    CpuCtx cpu;
+};
+
+// Make buffer b valid on the requested side, issuing a copy on the stream if needed.
+gao_status make_valid(RunCtx& R, int b, bool on_gpu, gao_loop_stat& stat) {
+    BufState& B = R.p->bufs[(size_t)b];
+    if (on_gpu) {
+        if (B.vd) return GAO_OK;
+        if (!B.vh) return fail(GAO_EINVAL, "buffer " + std::to_string(b) + " holds no data");
+        if (B.bytes) GAO_CUDA_TRY(cudaMemcpyAsync(B.dev, B.host, B.bytes, cudaMemcpyHostToDevice, R.p->st));
+        stat.h2d_bytes += B.bytes;
+        B.vd = true;
+    } else {
+        if (B.vh) return GAO_OK;
+        if (!B.vd) return fail(GAO_EINVAL, "buffer " + std::to_string(b) + " holds no data");
+        if (B.bytes) GAO_CUDA_TRY(cudaMemcpyAsync(B.host, B.dev, B.bytes, cudaMemcpyDeviceToHost, R.p->st));
+        stat.d2h_bytes += B.bytes;
+        B.vh = true;
+    }
+    return GAO_OK;
+}
+
+std::vector<int> loop_inputs(const gao_loop& L) {
+    std::vector<int> v;
+    if (L.kind == GAO_LOOP_INIT) return v;
+    for (int t = 0; t < GAO_MAX_IO; ++t)
+        if (L.ins[t] >= 0) {
+            if (L.kind == GAO_LOOP_GEMM && t == 2 && L.beta == 0.0) continue;
+            v.push_back(L.ins[t]);
+        }
+    return v;
+}
+
+std::vector<int> loop_outputs(const gao_loop& L) {
+    std::vector<int> v;
+    const int n = L.kind == GAO_LOOP_INIT ? GAO_MAX_IO : 1;
+    for (int t = 0; t < n; ++t)
+        if (L.outs[t] >= 0) v.push_back(L.outs[t]);
+    return v;
+}
+
+gao_status run_gpu_loop(RunCtx& R, int li) {
+    gao_prog* p = R.p;
+    const gao_loop& L = p->loops[(size_t)li];
+    cudaStream_t st = p->st;
+    auto dptr = [&](int b) { return (float*)p->bufs[(size_t)b].dev; };
+    auto shp = [&](int b) -> const gao_buffer& { return p->bufs[(size_t)b].d; };
+    char* a = p->arena;
+    int* d_err = (int*)(a + p->lay.err_off);
+    ReduceScratch rs{(double*)(a + p->lay.partial_off), (unsigned*)(a + p->lay.counter_off)};
+    cudaError_t e = cudaSuccess;
+    int& nl = p->stats[(size_t)li].launches;
+    switch (L.kind) {
+        case GAO_LOOP_INIT:
+            for (int t = 0; t < GAO_MAX_IO && e == cudaSuccess; ++t) {
+                const int b = L.outs[t];
+                if (b < 0) continue;
+                const int8_t* rx = nullptr;
+                if ((L.flags >> t) & 1) {
+                    rx = (const int8_t*)(a + p->lay.rowexp_off);
+                    e = launch_row_exponents((int8_t*)rx, shp(b).rows, p->opts.seed, st);
+                    if (e != cudaSuccess) break;
+                    nl += shp(b).rows > 0;
+                }
+                e = launch_init(dptr(b), shp(b).rows, shp(b).cols, p->opts.seed, (uint32_t)b, rx, st);
+                nl += shp(b).rows * shp(b).cols > 0;
+            }
+            break;
+        case GAO_LOOP_GEMM: {
+            const gao_buffer &A = shp(L.ins[0]), &B = shp(L.ins[1]);
+            const float* c0 = L.ins[2] >= 0 ? dptr(L.ins[2]) : nullptr;
+            const float beta = c0 ? (float)L.beta : 0.0f;
+            const int prec = p->opts.gemm_prec;
+            cudaEvent_t k0 = p->ev[(size_t)li * 6 + 4], k1 = p->ev[(size_t)li * 6 + 5];
+            if (prec == GAO_GEMM_FP32_SIMT) {
+                GAO_CUDA_TRY(cudaEventRecord(k0, st));
+                e = launch_gemm_simt(dptr(L.outs[0]), dptr(L.ins[0]), dptr(L.ins[1]), c0 ? c0 : dptr(L.outs[0]),
+                                     A.rows, B.cols, A.cols, (float)L.alpha, beta, p->opts.kchunk, st);
+                nl += A.rows * B.cols > 0;
+                if (e == cudaSuccess) GAO_CUDA_TRY(cudaEventRecord(k1, st));
+            } else {
+                std::string why;
+                TcEvents tev{k0, k1, 0};
+                e = launch_gemm_tc(prec, dptr(L.outs[0]), dptr(L.ins[0]), dptr(L.ins[1]), c0 ? c0 : dptr(L.outs[0]),
+                                   A.rows, B.cols, A.cols, (float)L.alpha, beta, p->opts.kchunk, p->opts.tile_cfg,
+                                   a + p->lay.tc_off, p->lay.tc_bytes, d_err, st, tev, &why);
+                if (e != cudaSuccess && !why.empty()) return fail(GAO_EINVAL, "tensor-core GEMM: " + why);
+                nl += tev.launches;
+            }
+            p->ev_used[(size_t)li] |= 4;
+            break;
+        }
+        case GAO_LOOP_AXPY: {
+            const gao_buffer& X = shp(L.ins[0]);
+            e = launch_axpy(dptr(L.outs[0]), dptr(L.ins[0]), (float)L.alpha, dptr(L.ins[1]), X.rows * X.cols, st);
+            nl += X.rows * X.cols > 0;
+            break;
+        }
+        case GAO_LOOP_TRANSPOSE: {
+            const gao_buffer& X = shp(L.ins[0]);
+            e = launch_transpose(dptr(L.outs[0]), dptr(L.ins[0]), X.rows, X.cols, st);
+            nl += X.rows * X.cols > 0;
+            break;
+        }
+        case GAO_LOOP_ROWSUM: {
+            const gao_buffer& X = shp(L.ins[0]);
+            e = launch_rowsum(dptr(L.outs[0]), dptr(L.ins[0]), X.rows, X.cols, st);
+            nl += X.rows > 0 && X.cols > 0;
+            break;
+        }
+        case GAO_LOOP_FROBENIUS: {
+            const gao_buffer& X = shp(L.ins[0]);
+            e = launch_frobenius((double*)p->bufs[(size_t)L.outs[0]].dev, dptr(L.ins[0]), X.rows * X.cols, rs, st);
+            nl += 1;
+            break;
+        }
+        case GAO_LOOP_SUM: {
+            const gao_buffer& X = shp(L.ins[0]);
+            e = launch_sum((double*)p->bufs[(size_t)L.outs[0]].dev, dptr(L.ins[0]), X.rows * X.cols, rs, st);
+            nl += 1;
+            break;
+        }
+        case GAO_LOOP_RELU: {
+            const gao_buffer& X = shp(L.ins[0]);
+            e = launch_relu(dptr(L.outs[0]), dptr(L.ins[0]), X.rows * X.cols, st);
+            nl += X.rows * X.cols > 0;
+            break;
+        }
+        case GAO_LOOP_SQUARE: {
+            const gao_buffer& X = shp(L.ins[0]);
+            e = launch_square(dptr(L.outs[0]), dptr(L.ins[0]), X.rows * X.cols, st);
+            nl += X.rows * X.cols > 0;
+            break;
+        }
+        case GAO_LOOP_COLMAX: {
+            const gao_buffer& X = shp(L.ins[0]);
+            e = launch_colmax(dptr(L.outs[0]), dptr(L.ins[0]), X.rows, X.cols, (uint32_t*)(a + p->lay.keys_off), st);
+            nl += (X.cols > 0) * (1 + (X.rows > 0));
+            break;
+        }
+        default:
+            return fail(GAO_EINVAL, "unknown loop kind");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return GAO_OK;
+}
+
+gao_status run_cpu_loop(RunCtx& R, int li) {
+    gao_prog* p = R.p;
+    const gao_loop& L = p->loops[(size_t)li];
+    auto hptr = [&](int b) { return (float*)p->bufs[(size_t)b].host; };
+    auto shp = [&](int b) -> const gao_buffer& { return p->bufs[(size_t)b].d; };
+    CpuCtx& c = R.cpu;
+    switch (L.kind) {
+        case GAO_LOOP_INIT:
+            for (int t = 0; t < GAO_MAX_IO; ++t) {
+                const int b = L.outs[t];
+                if (b < 0) continue;
+                cpu_init(hptr(b), shp(b).rows, shp(b).cols, p->opts.seed, (uint32_t)b, ((L.flags >> t) & 1) != 0, c);
+            }
+            break;
+        case GAO_LOOP_GEMM: {
+            const gao_buffer &A = shp(L.ins[0]), &B = shp(L.ins[1]);
+            const float* c0 = L.ins[2] >= 0 ? hptr(L.ins[2]) : nullptr;
+            const int kc = p->opts.gemm_prec == GAO_GEMM_FP32_SIMT ? p->opts.kchunk : 256;
+            cpu_gemm(hptr(L.outs[0]), hptr(L.ins[0]), hptr(L.ins[1]), c0 ? c0 : hptr(L.outs[0]), A.rows, B.cols,
+                     A.cols, (float)L.alpha, c0 ? (float)L.beta : 0.0f, kc, c);
+            break;
+        }
+        case GAO_LOOP_AXPY: {
+            const gao_buffer& X = shp(L.ins[0]);
+            cpu_axpy(hptr(L.outs[0]), hptr(L.ins[0]), (float)L.alpha, hptr(L.ins[1]), X.rows * X.cols, c);
+            break;
+        }
+        case GAO_LOOP_TRANSPOSE: {
+            const gao_buffer& X = shp(L.ins[0]);
+            cpu_transpose(hptr(L.outs[0]), hptr(L.ins[0]), X.rows, X.cols, c);
+            break;
+        }
+        case GAO_LOOP_ROWSUM: {
+            const gao_buffer& X = shp(L.ins[0]);
+            cpu_rowsum(hptr(L.outs[0]), hptr(L.ins[0]), X.rows, X.cols, c);
+            break;
+        }
+        case GAO_LOOP_FROBENIUS: {
+            const gao_buffer& X = shp(L.ins[0]);
+            *(double*)p->bufs[(size_t)L.outs[0]].host = cpu_frobenius(hptr(L.ins[0]), X.rows * X.cols, c);
+            break;
+        }
+        case GAO_LOOP_SUM: {
+            const gao_buffer& X = shp(L.ins[0]);
+            *(double*)p->bufs[(size_t)L.outs[0]].host = cpu_sum(hptr(L.ins[0]), X.rows * X.cols, c);
+            break;
+        }
+        case GAO_LOOP_RELU: {
+            const gao_buffer& X = shp(L.ins[0]);
+            cpu_relu(hptr(L.outs[0]), hptr(L.ins[0]), X.rows * X.cols, c);
+            break;
+        }
+        case GAO_LOOP_SQUARE: {
+            const gao_buffer& X = shp(L.ins[0]);
+            cpu_square(hptr(L.outs[0]), hptr(L.ins[0]), X.rows * X.cols, c);
+            break;
+        }
+        case GAO_LOOP_COLMAX: {
+            const gao_buffer& X = shp(L.ins[0]);
+            cpu_colmax(hptr(L.outs[0]), hptr(L.ins[0]), X.rows, X.cols, c);
+            break;
+        }
+        default:
+            return fail(GAO_EINVAL, "unknown loop kind");
+    }
+    return GAO_OK;
+}
+
+double ev_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.0;
+    return (double)ms;
+}
+
+}  // namespace
+
+extern "C" gao_status prog_run(gao_prog* p, uint64_t gene_mask, uint32_t flags, double* seconds_out) {
+    if (!p) return fail(GAO_EINVAL, "program is null");
+    const int n = (int)p->loops.size();
+    if (n < 64 && (gene_mask >> n) != 0)
+        return fail(GAO_EINVAL, "gene has bits set at or above the loop count (" + std::to_string(n) + ")");
+    for (auto& B : p->bufs)
+        if (B.d.role == GAO_BUF_INPUT && !B.input_set)
+            return fail(GAO_EINVAL, "INPUT buffers must be set with prog_set_input before a run");
+    if (p->dirty_stream) {
+        bool to = false;
+        gao_status s = stream_wait(p->st, 0.0, &to);
+        if (s != GAO_OK) return s;
+        p->dirty_stream = false;
+    }
+    cudaError_t ce = cudaSetDevice(p->device);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
+    RunCtx R{p, 0.0, false, CpuCtx{p->opts.cpu_threads, 0.0, false}};
+    const double t0 = now_s();
+    if (p->opts.timeout_s > 0.0) R.deadline = R.cpu.deadline = t0 + p->opts.timeout_s;
+    for (auto& B : p->bufs) {
+        B.vh = (B.d.role == GAO_BUF_INPUT);
+        B.vd = false;
+    }
+    std::fill(p->ev_used.begin(), p->ev_used.end(), 0);
+    for (auto& s : p->stats) s = gao_loop_stat{};
+    const bool uses_gpu = gene_mask != 0;
+    char* d_err = p->arena + p->lay.err_off;
+    if (uses_gpu) GAO_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), p->st));
+    gao_status status = GAO_OK;
+    for (int li = 0; li < n && status == GAO_OK; ++li) {
+        const gao_loop& L = p->loops[(size_t)li];
+        const bool gpu = (gene_mask >> li) & 1;
+        gao_loop_stat& S = p->stats[(size_t)li];
+        S.placement = gpu ? 1 : 0;
+        cudaEvent_t* ev = &p->ev[(size_t)li * 6];
+        const std::vector<int> ins = loop_inputs(L);
+        if (gpu) {
+            bool copies = false;
+            for (int b : ins) copies |= !p->bufs[(size_t)b].vd;
+            if (copies) GAO_CUDA_TRY(cudaEventRecord(ev[0], p->st));
+            for (int b : ins)
+                if ((status = make_valid(R, b, true, S)) != GAO_OK) break;
+            if (status != GAO_OK) break;
+            if (copies) {
+                GAO_CUDA_TRY(cudaEventRecord(ev[1], p->st));
+                p->ev_used[(size_t)li] |= 1;
+            }
+            GAO_CUDA_TRY(cudaEventRecord(ev[2], p->st));
+            if ((status = run_gpu_loop(R, li)) != GAO_OK) break;
+            GAO_CUDA_TRY(cudaEventRecord(ev[3], p->st));
+            p->ev_used[(size_t)li] |= 2;
+        } else {
+            const double c0 = now_s();
+            for (int b : ins)
+                if ((status = make_valid(R, b, false, S)) != GAO_OK) break;
+            if (status != GAO_OK) break;
+            // the host loop may overwrite mirrors that queued copies still read, and
+            // reads mirrors that queued copies fill: drain the stream first
+            if (uses_gpu && (status = stream_wait(p->st, R.deadline, &R.timed_out)) != GAO_OK) break;
+            const double c1 = now_s();
+            S.copy_ms = (c1 - c0) * 1e3;
+            if (R.timed_out) break;
+            status = run_cpu_loop(R, li);
+            S.cpu_ms = (now_s() - c1) * 1e3;
+            if (R.cpu.timed_out) R.timed_out = true;
+            if (status != GAO_OK || R.timed_out) break;
+        }
+        for (int b : loop_outputs(L)) {
+            p->bufs[(size_t)b].vh = !gpu;
+            p->bufs[(size_t)b].vd = gpu;
+        }
+        if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
+        if (R.timed_out) break;
+    }
+    if (status == GAO_OK && !R.timed_out && !(flags & GAO_RUN_KEEP_DEVICE)) {
+        gao_loop_stat dummy{};
+        for (size_t b = 0; b < p->bufs.size(); ++b)
+            if (p->bufs[b].d.role == GAO_BUF_OUTPUT && !p->bufs[b].vh)
+                if ((status = make_valid(R, (int)b, false, dummy)) != GAO_OK) break;
+        if (!p->stats.empty()) p->stats.back().d2h_bytes += dummy.d2h_bytes;
+    }
+    if (uses_gpu) {
+        cudaError_t e = cudaMemcpyAsync(p->h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, p->st);
+        if (e != cudaSuccess && status == GAO_OK) status = cuda_fail(e, "cudaMemcpyAsync(err)");
+        gao_status ws = stream_wait(p->st, R.deadline, &R.timed_out);
+        if (ws != GAO_OK) {
+            p->dirty_stream = true;
+            return ws;
+        }
+    }
+    const double t1 = now_s();
+    if (seconds_out) *seconds_out = t1 - t0;
+    if (status != GAO_OK) return status;
+    if (uses_gpu && *p->h_err != 0)
+        return fail(GAO_EDEVICE, "a kernel raised device error " + std::to_string(*p->h_err) +
+                                     (*p->h_err == DEV_WAIT_TIMEOUT ? " (bounded wait expired)" : ""));
+    if (R.timed_out) {
+        if (seconds_out) *seconds_out = p->opts.timeout_s;
+        return fail(GAO_ETIMEOUT, "run exceeded its budget of " + std::to_string(p->opts.timeout_s) + " s");
+    }
+    for (int li = 0; li < n; ++li) {
+        gao_loop_stat& S = p->stats[(size_t)li];
+        cudaEvent_t* ev = &p->ev[(size_t)li * 6];
+        const uint8_t u = p->ev_used[(size_t)li];
+        if (u & 1) S.copy_ms = ev_ms(ev[0], ev[1]);
+        if (u & 2) S.device_ms = ev_ms(ev[2], ev[3]);
+        if (u & 4) S.kernel_ms = ev_ms(ev[4], ev[5]);
+        else if (u & 2) S.kernel_ms = S.device_ms;
+    }
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_output(gao_prog* p, int buf, const void** host_ptr, gao_buffer* shape_out) {
+    if (!p || !host_ptr) return fail(GAO_EINVAL, "null argument");
+    if (buf < 0 || buf >= (int)p->bufs.size()) return fail(GAO_EINVAL, "no such buffer");
+    BufState& B = p->bufs[(size_t)buf];
+    if (!B.vh) return fail(GAO_EINVAL, "buffer " + std::to_string(buf) + " is not valid on the host after the last run");
+    *host_ptr = B.host;
+    if (shape_out) *shape_out = B.d;
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_device_ptr(gao_prog* p, int buf, void** dev_ptr) {
+    if (!p || !dev_ptr) return fail(GAO_EINVAL, "null argument");
+    if (buf < 0 || buf >= (int)p->bufs.size()) return fail(GAO_EINVAL, "no such buffer");
+    *dev_ptr = p->bufs[(size_t)buf].dev;
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_stats(gao_prog* p, gao_loop_stat* out, int n) {
+    if (!p || !out) return fail(GAO_EINVAL, "null argument");
+    if (n < (int)p->stats.size()) return fail(GAO_EINVAL, "stats array too short");
+    std::copy(p->stats.begin(), p->stats.end(), out);
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_cache_clear(gao_prog* p) {
+    if (!p) return fail(GAO_EINVAL, "program is null");
+    p->cache.clear();
+    return GAO_OK;
+}
+
+extern "C" void prog_destroy(gao_prog* p) { free_prog(p); }
+
+// ---- C ABI: GA ----------------------------------------------------------------------------
+
+namespace {
+
+// Time of one gene over all programs, measured once per program and then cached.
+gao_status gene_time(gao_prog* const* progs, int n_progs, uint64_t mask, double* seconds, bool* all_cached) {
+    double total = 0.0;
+    bool failed = false, cached = true;
+    for (int i = 0; i < n_progs; ++i) {
+        gao_prog* p = progs[i];
+        auto it = p->cache.find(mask);
+        CacheEntry ce;
+        if (it != p->cache.end()) {
+            ce = it->second;
+        } else {
+            cached = false;
+            double s = 0.0;
+            gao_status st = prog_run(p, mask, 0, &s);
+            if (st == GAO_EINVAL || st == GAO_ENODEV || st == GAO_ENOMEM || st == GAO_ECUDA) return st;
+            ce.status = st;
+            ce.seconds = st == GAO_OK ? s : (st == GAO_ETIMEOUT ? p->opts.timeout_s : -1.0);
+            p->cache.emplace(mask, ce);
+        }
+        if (ce.seconds < 0.0) failed = true;
+        total += ce.seconds;
+    }
+    *seconds = failed ? -1.0 : total;
+    if (all_cached) *all_cached = cached;
+    return GAO_OK;
+}
+
+gao_status check_progs(gao_prog* const* progs, int n_progs, int* n_genes) {
+    if (!progs || n_progs < 1) return fail(GAO_EINVAL, "need at least one program");
+    const int a = (int)progs[0]->loops.size();
+    for (int i = 0; i < n_progs; ++i) {
+        if (!progs[i]) return fail(GAO_EINVAL, "null program");
+        if ((int)progs[i]->loops.size() != a) return fail(GAO_EINVAL, "programs differ in gene length");
+    }
+    *n_genes = a;
+    return GAO_OK;
+}
+
+}  // namespace
+
+extern "C" gao_status ga_evaluate(gao_prog* const* progs, int n_progs, const uint64_t* population, int pop,
+                                  double* fitness_out, double* seconds_out, int* cache_hits_out) {
+    int a = 0;
+    gao_status s = check_progs(progs, n_progs, &a);
+    if (s != GAO_OK) return s;
+    if (!population || pop < 0) return fail(GAO_EINVAL, "bad population");
+    int hits = 0;
+    for (int i = 0; i < pop; ++i) {
+        double t = 0.0;
+        bool cached = false;
+        if ((s = gene_time(progs, n_progs, population[i], &t, &cached)) != GAO_OK) return s;
+        hits += cached ? 1 : 0;
+        if (seconds_out) seconds_out[i] = t;
+        if (fitness_out) fitness_out[i] = ga_fitness(t);
+    }
+    if (cache_hits_out) *cache_hits_out = hits;
+    return GAO_OK;
+}
+
+extern "C" gao_status ga_run(gao_prog* const* progs, int n_progs, const gao_ga_params* params,
+                             gao_ga_result* result) {
+    int a = 0;
+    gao_status s = check_progs(progs, n_progs, &a);
+    if (s != GAO_OK) return s;
+    if (!params || !result) return fail(GAO_EINVAL, "null params or result");
+    std::vector<double> saved((size_t)n_progs);
+    for (int i = 0; i < n_progs; ++i) saved[(size_t)i] = progs[i]->opts.timeout_s;
+    double budget = params->timeout_s;
+    if (budget < 0.0) {  // automatic: 10 x the all-GPU time, capped at 60 s
+        const uint64_t all = a >= 64 ? ~0ULL : ((1ULL << a) - 1);
+        double t = 0.0;
+        for (int i = 0; i < n_progs; ++i) {
+            double ti = 0.0;
+            progs[i]->opts.timeout_s = 0.0;
+            if ((s = prog_run(progs[i], all, 0, &ti)) != GAO_OK) return s;
+            t += ti;
+        }
+        budget = std::min(60.0, 10.0 * t / n_progs);
+    }
+    if (budget > 0.0)
+        for (int i = 0; i < n_progs; ++i) progs[i]->opts.timeout_s = budget;
+    TimeFn fn = [&](uint64_t m, double* t) { return gene_time(progs, n_progs, m, t, nullptr); };
+    s = ga_core(a, *params, fn, result);
+    for (int i = 0; i < n_progs; ++i) progs[i]->opts.timeout_s = saved[(size_t)i];
+    return s;
+}
+
+extern "C" gao_status ga_run_table(const double* times, int n_genes, const gao_ga_params* params,
+                                   gao_ga_result* result) {
+    if (!times || !params || !result) return fail(GAO_EINVAL, "null argument");
+    if (n_genes < 1 || n_genes > 24) return fail(GAO_EINVAL, "table GA supports 1..24 genes");
+    TimeFn fn = [&](uint64_t m, double* t) {
+        *t = times[m];
+        return GAO_OK;
+    };
+    return ga_core(n_genes, *params, fn, result);
+}
+
+// ---- C ABI: misc ------------------------------------------------------------------------------
+
+extern "C" const char* gao_last_error(void) { return t_err.c_str(); }
+
+extern "C" const char* gao_version(void) { return "gaoffload 0.1 (sm_103a)"; }
+
+extern "C" gao_status gao_selftest_device_wait(double limit_s, void* stream) {
+    gao_status s = check_device(nullptr);
+    if (s != GAO_OK) return s;
+    if (!(limit_s > 0.0 && limit_s <= 10.0)) return fail(GAO_EINVAL, "limit_s must be in (0, 10]");
+    cudaStream_t st = (cudaStream_t)stream;
+    int* d = nullptr;
+    GAO_CUDA_TRY(cudaMalloc((void**)&d, 2 * sizeof(int)));
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) e = launch_wait_selftest(d, d + 1, limit_s, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest");
+    if (h[1] == DEV_WAIT_TIMEOUT) return fail(GAO_ETIMEOUT, "device wait expired after the limit (expected)");
+    return fail(GAO_EDEVICE, "device wait returned without expiring");
+}

@@ -1,0 +1,269 @@
+"""GPU parity of the loop program through the C ABI against the FP64 oracle.
+
+Tolerances (normwise relative error ||x - ref||_F / ||ref||_F):
+  * bit-exact: INIT (counter hash), TRANSPOSE, AXPY/RELU/SQUARE given equal
+    inputs, COLMAX given equal inputs;
+  * 1e-6: FP32 SIMT GEMM and everything downstream of it (the stated bound for the
+    FP32 and split-BF16 paths);
+  * Frobenius / SUM over the device's own input: 2e-7 relative (binary32 partial
+    sums of 4 squares: each group carries at most ~4 units of 2^-24 relative error,
+    the binary64 accumulation adds nothing visible).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ga as oga
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def gao():
+    from paper_1806_01430_gb300 import _build
+    _build.build()
+    import paper_1806_01430_gb300 as g
+    return g
+
+
+def run_prog(gao, prog, mask, **kw):
+    p = gao.prog_from_workload(prog, **kw)
+    secs = gao.prog_run(p, mask)
+    out = {}
+    for i, b in enumerate(prog.buffers):
+        if b.role == W.OUTPUT:
+            v = gao.prog_output(p, i)
+            out[b.name] = float(v[0, 0]) if (b.rows, b.cols) == (1, 1) and b.dtype == W.F64 else v
+    stats = gao.prog_stats(p)
+    gao.prog_destroy(p)
+    return out, secs, stats
+
+
+def all_outputs(prog):
+    for b in prog.buffers:
+        b.role = W.OUTPUT
+    return prog
+
+
+def check_six(out, ref, tol=TOL):
+    for nm in ("C", "D", "E", "r"):
+        err = oracle.rel_err(out[nm], ref[nm])
+        assert err <= tol, f"{nm}: rel err {err:.3e} > {tol}"
+    if ref["f"] > 0:
+        assert abs(out["f"] - ref["f"]) / ref["f"] <= tol
+    else:
+        assert out["f"] == 0.0
+
+
+def check_internal_consistency(out):
+    """Relations that hold exactly (or within the reduction bound) among the run's own outputs."""
+    C, A, D, E = out["C"], out["A"], out["D"], out["E"]
+    Dx = (C.astype(np.float64) + 2.0 * A.astype(np.float64)).astype(np.float32)  # exact 2a, one rounding
+    assert np.array_equal(D, Dx), "scale-add is not c + 2a rounded once"
+    assert np.array_equal(E, D.T), "transpose is not exact"
+    E64 = E.astype(np.float64)
+    r_ref = E64.sum(axis=1, keepdims=True)
+    scale = np.abs(E64).sum(axis=1, keepdims=True) + 1e-300
+    assert np.all(np.abs(out["r"] - r_ref) <= 1e-6 * scale + 1e-30)
+    f_ref = math.sqrt(float((E64 * E64).sum()))
+    if f_ref > 0:
+        assert abs(out["f"] - f_ref) / f_ref <= 2e-7
+
+
+def test_config0_n256_all_gpu(gao):
+    prog = all_outputs(W.six_loop(256, W.SEED_CONFIG0))
+    ref = oracle.run_program(prog)
+    out, secs, stats = run_prog(gao, prog, 0b111111)
+    check_six(out, ref)
+    check_internal_consistency(out)
+    for nm in ("A", "B"):
+        assert np.array_equal(out[nm], ref[nm].astype(np.float32)), f"init {nm} not bit-exact"
+    assert all(s["placement"] == 1 for s in stats)
+    assert stats[1]["kernel_ms"] > 0
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 8, 64, 127, 129, 132, 300])
+def test_six_loop_ragged_sizes(gao, n):
+    prog = all_outputs(W.six_loop(n, 4242 + n))
+    ref = oracle.run_program(prog)
+    out, _, _ = run_prog(gao, prog, 0b111111)
+    if n == 0:
+        assert out["f"] == 0.0
+        return
+    check_six(out, ref)
+    check_internal_consistency(out)
+
+
+def test_all_64_masks_invariance(gao):
+    """Every gene gives the oracle's result within tolerance; loops with bitwise-equal
+    inputs give bitwise-equal outputs whichever side runs them."""
+    n = 96
+    prog = all_outputs(W.six_loop(n, 31))
+    ref = oracle.run_program(prog)
+    p = gao.prog_from_workload(prog)
+    by_gemm_side = {}
+    init0 = None
+    for mask in range(64):
+        gao.prog_run(p, mask)
+        out = {b.name: gao.prog_output(p, i) for i, b in enumerate(prog.buffers)}
+        out["f"] = float(out["f"][0, 0])
+        check_six(out, ref)
+        check_internal_consistency(out)
+        init = (out["A"], out["B"])
+        if init0 is None:
+            init0 = init
+            assert np.array_equal(init[0], ref["A"].astype(np.float32))
+        assert np.array_equal(init[0], init0[0]) and np.array_equal(init[1], init0[1])
+        key = (mask >> 1) & 1
+        if key in by_gemm_side:
+            C0, D0, E0 = by_gemm_side[key]
+            assert np.array_equal(out["C"], C0)
+            assert np.array_equal(out["D"], D0) and np.array_equal(out["E"], E0)
+        else:
+            by_gemm_side[key] = (out["C"], out["D"], out["E"])
+        st = gao.prog_stats(p)
+        for i, s in enumerate(st):
+            assert s["placement"] == ((mask >> i) & 1)
+        # data moves only at CPU/GPU boundaries
+        if mask == 0:
+            assert all(s["h2d_bytes"] == 0 and s["d2h_bytes"] == 0 for s in st[:-1])
+        if mask == 0b000011:  # init+GEMM on GPU, D = C + 2A on CPU: C and A come back
+            assert st[2]["d2h_bytes"] == 2 * n * n * 4
+    gao.prog_destroy(p)
+
+
+def test_row_scaled_init_bit_exact(gao):
+    prog = all_outputs(W.six_loop(200, W.SEED_CONFIG2_ROWS, rowscale_a=True))
+    ref = oracle.run_program(prog)
+    for mask in (0b111111, 0b111110):
+        out, _, _ = run_prog(gao, prog, mask)
+        assert np.array_equal(out["A"], ref["A"].astype(np.float32))
+        check_six(out, ref)
+
+
+@pytest.mark.parametrize("m,k", [(200, 72), (129, 33), (64, 256)])
+def test_twelve_loop_program(gao, m, k):
+    prog = all_outputs(W.twelve_loop(m, k, W.SEED_CONFIG4))
+    ref = oracle.run_program(prog)
+    rng = np.random.default_rng(m + k)
+    for mask in [(1 << 12) - 1, 0] + [int(x) for x in rng.integers(0, 1 << 12, size=3)]:
+        out, _, stats = run_prog(gao, prog, mask)
+        for nm in ("C", "D", "E", "F", "G", "H", "P", "r", "q"):
+            err = oracle.rel_err(out[nm], ref[nm])
+            assert err <= 2 * TOL, f"mask {mask:012b} {nm}: {err:.2e}"
+        for nm in ("f", "s"):
+            assert abs(out[nm] - ref[nm]) <= 2 * TOL * abs(ref[nm]), nm
+        # exact relations among the run's own outputs
+        E, F, G, H, P, D = (out[x] for x in "EFGHPD")
+        assert np.array_equal(F, np.maximum(E, 0).astype(np.float32))
+        assert np.array_equal(H, (G.astype(np.float64) ** 2).astype(np.float32))
+        assert np.array_equal(out["q"].ravel(), P.max(axis=0))
+        s_ref = float(P.astype(np.float64).sum())
+        assert abs(out["s"] - s_ref) <= 1e-6 * float(np.abs(P).astype(np.float64).sum())
+
+
+def test_host_input_program_matches(gao):
+    n, seed = 160, 77
+    prog = W.host_input_program(n, seed, outputs=("C", "r", "f"))
+    ins = {"A": oracle.init_matrix(seed, 0, n, n), "B": oracle.init_matrix(seed, 1, n, n),
+           "C0": oracle.init_matrix(seed, 2, n, n)}
+    ref = oracle.run_program(prog, ins)
+    p = gao.prog_from_workload(prog)
+    for nm, v in ins.items():
+        gao.prog_set_input(p, prog.index(nm), v.astype(np.float32))
+    for mask in (0b11111, 0b00000, 0b10101):
+        gao.prog_run(p, mask)
+        st = gao.prog_stats(p)
+        if mask & 1:
+            assert st[0]["h2d_bytes"] == 3 * n * n * 4  # A, B, C0 copied in every run
+        C = gao.prog_output(p, prog.index("C"))
+        assert oracle.rel_err(C, ref["C"]) <= TOL
+        assert oracle.rel_err(gao.prog_output(p, prog.index("r")), ref["r"]) <= TOL
+        f = float(gao.prog_output(p, prog.index("f"))[0, 0])
+        assert abs(f - ref["f"]) / ref["f"] <= TOL
+    gao.prog_destroy(p)
+
+
+def test_torch_arena_and_stream(gao):
+    torch = pytest.importorskip("torch")
+    prog = W.six_loop(128, 5, outputs=("C", "r", "f"))
+    nbytes = gao.prog_device_bytes(prog.buffers, prog.loops, seed=prog.seed)
+    arena = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    p = gao.prog_from_workload(prog, arena=arena, stream=s)
+    gao.prog_run(p, 0b111111)
+    ref = oracle.run_program(prog)
+    assert oracle.rel_err(gao.prog_output(p, prog.index("C")), ref["C"]) <= TOL
+    base = arena.data_ptr()
+    assert base <= gao.prog_device_ptr(p, prog.index("C")) < base + nbytes
+    gao.prog_destroy(p)
+    with pytest.raises(gao.GaoError):  # arena too small
+        gao.prog_from_workload(prog, arena=arena[: nbytes // 2])
+
+
+def test_timeout_then_reusable(gao):
+    prog = W.six_loop(1024, 9)
+    p = gao.prog_from_workload(prog, timeout_s=1e-3)
+    st, secs = gao.prog_run_status(p, 0b000000)  # CPU GEMM of 1024^3 cannot finish in 1 ms
+    assert st == gao.GAO_ETIMEOUT and secs == pytest.approx(1e-3)
+    st2, _ = gao.prog_run_status(p, 0b111111)
+    assert st2 in (gao.GAO_OK, gao.GAO_ETIMEOUT)
+    gao.prog_destroy(p)
+    p = gao.prog_from_workload(prog)
+    gao.prog_run(p, 0b111111)  # same program without a budget runs through
+    gao.prog_destroy(p)
+
+
+def test_device_wait_expires_without_trapping(gao):
+    assert gao.gao_selftest_device_wait(0.05) == gao.GAO_ETIMEOUT
+    # the context is still usable afterwards
+    out, _, _ = run_prog(gao, W.six_loop(32, 1), 0b111111)
+    assert out["f"] > 0
+
+
+def test_bad_gene_bits(gao):
+    p = gao.prog_from_workload(W.six_loop(16, 1))
+    st, _ = gao.prog_run_status(p, 1 << 6)
+    assert st == gao.GAO_EINVAL
+    gao.prog_destroy(p)
+
+
+def test_ga_evaluate_cache_and_ga_run_match_oracle(gao):
+    """The GA over measured times: after every gene is measured once (cached), ga_run
+    must follow the oracle GA's trajectory on that same time table, and the best gene
+    must be the exhaustive optimum of the table."""
+    prog = W.six_loop(256, W.SEED_CONFIG1)
+    p = gao.prog_from_workload(prog)
+    masks = list(range(64))
+    fit, secs, hits = gao.ga_evaluate([p], masks)
+    assert hits == 0 and np.all(secs > 0) and np.allclose(fit, 1 / np.sqrt(secs))
+    fit2, secs2, hits2 = gao.ga_evaluate([p], masks[::-1])
+    assert hits2 == 64 and np.array_equal(secs2, secs[::-1])  # repeated genes are not re-measured
+    table = secs.copy()
+    res = gao.ga_run([p], pop=12, generations=12, pc=0.9, pm=0.05, seed=5)
+    ref = oga.run(lambda m: float(table[m]), 6, 12, 12, 0.9, 0.05, 5)
+    assert res.populations == ref.populations and res.best_mask == ref.best_mask
+    best_m, best_t = oga.exhaustive(lambda m: float(table[m]), 6)
+    assert table[res.best_mask] >= best_t
+    gao.prog_destroy(p)
+
+
+def test_full_size_n4096_sampled(gao):
+    """configs[1] size: n = 4096, all-GPU gene, FP32 SIMT; sampled C entries against the
+    oracle computed entry by entry from the counter hash, plus exact relations."""
+    n, seed = 4096, W.SEED_CONFIG1
+    prog = all_outputs(W.six_loop(n, seed))
+    out, _, _ = run_prog(gao, prog, 0b111111)
+    rng = np.random.default_rng(0)
+    ii = rng.integers(0, n, 256)
+    jj = rng.integers(0, n, 256)
+    want = oracle.gemm_init_entries(seed, (0, 1, 2), False, n, n, n, 1.5, 0.5, ii, jj)
+    got = out["C"][ii, jj].astype(np.float64)
+    err = math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
+    assert err <= TOL, err
+    check_internal_consistency(out)
