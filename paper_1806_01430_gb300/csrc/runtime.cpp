@@ -140,7 +140,17 @@ struct gao_prog {
 
 namespace {
 
-int default_kchunk(int prec) { return prec == GAO_GEMM_FP32_SIMT ? 256 : 0; }
+// K elements per binary32 partial sum when the caller passes 0: the FP32 SIMT path and
+// the split tensor-core paths restart their accumulators so that rounding error does
+// not grow with K; plain bfloat16 is far above that error level and runs unchunked.
+int default_kchunk(int prec) {
+    switch (prec) {
+        case GAO_GEMM_FP32_SIMT: return 256;
+        case GAO_GEMM_BF16X6: return 256;
+        case GAO_GEMM_BF16X3: return 256;
+        default: return 0;
+    }
+}
 
 gao_status validate(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bufs, const gao_opts* opts) {
     if (!loops || !bufs) return fail(GAO_EINVAL, "loops and buffers must be non-null");
