@@ -76,7 +76,10 @@ class Clocks:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
 
     def __exit__(self, *a):
         if self.proc:
@@ -87,10 +90,13 @@ class Clocks:
                 self.proc.kill()
             self.t.join(timeout=2)
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and active throttle reasons of the samples taken in [t0, t1]."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        for ts, l in self.lines:
+            if t0 is not None and not (t0 <= ts <= t1):
+                continue
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -163,45 +169,68 @@ def allsum(world, x: float) -> float:
 
 # ---- CPU oracle baseline -------------------------------------------------------------------
 
-def oracle_sample(n: int, seed: int, target_s: float):
-    """Time the FP64 oracle on rows [0, r) of the program (GEMM rows, their scale-add,
-    transpose, row sums and norm contributions), r grown until ~target_s of work.
-    Returns (flops_equivalent_per_s, rows, seconds, threads)."""
+def oracle_rows(n: int, seed: int, r: int, B) -> float:
+    """Seconds the FP64 oracle takes for rows [0, r) of the six-loop program: INIT of
+    those rows of A and C, their GEMM rows (against the full B, initialised outside),
+    scale-add, transpose, row sums and norm."""
+    import oracle
+    t0 = time.perf_counter()
+    A = oracle.init_matrix(seed, 0, r, n)
+    C0 = oracle.init_matrix(seed, 2, r, n)
+    C = oracle.gemm(A, B, C0, 1.5, 0.5)
+    D = oracle.axpy(C, 2.0, A)
+    E = oracle.transpose(D)
+    oracle.rowsum(E)
+    oracle.frobenius(E)
+    return time.perf_counter() - t0
+
+
+def oracle_calibrate(n: int, seed: int, target_s: float):
+    """Rows r whose oracle time is about target_s (at most n); returns (r, B)."""
     import oracle
     B = oracle.init_matrix(seed, 1, n, n)
-    r = 16
+    r = 8
     while True:
-        t0 = time.perf_counter()
-        A = oracle.init_matrix(seed, 0, n, n)[:r]
-        C0 = oracle.init_matrix(seed, 2, n, n)[:r]
-        C = oracle.gemm(A, B, C0, 1.5, 0.5)
-        D = oracle.axpy(C, 2.0, A)
-        E = oracle.transpose(D)
-        oracle.rowsum(E)
-        oracle.frobenius(E)
-        dt = time.perf_counter() - t0
-        if dt >= target_s or r >= n:
-            return 2.0 * r * n * n / dt, r, dt, oracle.num_threads()
-        r = min(n, max(r * 2, int(r * target_s / max(dt, 1e-3) * 0.9)))
+        dt = oracle_rows(n, seed, r, B)
+        if dt >= 0.5 * target_s or r >= n:
+            r = max(1, min(n, int(r * target_s / max(dt, 1e-4))))
+            return r, B
+        r = min(n, r * 4)
+
+
+def oracle_sample(n: int, seed: int, target_s: float):
+    """(flop-equivalent per s, rows, seconds, threads) of one bounded oracle sample."""
+    import oracle
+    r, B = oracle_calibrate(n, seed, target_s)
+    dt = oracle_rows(n, seed, r, B)
+    return 2.0 * r * n * n / dt, r, dt, oracle.num_threads()
 
 
 def reference_arm(args, world, rank):
+    """The oracle, as it stands, on the host cores: each step is the same bounded
+    sample (rows 0..r-1 of the program), r sized so that the whole run takes about
+    two minutes whatever --steps/--warmup are."""
     if rank != 0:
         return
+    import oracle
     n = args.n
-    vals = []
-    rows = secs = thr = None
+    per_step = max(0.02, min(args.ref_target_s, 120.0 / (args.steps + args.warmup)))
+    r, B = oracle_calibrate(n, W.SEED_CONFIG1, per_step)
+    secs = []
     for i in range(args.warmup + args.steps):
-        v, rows, secs, thr = oracle_sample(n, W.SEED_CONFIG1, args.ref_target_s)
+        dt = oracle_rows(n, W.SEED_CONFIG1, r, B)
         if i >= args.warmup:
-            vals.append(v)
-    val = statistics.median(vals) / 1e12
-    sample = f"rows 0..{rows - 1} of the n={n} six-loop program (GEMM rows + their scale-add/transpose/row-sum/norm)"
+            secs.append(dt)
+    ms = statistics.median(secs) * 1e3
+    val = 2.0 * r * n * n / (ms / 1e3) / 1e12
+    sample = (f"rows 0..{r - 1} of the n={n} six-loop program per step (their init, GEMM rows against the full B, "
+              f"scale-add, transpose, row sums, norm) in FP64")
     line = {"impl": "reference", "metric": "gemm_program_tflops", "value": val, "unit": "TFLOP/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded counter hash)",
-            "config": {"workload": f"six_loop_n{n}_all_gpu", "n": n, "sample": sample},
-            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": thr, "kind": "oracle", "sample": sample},
+            "config": {"workload": f"six_loop_n{n}_all_gpu_bf16x6", "n": n, "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -220,29 +249,37 @@ def our_arm(args, world, rank, local):
     p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream)
     mask = (1 << prog.n_loops) - 1
     gemm_loop = 1
-    for _ in range(args.warmup):
-        gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
-    torch.cuda.synchronize()
     kern_ms, launches = [], 0
-    barrier(world)
-    torch.cuda.synchronize()
+    loop_ms = [0.0] * prog.n_loops
     with Clocks(local) as clk:
+        time.sleep(0.3)  # let the sampler start
+        for _ in range(args.warmup):
+            gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        t0 = clk.mark()
         ev0.record(stream)
         for _ in range(args.steps):
             gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
             st = gao.prog_stats(p)
             kern_ms.append(st[gemm_loop]["kernel_ms"])
             launches += sum(s["launches"] for s in st)
+            for i, s_ in enumerate(st):
+                loop_ms[i] += s_["device_ms"]
         ev1.record(stream)
         torch.cuda.synchronize()
+        t1 = clk.mark()
+        time.sleep(0.25)
     barrier(world)
     ms = ev0.elapsed_time(ev1) / args.steps
     ms = allmax(world, ms)
     total_flops = allsum(world, flops)
     value = total_flops / (ms / 1e3) / 1e12
-    clocks = clk.summary()
+    clocks = clk.summary(t0, t1)
+    loop_ms = {f"L{i}_{W.KIND_NAMES[lp.kind]}": round(v / args.steps, 4) for i, (lp, v) in enumerate(zip(prog.loops, loop_ms))}
 
     # accuracy of this run's GEMM against the oracle on sampled entries (no timing)
     err = None
@@ -265,7 +302,7 @@ def our_arm(args, world, rank, local):
             gao.prog_run(q, mask, gao.RUN_KEEP_DEVICE)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k = max(3, args.steps // 4)
+        k = max(3, min(args.steps // 4, 200))
         ks = []
         e0.record(stream)
         for _ in range(k):
@@ -289,7 +326,7 @@ def our_arm(args, world, rank, local):
         m5 = (1 << hp.n_loops) - 1
         for _ in range(2):
             gao.prog_run(q, m5)
-        k = max(3, args.steps // 2)
+        k = max(3, min(args.steps // 2, 400))
         walls = []
         for _ in range(k):
             walls.append(gao.prog_run(q, m5))
@@ -336,15 +373,15 @@ def our_arm(args, world, rank, local):
                        "gemm": prec, "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "working set 7 x 64 MiB + split planes > 129 MB L2"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "gemm_rel_err_sampled": err, "fp32_simt": simt}
+            "clocks": clocks, "gemm_rel_err_sampled": err, "fp32_simt": simt, "loop_ms": loop_ms}
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--prec", default="bf16x6", choices=list(PREC))
