@@ -217,6 +217,29 @@ const char *gao_version(void);
  * observed (the expected outcome), GAO_OK never.  stream may be NULL. */
 gao_status gao_selftest_device_wait(double limit_s, void *stream);
 
+/* ---- allocation-free variant ------------------------------------------------ */
+
+/* Column maxima out[j] = max_i in[i][j] of a rows x cols row-major binary32 matrix
+ * already on the device, written to dev_out (cols binary32 values, device memory);
+ * the same result as a GAO_LOOP_COLMAX loop.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they need
+ * the result -- code running under a host framework whose pool allocator owns the
+ * GPU's memory, or a latency-critical loop that cannot afford cudaMalloc/cudaFree
+ * (which may synchronise the device and can fail with out-of-memory mid-run).
+ *
+ * It allocates nothing and calls no allocating routine.  Its scratch, one 32-bit key
+ * per column, is a fixed array of GAO_COLMAX_NOALLOC_MAX_COLS keys (256 KiB) inside
+ * the library; every GPU that loads the library holds that array until the process
+ * exits.  cols above the maximum is rejected with GAO_EINVAL.  The first call on a
+ * device (with that device current) looks up the array's device address; make that
+ * first call before any stream capture.  Every call clears the keys it uses on
+ * `stream` before reducing, and all calls share the one array: calls whose work
+ * overlaps on the GPU (different streams, or several host threads) race and give
+ * wrong results.  Asynchronous on `stream` (NULL: the legacy default stream);
+ * dev_in and dev_out are owned by the caller. */
+#define GAO_COLMAX_NOALLOC_MAX_COLS 65536
+gao_status gao_colmax_noalloc(const float *dev_in, int64_t rows, int64_t cols, float *dev_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,7 @@ SIGNATURES = {
     "gao_last_error": (ctypes.c_char_p, []),
     "gao_version": (ctypes.c_char_p, []),
     "gao_selftest_device_wait": (ctypes.c_int, [ctypes.c_double, _P]),
+    "gao_colmax_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
 }
 
 _lib = None
@@ -347,3 +348,13 @@ def ga_run_table(times: np.ndarray, n_genes: int, pop=12, generations=12, pc=0.9
 def gao_selftest_device_wait(limit_s: float = 0.2, stream=None) -> int:
     """Returns the status (GAO_ETIMEOUT is the expected outcome)."""
     return int(lib().gao_selftest_device_wait(float(limit_s), _stream_handle(stream)))
+
+
+COLMAX_NOALLOC_MAX_COLS = 65536
+
+
+def gao_colmax_noalloc(dev_in: int, rows: int, cols: int, dev_out: int, stream=None) -> int:
+    """Column maxima of a device matrix into caller device memory, with no allocation;
+    returns the status (see include/gao.h for the shared-scratch rules)."""
+    return int(lib().gao_colmax_noalloc(ctypes.c_void_p(dev_in), int(rows), int(cols), ctypes.c_void_p(dev_out),
+                                        _stream_handle(stream)))

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "gao_internal.h"
 
 namespace gao {
@@ -431,4 +433,63 @@ cudaError_t launch_wait_selftest(int* flag, int* err, double limit_s, cudaStream
     return cudaGetLastError();
 }
 
+// ---- column maxima without any allocation ------------------------------------------------------
+//
+// Some callers cannot allocate device memory at the point where they need a result:
+// a host framework whose pool allocator owns the device memory and forbids other
+// allocations, or a latency-critical loop that cannot afford cudaMalloc/cudaFree
+// (they may synchronise the device and can fail with out-of-memory mid-run).  For
+// them the column-maxima loop has a variant whose scratch (one 32-bit key per
+// column) lives in the file-scope array below, loaded with the library and held by
+// every device that loads it until the process exits.  Host code must not use the
+// array's name as a device address: it is a host-side stand-in.  The device address
+// is looked up with cudaGetSymbolAddress once per device, on the first call made
+// while that device is current.
+
+namespace {
+
+constexpr int64_t kColmaxNoallocMaxCols = 65536;  // 256 KiB of keys
+static __device__ __align__(256) uint32_t g_colmax_noalloc_keys[kColmaxNoallocMaxCols];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_keys_dev[kMaxDevices] = {};  // device address of the array, per device
+
+cudaError_t colmax_noalloc_keys(uint32_t** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (g_noalloc_keys_dev[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_colmax_noalloc_keys);
+        if (e != cudaSuccess) return e;
+        g_noalloc_keys_dev[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_noalloc_keys_dev[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
 }  // namespace gao
+
+extern "C" gao_status gao_colmax_noalloc(const float* dev_in, int64_t rows, int64_t cols, float* dev_out,
+                                         void* stream) {
+    using namespace gao;
+    if (rows < 0 || cols < 0) return fail(GAO_EINVAL, "gao_colmax_noalloc: negative shape");
+    if (cols > kColmaxNoallocMaxCols)
+        return fail(GAO_EINVAL, "gao_colmax_noalloc: cols exceeds the fixed maximum of 65536 columns");
+    if (cols == 0) return GAO_OK;
+    if (dev_out == nullptr || (rows > 0 && dev_in == nullptr))
+        return fail(GAO_EINVAL, "gao_colmax_noalloc: null device pointer");
+    uint32_t* keys = nullptr;
+    cudaError_t e = colmax_noalloc_keys(&keys);
+    if (e != cudaSuccess) return cuda_fail(e, "gao_colmax_noalloc: cudaGetSymbolAddress");
+    // clears keys[0, cols) on the stream, then reduces and decodes into dev_out
+    e = launch_colmax(dev_out, dev_in, rows, cols, keys, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gao_colmax_noalloc: launch");
+    return GAO_OK;
+}
+
