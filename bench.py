@@ -235,6 +235,17 @@ def reference_arm(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def algorithmic_bytes(prog, lp) -> float:
+    """Bytes a loop must move at least once: every input read once, every output
+    written once (INIT only writes)."""
+    def nbytes(i):
+        b = prog.buffers[i]
+        return b.rows * b.cols * (8 if b.dtype == W.F64 else 4)
+    ins = [] if lp.kind == W.INIT else [i for i in lp.ins if i >= 0]
+    outs = [o for o in lp.outs if o >= 0]
+    return float(sum(nbytes(i) for i in ins) + sum(nbytes(o) for o in outs))
+
+
 # ---- our arm --------------------------------------------------------------------------------------
 
 def our_arm(args, world, rank, local):
@@ -244,8 +255,13 @@ def our_arm(args, world, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     n, prec = args.n, args.prec
-    flops = 2.0 * n ** 3
-    prog = W.six_loop(n, W.SEED_CONFIG1 + rank, outputs=("C", "r", "f"))
+    if args.workload == "twelve_loop":
+        prog = W.twelve_loop(args.m, args.k, W.SEED_CONFIG4 + rank, outputs=("C", "r", "f", "q", "s"))
+        wname = f"twelve_loop_m{args.m}_k{args.k}_all_gpu_{prec}"
+    else:
+        prog = W.six_loop(n, W.SEED_CONFIG1 + rank, outputs=("C", "r", "f"))
+        wname = f"six_loop_n{n}_all_gpu_{prec}"
+    flops = prog.gemm_flops()
     p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream)
     mask = (1 << prog.n_loops) - 1
     gemm_loop = 1
@@ -279,6 +295,13 @@ def our_arm(args, world, rank, local):
     total_flops = allsum(world, flops)
     value = total_flops / (ms / 1e3) / 1e12
     clocks = clk.summary(t0, t1)
+    loop_bytes = [algorithmic_bytes(prog, lp) for lp in prog.loops]
+    hbm = peaks().get("hbm_gbs", FALLBACK["hbm_gbs"])
+    loop_gbs = {}
+    for i, (lp, v, nb) in enumerate(zip(prog.loops, loop_ms, loop_bytes)):
+        if lp.kind != W.GEMM and v > 0:
+            g = nb / (v / args.steps / 1e3) / 1e9
+            loop_gbs[f"L{i}_{W.KIND_NAMES[lp.kind]}"] = {"gbs": round(g, 1), "hbm_frac": round(g / hbm, 3)}
     loop_ms = {f"L{i}_{W.KIND_NAMES[lp.kind]}": round(v / args.steps, 4) for i, (lp, v) in enumerate(zip(prog.loops, loop_ms))}
 
     # accuracy of this run's GEMM against the oracle on sampled entries (no timing)
@@ -287,9 +310,11 @@ def our_arm(args, world, rank, local):
         import oracle
         gao.prog_run(p, mask)
         C = gao.prog_output(p, prog.index("C"))
+        gm, gk = prog.buffers[prog.index("A")].rows, prog.buffers[prog.index("A")].cols
+        gn = prog.buffers[prog.index("B")].cols
         rng = np.random.default_rng(1)
-        ii, jj = rng.integers(0, n, 128), rng.integers(0, n, 128)
-        want = oracle.gemm_init_entries(prog.seed, (0, 1, 2), False, n, n, n, 1.5, 0.5, ii, jj)
+        ii, jj = rng.integers(0, gm, 128), rng.integers(0, gn, 128)
+        want = oracle.gemm_init_entries(prog.seed, (0, 1, 2), False, gm, gn, gk, 1.5, 0.5, ii, jj)
         got = C[ii, jj].astype(np.float64)
         err = math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
     gao.prog_destroy(p)
@@ -317,7 +342,7 @@ def our_arm(args, world, rank, local):
 
     # end to end: inputs from pinned host memory, results read back, every step
     e2e = None
-    if args.e2e:
+    if args.e2e and args.workload == "six_loop":
         hp = W.host_input_program(n, prog.seed, outputs=("r", "f"))
         q = gao.prog_from_workload(hp, gemm_prec=PREC[prec], stream=stream)
         import oracle  # input generation only (seeded counter hash); not on the timed path
@@ -369,11 +394,13 @@ def our_arm(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x6->f32" if prec == "bf16x6" else prec,
             "data": "synthetic (seeded counter hash, U[-1,1))",
-            "config": {"workload": f"six_loop_n{n}_all_gpu_{prec}", "n": n, "gene": f"{mask:06b}",
+            "config": {"workload": wname, "n": n if args.workload == "six_loop" else None,
+                       "gene": format(mask, f"0{prog.n_loops}b"),
                        "gemm": prec, "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "l2": "working set 7 x 64 MiB + split planes > 129 MB L2"},
+                       "l2": "working set larger than the 129 MB L2 (no flush)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "gemm_rel_err_sampled": err, "fp32_simt": simt, "loop_ms": loop_ms}
+            "clocks": clocks, "gemm_rel_err_sampled": err, "fp32_simt": simt, "loop_ms": loop_ms,
+            "loop_gbs": loop_gbs}
     print(json.dumps(line), flush=True)
 
 
@@ -384,6 +411,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--workload", default="six_loop", choices=["six_loop", "twelve_loop"])
+    ap.add_argument("--m", type=int, default=16384)
+    ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--prec", default="bf16x6", choices=list(PREC))
     ap.add_argument("--no-check", dest="check", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

@@ -9,6 +9,10 @@
 //   BF16X6  6 products: hi.hi + hi.mid + mid.hi + mid.mid + hi.lo + lo.hi
 //                                                       (three-term split, ~2^-24)
 // Each bfloat16 product is exact in binary32; the tensor core accumulates in binary32.
+//   FP8     e4m3 operands, one binary32 scale per (row of A, 128-element K block) and
+//           per (128-element K block, column of B), each the block's max |x| / 448;
+//           kind::f8f6f4 MMAs sum one K block in tensor memory and the epilogue adds
+//           sa * sb * block_sum into binary32 registers.
 // An optional K chunk restarts the tensor-memory accumulator every `kchunk`
 // elements and adds the chunk sums in registers, which bounds the growth of the
 // accumulation error with K.
@@ -31,6 +35,7 @@
 // memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
@@ -45,6 +50,7 @@ namespace {
 
 constexpr int BM = 128;  // UMMA M (one TMEM lane per output row)
 constexpr int BK = 64;   // 64 bfloat16 = 128 bytes = one swizzle row
+constexpr int BK8 = 128; // 128 e4m3 = 128 bytes = one swizzle row
 constexpr int kEpiWarps = 8;
 constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
@@ -142,6 +148,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+__device__ __forceinline__ void mma_fp8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -175,6 +191,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
+// Instruction descriptor for kind::f8f6f4 with e4m3 A and B (format code 0 at bits
+// 7-9 and 10-12), binary32 D, both K-major.
+template <int N_>
+__host__ __device__ constexpr uint32_t idesc_e4m3() {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
 // Products (plane of A, plane of B); planes: 0 = hi, 1 = mid (x6) or lo (x3), 2 = lo.
 //   x1: hi.hi;  x3: hi.hi, hi.lo, lo.hi;  x6: hi.hi, hi.mid, mid.hi, mid.mid, hi.lo, lo.hi
 __host__ __device__ constexpr int prod_a(int nprod, int i) {
@@ -196,7 +219,10 @@ struct EpiArgs {
     const float* C0;
     int M, N;
     float alpha, beta;
-    int vec;  // C, C0 16-byte aligned and N % 4 == 0
+    int vec;           // C, C0 16-byte aligned and N % 4 == 0
+    const float* sa;   // FP8: scale of (row, K block), row-major [Mp][kbs]
+    const float* sb;   // FP8: scale of (K block, column), row-major [kbs][sb_ld]
+    int kbs, sb_ld;
 };
 
 // Write 32 consecutive columns [gcol, gcol+32) of row grow from binary32 values v.
@@ -231,10 +257,10 @@ __device__ __forceinline__ void store_row32(const EpiArgs& e, int64_t grow, int6
     }
 }
 
-template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED>
+template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8 = false>
 struct TcCfg {
-    static constexpr uint32_t A_TILE = BM * BK * 2;
-    static constexpr uint32_t B_TILE = BN * BK * 2;
+    static constexpr uint32_t A_TILE = BM * 128;  // 128 rows x 128 bytes
+    static constexpr uint32_t B_TILE = BN * 128;
     static constexpr uint32_t STAGE = PA * A_TILE + PB * B_TILE;
     static constexpr int ACC = CHUNKED ? 2 : 1;  // accumulator buffers (double-buffered when chunked)
     // With more than one product, hi.hi accumulates in its own tensor-memory block and
@@ -250,14 +276,16 @@ struct TcCfg {
     static_assert(COLS <= 512, "accumulators exceed tensor memory");
     static_assert(BN % 64 == 0 && BN >= 64 && BN <= 256, "BN");
     static_assert(!CHUNKED || BN <= 128, "chunked sums live in registers: BN <= 128");
+    static_assert(!FP8 || (CHUNKED && NPROD == 1 && PA == 1 && PB == 1), "FP8 runs one plane, chunked per K block");
 };
 
-template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED>
+template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep,
                    int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int* err) {
-    using Cfg = TcCfg<BN, PA, PB, NPROD, STAGES, CHUNKED>;
-    constexpr uint32_t IDESC = idesc_bf16<BN>();
+    using Cfg = TcCfg<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>;
+    constexpr uint32_t IDESC = FP8 ? idesc_e4m3<BN>() : idesc_bf16<BN>();
+    constexpr int KBE = FP8 ? BK8 : BK;  // elements per K block
     constexpr int ACC = Cfg::ACC;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -330,10 +358,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                 const uint32_t st = tiles + (uint32_t)s * Cfg::STAGE;
 #pragma unroll
                 for (int p = 0; p < PA; ++p)
-                    tma_load_2d(st + (uint32_t)p * Cfg::A_TILE, &tmA, kb * BK, p * Mp + m0, full_bar(s));
+                    tma_load_2d(st + (uint32_t)p * Cfg::A_TILE, &tmA, kb * KBE, p * Mp + m0, full_bar(s));
 #pragma unroll
                 for (int p = 0; p < PB; ++p)
-                    tma_load_2d(st + PA * Cfg::A_TILE + (uint32_t)p * Cfg::B_TILE, &tmB, kb * BK, p * Np + n0,
+                    tma_load_2d(st + PA * Cfg::A_TILE + (uint32_t)p * Cfg::B_TILE, &tmB, kb * KBE, p * Np + n0,
                                 full_bar(s));
                 issued = kb + 1;
             }
@@ -375,7 +403,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                     const uint32_t a_base = tiles + (uint32_t)s * Cfg::STAGE;
                     const uint32_t b_base = a_base + PA * Cfg::A_TILE;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
+                    for (int kk = 0; kk < 4; ++kk) {  // 4 MMA K steps of 32 bytes per 128-byte block
 #pragma unroll
                         for (int pr = 0; pr < NPROD; ++pr) {
                             const uint64_t ad =
@@ -385,7 +413,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                             // first product into each accumulator block of a chunk overwrites it
                             const bool first = kb == kb0 && kk == 0 && (pr == 0 || (Cfg::SPLIT && pr == 1));
                             const uint32_t dd = d + ((Cfg::SPLIT && pr > 0) ? (uint32_t)BN : 0u);
-                            mma_bf16(dd, ad, bd, IDESC, first ? 0u : 1u);
+                            if constexpr (FP8)
+                                mma_fp8(dd, ad, bd, IDESC, first ? 0u : 1u);
+                            else
+                                mma_bf16(dd, ad, bd, IDESC, first ? 0u : 1u);
                         }
                     }
                     mma_commit(empty_bar(s));
@@ -437,7 +468,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] += __uint_as_float(r[i]);
                 }
-                if constexpr (CHUNKED) {
+                if constexpr (FP8) {
+                    // chunk c is K block c: scale by sa(row, c) * sb(c, column)
+                    const float sa = grow < ep.M ? ep.sa[grow * (int64_t)ep.kbs + c] : 0.0f;
+                    const float4* sb4 =
+                        reinterpret_cast<const float4*>(ep.sb + (int64_t)c * ep.sb_ld + n0 + colbase + g * 32);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 b = sb4[j];
+                        sum[g * 32 + 4 * j + 0] = fmaf(sa * b.x, v[4 * j + 0], sum[g * 32 + 4 * j + 0]);
+                        sum[g * 32 + 4 * j + 1] = fmaf(sa * b.y, v[4 * j + 1], sum[g * 32 + 4 * j + 1]);
+                        sum[g * 32 + 4 * j + 2] = fmaf(sa * b.z, v[4 * j + 2], sum[g * 32 + 4 * j + 2]);
+                        sum[g * 32 + 4 * j + 3] = fmaf(sa * b.w, v[4 * j + 3], sum[g * 32 + 4 * j + 3]);
+                    }
+                } else if constexpr (CHUNKED) {
 #pragma unroll
                     for (int i = 0; i < 32; ++i) sum[g * 32 + i] += v[i];
                 } else {
@@ -544,6 +588,78 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const float* __restrict
     }
 }
 
+// ---- FP8 quantise kernels -----------------------------------------------------------------------
+
+// e4m3 with one scale per 128-element block: s = max|x| / 448 (1 for an all-zero
+// block), q = e4m3(x / s) rounded to nearest, saturating.
+__device__ __forceinline__ float fp8_scale(float amax) { return amax > 0.0f ? amax * (1.0f / 448.0f) : 1.0f; }
+
+__device__ __forceinline__ uint32_t fp8_pack4(float a, float b, float c, float d, float inv) {
+    const uint32_t q0 = __nv_cvt_float_to_fp8(a * inv, __NV_SATFINITE, __NV_E4M3);
+    const uint32_t q1 = __nv_cvt_float_to_fp8(b * inv, __NV_SATFINITE, __NV_E4M3);
+    const uint32_t q2 = __nv_cvt_float_to_fp8(c * inv, __NV_SATFINITE, __NV_E4M3);
+    const uint32_t q3 = __nv_cvt_float_to_fp8(d * inv, __NV_SATFINITE, __NV_E4M3);
+    return q0 | (q1 << 8) | (q2 << 16) | (q3 << 24);
+}
+
+// A (M x K) -> q [Mp][Kp] e4m3, sa [Mp][Kp/128]; one warp per (row, K block), lane = 4 k.
+__global__ void quant_rows_fp8_kernel(const float* __restrict__ A, int64_t M, int64_t K, int64_t Mp, int64_t Kp,
+                                      uint8_t* __restrict__ q, float* __restrict__ sa) {
+    const int lane = threadIdx.x & 31;
+    const int64_t kbs = Kp / 128;
+    const int64_t nwork = Mp * kbs;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nwork;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t i = w / kbs, kb = w % kbs, k0 = kb * 128 + lane * 4;
+        float x[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[t] = (i < M && k0 + t < K) ? A[i * K + k0 + t] : 0.0f;
+        float amax = fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fmaxf(fabsf(x[2]), fabsf(x[3])));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        const float sc = fp8_scale(amax);
+        *reinterpret_cast<uint32_t*>(q + i * Kp + k0) = fp8_pack4(x[0], x[1], x[2], x[3], 1.0f / sc);
+        if (lane == 0) sa[i * kbs + kb] = sc;
+    }
+}
+
+// B (K x N) -> q^T [Np][Kp] e4m3, sb [Kp/128][Np]; CTA = (K block, 32 columns).
+__global__ void __launch_bounds__(256) quant_cols_fp8_kernel(const float* __restrict__ B, int64_t K, int64_t N,
+                                                             int64_t Np, int64_t Kp, uint8_t* __restrict__ q,
+                                                             float* __restrict__ sb) {
+    __shared__ float tile[128][33];
+    __shared__ float red[8][32];
+    __shared__ float inv[32];
+    const int t = threadIdx.x, c = t & 31, g = t >> 5;
+    const int64_t kb = blockIdx.y, n0 = (int64_t)blockIdx.x * 32;
+    float m = 0.0f;
+    for (int r = g; r < 128; r += 8) {
+        const int64_t k = kb * 128 + r, n = n0 + c;
+        const float v = (k < K && n < N) ? B[k * N + n] : 0.0f;
+        tile[r][c] = v;
+        m = fmaxf(m, fabsf(v));
+    }
+    red[g][c] = m;
+    __syncthreads();
+    if (g == 0) {
+        float a = red[0][c];
+        for (int j = 1; j < 8; ++j) a = fmaxf(a, red[j][c]);
+        const float sc = fp8_scale(a);
+        inv[c] = 1.0f / sc;
+        sb[kb * Np + n0 + c] = sc;
+    }
+    __syncthreads();
+    // column n = t / 8 of the tile becomes row n0 + n of q^T; 16 k per thread
+    const int n = t >> 3, k16 = (t & 7) * 16;
+    const float iv = inv[n];
+    uint4 o;
+    o.x = fp8_pack4(tile[k16 + 0][n], tile[k16 + 1][n], tile[k16 + 2][n], tile[k16 + 3][n], iv);
+    o.y = fp8_pack4(tile[k16 + 4][n], tile[k16 + 5][n], tile[k16 + 6][n], tile[k16 + 7][n], iv);
+    o.z = fp8_pack4(tile[k16 + 8][n], tile[k16 + 9][n], tile[k16 + 10][n], tile[k16 + 11][n], iv);
+    o.w = fp8_pack4(tile[k16 + 12][n], tile[k16 + 13][n], tile[k16 + 14][n], tile[k16 + 15][n], iv);
+    *reinterpret_cast<uint4*>(q + (n0 + n) * Kp + kb * 128 + k16) = o;
+}
+
 // ---- host side ------------------------------------------------------------------------------------
 
 inline int64_t ru(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -567,12 +683,16 @@ bool get_encode(std::string* why) {
     return true;
 }
 
-bool make_map(CUtensorMap* map, void* base, int64_t inner, int64_t rows, int box_rows, std::string* why) {
+// 2-D map over a row-major plane stack: `inner` elements per row (bf16, or e4m3 as
+// bytes), box = one 128-byte row segment x box_rows rows, 128-byte swizzle.
+bool make_map(CUtensorMap* map, void* base, int64_t inner, int64_t rows, int box_rows, bool fp8, std::string* why) {
+    const int esz = fp8 ? 1 : 2;
     cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-    cuuint64_t gstride[1] = {(cuuint64_t)inner * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)inner * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim, gstride, box, estr,
+    CUresult r = g_encode(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim,
+                          gstride, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -582,12 +702,12 @@ bool make_map(CUtensorMap* map, void* base, int64_t inner, int64_t rows, int box
     return true;
 }
 
-template <int BN, int P, int NPROD, int STAGES, bool CHUNKED>
+template <int BN, int P, int NPROD, int STAGES, bool CHUNKED, bool FP8 = false>
 cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const EpiArgs& ep, int Mp, int Np, int num_kb,
                        int chunk_kb, int* err, cudaStream_t st) {
     // Np is the plane stride (a multiple of 256); only ceil(N / BN) column tiles hold data
-    using Cfg = TcCfg<BN, P, P, NPROD, STAGES, CHUNKED>;
-    auto kern = gemm_tc_kernel<BN, P, P, NPROD, STAGES, CHUNKED>;
+    using Cfg = TcCfg<BN, P, P, NPROD, STAGES, CHUNKED, FP8>;
+    auto kern = gemm_tc_kernel<BN, P, P, NPROD, STAGES, CHUNKED, FP8>;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
@@ -601,9 +721,34 @@ cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const EpiAr
     return cudaGetLastError();
 }
 
+
+cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K,
+                            float alpha, float beta, void* scratch, size_t scratch_bytes, int* err, cudaStream_t st,
+                            TcEvents& ev, std::string* why);
+
 }  // namespace
 
+// FP8 scratch: q(A) [Mp][Kp], q(B^T) [Np][Kp], sa [Mp][Kp/128], sb [Kp/128][Np]
+struct Fp8Layout {
+    int64_t Mp, Np, Kp, kbs;
+    size_t qa, qb, sa, sb, total;
+};
+Fp8Layout fp8_layout(int64_t M, int64_t N, int64_t K) {
+    Fp8Layout L;
+    L.Mp = ru(std::max<int64_t>(M, 1), BM);
+    L.Np = ru(std::max<int64_t>(N, 1), 256);
+    L.Kp = ru(std::max<int64_t>(K, 1), BK8);
+    L.kbs = L.Kp / BK8;
+    L.qa = 0;
+    L.qb = ru((int64_t)(L.Mp * L.Kp), 1024);
+    L.sa = L.qb + ru(L.Np * L.Kp, 1024);
+    L.sb = L.sa + ru(L.Mp * L.kbs * 4, 1024);
+    L.total = L.sb + ru(L.kbs * L.Np * 4, 1024);
+    return L;
+}
+
 size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K) {
+    if (prec == GAO_GEMM_FP8) return fp8_layout(M, N, K).total;
     if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_BF16X6) return 0;
     const int64_t P = planes_of(prec);
     const int64_t Mp = ru(std::max<int64_t>(M, 1), BM), Np = ru(std::max<int64_t>(N, 1), 256),
@@ -615,7 +760,7 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
                            int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
                            size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why) {
     ev.launches = 0;
-    if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_BF16X6) {
+    if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_FP8) {
         if (why) *why = "precision not available on the tensor-core path";
         return cudaErrorNotSupported;
     }
@@ -632,6 +777,7 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         return cudaErrorInvalidValue;
     }
     if (!get_encode(why)) return cudaErrorNotSupported;
+    if (prec == GAO_GEMM_FP8) return launch_gemm_fp8(C, A, B, C0, M, N, K, alpha, beta, scratch, scratch_bytes, err, st, ev, why);
     const int P = planes_of(prec);
     const int64_t Mp = ru(M, BM), Np = ru(N, 256), Kp = ru(K, BK);
     if (tc_scratch_bytes(prec, M, N, K) > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
@@ -668,10 +814,10 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     int bn = 128;
     if (!chunked && P == 1 && (tile_cfg == 2 || tile_cfg == 0)) bn = 256;
     CUtensorMap ta, tb;
-    if (!make_map(&ta, pa, Kp, (int64_t)P * Mp, BM, why)) return cudaErrorInvalidValue;
-    if (!make_map(&tb, pb, Kp, (int64_t)P * Np, bn, why)) return cudaErrorInvalidValue;
+    if (!make_map(&ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;
+    if (!make_map(&tb, pb, Kp, (int64_t)P * Np, bn, false, why)) return cudaErrorInvalidValue;
     EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
-               (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0};
+               (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, nullptr, nullptr, 0, 0};
     if (ev.k0) cudaEventRecord(ev.k0, st);
     cudaError_t e;
     const int mp = (int)Mp, np = (int)Np;
@@ -692,5 +838,47 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     if (ev.k1) cudaEventRecord(ev.k1, st);
     return cudaSuccess;
 }
+
+
+namespace {
+cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K,
+                            float alpha, float beta, void* scratch, size_t scratch_bytes, int* err, cudaStream_t st,
+                            TcEvents& ev, std::string* why) {
+    const Fp8Layout L = fp8_layout(M, N, K);
+    if (L.total > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
+        if (why) *why = "FP8 scratch too small or misaligned";
+        return cudaErrorInvalidValue;
+    }
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    uint8_t *qa = base + L.qa, *qb = base + L.qb;
+    float *sa = reinterpret_cast<float*>(base + L.sa), *sb = reinterpret_cast<float*>(base + L.sb);
+    {
+        const int64_t warps = L.Mp * L.kbs;
+        int64_t g = (warps * 32 + 255) / 256;
+        if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
+        quant_rows_fp8_kernel<<<(unsigned)g, 256, 0, st>>>(A, M, K, L.Mp, L.Kp, qa, sa);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)(L.Np / 32), (unsigned)L.kbs);
+        if (grid.y > 65535u) return cudaErrorInvalidValue;
+        quant_cols_fp8_kernel<<<grid, 256, 0, st>>>(B, K, N, L.Np, L.Kp, qb, sb);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        ev.launches += 2;
+    }
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, qa, L.Kp, L.Mp, BM, true, why)) return cudaErrorInvalidValue;
+    if (!make_map(&tb, qb, L.Kp, L.Np, 128, true, why)) return cudaErrorInvalidValue;
+    EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
+               (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, sa, sb, (int)L.kbs,
+               (int)L.Np};
+    if (ev.k0) cudaEventRecord(ev.k0, st);
+    cudaError_t e = launch_mma<128, 1, 1, 6, true, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, (int)L.kbs, 1, err, st);
+    if (e != cudaSuccess) return e;
+    ev.launches += 1;
+    if (ev.k1) cudaEventRecord(ev.k1, st);
+    return cudaSuccess;
+}
+}  // namespace
 
 }  // namespace gao

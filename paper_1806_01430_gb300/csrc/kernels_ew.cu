@@ -218,11 +218,25 @@ __global__ void rowsum_kernel(float* __restrict__ out, const float* __restrict__
 
 // ---- FROBENIUS / SUM -------------------------------------------------------------------------
 
-// Each thread forms a binary32 partial over one float4 (sum of squares, or sum),
-// widens it to binary64 and accumulates in binary64; blocks reduce in a fixed tree;
-// the last block to finish adds the block partials in index order.  Binary64 work is
-// one add per 4 elements, so the loop stays bound by HBM on a part with a low
-// binary64 rate.
+// Neumaier-compensated binary32 accumulation: s + c carries the running sum with an
+// error of about 2u times the sum of magnitudes, independent of the term count.
+__device__ __forceinline__ void comp_add(float& s, float& c, float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+}
+
+template <bool SQUARES>
+__device__ __forceinline__ float part4(const float4 a) {
+    // squares: each rounded once, then a pairwise tree: at most 3u relative (positive terms)
+    return SQUARES ? (a.x * a.x + a.y * a.y) + (a.z * a.z + a.w * a.w) : (a.x + a.y) + (a.z + a.w);
+}
+
+// Each thread adds binary32 partials of one float4 into a compensated binary32 sum
+// (four independent 16-byte loads in flight per iteration); threads are combined in
+// binary64 by a fixed tree per block, and the last block to finish adds the block
+// partials in index order.  Binary64 arithmetic stays out of the streaming loop: its
+// rate on this part is far below what HBM bandwidth needs.
 template <bool SQUARES>
 __global__ void __launch_bounds__(256) reduce64_kernel(double* __restrict__ out, const float* __restrict__ in,
                                                        int64_t n, double* __restrict__ partials,
@@ -231,35 +245,26 @@ __global__ void __launch_bounds__(256) reduce64_kernel(double* __restrict__ out,
     __shared__ bool last;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    double acc = 0.0;
+    float s = 0.0f, c = 0.0f;
     const bool vec = aligned16(in);
     const int64_t nvec = vec ? n / 4 : 0;
     if (vec) {
         const float4* in4 = reinterpret_cast<const float4*>(in);
         int64_t i = tid;
-        for (; i + nthreads < nvec; i += 2 * nthreads) {
-            const float4 a = in4[i], b = in4[i + nthreads];
-            float pa, pb;
-            if (SQUARES) {
-                pa = fmaf(a.w, a.w, fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x)));
-                pb = fmaf(b.w, b.w, fmaf(b.z, b.z, fmaf(b.y, b.y, b.x * b.x)));
-            } else {
-                pa = (a.x + a.y) + (a.z + a.w);
-                pb = (b.x + b.y) + (b.z + b.w);
-            }
-            acc += (double)pa;
-            acc += (double)pb;
+        for (; i + 3 * nthreads < nvec; i += 4 * nthreads) {
+            const float4 a = in4[i], b = in4[i + nthreads], d = in4[i + 2 * nthreads], e = in4[i + 3 * nthreads];
+            comp_add(s, c, part4<SQUARES>(a));
+            comp_add(s, c, part4<SQUARES>(b));
+            comp_add(s, c, part4<SQUARES>(d));
+            comp_add(s, c, part4<SQUARES>(e));
         }
-        for (; i < nvec; i += nthreads) {
-            const float4 a = in4[i];
-            float pa = SQUARES ? fmaf(a.w, a.w, fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x))) : (a.x + a.y) + (a.z + a.w);
-            acc += (double)pa;
-        }
+        for (; i < nvec; i += nthreads) comp_add(s, c, part4<SQUARES>(in4[i]));
     }
     for (int64_t i = nvec * 4 + tid; i < n; i += nthreads) {
         const float v = in[i];
-        acc += SQUARES ? (double)v * (double)v : (double)v;
+        comp_add(s, c, SQUARES ? v * v : v);
     }
+    double acc = (double)s + (double)c;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -276,9 +281,9 @@ __global__ void __launch_bounds__(256) reduce64_kernel(double* __restrict__ out,
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double*)partials)[b];
-        *out = SQUARES ? sqrt(s) : s;
+        double t = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)partials)[b];
+        *out = SQUARES ? sqrt(t) : t;
         *counter = 0u;  // ready for the next launch on this stream
     }
 }
