@@ -404,6 +404,63 @@ def our_arm(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def batch_arm(args, world, rank, local):
+    """Batched-population workload: a suite of programs of uneven sizes (n log-uniform
+    in [128, 2048]), every gene evaluated over the whole suite with one graph launch
+    per GPU loop and one grouped tensor-core GEMM launch; the Simple GA runs on top.
+    value = GA fitness evaluations per second (individuals scored, measured or served
+    from the cache, over the wall time of the GA)."""
+    import torch
+
+    import paper_1806_01430_gb300 as gao
+    torch.cuda.set_device(local)
+    sizes = W.batch_sizes(args.programs)
+    progs = [W.six_loop(n, W.SEED_CONFIG3_BASE + p, outputs=("f",)) for p, n in enumerate(sizes)]
+    handles = [gao.prog_from_workload(pr, gemm_prec=PREC[args.prec]) for pr in progs]
+    b = gao.batch_create(handles)
+    # warm-up: the all-GPU gene once (not cached afterwards: fresh batch for the timed GA)
+    gao.batch_evaluate(b, [(1 << 6) - 1])
+    st_w = gao.batch_stats(b)
+    gao.batch_destroy(b)
+    b = gao.batch_create(handles)
+    torch.cuda.synchronize()
+    barrier(world)
+    with Clocks(local) as clk:
+        time.sleep(0.3)
+        t0 = clk.mark()
+        res = gao.batch_ga_run(b, pop=args.pop, generations=args.generations, pc=0.9, pm=0.05,
+                               seed=7 + rank, timeout_s=-1.0)
+        t1 = clk.mark()
+        time.sleep(0.25)
+    st = gao.batch_stats(b)
+    wall = allmax(world, t1 - t0)
+    evals = allsum(world, args.pop * args.generations)
+    gemm_tf = st["gemm_flops"] / (st["gemm_phase_ms"] / 1e3) / 1e12 if st["gemm_phase_ms"] > 0 else None
+    if rank == 0:
+        pk = peaks()
+        peak = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        line = {"metric": "ga_evals_per_s", "value": evals / wall, "unit": "evals/s", "n_gpus": world,
+                "steps": args.generations, "warmup": 1, "ms_per_step": wall / args.generations * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+                "data": "synthetic (seeded counter hash, U[-1,1))",
+                "config": {"workload": f"batch_{args.programs}_programs_n128_2048_pop{args.pop}_gen{args.generations}",
+                           "programs": args.programs, "sizes_min_max": [min(sizes), max(sizes)], "pop": args.pop,
+                           "generations": args.generations, "gemm": args.prec},
+                "executed_genes": st["executed"], "served_genes": st["served"],
+                "executed_program_evals_per_s": st["executed"] * args.programs / max(st["exec_seconds"], 1e-9),
+                "best_gene": format(res.best_mask, "06b"), "best_s": res.best_s,
+                "grouped_gemm": {"tiles": st["gemm_tiles"], "phase_ms": st["gemm_phase_ms"],
+                                 "effective_tflops": gemm_tf,
+                                 "hw_frac": (gemm_tf * PRODUCTS[args.prec] / peak) if gemm_tf else None},
+                "launches_per_all_gpu_gene": st["launches_per_gene"], "graphs": st["graphs"],
+                "all_gpu_gene_warm_s": st_w["exec_seconds"],
+                "history": [{"best_s": h["best_s"], "evaluated": h["evaluated"], "hits": h["cache_hits"]}
+                            for h in res.history],
+                "clocks": clk.summary(t0, t1)}
+        print(json.dumps(line), flush=True)
+    gao.batch_destroy(b)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,7 +468,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--workload", default="six_loop", choices=["six_loop", "twelve_loop"])
+    ap.add_argument("--workload", default="six_loop", choices=["six_loop", "twelve_loop", "batch"])
+    ap.add_argument("--programs", type=int, default=64)
+    ap.add_argument("--pop", type=int, default=20)
+    ap.add_argument("--generations", type=int, default=20)
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--prec", default="bf16x6", choices=list(PREC))
@@ -425,6 +485,8 @@ def main():
     world, rank, local = dist_init()
     if args.impl == "reference":
         reference_arm(args, world, rank)
+    elif args.workload == "batch":
+        batch_arm(args, world, rank, local)
     else:
         our_arm(args, world, rank, local)
     if world > 1:

@@ -203,6 +203,41 @@ gao_status ga_run(gao_prog *const *progs, int n_progs, const gao_ga_params *para
  * non-finite time marks a failed gene (fitness 0).  Host only, no GPU. */
 gao_status ga_run_table(const double *times, int n_genes, const gao_ga_params *params, gao_ga_result *result);
 
+/* ---- batched evaluation over a program suite ---------------------------------- */
+
+/* A batch scores genes over a suite of programs that share one loop structure (same
+ * loop kinds in the same order, same GEMM precision), e.g. six-loop programs of many
+ * sizes.  A gene runs on every program at once, loop by loop: on the GPU all programs'
+ * loop i is one CUDA graph launch (captured by batch_create; small kernels of different
+ * programs run concurrently; a tensor-core GEMM loop is one grouped tcgen05 launch over
+ * every program's tiles), on the host the programs' loops run one after another.  The
+ * gene's time is the wall time of the whole suite, boundary copies included; a gene
+ * measured before is served from the batch's cache (Sec. 4).  The programs stay owned
+ * by the caller, must outlive the batch, and must not run elsewhere meanwhile; each
+ * program's host and device buffers hold its results after a gene runs. */
+typedef struct gao_batch gao_batch;
+
+typedef struct gao_batch_stat {
+    int64_t executed;          /* genes measured                                        */
+    int64_t served;            /* genes answered from the cache                         */
+    double exec_seconds;       /* host wall time spent measuring genes                  */
+    double gemm_phase_ms;      /* GPU time of the last GEMM phase (splits + grouped MMA) */
+    double gemm_flops;         /* 2MNK summed over the suite's GEMMs                    */
+    int32_t gemm_tiles;        /* CTAs of the grouped GEMM launch                       */
+    int32_t launches_per_gene; /* kernels in the captured graphs (all loops on the GPU) */
+    int32_t graphs;            /* phase graphs captured                                 */
+    int32_t _pad;
+} gao_batch_stat;
+
+gao_status batch_create(gao_prog *const *progs, int n_progs, gao_batch **out);
+/* Same contract as ga_evaluate, for genes over the whole suite. */
+gao_status batch_evaluate(gao_batch *b, const uint64_t *population, int pop, double *fitness_out,
+                          double *seconds_out, int *cache_hits_out);
+/* The Simple GA with batched evaluation (same draws as ga_run). */
+gao_status batch_ga_run(gao_batch *b, const gao_ga_params *params, gao_ga_result *result);
+gao_status batch_stats(gao_batch *b, gao_batch_stat *out);
+void batch_destroy(gao_batch *b);
+
 /* ---- misc ------------------------------------------------------------------ */
 
 /* Message of the last failing call on this thread ("" if none). */

@@ -12,7 +12,7 @@
  * therefore the plain definition of each loop of the program, evaluated in
  * program order in IEEE double precision:
  *
- *   INIT       x = (h >> 40) * 2^-23 - 1,  h = SplitMix64(key)           [input generator]
+ *   INIT       x = u24 * 2^-23 - 1, u24 a 24-bit field of h = SplitMix64(key)  [input generator]
  *   GEMM       C = alpha * A B + beta * C0          (Sec. 5.1.1: matrix product benchmark)
  *   AXPY       D = X + alpha * Y                    (scale-add, D = C + 2A)
  *   TRANSPOSE  E = D^T
@@ -72,10 +72,11 @@ static uint64_t orc_key(uint64_t seed, uint64_t buf, uint64_t idx) {
 }
 
 /* U[-1,1) value of element idx of buffer buf: a 24-bit integer scaled by 2^-23,
- * minus one.  Exactly representable in binary32. */
+ * minus one, exactly representable in binary32.  One hash serves two elements:
+ * element 2j takes bits 40..63 and element 2j+1 bits 16..39 of the hash of key j. */
 double orc_init_value(uint64_t seed, int64_t buf, int64_t idx) {
-    uint64_t h = orc_splitmix64(orc_key(seed, (uint64_t)buf, (uint64_t)idx));
-    int64_t u24 = (int64_t)(h >> 40);
+    uint64_t h = orc_splitmix64(orc_key(seed, (uint64_t)buf, (uint64_t)(idx >> 1)));
+    int64_t u24 = (idx & 1) ? (int64_t)((h >> 16) & 0xFFFFFFu) : (int64_t)(h >> 40);
     return (double)(u24 - (1LL << 23)) / 8388608.0;
 }
 

@@ -72,6 +72,12 @@ class gao_ga_result(ctypes.Structure):
                 ("populations", ctypes.POINTER(ctypes.c_uint64))]
 
 
+class gao_batch_stat(ctypes.Structure):
+    _fields_ = [("executed", ctypes.c_int64), ("served", ctypes.c_int64), ("exec_seconds", ctypes.c_double),
+                ("gemm_phase_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double), ("gemm_tiles", ctypes.c_int32),
+                ("launches_per_gene", ctypes.c_int32), ("graphs", ctypes.c_int32), ("_pad", ctypes.c_int32)]
+
+
 # every entry point of include/gao.h: name -> (restype, argtypes)
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -97,6 +103,13 @@ SIGNATURES = {
     "gao_version": (ctypes.c_char_p, []),
     "gao_selftest_device_wait": (ctypes.c_int, [ctypes.c_double, _P]),
     "gao_colmax_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "batch_evaluate": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "batch_ga_run": (ctypes.c_int, [_P, ctypes.POINTER(gao_ga_params), ctypes.POINTER(gao_ga_result)]),
+    "batch_stats": (ctypes.c_int, [_P, ctypes.POINTER(gao_batch_stat)]),
+    "batch_destroy": (None, [_P]),
 }
 
 _lib = None
@@ -358,3 +371,54 @@ def gao_colmax_noalloc(dev_in: int, rows: int, cols: int, dev_out: int, stream=N
     returns the status (see include/gao.h for the shared-scratch rules)."""
     return int(lib().gao_colmax_noalloc(ctypes.c_void_p(dev_in), int(rows), int(cols), ctypes.c_void_p(dev_out),
                                         _stream_handle(stream)))
+
+
+class Batch:
+    """Handle of a gao_batch (owning); keeps its programs alive."""
+
+    def __init__(self, handle, progs):
+        self.handle = handle
+        self.progs = list(progs)
+
+    def __del__(self):
+        try:
+            batch_destroy(self)
+        except Exception:
+            pass
+
+
+def batch_create(progs: Sequence[Prog]) -> Batch:
+    h = ctypes.c_void_p(None)
+    _check(lib().batch_create(_handles(progs), len(progs), ctypes.byref(h)), "batch_create")
+    return Batch(h, progs)
+
+
+def batch_evaluate(b: Batch, population: Sequence[int]):
+    """Returns (fitness[pop], seconds[pop], cache_hits)."""
+    pop = len(population)
+    pa = (ctypes.c_uint64 * pop)(*[int(m) for m in population])
+    fit = (ctypes.c_double * pop)()
+    sec = (ctypes.c_double * pop)()
+    hits = ctypes.c_int(0)
+    _check(lib().batch_evaluate(b.handle, pa, pop, fit, sec, ctypes.byref(hits)), "batch_evaluate")
+    return np.array(fit[:]), np.array(sec[:]), int(hits.value)
+
+
+def batch_ga_run(b: Batch, pop=12, generations=12, pc=0.9, pm=0.05, seed=0, elite=1, mutation=0,
+                 timeout_s=0.0) -> GAResult:
+    params = _params(pop, generations, pc, pm, seed, elite, mutation, timeout_s)
+    r, hist, pops = _result(params)
+    _check(lib().batch_ga_run(b.handle, ctypes.byref(params), ctypes.byref(r)), "batch_ga_run")
+    return _unpack(r, hist, pops, params)
+
+
+def batch_stats(b: Batch) -> Dict:
+    st = gao_batch_stat()
+    _check(lib().batch_stats(b.handle, ctypes.byref(st)), "batch_stats")
+    return {k: getattr(st, k) for k, _ in gao_batch_stat._fields_ if k != "_pad"}
+
+
+def batch_destroy(b: Batch) -> None:
+    if b.handle is not None and b.handle.value:
+        lib().batch_destroy(b.handle)
+        b.handle = ctypes.c_void_p(None)

@@ -41,10 +41,13 @@ __host__ __device__ inline uint64_t sm64_hash(uint64_t state) { return sm64_mix(
 __host__ __device__ inline uint64_t init_key(uint64_t seed, uint32_t buf, uint64_t idx) {
     return (seed << 40) ^ ((uint64_t)buf << 36) ^ idx;
 }
-// U[-1,1) binary32 value: 24-bit integer times 2^-23, minus one (exact).
+// U[-1,1) binary32 value from a 24-bit integer u24: u24 * 2^-23 - 1 (exact).
+__host__ __device__ inline float u24_to_value(uint32_t u24) { return (float)((int32_t)u24 - (1 << 23)) * (1.0f / 8388608.0f); }
+// Element idx of an INIT buffer: the hash of key idx/2 gives two elements, bits 40..63
+// for the even one and bits 16..39 for the odd one.
 __host__ __device__ inline float init_value(uint64_t seed, uint32_t buf, uint64_t idx) {
-    const int32_t u24 = (int32_t)(sm64_hash(init_key(seed, buf, idx)) >> 40);
-    return (float)(u24 - (1 << 23)) * (1.0f / 8388608.0f);
+    const uint64_t h = sm64_hash(init_key(seed, buf, idx >> 1));
+    return u24_to_value((idx & 1) ? (uint32_t)((h >> 16) & 0xFFFFFFu) : (uint32_t)(h >> 40));
 }
 // Power-of-two exponent in [-10, 10] of row `row`'s factor for row-scaled inputs:
 // round((sum of twelve 24-bit uniforms / 2^24 - 6) * 10/3), in integer arithmetic.

@@ -40,10 +40,14 @@
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <string.h>
+
+#include <algorithm>
 #include <mutex>
 #include <string>
 
 #include "gao_internal.h"
+#include "gemm_tc.h"
 
 namespace gao {
 namespace {
@@ -214,16 +218,7 @@ static_assert(prod_a(3, 0) == 0 && prod_b(3, 0) == 0 && prod_a(3, 1) == 0 && pro
                   prod_b(3, 2) == 0,
               "x3 product table");
 
-struct EpiArgs {
-    float* C;
-    const float* C0;
-    int M, N;
-    float alpha, beta;
-    int vec;           // C, C0 16-byte aligned and N % 4 == 0
-    const float* sa;   // FP8: scale of (row, K block), row-major [Mp][kbs]
-    const float* sb;   // FP8: scale of (K block, column), row-major [kbs][sb_ld]
-    int kbs, sb_ld;
-};
+
 
 // Write 32 consecutive columns [gcol, gcol+32) of row grow from binary32 values v.
 __device__ __forceinline__ void store_row32(const EpiArgs& e, int64_t grow, int64_t gcol, const float* v) {
@@ -279,10 +274,10 @@ struct TcCfg {
     static_assert(!FP8 || (CHUNKED && NPROD == 1 && PA == 1 && PB == 1), "FP8 runs one plane, chunked per K block");
 };
 
+// One 128 x BN output tile (row tile tm, column tile tn) of one problem.
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
-__global__ void __launch_bounds__(kThreadsTc, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep,
-                   int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int* err) {
+__device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmB, const EpiArgs& ep,
+                                             int Mp, int Np, int num_kb, int chunk_kb, int tm, int tn, int* err) {
     using Cfg = TcCfg<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>;
     constexpr uint32_t IDESC = FP8 ? idesc_e4m3<BN>() : idesc_bf16<BN>();
     constexpr int KBE = FP8 ? BK8 : BK;  // elements per K block
@@ -303,15 +298,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // tile of this CTA: groups of 16 row-tiles, row-tile fastest inside a group, so the
-    // CTAs of one wave share A row panels and B column panels in L2
-    const int bid = blockIdx.x;
-    constexpr int GROUP = 16;
-    const int group_tiles = GROUP * tiles_n;
-    const int first_m = (bid / group_tiles) * GROUP;
-    const int gm = min(tiles_m - first_m, GROUP);
-    const int tm = first_m + (bid % group_tiles) % gm;
-    const int tn = (bid % group_tiles) / gm;
     const int m0 = tm * BM, n0 = tn * BN;
     const int nchunks = (num_kb + chunk_kb - 1) / chunk_kb;
 
@@ -334,8 +320,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         tmem_relinquish();
     }
     if (warp == 0 && lane == 0) {
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
+        tma_prefetch_desc(tmA);
+        tma_prefetch_desc(tmB);
     }
     tc_fence_before();
     __syncthreads();
@@ -358,10 +344,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                 const uint32_t st = tiles + (uint32_t)s * Cfg::STAGE;
 #pragma unroll
                 for (int p = 0; p < PA; ++p)
-                    tma_load_2d(st + (uint32_t)p * Cfg::A_TILE, &tmA, kb * KBE, p * Mp + m0, full_bar(s));
+                    tma_load_2d(st + (uint32_t)p * Cfg::A_TILE, tmA, kb * KBE, p * Mp + m0, full_bar(s));
 #pragma unroll
                 for (int p = 0; p < PB; ++p)
-                    tma_load_2d(st + PA * Cfg::A_TILE + (uint32_t)p * Cfg::B_TILE, &tmB, kb * KBE, p * Np + n0,
+                    tma_load_2d(st + PA * Cfg::A_TILE + (uint32_t)p * Cfg::B_TILE, tmB, kb * KBE, p * Np + n0,
                                 full_bar(s));
                 issued = kb + 1;
             }
@@ -506,6 +492,47 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         tc_fence_after();
         tmem_dealloc(tmem, Cfg::TMEM_COLS);
     }
+}
+
+// Row tile tm and column tile tn of CTA `bid` in a tiles_m x tiles_n grid: groups of 16
+// row tiles, row tile fastest inside a group, so the CTAs of one wave share A row
+// panels and B column panels in L2.
+__device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int& tm, int& tn) {
+    constexpr int GROUP = 16;
+    const int group_tiles = GROUP * tiles_n;
+    const int first_m = (bid / group_tiles) * GROUP;
+    const int gm = min(tiles_m - first_m, GROUP);
+    tm = first_m + (bid % group_tiles) % gm;
+    tn = (bid % group_tiles) / gm;
+}
+
+template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep,
+                   int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int* err) {
+    int tm, tn;
+    raster((int)blockIdx.x, tiles_m, tiles_n, tm, tn);
+    gemm_tc_tile<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tm, tn, err);
+}
+
+// Grouped launch: CTA b serves tile b - tile_start of the problem whose range holds b
+// (binary search over the problems' tile_start, which increase with the index).
+template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    gemm_tc_grouped_kernel(const TcProblem* __restrict__ probs, int nprob, int* err) {
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].tile_start <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const TcProblem* P = probs + lo;
+    const EpiArgs ep = P->ep;
+    int tm, tn;
+    raster(b - P->tile_start, P->tiles_m, P->tiles_n, tm, tn);
+    gemm_tc_tile<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(&P->ta, &P->tb, ep, P->Mp, P->Np, P->num_kb, P->chunk_kb,
+                                                          tm, tn, err);
 }
 
 // ---- split kernels ------------------------------------------------------------------------------
@@ -880,5 +907,121 @@ cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const floa
     return cudaSuccess;
 }
 }  // namespace
+
+
+// ---- grouped launches ------------------------------------------------------------------------------
+
+namespace {
+
+template <int BN, int P, int NPROD, int STAGES, bool CHUNKED, bool FP8 = false>
+cudaError_t launch_grouped_t(const TcProblem* d_probs, int nprob, int total_tiles, int* err, cudaStream_t st) {
+    using Cfg = TcCfg<BN, P, P, NPROD, STAGES, CHUNKED, FP8>;
+    auto kern = gemm_tc_grouped_kernel<BN, P, P, NPROD, STAGES, CHUNKED, FP8>;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (total_tiles <= 0) return cudaSuccess;
+    kern<<<(unsigned)total_tiles, kThreadsTc, Cfg::SMEM, st>>>(d_probs, nprob, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_available(std::string* why) { return get_encode(why); }
+
+cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
+                       int64_t K, float alpha, float beta, int kchunk, void* scratch, size_t scratch_bytes,
+                       cudaStream_t st, TcProblem* prob, int* launches, std::string* why) {
+    *launches = 0;
+    memset(prob, 0, sizeof(*prob));
+    if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_FP8 || M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) ||
+        N > (1 << 30) || K > (1 << 30)) {
+        if (why) *why = "grouped tensor-core GEMM needs a tensor-core precision and positive sizes";
+        return cudaErrorInvalidValue;
+    }
+    if (!get_encode(why)) return cudaErrorNotSupported;
+    if (tc_scratch_bytes(prec, M, N, K) > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
+        if (why) *why = "tensor-core scratch too small or misaligned";
+        return cudaErrorInvalidValue;
+    }
+    const int vec = (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0;
+    if (prec == GAO_GEMM_FP8) {
+        const Fp8Layout L = fp8_layout(M, N, K);
+        uint8_t* base = static_cast<uint8_t*>(scratch);
+        uint8_t *qa = base + L.qa, *qb = base + L.qb;
+        float *sa = reinterpret_cast<float*>(base + L.sa), *sb = reinterpret_cast<float*>(base + L.sb);
+        const int64_t warps = L.Mp * L.kbs;
+        int64_t g = (warps * 32 + 255) / 256;
+        if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
+        quant_rows_fp8_kernel<<<(unsigned)g, 256, 0, st>>>(A, M, K, L.Mp, L.Kp, qa, sa);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)(L.Np / 32), (unsigned)L.kbs);
+        if (grid.y > 65535u) return cudaErrorInvalidValue;
+        quant_cols_fp8_kernel<<<grid, 256, 0, st>>>(B, K, N, L.Np, L.Kp, qb, sb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches = 2;
+        if (!make_map(&prob->ta, qa, L.Kp, L.Mp, BM, true, why)) return cudaErrorInvalidValue;
+        if (!make_map(&prob->tb, qb, L.Kp, L.Np, 128, true, why)) return cudaErrorInvalidValue;
+        prob->ep = EpiArgs{C, C0, (int)M, (int)N, alpha, beta, vec, sa, sb, (int)L.kbs, (int)L.Np};
+        prob->Mp = (int)L.Mp;
+        prob->Np = (int)L.Np;
+        prob->num_kb = (int)L.kbs;
+        prob->chunk_kb = 1;
+    } else {
+        const int P = planes_of(prec);
+        const int64_t Mp = ru(M, BM), Np = ru(N, 256), Kp = ru(K, BK);
+        __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(scratch);
+        __nv_bfloat16* pb = pa + (size_t)P * Mp * Kp;
+        const int64_t work = Mp * (Kp / 8);
+        int64_t g = (work + 255) / 256;
+        if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
+        if (P == 3) split_rows_kernel<3><<<(unsigned)g, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
+        else if (P == 2) split_rows_kernel<2><<<(unsigned)g, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
+        else split_rows_kernel<1><<<(unsigned)g, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)(Np / 64), (unsigned)(Kp / 64));
+        if (grid.y > 65535u) return cudaErrorInvalidValue;
+        if (P == 3) split_cols_kernel<3><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+        else if (P == 2) split_cols_kernel<2><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+        else split_cols_kernel<1><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches = 2;
+        if (!make_map(&prob->ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;
+        if (!make_map(&prob->tb, pb, Kp, (int64_t)P * Np, 128, false, why)) return cudaErrorInvalidValue;
+        prob->ep = EpiArgs{C, C0, (int)M, (int)N, alpha, beta, vec, nullptr, nullptr, 0, 0};
+        prob->Mp = (int)Mp;
+        prob->Np = (int)Np;
+        prob->num_kb = (int)(Kp / BK);
+        prob->chunk_kb = kchunk > 0 ? std::max(1, (int)((kchunk + BK - 1) / BK)) : prob->num_kb;
+    }
+    prob->tiles_m = prob->Mp / BM;
+    prob->tiles_n = (int)((N + 127) / 128);
+    return cudaSuccess;
+}
+
+cudaError_t tc_launch_grouped(int prec, bool chunked, const TcProblem* d_probs, int nprob, int total_tiles, int* err,
+                              cudaStream_t st) {
+    // nprob == 0 / total_tiles == 0: only sets the kernel's shared-memory attribute
+    switch (prec) {
+        case GAO_GEMM_BF16X6:
+            return chunked ? launch_grouped_t<128, 3, 6, 2, true>(d_probs, nprob, total_tiles, err, st)
+                           : launch_grouped_t<128, 3, 6, 2, false>(d_probs, nprob, total_tiles, err, st);
+        case GAO_GEMM_BF16X3:
+            return chunked ? launch_grouped_t<128, 2, 3, 3, true>(d_probs, nprob, total_tiles, err, st)
+                           : launch_grouped_t<128, 2, 3, 3, false>(d_probs, nprob, total_tiles, err, st);
+        case GAO_GEMM_BF16:
+            return chunked ? launch_grouped_t<128, 1, 1, 6, true>(d_probs, nprob, total_tiles, err, st)
+                           : launch_grouped_t<128, 1, 1, 6, false>(d_probs, nprob, total_tiles, err, st);
+        case GAO_GEMM_FP8:
+            return launch_grouped_t<128, 1, 1, 6, true, true>(d_probs, nprob, total_tiles, err, st);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
 
 }  // namespace gao

@@ -1,0 +1,47 @@
+// Tensor-core GEMM interface shared by the runtime and the batch executor.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace gao {
+
+// Epilogue of one GEMM: C = alpha * acc + beta * C0 (FP8: acc scaled per K block).
+struct EpiArgs {
+    float* C;
+    const float* C0;
+    int M, N;
+    float alpha, beta;
+    int vec;           // C, C0 16-byte aligned and N % 4 == 0
+    const float* sa;   // FP8: scale of (row, K block), row-major [Mp][kbs]
+    const float* sb;   // FP8: scale of (K block, column), row-major [kbs][sb_ld]
+    int kbs, sb_ld;
+};
+
+// One problem of a grouped launch: its operand planes' TMA descriptors and epilogue.
+// tile_start is the index of its first CTA in the launch (prefix sum of tiles).
+struct alignas(128) TcProblem {
+    CUtensorMap ta, tb;
+    EpiArgs ep;
+    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, tile_start, pad;
+};
+
+// Looks up the driver's tensor-map encoder (once); false with a reason if unavailable.
+bool tc_available(std::string* why);
+
+// Split/quantise the operands of one GEMM into `scratch` (kernels on st) and describe it
+// in *prob for a grouped launch (tile_start left 0).  *launches counts kernels issued.
+cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
+                       int64_t K, float alpha, float beta, int kchunk, void* scratch, size_t scratch_bytes,
+                       cudaStream_t st, TcProblem* prob, int* launches, std::string* why);
+
+// One launch over nprob problems whose table (tile_start set, in order) is at d_probs
+// in device memory; every problem must come from tc_prepare with the same prec and
+// the same chunked-ness.  total_tiles = sum of tiles_m * tiles_n.  With total_tiles
+// = 0 it only prepares the kernel (shared-memory attribute), launching nothing.
+cudaError_t tc_launch_grouped(int prec, bool chunked, const TcProblem* d_probs, int nprob, int total_tiles, int* err,
+                              cudaStream_t st);
+
+}  // namespace gao

@@ -45,11 +45,14 @@ __global__ void init_kernel(float* __restrict__ out, int64_t rows, int64_t cols,
     const bool vec = (cols % 4 == 0) && aligned16(out);
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; i < n; i += stride) {
         if (vec) {
+            // i is a multiple of 4: two hashes give the four elements
+            const uint64_t h0 = sm64_hash(init_key(seed, buf, (uint64_t)i >> 1));
+            const uint64_t h1 = sm64_hash(init_key(seed, buf, ((uint64_t)i >> 1) + 1));
             float4 v;
-            v.x = init_value(seed, buf, (uint64_t)i);
-            v.y = init_value(seed, buf, (uint64_t)i + 1);
-            v.z = init_value(seed, buf, (uint64_t)i + 2);
-            v.w = init_value(seed, buf, (uint64_t)i + 3);
+            v.x = u24_to_value((uint32_t)(h0 >> 40));
+            v.y = u24_to_value((uint32_t)((h0 >> 16) & 0xFFFFFFu));
+            v.z = u24_to_value((uint32_t)(h1 >> 40));
+            v.w = u24_to_value((uint32_t)((h1 >> 16) & 0xFFFFFFu));
             if (rowexp) {
                 const int e = rowexp[i / cols];
                 v.x = ldexpf(v.x, e);
@@ -279,12 +282,21 @@ __global__ void __launch_bounds__(256) reduce64_kernel(double* __restrict__ out,
         last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {  // block-uniform: the whole last block adds the partials in a fixed order
         __threadfence();
         double t = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)partials)[b];
-        *out = SQUARES ? sqrt(t) : t;
-        *counter = 0u;  // ready for the next launch on this stream
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += ((volatile double*)partials)[b];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        __syncthreads();  // wsum is reused
+        if (lane == 0) wsum[warp] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double u = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += wsum[w];
+            *out = SQUARES ? sqrt(u) : u;
+            *counter = 0u;  // ready for the next launch on this stream
+        }
     }
 }
 

@@ -1,0 +1,73 @@
+// Program state shared by the runtime's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <unordered_map>
+#include <vector>
+
+#include "gao_internal.h"
+
+namespace gao {
+
+struct BufState {
+    gao_buffer d;
+    size_t bytes = 0;
+    char* dev = nullptr;
+    void* host = nullptr;  // pinned mirror
+    bool vh = false, vd = false;
+    bool input_set = false;
+};
+
+struct CacheEntry {
+    double seconds;
+    gao_status status;
+};
+
+struct Layout {
+    std::vector<size_t> buf_off;
+    size_t err_off = 0, partial_off = 0, counter_off = 0, keys_off = 0, rowexp_off = 0, tc_off = 0;
+    size_t tc_bytes = 0, keys_bytes = 0, rowexp_bytes = 0;
+    size_t total = 0;
+};
+
+}  // namespace gao
+
+struct gao_prog {
+    std::vector<gao_loop> loops;
+    std::vector<gao::BufState> bufs;
+    gao_opts opts{};
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    char* arena = nullptr;
+    bool own_arena = false;
+    gao::Layout lay;
+    int* h_err = nullptr;  // pinned
+    std::vector<gao_loop_stat> stats;
+    std::vector<cudaEvent_t> ev;   // 6 per loop: copy0, copy1, loop0, loop1, kern0, kern1
+    std::vector<uint8_t> ev_used;  // bit 0 copies, bit 1 loop, bit 2 kernel
+    std::unordered_map<uint64_t, gao::CacheEntry> cache;
+    bool dirty_stream = false;  // a previous run left work in flight
+};
+
+namespace gao {
+
+// One execution of a program (or of a batch of programs sharing a stream).
+struct RunCtx {
+    gao_prog* p;
+    double deadline;
+    bool timed_out;
+    CpuCtx cpu;
+    cudaStream_t st;    // stream the GPU work and copies go to
+    bool events;        // record per-loop CUDA events (not while capturing a graph)
+};
+
+gao_status make_valid(RunCtx& R, int b, bool on_gpu, gao_loop_stat& stat);
+std::vector<int> loop_inputs(const gao_loop& L);
+std::vector<int> loop_outputs(const gao_loop& L);
+gao_status run_gpu_loop(RunCtx& R, int li);
+gao_status run_cpu_loop(RunCtx& R, int li);
+gao_status stream_wait(cudaStream_t st, double deadline, bool* timed_out, double hard_cap_s = 300.0);
+gao_status check_device(int* dev_out);
+
+}  // namespace gao

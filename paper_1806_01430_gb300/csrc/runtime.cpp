@@ -22,6 +22,7 @@
 
 #include "ga_engine.h"
 #include "gao_internal.h"
+#include "prog_internal.h"
 
 namespace gao {
 
@@ -51,6 +52,7 @@ gao_status cuda_fail(cudaError_t e, const char* what) {
 namespace {
 std::mutex g_dev_mu;
 int g_sm_count = 0;
+}  // namespace
 
 gao_status check_device(int* dev_out) {
     int dev = 0;
@@ -69,7 +71,6 @@ gao_status check_device(int* dev_out) {
     if (dev_out) *dev_out = dev;
     return GAO_OK;
 }
-}  // namespace
 
 int sm_count() {
     std::lock_guard<std::mutex> g(g_dev_mu);
@@ -94,49 +95,9 @@ namespace {
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
-
-struct BufState {
-    gao_buffer d;
-    size_t bytes = 0;
-    char* dev = nullptr;
-    void* host = nullptr;  // pinned mirror
-    bool vh = false, vd = false;
-    bool input_set = false;
-};
-
-struct CacheEntry {
-    double seconds;
-    gao_status status;
-};
-
-struct Layout {
-    std::vector<size_t> buf_off;
-    size_t err_off = 0, partial_off = 0, counter_off = 0, keys_off = 0, rowexp_off = 0, tc_off = 0;
-    size_t tc_bytes = 0, keys_bytes = 0, rowexp_bytes = 0;
-    size_t total = 0;
-};
-
 size_t elem_size(int32_t dtype) { return dtype == GAO_F64 ? 8 : 4; }
 
 }  // namespace
-
-struct gao_prog {
-    std::vector<gao_loop> loops;
-    std::vector<BufState> bufs;
-    gao_opts opts{};
-    int device = 0;
-    cudaStream_t st = nullptr;
-    bool own_stream = false;
-    char* arena = nullptr;
-    bool own_arena = false;
-    Layout lay;
-    int* h_err = nullptr;  // pinned
-    std::vector<gao_loop_stat> stats;
-    std::vector<cudaEvent_t> ev;  // 6 per loop: copy0, copy1, loop0, loop1, kern0, kern1
-    std::vector<uint8_t> ev_used; // bit 0 copies, bit 1 loop, bit 2 kernel
-    std::unordered_map<uint64_t, CacheEntry> cache;
-    bool dirty_stream = false;  // a previous run left work in flight
-};
 
 namespace {
 
@@ -313,10 +274,12 @@ Layout plan(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bu
     return L;
 }
 
+}  // namespace
+
 // Wait for the stream; with a deadline, poll and report expiry.  Work already queued
 // always completes before returning (kernels bound their own waits), so the program
 // is reusable afterwards; hard_cap_s bounds the wait for a GPU that stopped answering.
-gao_status stream_wait(cudaStream_t st, double deadline, bool* timed_out, double hard_cap_s = 300.0) {
+gao_status gao::stream_wait(cudaStream_t st, double deadline, bool* timed_out, double hard_cap_s) {
     if (deadline <= 0.0) {
         cudaError_t e = cudaStreamSynchronize(st);
         return e == cudaSuccess ? GAO_OK : cuda_fail(e, "cudaStreamSynchronize");
@@ -332,6 +295,8 @@ gao_status stream_wait(cudaStream_t st, double deadline, bool* timed_out, double
         std::this_thread::yield();
     }
 }
+
+namespace {
 
 void free_prog(gao_prog* p) {
     if (!p) return;
@@ -442,14 +407,7 @@ extern "C" gao_status prog_set_input(gao_prog* p, int buf, const void* host_src,
     return GAO_OK;
 }
 
-namespace {
-
-struct RunCtx {
-    gao_prog* p;
-    double deadline;
-    bool timed_out;
-    CpuCtx cpu;
-};
+namespace gao {
 
 // Make buffer b valid on the requested side, issuing a copy on the stream if needed.
 gao_status make_valid(RunCtx& R, int b, bool on_gpu, gao_loop_stat& stat) {
@@ -457,13 +415,13 @@ gao_status make_valid(RunCtx& R, int b, bool on_gpu, gao_loop_stat& stat) {
     if (on_gpu) {
         if (B.vd) return GAO_OK;
         if (!B.vh) return fail(GAO_EINVAL, "buffer " + std::to_string(b) + " holds no data");
-        if (B.bytes) GAO_CUDA_TRY(cudaMemcpyAsync(B.dev, B.host, B.bytes, cudaMemcpyHostToDevice, R.p->st));
+        if (B.bytes) GAO_CUDA_TRY(cudaMemcpyAsync(B.dev, B.host, B.bytes, cudaMemcpyHostToDevice, R.st));
         stat.h2d_bytes += B.bytes;
         B.vd = true;
     } else {
         if (B.vh) return GAO_OK;
         if (!B.vd) return fail(GAO_EINVAL, "buffer " + std::to_string(b) + " holds no data");
-        if (B.bytes) GAO_CUDA_TRY(cudaMemcpyAsync(B.host, B.dev, B.bytes, cudaMemcpyDeviceToHost, R.p->st));
+        if (B.bytes) GAO_CUDA_TRY(cudaMemcpyAsync(B.host, B.dev, B.bytes, cudaMemcpyDeviceToHost, R.st));
         stat.d2h_bytes += B.bytes;
         B.vh = true;
     }
@@ -492,7 +450,7 @@ std::vector<int> loop_outputs(const gao_loop& L) {
 gao_status run_gpu_loop(RunCtx& R, int li) {
     gao_prog* p = R.p;
     const gao_loop& L = p->loops[(size_t)li];
-    cudaStream_t st = p->st;
+    cudaStream_t st = R.st;
     auto dptr = [&](int b) { return (float*)p->bufs[(size_t)b].dev; };
     auto shp = [&](int b) -> const gao_buffer& { return p->bufs[(size_t)b].d; };
     char* a = p->arena;
@@ -521,13 +479,14 @@ gao_status run_gpu_loop(RunCtx& R, int li) {
             const float* c0 = L.ins[2] >= 0 ? dptr(L.ins[2]) : nullptr;
             const float beta = c0 ? (float)L.beta : 0.0f;
             const int prec = p->opts.gemm_prec;
-            cudaEvent_t k0 = p->ev[(size_t)li * 6 + 4], k1 = p->ev[(size_t)li * 6 + 5];
+            cudaEvent_t k0 = R.events ? p->ev[(size_t)li * 6 + 4] : nullptr;
+            cudaEvent_t k1 = R.events ? p->ev[(size_t)li * 6 + 5] : nullptr;
             if (prec == GAO_GEMM_FP32_SIMT) {
-                GAO_CUDA_TRY(cudaEventRecord(k0, st));
+                if (k0) GAO_CUDA_TRY(cudaEventRecord(k0, st));
                 e = launch_gemm_simt(dptr(L.outs[0]), dptr(L.ins[0]), dptr(L.ins[1]), c0 ? c0 : dptr(L.outs[0]),
                                      A.rows, B.cols, A.cols, (float)L.alpha, beta, p->opts.kchunk, st);
                 nl += A.rows * B.cols > 0;
-                if (e == cudaSuccess) GAO_CUDA_TRY(cudaEventRecord(k1, st));
+                if (e == cudaSuccess && k1) GAO_CUDA_TRY(cudaEventRecord(k1, st));
             } else {
                 std::string why;
                 TcEvents tev{k0, k1, 0};
@@ -663,12 +622,14 @@ gao_status run_cpu_loop(RunCtx& R, int li) {
     return GAO_OK;
 }
 
+}  // namespace gao
+
+namespace {
 double ev_ms(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.0;
     return (double)ms;
 }
-
 }  // namespace
 
 extern "C" gao_status prog_run(gao_prog* p, uint64_t gene_mask, uint32_t flags, double* seconds_out) {
@@ -687,7 +648,7 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene_mask, uint32_t flags, 
     }
     cudaError_t ce = cudaSetDevice(p->device);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
-    RunCtx R{p, 0.0, false, CpuCtx{p->opts.cpu_threads, 0.0, false}};
+    RunCtx R{p, 0.0, false, CpuCtx{p->opts.cpu_threads, 0.0, false}, p->st, true};
     const double t0 = now_s();
     if (p->opts.timeout_s > 0.0) R.deadline = R.cpu.deadline = t0 + p->opts.timeout_s;
     for (auto& B : p->bufs) {

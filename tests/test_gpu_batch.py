@@ -1,0 +1,95 @@
+"""Batched gene evaluation over a suite of programs of uneven sizes (C ABI batch_*):
+every program's outputs after every gene match the FP64 oracle, the cache serves
+repeated genes, and the GA on top follows the oracle GA's trajectory on the measured
+times."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ga as oga
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 5e-3, 2: 2e-5, 3: 1e-6, 0: 1e-6, 4: 6e-2}  # by gemm_prec
+
+
+@pytest.fixture(scope="module")
+def gao():
+    from paper_1806_01430_gb300 import _build
+    _build.build()
+    import paper_1806_01430_gb300 as g
+    return g
+
+
+def suite(gao, sizes, prec, outputs=("C", "D", "E", "r", "f")):
+    progs = [W.six_loop(n, 3000 + i, outputs=outputs) for i, n in enumerate(sizes)]
+    handles = [gao.prog_from_workload(p, gemm_prec=prec) for p in progs]
+    return progs, handles
+
+
+def check_outputs(gao, progs, handles, refs, mask, prec):
+    tol = TOL[prec] if (mask >> 1) & 1 else 1e-6
+    for prog, h, ref in zip(progs, handles, refs):
+        for nm in ("C", "D", "E", "r"):
+            got = gao.prog_output(h, prog.index(nm))
+            err = oracle.rel_err(got, ref[nm])
+            assert err <= tol, (prog.name, mask, nm, err)
+        f = float(gao.prog_output(h, prog.index("f"))[0, 0])
+        assert abs(f - ref["f"]) <= tol * ref["f"]
+
+
+@pytest.mark.parametrize("prec", [3, 2])
+def test_batch_all_genes_match_oracle(gao, prec):
+    sizes = [130, 64, 257, 200, 96, 300]
+    progs, handles = suite(gao, sizes, prec)
+    refs = [oracle.run_program(p) for p in progs]
+    b = gao.batch_create(handles)
+    st0 = gao.batch_stats(b)
+    assert st0["graphs"] == 6 and st0["gemm_tiles"] == sum(((n + 127) // 128) ** 2 for n in sizes)
+    for mask in range(64):
+        fit, sec, hits = gao.batch_evaluate(b, [mask])
+        assert hits == 0 and sec[0] > 0 and fit[0] == pytest.approx(1 / np.sqrt(sec[0]))
+        check_outputs(gao, progs, handles, refs, mask, prec)
+    fit, sec, hits = gao.batch_evaluate(b, list(range(64)))
+    assert hits == 64
+    st = gao.batch_stats(b)
+    assert st["executed"] == 64 and st["served"] == 64 and st["gemm_phase_ms"] > 0
+    gao.batch_destroy(b)
+
+
+def test_batch_fp32_simt_and_fp8(gao):
+    for prec in (0, 4):
+        sizes = [70, 129, 256]
+        progs, handles = suite(gao, sizes, prec)
+        refs = [oracle.run_program(p) for p in progs]
+        b = gao.batch_create(handles)
+        for mask in (0b111111, 0b000010, 0b111101):
+            gao.batch_evaluate(b, [mask])
+            check_outputs(gao, progs, handles, refs, mask, prec)
+        gao.batch_destroy(b)
+
+
+def test_batch_ga_matches_oracle_on_measured_times(gao):
+    sizes = [128, 192, 384, 160]
+    progs, handles = suite(gao, sizes, 2, outputs=("f",))
+    b = gao.batch_create(handles)
+    _, secs, _ = gao.batch_evaluate(b, list(range(64)))
+    table = secs.copy()
+    res = gao.batch_ga_run(b, pop=20, generations=20, pc=0.9, pm=0.05, seed=7)
+    ref = oga.run(lambda m: float(table[m]), 6, 20, 20, 0.9, 0.05, 7)
+    assert res.populations == ref.populations
+    assert res.best_mask == ref.best_mask and res.best_s == ref.best_s
+    gao.batch_destroy(b)
+
+
+def test_batch_rejects_mixed_programs(gao):
+    a = gao.prog_from_workload(W.six_loop(64, 1), gemm_prec=3)
+    c = gao.prog_from_workload(W.six_loop(64, 2), gemm_prec=2)
+    with pytest.raises(gao.GaoError):
+        gao.batch_create([a, c])
+    d = gao.prog_from_workload(W.twelve_loop(32, 16, 3), gemm_prec=3)
+    with pytest.raises(gao.GaoError):
+        gao.batch_create([a, d])
+    with pytest.raises(gao.GaoError):
+        gao.batch_create([a, a])
