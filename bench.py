@@ -423,6 +423,7 @@ def batch_arm(args, world, rank, local):
     st_w = gao.batch_stats(b)
     gao.batch_destroy(b)
     b = gao.batch_create(handles)
+    tune = gao.batch_autotune(b, pop=8, generations=6, seed=3) if args.autotune else None
     torch.cuda.synchronize()
     barrier(world)
     with Clocks(local) as clk:
@@ -453,6 +454,7 @@ def batch_arm(args, world, rank, local):
                                  "effective_tflops": gemm_tf,
                                  "hw_frac": (gemm_tf * PRODUCTS[args.prec] / peak) if gemm_tf else None},
                 "launches_per_all_gpu_gene": st["launches_per_gene"], "graphs": st["graphs"],
+                "autotune": tune,
                 "all_gpu_gene_warm_s": st_w["exec_seconds"],
                 "history": [{"best_s": h["best_s"], "evaluated": h["evaluated"], "hits": h["cache_hits"]}
                             for h in res.history],
@@ -472,6 +474,7 @@ def main():
     ap.add_argument("--programs", type=int, default=64)
     ap.add_argument("--pop", type=int, default=20)
     ap.add_argument("--generations", type=int, default=20)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--prec", default="bf16x6", choices=list(PREC))

@@ -99,7 +99,9 @@ typedef enum gao_gemm_prec {
 typedef struct gao_opts {
     int32_t gemm_prec;       /* gao_gemm_prec                                               */
     int32_t kchunk;          /* K elements per binary32 partial sum (0: library default)    */
-    int32_t tile_cfg;        /* tensor-core tile configuration id (0: default)              */
+    int32_t tile_cfg;        /* tensor-core tile configuration: bits 0-1 tile width (0 default,
+                                1 = 128, 2 = 256 columns), bits 4-7 log2 of the raster group
+                                (0: default 16); prog_autotune picks one               */
     int32_t cpu_threads;     /* OpenMP threads for CPU loops (0: all)                       */
     uint64_t seed;           /* seed of the INIT loop's counter hash                        */
     double timeout_s;        /* wall-clock budget of one prog_run (0: none)                 */
@@ -107,7 +109,17 @@ typedef struct gao_opts {
     void *dev_arena;         /* caller-owned device memory for every buffer and all scratch
                                 (NULL: the library allocates it); must outlive the program */
     uint64_t dev_arena_bytes;
+    int32_t transfer_mode;   /* GAO_TRANSFER_RESIDENT or GAO_TRANSFER_PER_LOOP               */
+    int32_t _reserved;
 } gao_opts;
+
+/* Data movement between host and device under a gene (Sec. 2 and Sec. 3.3: CPU-GPU
+ * transfers are why naive offloading loses):
+ *   RESIDENT  a buffer moves only when a loop needs it on the side where it is not valid;
+ *   PER_LOOP  every GPU loop copies its inputs in and its outputs back out, as a directive
+ *             offload without a data region does (the paper's measured setting). */
+#define GAO_TRANSFER_RESIDENT 0
+#define GAO_TRANSFER_PER_LOOP 1
 
 typedef struct gao_prog gao_prog;
 
@@ -203,6 +215,28 @@ gao_status ga_run(gao_prog *const *progs, int n_progs, const gao_ga_params *para
  * non-finite time marks a failed gene (fitness 0).  Host only, no GPU. */
 gao_status ga_run_table(const double *times, int n_genes, const gao_ga_params *params, gao_ga_result *result);
 
+/* ---- tile autotuning with the GA ----------------------------------------------- */
+
+/* The Simple GA reused as the tensor-core GEMM's autotuner: a 4-bit gene encodes
+ * bits 0-1  raster group of 4, 8, 16 or 32 row tiles per CTA group (L2 reuse order),
+ * bits 2-3  split precisions: K chunk of 64, 128, 256 or 512 elements (all within the
+ *           stated error bound); plain BF16: tile width 128 or 256 columns,
+ * and fitness is (measured GEMM time)^(-1/2), the paper's fitness with the kernel time
+ * as the benchmark.  The best configuration is written into the program's (or the
+ * batch's) options and used from then on. */
+typedef struct gao_autotune_result {
+    int32_t kchunk;     /* best K chunk (0: unchunked)                         */
+    int32_t tile_cfg;   /* best tile configuration id (see gao_opts.tile_cfg)  */
+    double best_ms;     /* GEMM time of the best configuration                 */
+    double default_ms;  /* GEMM time of the configuration in place beforehand  */
+    int32_t evaluations;/* configurations measured                             */
+    int32_t _pad;
+} gao_autotune_result;
+
+/* Tunes the program's GEMM loop (tensor-core precisions); runs the program once under
+ * the all-GPU gene first so that the GEMM's inputs are on the device. */
+gao_status prog_autotune(gao_prog *p, const gao_ga_params *params, gao_autotune_result *out);
+
 /* ---- batched evaluation over a program suite ---------------------------------- */
 
 /* A batch scores genes over a suite of programs that share one loop structure (same
@@ -236,6 +270,9 @@ gao_status batch_evaluate(gao_batch *b, const uint64_t *population, int pop, dou
 /* The Simple GA with batched evaluation (same draws as ga_run). */
 gao_status batch_ga_run(gao_batch *b, const gao_ga_params *params, gao_ga_result *result);
 gao_status batch_stats(gao_batch *b, gao_batch_stat *out);
+/* Tunes the batch's grouped GEMM launch (same gene as prog_autotune; the time is the
+ * GEMM phase of the whole suite). */
+gao_status batch_autotune(gao_batch *b, const gao_ga_params *params, gao_autotune_result *out);
 void batch_destroy(gao_batch *b);
 
 /* ---- misc ------------------------------------------------------------------ */

@@ -30,6 +30,7 @@ TEMP, INPUT, OUTPUT = 0, 1, 2
 FP32_SIMT, BF16, BF16X3, BF16X6, FP8 = range(5)
 PREC_NAMES = ["fp32_simt", "bf16", "bf16x3", "bf16x6", "fp8"]
 RUN_KEEP_DEVICE = 1
+TRANSFER_RESIDENT, TRANSFER_PER_LOOP = 0, 1
 MAX_IO = 4
 
 
@@ -46,7 +47,8 @@ class gao_loop(ctypes.Structure):
 class gao_opts(ctypes.Structure):
     _fields_ = [("gemm_prec", ctypes.c_int32), ("kchunk", ctypes.c_int32), ("tile_cfg", ctypes.c_int32),
                 ("cpu_threads", ctypes.c_int32), ("seed", ctypes.c_uint64), ("timeout_s", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("dev_arena", ctypes.c_void_p), ("dev_arena_bytes", ctypes.c_uint64)]
+                ("stream", ctypes.c_void_p), ("dev_arena", ctypes.c_void_p), ("dev_arena_bytes", ctypes.c_uint64),
+                ("transfer_mode", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
 
 
 class gao_loop_stat(ctypes.Structure):
@@ -70,6 +72,11 @@ class gao_ga_result(ctypes.Structure):
     _fields_ = [("best_mask", ctypes.c_uint64), ("best_s", ctypes.c_double), ("evaluations", ctypes.c_int32),
                 ("cache_hits", ctypes.c_int32), ("history", ctypes.POINTER(gao_ga_gen)),
                 ("populations", ctypes.POINTER(ctypes.c_uint64))]
+
+
+class gao_autotune_result(ctypes.Structure):
+    _fields_ = [("kchunk", ctypes.c_int32), ("tile_cfg", ctypes.c_int32), ("best_ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double), ("evaluations", ctypes.c_int32), ("_pad", ctypes.c_int32)]
 
 
 class gao_batch_stat(ctypes.Structure):
@@ -110,6 +117,8 @@ SIGNATURES = {
     "batch_ga_run": (ctypes.c_int, [_P, ctypes.POINTER(gao_ga_params), ctypes.POINTER(gao_ga_result)]),
     "batch_stats": (ctypes.c_int, [_P, ctypes.POINTER(gao_batch_stat)]),
     "batch_destroy": (None, [_P]),
+    "prog_autotune": (ctypes.c_int, [_P, ctypes.POINTER(gao_ga_params), ctypes.POINTER(gao_autotune_result)]),
+    "batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(gao_ga_params), ctypes.POINTER(gao_autotune_result)]),
 }
 
 _lib = None
@@ -176,8 +185,10 @@ def _marshal(buffers, loops):
     return cb, nb, cl, nl
 
 
-def _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, arena_ptr, arena_bytes):
+def _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, arena_ptr, arena_bytes,
+          transfer_mode=TRANSFER_RESIDENT):
     o = gao_opts()
+    o.transfer_mode = int(transfer_mode)
     o.gemm_prec, o.kchunk, o.tile_cfg, o.cpu_threads = int(gemm_prec), int(kchunk), int(tile_cfg), int(cpu_threads)
     o.seed, o.timeout_s = int(seed), float(timeout_s)
     o.stream = _stream_handle(stream)
@@ -215,7 +226,8 @@ def prog_device_bytes(buffers, loops, seed=0, gemm_prec=FP32_SIMT, kchunk=0, til
 
 
 def prog_create(buffers, loops, seed: int = 0, gemm_prec: int = FP32_SIMT, kchunk: int = 0, tile_cfg: int = 0,
-                cpu_threads: int = 0, timeout_s: float = 0.0, stream=None, arena=None) -> Prog:
+                cpu_threads: int = 0, timeout_s: float = 0.0, stream=None, arena=None,
+                transfer_mode: int = TRANSFER_RESIDENT) -> Prog:
     """Declare a program.  ``buffers``/``loops`` are sequences of objects with the
     gao_buffer / gao_loop fields (e.g. workloads.Buffer / workloads.Loop).  ``arena``:
     optional device memory (a torch uint8 CUDA tensor, or (ptr, bytes))."""
@@ -226,7 +238,7 @@ def prog_create(buffers, loops, seed: int = 0, gemm_prec: int = FP32_SIMT, kchun
             ptr, nbytes = int(arena[0]), int(arena[1])
         else:
             ptr, nbytes, keep = int(arena.data_ptr()), int(arena.numel() * arena.element_size()), arena
-    o = _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, ptr, nbytes)
+    o = _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, ptr, nbytes, transfer_mode)
     h = ctypes.c_void_p(None)
     _check(lib().prog_create(cl, nl, cb, nb, ctypes.byref(o), ctypes.byref(h)), "prog_create")
     return Prog(h, buffers, loops, keep)
@@ -422,3 +434,22 @@ def batch_destroy(b: Batch) -> None:
     if b.handle is not None and b.handle.value:
         lib().batch_destroy(b.handle)
         b.handle = ctypes.c_void_p(None)
+
+
+def _autotune_out(r) -> Dict:
+    return {k: getattr(r, k) for k, _ in gao_autotune_result._fields_ if k != "_pad"}
+
+
+def prog_autotune(p: Prog, pop=8, generations=6, pc=0.9, pm=0.05, seed=0) -> Dict:
+    """GA over the GEMM's tile configuration (4-bit gene); applies and returns the best."""
+    params = _params(pop, generations, pc, pm, seed)
+    r = gao_autotune_result()
+    _check(lib().prog_autotune(p.handle, ctypes.byref(params), ctypes.byref(r)), "prog_autotune")
+    return _autotune_out(r)
+
+
+def batch_autotune(b: Batch, pop=8, generations=6, pc=0.9, pm=0.05, seed=0) -> Dict:
+    params = _params(pop, generations, pc, pm, seed)
+    r = gao_autotune_result()
+    _check(lib().batch_autotune(b.handle, ctypes.byref(params), ctypes.byref(r)), "batch_autotune")
+    return _autotune_out(r)

@@ -44,6 +44,7 @@ struct gao_batch {
     TcProblem* d_probs = nullptr;
     int n_probs = 0, total_tiles = 0;
     std::vector<size_t> gemm_order;  // programs in problem-table order (largest GEMM first)
+    std::vector<TcProblem> h_probs;  // host copy of the problem table
     double gemm_flops = 0.0;
     int* d_err = nullptr;
     int* h_err = nullptr;
@@ -102,8 +103,8 @@ gao_status capture_phase(gao_batch* b, int li, std::vector<TcProblem>* probs) {
             int nl = 0;
             e = tc_prepare(b->prec, (float*)p->bufs[(size_t)L.outs[0]].dev, (const float*)p->bufs[(size_t)L.ins[0]].dev,
                            (const float*)p->bufs[(size_t)L.ins[1]].dev, c0, A.rows, B.cols, A.cols, (float)L.alpha,
-                           L.ins[2] >= 0 ? (float)L.beta : 0.0f, p->opts.kchunk, p->arena + p->lay.tc_off,
-                           p->lay.tc_bytes, s, &(*probs)[j], &nl, &why);
+                           L.ins[2] >= 0 ? (float)L.beta : 0.0f, p->opts.kchunk, p->opts.tile_cfg,
+                           p->arena + p->lay.tc_off, p->lay.tc_bytes, s, &(*probs)[j], &nl, &why);
             if (e != cudaSuccess && !why.empty()) status = fail(GAO_EINVAL, "batch GEMM: " + why);
             b->stat.launches_per_gene += nl;
         } else {
@@ -247,6 +248,8 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
         for (size_t l = 0; l < p->loops.size(); ++l)
             if (p->loops[l].kind != p0->loops[l].kind) return fail(GAO_EINVAL, "batch programs differ in loop kinds");
         if (p->opts.gemm_prec != p0->opts.gemm_prec) return fail(GAO_EINVAL, "batch programs differ in GEMM precision");
+        if (p->opts.transfer_mode != GAO_TRANSFER_RESIDENT)
+            return fail(GAO_EINVAL, "batches keep buffers resident (transfer_mode RESIDENT only)");
         for (auto& B : p->bufs)
             if (B.d.role == GAO_BUF_INPUT && !B.input_set) return fail(GAO_EINVAL, "INPUT buffers must be set first");
         for (int j = 0; j < i; ++j)
@@ -348,6 +351,7 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
             if ((e = cudaMemcpy(b->d_probs, probs.data(), sizeof(TcProblem) * probs.size(),
                                 cudaMemcpyHostToDevice)) != cudaSuccess)
                 return bail(cuda_fail(e, "problem table upload"));
+            b->h_probs = probs;
         }
     }
     b->stat.graphs = b->n_loops;
@@ -400,6 +404,75 @@ extern "C" gao_status batch_stats(gao_batch* b, gao_batch_stat* out) {
     *out = b->stat;
     out->gemm_flops = b->gemm_flops;
     out->gemm_tiles = b->total_tiles;
+    return GAO_OK;
+}
+
+extern "C" gao_status batch_autotune(gao_batch* b, const gao_ga_params* params, gao_autotune_result* out) {
+    if (!b || !params || !out) return fail(GAO_EINVAL, "null argument");
+    if (!b->grouped_gemm) return fail(GAO_EINVAL, "batch has no tensor-core GEMM loop");
+    const uint64_t all = b->n_loops >= 64 ? ~0ULL : ((1ULL << b->n_loops) - 1);
+    double s0 = 0.0;
+    gao_status st = run_gene(b, all, &s0);  // the GEMM's inputs on the device
+    if (st != GAO_OK) return st;
+    bool chunked_variant = false;
+    for (auto* p : b->progs) chunked_variant |= p->opts.kchunk > 0;
+    std::vector<TcProblem> table = b->h_probs;
+    auto apply = [&](int kchunk, int tile_cfg) -> gao_status {
+        for (auto& pr : table) {
+            pr.group = tc_group_of(tile_cfg);
+            if (chunked_variant && kchunk > 0) pr.chunk_kb = std::max(1, std::min(pr.num_kb, kchunk / 64));
+        }
+        GAO_CUDA_TRY(cudaMemcpyAsync(b->d_probs, table.data(), sizeof(TcProblem) * table.size(),
+                                     cudaMemcpyHostToDevice, b->st));
+        return GAO_OK;
+    };
+    auto time_cfg = [&](int kchunk, int tile_cfg, double* ms) -> gao_status {
+        gao_status s = apply(kchunk, tile_cfg);
+        if (s != GAO_OK) return s;
+        std::vector<double> v;
+        for (int r = 0; r < 4; ++r) {
+            GAO_CUDA_TRY(cudaEventRecord(b->g0, b->st));
+            GAO_CUDA_TRY(cudaGraphLaunch(b->exec[(size_t)b->gemm_loop], b->st));
+            GAO_CUDA_TRY(cudaEventRecord(b->g1, b->st));
+            GAO_CUDA_TRY(cudaEventSynchronize(b->g1));
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, b->g0, b->g1);
+            if (r > 0) v.push_back(t);
+        }
+        std::sort(v.begin(), v.end());
+        *ms = v[v.size() / 2];
+        return GAO_OK;
+    };
+    int kc0 = b->progs[0]->opts.kchunk, tc0 = b->progs[0]->opts.tile_cfg;
+    double def_ms = 0.0;
+    if ((st = time_cfg(kc0, tc0, &def_ms)) != GAO_OK) return st;
+    int evals = 0;
+    TimeFn fn = [&](uint64_t g, double* t) {
+        int kc = 0, tc = 0;
+        autotune_decode(b->prec, g, &kc, &tc);
+        double ms = 0.0;
+        gao_status s2 = time_cfg(kc, tc, &ms);
+        *t = ms * 1e-3;
+        ++evals;
+        return s2;
+    };
+    gao_ga_result res{};
+    if ((st = ga_core(4, *params, fn, &res)) != GAO_OK) return st;
+    int kc = 0, tc = 0;
+    autotune_decode(b->prec, res.best_mask, &kc, &tc);
+    if ((st = apply(kc, tc)) != GAO_OK) return st;
+    b->h_probs = table;
+    for (auto* p : b->progs) {
+        if (chunked_variant) p->opts.kchunk = kc;
+        p->opts.tile_cfg = tc;
+    }
+    b->cache.clear();  // genes measured under the old configuration
+    GAO_CUDA_TRY(cudaStreamSynchronize(b->st));
+    out->kchunk = chunked_variant ? kc : 0;
+    out->tile_cfg = tc;
+    out->best_ms = res.best_s * 1e3;
+    out->default_ms = def_ms;
+    out->evaluations = evals;
     return GAO_OK;
 }
 

@@ -15,4 +15,24 @@ double ga_fitness(double seconds);
 
 gao_status ga_core(int n_genes, const gao_ga_params& p, const TimeFn& time_of, gao_ga_result* res);
 
+// Tile configuration of a 4-bit autotuning gene for GEMM precision `prec`:
+// bits 0-1 raster group 4/8/16/32 (log2 2..5, stored in tile_cfg bits 4-7); bits 2-3
+// K chunk 64 << v for split precisions, tile width 128/256 for plain bfloat16.
+inline void autotune_decode(int prec, uint64_t gene, int* kchunk, int* tile_cfg) {
+    const int glog = 2 + (int)(gene & 3);
+    const int v = (int)((gene >> 2) & 3);
+    int bn_sel = 0;
+    if (prec == GAO_GEMM_BF16X3 || prec == GAO_GEMM_BF16X6) {
+        *kchunk = 64 << v;
+        bn_sel = 1;
+    } else if (prec == GAO_GEMM_BF16) {
+        *kchunk = 0;
+        bn_sel = (v & 1) ? 2 : 1;
+    } else {
+        *kchunk = 0;
+        bn_sel = 1;
+    }
+    *tile_cfg = bn_sel | (glog << 4);
+}
+
 }  // namespace gao

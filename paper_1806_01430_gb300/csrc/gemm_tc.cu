@@ -494,11 +494,11 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmA, const CUten
     }
 }
 
-// Row tile tm and column tile tn of CTA `bid` in a tiles_m x tiles_n grid: groups of 16
-// row tiles, row tile fastest inside a group, so the CTAs of one wave share A row
-// panels and B column panels in L2.
-__device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int& tm, int& tn) {
-    constexpr int GROUP = 16;
+// Row tile tm and column tile tn of CTA `bid` in a tiles_m x tiles_n grid: groups of
+// `group` row tiles (16 by default), row tile fastest inside a group, so the CTAs of
+// one wave share A row panels and B column panels in L2.
+__device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int group, int& tm, int& tn) {
+    const int GROUP = group > 0 ? group : 16;
     const int group_tiles = GROUP * tiles_n;
     const int first_m = (bid / group_tiles) * GROUP;
     const int gm = min(tiles_m - first_m, GROUP);
@@ -509,9 +509,9 @@ __device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int& t
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep,
-                   int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int* err) {
+                   int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int group, int* err) {
     int tm, tn;
-    raster((int)blockIdx.x, tiles_m, tiles_n, tm, tn);
+    raster((int)blockIdx.x, tiles_m, tiles_n, group, tm, tn);
     gemm_tc_tile<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tm, tn, err);
 }
 
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const TcProblem* P = probs + lo;
     const EpiArgs ep = P->ep;
     int tm, tn;
-    raster(b - P->tile_start, P->tiles_m, P->tiles_n, tm, tn);
+    raster(b - P->tile_start, P->tiles_m, P->tiles_n, P->group, tm, tn);
     gemm_tc_tile<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(&P->ta, &P->tb, ep, P->Mp, P->Np, P->num_kb, P->chunk_kb,
                                                           tm, tn, err);
 }
@@ -731,7 +731,7 @@ bool make_map(CUtensorMap* map, void* base, int64_t inner, int64_t rows, int box
 
 template <int BN, int P, int NPROD, int STAGES, bool CHUNKED, bool FP8 = false>
 cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const EpiArgs& ep, int Mp, int Np, int num_kb,
-                       int chunk_kb, int* err, cudaStream_t st) {
+                       int chunk_kb, int group, int* err, cudaStream_t st) {
     // Np is the plane stride (a multiple of 256); only ceil(N / BN) column tiles hold data
     using Cfg = TcCfg<BN, P, P, NPROD, STAGES, CHUNKED, FP8>;
     auto kern = gemm_tc_kernel<BN, P, P, NPROD, STAGES, CHUNKED, FP8>;
@@ -744,14 +744,15 @@ cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const EpiAr
     const int tiles_m = Mp / BM, tiles_n = (ep.N + BN - 1) / BN;
     const int64_t grid = (int64_t)tiles_m * tiles_n;
     if (grid > 0x7fffffff) return cudaErrorInvalidValue;
-    kern<<<(unsigned)grid, kThreadsTc, Cfg::SMEM, st>>>(ta, tb, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, err);
+    kern<<<(unsigned)grid, kThreadsTc, Cfg::SMEM, st>>>(ta, tb, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group,
+                                                        err);
     return cudaGetLastError();
 }
 
 
 cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K,
-                            float alpha, float beta, void* scratch, size_t scratch_bytes, int* err, cudaStream_t st,
-                            TcEvents& ev, std::string* why);
+                            float alpha, float beta, int group, void* scratch, size_t scratch_bytes, int* err,
+                            cudaStream_t st, TcEvents& ev, std::string* why);
 
 }  // namespace
 
@@ -804,7 +805,9 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         return cudaErrorInvalidValue;
     }
     if (!get_encode(why)) return cudaErrorNotSupported;
-    if (prec == GAO_GEMM_FP8) return launch_gemm_fp8(C, A, B, C0, M, N, K, alpha, beta, scratch, scratch_bytes, err, st, ev, why);
+    if (prec == GAO_GEMM_FP8)
+        return launch_gemm_fp8(C, A, B, C0, M, N, K, alpha, beta, tc_group_of(tile_cfg), scratch, scratch_bytes, err,
+                               st, ev, why);
     const int P = planes_of(prec);
     const int64_t Mp = ru(M, BM), Np = ru(N, 256), Kp = ru(K, BK);
     if (tc_scratch_bytes(prec, M, N, K) > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
@@ -836,10 +839,13 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     int chunk_kb = num_kb;
     if (kchunk > 0) chunk_kb = std::max(1, (int)((kchunk + BK - 1) / BK));
     const bool chunked = chunk_kb < num_kb;
-    // tile_cfg: 0 = default (128 x 256 for the unchunked single product, else 128 x 128),
-    // 1 = 128 x 128, 2 = 128 x 256 (single product, unchunked only)
+    // tile_cfg bits 0-1: 0 = default (128 x 256 for the unchunked single product, else
+    // 128 x 128), 1 = 128 x 128, 2 = 128 x 256 (single product, unchunked only);
+    // bits 4-7: raster group = 2^value row tiles (0: default 16)
+    const int bn_sel = tile_cfg & 3;
+    const int group = tc_group_of(tile_cfg);
     int bn = 128;
-    if (!chunked && P == 1 && (tile_cfg == 2 || tile_cfg == 0)) bn = 256;
+    if (!chunked && P == 1 && (bn_sel == 2 || bn_sel == 0)) bn = 256;
     CUtensorMap ta, tb;
     if (!make_map(&ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;
     if (!make_map(&tb, pb, Kp, (int64_t)P * Np, bn, false, why)) return cudaErrorInvalidValue;
@@ -849,17 +855,17 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     cudaError_t e;
     const int mp = (int)Mp, np = (int)Np;
     if (P == 3)
-        e = chunked ? launch_mma<128, 3, 6, 2, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, err, st)
-                    : launch_mma<128, 3, 6, 2, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, err, st);
+        e = chunked ? launch_mma<128, 3, 6, 2, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st)
+                    : launch_mma<128, 3, 6, 2, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
     else if (P == 2)
-        e = chunked ? launch_mma<128, 2, 3, 3, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, err, st)
-                    : launch_mma<128, 2, 3, 3, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, err, st);
+        e = chunked ? launch_mma<128, 2, 3, 3, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st)
+                    : launch_mma<128, 2, 3, 3, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
     else if (chunked)
-        e = launch_mma<128, 1, 1, 6, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, err, st);
+        e = launch_mma<128, 1, 1, 6, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
     else if (bn == 256)
-        e = launch_mma<256, 1, 1, 4, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, err, st);
+        e = launch_mma<256, 1, 1, 4, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
     else
-        e = launch_mma<128, 1, 1, 6, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, err, st);
+        e = launch_mma<128, 1, 1, 6, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
     if (e != cudaSuccess) return e;
     ev.launches += 1;
     if (ev.k1) cudaEventRecord(ev.k1, st);
@@ -869,8 +875,8 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
 
 namespace {
 cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K,
-                            float alpha, float beta, void* scratch, size_t scratch_bytes, int* err, cudaStream_t st,
-                            TcEvents& ev, std::string* why) {
+                            float alpha, float beta, int group, void* scratch, size_t scratch_bytes, int* err,
+                            cudaStream_t st, TcEvents& ev, std::string* why) {
     const Fp8Layout L = fp8_layout(M, N, K);
     if (L.total > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
         if (why) *why = "FP8 scratch too small or misaligned";
@@ -900,7 +906,7 @@ cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const floa
                (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, sa, sb, (int)L.kbs,
                (int)L.Np};
     if (ev.k0) cudaEventRecord(ev.k0, st);
-    cudaError_t e = launch_mma<128, 1, 1, 6, true, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, (int)L.kbs, 1, err, st);
+    cudaError_t e = launch_mma<128, 1, 1, 6, true, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, (int)L.kbs, 1, group, err, st);
     if (e != cudaSuccess) return e;
     ev.launches += 1;
     if (ev.k1) cudaEventRecord(ev.k1, st);
@@ -933,8 +939,8 @@ cudaError_t launch_grouped_t(const TcProblem* d_probs, int nprob, int total_tile
 bool tc_available(std::string* why) { return get_encode(why); }
 
 cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
-                       int64_t K, float alpha, float beta, int kchunk, void* scratch, size_t scratch_bytes,
-                       cudaStream_t st, TcProblem* prob, int* launches, std::string* why) {
+                       int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
+                       size_t scratch_bytes, cudaStream_t st, TcProblem* prob, int* launches, std::string* why) {
     *launches = 0;
     memset(prob, 0, sizeof(*prob));
     if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_FP8 || M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) ||
@@ -1001,6 +1007,7 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
     }
     prob->tiles_m = prob->Mp / BM;
     prob->tiles_n = (int)((N + 127) / 128);
+    prob->group = tc_group_of(tile_cfg);
     return cudaSuccess;
 }
 

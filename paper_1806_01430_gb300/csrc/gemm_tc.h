@@ -25,8 +25,15 @@ struct EpiArgs {
 struct alignas(128) TcProblem {
     CUtensorMap ta, tb;
     EpiArgs ep;
-    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, tile_start, pad;
+    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, tile_start, group;
 };
+
+// Raster group (row tiles per CTA group) encoded in bits 4-7 of a tile configuration
+// id as a power of two; 0 selects the default of 16.
+inline int tc_group_of(int tile_cfg) {
+    const int g = (tile_cfg >> 4) & 15;
+    return g == 0 ? 16 : (1 << g);
+}
 
 // Looks up the driver's tensor-map encoder (once); false with a reason if unavailable.
 bool tc_available(std::string* why);
@@ -34,8 +41,8 @@ bool tc_available(std::string* why);
 // Split/quantise the operands of one GEMM into `scratch` (kernels on st) and describe it
 // in *prob for a grouped launch (tile_start left 0).  *launches counts kernels issued.
 cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
-                       int64_t K, float alpha, float beta, int kchunk, void* scratch, size_t scratch_bytes,
-                       cudaStream_t st, TcProblem* prob, int* launches, std::string* why);
+                       int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
+                       size_t scratch_bytes, cudaStream_t st, TcProblem* prob, int* launches, std::string* why);
 
 // One launch over nprob problems whose table (tile_start set, in order) is at d_probs
 // in device memory; every problem must come from tc_prepare with the same prec and

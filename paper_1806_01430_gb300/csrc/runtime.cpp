@@ -119,6 +119,8 @@ gao_status validate(const gao_loop* loops, int n_loops, const gao_buffer* bufs, 
     if (n_bufs < 1 || n_bufs > 4096) return fail(GAO_EINVAL, "buffer count must be in [1, 4096]");
     if (opts && (opts->gemm_prec < GAO_GEMM_FP32_SIMT || opts->gemm_prec > GAO_GEMM_FP8))
         return fail(GAO_EINVAL, "unknown gemm_prec");
+    if (opts && opts->transfer_mode != GAO_TRANSFER_RESIDENT && opts->transfer_mode != GAO_TRANSFER_PER_LOOP)
+        return fail(GAO_EINVAL, "unknown transfer_mode");
     for (int b = 0; b < n_bufs; ++b) {
         const gao_buffer& d = bufs[b];
         if (d.rows < 0 || d.cols < 0) return fail(GAO_EINVAL, "buffer " + std::to_string(b) + ": negative shape");
@@ -668,6 +670,9 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene_mask, uint32_t flags, 
         S.placement = gpu ? 1 : 0;
         cudaEvent_t* ev = &p->ev[(size_t)li * 6];
         const std::vector<int> ins = loop_inputs(L);
+        const bool per_loop = p->opts.transfer_mode == GAO_TRANSFER_PER_LOOP;
+        if (gpu && per_loop)  // directive offload without a data region: inputs always copied in
+            for (int b : ins) p->bufs[(size_t)b].vd = false;
         if (gpu) {
             bool copies = false;
             for (int b : ins) copies |= !p->bufs[(size_t)b].vd;
@@ -702,6 +707,12 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene_mask, uint32_t flags, 
         for (int b : loop_outputs(L)) {
             p->bufs[(size_t)b].vh = !gpu;
             p->bufs[(size_t)b].vd = gpu;
+        }
+        if (gpu && per_loop) {  // ... and outputs always copied back out; the device copy is dropped
+            for (int b : loop_outputs(L))
+                if ((status = make_valid(R, b, false, S)) != GAO_OK) break;
+            if (status != GAO_OK) break;
+            for (int b : loop_outputs(L)) p->bufs[(size_t)b].vd = false;
         }
         if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
         if (R.timed_out) break;
@@ -876,6 +887,89 @@ extern "C" gao_status ga_run_table(const double* times, int n_genes, const gao_g
         return GAO_OK;
     };
     return ga_core(n_genes, *params, fn, result);
+}
+
+// ---- C ABI: autotuning -------------------------------------------------------------------------
+
+extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, gao_autotune_result* out) {
+    if (!p || !params || !out) return fail(GAO_EINVAL, "null argument");
+    const int prec = p->opts.gemm_prec;
+    if (prec == GAO_GEMM_FP32_SIMT) return fail(GAO_EINVAL, "autotuning covers the tensor-core GEMM only");
+    int li = -1;
+    for (size_t i = 0; i < p->loops.size(); ++i)
+        if (p->loops[i].kind == GAO_LOOP_GEMM) {
+            li = (int)i;
+            break;
+        }
+    if (li < 0) return fail(GAO_EINVAL, "program has no GEMM loop");
+    const int n = (int)p->loops.size();
+    const uint64_t all = n >= 64 ? ~0ULL : ((1ULL << n) - 1);
+    double s0 = 0.0;
+    gao_status st = prog_run(p, all, GAO_RUN_KEEP_DEVICE, &s0);  // puts the GEMM's inputs on the device
+    if (st != GAO_OK) return st;
+    const gao_loop& L = p->loops[(size_t)li];
+    const gao_buffer &A = p->bufs[(size_t)L.ins[0]].d, &B = p->bufs[(size_t)L.ins[1]].d;
+    float* C = (float*)p->bufs[(size_t)L.outs[0]].dev;
+    const float* C0 = L.ins[2] >= 0 ? (const float*)p->bufs[(size_t)L.ins[2]].dev : C;
+    const float beta = L.ins[2] >= 0 ? (float)L.beta : 0.0f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GAO_CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate");
+    }
+    int* d_err = (int*)(p->arena + p->lay.err_off);
+    auto time_cfg = [&](int kchunk, int tile_cfg, double* ms) -> gao_status {
+        std::vector<double> v;
+        for (int r = 0; r < 6; ++r) {
+            TcEvents ev{e0, e1, 0};
+            std::string why;
+            cudaError_t e = launch_gemm_tc(prec, C, (const float*)p->bufs[(size_t)L.ins[0]].dev,
+                                           (const float*)p->bufs[(size_t)L.ins[1]].dev, C0, A.rows, B.cols, A.cols,
+                                           (float)L.alpha, beta, kchunk, tile_cfg, p->arena + p->lay.tc_off,
+                                           p->lay.tc_bytes, d_err, p->st, ev, &why);
+            if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "autotune launch") : fail(GAO_EINVAL, why);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return cuda_fail(e, "autotune sync");
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (r > 0) v.push_back(t);  // first launch warms up
+        }
+        std::sort(v.begin(), v.end());
+        *ms = v[v.size() / 2];
+        return GAO_OK;
+    };
+    double def_ms = 0.0;
+    st = time_cfg(p->opts.kchunk, p->opts.tile_cfg, &def_ms);
+    int evals = 0;
+    if (st == GAO_OK) {
+        TimeFn fn = [&](uint64_t g, double* t) {
+            int kc = 0, tc = 0;
+            autotune_decode(prec, g, &kc, &tc);
+            double ms = 0.0;
+            gao_status s2 = time_cfg(kc, tc, &ms);
+            *t = ms * 1e-3;
+            ++evals;
+            return s2;
+        };
+        gao_ga_result res{};
+        st = ga_core(4, *params, fn, &res);
+        if (st == GAO_OK) {
+            int kc = 0, tc = 0;
+            autotune_decode(prec, res.best_mask, &kc, &tc);
+            p->opts.kchunk = kc;
+            p->opts.tile_cfg = tc;
+            p->cache.clear();  // times measured under the old configuration
+            out->kchunk = kc;
+            out->tile_cfg = tc;
+            out->best_ms = res.best_s * 1e3;
+            out->default_ms = def_ms;
+            out->evaluations = evals;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }
 
 // ---- C ABI: misc ------------------------------------------------------------------------------

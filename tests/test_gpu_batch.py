@@ -93,3 +93,16 @@ def test_batch_rejects_mixed_programs(gao):
         gao.batch_create([a, d])
     with pytest.raises(gao.GaoError):
         gao.batch_create([a, a])
+
+
+def test_batch_autotune_keeps_parity(gao):
+    sizes = [300, 129, 520, 64]
+    progs, handles = suite(gao, sizes, 3)
+    refs = [oracle.run_program(p) for p in progs]
+    b = gao.batch_create(handles)
+    r = gao.batch_autotune(b, pop=6, generations=4, seed=2)
+    assert r["evaluations"] >= 1 and r["best_ms"] > 0 and r["kchunk"] in (64, 128, 256, 512)
+    for mask in (0b111111, 0b111110, 0b101011):
+        gao.batch_evaluate(b, [mask])
+        check_outputs(gao, progs, handles, refs, mask, 3)
+    gao.batch_destroy(b)

@@ -267,3 +267,29 @@ def test_full_size_n4096_sampled(gao):
     err = math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
     assert err <= TOL, err
     check_internal_consistency(out)
+
+
+def test_per_loop_transfer_mode(gao):
+    """Directive-style offload without a data region: every GPU loop copies its inputs in
+    and its outputs out.  Same results as resident buffers, more traffic, more time."""
+    n = 512
+    prog = all_outputs(W.six_loop(n, 91))
+    ref = oracle.run_program(prog)
+    res, naive = {}, {}
+    for mode, out in ((gao.TRANSFER_RESIDENT, res), (gao.TRANSFER_PER_LOOP, naive)):
+        p = gao.prog_from_workload(prog, transfer_mode=mode)
+        for _ in range(2):
+            out["s"] = gao.prog_run(p, 0b111111)
+        out["vals"] = {b.name: gao.prog_output(p, i) for i, b in enumerate(prog.buffers)}
+        out["stats"] = gao.prog_stats(p)
+        gao.prog_destroy(p)
+    for nm in ("A", "B", "C", "D", "E", "r", "f"):
+        assert np.array_equal(res["vals"][nm], naive["vals"][nm])
+    check_six({k: (float(v[0, 0]) if k == "f" else v) for k, v in naive["vals"].items()}, ref)
+    st = naive["stats"]
+    mat = n * n * 4
+    assert st[0]["d2h_bytes"] == 3 * mat  # INIT: A, B, C out
+    assert st[1]["h2d_bytes"] == 3 * mat and st[1]["d2h_bytes"] == mat  # GEMM: A, B, C in; C out
+    assert st[2]["h2d_bytes"] == 2 * mat and st[3]["h2d_bytes"] == mat
+    assert sum(s["h2d_bytes"] for s in res["stats"]) == 0
+    assert naive["s"] > res["s"]

@@ -170,3 +170,22 @@ def test_full_size_fp8_sampled(gao):
     err = _sampled_err(C, seed, n, False, ii, jj)
     print(f"fp8 n={n} sampled normwise error {err:.3e}")
     assert err <= 6e-2, err
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16"])
+def test_prog_autotune_keeps_parity(gao, prec):
+    """The GA picks a tile configuration by measured GEMM time; every configuration in its
+    search space stays within the precision's error gate, and the program keeps matching
+    the oracle afterwards."""
+    prog = W.six_loop(1024, 77, outputs=("C", "r", "f"))
+    p = gao.prog_from_workload(prog, gemm_prec=PREC[prec])
+    r = gao.prog_autotune(p, pop=6, generations=4, seed=1)
+    assert r["evaluations"] >= 1 and r["best_ms"] > 0 and r["default_ms"] > 0
+    assert r["best_ms"] <= 1.25 * r["default_ms"]
+    if prec == "bf16x6":
+        assert r["kchunk"] in (64, 128, 256, 512)
+    assert ((r["tile_cfg"] >> 4) & 15) in (2, 3, 4, 5)
+    gao.prog_run(p, 0b111111)
+    ref = oracle.run_program(prog)
+    assert oracle.rel_err(gao.prog_output(p, prog.index("C")), ref["C"]) <= TOL[prec]
+    gao.prog_destroy(p)
