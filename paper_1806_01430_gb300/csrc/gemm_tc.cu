@@ -257,7 +257,7 @@ struct TcCfg {
     static constexpr uint32_t A_TILE = BM * 128;  // 128 rows x 128 bytes
     static constexpr uint32_t B_TILE = BN * 128;
     static constexpr uint32_t STAGE = PA * A_TILE + PB * B_TILE;
-    static constexpr int ACC = CHUNKED ? 2 : 1;  // accumulator buffers (double-buffered when chunked)
+    static constexpr int ACC = 2;  // accumulator buffers: a tile's epilogue overlaps the next tile's MMAs
     // With more than one product, hi.hi accumulates in its own tensor-memory block and
     // the smaller products in a second one, so the large accumulator takes one rounded
     // addition per K step instead of NPROD.
@@ -275,9 +275,80 @@ struct TcCfg {
 };
 
 // One 128 x BN output tile (row tile tm, column tile tn) of one problem.
-template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
-__device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmB, const EpiArgs& ep,
-                                             int Mp, int Np, int num_kb, int chunk_kb, int tm, int tn, int* err) {
+// Row tile tm and column tile tn of tile `bid` in a tiles_m x tiles_n grid: groups of
+// `group` row tiles (16 by default), row tile fastest inside a group, so the tiles
+// processed at the same time share A row panels and B column panels in L2.
+__device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int group, int& tm, int& tn) {
+    const int GROUP = group > 0 ? group : 16;
+    const int group_tiles = GROUP * tiles_n;
+    const int first_m = (bid / group_tiles) * GROUP;
+    const int gm = min(tiles_m - first_m, GROUP);
+    tm = first_m + (bid % group_tiles) % gm;
+    tn = (bid % group_tiles) / gm;
+}
+
+// Everything one output tile needs.
+struct TileInfo {
+    const CUtensorMap* ta;
+    const CUtensorMap* tb;
+    EpiArgs ep;
+    int Mp, Np, num_kb, chunk_kb, m0, n0;
+};
+
+// Tiles of one problem (kernel arguments).
+struct OneProblem {
+    const CUtensorMap* ta;
+    const CUtensorMap* tb;
+    EpiArgs ep;
+    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, bn;
+    __device__ __forceinline__ void get(int t, TileInfo& ti) const {
+        int tm, tn;
+        raster(t, tiles_m, tiles_n, group, tm, tn);
+        ti.ta = ta;
+        ti.tb = tb;
+        ti.ep = ep;
+        ti.Mp = Mp;
+        ti.Np = Np;
+        ti.num_kb = num_kb;
+        ti.chunk_kb = chunk_kb;
+        ti.m0 = tm * BM;
+        ti.n0 = tn * bn;
+    }
+};
+
+// Tiles of a grouped launch: tile t belongs to the problem whose range holds t
+// (binary search over tile_start, which increases along the table).
+struct ProblemTable {
+    const TcProblem* probs;
+    int nprob, bn;
+    __device__ __forceinline__ void get(int t, TileInfo& ti) const {
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (probs[mid].tile_start <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const TcProblem* P = probs + lo;
+        int tm, tn;
+        raster(t - P->tile_start, P->tiles_m, P->tiles_n, P->group, tm, tn);
+        ti.ta = &P->ta;
+        ti.tb = &P->tb;
+        ti.ep = P->ep;
+        ti.Mp = P->Mp;
+        ti.Np = P->Np;
+        ti.num_kb = P->num_kb;
+        ti.chunk_kb = P->chunk_kb;
+        ti.m0 = tm * BM;
+        ti.n0 = tn * bn;
+    }
+};
+
+// Persistent body: the CTA serves tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The
+// shared-memory stage ring and the two tensor-memory accumulator buffers carry on
+// from tile to tile, so the producer runs ahead into the next tile and the MMAs of a
+// tile overlap the epilogue of the previous one.
+template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8, class Src>
+__device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_tiles, int* err) {
     using Cfg = TcCfg<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>;
     constexpr uint32_t IDESC = FP8 ? idesc_e4m3<BN>() : idesc_bf16<BN>();
     constexpr int KBE = FP8 ? BK8 : BK;  // elements per K block
@@ -298,9 +369,6 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmA, const CUten
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    const int m0 = tm * BM, n0 = tn * BN;
-    const int nchunks = (num_kb + chunk_kb - 1) / chunk_kb;
-
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full_bar(s), 1);
@@ -319,10 +387,6 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmA, const CUten
         tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
         tmem_relinquish();
     }
-    if (warp == 0 && lane == 0) {
-        tma_prefetch_desc(tmA);
-        tma_prefetch_desc(tmB);
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -331,30 +395,35 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmA, const CUten
     if (warp == 0) {
         if (lane == 0) {
             // ---- TMA producer ----
-            int issued = 0;
+            int it = 0;  // k blocks issued so far (all tiles)
             bool ok = true;
-            for (int kb = 0; kb < num_kb; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-                if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, err)) {
-                    ok = false;
-                    break;
+            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+                TileInfo ti;
+                src.get(t, ti);
+                tma_prefetch_desc(ti.ta);
+                tma_prefetch_desc(ti.tb);
+                for (int kb = 0; kb < ti.num_kb; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(full_bar(s), Cfg::STAGE);
+                    const uint32_t st = tiles + (uint32_t)s * Cfg::STAGE;
+#pragma unroll
+                    for (int p = 0; p < PA; ++p)
+                        tma_load_2d(st + (uint32_t)p * Cfg::A_TILE, ti.ta, kb * KBE, p * ti.Mp + ti.m0, full_bar(s));
+#pragma unroll
+                    for (int p = 0; p < PB; ++p)
+                        tma_load_2d(st + PA * Cfg::A_TILE + (uint32_t)p * Cfg::B_TILE, ti.tb, kb * KBE,
+                                    p * ti.Np + ti.n0, full_bar(s));
                 }
-                mbar_expect_tx(full_bar(s), Cfg::STAGE);
-                const uint32_t st = tiles + (uint32_t)s * Cfg::STAGE;
-#pragma unroll
-                for (int p = 0; p < PA; ++p)
-                    tma_load_2d(st + (uint32_t)p * Cfg::A_TILE, tmA, kb * KBE, p * Mp + m0, full_bar(s));
-#pragma unroll
-                for (int p = 0; p < PB; ++p)
-                    tma_load_2d(st + PA * Cfg::A_TILE + (uint32_t)p * Cfg::B_TILE, tmB, kb * KBE, p * Np + n0,
-                                full_bar(s));
-                issued = kb + 1;
             }
-            const int first = issued > STAGES ? issued - STAGES : 0;
-            for (int kb = first; kb < issued; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            const int first = it > STAGES ? it - STAGES : 0;
+            for (int u = first; u < it; ++u) {
+                const int s = u % STAGES;
+                const uint32_t ph = (uint32_t)(u / STAGES) & 1u;
                 if (ok) {
                     // the MMA's release of the last uses of each stage
                     if (!mbar_wait(empty_bar(s), ph, abort_flag, err)) ok = false;
@@ -366,49 +435,55 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmA, const CUten
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
+            int it = 0, gc = 0;  // k blocks consumed, accumulator chunks used (all tiles)
             bool ok = true;
-            for (int c = 0; c < nchunks && ok; ++c) {
-                const int ab = CHUNKED ? (c & 1) : 0;
-                const uint32_t aph = CHUNKED ? ((uint32_t)(c >> 1) & 1u) : ((uint32_t)c & 1u);
-                if (!mbar_wait(acce_bar(ab), aph ^ 1u, abort_flag, err)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(ab * Cfg::BUF_COLS);
-                const int kb0 = c * chunk_kb;
-                const int kb1 = min(num_kb, kb0 + chunk_kb);
-                for (int kb = kb0; kb < kb1; ++kb) {
-                    const int s = kb % STAGES;
-                    const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-                    if (!mbar_wait(full_bar(s), ph, abort_flag, err)) {
+            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+                TileInfo ti;
+                src.get(t, ti);
+                const int nchunks = (ti.num_kb + ti.chunk_kb - 1) / ti.chunk_kb;
+                for (int c = 0; c < nchunks; ++c, ++gc) {
+                    const int ab = gc & 1;
+                    const uint32_t aph = (uint32_t)(gc >> 1) & 1u;
+                    if (!mbar_wait(acce_bar(ab), aph ^ 1u, abort_flag, err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_base = tiles + (uint32_t)s * Cfg::STAGE;
-                    const uint32_t b_base = a_base + PA * Cfg::A_TILE;
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {  // 4 MMA K steps of 32 bytes per 128-byte block
-#pragma unroll
-                        for (int pr = 0; pr < NPROD; ++pr) {
-                            const uint64_t ad =
-                                sw128_kmajor_desc(a_base + (uint32_t)prod_a(NPROD, pr) * Cfg::A_TILE + kk * 32);
-                            const uint64_t bd =
-                                sw128_kmajor_desc(b_base + (uint32_t)prod_b(NPROD, pr) * Cfg::B_TILE + kk * 32);
-                            // first product into each accumulator block of a chunk overwrites it
-                            const bool first = kb == kb0 && kk == 0 && (pr == 0 || (Cfg::SPLIT && pr == 1));
-                            const uint32_t dd = d + ((Cfg::SPLIT && pr > 0) ? (uint32_t)BN : 0u);
-                            if constexpr (FP8)
-                                mma_fp8(dd, ad, bd, IDESC, first ? 0u : 1u);
-                            else
-                                mma_bf16(dd, ad, bd, IDESC, first ? 0u : 1u);
+                    const uint32_t d = tmem + (uint32_t)(ab * Cfg::BUF_COLS);
+                    const int kb0 = c * ti.chunk_kb;
+                    const int kb1 = min(ti.num_kb, kb0 + ti.chunk_kb);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                        if (!mbar_wait(full_bar(s), ph, abort_flag, err)) {
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t a_base = tiles + (uint32_t)s * Cfg::STAGE;
+                        const uint32_t b_base = a_base + PA * Cfg::A_TILE;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {  // 4 MMA K steps of 32 bytes per 128-byte block
+#pragma unroll
+                            for (int pr = 0; pr < NPROD; ++pr) {
+                                const uint64_t ad =
+                                    sw128_kmajor_desc(a_base + (uint32_t)prod_a(NPROD, pr) * Cfg::A_TILE + kk * 32);
+                                const uint64_t bd =
+                                    sw128_kmajor_desc(b_base + (uint32_t)prod_b(NPROD, pr) * Cfg::B_TILE + kk * 32);
+                                // first product into each accumulator block of a chunk overwrites it
+                                const bool first = kb == kb0 && kk == 0 && (pr == 0 || (Cfg::SPLIT && pr == 1));
+                                const uint32_t dd = d + ((Cfg::SPLIT && pr > 0) ? (uint32_t)BN : 0u);
+                                if constexpr (FP8)
+                                    mma_fp8(dd, ad, bd, IDESC, first ? 0u : 1u);
+                                else
+                                    mma_bf16(dd, ad, bd, IDESC, first ? 0u : 1u);
+                            }
+                        }
+                        mma_commit(empty_bar(s));
                     }
-                    mma_commit(empty_bar(s));
+                    if (!ok) break;
+                    mma_commit(accf_bar(ab));
                 }
-                if (!ok) break;
-                mma_commit(accf_bar(ab));
             }
             if (!ok) {  // no MMA may still be running when tensor memory is freed
                 mma_commit(tail_bar);
@@ -422,66 +497,72 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmA, const CUten
         const int q = warp & 3;  // TMEM lane quadrant this warp may access
         const int half = ew >> 2;
         const int colbase = half * (BN / 2);
-        const int64_t grow = (int64_t)m0 + q * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         constexpr int G = BN / 2 / 32;  // 32-column groups per thread
-        float sum[CHUNKED ? BN / 2 : 1];
-        if (CHUNKED) {
+        int gc = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+            TileInfo ti;
+            src.get(t, ti);
+            const EpiArgs& ep = ti.ep;
+            const int nchunks = (ti.num_kb + ti.chunk_kb - 1) / ti.chunk_kb;
+            const int64_t grow = (int64_t)ti.m0 + q * 32 + lane;
+            const int n0 = ti.n0;
+            float sum[CHUNKED ? BN / 2 : 1];
 #pragma unroll
             for (int i = 0; i < (CHUNKED ? BN / 2 : 1); ++i) sum[i] = 0.0f;
-        }
-        bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int ab = CHUNKED ? (c & 1) : 0;
-            const uint32_t aph = CHUNKED ? ((uint32_t)(c >> 1) & 1u) : ((uint32_t)c & 1u);
-            if (!mbar_wait(accf_bar(ab), aph, abort_flag, err)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t tb = tmem + lane_addr + (uint32_t)(ab * Cfg::BUF_COLS + colbase);
+            for (int c = 0; c < nchunks; ++c, ++gc) {
+                const int ab = gc & 1;
+                const uint32_t aph = (uint32_t)(gc >> 1) & 1u;
+                if (!mbar_wait(accf_bar(ab), aph, abort_flag, err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tb = tmem + lane_addr + (uint32_t)(ab * Cfg::BUF_COLS + colbase);
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                uint32_t r[32];
-                float v[32];
-                tmem_ld32(tb + (uint32_t)(g * 32), r);
-                tmem_ld_wait();
-#pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-                if constexpr (Cfg::SPLIT) {  // small products: same columns, second block
-                    tmem_ld32(tb + (uint32_t)(BN + g * 32), r);
+                for (int g = 0; g < G; ++g) {
+                    uint32_t r[32];
+                    float v[32];
+                    tmem_ld32(tb + (uint32_t)(g * 32), r);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] += __uint_as_float(r[i]);
-                }
-                if constexpr (FP8) {
-                    // chunk c is K block c: scale by sa(row, c) * sb(c, column)
-                    const float sa = grow < ep.M ? ep.sa[grow * (int64_t)ep.kbs + c] : 0.0f;
-                    const float4* sb4 =
-                        reinterpret_cast<const float4*>(ep.sb + (int64_t)c * ep.sb_ld + n0 + colbase + g * 32);
+                    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+                    if constexpr (Cfg::SPLIT) {  // small products: same columns, second block
+                        tmem_ld32(tb + (uint32_t)(BN + g * 32), r);
+                        tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float4 b = sb4[j];
-                        sum[g * 32 + 4 * j + 0] = fmaf(sa * b.x, v[4 * j + 0], sum[g * 32 + 4 * j + 0]);
-                        sum[g * 32 + 4 * j + 1] = fmaf(sa * b.y, v[4 * j + 1], sum[g * 32 + 4 * j + 1]);
-                        sum[g * 32 + 4 * j + 2] = fmaf(sa * b.z, v[4 * j + 2], sum[g * 32 + 4 * j + 2]);
-                        sum[g * 32 + 4 * j + 3] = fmaf(sa * b.w, v[4 * j + 3], sum[g * 32 + 4 * j + 3]);
+                        for (int i = 0; i < 32; ++i) v[i] += __uint_as_float(r[i]);
                     }
-                } else if constexpr (CHUNKED) {
+                    if constexpr (FP8) {
+                        // chunk c is K block c: scale by sa(row, c) * sb(c, column)
+                        const float sa = grow < ep.M ? ep.sa[grow * (int64_t)ep.kbs + c] : 0.0f;
+                        const float4* sb4 =
+                            reinterpret_cast<const float4*>(ep.sb + (int64_t)c * ep.sb_ld + n0 + colbase + g * 32);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) sum[g * 32 + i] += v[i];
-                } else {
-                    store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, v);
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 b = sb4[j];
+                            sum[g * 32 + 4 * j + 0] = fmaf(sa * b.x, v[4 * j + 0], sum[g * 32 + 4 * j + 0]);
+                            sum[g * 32 + 4 * j + 1] = fmaf(sa * b.y, v[4 * j + 1], sum[g * 32 + 4 * j + 1]);
+                            sum[g * 32 + 4 * j + 2] = fmaf(sa * b.z, v[4 * j + 2], sum[g * 32 + 4 * j + 2]);
+                            sum[g * 32 + 4 * j + 3] = fmaf(sa * b.w, v[4 * j + 3], sum[g * 32 + 4 * j + 3]);
+                        }
+                    } else if constexpr (CHUNKED) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) sum[g * 32 + i] += v[i];
+                    } else {
+                        store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, v);
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce_bar(ab));
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce_bar(ab));
-        }
-        if constexpr (CHUNKED) {
-            if (ok) {
+            if constexpr (CHUNKED) {
+                if (ok) {
 #pragma unroll
-                for (int g = 0; g < G; ++g) store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, sum + g * 32);
+                    for (int g = 0; g < G; ++g) store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, sum + g * 32);
+                }
             }
         }
     }
@@ -494,45 +575,19 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmA, const CUten
     }
 }
 
-// Row tile tm and column tile tn of CTA `bid` in a tiles_m x tiles_n grid: groups of
-// `group` row tiles (16 by default), row tile fastest inside a group, so the CTAs of
-// one wave share A row panels and B column panels in L2.
-__device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int group, int& tm, int& tn) {
-    const int GROUP = group > 0 ? group : 16;
-    const int group_tiles = GROUP * tiles_n;
-    const int first_m = (bid / group_tiles) * GROUP;
-    const int gm = min(tiles_m - first_m, GROUP);
-    tm = first_m + (bid % group_tiles) % gm;
-    tn = (bid % group_tiles) / gm;
-}
-
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep,
                    int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int group, int* err) {
-    int tm, tn;
-    raster((int)blockIdx.x, tiles_m, tiles_n, group, tm, tn);
-    gemm_tc_tile<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tm, tn, err);
+    const OneProblem src{&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, BN};
+    gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(src, tiles_m * tiles_n, err);
 }
 
-// Grouped launch: CTA b serves tile b - tile_start of the problem whose range holds b
-// (binary search over the problems' tile_start, which increase with the index).
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
 __global__ void __launch_bounds__(kThreadsTc, 1)
-    gemm_tc_grouped_kernel(const TcProblem* __restrict__ probs, int nprob, int* err) {
-    const int b = (int)blockIdx.x;
-    int lo = 0, hi = nprob - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (probs[mid].tile_start <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    const TcProblem* P = probs + lo;
-    const EpiArgs ep = P->ep;
-    int tm, tn;
-    raster(b - P->tile_start, P->tiles_m, P->tiles_n, P->group, tm, tn);
-    gemm_tc_tile<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(&P->ta, &P->tb, ep, P->Mp, P->Np, P->num_kb, P->chunk_kb,
-                                                          tm, tn, err);
+    gemm_tc_grouped_kernel(const TcProblem* __restrict__ probs, int nprob, int total_tiles, int* err) {
+    const ProblemTable src{probs, nprob, BN};
+    gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(src, total_tiles, err);
 }
 
 // ---- split kernels ------------------------------------------------------------------------------
@@ -742,8 +797,9 @@ cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const EpiAr
         attr_set = true;
     }
     const int tiles_m = Mp / BM, tiles_n = (ep.N + BN - 1) / BN;
-    const int64_t grid = (int64_t)tiles_m * tiles_n;
-    if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+    const int64_t total = (int64_t)tiles_m * tiles_n;
+    if (total > 0x7fffffff) return cudaErrorInvalidValue;
+    const int64_t grid = std::min<int64_t>(total, (int64_t)sm_count());  // persistent: one CTA per SM
     kern<<<(unsigned)grid, kThreadsTc, Cfg::SMEM, st>>>(ta, tb, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group,
                                                         err);
     return cudaGetLastError();
@@ -930,7 +986,8 @@ cudaError_t launch_grouped_t(const TcProblem* d_probs, int nprob, int total_tile
         attr_set = true;
     }
     if (total_tiles <= 0) return cudaSuccess;
-    kern<<<(unsigned)total_tiles, kThreadsTc, Cfg::SMEM, st>>>(d_probs, nprob, err);
+    const int grid = std::min(total_tiles, sm_count());  // persistent: one CTA per SM
+    kern<<<(unsigned)grid, kThreadsTc, Cfg::SMEM, st>>>(d_probs, nprob, total_tiles, err);
     return cudaGetLastError();
 }
 
