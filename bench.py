@@ -147,24 +147,23 @@ def barrier(world):
         dist.barrier()
 
 
-def allmax(world, x: float) -> float:
-    if world == 1:
-        return x
+def _reduce(x: float, op: str) -> float:
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def allmax(world, x: float) -> float:
+    """Max over ranks (the slowest rank's time is the job's time)."""
+    return x if world == 1 else _reduce(x, "max")
 
 
 def allsum(world, x: float) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    """Sum over ranks (the whole job's work)."""
+    return x if world == 1 else _reduce(x, "sum")
 
 
 # ---- CPU oracle baseline -------------------------------------------------------------------

@@ -275,6 +275,16 @@ gao_status batch_stats(gao_batch *b, gao_batch_stat *out);
 gao_status batch_autotune(gao_batch *b, const gao_ga_params *params, gao_autotune_result *out);
 void batch_destroy(gao_batch *b);
 
+/* Measures n genes (distinct, not measured before); writes seconds_out[i] (negative or
+ * non-finite for a failed gene) and returns GAO_OK, or another status to stop the GA. */
+typedef int (*gao_gene_eval_fn)(const uint64_t *genes, int n, double *seconds_out, void *ctx);
+
+/* The Simple GA with a caller-supplied evaluation of each generation's new genes (same
+ * draws as ga_run).  Lets a caller measure a generation's genes in parallel, e.g. one
+ * process per GPU, each measuring a share and exchanging the times. */
+gao_status ga_run_callback(int n_genes, const gao_ga_params *params, gao_gene_eval_fn eval, void *ctx,
+                           gao_ga_result *result);
+
 /* ---- misc ------------------------------------------------------------------ */
 
 /* Message of the last failing call on this thread ("" if none). */

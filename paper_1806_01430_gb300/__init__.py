@@ -117,6 +117,8 @@ SIGNATURES = {
     "batch_ga_run": (ctypes.c_int, [_P, ctypes.POINTER(gao_ga_params), ctypes.POINTER(gao_ga_result)]),
     "batch_stats": (ctypes.c_int, [_P, ctypes.POINTER(gao_batch_stat)]),
     "batch_destroy": (None, [_P]),
+    "ga_run_callback": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(gao_ga_params), ctypes.c_void_p, _P,
+                                       ctypes.POINTER(gao_ga_result)]),
     "prog_autotune": (ctypes.c_int, [_P, ctypes.POINTER(gao_ga_params), ctypes.POINTER(gao_autotune_result)]),
     "batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(gao_ga_params), ctypes.POINTER(gao_autotune_result)]),
 }
@@ -453,3 +455,38 @@ def batch_autotune(b: Batch, pop=8, generations=6, pc=0.9, pm=0.05, seed=0) -> D
     r = gao_autotune_result()
     _check(lib().batch_autotune(b.handle, ctypes.byref(params), ctypes.byref(r)), "batch_autotune")
     return _autotune_out(r)
+
+
+GENE_EVAL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+
+
+def ga_run_callback(evaluate, n_genes: int, pop=12, generations=12, pc=0.9, pm=0.05, seed=0, elite=1,
+                    mutation=0) -> GAResult:
+    """Simple GA whose new genes of each generation are measured by ``evaluate(genes) ->
+    seconds`` (lists).  An exception inside ``evaluate`` stops the GA (GaoError)."""
+    errors = []
+
+    def cb(genes_p, n, out_p, ctx):
+        try:
+            secs = evaluate([int(genes_p[i]) for i in range(n)])
+            if len(secs) != n:
+                raise ValueError("evaluate returned the wrong number of times")
+            for i in range(n):
+                out_p[i] = float(secs[i])
+            return GAO_OK
+        except BaseException as e:  # noqa: BLE001 - reported to the caller below
+            errors.append(e)
+            return GAO_ECPU
+
+    c_cb = GENE_EVAL_FN(cb)
+    params = _params(pop, generations, pc, pm, seed, elite, mutation, 0.0)
+    r, hist, pops = _result(params)
+    st = lib().ga_run_callback(n_genes, ctypes.byref(params), ctypes.cast(c_cb, ctypes.c_void_p), None,
+                               ctypes.byref(r))
+    if st != GAO_OK:
+        err = GaoError(st, "ga_run_callback")
+        if errors:
+            raise err from errors[0]
+        raise err
+    return _unpack(r, hist, pops, params)

@@ -12,6 +12,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <functional>
 #include <unordered_map>
 #include <vector>
@@ -68,6 +69,18 @@ uint64_t mutate(Sm64& r, uint64_t c, int n_genes, double pm, int mode) {
 double ga_fitness(double seconds) { return fitness_of(seconds); }
 
 gao_status ga_core(int n_genes, const gao_ga_params& p, const TimeFn& time_of, gao_ga_result* res) {
+    PopFn each = [&](const std::vector<uint64_t>& genes, std::vector<double>* secs) {
+        secs->assign(genes.size(), -1.0);
+        for (size_t i = 0; i < genes.size(); ++i) {
+            const gao_status st = time_of(genes[i], &(*secs)[i]);
+            if (st != GAO_OK) return st;
+        }
+        return GAO_OK;
+    };
+    return ga_core_pop(n_genes, p, each, res);
+}
+
+gao_status ga_core_pop(int n_genes, const gao_ga_params& p, const PopFn& eval, gao_ga_result* res) {
     if (n_genes < 1 || n_genes > 64) return fail(GAO_EINVAL, "gene length must be in [1, 64]");
     if (p.pop < 1 || p.generations < 1) return fail(GAO_EINVAL, "pop and generations must be >= 1");
     if (!(p.pc >= 0.0 && p.pc <= 1.0) || !(p.pm >= 0.0 && p.pm <= 1.0))
@@ -86,19 +99,30 @@ gao_status ga_core(int n_genes, const gao_ga_params& p, const TimeFn& time_of, g
     std::vector<double> times((size_t)M), fit((size_t)M);
     for (int g = 0; g < p.generations; ++g) {
         int ev = 0, hits = 0;
+        // distinct genes not measured yet, in population order
+        std::vector<uint64_t> fresh;
         for (int i = 0; i < M; ++i) {
             const uint64_t m = popu[(size_t)i];
-            auto it = cache.find(m);
-            if (it != cache.end()) {
-                ++hits;
-                times[(size_t)i] = it->second;
-            } else {
-                double t = -1.0;
-                const gao_status st = time_of(m, &t);
-                if (st != GAO_OK) return st;  // systemic failure: stop the search
-                cache.emplace(m, t);
-                times[(size_t)i] = t;
+            if (cache.find(m) == cache.end() && std::find(fresh.begin(), fresh.end(), m) == fresh.end())
+                fresh.push_back(m);
+        }
+        if (!fresh.empty()) {
+            std::vector<double> secs;
+            const gao_status st = eval(fresh, &secs);
+            if (st != GAO_OK) return st;  // systemic failure: stop the search
+            if (secs.size() != fresh.size()) return fail(GAO_EINVAL, "gene evaluation returned the wrong count");
+            for (size_t j = 0; j < fresh.size(); ++j) cache.emplace(fresh[j], secs[j]);
+        }
+        for (int i = 0; i < M; ++i) {
+            const uint64_t m = popu[(size_t)i];
+            times[(size_t)i] = cache.find(m)->second;
+            // the first individual carrying a fresh gene measured it; every other one is served
+            const auto pos = std::find(fresh.begin(), fresh.end(), m);
+            if (pos != fresh.end()) {
                 ++ev;
+                fresh.erase(pos);
+            } else {
+                ++hits;
             }
         }
         for (int i = 0; i < M; ++i) fit[(size_t)i] = fitness_of(times[(size_t)i]);

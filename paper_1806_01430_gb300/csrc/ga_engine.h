@@ -1,6 +1,7 @@
 // Simple-GA core shared by ga_run, ga_run_table and the tile autotuner.
 #pragma once
 #include <functional>
+#include <vector>
 
 #include "../../include/gao.h"
 
@@ -14,6 +15,14 @@ using TimeFn = std::function<gao_status(uint64_t gene, double* seconds)>;
 double ga_fitness(double seconds);
 
 gao_status ga_core(int n_genes, const gao_ga_params& p, const TimeFn& time_of, gao_ga_result* res);
+
+// Measures several genes at once (the distinct genes of a generation that are not in
+// the cache yet, in population order).  Returns GAO_OK and fills seconds (same length).
+using PopFn = std::function<gao_status(const std::vector<uint64_t>& genes, std::vector<double>* seconds)>;
+
+// The same GA with per-generation evaluation: identical draws, cache and results as
+// ga_core when the times agree.
+gao_status ga_core_pop(int n_genes, const gao_ga_params& p, const PopFn& eval, gao_ga_result* res);
 
 // Tile configuration of a 4-bit autotuning gene for GEMM precision `prec`:
 // bits 0-1 raster group 4/8/16/32 (log2 2..5, stored in tile_cfg bits 4-7); bits 2-3

@@ -889,6 +889,18 @@ extern "C" gao_status ga_run_table(const double* times, int n_genes, const gao_g
     return ga_core(n_genes, *params, fn, result);
 }
 
+extern "C" gao_status ga_run_callback(int n_genes, const gao_ga_params* params, gao_gene_eval_fn eval, void* ctx,
+                                      gao_ga_result* result) {
+    if (!params || !eval || !result) return fail(GAO_EINVAL, "null argument");
+    PopFn fn = [&](const std::vector<uint64_t>& genes, std::vector<double>* secs) {
+        secs->assign(genes.size(), -1.0);
+        const int st = eval(genes.data(), (int)genes.size(), secs->data(), ctx);
+        if (st != GAO_OK) return fail((gao_status)(st > 0 && st <= GAO_ECPU ? st : GAO_ECPU), "gene evaluation callback failed");
+        return GAO_OK;
+    };
+    return ga_core_pop(n_genes, *params, fn, result);
+}
+
 // ---- C ABI: autotuning -------------------------------------------------------------------------
 
 extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, gao_autotune_result* out) {
