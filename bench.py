@@ -362,6 +362,31 @@ def our_arm(args, world, rank, local):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ew * 1e3}
         gao.prog_destroy(q)
 
+    # the all-64-genes search of the n = 4096 FP32 SIMT program (the paper's experiment
+    # shape): every gene measured once (CPU loops included), then the paper's GA
+    # (M = T = 12, Pc 0.9, Pm 0.05) on the measured table; the paper's metric is the
+    # all-CPU time over the best gene's time
+    search = None
+    if args.search and rank == 0 and args.workload == "six_loop":
+        sp = W.six_loop(args.n, W.SEED_CONFIG1, outputs=("C", "r", "f"))
+        q = gao.prog_from_workload(sp, gemm_prec=PREC["fp32_simt"], stream=stream)
+        gao.prog_run(q, 0b111111)
+        t0 = time.perf_counter()
+        fit, secs, hits = gao.ga_evaluate([q], list(range(64)))
+        t_search = time.perf_counter() - t0
+        ga = gao.ga_run([q], **W.PAPER_GA, seed=11)
+        order = np.argsort(secs)
+        search = {"workload": f"six_loop_n{args.n}_fp32_simt_all_64_genes", "evals": 64,
+                  "wall_s": t_search, "evals_per_s": 64 / t_search,
+                  "all_cpu_s": float(secs[0]), "all_gpu_s": float(secs[63]),
+                  "best_gene": format(int(order[0]), "06b"), "best_s": float(secs[order[0]]),
+                  "speedup_best_vs_all_cpu": float(secs[0] / secs[order[0]]),
+                  "top5": [[format(int(m), "06b"), float(secs[m])] for m in order[:5]],
+                  "paper_ga": {"best_gene": format(ga.best_mask, "06b"), "best_s": ga.best_s,
+                               "found_exhaustive_best": bool(ga.best_mask == int(order[0])),
+                               "measured": ga.evaluations, "served": ga.cache_hits}}
+        gao.prog_destroy(q)
+
     if rank != 0:
         return
     pk = peaks()
@@ -399,7 +424,7 @@ def our_arm(args, world, rank, local):
                        "l2": "working set larger than the 129 MB L2 (no flush)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "gemm_rel_err_sampled": err, "fp32_simt": simt, "loop_ms": loop_ms,
-            "loop_gbs": loop_gbs}
+            "loop_gbs": loop_gbs, "ga_search": search}
     print(json.dumps(line), flush=True)
 
 
@@ -481,6 +506,7 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-simt", dest="compare_simt", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-search", dest="search", action="store_false")
     ap.add_argument("--ref-target-s", type=float, default=8.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

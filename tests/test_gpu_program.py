@@ -293,3 +293,35 @@ def test_per_loop_transfer_mode(gao):
     assert st[2]["h2d_bytes"] == 2 * mat and st[3]["h2d_bytes"] == mat
     assert sum(s["h2d_bytes"] for s in res["stats"]) == 0
     assert naive["s"] > res["s"]
+
+
+def test_config1_all_64_genes_n4096(gao):
+    """configs[1]: the n = 4096 FP32 SIMT program under all 64 genes (CPU loops included).
+    Every gene is measured once (cache), the fastest gene places the GEMM on the GPU, the
+    paper's GA finds the exhaustive optimum of the measured times, and the outputs of
+    the all-CPU and of the best gene both match the oracle on sampled GEMM entries and in
+    their exact relations."""
+    n, seed = 4096, W.SEED_CONFIG1
+    prog = W.six_loop(n, seed, outputs=("A", "C", "D", "E", "r", "f"))
+    p = gao.prog_from_workload(prog, gemm_prec=0)
+    fit, secs, hits = gao.ga_evaluate([p], list(range(64)))
+    assert hits == 0 and np.all(secs > 0)
+    best = int(np.argmin(secs))
+    assert (best >> 1) & 1 == 1  # the GEMM belongs on the GPU
+    assert secs[0] > 10 * secs[best]  # offloading pays off by an order of magnitude at least
+    res = gao.ga_run([p], **W.PAPER_GA, seed=11)
+    table = secs.copy()
+    ref = oga.run(lambda m: float(table[m]), 6, 12, 12, 0.9, 0.05, 11)
+    assert res.populations == ref.populations and res.best_mask == ref.best_mask
+    rng = np.random.default_rng(4)
+    ii, jj = rng.integers(0, n, 96), rng.integers(0, n, 96)
+    want = oracle.gemm_init_entries(seed, (0, 1, 2), False, n, n, n, 1.5, 0.5, ii, jj)
+    for mask in (0, best):
+        gao.prog_run(p, mask)
+        out = {nm: gao.prog_output(p, prog.index(nm)) for nm in ("A", "C", "D", "E", "r", "f")}
+        out["f"] = float(out["f"][0, 0])
+        got = out["C"][ii, jj].astype(np.float64)
+        err = math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
+        assert err <= TOL, (mask, err)
+        check_internal_consistency(out)
+    gao.prog_destroy(p)
