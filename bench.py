@@ -261,7 +261,7 @@ def our_arm(args, world, rank, local):
         prog = W.six_loop(n, W.SEED_CONFIG1 + rank, outputs=("C", "r", "f"))
         wname = f"six_loop_n{n}_all_gpu_{prec}"
     flops = prog.gemm_flops()
-    p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream)
+    p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream, fuse_chains=args.fuse)
     mask = (1 << prog.n_loops) - 1
     gemm_loop = 1
     kern_ms, launches = [], 0
@@ -343,7 +343,7 @@ def our_arm(args, world, rank, local):
     e2e = None
     if args.e2e and args.workload == "six_loop":
         hp = W.host_input_program(n, prog.seed, outputs=("r", "f"))
-        q = gao.prog_from_workload(hp, gemm_prec=PREC[prec], stream=stream)
+        q = gao.prog_from_workload(hp, gemm_prec=PREC[prec], stream=stream, fuse_chains=args.fuse)
         import oracle  # input generation only (seeded counter hash); not on the timed path
         for nm, b in (("A", 0), ("B", 1), ("C0", 2)):
             gao.prog_set_input(q, hp.index(nm), oracle.init_matrix(prog.seed, b, n, n).astype(np.float32))
@@ -420,7 +420,8 @@ def our_arm(args, world, rank, local):
             "data": "synthetic (seeded counter hash, U[-1,1))",
             "config": {"workload": wname, "n": n if args.workload == "six_loop" else None,
                        "gene": format(mask, f"0{prog.n_loops}b"),
-                       "gemm": prec, "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "gemm": prec, "fused_chain": bool(args.fuse),
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "working set larger than the 129 MB L2 (no flush)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "gemm_rel_err_sampled": err, "fp32_simt": simt, "loop_ms": loop_ms,
@@ -507,6 +508,8 @@ def main():
     ap.add_argument("--no-simt", dest="compare_simt", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-search", dest="search", action="store_false")
+    ap.add_argument("--fuse", dest="fuse", action="store_true",
+                    help="fuse GEMM -> scale-add -> transpose -> norm into the GEMM epilogue")
     ap.add_argument("--ref-target-s", type=float, default=8.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

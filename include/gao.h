@@ -110,7 +110,10 @@ typedef struct gao_opts {
                                 (NULL: the library allocates it); must outlive the program */
     uint64_t dev_arena_bytes;
     int32_t transfer_mode;   /* GAO_TRANSFER_RESIDENT or GAO_TRANSFER_PER_LOOP               */
-    int32_t _reserved;
+    int32_t fuse_chains;     /* 1: when a gene puts a chain GEMM -> AXPY(C + a X) -> TRANSPOSE
+                                [-> FROBENIUS of the transpose] on the GPU (tensor-core BF16
+                                precisions, resident transfers), run it as one pass: the GEMM's
+                                epilogue writes C, D and E and the norm's partial sums     */
 } gao_opts;
 
 /* Data movement between host and device under a gene (Sec. 2 and Sec. 3.3: CPU-GPU
@@ -152,7 +155,8 @@ gao_status prog_output(gao_prog *p, int buf, const void **host_ptr, gao_buffer *
 gao_status prog_device_ptr(gao_prog *p, int buf, void **dev_ptr);
 
 typedef struct gao_loop_stat {
-    int32_t placement;  /* 1: ran on the GPU, 0: on the CPU                           */
+    int32_t placement;  /* 1: ran on the GPU, 0: on the CPU, 2: on the GPU inside the
+                           fused pass of an earlier GEMM loop (its time is that loop's)  */
     int32_t launches;   /* kernels of this library launched for the loop              */
     double device_ms;   /* GPU time of the loop's kernels (CUDA events)                */
     double kernel_ms;   /* GPU time of its main kernel only (GEMM: without the split)  */

@@ -48,7 +48,7 @@ class gao_opts(ctypes.Structure):
     _fields_ = [("gemm_prec", ctypes.c_int32), ("kchunk", ctypes.c_int32), ("tile_cfg", ctypes.c_int32),
                 ("cpu_threads", ctypes.c_int32), ("seed", ctypes.c_uint64), ("timeout_s", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("dev_arena", ctypes.c_void_p), ("dev_arena_bytes", ctypes.c_uint64),
-                ("transfer_mode", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
+                ("transfer_mode", ctypes.c_int32), ("fuse_chains", ctypes.c_int32)]
 
 
 class gao_loop_stat(ctypes.Structure):
@@ -188,9 +188,10 @@ def _marshal(buffers, loops):
 
 
 def _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, arena_ptr, arena_bytes,
-          transfer_mode=TRANSFER_RESIDENT):
+          transfer_mode=TRANSFER_RESIDENT, fuse_chains=False):
     o = gao_opts()
     o.transfer_mode = int(transfer_mode)
+    o.fuse_chains = 1 if fuse_chains else 0
     o.gemm_prec, o.kchunk, o.tile_cfg, o.cpu_threads = int(gemm_prec), int(kchunk), int(tile_cfg), int(cpu_threads)
     o.seed, o.timeout_s = int(seed), float(timeout_s)
     o.stream = _stream_handle(stream)
@@ -229,7 +230,7 @@ def prog_device_bytes(buffers, loops, seed=0, gemm_prec=FP32_SIMT, kchunk=0, til
 
 def prog_create(buffers, loops, seed: int = 0, gemm_prec: int = FP32_SIMT, kchunk: int = 0, tile_cfg: int = 0,
                 cpu_threads: int = 0, timeout_s: float = 0.0, stream=None, arena=None,
-                transfer_mode: int = TRANSFER_RESIDENT) -> Prog:
+                transfer_mode: int = TRANSFER_RESIDENT, fuse_chains: bool = False) -> Prog:
     """Declare a program.  ``buffers``/``loops`` are sequences of objects with the
     gao_buffer / gao_loop fields (e.g. workloads.Buffer / workloads.Loop).  ``arena``:
     optional device memory (a torch uint8 CUDA tensor, or (ptr, bytes))."""
@@ -240,7 +241,8 @@ def prog_create(buffers, loops, seed: int = 0, gemm_prec: int = FP32_SIMT, kchun
             ptr, nbytes = int(arena[0]), int(arena[1])
         else:
             ptr, nbytes, keep = int(arena.data_ptr()), int(arena.numel() * arena.element_size()), arena
-    o = _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, ptr, nbytes, transfer_mode)
+    o = _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, ptr, nbytes, transfer_mode,
+              fuse_chains)
     h = ctypes.c_void_p(None)
     _check(lib().prog_create(cl, nl, cb, nb, ctypes.byref(o), ctypes.byref(h)), "prog_create")
     return Prog(h, buffers, loops, keep)

@@ -106,9 +106,11 @@ struct TcEvents {
     int launches = 0;                         // out: kernels launched
 };
 size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K);
+struct TcFuse;
 cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M,
                            int64_t N, int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
-                           size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why);
+                           size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why,
+                           const TcFuse* fuse = nullptr);
 
 // ---- CPU loops (binary32, OpenMP) ------------------------------------------------
 struct CpuCtx {

@@ -128,6 +128,10 @@ __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -221,35 +225,79 @@ static_assert(prod_a(3, 0) == 0 && prod_b(3, 0) == 0 && prod_a(3, 1) == 0 && pro
 
 
 // Write 32 consecutive columns [gcol, gcol+32) of row grow from binary32 values v.
-__device__ __forceinline__ void store_row32(const EpiArgs& e, int64_t grow, int64_t gcol, const float* v) {
+// With a fused chain, also D = C + alpha2 X (same single rounding as the AXPY loop),
+// E = D^T (for each column the warp's 32 rows are 32 consecutive floats of an E row: a
+// coalesced 128-byte store), and the thread's sum of D^2 into *sq.
+// C0 and X are read through the non-coherent read-only path: within the kernel every
+// element of C0 is read once, by the thread that later overwrites it when C aliases C0,
+// and X is never written, so these loads need not wait behind earlier stores.
+__device__ __forceinline__ void store_row32(const EpiArgs& e, int64_t grow, int64_t gcol, const float* v,
+                                            double* sq = nullptr) {
     if (grow >= e.M) return;
     float* crow = e.C + grow * (int64_t)e.N;
     const float* c0row = e.C0 + grow * (int64_t)e.N;
+    const bool fuse = e.fuse != 0;
+    const float* xrow = fuse ? e.X + grow * (int64_t)e.N : nullptr;
+    float* drow = fuse ? e.D + grow * (int64_t)e.N : nullptr;
+    float s2 = 0.0f, s3 = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int64_t c = gcol + 4 * j;
-        if (e.vec && c + 3 < e.N) {
-            float4 o = make_float4(e.alpha * v[4 * j], e.alpha * v[4 * j + 1], e.alpha * v[4 * j + 2],
-                                   e.alpha * v[4 * j + 3]);
-            if (e.beta != 0.0f) {
-                const float4 c0 = *reinterpret_cast<const float4*>(c0row + c);
-                o.x = fmaf(e.beta, c0.x, o.x);
-                o.y = fmaf(e.beta, c0.y, o.y);
-                o.z = fmaf(e.beta, c0.z, o.z);
-                o.w = fmaf(e.beta, c0.w, o.w);
+    for (int u = 0; u < 8; ++u) {
+        const int64_t c = gcol + 4 * u;
+        float cv[4], xv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const bool full = e.vec && c + 3 < e.N;
+        if (full) {
+            float4 c0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (e.beta != 0.0f) c0 = __ldg(reinterpret_cast<const float4*>(c0row + c));
+            if (fuse) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(xrow + c));
+                xv[0] = x.x, xv[1] = x.y, xv[2] = x.z, xv[3] = x.w;
             }
-            *reinterpret_cast<float4*>(crow + c) = o;
+            cv[0] = e.alpha * v[4 * u + 0];
+            cv[1] = e.alpha * v[4 * u + 1];
+            cv[2] = e.alpha * v[4 * u + 2];
+            cv[3] = e.alpha * v[4 * u + 3];
+            if (e.beta != 0.0f) {
+                cv[0] = fmaf(e.beta, c0.x, cv[0]);
+                cv[1] = fmaf(e.beta, c0.y, cv[1]);
+                cv[2] = fmaf(e.beta, c0.z, cv[2]);
+                cv[3] = fmaf(e.beta, c0.w, cv[3]);
+            }
+            *reinterpret_cast<float4*>(crow + c) = make_float4(cv[0], cv[1], cv[2], cv[3]);
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                cv[q] = 0.0f;
                 if (c + q < e.N) {
-                    float o = e.alpha * v[4 * j + q];
-                    if (e.beta != 0.0f) o = fmaf(e.beta, c0row[c + q], o);
+                    float o = e.alpha * v[4 * u + q];
+                    if (e.beta != 0.0f) o = fmaf(e.beta, __ldg(c0row + c + q), o);
+                    cv[q] = o;
+                    if (fuse) xv[q] = __ldg(xrow + c + q);
                     crow[c + q] = o;
                 }
             }
         }
+        if (fuse) {
+            float d[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[q] = fmaf(e.alpha2, xv[q], cv[q]);  // D = C + alpha2 X, one rounding
+            if (full) {
+                *reinterpret_cast<float4*>(drow + c) = make_float4(d[0], d[1], d[2], d[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c + q < e.N) drow[c + q] = d[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (c + q < e.N) {
+                    e.E[(c + q) * (int64_t)e.M + grow] = d[q];
+                    if (q & 1) s3 = fmaf(d[q], d[q], s3);
+                    else s2 = fmaf(d[q], d[q], s2);
+                }
+            }
+        }
     }
+    if (fuse) *sq += (double)s2 + (double)s3;
 }
 
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8 = false>
@@ -508,12 +556,23 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
             const int nchunks = (ti.num_kb + ti.chunk_kb - 1) / ti.chunk_kb;
             const int64_t grow = (int64_t)ti.m0 + q * 32 + lane;
             const int n0 = ti.n0;
+            double sq = 0.0;  // fused chain: this thread's sum of D^2 over the tile
             float sum[CHUNKED ? BN / 2 : 1];
 #pragma unroll
             for (int i = 0; i < (CHUNKED ? BN / 2 : 1); ++i) sum[i] = 0.0f;
             for (int c = 0; c < nchunks; ++c, ++gc) {
                 const int ab = gc & 1;
                 const uint32_t aph = (uint32_t)(gc >> 1) & 1u;
+                if (c == (nchunks > 2 ? nchunks - 2 : 0) && grow < ep.M) {
+                    // the final store reads this thread's C0 (and X) row segment: start
+                    // bringing it into L2 a chunk or two ahead
+                    const int64_t off = grow * (int64_t)ep.N + n0 + colbase;
+#pragma unroll
+                    for (int k = 0; k < BN / 2; k += 32) {
+                        if (ep.beta != 0.0f) prefetch_l2(ep.C0 + off + k);
+                        if (ep.fuse) prefetch_l2(ep.X + off + k);
+                    }
+                }
                 if (!mbar_wait(accf_bar(ab), aph, abort_flag, err)) {
                     ok = false;
                     break;
@@ -551,7 +610,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
 #pragma unroll
                         for (int i = 0; i < 32; ++i) sum[g * 32 + i] += v[i];
                     } else {
-                        store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, v);
+                        store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, v, &sq);
                     }
                 }
                 tc_fence_before();
@@ -561,8 +620,14 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
             if constexpr (CHUNKED) {
                 if (ok) {
 #pragma unroll
-                    for (int g = 0; g < G; ++g) store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, sum + g * 32);
+                    for (int g = 0; g < G; ++g)
+                        store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, sum + g * 32, &sq);
                 }
+            }
+            if (ep.fuse && ok) {  // fixed butterfly over the warp's rows, one partial per warp
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+                if (lane == 0 && ep.frob_part) ep.frob_part[(int64_t)t * kEpiWarps + ew] = sq;
             }
         }
     }
@@ -588,6 +653,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     gemm_tc_grouped_kernel(const TcProblem* __restrict__ probs, int nprob, int total_tiles, int* err) {
     const ProblemTable src{probs, nprob, BN};
     gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(src, total_tiles, err);
+}
+
+// Frobenius norm of a fused chain: the per-warp partials summed in index order by one
+// block (fixed partition and tree), then the square root.
+__global__ void __launch_bounds__(256) frob_partials_kernel(const double* __restrict__ part, int64_t n,
+                                                            double* __restrict__ out) {
+    __shared__ double w[8];
+    double t = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) t += part[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int i = 0; i < 8; ++i) u += w[i];
+        *out = sqrt(u);
+    }
 }
 
 // ---- split kernels ------------------------------------------------------------------------------
@@ -831,24 +914,41 @@ Fp8Layout fp8_layout(int64_t M, int64_t N, int64_t K) {
     return L;
 }
 
-size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K) {
+// Planes (or FP8 arrays) first, then binary64 partials for a fused chain's norm
+// (8 per 128 x 128 tile).
+size_t tc_planes_bytes(int prec, int64_t M, int64_t N, int64_t K) {
     if (prec == GAO_GEMM_FP8) return fp8_layout(M, N, K).total;
     if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_BF16X6) return 0;
     const int64_t P = planes_of(prec);
     const int64_t Mp = ru(std::max<int64_t>(M, 1), BM), Np = ru(std::max<int64_t>(N, 1), 256),
                   Kp = ru(std::max<int64_t>(K, 1), BK);
-    return (size_t)(P * (Mp + Np) * Kp * 2);
+    return (size_t)ru(P * (Mp + Np) * Kp * 2, 1024);
+}
+
+size_t tc_partials_bytes(int64_t M, int64_t N) {
+    const int64_t tiles = (ru(std::max<int64_t>(M, 1), BM) / BM) * ((std::max<int64_t>(N, 1) + 127) / 128);
+    return (size_t)ru(tiles * kEpiWarps * (int64_t)sizeof(double), 1024);
+}
+
+size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K) {
+    if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_FP8) return 0;
+    return tc_planes_bytes(prec, M, N, K) + tc_partials_bytes(M, N);
 }
 
 cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
                            int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
-                           size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why) {
+                           size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why,
+                           const TcFuse* fuse) {
     ev.launches = 0;
     if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_FP8) {
         if (why) *why = "precision not available on the tensor-core path";
         return cudaErrorNotSupported;
     }
     if (M <= 0 || N <= 0) return cudaSuccess;
+    if (fuse && K <= 0) {
+        if (why) *why = "a fused chain needs K > 0";
+        return cudaErrorInvalidValue;
+    }
     if (K <= 0) {  // empty inner dimension: C = beta * C0, no tensor-core work
         if (ev.k0) cudaEventRecord(ev.k0, st);
         cudaError_t e = launch_gemm_simt(C, A, B, C0, M, N, 0, alpha, beta, 0, st);
@@ -861,9 +961,14 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         return cudaErrorInvalidValue;
     }
     if (!get_encode(why)) return cudaErrorNotSupported;
-    if (prec == GAO_GEMM_FP8)
+    if (prec == GAO_GEMM_FP8) {
+        if (fuse) {
+            if (why) *why = "chains are not fused on the FP8 path";
+            return cudaErrorInvalidValue;
+        }
         return launch_gemm_fp8(C, A, B, C0, M, N, K, alpha, beta, tc_group_of(tile_cfg), scratch, scratch_bytes, err,
                                st, ev, why);
+    }
     const int P = planes_of(prec);
     const int64_t Mp = ru(M, BM), Np = ru(N, 256), Kp = ru(K, BK);
     if (tc_scratch_bytes(prec, M, N, K) > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
@@ -907,6 +1012,15 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     if (!make_map(&tb, pb, Kp, (int64_t)P * Np, bn, false, why)) return cudaErrorInvalidValue;
     EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
                (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, nullptr, nullptr, 0, 0};
+    double* part = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, M, N, K));
+    if (fuse) {
+        ep.X = fuse->X;
+        ep.D = fuse->D;
+        ep.E = fuse->E;
+        ep.alpha2 = fuse->alpha2;
+        ep.frob_part = fuse->frob_out ? part : nullptr;
+        ep.fuse = 1;
+    }
     if (ev.k0) cudaEventRecord(ev.k0, st);
     cudaError_t e;
     const int mp = (int)Mp, np = (int)Np;
@@ -925,6 +1039,12 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     if (e != cudaSuccess) return e;
     ev.launches += 1;
     if (ev.k1) cudaEventRecord(ev.k1, st);
+    if (fuse && fuse->frob_out) {
+        const int64_t tiles = (Mp / BM) * ((N + bn - 1) / bn);
+        frob_partials_kernel<<<1, 256, 0, st>>>(part, tiles * kEpiWarps, fuse->frob_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ev.launches += 1;
+    }
     return cudaSuccess;
 }
 

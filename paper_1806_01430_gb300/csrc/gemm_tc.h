@@ -18,6 +18,25 @@ struct EpiArgs {
     const float* sa;   // FP8: scale of (row, K block), row-major [Mp][kbs]
     const float* sb;   // FP8: scale of (K block, column), row-major [kbs][sb_ld]
     int kbs, sb_ld;
+    // Fused loop chain (fuse != 0): D = C + alpha2 * X written row-major like C, E = D^T
+    // written with row stride M, and per-warp binary64 partials of sum(D^2) (8 per tile,
+    // at frob_part[tile * 8 + epilogue warp]).  D, E, X must not alias C, C0 or each other.
+    const float* X;
+    float* D;
+    float* E;
+    double* frob_part;
+    float alpha2;
+    int fuse;
+};
+
+// Loops of a chain GEMM -> AXPY (D = C + alpha2 X) -> TRANSPOSE (E = D^T) [-> FROBENIUS of
+// E] done inside the GEMM's epilogue.
+struct TcFuse {
+    const float* X;
+    float* D;
+    float* E;
+    double* frob_out;  // nullptr: no Frobenius loop in the chain
+    float alpha2;
 };
 
 // One problem of a grouped launch: its operand planes' TMA descriptors and epilogue.

@@ -22,6 +22,7 @@
 
 #include "ga_engine.h"
 #include "gao_internal.h"
+#include "gemm_tc.h"
 #include "prog_internal.h"
 
 namespace gao {
@@ -121,6 +122,7 @@ gao_status validate(const gao_loop* loops, int n_loops, const gao_buffer* bufs, 
         return fail(GAO_EINVAL, "unknown gemm_prec");
     if (opts && opts->transfer_mode != GAO_TRANSFER_RESIDENT && opts->transfer_mode != GAO_TRANSFER_PER_LOOP)
         return fail(GAO_EINVAL, "unknown transfer_mode");
+    if (opts && opts->fuse_chains != 0 && opts->fuse_chains != 1) return fail(GAO_EINVAL, "fuse_chains must be 0 or 1");
     for (int b = 0; b < n_bufs; ++b) {
         const gao_buffer& d = bufs[b];
         if (d.rows < 0 || d.cols < 0) return fail(GAO_EINVAL, "buffer " + std::to_string(b) + ": negative shape");
@@ -627,6 +629,69 @@ gao_status run_cpu_loop(RunCtx& R, int li) {
 }  // namespace gao
 
 namespace {
+
+// A chain the GEMM loop li can run as one pass when the gene puts it all on the GPU:
+// GEMM (C) -> AXPY (D = C + a X) -> TRANSPOSE (E = D^T) [-> FROBENIUS of E, later, with no
+// loop in between writing E].  The buffers must be distinct so that the epilogue's
+// writes cannot race with its reads.
+struct Chain {
+    int axpy = -1, transpose = -1, frob = -1;
+};
+
+bool find_chain(const gao_prog* p, int li, uint64_t mask, Chain* ch) {
+    if (!p->opts.fuse_chains || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT) return false;
+    const int prec = p->opts.gemm_prec;
+    if (prec != GAO_GEMM_BF16 && prec != GAO_GEMM_BF16X3 && prec != GAO_GEMM_BF16X6) return false;
+    const int n = (int)p->loops.size();
+    if (li + 2 >= n) return false;
+    for (int k = li; k <= li + 2; ++k)
+        if (!((mask >> k) & 1)) return false;
+    const gao_loop &G = p->loops[(size_t)li], &X = p->loops[(size_t)li + 1], &T = p->loops[(size_t)li + 2];
+    if (G.kind != GAO_LOOP_GEMM || X.kind != GAO_LOOP_AXPY || T.kind != GAO_LOOP_TRANSPOSE) return false;
+    const int Cb = G.outs[0], Xb = X.ins[1], Db = X.outs[0], Eb = T.outs[0];
+    if (X.ins[0] != Cb || T.ins[0] != Db) return false;
+    if (p->bufs[(size_t)G.ins[0]].d.cols <= 0) return false;  // K = 0
+    const int gin[3] = {G.ins[0], G.ins[1], G.ins[2]};
+    if (Xb == Cb || Db == Cb || Db == Xb || Eb == Cb || Eb == Xb || Eb == Db) return false;
+    for (int g : gin)
+        if (g >= 0 && (g == Db || g == Eb)) return false;
+    ch->axpy = li + 1;
+    ch->transpose = li + 2;
+    ch->frob = -1;
+    for (int j = li + 3; j < n; ++j) {
+        const gao_loop& L = p->loops[(size_t)j];
+        if (L.kind == GAO_LOOP_FROBENIUS && L.ins[0] == Eb && ((mask >> j) & 1)) {
+            ch->frob = j;
+            break;
+        }
+        bool writes_e = false;
+        for (int o : loop_outputs(L)) writes_e |= (o == Eb);
+        if (writes_e) break;
+    }
+    return true;
+}
+
+gao_status run_gpu_chain(RunCtx& R, int li, const Chain& ch) {
+    gao_prog* p = R.p;
+    const gao_loop &G = p->loops[(size_t)li], &X = p->loops[(size_t)ch.axpy], &T = p->loops[(size_t)ch.transpose];
+    auto dptr = [&](int b) { return (float*)p->bufs[(size_t)b].dev; };
+    const gao_buffer &A = p->bufs[(size_t)G.ins[0]].d, &B = p->bufs[(size_t)G.ins[1]].d;
+    const float* c0 = G.ins[2] >= 0 ? dptr(G.ins[2]) : dptr(G.outs[0]);
+    TcFuse fz{dptr(X.ins[1]), dptr(X.outs[0]), dptr(T.outs[0]),
+              ch.frob >= 0 ? (double*)p->bufs[(size_t)p->loops[(size_t)ch.frob].outs[0]].dev : nullptr,
+              (float)X.alpha};
+    TcEvents tev{R.events ? p->ev[(size_t)li * 6 + 4] : nullptr, R.events ? p->ev[(size_t)li * 6 + 5] : nullptr, 0};
+    std::string why;
+    cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, dptr(G.outs[0]), dptr(G.ins[0]), dptr(G.ins[1]), c0, A.rows,
+                                   B.cols, A.cols, (float)G.alpha, G.ins[2] >= 0 ? (float)G.beta : 0.0f,
+                                   p->opts.kchunk, p->opts.tile_cfg, p->arena + p->lay.tc_off, p->lay.tc_bytes,
+                                   (int*)(p->arena + p->lay.err_off), R.st, tev, &why, &fz);
+    if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "fused chain launch") : fail(GAO_EINVAL, why);
+    p->stats[(size_t)li].launches += tev.launches;
+    p->ev_used[(size_t)li] |= 4;
+    return GAO_OK;
+}
+
 double ev_ms(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.0;
@@ -663,12 +728,48 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene_mask, uint32_t flags, 
     char* d_err = p->arena + p->lay.err_off;
     if (uses_gpu) GAO_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), p->st));
     gao_status status = GAO_OK;
+    uint64_t fused = 0;  // loops already run inside a fused pass
     for (int li = 0; li < n && status == GAO_OK; ++li) {
         const gao_loop& L = p->loops[(size_t)li];
         const bool gpu = (gene_mask >> li) & 1;
         gao_loop_stat& S = p->stats[(size_t)li];
         S.placement = gpu ? 1 : 0;
+        if ((fused >> li) & 1) {
+            S.placement = 2;
+            continue;
+        }
         cudaEvent_t* ev = &p->ev[(size_t)li * 6];
+        Chain chain;
+        if (gpu && L.kind == GAO_LOOP_GEMM && find_chain(p, li, gene_mask, &chain)) {
+            // inputs of the whole chain: the GEMM's and the AXPY's second operand
+            std::vector<int> cin = loop_inputs(L);
+            cin.push_back(p->loops[(size_t)chain.axpy].ins[1]);
+            bool copies = false;
+            for (int b : cin) copies |= !p->bufs[(size_t)b].vd;
+            if (copies) GAO_CUDA_TRY(cudaEventRecord(ev[0], p->st));
+            for (int b : cin)
+                if ((status = make_valid(R, b, true, S)) != GAO_OK) break;
+            if (status != GAO_OK) break;
+            if (copies) {
+                GAO_CUDA_TRY(cudaEventRecord(ev[1], p->st));
+                p->ev_used[(size_t)li] |= 1;
+            }
+            GAO_CUDA_TRY(cudaEventRecord(ev[2], p->st));
+            if ((status = run_gpu_chain(R, li, chain)) != GAO_OK) break;
+            GAO_CUDA_TRY(cudaEventRecord(ev[3], p->st));
+            p->ev_used[(size_t)li] |= 2;
+            for (int j : {li, chain.axpy, chain.transpose, chain.frob}) {
+                if (j < 0) continue;
+                for (int b : loop_outputs(p->loops[(size_t)j])) {
+                    p->bufs[(size_t)b].vh = false;
+                    p->bufs[(size_t)b].vd = true;
+                }
+                if (j != li) fused |= 1ULL << j;
+            }
+            if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
+            if (R.timed_out) break;
+            continue;
+        }
         const std::vector<int> ins = loop_inputs(L);
         const bool per_loop = p->opts.transfer_mode == GAO_TRANSFER_PER_LOOP;
         if (gpu && per_loop)  // directive offload without a data region: inputs always copied in

@@ -1,0 +1,98 @@
+"""Fused loop chain (GEMM -> scale-add -> transpose [-> Frobenius] in one GEMM epilogue):
+bit-identical C, D, E and row sums to the unfused run, the norm within the reduction's
+rounding bound, the oracle's tolerance, and fusion only when the gene puts the whole
+chain on the GPU."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 5e-3, 2: 2e-5, 3: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def gao():
+    from paper_1806_01430_gb300 import _build
+    _build.build()
+    import paper_1806_01430_gb300 as g
+    return g
+
+
+def outputs(gao, p, prog):
+    out = {b.name: gao.prog_output(p, i) for i, b in enumerate(prog.buffers) if b.role == W.OUTPUT}
+    for nm in ("f", "s"):
+        if nm in out:
+            out[nm] = float(out[nm][0, 0])
+    return out
+
+
+@pytest.mark.parametrize("prec", [3, 2, 1])
+@pytest.mark.parametrize("n", [256, 129, 300, 1000])
+def test_fused_six_loop_matches_unfused(gao, prec, n):
+    prog = W.six_loop(n, 600 + n, outputs=("C", "D", "E", "r", "f"))
+    ref = oracle.run_program(prog)
+    res = {}
+    for fuse in (False, True):
+        p = gao.prog_from_workload(prog, gemm_prec=prec, fuse_chains=fuse)
+        gao.prog_run(p, 0b111111)
+        res[fuse] = (outputs(gao, p, prog), gao.prog_stats(p))
+        gao.prog_destroy(p)
+    (a, _), (b, st) = res[False], res[True]
+    for nm in ("C", "D", "E", "r"):
+        assert np.array_equal(a[nm], b[nm]), nm
+    assert abs(a["f"] - b["f"]) <= 2e-7 * a["f"]
+    assert [s["placement"] for s in st] == [1, 1, 2, 2, 1, 2]
+    assert st[1]["launches"] == 4  # split A, split B, fused GEMM, norm partials
+    for nm in ("C", "D", "E", "r"):
+        assert oracle.rel_err(b[nm], ref[nm]) <= TOL[prec]
+    assert abs(b["f"] - ref["f"]) <= TOL[prec] * ref["f"]
+
+
+def test_fused_chain_only_when_all_on_gpu(gao):
+    prog = W.six_loop(200, 71, outputs=("C", "E", "r", "f"))
+    ref = oracle.run_program(prog)
+    p = gao.prog_from_workload(prog, gemm_prec=3, fuse_chains=True)
+    for mask, fused in ((0b111111, True), (0b111011, False), (0b110111, False), (0b011111, True),
+                        (0b101111, True), (0b000111, False)):
+        gao.prog_run(p, mask)
+        st = gao.prog_stats(p)
+        assert (st[2]["placement"] == 2) == fused, mask
+        if fused:
+            assert st[5]["placement"] == (2 if (mask >> 5) & 1 else 0)
+        out = outputs(gao, p, prog)
+        for nm in ("C", "E", "r"):
+            assert oracle.rel_err(out[nm], ref[nm]) <= 1e-6
+        assert abs(out["f"] - ref["f"]) <= 1e-6 * ref["f"]
+    gao.prog_destroy(p)
+
+
+def test_fused_twelve_loop(gao):
+    prog = W.twelve_loop(200, 72, W.SEED_CONFIG4, outputs=("C", "D", "E", "r", "f", "P", "q", "s"))
+    ref = oracle.run_program(prog)
+    p = gao.prog_from_workload(prog, gemm_prec=3, fuse_chains=True)
+    gao.prog_run(p, (1 << 12) - 1)
+    st = gao.prog_stats(p)
+    assert [s["placement"] for s in st[:6]] == [1, 1, 2, 2, 1, 2]
+    out = outputs(gao, p, prog)
+    for nm in ("C", "D", "E", "P", "r", "q"):
+        assert oracle.rel_err(out[nm], ref[nm]) <= 2e-6, nm
+    for nm in ("f", "s"):
+        assert abs(out[nm] - ref[nm]) <= 2e-6 * abs(ref[nm])
+    gao.prog_destroy(p)
+
+
+def test_fused_full_size_n4096(gao):
+    n, seed = 4096, W.SEED_CONFIG1
+    prog = W.six_loop(n, seed, outputs=("C", "D", "E", "r", "f"))
+    res = {}
+    for fuse in (False, True):
+        p = gao.prog_from_workload(prog, gemm_prec=3, fuse_chains=fuse)
+        gao.prog_run(p, 0b111111)
+        res[fuse] = outputs(gao, p, prog)
+        gao.prog_destroy(p)
+    for nm in ("C", "D", "E", "r"):
+        assert np.array_equal(res[False][nm], res[True][nm]), nm
+    assert abs(res[False]["f"] - res[True]["f"]) <= 2e-7 * res[False]["f"]
