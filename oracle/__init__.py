@@ -76,6 +76,8 @@ def lib():
             L.orc_gemm_init_entries.argtypes = [_u64, _i64, _i64, _i64, ctypes.c_int, _i64, _i64, _i64, _d, _d,
                                                 _i64, _PI, _PI, _P]
             L.orc_gemm_column.argtypes = [_i64, _i64, _i64, _d, _P, _P, _d, _P, _i64, _P]
+            L.orc_stencil3.restype = ctypes.c_int
+            L.orc_stencil3.argtypes = [_i64, _i64, _P, ctypes.c_int, _P]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -180,6 +182,18 @@ def total(X) -> float:
     return float(lib().orc_sum(X.size, X))
 
 
+STENCIL_PRESETS = {"blur": 0, "laplacian": 1, "sobel_x": 2, "sobel_y": 3}
+
+
+def stencil3(X, preset: int) -> np.ndarray:
+    X = _c(X)
+    r, c = X.shape
+    out = np.empty_like(X)
+    if lib().orc_stencil3(r, c, X, int(preset), out) != 0:
+        raise ValueError("unknown stencil preset")
+    return out
+
+
 def gemm_init_entries(seed: int, bufs, rowscale_a: bool, M: int, N: int, K: int, alpha: float, beta: float,
                       ii, jj) -> np.ndarray:
     """C[i,j] of C = alpha*A@B + beta*C0 for freshly initialised A, B, C0 (buffer ids
@@ -213,7 +227,7 @@ def set_num_threads(n: int) -> None:
 
 # loop kinds (gao_loop_kind); kept as literals so that the oracle does not depend
 # on the product package.
-_INIT, _GEMM, _AXPY, _TRANSPOSE, _ROWSUM, _FROB, _RELU, _SQUARE, _COLMAX, _SUM = range(10)
+_INIT, _GEMM, _AXPY, _TRANSPOSE, _ROWSUM, _FROB, _RELU, _SQUARE, _COLMAX, _SUM, _STENCIL3 = range(11)
 
 
 def run_program(prog, inputs: dict | None = None) -> dict:
@@ -250,6 +264,8 @@ def run_program(prog, inputs: dict | None = None) -> dict:
             vals[o] = colmax(ins[0])
         elif lp.kind == _SUM:
             vals[o] = total(ins[0])
+        elif lp.kind == _STENCIL3:
+            vals[o] = stencil3(ins[0], lp.flags)
         else:
             raise ValueError(f"unknown loop kind {lp.kind}")
     return {prog.buffers[i].name: v for i, v in vals.items()}

@@ -22,6 +22,8 @@
  *   SQUARE     H = G (.) G
  *   COLMAX     q_j = max_i P_ij
  *   SUM        s = sum_ij P_ij
+ *   STENCIL3   Y_ij = sum_{a,b in -1..1} w_ab X_{i+a, j+b}, X = 0 outside the image
+ *              (image-analysis loops, the paper's motivating IoT camera workload, Sec. 1)
  *
  * Every loop is the textbook double/triple loop.  The GEMM runs its loops in
  * i-k-j order so that the row of B is read contiguously; for every output
@@ -195,6 +197,35 @@ double orc_sum(int64_t n, const double *in) {
     double s = 0.0;
     for (int64_t i = 0; i < n; ++i) s += in[i];
     return s;
+}
+
+/* Weights of the 3x3 stencil presets, row-major over (a, b) = (-1..1, -1..1):
+ * 0 binomial blur (1 2 1; 2 4 2; 1 2 1) / 16, 1 Laplacian (0 1 0; 1 -4 1; 0 1 0),
+ * 2 Sobel x (-1 0 1; -2 0 2; -1 0 1), 3 Sobel y (-1 -2 -1; 0 0 0; 1 2 1). */
+static const double ORC_STENCIL_W[4][9] = {
+    {1.0 / 16, 2.0 / 16, 1.0 / 16, 2.0 / 16, 4.0 / 16, 2.0 / 16, 1.0 / 16, 2.0 / 16, 1.0 / 16},
+    {0, 1, 0, 1, -4, 1, 0, 1, 0},
+    {-1, 0, 1, -2, 0, 2, -1, 0, 1},
+    {-1, -2, -1, 0, 0, 0, 1, 2, 1},
+};
+
+/* STENCIL3 loop: out[i][j] = sum of w[a][b] * in[i+a][j+b] over a, b in {-1, 0, 1},
+ * terms outside the image taken as 0. */
+int orc_stencil3(int64_t rows, int64_t cols, const double *in, int preset, double *out) {
+    if (preset < 0 || preset > 3) return -1;
+    const double *w = ORC_STENCIL_W[preset];
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < rows; ++i)
+        for (int64_t j = 0; j < cols; ++j) {
+            double s = 0.0;
+            for (int a = -1; a <= 1; ++a)
+                for (int b = -1; b <= 1; ++b) {
+                    const int64_t y = i + a, x = j + b;
+                    if (y >= 0 && y < rows && x >= 0 && x < cols) s += w[(a + 1) * 3 + (b + 1)] * in[y * cols + x];
+                }
+            out[i * cols + j] = s;
+        }
+    return 0;
 }
 
 /* ---- sampled entries at full size, without materialising the matrices ---- */

@@ -259,3 +259,52 @@ def test_host_input_program_matches_six_loop():
            "C0": oracle.init_matrix(seed, 2, n, n)}
     out = oracle.run_program(hp, ins)
     assert np.array_equal(out["C"], six["C"]) and np.array_equal(out["r"], six["r"]) and out["f"] == six["f"]
+
+
+# ---- stencil loops (second workload) ------------------------------------------------------
+
+def test_stencil_closed_forms():
+    r, c = 11, 13
+    const = np.full((r, c), 0.75)
+    B = oracle.stencil3(const, 0)
+    assert np.array_equal(B[1:-1, 1:-1], const[1:-1, 1:-1])  # weights sum to 1
+    assert B[0, 0] == 0.75 * 9 / 16 and B[0, 5] == 0.75 * 12 / 16  # corner, edge with zero padding
+    yy, xx = np.mgrid[0:r, 0:c].astype(np.float64)
+    ramp = 3.0 * xx - 2.0 * yy + 1.0
+    assert np.all(oracle.stencil3(ramp, 1)[1:-1, 1:-1] == 0.0)  # Laplacian of a linear function
+    assert np.all(oracle.stencil3(ramp, 2)[1:-1, 1:-1] == 8.0 * 3.0)  # Sobel x: 2 * (1+2+1) * slope
+    assert np.all(oracle.stencil3(ramp, 3)[1:-1, 1:-1] == 8.0 * -2.0)
+    with pytest.raises(ValueError):
+        oracle.stencil3(const, 7)
+
+
+def test_stencil_exact_rational_and_adjoint():
+    X = oracle.init_matrix(21, 0, 7, 9)
+    Wt = [[Fraction(1, 16), Fraction(2, 16), Fraction(1, 16)], [Fraction(2, 16), Fraction(4, 16), Fraction(2, 16)],
+         [Fraction(1, 16), Fraction(2, 16), Fraction(1, 16)]]
+    F = _frac_matrix(X)
+    got = oracle.stencil3(X, 0)
+    for i in range(7):
+        for j in range(9):
+            ex = sum(Wt[a + 1][b + 1] * F[i + a][j + b] for a in (-1, 0, 1) for b in (-1, 0, 1)
+                     if 0 <= i + a < 7 and 0 <= j + b < 9)
+            assert abs(Fraction(float(got[i, j])) - ex) <= Fraction(10 * U) * 2
+    # the symmetric presets are self-adjoint: <S x, y> = <x, S y>; Sobel-x is anti-symmetric
+    Y = oracle.init_matrix(21, 1, 7, 9)
+    for preset, sign in ((0, 1.0), (1, 1.0), (2, -1.0), (3, -1.0)):
+        lhs = float((oracle.stencil3(X, preset) * Y).sum())
+        rhs = sign * float((X * oracle.stencil3(Y, preset)).sum())
+        assert abs(lhs - rhs) < 1e-12
+
+
+def test_image_program_exact_small():
+    prog = W.image_program(6, 7, seed=9, outputs=("B", "gx", "M2", "e", "q"))
+    out = oracle.run_program(prog)
+    X = oracle.init_matrix(9, 0, 6, 7)
+    B = oracle.stencil3(X, 0)
+    gx, gy = oracle.stencil3(B, 2), oracle.stencil3(B, 3)
+    M2 = gx * gx + gy * gy
+    assert np.array_equal(out["B"], B) and np.array_equal(out["gx"], gx)
+    assert np.allclose(out["M2"], M2, rtol=1e-15, atol=0)
+    assert abs(out["e"] - float(M2.sum())) <= 1e-13 * float(M2.sum())
+    assert np.array_equal(out["q"].ravel(), out["M2"].max(axis=0))

@@ -20,8 +20,11 @@ from typing import List, Optional
 import numpy as np
 
 # gao_loop_kind values (include/gao.h)
-INIT, GEMM, AXPY, TRANSPOSE, ROWSUM, FROBENIUS, RELU, SQUARE, COLMAX, SUM = range(10)
-KIND_NAMES = ["init", "gemm", "axpy", "transpose", "rowsum", "frobenius", "relu", "square", "colmax", "sum"]
+INIT, GEMM, AXPY, TRANSPOSE, ROWSUM, FROBENIUS, RELU, SQUARE, COLMAX, SUM, STENCIL3 = range(11)
+KIND_NAMES = ["init", "gemm", "axpy", "transpose", "rowsum", "frobenius", "relu", "square", "colmax", "sum",
+              "stencil3"]
+# STENCIL3 presets (loop flags)
+BLUR, LAPLACIAN, SOBEL_X, SOBEL_Y = range(4)
 # gao_dtype
 F32, F64 = 0, 1
 # gao_buf_role
@@ -151,6 +154,35 @@ def twelve_loop(m: int, k: int, seed: int, alpha: float = 1.5, beta: float = 0.5
     return Program(f"twelve_loop_m{m}_k{k}", bufs, loops, seed, {"m": m, "k": k, "alpha": alpha, "beta": beta})
 
 
+def image_program(h: int, w: int, seed: int, outputs=("M2", "e", "q"), host_image: bool = False) -> Program:
+    """Edge-detection program on an h x w image (the paper's motivating camera-analysis
+    workload, Sec. 1): L0 init X; L1 B = binomial blur of X; L2 gx = Sobel-x of B;
+    L3 gy = Sobel-y of B; L4 sx = gx(.)gx; L5 sy = gy(.)gy; L6 M2 = sx + sy (squared
+    gradient magnitude); L7 e = sum of M2 (edge energy); L8 q = column maxima of M2.
+    With ``host_image`` the image X is an INPUT buffer supplied from host memory (a
+    camera frame) and the INIT loop is dropped (eight loops)."""
+    names = ["X", "B", "gx", "gy", "sx", "sy", "M2", "e", "q"]
+    shapes = {"e": (1, 1), "q": (1, w)}
+    bufs = []
+    for nm in names:
+        rows, cols = shapes.get(nm, (h, w))
+        role = INPUT if (nm == "X" and host_image) else (OUTPUT if nm in outputs else TEMP)
+        bufs.append(Buffer(nm, rows, cols, F64 if nm == "e" else F32, role))
+    X, B_, gx, gy, sx, sy, M2, e, q = range(9)
+    loops = [] if host_image else [Loop(INIT, [], [X])]
+    loops += [
+        Loop(STENCIL3, [X], [B_], flags=BLUR),
+        Loop(STENCIL3, [B_], [gx], flags=SOBEL_X),
+        Loop(STENCIL3, [B_], [gy], flags=SOBEL_Y),
+        Loop(SQUARE, [gx], [sx]),
+        Loop(SQUARE, [gy], [sy]),
+        Loop(AXPY, [sx, sy], [M2], alpha=1.0),
+        Loop(SUM, [M2], [e]),
+        Loop(COLMAX, [M2], [q]),
+    ]
+    return Program(f"image_{h}x{w}", bufs, loops, seed, {"h": h, "w": w})
+
+
 # ---- seeds of the benchmark configurations ----------------------------------
 SEED_CONFIG0 = 1000      # n = 256, all-GPU gene
 SEED_CONFIG1 = 1001      # n = 4096, all 64 genes
@@ -158,6 +190,8 @@ SEED_CONFIG2 = 1002      # n = 8192 precision, U[-1,1)
 SEED_CONFIG2_ROWS = 1003  # n = 8192 precision, rows of A scaled by 2^e
 SEED_CONFIG3_BASE = 2000  # batch programs use 2000 + p
 SEED_CONFIG4 = 1005      # rectangular 16384 x 16384 x 4096, twelve loops
+SEED_IMAGE = 1006        # edge-detection image program
+SEED_IMAGE = 1006        # edge-detection image program
 
 # GA parameters of the paper's evaluation (Sec. 5.1.2)
 PAPER_GA = dict(pop=12, generations=12, pc=0.9, pm=0.05, elite=1, mutation=0)
