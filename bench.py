@@ -429,6 +429,137 @@ def our_arm(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def image_arm(args, world, rank, local):
+    """Edge-detection image program (the paper's motivating camera workload, Sec. 1):
+    nine loops (init, blur, Sobel x/y, squares, magnitude, energy, column maxima) on an
+    h x w binary32 image, all on the GPU; metric: image pixels processed per second."""
+    import torch
+
+    import paper_1806_01430_gb300 as gao
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    h, w = args.h, args.w
+    prog = W.image_program(h, w, W.SEED_IMAGE + rank, outputs=("e", "q"))
+    p = gao.prog_from_workload(prog, stream=stream)
+    mask = (1 << prog.n_loops) - 1
+    loop_ms = [0.0] * prog.n_loops
+    launches = 0
+    with Clocks(local) as clk:
+        time.sleep(0.3)
+        for _ in range(args.warmup):
+            gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        t0 = clk.mark()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
+            st = gao.prog_stats(p)
+            launches += sum(s_["launches"] for s_ in st)
+            for i, s_ in enumerate(st):
+                loop_ms[i] += s_["device_ms"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t1 = clk.mark()
+        time.sleep(0.25)
+    barrier(world)
+    ms = allmax(world, ev0.elapsed_time(ev1) / args.steps)
+    pixels = float(h * w)
+    value = allsum(world, pixels) / (ms / 1e3) / 1e9
+    clocks = clk.summary(t0, t1)
+    hbm = peaks().get("hbm_gbs", FALLBACK["hbm_gbs"])
+    loop_gbs, per_loop = {}, {}
+    for i, (lp, v) in enumerate(zip(prog.loops, loop_ms)):
+        key = f"L{i}_{W.KIND_NAMES[lp.kind]}"
+        per_loop[key] = round(v / args.steps, 4)
+        if v > 0:
+            g = algorithmic_bytes(prog, lp) / (v / args.steps / 1e3) / 1e9
+            loop_gbs[key] = {"gbs": round(g, 1), "hbm_frac": round(g / hbm, 3)}
+    # dominant kernel: the three stencil loops, 8 algorithmic bytes per pixel each
+    st_idx = [i for i, lp in enumerate(prog.loops) if lp.kind == W.STENCIL3]
+    st_ms = sum(loop_ms[i] for i in st_idx) / (len(st_idx) * args.steps)
+    achieved = 8.0 * pixels / (st_ms / 1e3) / 1e9
+    gao.prog_destroy(p)
+
+    # end to end: the image arrives from pinned host memory every step (a camera
+    # frame, INPUT buffer), the energy and column maxima are read back
+    e2e = None
+    if args.e2e:
+        hp = W.image_program(h, w, W.SEED_IMAGE + rank, outputs=("e", "q"), host_image=True)
+        q = gao.prog_from_workload(hp, stream=stream)
+        import oracle  # input generation only (seeded counter hash); not on the timed path
+        gao.prog_set_input(q, hp.index("X"), oracle.init_matrix(hp.seed, 0, h, w).astype(np.float32))
+        m8 = (1 << hp.n_loops) - 1
+        for _ in range(2):
+            gao.prog_run(q, m8)
+        k = max(3, min(args.steps // 2, 200))
+        walls = [gao.prog_run(q, m8) for _ in range(k)]
+        st = gao.prog_stats(q)
+        ew = statistics.median(walls)
+        e2e = {"value": allsum(world, pixels) / allmax(world, ew) / 1e9, "unit": "Gpixel/s",
+               "h2d_bytes_per_step": int(sum(s_["h2d_bytes"] for s_ in st)),
+               "d2h_bytes_per_step": int(sum(s_["d2h_bytes"] for s_ in st)), "ms_per_step": ew * 1e3}
+        gao.prog_destroy(q)
+
+    # the offload search on a 2048 x 2048 frame: all 512 genes measured (CPU loops
+    # included), then the paper's GA (M = T = 12, Pc 0.9, Pm 0.05) on the same program
+    search = None
+    if args.search and rank == 0:
+        sh = sw = 2048
+        sp = W.image_program(sh, sw, W.SEED_IMAGE, outputs=("e", "q"))
+        q = gao.prog_from_workload(sp, stream=stream)
+        gao.prog_run(q, (1 << sp.n_loops) - 1)
+        t0s = time.perf_counter()
+        fit, secs, hits = gao.ga_evaluate([q], list(range(1 << sp.n_loops)))
+        t_search = time.perf_counter() - t0s
+        ga = gao.ga_run([q], **W.PAPER_GA, seed=11)
+        order = np.argsort(secs)
+        nb = sp.n_loops
+        search = {"workload": f"image_{sh}x{sw}_all_{1 << nb}_genes", "evals": 1 << nb, "wall_s": t_search,
+                  "all_cpu_s": float(secs[0]), "all_gpu_s": float(secs[-1]),
+                  "best_gene": format(int(order[0]), f"0{nb}b"), "best_s": float(secs[order[0]]),
+                  "speedup_best_vs_all_cpu": float(secs[0] / secs[order[0]]),
+                  "top5": [[format(int(m), f"0{nb}b"), float(secs[m])] for m in order[:5]],
+                  "paper_ga": {"best_gene": format(ga.best_mask, f"0{nb}b"), "best_s": ga.best_s,
+                               "rank_in_exhaustive": int(np.where(order == ga.best_mask)[0][0]),
+                               "measured": ga.evaluations, "served": ga.cache_hits}}
+        gao.prog_destroy(q)
+
+    if rank != 0:
+        return
+    cpu = None
+    if args.cpu_baseline:
+        import oracle
+        rows = 16
+        while True:
+            sub = W.image_program(rows, w, W.SEED_IMAGE, outputs=("e", "q"))
+            t0c = time.perf_counter()
+            oracle.run_program(sub)
+            dt = time.perf_counter() - t0c
+            if dt >= args.ref_target_s or rows >= h:
+                break
+            rows = min(h, rows * max(2, int(args.ref_target_s / max(dt, 1e-3) * 0.7)))
+        cpu = {"value": rows * w / dt / 1e9, "unit": "Gpixel/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"a {rows} x {w} image through the nine loops in FP64 ({dt:.1f} s)"}
+    line = {"metric": "image_program_gpixels", "value": value, "unit": "Gpixel/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded counter hash, U[-1,1))",
+            "config": {"workload": f"image_{h}x{w}_all_gpu", "h": h, "w": w,
+                       "gene": format(mask, f"0{prog.n_loops}b"),
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "working set larger than the 129 MB L2 (no flush)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": profile_traffic("kernels_ew.cu", f"stencil3_image_{h}x{w}.md"),
+                         "kernel": "stencil3 (8 algorithmic bytes per pixel)",
+                         "peak_source": f"{peaks()['source']} hbm_gbs"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "loop_ms": per_loop, "loop_gbs": loop_gbs, "ga_search": search}
+    print(json.dumps(line), flush=True)
+
+
 def batch_arm(args, world, rank, local):
     """Batched-population workload: a suite of programs of uneven sizes (n log-uniform
     in [128, 2048]), every gene evaluated over the whole suite with one graph launch
@@ -495,7 +626,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--workload", default="six_loop", choices=["six_loop", "twelve_loop", "batch"])
+    ap.add_argument("--workload", default="six_loop", choices=["six_loop", "twelve_loop", "batch", "image"])
+    ap.add_argument("--h", type=int, default=8192)
+    ap.add_argument("--w", type=int, default=8192)
     ap.add_argument("--programs", type=int, default=64)
     ap.add_argument("--pop", type=int, default=20)
     ap.add_argument("--generations", type=int, default=20)
@@ -518,6 +651,8 @@ def main():
         reference_arm(args, world, rank)
     elif args.workload == "batch":
         batch_arm(args, world, rank, local)
+    elif args.workload == "image":
+        image_arm(args, world, rank, local)
     else:
         our_arm(args, world, rank, local)
     if world > 1:

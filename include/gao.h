@@ -61,7 +61,14 @@ typedef enum gao_loop_kind {
     GAO_LOOP_RELU = 6,      /* outs[0] = max(ins[0], 0)                                          */
     GAO_LOOP_SQUARE = 7,    /* outs[0] = ins[0] (.) ins[0]                                       */
     GAO_LOOP_COLMAX = 8,    /* outs[0][j] = max_i ins[0][i,j]   (1 x cols, binary32)             */
-    GAO_LOOP_SUM = 9        /* outs[0] = sum ins[0]             (1 x 1, binary64)                */
+    GAO_LOOP_SUM = 9,       /* outs[0] = sum ins[0]             (1 x 1, binary64)                */
+    GAO_LOOP_STENCIL3 = 10  /* outs[0][i,j] = sum_{a,b in -1..1} w_ab ins[0][i+a,j+b], ins[0] taken as 0
+                               outside the image; the nine terms are added in row-major (a, b)
+                               order with fused multiply-adds, zero terms included.  flags picks
+                               w: 0 binomial blur (1 2 1; 2 4 2; 1 2 1)/16, 1 Laplacian
+                               (0 1 0; 1 -4 1; 0 1 0), 2 Sobel x (-1 0 1; -2 0 2; -1 0 1),
+                               3 Sobel y (-1 -2 -1; 0 0 0; 1 2 1).  The image-analysis loops
+                               of the paper's motivating camera workload (Sec. 1).           */
 } gao_loop_kind;
 
 typedef enum gao_dtype { GAO_F32 = 0, GAO_F64 = 1 } gao_dtype;

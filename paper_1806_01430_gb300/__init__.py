@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(_HERE, "libgao.so")
 # enums (include/gao.h)
 GAO_OK, GAO_EINVAL, GAO_ENOMEM, GAO_ECUDA, GAO_ETIMEOUT, GAO_EDEVICE, GAO_ENODEV, GAO_ECPU = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EDEVICE", "ENODEV", "ECPU"]
-INIT, GEMM, AXPY, TRANSPOSE, ROWSUM, FROBENIUS, RELU, SQUARE, COLMAX, SUM = range(10)
+INIT, GEMM, AXPY, TRANSPOSE, ROWSUM, FROBENIUS, RELU, SQUARE, COLMAX, SUM, STENCIL3 = range(11)
+STENCIL_BLUR, STENCIL_LAPLACIAN, STENCIL_SOBEL_X, STENCIL_SOBEL_Y = range(4)  # STENCIL3 loop flags
 F32, F64 = 0, 1
 TEMP, INPUT, OUTPUT = 0, 1, 2
 FP32_SIMT, BF16, BF16X3, BF16X6, FP8 = range(5)

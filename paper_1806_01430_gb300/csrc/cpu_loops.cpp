@@ -2,7 +2,8 @@
 //
 // These are the loops as a CPU program would run them when the gene leaves them on
 // the host.  Loops whose GPU version is exact (INIT, AXPY, TRANSPOSE, RELU, SQUARE,
-// COLMAX) produce bit-identical results here; the others agree within rounding.
+// COLMAX) or fixes its rounding order (STENCIL3) produce bit-identical results here;
+// the others agree within rounding.
 // Every loop polls a deadline between blocks of work so that a run over its time
 // budget stops early (the run then reports a timeout).
 #include <math.h>
@@ -220,6 +221,52 @@ void cpu_colmax(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx&
         float v;
         memcpy(&v, &bits, 4);
         out[j] = rows > 0 ? v : -INFINITY;
+    }
+}
+
+// 3x3 stencil with zero padding.  Each output adds its nine terms in row-major (a, b)
+// order with fmaf, out-of-image and zero-weight terms included, exactly as the GPU
+// kernel does, so both give the same bits.
+void cpu_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, CpuCtx& c) {
+    float w[9];
+    if (!stencil_weights(preset, w)) return;
+    std::atomic<bool> stop{false};
+#pragma omp parallel num_threads(nthreads(c))
+    {
+        std::vector<float> pad[3];
+        for (auto& v : pad) v.assign((size_t)cols + 2, 0.0f);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < rows; ++i) {
+            if (stop.load(std::memory_order_relaxed)) continue;
+            if ((i & 63) == 0 && expired(c)) {
+                stop = true;
+                continue;
+            }
+            // rows i-1, i, i+1 with one zero column on each side
+            for (int a = 0; a < 3; ++a) {
+                const int64_t y = i + a - 1;
+                float* d = pad[a].data();
+                if (y >= 0 && y < rows)
+                    memcpy(d + 1, in + y * cols, sizeof(float) * (size_t)cols);
+                else
+                    memset(d + 1, 0, sizeof(float) * (size_t)cols);
+            }
+            const float *u = pad[0].data(), *m = pad[1].data(), *d = pad[2].data();
+            float* o = out + i * cols;
+            for (int64_t j = 0; j < cols; ++j) {
+                float s = 0.0f;
+                s = fmaf(w[0], u[j], s);
+                s = fmaf(w[1], u[j + 1], s);
+                s = fmaf(w[2], u[j + 2], s);
+                s = fmaf(w[3], m[j], s);
+                s = fmaf(w[4], m[j + 1], s);
+                s = fmaf(w[5], m[j + 2], s);
+                s = fmaf(w[6], d[j], s);
+                s = fmaf(w[7], d[j + 1], s);
+                s = fmaf(w[8], d[j + 2], s);
+                o[j] = s;
+            }
+        }
     }
 }
 

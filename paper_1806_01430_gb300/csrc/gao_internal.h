@@ -92,6 +92,21 @@ cudaError_t launch_sum(double* out, const float* in, int64_t n, ReduceScratch rs
 cudaError_t launch_relu(float* out, const float* in, int64_t n, cudaStream_t st);
 cudaError_t launch_square(float* out, const float* in, int64_t n, cudaStream_t st);
 cudaError_t launch_colmax(float* out, const float* in, int64_t rows, int64_t cols, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st);
+
+// Weights of the 3x3 stencil presets of GAO_LOOP_STENCIL3, row-major over (a, b).
+// Every weight is a small integer or a power-of-two fraction, exact in binary32.
+inline bool stencil_weights(int preset, float w[9]) {
+    static const float k[4][9] = {
+        {0.0625f, 0.125f, 0.0625f, 0.125f, 0.25f, 0.125f, 0.0625f, 0.125f, 0.0625f},
+        {0.0f, 1.0f, 0.0f, 1.0f, -4.0f, 1.0f, 0.0f, 1.0f, 0.0f},
+        {-1.0f, 0.0f, 1.0f, -2.0f, 0.0f, 2.0f, -1.0f, 0.0f, 1.0f},
+        {-1.0f, -2.0f, -1.0f, 0.0f, 0.0f, 0.0f, 1.0f, 2.0f, 1.0f},
+    };
+    if (preset < 0 || preset > 3) return false;
+    for (int t = 0; t < 9; ++t) w[t] = k[preset][t];
+    return true;
+}
 cudaError_t launch_wait_selftest(int* flag, int* err, double limit_s, cudaStream_t st);
 
 // FP32 SIMT GEMM: C = alpha*A@B + beta*C0 (C may alias C0).  kchunk: K elements per
@@ -130,5 +145,6 @@ double cpu_sum(const float* in, int64_t n, CpuCtx& c);
 void cpu_relu(float* out, const float* in, int64_t n, CpuCtx& c);
 void cpu_square(float* out, const float* in, int64_t n, CpuCtx& c);
 void cpu_colmax(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx& c);
+void cpu_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, CpuCtx& c);
 
 }  // namespace gao

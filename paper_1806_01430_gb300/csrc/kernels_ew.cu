@@ -1,5 +1,5 @@
 // Memory-bound loops of the program on the GPU: INIT, AXPY (scale-add), TRANSPOSE,
-// ROWSUM, FROBENIUS, SUM, RELU, SQUARE, COLMAX.
+// ROWSUM, FROBENIUS, SUM, RELU, SQUARE, COLMAX, STENCIL3.
 //
 // All kernels read and write row-major binary32 with 128-bit accesses where the
 // shape allows (element count or row length a multiple of 4), grid-stride over a
@@ -334,6 +334,108 @@ __global__ void colmax_decode_kernel(float* __restrict__ out, const uint32_t* __
         out[c] = rows > 0 ? __uint_as_float(fmax_unkey(keys[c])) : -INFINITY;
 }
 
+// ---- STENCIL3 --------------------------------------------------------------------------
+
+struct StencilW {
+    float w[9];
+};
+
+constexpr int kStencilThreads = 128;  // one block: 4 warps x 32 lanes x 4 columns = 512 columns
+
+// One image row as a thread sees it: its four columns c0..c0+3 (one 128-bit load when
+// rows are 16-byte aligned) and the two edge columns c0-1 and c0+4, which lanes
+// exchange with shuffles; only the first and last lane of a warp read them.
+template <bool VEC>
+struct StencilRow {
+    float4 m;
+    float l, r;
+    __device__ __forceinline__ void load(const float* __restrict__ in, int64_t y, int64_t rows, int64_t cols, int64_t c0,
+                                         int lane) {
+        m = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        l = 0.0f;
+        r = 0.0f;
+        if (y < 0 || y >= rows) return;
+        const float* p = in + y * cols;
+        if (VEC) {
+            if (c0 < cols) m = __ldg(reinterpret_cast<const float4*>(p + c0));
+        } else {
+            if (c0 < cols) m.x = __ldg(p + c0);
+            if (c0 + 1 < cols) m.y = __ldg(p + c0 + 1);
+            if (c0 + 2 < cols) m.z = __ldg(p + c0 + 2);
+            if (c0 + 3 < cols) m.w = __ldg(p + c0 + 3);
+        }
+        if (lane == 0 && c0 >= 1 && c0 - 1 < cols) l = __ldg(p + c0 - 1);
+        if (lane == 31 && c0 + 4 < cols) r = __ldg(p + c0 + 4);
+    }
+    // the six values c0-1 .. c0+4 of this row
+    __device__ __forceinline__ void spread(float v[6], int lane) const {
+        const float fl = __shfl_up_sync(0xffffffffu, m.w, 1);
+        const float fr = __shfl_down_sync(0xffffffffu, m.x, 1);
+        v[0] = lane == 0 ? l : fl;
+        v[1] = m.x;
+        v[2] = m.y;
+        v[3] = m.z;
+        v[4] = m.w;
+        v[5] = lane == 31 ? r : fr;
+    }
+};
+
+// out[i][j] = sum_{a,b} w_ab in[i+a][j+b], zero outside the image.  Each thread owns
+// four adjacent columns of a strip of `strip` rows and walks down it with a three-row
+// register window, so every input row is read once per strip (plus two halo rows at
+// the strip's ends); the next row's loads are issued one iteration ahead.  The nine
+// terms of an output are fmaf'd in row-major order, zero terms included.  Every lane
+// of a warp runs the same number of iterations (the strip is per block), so the
+// shuffles always see a full warp.
+template <bool VEC>
+__global__ void __launch_bounds__(kStencilThreads) stencil3_kernel(float* __restrict__ out,
+                                                                   const float* __restrict__ in, int64_t rows,
+                                                                   int64_t cols, StencilW w, int strip) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c0 = ((int64_t)blockIdx.x * kStencilThreads + threadIdx.x) * 4;
+    const int64_t r0 = (int64_t)blockIdx.y * strip;
+    const int64_t r1 = r0 + strip < rows ? r0 + strip : rows;
+    StencilRow<VEC> raw;
+    float up[6], md[6], dn[6];
+    raw.load(in, r0 - 1, rows, cols, c0, lane);
+    raw.spread(up, lane);
+    raw.load(in, r0, rows, cols, c0, lane);
+    raw.spread(md, lane);
+    raw.load(in, r0 + 1, rows, cols, c0, lane);
+    for (int64_t i = r0; i < r1; ++i) {
+        raw.spread(dn, lane);
+        raw.load(in, i + 2, rows, cols, c0, lane);  // in flight while row i is formed
+        float o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float s = 0.0f;
+            s = __fmaf_rn(w.w[0], up[q], s);
+            s = __fmaf_rn(w.w[1], up[q + 1], s);
+            s = __fmaf_rn(w.w[2], up[q + 2], s);
+            s = __fmaf_rn(w.w[3], md[q], s);
+            s = __fmaf_rn(w.w[4], md[q + 1], s);
+            s = __fmaf_rn(w.w[5], md[q + 2], s);
+            s = __fmaf_rn(w.w[6], dn[q], s);
+            s = __fmaf_rn(w.w[7], dn[q + 1], s);
+            s = __fmaf_rn(w.w[8], dn[q + 2], s);
+            o[q] = s;
+        }
+        float* po = out + i * cols;
+        if (VEC) {
+            if (c0 < cols) *reinterpret_cast<float4*>(po + c0) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c0 + q < cols) po[c0 + q] = o[q];
+        }
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            up[t] = md[t];
+            md[t] = dn[t];
+        }
+    }
+}
+
 // ---- device-wait self test --------------------------------------------------------------------
 
 __global__ void wait_selftest_kernel(volatile int* flag, int* err, unsigned long long limit_ns) {
@@ -442,6 +544,29 @@ cudaError_t launch_colmax(float* out, const float* in, int64_t rows, int64_t col
         if (e != cudaSuccess) return e;
     }
     colmax_decode_kernel<<<grid_for(cols), kThreads, 0, st>>>(out, keys, cols, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st) {
+    StencilW w;
+    if (!stencil_weights(preset, w.w)) return cudaErrorInvalidValue;
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int64_t gx = ((cols + 3) / 4 + kStencilThreads - 1) / kStencilThreads;
+    if (gx > 0x7fffffff) return cudaErrorInvalidValue;
+    // strips of rows: about 12 resident 128-thread blocks per SM (40 registers), two waves, and at
+    // least 16 rows per strip so that the two halo rows stay a small share
+    const int64_t want_blocks = (int64_t)sm_count() * 24;
+    int64_t strips = (want_blocks + gx - 1) / gx;
+    int64_t strip = (rows + strips - 1) / strips;
+    if (strip < 16) strip = 16;
+    if ((rows + strip - 1) / strip > 65535) strip = (rows + 65534) / 65535;
+    if (strip > 0x7fffffff) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)gx, (unsigned)((rows + strip - 1) / strip));
+    const bool vec = (cols % 4 == 0) && (((uintptr_t)in | (uintptr_t)out) & 15u) == 0;
+    if (vec)
+        stencil3_kernel<true><<<grid, kStencilThreads, 0, st>>>(out, in, rows, cols, w, (int)strip);
+    else
+        stencil3_kernel<false><<<grid, kStencilThreads, 0, st>>>(out, in, rows, cols, w, (int)strip);
     return cudaGetLastError();
 }
 

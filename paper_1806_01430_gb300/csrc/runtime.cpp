@@ -227,6 +227,13 @@ gao_status validate(const gao_loop* loops, int n_loops, const gao_buffer* bufs, 
                 if (L.outs[0] == L.ins[0]) return fail(GAO_EINVAL, where + "COLMAX cannot run in place");
                 break;
             }
+            case GAO_LOOP_STENCIL3: {
+                if ((s = need_in(0))) return s;
+                if ((s = need_out(0, bufs[L.ins[0]].rows, bufs[L.ins[0]].cols, GAO_F32))) return s;
+                if (L.outs[0] == L.ins[0]) return fail(GAO_EINVAL, where + "STENCIL3 cannot run in place");
+                if (L.flags > 3) return fail(GAO_EINVAL, where + "unknown STENCIL3 preset " + std::to_string(L.flags));
+                break;
+            }
             default:
                 return fail(GAO_EINVAL, where + "unknown loop kind " + std::to_string(L.kind));
         }
@@ -551,6 +558,12 @@ gao_status run_gpu_loop(RunCtx& R, int li) {
             nl += (X.cols > 0) * (1 + (X.rows > 0));
             break;
         }
+        case GAO_LOOP_STENCIL3: {
+            const gao_buffer& X = shp(L.ins[0]);
+            e = launch_stencil3(dptr(L.outs[0]), dptr(L.ins[0]), X.rows, X.cols, (int)L.flags, st);
+            nl += X.rows * X.cols > 0;
+            break;
+        }
         default:
             return fail(GAO_EINVAL, "unknown loop kind");
     }
@@ -618,6 +631,11 @@ gao_status run_cpu_loop(RunCtx& R, int li) {
         case GAO_LOOP_COLMAX: {
             const gao_buffer& X = shp(L.ins[0]);
             cpu_colmax(hptr(L.outs[0]), hptr(L.ins[0]), X.rows, X.cols, c);
+            break;
+        }
+        case GAO_LOOP_STENCIL3: {
+            const gao_buffer& X = shp(L.ins[0]);
+            cpu_stencil3(hptr(L.outs[0]), hptr(L.ins[0]), X.rows, X.cols, (int)L.flags, c);
             break;
         }
         default:

@@ -1,0 +1,186 @@
+"""GPU parity of the 3x3 stencil loop and of the edge-detection image program
+(the paper's motivating camera-analysis workload, Sec. 1) against the FP64 oracle.
+
+Tolerances:
+  * a stencil output is nine binary32 fused multiply-adds of exact products, so
+    |y - y_ref| <= 9 * 2^-24 * sum |w| |x| (componentwise, gamma_9 bound);
+  * the CPU loop (gene bit 0) and the GPU kernel add the terms in the same order
+    with fused multiply-adds: bit-identical, for every loop of the program but the
+    SUM, whose GPU form adds groups of four binary32 values before its binary64
+    accumulation (at most 3 roundings of 2^-24 per group on non-negative data:
+    2e-7 relative);
+  * squared gradient magnitude: |M2 - M2_ref| <= 64 * 2^-24 * (Gx^2 + Gy^2), with
+    Gx, Gy the Sobel responses of the blur computed with |w| and |x| (the first-order
+    propagation of the per-stage gamma_9 bounds through the square, with slack).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+SUM_REL = 2e-7
+KERNELS = {
+    0: np.array([[1, 2, 1], [2, 4, 2], [1, 2, 1]], dtype=np.float64) / 16,
+    1: np.array([[0, 1, 0], [1, -4, 1], [0, 1, 0]], dtype=np.float64),
+    2: np.array([[-1, 0, 1], [-2, 0, 2], [-1, 0, 1]], dtype=np.float64),
+    3: np.array([[-1, -2, -1], [0, 0, 0], [1, 2, 1]], dtype=np.float64),
+}
+
+
+@pytest.fixture(scope="module")
+def gao():
+    from paper_1806_01430_gb300 import _build
+    _build.build()
+    import paper_1806_01430_gb300 as g
+    return g
+
+
+def abs_stencil(X, preset):
+    """sum |w_ab| |x_{i+a,j+b}| with zero padding (the scale of the rounding bound)."""
+    Xp = np.pad(np.abs(np.asarray(X, dtype=np.float64)), 1)
+    r, c = X.shape
+    out = np.zeros((r, c))
+    K = np.abs(KERNELS[preset])
+    for a in range(3):
+        for b in range(3):
+            out += K[a, b] * Xp[a:a + r, b:b + c]
+    return out
+
+
+def one_stencil(rows, cols, preset):
+    bufs = [W.Buffer("X", rows, cols, W.F32, W.INPUT), W.Buffer("Y", rows, cols, W.F32, W.OUTPUT)]
+    return W.Program(f"stencil_{rows}x{cols}", bufs, [W.Loop(W.STENCIL3, [0], [1], flags=preset)], 5)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (5, 1), (2, 2), (3, 4), (17, 513), (129, 260), (300, 1001),
+                                   (64, 2048), (41, 2052)])
+def test_stencil_loop_parity(gao, shape):
+    rows, cols = shape
+    X = oracle.init_matrix(31, 0, rows, cols, rowscale=True).astype(np.float32)
+    for preset in range(4):
+        prog = one_stencil(rows, cols, preset)
+        ref = oracle.stencil3(X, preset)
+        bound = 9 * U32 * abs_stencil(X, preset) + 1e-300
+        p = gao.prog_from_workload(prog)
+        gao.prog_set_input(p, 0, X)
+        gao.prog_run(p, 0b1)
+        Yg = gao.prog_output(p, 1)
+        gao.prog_run(p, 0b0)
+        Yc = gao.prog_output(p, 1)
+        gao.prog_destroy(p)
+        assert np.all(np.abs(Yg.astype(np.float64) - ref) <= bound), f"preset {preset}"
+        assert np.array_equal(Yg.view(np.uint32), Yc.view(np.uint32)), f"preset {preset}: CPU and GPU bits differ"
+
+
+def test_stencil_invalid_preset_and_in_place(gao):
+    bufs = [W.Buffer("X", 8, 8, W.F32, W.INPUT), W.Buffer("Y", 8, 8, W.F32, W.OUTPUT)]
+    with pytest.raises(gao.GaoError):
+        gao.prog_from_workload(W.Program("bad", bufs, [W.Loop(W.STENCIL3, [0], [1], flags=4)], 1))
+    bufs = [W.Buffer("X", 8, 8, W.F32, W.OUTPUT)]
+    with pytest.raises(gao.GaoError):
+        gao.prog_from_workload(W.Program("bad", bufs, [W.Loop(W.INIT, [], [0]), W.Loop(W.STENCIL3, [0], [0])], 1))
+
+
+def m2_bound(X):
+    """64 u (Gx^2 + Gy^2) with Gx, Gy the absolute-value Sobel responses of the absolute blur."""
+    Babs = abs_stencil(X, 0)
+    return 64 * U32 * (abs_stencil(Babs, 2) ** 2 + abs_stencil(Babs, 3) ** 2) + 1e-300
+
+
+@pytest.mark.parametrize("hw", [(1, 1), (3, 5), (64, 64), (127, 257), (256, 383)])
+def test_image_program_all_gpu(gao, hw):
+    h, w = hw
+    prog = W.image_program(h, w, W.SEED_IMAGE, outputs=("B", "gx", "M2", "e", "q"))
+    ref = oracle.run_program(prog)
+    p = gao.prog_from_workload(prog)
+    gao.prog_run(p, (1 << prog.n_loops) - 1)
+    out = {nm: gao.prog_output(p, prog.index(nm)) for nm in ("B", "gx", "M2", "e", "q")}
+    gao.prog_destroy(p)
+    X = oracle.init_matrix(W.SEED_IMAGE, 0, h, w)
+    assert np.all(np.abs(out["B"] - ref["B"]) <= 9 * U32 * abs_stencil(X, 0) + 1e-300)
+    M2 = out["M2"].astype(np.float64)
+    assert np.all(np.abs(M2 - ref["M2"]) <= m2_bound(X))
+    # reductions over the run's own M2: SUM in binary64, COLMAX exact
+    e = float(out["e"][0, 0])
+    assert abs(e - M2.sum()) <= SUM_REL * M2.sum() + 1e-300
+    assert np.array_equal(out["q"].ravel(), out["M2"].max(axis=0))
+    assert abs(e - ref["e"]) <= float(m2_bound(X).sum()) + SUM_REL * abs(ref["e"])
+
+
+def test_image_genes_bit_identical(gao):
+    h, w = 200, 300
+    prog = W.image_program(h, w, W.SEED_IMAGE + 1, outputs=("M2", "e", "q"))
+    p = gao.prog_from_workload(prog)
+    rng = np.random.default_rng(3)
+    masks = [0, (1 << prog.n_loops) - 1] + [int(m) for m in rng.integers(0, 1 << prog.n_loops, 14)]
+    first = None
+    for m in masks:
+        gao.prog_run(p, m)
+        got = (gao.prog_output(p, prog.index("M2")), float(gao.prog_output(p, prog.index("e"))[0, 0]),
+               gao.prog_output(p, prog.index("q")))
+        if first is None:
+            first = got
+            continue
+        assert np.array_equal(got[0].view(np.uint32), first[0].view(np.uint32)), f"gene {m:09b}"
+        assert np.array_equal(got[2].view(np.uint32), first[2].view(np.uint32)), f"gene {m:09b}"
+        assert abs(got[1] - first[1]) <= SUM_REL * abs(first[1])
+    gao.prog_destroy(p)
+
+
+def test_host_image_program(gao):
+    h, w = 96, 130
+    prog = W.image_program(h, w, 44, outputs=("M2", "q"), host_image=True)
+    X = oracle.init_matrix(44, 0, h, w).astype(np.float32)
+    ref = oracle.run_program(prog, {"X": X})
+    p = gao.prog_from_workload(prog)
+    gao.prog_set_input(p, prog.index("X"), X)
+    for mask in ((1 << prog.n_loops) - 1, 0, 0b10110101):
+        gao.prog_run(p, mask)
+        M2 = gao.prog_output(p, prog.index("M2")).astype(np.float64)
+        assert np.all(np.abs(M2 - ref["M2"]) <= m2_bound(X))
+        if mask & 1:
+            assert gao.prog_stats(p)[0]["h2d_bytes"] == h * w * 4
+    gao.prog_destroy(p)
+
+
+def sample_m2(seed, h, w, i, j):
+    """M2[i, j] of the full-size program from the 5 x 5 neighbourhood of X (oracle values)."""
+    P = np.zeros((5, 5))
+    for a in range(5):
+        for b in range(5):
+            y, x = i + a - 2, j + b - 2
+            if 0 <= y < h and 0 <= x < w:
+                P[a, b] = oracle.init_value(seed, 0, y * w + x)
+    Bp = oracle.stencil3(P, 0)[1:4, 1:4]  # blur at rows i-1..i+1, cols j-1..j+1 (exact neighbourhood)
+    for a in range(3):
+        for b in range(3):
+            if not (0 <= i + a - 1 < h and 0 <= j + b - 1 < w):
+                Bp[a, b] = 0.0  # the blurred image is zero-padded too
+    gx = float((KERNELS[2] * Bp).sum())
+    gy = float((KERNELS[3] * Bp).sum())
+    return gx * gx + gy * gy, P
+
+
+def test_full_size_8192_sampled(gao):
+    h = w = 8192
+    prog = W.image_program(h, w, W.SEED_IMAGE, outputs=("M2", "e", "q"))
+    p = gao.prog_from_workload(prog)
+    gao.prog_run(p, (1 << prog.n_loops) - 1)
+    M2 = gao.prog_output(p, prog.index("M2"))
+    e = float(gao.prog_output(p, prog.index("e"))[0, 0])
+    q = gao.prog_output(p, prog.index("q"))
+    gao.prog_destroy(p)
+    rng = np.random.default_rng(8)
+    pts = [(0, 0), (h - 1, w - 1), (0, w - 1), (h - 1, 0), (1, 4095), (4096, 1)]
+    pts += [(int(a), int(b)) for a, b in zip(rng.integers(0, h, 40), rng.integers(0, w, 40))]
+    for i, j in pts:
+        want, P = sample_m2(W.SEED_IMAGE, h, w, i, j)
+        bnd = m2_bound(P)[2, 2]
+        assert abs(float(M2[i, j]) - want) <= bnd, (i, j)
+    M2d = M2.astype(np.float64)
+    assert abs(e - M2d.sum()) <= SUM_REL * M2d.sum()
+    assert np.array_equal(q.ravel(), M2.max(axis=0))
