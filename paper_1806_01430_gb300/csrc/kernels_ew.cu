@@ -383,55 +383,68 @@ struct StencilRow {
 // out[i][j] = sum_{a,b} w_ab in[i+a][j+b], zero outside the image.  Each thread owns
 // four adjacent columns of a strip of `strip` rows and walks down it with a three-row
 // register window, so every input row is read once per strip (plus two halo rows at
-// the strip's ends); the next row's loads are issued one iteration ahead.  The nine
-// terms of an output are fmaf'd in row-major order, zero terms included.  Every lane
-// of a warp runs the same number of iterations (the strip is per block), so the
-// shuffles always see a full warp.
+// the strip's ends).  The loads of the next kStencilAhead rows are in flight while a
+// row is formed (a ring of raw rows, indexed statically under the unrolled inner
+// loop); no row past the strip's lower halo is fetched.  The nine terms of an output
+// are fmaf'd in row-major order, zero terms included.  Every lane of a warp runs the
+// same iterations (the strip is per block), so the shuffles always see a full warp.
+constexpr int kStencilAhead = 3;
+
 template <bool VEC>
-__global__ void __launch_bounds__(kStencilThreads) stencil3_kernel(float* __restrict__ out,
+__global__ void __launch_bounds__(kStencilThreads, 8) stencil3_kernel(float* __restrict__ out,
                                                                    const float* __restrict__ in, int64_t rows,
                                                                    int64_t cols, StencilW w, int strip) {
     const int lane = threadIdx.x & 31;
     const int64_t c0 = ((int64_t)blockIdx.x * kStencilThreads + threadIdx.x) * 4;
     const int64_t r0 = (int64_t)blockIdx.y * strip;
     const int64_t r1 = r0 + strip < rows ? r0 + strip : rows;
-    StencilRow<VEC> raw;
+    const int64_t ylim = r1 + 1 < rows ? r1 + 1 : rows;  // rows >= ylim are never needed
+    StencilRow<VEC> ring[kStencilAhead];
     float up[6], md[6], dn[6];
-    raw.load(in, r0 - 1, rows, cols, c0, lane);
-    raw.spread(up, lane);
-    raw.load(in, r0, rows, cols, c0, lane);
-    raw.spread(md, lane);
-    raw.load(in, r0 + 1, rows, cols, c0, lane);
-    for (int64_t i = r0; i < r1; ++i) {
-        raw.spread(dn, lane);
-        raw.load(in, i + 2, rows, cols, c0, lane);  // in flight while row i is formed
-        float o[4];
+    {
+        StencilRow<VEC> a;
+        a.load(in, r0 - 1, rows, cols, c0, lane);
+        a.spread(up, lane);
+        a.load(in, r0, rows, cols, c0, lane);
+        a.spread(md, lane);
+    }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float s = 0.0f;
-            s = __fmaf_rn(w.w[0], up[q], s);
-            s = __fmaf_rn(w.w[1], up[q + 1], s);
-            s = __fmaf_rn(w.w[2], up[q + 2], s);
-            s = __fmaf_rn(w.w[3], md[q], s);
-            s = __fmaf_rn(w.w[4], md[q + 1], s);
-            s = __fmaf_rn(w.w[5], md[q + 2], s);
-            s = __fmaf_rn(w.w[6], dn[q], s);
-            s = __fmaf_rn(w.w[7], dn[q + 1], s);
-            s = __fmaf_rn(w.w[8], dn[q + 2], s);
-            o[q] = s;
-        }
-        float* po = out + i * cols;
-        if (VEC) {
-            if (c0 < cols) *reinterpret_cast<float4*>(po + c0) = make_float4(o[0], o[1], o[2], o[3]);
-        } else {
+    for (int k = 0; k < kStencilAhead; ++k) ring[k].load(in, r0 + 1 + k, ylim, cols, c0, lane);
+    for (int64_t i = r0; i < r1; i += kStencilAhead) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (c0 + q < cols) po[c0 + q] = o[q];
-        }
+        for (int k = 0; k < kStencilAhead; ++k) {
+            const int64_t row = i + k;
+            if (row >= r1) break;  // block-uniform
+            ring[k].spread(dn, lane);                                            // row + 1
+            ring[k].load(in, row + 1 + kStencilAhead, ylim, cols, c0, lane);  // in flight for the next rows
+            float o[4];
 #pragma unroll
-        for (int t = 0; t < 6; ++t) {
-            up[t] = md[t];
-            md[t] = dn[t];
+            for (int q = 0; q < 4; ++q) {
+                float s = 0.0f;
+                s = __fmaf_rn(w.w[0], up[q], s);
+                s = __fmaf_rn(w.w[1], up[q + 1], s);
+                s = __fmaf_rn(w.w[2], up[q + 2], s);
+                s = __fmaf_rn(w.w[3], md[q], s);
+                s = __fmaf_rn(w.w[4], md[q + 1], s);
+                s = __fmaf_rn(w.w[5], md[q + 2], s);
+                s = __fmaf_rn(w.w[6], dn[q], s);
+                s = __fmaf_rn(w.w[7], dn[q + 1], s);
+                s = __fmaf_rn(w.w[8], dn[q + 2], s);
+                o[q] = s;
+            }
+            float* po = out + row * cols;
+            if (VEC) {
+                if (c0 < cols) *reinterpret_cast<float4*>(po + c0) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + q < cols) po[c0 + q] = o[q];
+            }
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                up[t] = md[t];
+                md[t] = dn[t];
+            }
         }
     }
 }
@@ -553,9 +566,9 @@ cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t c
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     const int64_t gx = ((cols + 3) / 4 + kStencilThreads - 1) / kStencilThreads;
     if (gx > 0x7fffffff) return cudaErrorInvalidValue;
-    // strips of rows: about 12 resident 128-thread blocks per SM (40 registers), two waves, and at
-    // least 16 rows per strip so that the two halo rows stay a small share
-    const int64_t want_blocks = (int64_t)sm_count() * 24;
+    // strips of rows: about 8 resident 128-thread blocks per SM (<= 64 registers), two
+    // waves, and at least 16 rows per strip so that the two halo rows stay a small share
+    const int64_t want_blocks = (int64_t)sm_count() * 16;
     int64_t strips = (want_blocks + gx - 1) / gx;
     int64_t strip = (rows + strips - 1) / strips;
     if (strip < 16) strip = 16;
