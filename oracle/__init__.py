@@ -78,6 +78,8 @@ def lib():
             L.orc_gemm_column.argtypes = [_i64, _i64, _i64, _d, _P, _P, _d, _P, _i64, _P]
             L.orc_stencil3.restype = ctypes.c_int
             L.orc_stencil3.argtypes = [_i64, _i64, _P, ctypes.c_int, _P]
+            L.orc_recurrence.argtypes = [_i64, _i64, _P, _d, _P]
+            L.orc_find.argtypes = [_i64, _i64, _P, _d, _P]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -194,6 +196,22 @@ def stencil3(X, preset: int) -> np.ndarray:
     return out
 
 
+def recurrence(X, alpha: float) -> np.ndarray:
+    X = _c(X)
+    r, c = X.shape
+    out = np.empty_like(X)
+    lib().orc_recurrence(r, c, X, float(alpha), out)
+    return out
+
+
+def find_first(X, threshold: float) -> np.ndarray:
+    X = _c(X)
+    r, c = X.shape
+    out = np.empty((r, 1), dtype=np.float64)
+    lib().orc_find(r, c, X, float(threshold), out)
+    return out
+
+
 def gemm_init_entries(seed: int, bufs, rowscale_a: bool, M: int, N: int, K: int, alpha: float, beta: float,
                       ii, jj) -> np.ndarray:
     """C[i,j] of C = alpha*A@B + beta*C0 for freshly initialised A, B, C0 (buffer ids
@@ -227,7 +245,8 @@ def set_num_threads(n: int) -> None:
 
 # loop kinds (gao_loop_kind); kept as literals so that the oracle does not depend
 # on the product package.
-_INIT, _GEMM, _AXPY, _TRANSPOSE, _ROWSUM, _FROB, _RELU, _SQUARE, _COLMAX, _SUM, _STENCIL3 = range(11)
+_INIT, _GEMM, _AXPY, _TRANSPOSE, _ROWSUM, _FROB, _RELU, _SQUARE, _COLMAX, _SUM, _STENCIL3, _RECURRENCE, _FIND = range(13)
+_EXTERNAL_CALL = 1 << 63  # loop flag that only decides placement
 
 
 def run_program(prog, inputs: dict | None = None) -> dict:
@@ -247,7 +266,8 @@ def run_program(prog, inputs: dict | None = None) -> dict:
                 b = prog.buffers[ob]
                 vals[ob] = init_matrix(prog.seed, ob, b.rows, b.cols, bool((lp.flags >> t) & 1))
         elif lp.kind == _GEMM:
-            vals[o] = gemm(ins[0], ins[1], ins[2], lp.alpha, lp.beta)
+            c0 = ins[2] if len(ins) > 2 else np.zeros((ins[0].shape[0], ins[1].shape[1]))  # no C0: beta = 0
+            vals[o] = gemm(ins[0], ins[1], c0, lp.alpha, lp.beta if len(ins) > 2 else 0.0)
         elif lp.kind == _AXPY:
             vals[o] = axpy(ins[0], lp.alpha, ins[1])
         elif lp.kind == _TRANSPOSE:
@@ -265,7 +285,11 @@ def run_program(prog, inputs: dict | None = None) -> dict:
         elif lp.kind == _SUM:
             vals[o] = total(ins[0])
         elif lp.kind == _STENCIL3:
-            vals[o] = stencil3(ins[0], lp.flags)
+            vals[o] = stencil3(ins[0], lp.flags & ~_EXTERNAL_CALL)
+        elif lp.kind == _RECURRENCE:
+            vals[o] = recurrence(ins[0], lp.alpha)
+        elif lp.kind == _FIND:
+            vals[o] = find_first(ins[0], lp.alpha)
         else:
             raise ValueError(f"unknown loop kind {lp.kind}")
     return {prog.buffers[i].name: v for i, v in vals.items()}

@@ -24,6 +24,9 @@
  *   SUM        s = sum_ij P_ij
  *   STENCIL3   Y_ij = sum_{a,b in -1..1} w_ab X_{i+a, j+b}, X = 0 outside the image
  *              (image-analysis loops, the paper's motivating IoT camera workload, Sec. 1)
+ *   RECURRENCE Y_i0 = X_i0, Y_ij = alpha Y_i,j-1 + X_ij   (a loop-carried dependence)
+ *   FIND       k_i = min { j : X_ij > t } (cols if none), t = alpha rounded to binary32
+ *              (a loop with an early exit); both are loops Sec. 4 keeps on the CPU
  *
  * Every loop is the textbook double/triple loop.  The GEMM runs its loops in
  * i-k-j order so that the row of B is read contiguously; for every output
@@ -226,6 +229,27 @@ int orc_stencil3(int64_t rows, int64_t cols, const double *in, int preset, doubl
             out[i * cols + j] = s;
         }
     return 0;
+}
+
+/* RECURRENCE loop along each row, in binary64. */
+void orc_recurrence(int64_t rows, int64_t cols, const double *in, double alpha, double *out) {
+    for (int64_t i = 0; i < rows; ++i) {
+        const double *x = in + i * cols;
+        double *y = out + i * cols;
+        for (int64_t j = 0; j < cols; ++j) y[j] = j == 0 ? x[0] : alpha * y[j - 1] + x[j];
+    }
+}
+
+/* FIND loop: the first column whose element exceeds the threshold (the threshold is the
+ * binary32 value of alpha, the precision the loop's data has). */
+void orc_find(int64_t rows, int64_t cols, const double *in, double alpha, double *out) {
+    const double t = (double)(float)alpha;
+    for (int64_t i = 0; i < rows; ++i) {
+        int64_t k = cols;
+        for (int64_t j = cols - 1; j >= 0; --j)
+            if (in[i * cols + j] > t) k = j;
+        out[i] = (double)k;
+    }
 }
 
 /* ---- sampled entries at full size, without materialising the matrices ---- */

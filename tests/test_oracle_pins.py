@@ -308,3 +308,59 @@ def test_image_program_exact_small():
     assert np.allclose(out["M2"], M2, rtol=1e-15, atol=0)
     assert abs(out["e"] - float(M2.sum())) <= 1e-13 * float(M2.sum())
     assert np.array_equal(out["q"].ravel(), out["M2"].max(axis=0))
+
+
+# ---- loops Sec. 4 keeps on the CPU (dependence, early exit) -----------------------------
+
+def test_recurrence_closed_forms():
+    rng = np.random.default_rng(12)
+    Xi = rng.integers(-50, 51, size=(6, 40)).astype(np.float64)
+    assert np.array_equal(oracle.recurrence(Xi, 1.0), np.cumsum(Xi, axis=1))  # prefix sums, exact
+    assert np.array_equal(oracle.recurrence(Xi, 0.0), Xi)
+    E = np.zeros((2, 30))
+    E[:, 0] = 1.0
+    assert np.array_equal(oracle.recurrence(E, 0.5)[0], 0.5 ** np.arange(30))  # impulse response
+    ones = np.ones((1, 40))
+    assert np.array_equal(oracle.recurrence(ones, 2.0)[0], 2.0 ** (np.arange(40) + 1) - 1)  # geometric series
+    assert oracle.recurrence(np.zeros((0, 5)), 1.0).shape == (0, 5)
+
+
+def test_recurrence_exact_rational_bound():
+    X = oracle.init_matrix(22, 0, 3, 25)
+    alpha = 1.5
+    got = oracle.recurrence(X, alpha)
+    for i in range(3):
+        y, scale = Fraction(0), 0.0
+        for j in range(25):
+            y = Fraction(float(X[i, j])) if j == 0 else Fraction(alpha) * y + Fraction(float(X[i, j]))
+            scale = abs(float(X[i, j])) if j == 0 else alpha * scale + abs(float(X[i, j]))
+            bound = 2 * (j + 1) * U / (1 - 2 * (j + 1) * U) * scale
+            assert abs(Fraction(float(got[i, j])) - y) <= Fraction(bound)
+
+
+def test_find_first_bruteforce_and_binary32_threshold():
+    X = oracle.init_matrix(23, 0, 9, 17)
+    for t in (-2.0, -0.5, 0.0, 0.7, 0.99, 1.0):
+        got = oracle.find_first(X, t)
+        for i in range(9):
+            hits = [j for j in range(17) if X[i, j] > t]
+            assert got[i, 0] == (hits[0] if hits else 17)
+    # the threshold is the binary32 value of alpha: a binary32 0.1 does not exceed 0.1
+    v = float(np.float32(0.1))
+    row = np.array([[0.0, v, 1.0]])
+    assert oracle.find_first(row, 0.1)[0, 0] == 2
+    assert oracle.find_first(row, 0.0999)[0, 0] == 1
+    assert oracle.find_first(np.zeros((2, 0)), 0.0)[0, 0] == 0  # empty rows: cols
+
+
+def test_program_with_host_only_loops_exact_small():
+    prog = W.analysis_program(6, 7, seed=5, outputs=("R", "C", "k", "s"))
+    out = oracle.run_program(prog)
+    X = oracle.init_matrix(5, 0, 6, 7)
+    Bm = oracle.init_matrix(5, 1, 7, 7)
+    R = oracle.recurrence(X, W.ANALYSIS_ALPHA)
+    C = oracle.gemm(R, Bm, np.zeros((6, 7)), 1.0, 0.0)
+    assert np.array_equal(out["R"], R) and np.array_equal(out["C"], C)
+    k = oracle.find_first(C.T, W.ANALYSIS_THRESHOLD)
+    assert np.array_equal(out["k"], k)
+    assert out["s"] == oracle.total(np.maximum(C.T, 0.0))

@@ -20,9 +20,10 @@ from typing import List, Optional
 import numpy as np
 
 # gao_loop_kind values (include/gao.h)
-INIT, GEMM, AXPY, TRANSPOSE, ROWSUM, FROBENIUS, RELU, SQUARE, COLMAX, SUM, STENCIL3 = range(11)
+INIT, GEMM, AXPY, TRANSPOSE, ROWSUM, FROBENIUS, RELU, SQUARE, COLMAX, SUM, STENCIL3, RECURRENCE, FIND = range(13)
 KIND_NAMES = ["init", "gemm", "axpy", "transpose", "rowsum", "frobenius", "relu", "square", "colmax", "sum",
-              "stencil3"]
+              "stencil3", "recurrence", "find"]
+EXTERNAL_CALL = 1 << 63  # loop flag: the body calls a host routine
 # STENCIL3 presets (loop flags)
 BLUR, LAPLACIAN, SOBEL_X, SOBEL_Y = range(4)
 # gao_dtype
@@ -181,6 +182,34 @@ def image_program(h: int, w: int, seed: int, outputs=("M2", "e", "q"), host_imag
         Loop(COLMAX, [M2], [q]),
     ]
     return Program(f"image_{h}x{w}", bufs, loops, seed, {"h": h, "w": w})
+
+
+ANALYSIS_ALPHA = 0.5       # decay of the recurrence loop
+ANALYSIS_THRESHOLD = 0.75  # threshold of the find loop
+
+
+def analysis_program(m: int, n: int, seed: int, outputs=("C", "k", "s")) -> Program:
+    """Seven loops, three of which Sec. 4's parallelisability check excludes:
+    L0 init X (m x n), B (n x n); L1 R = recurrence of X along rows (carried dependence);
+    L2 C = R @ B; L3 T = C^T; L4 k = first column of each row of T above the threshold
+    (early exit); L5 P = max(T, 0) in a loop that calls a host routine (external call);
+    L6 s = sum of P.  Gene length 4 (loops 0, 2, 3, 6)."""
+    names = ["X", "B", "R", "C", "T", "k", "P", "s"]
+    shapes = {"X": (m, n), "B": (n, n), "R": (m, n), "C": (m, n), "T": (n, m), "k": (n, 1), "P": (n, m),
+              "s": (1, 1)}
+    bufs = [Buffer(nm, *shapes[nm], F64 if nm in ("k", "s") else F32, OUTPUT if nm in outputs else TEMP)
+            for nm in names]
+    X, B_, R, C, T, k, P, s = range(8)
+    loops = [
+        Loop(INIT, [], [X, B_]),
+        Loop(RECURRENCE, [X], [R], alpha=ANALYSIS_ALPHA),
+        Loop(GEMM, [R, B_, -1], [C], alpha=1.0, beta=0.0),
+        Loop(TRANSPOSE, [C], [T]),
+        Loop(FIND, [T], [k], alpha=ANALYSIS_THRESHOLD),
+        Loop(RELU, [T], [P], flags=EXTERNAL_CALL),
+        Loop(SUM, [P], [s]),
+    ]
+    return Program(f"analysis_{m}x{n}", bufs, loops, seed, {"m": m, "n": n})
 
 
 # ---- seeds of the benchmark configurations ----------------------------------
