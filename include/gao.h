@@ -9,8 +9,9 @@
  * Simple GA whose fitness is (processing time)^(-1/2) (Sec. 5.1.2).
  *
  * This library runs such a program on one GPU (sm_103a) and its host CPU:
- *   prog_create  declares the buffers and loops (Sec. 4: the loop list and its
- *                gene length a),
+ *   prog_create  declares the buffers and loops and classifies each loop as
+ *                offloadable or not (Sec. 4: the loop list, the parallelisability
+ *                check and the gene length a),
  *   prog_run     executes the program under one gene and returns its time
  *                (Sec. 3.3 "evaluation": run the pattern and measure it),
  *   ga_evaluate  scores a population, reusing the time of any gene measured
@@ -23,8 +24,9 @@
  *   - Arrays passed in are borrowed for the duration of the call only.
  *   - Matrices are row-major binary32; scalars produced by FROBENIUS and SUM
  *     are binary64 (a 1 x 1 buffer of dtype GAO_F64).
- *   - Gene bit i (bit 0 = least significant) places loop i; bits at or above
- *     the loop count must be zero (GAO_EINVAL otherwise).  At most 64 loops.
+ *   - Gene bit k (bit 0 = least significant) places the k-th offloadable loop;
+ *     when every loop is offloadable, bit i places loop i.  Bits at or above the
+ *     gene length must be zero (GAO_EINVAL otherwise).  At most 64 loops.
  *   - A program is not thread-safe: one call at a time per gao_prog.
  */
 #ifndef GAO_H
@@ -62,14 +64,38 @@ typedef enum gao_loop_kind {
     GAO_LOOP_SQUARE = 7,    /* outs[0] = ins[0] (.) ins[0]                                       */
     GAO_LOOP_COLMAX = 8,    /* outs[0][j] = max_i ins[0][i,j]   (1 x cols, binary32)             */
     GAO_LOOP_SUM = 9,       /* outs[0] = sum ins[0]             (1 x 1, binary64)                */
-    GAO_LOOP_STENCIL3 = 10  /* outs[0][i,j] = sum_{a,b in -1..1} w_ab ins[0][i+a,j+b], ins[0] taken as 0
+    GAO_LOOP_STENCIL3 = 10, /* outs[0][i,j] = sum_{a,b in -1..1} w_ab ins[0][i+a,j+b], ins[0] taken as 0
                                outside the image; the nine terms are added in row-major (a, b)
                                order with fused multiply-adds, zero terms included.  flags picks
                                w: 0 binomial blur (1 2 1; 2 4 2; 1 2 1)/16, 1 Laplacian
                                (0 1 0; 1 -4 1; 0 1 0), 2 Sobel x (-1 0 1; -2 0 2; -1 0 1),
                                3 Sobel y (-1 -2 -1; 0 0 0; 1 2 1).  The image-analysis loops
                                of the paper's motivating camera workload (Sec. 1).           */
+    GAO_LOOP_RECURRENCE = 11, /* outs[0][i,0] = ins[0][i,0];
+                               outs[0][i,j] = alpha * outs[0][i,j-1] + ins[0][i,j]  (j >= 1,
+                               one fused multiply-add).  Each element depends on the one
+                               before it: never offloaded (see gao_offload).                 */
+    GAO_LOOP_FIND = 12      /* outs[0][i] = smallest j with ins[0][i,j] > alpha, cols if none
+                               (rows x 1, binary64; alpha and the elements compared as
+                               binary32).  The loop leaves a row early: never offloaded.     */
 } gao_loop_kind;
+
+/* A loop whose body calls an external (host) routine: set this bit in gao_loop.flags.
+ * The loop still runs, on the CPU only (see gao_offload). */
+#define GAO_LOOP_EXTERNAL_CALL (1ull << 63)
+
+/* Parallelisability of a loop, decided at prog_create.  Sec. 4 tries a parallel
+ * directive on each loop and keeps only the loops that compile; the compile errors it
+ * names are data dependences between iterations, calls of external routines, loops that
+ * exit early (break) and directives at two levels of one nest.  The loops here are whole
+ * nests, so the last case cannot occur.  Loops that are not OK run on the CPU under every
+ * gene, and the gene has one bit per OK loop (gene length a, Sec. 4). */
+typedef enum gao_offload {
+    GAO_OFFLOAD_OK = 0,
+    GAO_OFFLOAD_DEPENDENCE = 1,    /* loop-carried data dependence (RECURRENCE)        */
+    GAO_OFFLOAD_EARLY_EXIT = 2,    /* the loop leaves early (FIND)                     */
+    GAO_OFFLOAD_EXTERNAL_CALL = 3  /* flags has GAO_LOOP_EXTERNAL_CALL                 */
+} gao_offload;
 
 typedef enum gao_dtype { GAO_F32 = 0, GAO_F64 = 1 } gao_dtype;
 
@@ -137,8 +163,9 @@ typedef struct gao_prog gao_prog;
 gao_status prog_device_bytes(const gao_loop *loops, int n_loops, const gao_buffer *bufs, int n_bufs,
                              const gao_opts *opts, uint64_t *bytes_out);
 
-/* Declare a program: its buffers and its loops in program order (gene length = n_loops).
- * Validates shapes and the dataflow (every input is produced earlier or is an INPUT buffer).
+/* Declare a program: its buffers and its loops in program order.  Validates shapes and the
+ * dataflow (every input is produced earlier or is an INPUT buffer) and classifies every
+ * loop (gao_offload); the gene length is the number of offloadable loops.
  * On success *out owns device memory (or uses opts->dev_arena) and pinned host mirrors. */
 gao_status prog_create(const gao_loop *loops, int n_loops, const gao_buffer *bufs, int n_bufs,
                        const gao_opts *opts, gao_prog **out);
@@ -148,7 +175,10 @@ gao_status prog_set_input(gao_prog *p, int buf, const void *host_src, uint64_t b
 
 #define GAO_RUN_KEEP_DEVICE 1u /* leave OUTPUT buffers on the device (no final copy) */
 
-/* Run every loop in program order, loop i on the GPU iff gene bit i is 1.  Data moves
+/* Run every loop in program order.  Gene bit k belongs to the k-th offloadable loop in
+ * program order (bit i to loop i when every loop is offloadable); that loop runs on the
+ * GPU iff the bit is 1, the other loops on the CPU.  Bits at or above the gene length:
+ * GAO_EINVAL.  Data moves
  * between host and device only where a loop needs a buffer last written on the other
  * side (Sec. 3.3: CPU-GPU transfers decide which loop combinations are fast).
  * *seconds_out = wall time from the first loop until the outputs are on the host. */
@@ -172,6 +202,13 @@ typedef struct gao_loop_stat {
     uint64_t h2d_bytes; /* bytes copied host->device before the loop                   */
     uint64_t d2h_bytes; /* bytes copied device->host before the loop                   */
 } gao_loop_stat;
+
+/* Gene length a: the number of offloadable loops (Sec. 4). */
+gao_status prog_gene_length(const gao_prog *p, int *length);
+
+/* Classification of loop `loop`: *verdict = gao_offload, *gene_bit = its bit in the gene,
+ * -1 when it is not offloadable.  Either output may be NULL. */
+gao_status prog_loop_offload(const gao_prog *p, int loop, int *verdict, int *gene_bit);
 
 /* Per-loop statistics of the last prog_run (n >= loop count). */
 gao_status prog_stats(gao_prog *p, gao_loop_stat *out, int n);

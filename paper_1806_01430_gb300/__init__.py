@@ -24,7 +24,10 @@ LIB_PATH = os.path.join(_HERE, "libgao.so")
 # enums (include/gao.h)
 GAO_OK, GAO_EINVAL, GAO_ENOMEM, GAO_ECUDA, GAO_ETIMEOUT, GAO_EDEVICE, GAO_ENODEV, GAO_ECPU = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EDEVICE", "ENODEV", "ECPU"]
-INIT, GEMM, AXPY, TRANSPOSE, ROWSUM, FROBENIUS, RELU, SQUARE, COLMAX, SUM, STENCIL3 = range(11)
+INIT, GEMM, AXPY, TRANSPOSE, ROWSUM, FROBENIUS, RELU, SQUARE, COLMAX, SUM, STENCIL3, RECURRENCE, FIND = range(13)
+LOOP_EXTERNAL_CALL = 1 << 63  # loop flag: the body calls a host routine (never offloaded)
+OFFLOAD_OK, OFFLOAD_DEPENDENCE, OFFLOAD_EARLY_EXIT, OFFLOAD_EXTERNAL_CALL = range(4)
+OFFLOAD_NAMES = ["ok", "dependence", "early_exit", "external_call"]
 STENCIL_BLUR, STENCIL_LAPLACIAN, STENCIL_SOBEL_X, STENCIL_SOBEL_Y = range(4)  # STENCIL3 loop flags
 F32, F64 = 0, 1
 TEMP, INPUT, OUTPUT = 0, 1, 2
@@ -96,6 +99,8 @@ SIGNATURES = {
     "prog_set_input": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint64]),
     "prog_run": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]),
     "prog_output": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(gao_buffer)]),
+    "prog_gene_length": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "prog_loop_offload": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "prog_device_ptr": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "prog_stats": (ctypes.c_int, [_P, ctypes.POINTER(gao_loop_stat), ctypes.c_int]),
     "prog_cache_clear": (ctypes.c_int, [_P]),
@@ -257,6 +262,20 @@ def prog_from_workload(program, **kw) -> Prog:
 def prog_set_input(p: Prog, buf: int, data: np.ndarray) -> None:
     a = np.ascontiguousarray(data, dtype=np.float64 if p.buffers[buf].dtype == F64 else np.float32)
     _check(lib().prog_set_input(p.handle, buf, a.ctypes.data_as(ctypes.c_void_p), a.nbytes), "prog_set_input")
+
+
+def prog_gene_length(p: Prog) -> int:
+    """Gene length a: the number of offloadable loops."""
+    a = ctypes.c_int(0)
+    _check(lib().prog_gene_length(p.handle, ctypes.byref(a)), "prog_gene_length")
+    return int(a.value)
+
+
+def prog_loop_offload(p: Prog, loop: int):
+    """(verdict, gene bit) of one loop; verdict is one of OFFLOAD_*, gene bit -1 when not offloadable."""
+    v, g = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().prog_loop_offload(p.handle, loop, ctypes.byref(v), ctypes.byref(g)), "prog_loop_offload")
+    return int(v.value), int(g.value)
 
 
 def prog_run(p: Prog, gene_mask: int, flags: int = 0) -> float:

@@ -32,6 +32,7 @@ using namespace gao;
 struct gao_batch {
     std::vector<gao_prog*> progs;
     int n_loops = 0;
+    int n_genes = 0;  // offloadable loops (gene length)
     int prec = 0;
     cudaStream_t st = nullptr;
     std::vector<cudaStream_t> side;
@@ -142,9 +143,10 @@ gao_status capture_phase(gao_batch* b, int li, std::vector<TcProblem>* probs) {
 }
 
 // One gene over the whole suite; *seconds = wall time (budget on timeout, -1 on failure).
-gao_status run_gene(gao_batch* b, uint64_t mask, double* seconds) {
+gao_status run_gene(gao_batch* b, uint64_t gene, double* seconds) {
     const int n = b->n_loops;
-    if (n < 64 && (mask >> n) != 0) return fail(GAO_EINVAL, "gene has bits above the loop count");
+    if (b->n_genes < 64 && (gene >> b->n_genes) != 0) return fail(GAO_EINVAL, "gene has bits above the gene length");
+    const uint64_t mask = loop_mask_of(b->progs[0], gene);  // bit li: loop li on the GPU
     const double t0 = now_s();
     const double deadline = b->timeout_s > 0.0 ? t0 + b->timeout_s : 0.0;
     std::vector<RunCtx> R;
@@ -246,7 +248,8 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
         if (!p) return fail(GAO_EINVAL, "null program");
         if (p->loops.size() != p0->loops.size()) return fail(GAO_EINVAL, "batch programs differ in loop count");
         for (size_t l = 0; l < p->loops.size(); ++l)
-            if (p->loops[l].kind != p0->loops[l].kind) return fail(GAO_EINVAL, "batch programs differ in loop kinds");
+            if (p->loops[l].kind != p0->loops[l].kind || p->verdict[l] != p0->verdict[l])
+                return fail(GAO_EINVAL, "batch programs differ in loop kinds or in which loops are offloadable");
         if (p->opts.gemm_prec != p0->opts.gemm_prec) return fail(GAO_EINVAL, "batch programs differ in GEMM precision");
         if (p->opts.transfer_mode != GAO_TRANSFER_RESIDENT)
             return fail(GAO_EINVAL, "batches keep buffers resident (transfer_mode RESIDENT only)");
@@ -264,9 +267,10 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
     };
     b->progs.assign(progs, progs + n_progs);
     b->n_loops = (int)p0->loops.size();
+    b->n_genes = gene_length(p0);
     b->prec = p0->opts.gemm_prec;
     for (int l = 0; l < b->n_loops; ++l)
-        if (p0->loops[(size_t)l].kind == GAO_LOOP_GEMM) {
+        if (p0->loops[(size_t)l].kind == GAO_LOOP_GEMM && p0->verdict[(size_t)l] == GAO_OFFLOAD_OK) {
             if (b->gemm_loop >= 0) return bail(fail(GAO_EINVAL, "a batch supports one GEMM loop per program"));
             b->gemm_loop = l;
         }
@@ -340,6 +344,7 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
     }
     b->stat.launches_per_gene = 0;
     for (int li = 0; li < b->n_loops; ++li) {
+        if (p0->verdict[(size_t)li] != GAO_OFFLOAD_OK) continue;  // host-only loop: no graph
         if ((s = capture_phase(b, li, &probs)) != GAO_OK) return bail(s);
         if (li == b->gemm_loop && b->grouped_gemm) {
             int start = 0;
@@ -354,7 +359,7 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
             b->h_probs = probs;
         }
     }
-    b->stat.graphs = b->n_loops;
+    b->stat.graphs = b->n_genes;
     *out = b;
     return GAO_OK;
 }
@@ -381,7 +386,7 @@ extern "C" gao_status batch_ga_run(gao_batch* b, const gao_ga_params* params, ga
     const double saved = b->timeout_s;
     double budget = params->timeout_s;
     if (budget < 0.0) {  // automatic: 10 x the all-GPU time of the suite, capped at 60 s
-        const uint64_t all = b->n_loops >= 64 ? ~0ULL : ((1ULL << b->n_loops) - 1);
+        const uint64_t all = all_genes(b->n_genes);
         double t = 0.0;
         bool cached = false;
         b->timeout_s = 0.0;
@@ -394,7 +399,8 @@ extern "C" gao_status batch_ga_run(gao_batch* b, const gao_ga_params* params, ga
         bool cached = false;
         return gene_seconds(b, m, t, &cached);
     };
-    gao_status s = ga_core(b->n_loops, *params, fn, result);
+    if (b->n_genes < 1) return fail(GAO_EINVAL, "no loop of the batch is offloadable (gene length 0)");
+    gao_status s = ga_core(b->n_genes, *params, fn, result);
     b->timeout_s = saved;
     return s;
 }
@@ -410,7 +416,7 @@ extern "C" gao_status batch_stats(gao_batch* b, gao_batch_stat* out) {
 extern "C" gao_status batch_autotune(gao_batch* b, const gao_ga_params* params, gao_autotune_result* out) {
     if (!b || !params || !out) return fail(GAO_EINVAL, "null argument");
     if (!b->grouped_gemm) return fail(GAO_EINVAL, "batch has no tensor-core GEMM loop");
-    const uint64_t all = b->n_loops >= 64 ? ~0ULL : ((1ULL << b->n_loops) - 1);
+    const uint64_t all = all_genes(b->n_genes);
     double s0 = 0.0;
     gao_status st = run_gene(b, all, &s0);  // the GEMM's inputs on the device
     if (st != GAO_OK) return st;

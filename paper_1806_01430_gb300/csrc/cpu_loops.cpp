@@ -270,4 +270,47 @@ void cpu_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int p
     }
 }
 
+// First-order recurrence along each row: out[i][0] = in[i][0], then
+// out[i][j] = fmaf(alpha, out[i][j-1], in[i][j]).  Rows are independent, elements of a
+// row are not (the loop-carried dependence that keeps this loop on the CPU).
+void cpu_recurrence(float* out, const float* in, int64_t rows, int64_t cols, float alpha, CpuCtx& c) {
+    std::atomic<bool> stop{false};
+#pragma omp parallel for schedule(static) num_threads(nthreads(c))
+    for (int64_t i = 0; i < rows; ++i) {
+        if (stop.load(std::memory_order_relaxed)) continue;
+        if ((i & 255) == 0 && expired(c)) {
+            stop = true;
+            continue;
+        }
+        const float* x = in + i * cols;
+        float* y = out + i * cols;
+        if (cols <= 0) continue;
+        float prev = x[0];
+        y[0] = prev;
+        for (int64_t j = 1; j < cols; ++j) {
+            prev = fmaf(alpha, prev, x[j]);
+            y[j] = prev;
+        }
+    }
+}
+
+// out[i] = the first column j with in[i][j] > threshold, cols if there is none; the
+// scan of a row stops at the first hit (the early exit that keeps this loop on the CPU).
+void cpu_find(double* out, const float* in, int64_t rows, int64_t cols, float threshold, CpuCtx& c) {
+    std::atomic<bool> stop{false};
+#pragma omp parallel for schedule(static) num_threads(nthreads(c))
+    for (int64_t i = 0; i < rows; ++i) {
+        if (stop.load(std::memory_order_relaxed)) continue;
+        if ((i & 255) == 0 && expired(c)) {
+            stop = true;
+            continue;
+        }
+        const float* x = in + i * cols;
+        int64_t j = 0;
+        for (; j < cols; ++j)
+            if (x[j] > threshold) break;
+        out[i] = (double)j;
+    }
+}
+
 }  // namespace gao

@@ -146,5 +146,7 @@ void cpu_relu(float* out, const float* in, int64_t n, CpuCtx& c);
 void cpu_square(float* out, const float* in, int64_t n, CpuCtx& c);
 void cpu_colmax(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx& c);
 void cpu_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, CpuCtx& c);
+void cpu_recurrence(float* out, const float* in, int64_t rows, int64_t cols, float alpha, CpuCtx& c);
+void cpu_find(double* out, const float* in, int64_t rows, int64_t cols, float threshold, CpuCtx& c);
 
 }  // namespace gao

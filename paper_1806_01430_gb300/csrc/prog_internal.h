@@ -48,6 +48,8 @@ struct gao_prog {
     std::vector<uint8_t> ev_used;  // bit 0 copies, bit 1 loop, bit 2 kernel
     std::unordered_map<uint64_t, gao::CacheEntry> cache;
     bool dirty_stream = false;  // a previous run left work in flight
+    std::vector<int8_t> verdict;  // gao_offload of every loop
+    std::vector<int> gene_loop;   // gene bit k -> index of the k-th offloadable loop
 };
 
 namespace gao {
@@ -69,5 +71,10 @@ gao_status run_gpu_loop(RunCtx& R, int li);
 gao_status run_cpu_loop(RunCtx& R, int li);
 gao_status stream_wait(cudaStream_t st, double deadline, bool* timed_out, double hard_cap_s = 300.0);
 gao_status check_device(int* dev_out);
+// Parallelisability of one loop (gao_offload), and the loop placement of a gene.
+int offload_verdict(const gao_loop& L);
+uint64_t loop_mask_of(const gao_prog* p, uint64_t gene);
+inline int gene_length(const gao_prog* p) { return (int)p->gene_loop.size(); }
+inline uint64_t all_genes(int a) { return a >= 64 ? ~0ULL : ((1ULL << a) - 1); }
 
 }  // namespace gao

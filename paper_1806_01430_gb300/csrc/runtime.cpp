@@ -231,7 +231,20 @@ gao_status validate(const gao_loop* loops, int n_loops, const gao_buffer* bufs, 
                 if ((s = need_in(0))) return s;
                 if ((s = need_out(0, bufs[L.ins[0]].rows, bufs[L.ins[0]].cols, GAO_F32))) return s;
                 if (L.outs[0] == L.ins[0]) return fail(GAO_EINVAL, where + "STENCIL3 cannot run in place");
-                if (L.flags > 3) return fail(GAO_EINVAL, where + "unknown STENCIL3 preset " + std::to_string(L.flags));
+                if ((L.flags & ~GAO_LOOP_EXTERNAL_CALL) > 3)
+                    return fail(GAO_EINVAL, where + "unknown STENCIL3 preset " +
+                                                std::to_string(L.flags & ~GAO_LOOP_EXTERNAL_CALL));
+                break;
+            }
+            case GAO_LOOP_RECURRENCE: {
+                if ((s = need_in(0))) return s;
+                if ((s = need_out(0, bufs[L.ins[0]].rows, bufs[L.ins[0]].cols, GAO_F32))) return s;
+                if (L.outs[0] == L.ins[0]) return fail(GAO_EINVAL, where + "RECURRENCE cannot run in place");
+                break;
+            }
+            case GAO_LOOP_FIND: {
+                if ((s = need_in(0))) return s;
+                if ((s = need_out(0, bufs[L.ins[0]].rows, 1, GAO_F64))) return s;
                 break;
             }
             default:
@@ -351,6 +364,10 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
     if (opts) p->opts = *opts;
     if (p->opts.kchunk <= 0) p->opts.kchunk = default_kchunk(p->opts.gemm_prec);
     p->loops.assign(loops, loops + n_loops);
+    for (int i = 0; i < n_loops; ++i) {
+        p->verdict.push_back((int8_t)offload_verdict(loops[i]));
+        if (p->verdict.back() == GAO_OFFLOAD_OK) p->gene_loop.push_back(i);
+    }
     p->lay = plan(loops, n_loops, bufs, n_bufs, p->opts);
     auto bail = [&](gao_status st) {
         free_prog(p);
@@ -419,6 +436,21 @@ extern "C" gao_status prog_set_input(gao_prog* p, int buf, const void* host_src,
 }
 
 namespace gao {
+
+int offload_verdict(const gao_loop& L) {
+    if (L.flags & GAO_LOOP_EXTERNAL_CALL) return GAO_OFFLOAD_EXTERNAL_CALL;
+    if (L.kind == GAO_LOOP_RECURRENCE) return GAO_OFFLOAD_DEPENDENCE;
+    if (L.kind == GAO_LOOP_FIND) return GAO_OFFLOAD_EARLY_EXIT;
+    return GAO_OFFLOAD_OK;
+}
+
+uint64_t loop_mask_of(const gao_prog* p, uint64_t gene) {
+    uint64_t m = 0;
+    for (size_t k = 0; k < p->gene_loop.size(); ++k)
+        if ((gene >> k) & 1) m |= 1ULL << p->gene_loop[k];
+    return m;
+}
+
 
 // Make buffer b valid on the requested side, issuing a copy on the stream if needed.
 gao_status make_valid(RunCtx& R, int b, bool on_gpu, gao_loop_stat& stat) {
@@ -560,10 +592,14 @@ gao_status run_gpu_loop(RunCtx& R, int li) {
         }
         case GAO_LOOP_STENCIL3: {
             const gao_buffer& X = shp(L.ins[0]);
-            e = launch_stencil3(dptr(L.outs[0]), dptr(L.ins[0]), X.rows, X.cols, (int)L.flags, st);
+            e = launch_stencil3(dptr(L.outs[0]), dptr(L.ins[0]), X.rows, X.cols,
+                                (int)(L.flags & ~GAO_LOOP_EXTERNAL_CALL), st);
             nl += X.rows * X.cols > 0;
             break;
         }
+        case GAO_LOOP_RECURRENCE:
+        case GAO_LOOP_FIND:
+            return fail(GAO_EINVAL, "loop " + std::to_string(li) + " is not offloadable");
         default:
             return fail(GAO_EINVAL, "unknown loop kind");
     }
@@ -635,7 +671,17 @@ gao_status run_cpu_loop(RunCtx& R, int li) {
         }
         case GAO_LOOP_STENCIL3: {
             const gao_buffer& X = shp(L.ins[0]);
-            cpu_stencil3(hptr(L.outs[0]), hptr(L.ins[0]), X.rows, X.cols, (int)L.flags, c);
+            cpu_stencil3(hptr(L.outs[0]), hptr(L.ins[0]), X.rows, X.cols, (int)(L.flags & ~GAO_LOOP_EXTERNAL_CALL), c);
+            break;
+        }
+        case GAO_LOOP_RECURRENCE: {
+            const gao_buffer& X = shp(L.ins[0]);
+            cpu_recurrence(hptr(L.outs[0]), hptr(L.ins[0]), X.rows, X.cols, (float)L.alpha, c);
+            break;
+        }
+        case GAO_LOOP_FIND: {
+            const gao_buffer& X = shp(L.ins[0]);
+            cpu_find((double*)p->bufs[(size_t)L.outs[0]].host, hptr(L.ins[0]), X.rows, X.cols, (float)L.alpha, c);
             break;
         }
         default:
@@ -717,11 +763,13 @@ double ev_ms(cudaEvent_t a, cudaEvent_t b) {
 }
 }  // namespace
 
-extern "C" gao_status prog_run(gao_prog* p, uint64_t gene_mask, uint32_t flags, double* seconds_out) {
+extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, double* seconds_out) {
     if (!p) return fail(GAO_EINVAL, "program is null");
     const int n = (int)p->loops.size();
-    if (n < 64 && (gene_mask >> n) != 0)
-        return fail(GAO_EINVAL, "gene has bits set at or above the loop count (" + std::to_string(n) + ")");
+    const int a = gene_length(p);
+    if (a < 64 && (gene >> a) != 0)
+        return fail(GAO_EINVAL, "gene has bits set at or above the gene length (" + std::to_string(a) + ")");
+    const uint64_t gene_mask = loop_mask_of(p, gene);  // bit li: loop li runs on the GPU
     for (auto& B : p->bufs)
         if (B.d.role == GAO_BUF_INPUT && !B.input_set)
             return fail(GAO_EINVAL, "INPUT buffers must be set with prog_set_input before a run");
@@ -891,6 +939,24 @@ extern "C" gao_status prog_device_ptr(gao_prog* p, int buf, void** dev_ptr) {
     return GAO_OK;
 }
 
+extern "C" gao_status prog_gene_length(const gao_prog* p, int* length) {
+    if (!p || !length) return fail(GAO_EINVAL, "null argument");
+    *length = gene_length(p);
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_loop_offload(const gao_prog* p, int loop, int* verdict, int* gene_bit) {
+    if (!p) return fail(GAO_EINVAL, "program is null");
+    if (loop < 0 || loop >= (int)p->loops.size()) return fail(GAO_EINVAL, "no such loop");
+    if (verdict) *verdict = p->verdict[(size_t)loop];
+    if (gene_bit) {
+        *gene_bit = -1;
+        for (size_t k = 0; k < p->gene_loop.size(); ++k)
+            if (p->gene_loop[k] == loop) *gene_bit = (int)k;
+    }
+    return GAO_OK;
+}
+
 extern "C" gao_status prog_stats(gao_prog* p, gao_loop_stat* out, int n) {
     if (!p || !out) return fail(GAO_EINVAL, "null argument");
     if (n < (int)p->stats.size()) return fail(GAO_EINVAL, "stats array too short");
@@ -939,11 +1005,11 @@ gao_status gene_time(gao_prog* const* progs, int n_progs, uint64_t mask, double*
 
 gao_status check_progs(gao_prog* const* progs, int n_progs, int* n_genes) {
     if (!progs || n_progs < 1) return fail(GAO_EINVAL, "need at least one program");
-    const int a = (int)progs[0]->loops.size();
-    for (int i = 0; i < n_progs; ++i) {
+    for (int i = 0; i < n_progs; ++i)
         if (!progs[i]) return fail(GAO_EINVAL, "null program");
-        if ((int)progs[i]->loops.size() != a) return fail(GAO_EINVAL, "programs differ in gene length");
-    }
+    const int a = gene_length(progs[0]);
+    for (int i = 0; i < n_progs; ++i)
+        if (gene_length(progs[i]) != a) return fail(GAO_EINVAL, "programs differ in gene length");
     *n_genes = a;
     return GAO_OK;
 }
@@ -975,11 +1041,12 @@ extern "C" gao_status ga_run(gao_prog* const* progs, int n_progs, const gao_ga_p
     gao_status s = check_progs(progs, n_progs, &a);
     if (s != GAO_OK) return s;
     if (!params || !result) return fail(GAO_EINVAL, "null params or result");
+    if (a < 1) return fail(GAO_EINVAL, "no loop of the program is offloadable (gene length 0)");
     std::vector<double> saved((size_t)n_progs);
     for (int i = 0; i < n_progs; ++i) saved[(size_t)i] = progs[i]->opts.timeout_s;
     double budget = params->timeout_s;
     if (budget < 0.0) {  // automatic: 10 x the all-GPU time, capped at 60 s
-        const uint64_t all = a >= 64 ? ~0ULL : ((1ULL << a) - 1);
+        const uint64_t all = all_genes(a);
         double t = 0.0;
         for (int i = 0; i < n_progs; ++i) {
             double ti = 0.0;
@@ -1033,8 +1100,8 @@ extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, ga
             break;
         }
     if (li < 0) return fail(GAO_EINVAL, "program has no GEMM loop");
-    const int n = (int)p->loops.size();
-    const uint64_t all = n >= 64 ? ~0ULL : ((1ULL << n) - 1);
+    if (p->verdict[(size_t)li] != GAO_OFFLOAD_OK) return fail(GAO_EINVAL, "the program's GEMM loop is not offloadable");
+    const uint64_t all = all_genes(gene_length(p));
     double s0 = 0.0;
     gao_status st = prog_run(p, all, GAO_RUN_KEEP_DEVICE, &s0);  // puts the GEMM's inputs on the device
     if (st != GAO_OK) return st;

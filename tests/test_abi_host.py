@@ -96,6 +96,14 @@ def test_validation_rejects_malformed_programs(gao):
     # unknown loop kind
     e = _bad(gao, [B("X", 2, 2)], [L(W.INIT, [], [0]), L(42, [0], [0])])
     assert e.status == gao.GAO_EINVAL
+    # the loops kept on the CPU are validated like the others
+    e = _bad(gao, [B("X", 3, 5), B("k", 3, 1, W.F32)], [L(W.INIT, [], [0]), L(W.FIND, [0], [1], 0.5)])
+    assert e.status == gao.GAO_EINVAL and "expected 3x1" in str(e)
+    e = _bad(gao, [B("X", 3, 5)], [L(W.INIT, [], [0]), L(W.RECURRENCE, [0], [0], 0.5)])
+    assert e.status == gao.GAO_EINVAL and "in place" in str(e)
+    e = _bad(gao, [B("X", 4, 4), B("Y", 4, 4)],
+             [L(W.INIT, [], [0]), L(W.STENCIL3, [0], [1], flags=W.EXTERNAL_CALL | 5)])
+    assert e.status == gao.GAO_EINVAL and "preset" in str(e)
 
 
 @pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="a GPU is present")
