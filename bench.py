@@ -279,14 +279,19 @@ def our_arm(args, world, rank, local):
         ev0.record(stream)
         for _ in range(args.steps):
             gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
-            st = gao.prog_stats(p)
-            kern_ms.append(st[gemm_loop]["kernel_ms"])
-            launches += sum(s["launches"] for s in st)
-            for i, s_ in enumerate(st):
-                loop_ms[i] += s_["device_ms"]
         ev1.record(stream)
         torch.cuda.synchronize()
         t1 = clk.mark()
+        # per-loop CUDA-event times (kernel roofline, loop shares) from a second pass, so
+        # that reading the statistics stays out of the timed region
+        stat_steps = max(3, min(args.steps, 300))
+        for _ in range(stat_steps):
+            gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
+            st = gao.prog_stats(p)
+            kern_ms.append(st[gemm_loop]["kernel_ms"])
+            for i, s_ in enumerate(st):
+                loop_ms[i] += s_["device_ms"]
+        launches = sum(s_["launches"] for s_ in st) * args.steps  # the same kernels every step
         time.sleep(0.25)
     barrier(world)
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -299,9 +304,9 @@ def our_arm(args, world, rank, local):
     loop_gbs = {}
     for i, (lp, v, nb) in enumerate(zip(prog.loops, loop_ms, loop_bytes)):
         if lp.kind != W.GEMM and v > 0:
-            g = nb / (v / args.steps / 1e3) / 1e9
+            g = nb / (v / stat_steps / 1e3) / 1e9
             loop_gbs[f"L{i}_{W.KIND_NAMES[lp.kind]}"] = {"gbs": round(g, 1), "hbm_frac": round(g / hbm, 3)}
-    loop_ms = {f"L{i}_{W.KIND_NAMES[lp.kind]}": round(v / args.steps, 4) for i, (lp, v) in enumerate(zip(prog.loops, loop_ms))}
+    loop_ms = {f"L{i}_{W.KIND_NAMES[lp.kind]}": round(v / stat_steps, 4) for i, (lp, v) in enumerate(zip(prog.loops, loop_ms))}
 
     # accuracy of this run's GEMM against the oracle on sampled entries (no timing)
     err = None
@@ -393,15 +398,19 @@ def our_arm(args, world, rank, local):
     gemm_ms = statistics.mean(kern_ms)
     tc = prec != "fp32_simt"
     if tc:
-        peak = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
-        if prec == "fp8":
-            peak *= 2.0
+        bf16 = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        # peak of the kernel's own arithmetic: FP8 at the nominal 2x of bf16; a split
+        # variant spends PRODUCTS bf16 MMAs on every FP32-accurate multiply-add
+        peak = bf16 * 2.0 if prec == "fp8" else bf16 / PRODUCTS[prec]
         achieved = flops / (gemm_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_{prec}_n{n}.md"),
                 "kernel": f"gemm_tc ({prec})", "products": PRODUCTS[prec],
-                "hw_tflops": achieved * PRODUCTS[prec], "hw_frac": achieved * PRODUCTS[prec] / peak,
-                "peak_source": f"{pk['source']} bf16 sustained" + (" x2 (fp8 nominal ratio)" if prec == "fp8" else "")}
+                "hw_tflops": achieved * PRODUCTS[prec], "hw_frac": achieved * PRODUCTS[prec] / bf16,
+                "peak_source": f"{pk['source']} bf16 sustained" +
+                               (" x2 (fp8 nominal ratio)" if prec == "fp8" else
+                                f" / {PRODUCTS[prec]} (bf16 products per FP32-accurate product)"
+                                if PRODUCTS[prec] > 1 else "")}
     else:
         mhz = pk.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
@@ -457,13 +466,16 @@ def image_arm(args, world, rank, local):
         ev0.record(stream)
         for _ in range(args.steps):
             gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
-            st = gao.prog_stats(p)
-            launches += sum(s_["launches"] for s_ in st)
-            for i, s_ in enumerate(st):
-                loop_ms[i] += s_["device_ms"]
         ev1.record(stream)
         torch.cuda.synchronize()
         t1 = clk.mark()
+        stat_steps = max(3, min(args.steps, 300))  # per-loop event times, outside the timed region
+        for _ in range(stat_steps):
+            gao.prog_run(p, mask, gao.RUN_KEEP_DEVICE)
+            st = gao.prog_stats(p)
+            for i, s_ in enumerate(st):
+                loop_ms[i] += s_["device_ms"]
+        launches = sum(s_["launches"] for s_ in st) * args.steps
         time.sleep(0.25)
     barrier(world)
     ms = allmax(world, ev0.elapsed_time(ev1) / args.steps)
@@ -474,13 +486,13 @@ def image_arm(args, world, rank, local):
     loop_gbs, per_loop = {}, {}
     for i, (lp, v) in enumerate(zip(prog.loops, loop_ms)):
         key = f"L{i}_{W.KIND_NAMES[lp.kind]}"
-        per_loop[key] = round(v / args.steps, 4)
+        per_loop[key] = round(v / stat_steps, 4)
         if v > 0:
-            g = algorithmic_bytes(prog, lp) / (v / args.steps / 1e3) / 1e9
+            g = algorithmic_bytes(prog, lp) / (v / stat_steps / 1e3) / 1e9
             loop_gbs[key] = {"gbs": round(g, 1), "hbm_frac": round(g / hbm, 3)}
     # dominant kernel: the three stencil loops, 8 algorithmic bytes per pixel each
     st_idx = [i for i, lp in enumerate(prog.loops) if lp.kind == W.STENCIL3]
-    st_ms = sum(loop_ms[i] for i in st_idx) / (len(st_idx) * args.steps)
+    st_ms = sum(loop_ms[i] for i in st_idx) / (len(st_idx) * stat_steps)
     achieved = 8.0 * pixels / (st_ms / 1e3) / 1e9
     gao.prog_destroy(p)
 
