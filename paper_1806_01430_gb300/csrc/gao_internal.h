@@ -122,10 +122,17 @@ struct TcEvents {
 };
 size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K);
 struct TcFuse;
+// One row block of a larger GEMM (the split-precision paths): the scratch is laid out for
+// m_layout rows (the whole problem), and b_ready says that B's planes are already in it
+// (split by an earlier row block of the same problem).
+struct TcPart {
+    int64_t m_layout;
+    bool b_ready;
+};
 cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M,
                            int64_t N, int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
                            size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why,
-                           const TcFuse* fuse = nullptr);
+                           const TcFuse* fuse = nullptr, const TcPart* part = nullptr);
 
 // ---- CPU loops (binary32, OpenMP) ------------------------------------------------
 struct CpuCtx {

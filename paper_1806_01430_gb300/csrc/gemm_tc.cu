@@ -938,7 +938,7 @@ size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K) {
 cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
                            int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
                            size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why,
-                           const TcFuse* fuse) {
+                           const TcFuse* fuse, const TcPart* part) {
     ev.launches = 0;
     if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_FP8) {
         if (why) *why = "precision not available on the tensor-core path";
@@ -962,21 +962,28 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     }
     if (!get_encode(why)) return cudaErrorNotSupported;
     if (prec == GAO_GEMM_FP8) {
-        if (fuse) {
-            if (why) *why = "chains are not fused on the FP8 path";
+        if (fuse || part) {
+            if (why) *why = "chains and row blocks are not supported on the FP8 path";
             return cudaErrorInvalidValue;
         }
         return launch_gemm_fp8(C, A, B, C0, M, N, K, alpha, beta, tc_group_of(tile_cfg), scratch, scratch_bytes, err,
                                st, ev, why);
     }
     const int P = planes_of(prec);
+    const int64_t Mlay = part ? part->m_layout : M;
+    if (Mlay < M || (part && fuse)) {
+        if (why) *why = "bad row-block arguments";
+        return cudaErrorInvalidValue;
+    }
     const int64_t Mp = ru(M, BM), Np = ru(N, 256), Kp = ru(K, BK);
-    if (tc_scratch_bytes(prec, M, N, K) > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
+    if (tc_scratch_bytes(prec, Mlay, N, K) > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
         if (why) *why = "tensor-core scratch too small or misaligned";
         return cudaErrorInvalidValue;
     }
+    // A's planes ([P][Mp][Kp], this call's rows) at the start; B's ([P][Np][Kp]) after
+    // room for the whole problem's A planes, so that row blocks can share them
     __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(scratch);
-    __nv_bfloat16* pb = pa + (size_t)P * Mp * Kp;
+    __nv_bfloat16* pb = pa + (size_t)P * ru(Mlay, BM) * Kp;
     const int sms = sm_count();
     {
         const int64_t work = Mp * (Kp / 8);
@@ -987,14 +994,17 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         else split_rows_kernel<1><<<(unsigned)g, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)(Np / 64), (unsigned)(Kp / 64));
-        if (grid.y > 65535u) return cudaErrorInvalidValue;
-        if (P == 3) split_cols_kernel<3><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-        else if (P == 2) split_cols_kernel<2><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-        else split_cols_kernel<1><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        ev.launches += 2;
+        ev.launches += 1;
+        if (!(part && part->b_ready)) {
+            dim3 grid((unsigned)(Np / 64), (unsigned)(Kp / 64));
+            if (grid.y > 65535u) return cudaErrorInvalidValue;
+            if (P == 3) split_cols_kernel<3><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+            else if (P == 2) split_cols_kernel<2><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+            else split_cols_kernel<1><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            ev.launches += 1;
+        }
     }
     const int num_kb = (int)(Kp / BK);
     int chunk_kb = num_kb;
@@ -1012,13 +1022,13 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     if (!make_map(&tb, pb, Kp, (int64_t)P * Np, bn, false, why)) return cudaErrorInvalidValue;
     EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
                (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, nullptr, nullptr, 0, 0};
-    double* part = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, M, N, K));
+    double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, M, N, K));
     if (fuse) {
         ep.X = fuse->X;
         ep.D = fuse->D;
         ep.E = fuse->E;
         ep.alpha2 = fuse->alpha2;
-        ep.frob_part = fuse->frob_out ? part : nullptr;
+        ep.frob_part = fuse->frob_out ? fpart : nullptr;
         ep.fuse = 1;
     }
     if (ev.k0) cudaEventRecord(ev.k0, st);
@@ -1041,7 +1051,7 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     if (ev.k1) cudaEventRecord(ev.k1, st);
     if (fuse && fuse->frob_out) {
         const int64_t tiles = (Mp / BM) * ((N + bn - 1) / bn);
-        frob_partials_kernel<<<1, 256, 0, st>>>(part, tiles * kEpiWarps, fuse->frob_out);
+        frob_partials_kernel<<<1, 256, 0, st>>>(fpart, tiles * kEpiWarps, fuse->frob_out);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ev.launches += 1;
     }

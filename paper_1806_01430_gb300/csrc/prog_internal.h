@@ -48,11 +48,16 @@ struct gao_prog {
     std::vector<uint8_t> ev_used;  // bit 0 copies, bit 1 loop, bit 2 kernel
     std::unordered_map<uint64_t, gao::CacheEntry> cache;
     bool dirty_stream = false;  // a previous run left work in flight
+    cudaStream_t cst = nullptr;           // copy stream of the copy/compute overlap
+    std::vector<cudaEvent_t> pipe_ev;     // its events: fork, B landed, one per row block
     std::vector<int8_t> verdict;  // gao_offload of every loop
     std::vector<int> gene_loop;   // gene bit k -> index of the k-th offloadable loop
 };
 
 namespace gao {
+
+constexpr int kMaxRowBlocks = 4;                 // row blocks of an overlapped GEMM loop
+constexpr size_t kPipelineMinBytes = 16u << 20;  // smallest A worth overlapping
 
 // One execution of a program (or of a batch of programs sharing a stream).
 struct RunCtx {

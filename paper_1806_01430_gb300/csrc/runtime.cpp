@@ -328,8 +328,12 @@ void free_prog(gao_prog* p) {
     for (auto& b : p->bufs)
         if (b.host) cudaFreeHost(b.host);
     if (p->h_err) cudaFreeHost(p->h_err);
+    if (p->cst) cudaStreamSynchronize(p->cst);
     for (auto e : p->ev)
         if (e) cudaEventDestroy(e);
+    for (auto e : p->pipe_ev)
+        if (e) cudaEventDestroy(e);
+    if (p->cst) cudaStreamDestroy(p->cst);
     if (p->own_arena && p->arena) cudaFree(p->arena);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
     delete p;
@@ -412,6 +416,13 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
     p->ev.assign((size_t)n_loops * 6, nullptr);
     for (auto& ev : p->ev) {
         e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    }
+    e = cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate(copy stream)"));
+    p->pipe_ev.assign(2 + kMaxRowBlocks, nullptr);
+    for (auto& ev : p->pipe_ev) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
     }
     p->ev_used.assign((size_t)n_loops, 0);
@@ -756,6 +767,89 @@ gao_status run_gpu_chain(RunCtx& R, int li, const Chain& ch) {
     return GAO_OK;
 }
 
+// Copy/compute overlap for a GPU GEMM loop whose A has to come from the host (the
+// host-to-device link, ~210 GB/s on this machine, is 30x slower than HBM): B is copied
+// first, then A and C0 in row blocks on a copy stream, and each row block's split and
+// tensor-core GEMM start as soon as its rows have landed, while the next block is still
+// on the link.  Row blocks give the same bits as one launch (every output is formed the
+// same way); only the split precisions take this path.
+int64_t pipeline_blocks(const gao_prog* p, const gao_loop& L) {
+    const int prec = p->opts.gemm_prec;
+    if (L.kind != GAO_LOOP_GEMM) return 0;
+    if (prec != GAO_GEMM_BF16 && prec != GAO_GEMM_BF16X3 && prec != GAO_GEMM_BF16X6) return 0;
+    if (L.ins[0] == L.ins[1] || L.ins[2] == L.ins[0] || L.ins[2] == L.ins[1]) return 0;
+    const BufState& A = p->bufs[(size_t)L.ins[0]];
+    const gao_buffer& B = p->bufs[(size_t)L.ins[1]].d;
+    if (A.vd || A.bytes < kPipelineMinBytes || A.d.cols <= 0 || B.cols <= 0) return 0;
+    const int64_t blocks = std::min<int64_t>(kMaxRowBlocks, A.d.rows / 256);
+    return blocks >= 2 ? blocks : 0;
+}
+
+gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks) {
+    gao_prog* p = R.p;
+    const gao_loop& L = p->loops[(size_t)li];
+    gao_loop_stat& S = p->stats[(size_t)li];
+    BufState &A = p->bufs[(size_t)L.ins[0]], &B = p->bufs[(size_t)L.ins[1]];
+    const bool use_c0 = L.ins[2] >= 0 && L.beta != 0.0;
+    BufState* C0 = use_c0 ? &p->bufs[(size_t)L.ins[2]] : nullptr;
+    BufState& C = p->bufs[(size_t)L.outs[0]];
+    if (!A.vh || !(B.vd || B.vh) || (C0 && !(C0->vd || C0->vh)))
+        return fail(GAO_EINVAL, "a GEMM input holds no data");
+    const int64_t M = A.d.rows, K = A.d.cols, N = B.d.cols;
+    const int64_t rows = ((M + blocks - 1) / blocks + 127) / 128 * 128;
+    cudaStream_t st = R.st, cs = p->cst;
+    cudaEvent_t* ev = &p->ev[(size_t)li * 6];
+    cudaEvent_t fork = p->pipe_ev[0], b_done = p->pipe_ev[1];
+    GAO_CUDA_TRY(cudaEventRecord(fork, st));  // the copies overwrite device buffers: after earlier work
+    GAO_CUDA_TRY(cudaStreamWaitEvent(cs, fork, 0));
+    GAO_CUDA_TRY(cudaEventRecord(ev[0], cs));
+    if (!B.vd) {
+        GAO_CUDA_TRY(cudaMemcpyAsync(B.dev, B.host, B.bytes, cudaMemcpyHostToDevice, cs));
+        S.h2d_bytes += B.bytes;
+    }
+    GAO_CUDA_TRY(cudaEventRecord(b_done, cs));
+    const bool copy_c0 = C0 && !C0->vd;
+    int nb = 0;
+    for (int64_t r0 = 0; r0 < M; r0 += rows, ++nb) {
+        const int64_t r1 = std::min(M, r0 + rows);
+        const size_t off_a = (size_t)r0 * K * 4, len_a = (size_t)(r1 - r0) * K * 4;
+        GAO_CUDA_TRY(cudaMemcpyAsync(A.dev + off_a, (char*)A.host + off_a, len_a, cudaMemcpyHostToDevice, cs));
+        S.h2d_bytes += len_a;
+        if (copy_c0) {
+            const size_t off_c = (size_t)r0 * N * 4, len_c = (size_t)(r1 - r0) * N * 4;
+            GAO_CUDA_TRY(
+                cudaMemcpyAsync(C0->dev + off_c, (char*)C0->host + off_c, len_c, cudaMemcpyHostToDevice, cs));
+            S.h2d_bytes += len_c;
+        }
+        GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + (size_t)nb], cs));
+    }
+    GAO_CUDA_TRY(cudaEventRecord(ev[1], cs));
+    GAO_CUDA_TRY(cudaEventRecord(ev[2], st));
+    GAO_CUDA_TRY(cudaStreamWaitEvent(st, b_done, 0));
+    const float beta = C0 ? (float)L.beta : 0.0f;
+    int i = 0;
+    for (int64_t r0 = 0; r0 < M; r0 += rows, ++i) {
+        const int64_t r1 = std::min(M, r0 + rows);
+        GAO_CUDA_TRY(cudaStreamWaitEvent(st, p->pipe_ev[2 + (size_t)i], 0));
+        TcPart part{M, i > 0};
+        TcEvents tev{i == 0 ? ev[4] : nullptr, i == nb - 1 ? ev[5] : nullptr, 0};
+        std::string why;
+        float* c = (float*)C.dev + (size_t)r0 * N;
+        const float* c0 = C0 ? (const float*)C0->dev + (size_t)r0 * N : c;
+        cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, c, (const float*)A.dev + (size_t)r0 * K,
+                                       (const float*)B.dev, c0, r1 - r0, N, K, (float)L.alpha, beta, p->opts.kchunk,
+                                       p->opts.tile_cfg, p->arena + p->lay.tc_off, p->lay.tc_bytes,
+                                       (int*)(p->arena + p->lay.err_off), st, tev, &why, nullptr, &part);
+        if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "row-block GEMM") : fail(GAO_EINVAL, why);
+        S.launches += tev.launches;
+    }
+    GAO_CUDA_TRY(cudaEventRecord(ev[3], st));
+    A.vd = B.vd = true;
+    if (C0) C0->vd = true;
+    p->ev_used[(size_t)li] |= 1 | 2 | 4;
+    return GAO_OK;
+}
+
 double ev_ms(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.0;
@@ -840,7 +934,10 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
         const bool per_loop = p->opts.transfer_mode == GAO_TRANSFER_PER_LOOP;
         if (gpu && per_loop)  // directive offload without a data region: inputs always copied in
             for (int b : ins) p->bufs[(size_t)b].vd = false;
-        if (gpu) {
+        const int64_t blocks = gpu ? pipeline_blocks(p, L) : 0;
+        if (blocks > 0) {
+            if ((status = run_gpu_gemm_pipelined(R, li, blocks)) != GAO_OK) break;
+        } else if (gpu) {
             bool copies = false;
             for (int b : ins) copies |= !p->bufs[(size_t)b].vd;
             if (copies) GAO_CUDA_TRY(cudaEventRecord(ev[0], p->st));

@@ -167,6 +167,33 @@ def test_twelve_loop_program(gao, m, k):
         assert abs(out["s"] - s_ref) <= 1e-6 * float(np.abs(P).astype(np.float64).sum())
 
 
+@pytest.mark.parametrize("n,prec", [(2048, "BF16X6"), (2500, "BF16X3"), (2304, "BF16")])
+def test_overlapped_host_gemm_is_bit_identical(gao, n, prec):
+    """A GEMM loop whose A comes from the host runs in row blocks overlapped with the copy;
+    its C must carry the same bits as the one-launch GEMM on device-resident inputs."""
+    seed = 91
+    pr = getattr(gao, prec)
+    dev = W.six_loop(n, seed, outputs=("C", "r", "f"))
+    p = gao.prog_from_workload(dev, gemm_prec=pr)
+    gao.prog_run(p, 0b111111)
+    C_dev = gao.prog_output(p, dev.index("C")).copy()
+    r_dev = gao.prog_output(p, dev.index("r")).copy()
+    gao.prog_run(p, 0b111110)  # INIT on the CPU: A, B and C reach the GEMM from the host
+    st = gao.prog_stats(p)
+    assert st[1]["h2d_bytes"] == 3 * n * n * 4
+    C_mix = gao.prog_output(p, dev.index("C"))
+    assert np.array_equal(C_mix.view(np.uint32), C_dev.view(np.uint32))
+    assert np.array_equal(gao.prog_output(p, dev.index("r")), r_dev)
+    gao.prog_destroy(p)
+    hp = W.host_input_program(n, seed, outputs=("C", "r", "f"))
+    q = gao.prog_from_workload(hp, gemm_prec=pr)
+    for nm, b in (("A", 0), ("B", 1), ("C0", 2)):
+        gao.prog_set_input(q, hp.index(nm), oracle.init_matrix(seed, b, n, n).astype(np.float32))
+    gao.prog_run(q, (1 << hp.n_loops) - 1)
+    assert np.array_equal(gao.prog_output(q, hp.index("C")).view(np.uint32), C_dev.view(np.uint32))
+    gao.prog_destroy(q)
+
+
 def test_host_input_program_matches(gao):
     n, seed = 160, 77
     prog = W.host_input_program(n, seed, outputs=("C", "r", "f"))
