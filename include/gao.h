@@ -143,10 +143,11 @@ typedef struct gao_opts {
                                 (NULL: the library allocates it); must outlive the program */
     uint64_t dev_arena_bytes;
     int32_t transfer_mode;   /* GAO_TRANSFER_RESIDENT or GAO_TRANSFER_PER_LOOP               */
-    int32_t fuse_chains;     /* 1: when a gene puts a chain GEMM -> AXPY(C + a X) -> TRANSPOSE
-                                [-> FROBENIUS of the transpose] on the GPU (tensor-core BF16
-                                precisions, resident transfers), run it as one pass: the GEMM's
-                                epilogue writes C, D and E and the norm's partial sums     */
+    int32_t fuse_chains;     /* GAO_FUSE_*: whether a chain GEMM -> AXPY(C + a X) -> TRANSPOSE
+                                [-> FROBENIUS of the transpose] that a gene puts on the GPU
+                                (tensor-core BF16 precisions, resident transfers) runs as one
+                                pass: the GEMM's epilogue writes C, D and E and the norm's
+                                partial sums                                                */
 } gao_opts;
 
 /* Data movement between host and device under a gene (Sec. 2 and Sec. 3.3: CPU-GPU
@@ -156,6 +157,14 @@ typedef struct gao_opts {
  *             offload without a data region does (the paper's measured setting). */
 #define GAO_TRANSFER_RESIDENT 0
 #define GAO_TRANSFER_PER_LOOP 1
+
+/* Loop-chain fusion: never, whenever the chain is on the GPU, or as the gene decides:
+ * GAO_FUSE_GENE adds one bit to the gene, after the loop bits (bit a-1 of a gene of
+ * length a), so that the GA chooses fusion like any placement (loop combinations decide
+ * the time, Sec. 3.3). */
+#define GAO_FUSE_OFF 0
+#define GAO_FUSE_ON 1
+#define GAO_FUSE_GENE 2
 
 typedef struct gao_prog gao_prog;
 
@@ -203,7 +212,7 @@ typedef struct gao_loop_stat {
     uint64_t d2h_bytes; /* bytes copied device->host before the loop                   */
 } gao_loop_stat;
 
-/* Gene length a: the number of offloadable loops (Sec. 4). */
+/* Gene length a: the number of offloadable loops (Sec. 4), plus one with GAO_FUSE_GENE. */
 gao_status prog_gene_length(const gao_prog *p, int *length);
 
 /* Classification of loop `loop`: *verdict = gao_offload, *gene_bit = its bit in the gene,

@@ -35,6 +35,7 @@ FP32_SIMT, BF16, BF16X3, BF16X6, FP8 = range(5)
 PREC_NAMES = ["fp32_simt", "bf16", "bf16x3", "bf16x6", "fp8"]
 RUN_KEEP_DEVICE = 1
 TRANSFER_RESIDENT, TRANSFER_PER_LOOP = 0, 1
+FUSE_OFF, FUSE_ON, FUSE_GENE = 0, 1, 2
 MAX_IO = 4
 
 
@@ -194,10 +195,10 @@ def _marshal(buffers, loops):
 
 
 def _opts(seed, gemm_prec, kchunk, tile_cfg, cpu_threads, timeout_s, stream, arena_ptr, arena_bytes,
-          transfer_mode=TRANSFER_RESIDENT, fuse_chains=False):
+          transfer_mode=TRANSFER_RESIDENT, fuse_chains=FUSE_OFF):
     o = gao_opts()
     o.transfer_mode = int(transfer_mode)
-    o.fuse_chains = 1 if fuse_chains else 0
+    o.fuse_chains = int(fuse_chains)  # False/True or FUSE_OFF/FUSE_ON/FUSE_GENE
     o.gemm_prec, o.kchunk, o.tile_cfg, o.cpu_threads = int(gemm_prec), int(kchunk), int(tile_cfg), int(cpu_threads)
     o.seed, o.timeout_s = int(seed), float(timeout_s)
     o.stream = _stream_handle(stream)
@@ -236,7 +237,7 @@ def prog_device_bytes(buffers, loops, seed=0, gemm_prec=FP32_SIMT, kchunk=0, til
 
 def prog_create(buffers, loops, seed: int = 0, gemm_prec: int = FP32_SIMT, kchunk: int = 0, tile_cfg: int = 0,
                 cpu_threads: int = 0, timeout_s: float = 0.0, stream=None, arena=None,
-                transfer_mode: int = TRANSFER_RESIDENT, fuse_chains: bool = False) -> Prog:
+                transfer_mode: int = TRANSFER_RESIDENT, fuse_chains: int = FUSE_OFF) -> Prog:
     """Declare a program.  ``buffers``/``loops`` are sequences of objects with the
     gao_buffer / gao_loop fields (e.g. workloads.Buffer / workloads.Loop).  ``arena``:
     optional device memory (a torch uint8 CUDA tensor, or (ptr, bytes))."""

@@ -253,6 +253,8 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
         if (p->opts.gemm_prec != p0->opts.gemm_prec) return fail(GAO_EINVAL, "batch programs differ in GEMM precision");
         if (p->opts.transfer_mode != GAO_TRANSFER_RESIDENT)
             return fail(GAO_EINVAL, "batches keep buffers resident (transfer_mode RESIDENT only)");
+        if (p->opts.fuse_chains != GAO_FUSE_OFF)
+            return fail(GAO_EINVAL, "batches run loop by loop (fuse_chains must be GAO_FUSE_OFF)");
         for (auto& B : p->bufs)
             if (B.d.role == GAO_BUF_INPUT && !B.input_set) return fail(GAO_EINVAL, "INPUT buffers must be set first");
         for (int j = 0; j < i; ++j)

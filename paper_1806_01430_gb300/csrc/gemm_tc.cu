@@ -231,72 +231,129 @@ static_assert(prod_a(3, 0) == 0 && prod_b(3, 0) == 0 && prod_a(3, 1) == 0 && pro
 // C0 and X are read through the non-coherent read-only path: within the kernel every
 // element of C0 is read once, by the thread that later overwrites it when C aliases C0,
 // and X is never written, so these loads need not wait behind earlier stores.
-__device__ __forceinline__ void store_row32(const EpiArgs& e, int64_t grow, int64_t gcol, const float* v,
-                                            double* sq = nullptr) {
-    if (grow >= e.M) return;
-    float* crow = e.C + grow * (int64_t)e.N;
-    const float* c0row = e.C0 + grow * (int64_t)e.N;
+// Shared-memory staging of the epilogue: one 32 x 16 binary32 block per warp, rows 80
+// bytes apart, so that both the row-per-lane writes and the row-major reads are free of
+// bank conflicts (one two-way conflict on the reads).
+constexpr int kStgStride = 20;                       // floats per staged row
+constexpr uint32_t kStgBytes = 32 * kStgStride * 4;  // per epilogue warp
+
+// Final values of 32 columns [gcol, gcol + 32) of the warp's 32 rows (row0 + lane holds
+// v[0..31], a row per lane as tensor memory delivers them): alpha v + beta C0 stored to C,
+// and for a fused chain D = C + alpha2 X, E = D^T and the running sum of D^2.  Each 32 x 16
+// half goes through the warp's staging block and is then handled row-major, four
+// consecutive columns per lane, so that C0, X, C and D move in full 64-byte row segments;
+// every element is formed with the same operations as in the separate loops.
+__device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, int64_t gcol, const float* v,
+                                               float* stg, int lane, double* sq) {
     const bool fuse = e.fuse != 0;
-    const float* xrow = fuse ? e.X + grow * (int64_t)e.N : nullptr;
-    float* drow = fuse ? e.D + grow * (int64_t)e.N : nullptr;
     float s2 = 0.0f, s3 = 0.0f;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int64_t c = gcol + 4 * u;
-        float cv[4], xv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        const bool full = e.vec && c + 3 < e.N;
-        if (full) {
-            float4 c0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (e.beta != 0.0f) c0 = __ldg(reinterpret_cast<const float4*>(c0row + c));
-            if (fuse) {
-                const float4 x = __ldg(reinterpret_cast<const float4*>(xrow + c));
-                xv[0] = x.x, xv[1] = x.y, xv[2] = x.z, xv[3] = x.w;
-            }
-            cv[0] = e.alpha * v[4 * u + 0];
-            cv[1] = e.alpha * v[4 * u + 1];
-            cv[2] = e.alpha * v[4 * u + 2];
-            cv[3] = e.alpha * v[4 * u + 3];
-            if (e.beta != 0.0f) {
-                cv[0] = fmaf(e.beta, c0.x, cv[0]);
-                cv[1] = fmaf(e.beta, c0.y, cv[1]);
-                cv[2] = fmaf(e.beta, c0.z, cv[2]);
-                cv[3] = fmaf(e.beta, c0.w, cv[3]);
-            }
-            *reinterpret_cast<float4*>(crow + c) = make_float4(cv[0], cv[1], cv[2], cv[3]);
-        } else {
+    for (int h = 0; h < 2; ++h) {
+        __syncwarp();  // the previous half's reads are done
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                cv[q] = 0.0f;
-                if (c + q < e.N) {
-                    float o = e.alpha * v[4 * u + q];
-                    if (e.beta != 0.0f) o = fmaf(e.beta, __ldg(c0row + c + q), o);
-                    cv[q] = o;
-                    if (fuse) xv[q] = __ldg(xrow + c + q);
-                    crow[c + q] = o;
+        for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<float4*>(stg + lane * kStgStride + 4 * j) =
+                make_float4(v[16 * h + 4 * j], v[16 * h + 4 * j + 1], v[16 * h + 4 * j + 2], v[16 * h + 4 * j + 3]);
+        __syncwarp();
+        const int cq = lane & 3;
+        const int64_t c = gcol + 16 * h + 4 * cq;
+        const bool vec = e.vec && c + 3 < e.N;
+        // all of this half's full-width C0 (and X) loads in flight before any is used
+        float4 c0p[4], xp[4];
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int64_t grow = row0 + it * 8 + (lane >> 2);
+            c0p[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            xp[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (vec && grow < e.M) {
+                const int64_t base = grow * (int64_t)e.N + c;
+                if (e.beta != 0.0f) c0p[it] = __ldg(reinterpret_cast<const float4*>(e.C0 + base));
+                if (fuse) xp[it] = __ldg(reinterpret_cast<const float4*>(e.X + base));
+            }
+        }
+        float dd[4][4];  // fused chain: this lane's D values, staged back for the transposed store
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int r = it * 8 + (lane >> 2);
+            const int64_t grow = row0 + r;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dd[it][q] = 0.0f;
+            if (grow >= e.M) continue;
+            const float4 a = *reinterpret_cast<const float4*>(stg + r * kStgStride + 4 * cq);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const int64_t base = grow * (int64_t)e.N + c;
+            const bool full = vec;
+            float cv[4], xv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (full) {
+                const float4 c0 = c0p[it];
+                if (fuse) xv[0] = xp[it].x, xv[1] = xp[it].y, xv[2] = xp[it].z, xv[3] = xp[it].w;
+                const float c0v[4] = {c0.x, c0.y, c0.z, c0.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    cv[q] = e.alpha * av[q];
+                    if (e.beta != 0.0f) cv[q] = fmaf(e.beta, c0v[q], cv[q]);
+                }
+                *reinterpret_cast<float4*>(e.C + base) = make_float4(cv[0], cv[1], cv[2], cv[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    cv[q] = 0.0f;
+                    if (c + q < e.N) {
+                        float o = e.alpha * av[q];
+                        if (e.beta != 0.0f) o = fmaf(e.beta, __ldg(e.C0 + base + q), o);
+                        cv[q] = o;
+                        if (fuse) xv[q] = __ldg(e.X + base + q);
+                        e.C[base + q] = o;
+                    }
+                }
+            }
+            if (fuse) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dd[it][q] = fmaf(e.alpha2, xv[q], cv[q]);  // D = C + alpha2 X, one rounding
+                if (full) {
+                    *reinterpret_cast<float4*>(e.D + base) = make_float4(dd[it][0], dd[it][1], dd[it][2], dd[it][3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (c + q < e.N) e.D[base + q] = dd[it][q];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (c + q < e.N) {
+                        if (q & 1) s3 = fmaf(dd[it][q], dd[it][q], s3);
+                        else s2 = fmaf(dd[it][q], dd[it][q], s2);
+                    }
                 }
             }
         }
         if (fuse) {
-            float d[4];
+            // E = D^T: D goes back through the staging block, then each lane writes its own
+            // row's 16 values down 16 columns of E, so that every store covers 32 rows of
+            // E in one 128-byte segment
+            __syncwarp();
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d[q] = fmaf(e.alpha2, xv[q], cv[q]);  // D = C + alpha2 X, one rounding
-            if (full) {
-                *reinterpret_cast<float4*>(drow + c) = make_float4(d[0], d[1], d[2], d[3]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (c + q < e.N) drow[c + q] = d[q];
+            for (int it = 0; it < 4; ++it) {
+                const int r = it * 8 + (lane >> 2);
+                *reinterpret_cast<float4*>(stg + r * kStgStride + 4 * cq) =
+                    make_float4(dd[it][0], dd[it][1], dd[it][2], dd[it][3]);
             }
+            __syncwarp();
+            const int64_t grow = row0 + lane;
+            if (grow < e.M) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (c + q < e.N) {
-                    e.E[(c + q) * (int64_t)e.M + grow] = d[q];
-                    if (q & 1) s3 = fmaf(d[q], d[q], s3);
-                    else s2 = fmaf(d[q], d[q], s2);
+                for (int j = 0; j < 4; ++j) {
+                    const float4 d = *reinterpret_cast<const float4*>(stg + lane * kStgStride + 4 * j);
+                    const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int64_t col = gcol + 16 * h + 4 * j + q;
+                        if (col < e.N) e.E[col * (int64_t)e.M + grow] = dv[q];
+                    }
                 }
             }
         }
     }
+    __syncwarp();  // the staging block is free for the caller's next group
     if (fuse) *sq += (double)s2 + (double)s3;
 }
 
@@ -315,7 +372,9 @@ struct TcCfg {
     static constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256
                                                                                                               : 512;
     static constexpr uint32_t NBARS = 2 * STAGES + 2 * ACC + 1;
-    static constexpr size_t SMEM = 1024 /*align slack*/ + (size_t)STAGES * STAGE + 8 * NBARS + 16;
+    static constexpr uint32_t STG = kEpiWarps * kStgBytes;  // epilogue staging blocks
+    static constexpr size_t SMEM = 1024 /*align slack*/ + (size_t)STAGES * STAGE + STG + 8 * NBARS + 16;
+    static_assert(SMEM <= 232448, "shared memory per CTA");
     static_assert(COLS <= 512, "accumulators exceed tensor memory");
     static_assert(BN % 64 == 0 && BN >= 64 && BN <= 256, "BN");
     static_assert(!CHUNKED || BN <= 128, "chunked sums live in registers: BN <= 128");
@@ -405,7 +464,8 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const uint32_t tiles = smem_u32(smem);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)STAGES * Cfg::STAGE);
+    float* stg_all = reinterpret_cast<float*>(smem + (size_t)STAGES * Cfg::STAGE);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)STAGES * Cfg::STAGE + Cfg::STG);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + Cfg::NBARS);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const uint32_t bar0 = smem_u32(bars);
@@ -546,6 +606,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
         const int half = ew >> 2;
         const int colbase = half * (BN / 2);
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        float* stg = stg_all + ew * (kStgBytes / 4);
         constexpr int G = BN / 2 / 32;  // 32-column groups per thread
         int gc = 0;
         bool ok = true;
@@ -554,7 +615,8 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
             src.get(t, ti);
             const EpiArgs& ep = ti.ep;
             const int nchunks = (ti.num_kb + ti.chunk_kb - 1) / ti.chunk_kb;
-            const int64_t grow = (int64_t)ti.m0 + q * 32 + lane;
+            const int64_t row0 = (int64_t)ti.m0 + q * 32;
+            const int64_t grow = row0 + lane;
             const int n0 = ti.n0;
             double sq = 0.0;  // fused chain: this thread's sum of D^2 over the tile
             float sum[CHUNKED ? BN / 2 : 1];
@@ -573,7 +635,8 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                         if (ep.fuse) prefetch_l2(ep.X + off + k);
                     }
                 }
-                if (!mbar_wait(accf_bar(ab), aph, abort_flag, err)) {
+                // warp-uniform outcome: the stores below synchronise the warp
+                if (!__all_sync(0xffffffffu, mbar_wait(accf_bar(ab), aph, abort_flag, err))) {
                     ok = false;
                     break;
                 }
@@ -610,7 +673,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
 #pragma unroll
                         for (int i = 0; i < 32; ++i) sum[g * 32 + i] += v[i];
                     } else {
-                        store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, v, &sq);
+                        store_staged32(ep, row0, (int64_t)n0 + colbase + g * 32, v, stg, lane, &sq);
                     }
                 }
                 tc_fence_before();
@@ -621,7 +684,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                 if (ok) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        store_row32(ep, grow, (int64_t)n0 + colbase + g * 32, sum + g * 32, &sq);
+                        store_staged32(ep, row0, (int64_t)n0 + colbase + g * 32, sum + g * 32, stg, lane, &sq);
                 }
             }
             if (ep.fuse && ok) {  // fixed butterfly over the warp's rows, one partial per warp

@@ -79,7 +79,14 @@ gao_status check_device(int* dev_out);
 // Parallelisability of one loop (gao_offload), and the loop placement of a gene.
 int offload_verdict(const gao_loop& L);
 uint64_t loop_mask_of(const gao_prog* p, uint64_t gene);
-inline int gene_length(const gao_prog* p) { return (int)p->gene_loop.size(); }
+inline int gene_length(const gao_prog* p) {
+    return (int)p->gene_loop.size() + (p->opts.fuse_chains == GAO_FUSE_GENE ? 1 : 0);
+}
+// Whether a run under `gene` fuses loop chains.
+inline bool gene_fuses(const gao_prog* p, uint64_t gene) {
+    if (p->opts.fuse_chains == GAO_FUSE_ON) return true;
+    return p->opts.fuse_chains == GAO_FUSE_GENE && ((gene >> p->gene_loop.size()) & 1);
+}
 inline uint64_t all_genes(int a) { return a >= 64 ? ~0ULL : ((1ULL << a) - 1); }
 
 }  // namespace gao

@@ -122,7 +122,8 @@ gao_status validate(const gao_loop* loops, int n_loops, const gao_buffer* bufs, 
         return fail(GAO_EINVAL, "unknown gemm_prec");
     if (opts && opts->transfer_mode != GAO_TRANSFER_RESIDENT && opts->transfer_mode != GAO_TRANSFER_PER_LOOP)
         return fail(GAO_EINVAL, "unknown transfer_mode");
-    if (opts && opts->fuse_chains != 0 && opts->fuse_chains != 1) return fail(GAO_EINVAL, "fuse_chains must be 0 or 1");
+    if (opts && (opts->fuse_chains < GAO_FUSE_OFF || opts->fuse_chains > GAO_FUSE_GENE))
+        return fail(GAO_EINVAL, "fuse_chains must be GAO_FUSE_OFF, GAO_FUSE_ON or GAO_FUSE_GENE");
     for (int b = 0; b < n_bufs; ++b) {
         const gao_buffer& d = bufs[b];
         if (d.rows < 0 || d.cols < 0) return fail(GAO_EINVAL, "buffer " + std::to_string(b) + ": negative shape");
@@ -713,8 +714,8 @@ struct Chain {
     int axpy = -1, transpose = -1, frob = -1;
 };
 
-bool find_chain(const gao_prog* p, int li, uint64_t mask, Chain* ch) {
-    if (!p->opts.fuse_chains || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT) return false;
+bool find_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, Chain* ch) {
+    if (!fuse || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT) return false;
     const int prec = p->opts.gemm_prec;
     if (prec != GAO_GEMM_BF16 && prec != GAO_GEMM_BF16X3 && prec != GAO_GEMM_BF16X6) return false;
     const int n = (int)p->loops.size();
@@ -864,6 +865,7 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
     if (a < 64 && (gene >> a) != 0)
         return fail(GAO_EINVAL, "gene has bits set at or above the gene length (" + std::to_string(a) + ")");
     const uint64_t gene_mask = loop_mask_of(p, gene);  // bit li: loop li runs on the GPU
+    const bool fuse = gene_fuses(p, gene);
     for (auto& B : p->bufs)
         if (B.d.role == GAO_BUF_INPUT && !B.input_set)
             return fail(GAO_EINVAL, "INPUT buffers must be set with prog_set_input before a run");
@@ -900,7 +902,9 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
         }
         cudaEvent_t* ev = &p->ev[(size_t)li * 6];
         Chain chain;
-        if (gpu && L.kind == GAO_LOOP_GEMM && find_chain(p, li, gene_mask, &chain)) {
+        // a GEMM whose A comes from the host overlaps the copy (row blocks) rather than fusing
+        const int64_t blocks = gpu ? pipeline_blocks(p, L) : 0;
+        if (gpu && blocks == 0 && L.kind == GAO_LOOP_GEMM && find_chain(p, li, gene_mask, fuse, &chain)) {
             // inputs of the whole chain: the GEMM's and the AXPY's second operand
             std::vector<int> cin = loop_inputs(L);
             cin.push_back(p->loops[(size_t)chain.axpy].ins[1]);
@@ -934,7 +938,6 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
         const bool per_loop = p->opts.transfer_mode == GAO_TRANSFER_PER_LOOP;
         if (gpu && per_loop)  // directive offload without a data region: inputs always copied in
             for (int b : ins) p->bufs[(size_t)b].vd = false;
-        const int64_t blocks = gpu ? pipeline_blocks(p, L) : 0;
         if (blocks > 0) {
             if ((status = run_gpu_gemm_pipelined(R, li, blocks)) != GAO_OK) break;
         } else if (gpu) {

@@ -96,3 +96,31 @@ def test_fused_full_size_n4096(gao):
     for nm in ("C", "D", "E", "r"):
         assert np.array_equal(res[False][nm], res[True][nm]), nm
     assert abs(res[False]["f"] - res[True]["f"]) <= 2e-7 * res[False]["f"]
+
+
+def test_fusion_as_a_gene_bit(gao):
+    """GAO_FUSE_GENE: one extra gene bit after the loop bits decides fusion; the GA searches
+    placements and fusion together, and every gene gives the same C, E and row sums."""
+    prog = W.six_loop(384, 73, outputs=("C", "E", "r", "f"))
+    p = gao.prog_from_workload(prog, gemm_prec=3, fuse_chains=gao.FUSE_GENE)
+    assert gao.prog_gene_length(p) == 7
+    first = None
+    for gene, fused in ((0b0111111, False), (0b1111111, True), (0b1111011, False), (0b1110111, False)):
+        gao.prog_run(p, gene)
+        st = gao.prog_stats(p)
+        assert (st[2]["placement"] == 2) == fused, bin(gene)
+        out = outputs(gao, p, prog)
+        if first is None:
+            first = out
+        for nm in ("C", "E", "r"):
+            assert np.array_equal(out[nm], first[nm]), (bin(gene), nm)
+    gao.prog_run(p, 0b1000000)  # fusion bit alone: every loop on the CPU
+    ref = oracle.run_program(prog)
+    assert oracle.rel_err(outputs(gao, p, prog)["C"], ref["C"]) <= 1e-6
+    with pytest.raises(gao.GaoError):
+        gao.prog_run(p, 1 << 7)
+    r = gao.ga_run([p], pop=8, generations=3, seed=2)
+    assert 0 <= r.best_mask < (1 << 7)
+    with pytest.raises(gao.GaoError):
+        gao.batch_create([p])  # batches run loop by loop
+    gao.prog_destroy(p)
