@@ -183,6 +183,7 @@ gao_status prog_create(const gao_loop *loops, int n_loops, const gao_buffer *buf
 gao_status prog_set_input(gao_prog *p, int buf, const void *host_src, uint64_t bytes);
 
 #define GAO_RUN_KEEP_DEVICE 1u /* leave OUTPUT buffers on the device (no final copy) */
+#define GAO_RUN_NO_GRAPH 2u    /* plain launches: no CUDA graph is captured or replayed       */
 
 /* Run every loop in program order.  Gene bit k belongs to the k-th offloadable loop in
  * program order (bit i to loop i when every loop is offloadable); that loop runs on the
@@ -190,7 +191,11 @@ gao_status prog_set_input(gao_prog *p, int buf, const void *host_src, uint64_t b
  * GAO_EINVAL.  Data moves
  * between host and device only where a loop needs a buffer last written on the other
  * side (Sec. 3.3: CPU-GPU transfers decide which loop combinations are fast).
- * *seconds_out = wall time from the first loop until the outputs are on the host. */
+ * *seconds_out = wall time from the first loop until the outputs are on the host.
+ * A gene that puts every loop on the GPU is captured as one CUDA graph the second time it
+ * runs (with the same KEEP_DEVICE flag) and replayed from then on: same kernels, copies and
+ * per-loop statistics, one launch.  Changing the program's tile configuration
+ * (prog_autotune) or prog_cache_clear drops the graphs. */
 gao_status prog_run(gao_prog *p, uint64_t gene_mask, uint32_t flags, double *seconds_out);
 
 /* Borrowed pointer to buffer `buf`'s host copy after a run (valid until the next

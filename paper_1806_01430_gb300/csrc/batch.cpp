@@ -473,6 +473,7 @@ extern "C" gao_status batch_autotune(gao_batch* b, const gao_ga_params* params, 
     for (auto* p : b->progs) {
         if (chunked_variant) p->opts.kchunk = kc;
         p->opts.tile_cfg = tc;
+        drop_graphs(p);
     }
     b->cache.clear();  // genes measured under the old configuration
     GAO_CUDA_TRY(cudaStreamSynchronize(b->st));

@@ -116,6 +116,13 @@ cudaError_t launch_gemm_simt(float* C, const float* A, const float* B, const flo
 
 // Tensor-core GEMM (split operands + tcgen05).  Scratch layout and size are given
 // by tc_scratch_bytes; `err` receives DEV_* codes.
+// Set while a run is being captured as a CUDA graph: timing events are then recorded as
+// graph nodes (external events), so that a replay records them too.
+extern thread_local bool g_capturing;
+inline cudaError_t record_timing(cudaEvent_t e, cudaStream_t s) {
+    return g_capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
 struct TcEvents {
     cudaEvent_t k0 = nullptr, k1 = nullptr;  // recorded around the MMA kernel if non-null
     int launches = 0;                         // out: kernels launched

@@ -1013,9 +1013,9 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         return cudaErrorInvalidValue;
     }
     if (K <= 0) {  // empty inner dimension: C = beta * C0, no tensor-core work
-        if (ev.k0) cudaEventRecord(ev.k0, st);
+        if (ev.k0) record_timing(ev.k0, st);
         cudaError_t e = launch_gemm_simt(C, A, B, C0, M, N, 0, alpha, beta, 0, st);
-        if (ev.k1) cudaEventRecord(ev.k1, st);
+        if (ev.k1) record_timing(ev.k1, st);
         ev.launches = 1;
         return e;
     }
@@ -1094,7 +1094,7 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         ep.frob_part = fuse->frob_out ? fpart : nullptr;
         ep.fuse = 1;
     }
-    if (ev.k0) cudaEventRecord(ev.k0, st);
+    if (ev.k0) record_timing(ev.k0, st);
     cudaError_t e;
     const int mp = (int)Mp, np = (int)Np;
     if (P == 3)
@@ -1111,7 +1111,7 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         e = launch_mma<128, 1, 1, 6, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
     if (e != cudaSuccess) return e;
     ev.launches += 1;
-    if (ev.k1) cudaEventRecord(ev.k1, st);
+    if (ev.k1) record_timing(ev.k1, st);
     if (fuse && fuse->frob_out) {
         const int64_t tiles = (Mp / BM) * ((N + bn - 1) / bn);
         frob_partials_kernel<<<1, 256, 0, st>>>(fpart, tiles * kEpiWarps, fuse->frob_out);
@@ -1154,11 +1154,11 @@ cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const floa
     EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
                (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, sa, sb, (int)L.kbs,
                (int)L.Np};
-    if (ev.k0) cudaEventRecord(ev.k0, st);
+    if (ev.k0) record_timing(ev.k0, st);
     cudaError_t e = launch_mma<128, 1, 1, 6, true, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, (int)L.kbs, 1, group, err, st);
     if (e != cudaSuccess) return e;
     ev.launches += 1;
-    if (ev.k1) cudaEventRecord(ev.k1, st);
+    if (ev.k1) record_timing(ev.k1, st);
     return cudaSuccess;
 }
 }  // namespace

@@ -32,6 +32,16 @@ struct Layout {
 
 }  // namespace gao
 
+// A run of one all-GPU gene captured as a CUDA graph, and the host-side state it leaves.
+struct GraphEntry {
+    int runs = 0;
+    bool failed = false;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint8_t> vh, vd;
+    std::vector<gao_loop_stat> stats;
+    std::vector<uint8_t> ev_used;
+};
+
 struct gao_prog {
     std::vector<gao_loop> loops;
     std::vector<gao::BufState> bufs;
@@ -52,6 +62,7 @@ struct gao_prog {
     std::vector<cudaEvent_t> pipe_ev;     // its events: fork, B landed, one per row block
     std::vector<int8_t> verdict;  // gao_offload of every loop
     std::vector<int> gene_loop;   // gene bit k -> index of the k-th offloadable loop
+    std::unordered_map<uint64_t, GraphEntry> graphs;  // key: gene * 4 + run flags
 };
 
 namespace gao {
@@ -88,5 +99,6 @@ inline bool gene_fuses(const gao_prog* p, uint64_t gene) {
     return p->opts.fuse_chains == GAO_FUSE_GENE && ((gene >> p->gene_loop.size()) & 1);
 }
 inline uint64_t all_genes(int a) { return a >= 64 ? ~0ULL : ((1ULL << a) - 1); }
+void drop_graphs(gao_prog* p);
 
 }  // namespace gao

@@ -330,6 +330,7 @@ void free_prog(gao_prog* p) {
         if (b.host) cudaFreeHost(b.host);
     if (p->h_err) cudaFreeHost(p->h_err);
     if (p->cst) cudaStreamSynchronize(p->cst);
+    drop_graphs(p);
     for (auto e : p->ev)
         if (e) cudaEventDestroy(e);
     for (auto e : p->pipe_ev)
@@ -449,6 +450,14 @@ extern "C" gao_status prog_set_input(gao_prog* p, int buf, const void* host_src,
 
 namespace gao {
 
+thread_local bool g_capturing = false;
+
+void drop_graphs(gao_prog* p) {
+    for (auto& kv : p->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    p->graphs.clear();
+}
+
 int offload_verdict(const gao_loop& L) {
     if (L.flags & GAO_LOOP_EXTERNAL_CALL) return GAO_OFFLOAD_EXTERNAL_CALL;
     if (L.kind == GAO_LOOP_RECURRENCE) return GAO_OFFLOAD_DEPENDENCE;
@@ -537,11 +546,11 @@ gao_status run_gpu_loop(RunCtx& R, int li) {
             cudaEvent_t k0 = R.events ? p->ev[(size_t)li * 6 + 4] : nullptr;
             cudaEvent_t k1 = R.events ? p->ev[(size_t)li * 6 + 5] : nullptr;
             if (prec == GAO_GEMM_FP32_SIMT) {
-                if (k0) GAO_CUDA_TRY(cudaEventRecord(k0, st));
+                if (k0) GAO_CUDA_TRY(record_timing(k0, st));
                 e = launch_gemm_simt(dptr(L.outs[0]), dptr(L.ins[0]), dptr(L.ins[1]), c0 ? c0 : dptr(L.outs[0]),
                                      A.rows, B.cols, A.cols, (float)L.alpha, beta, p->opts.kchunk, st);
                 nl += A.rows * B.cols > 0;
-                if (e == cudaSuccess && k1) GAO_CUDA_TRY(cudaEventRecord(k1, st));
+                if (e == cudaSuccess && k1) GAO_CUDA_TRY(record_timing(k1, st));
             } else {
                 std::string why;
                 TcEvents tev{k0, k1, 0};
@@ -803,7 +812,7 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks) {
     cudaEvent_t fork = p->pipe_ev[0], b_done = p->pipe_ev[1];
     GAO_CUDA_TRY(cudaEventRecord(fork, st));  // the copies overwrite device buffers: after earlier work
     GAO_CUDA_TRY(cudaStreamWaitEvent(cs, fork, 0));
-    GAO_CUDA_TRY(cudaEventRecord(ev[0], cs));
+    GAO_CUDA_TRY(record_timing(ev[0], cs));
     if (!B.vd) {
         GAO_CUDA_TRY(cudaMemcpyAsync(B.dev, B.host, B.bytes, cudaMemcpyHostToDevice, cs));
         S.h2d_bytes += B.bytes;
@@ -824,8 +833,8 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks) {
         }
         GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + (size_t)nb], cs));
     }
-    GAO_CUDA_TRY(cudaEventRecord(ev[1], cs));
-    GAO_CUDA_TRY(cudaEventRecord(ev[2], st));
+    GAO_CUDA_TRY(record_timing(ev[1], cs));
+    GAO_CUDA_TRY(record_timing(ev[2], st));
     GAO_CUDA_TRY(cudaStreamWaitEvent(st, b_done, 0));
     const float beta = C0 ? (float)L.beta : 0.0f;
     int i = 0;
@@ -844,7 +853,7 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks) {
         if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "row-block GEMM") : fail(GAO_EINVAL, why);
         S.launches += tev.launches;
     }
-    GAO_CUDA_TRY(cudaEventRecord(ev[3], st));
+    GAO_CUDA_TRY(record_timing(ev[3], st));
     A.vd = B.vd = true;
     if (C0) C0->vd = true;
     p->ev_used[(size_t)li] |= 1 | 2 | 4;
@@ -858,28 +867,13 @@ double ev_ms(cudaEvent_t a, cudaEvent_t b) {
 }
 }  // namespace
 
-extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, double* seconds_out) {
-    if (!p) return fail(GAO_EINVAL, "program is null");
+// Everything a run under a gene puts on the program's stream, in program order, with the
+// host loops run in between: residency reset, the error word, each loop's copies and
+// kernels (or its host loop), the outputs' copies back and the error word's read-back.
+// When every loop is on the GPU this is also what a CUDA graph of the run captures.
+gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags) {
+    gao_prog* p = R.p;
     const int n = (int)p->loops.size();
-    const int a = gene_length(p);
-    if (a < 64 && (gene >> a) != 0)
-        return fail(GAO_EINVAL, "gene has bits set at or above the gene length (" + std::to_string(a) + ")");
-    const uint64_t gene_mask = loop_mask_of(p, gene);  // bit li: loop li runs on the GPU
-    const bool fuse = gene_fuses(p, gene);
-    for (auto& B : p->bufs)
-        if (B.d.role == GAO_BUF_INPUT && !B.input_set)
-            return fail(GAO_EINVAL, "INPUT buffers must be set with prog_set_input before a run");
-    if (p->dirty_stream) {
-        bool to = false;
-        gao_status s = stream_wait(p->st, 0.0, &to);
-        if (s != GAO_OK) return s;
-        p->dirty_stream = false;
-    }
-    cudaError_t ce = cudaSetDevice(p->device);
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
-    RunCtx R{p, 0.0, false, CpuCtx{p->opts.cpu_threads, 0.0, false}, p->st, true};
-    const double t0 = now_s();
-    if (p->opts.timeout_s > 0.0) R.deadline = R.cpu.deadline = t0 + p->opts.timeout_s;
     for (auto& B : p->bufs) {
         B.vh = (B.d.role == GAO_BUF_INPUT);
         B.vd = false;
@@ -910,17 +904,17 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
             cin.push_back(p->loops[(size_t)chain.axpy].ins[1]);
             bool copies = false;
             for (int b : cin) copies |= !p->bufs[(size_t)b].vd;
-            if (copies) GAO_CUDA_TRY(cudaEventRecord(ev[0], p->st));
+            if (copies) GAO_CUDA_TRY(record_timing(ev[0], p->st));
             for (int b : cin)
                 if ((status = make_valid(R, b, true, S)) != GAO_OK) break;
             if (status != GAO_OK) break;
             if (copies) {
-                GAO_CUDA_TRY(cudaEventRecord(ev[1], p->st));
+                GAO_CUDA_TRY(record_timing(ev[1], p->st));
                 p->ev_used[(size_t)li] |= 1;
             }
-            GAO_CUDA_TRY(cudaEventRecord(ev[2], p->st));
+            GAO_CUDA_TRY(record_timing(ev[2], p->st));
             if ((status = run_gpu_chain(R, li, chain)) != GAO_OK) break;
-            GAO_CUDA_TRY(cudaEventRecord(ev[3], p->st));
+            GAO_CUDA_TRY(record_timing(ev[3], p->st));
             p->ev_used[(size_t)li] |= 2;
             for (int j : {li, chain.axpy, chain.transpose, chain.frob}) {
                 if (j < 0) continue;
@@ -943,17 +937,17 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
         } else if (gpu) {
             bool copies = false;
             for (int b : ins) copies |= !p->bufs[(size_t)b].vd;
-            if (copies) GAO_CUDA_TRY(cudaEventRecord(ev[0], p->st));
+            if (copies) GAO_CUDA_TRY(record_timing(ev[0], p->st));
             for (int b : ins)
                 if ((status = make_valid(R, b, true, S)) != GAO_OK) break;
             if (status != GAO_OK) break;
             if (copies) {
-                GAO_CUDA_TRY(cudaEventRecord(ev[1], p->st));
+                GAO_CUDA_TRY(record_timing(ev[1], p->st));
                 p->ev_used[(size_t)li] |= 1;
             }
-            GAO_CUDA_TRY(cudaEventRecord(ev[2], p->st));
+            GAO_CUDA_TRY(record_timing(ev[2], p->st));
             if ((status = run_gpu_loop(R, li)) != GAO_OK) break;
-            GAO_CUDA_TRY(cudaEventRecord(ev[3], p->st));
+            GAO_CUDA_TRY(record_timing(ev[3], p->st));
             p->ev_used[(size_t)li] |= 2;
         } else {
             const double c0 = now_s();
@@ -994,6 +988,90 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
     if (uses_gpu) {
         cudaError_t e = cudaMemcpyAsync(p->h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, p->st);
         if (e != cudaSuccess && status == GAO_OK) status = cuda_fail(e, "cudaMemcpyAsync(err)");
+    }
+    return status;
+}
+
+// Capture one run of an all-GPU gene as a graph (nothing executes during the capture)
+// and keep what the run leaves on the host side: residency flags and per-loop statistics.
+void capture_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags, GraphEntry* ge) {
+    gao_prog* p = R.p;
+    if (cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        ge->failed = true;
+        return;
+    }
+    g_capturing = true;
+    const gao_status st = enqueue_run(R, gene_mask, fuse, flags);
+    g_capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->st, &g);
+    cudaGraphExec_t exec = nullptr;
+    if (st == GAO_OK && e == cudaSuccess && g && !R.timed_out &&
+        cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+        ge->exec = exec;
+        ge->vh.resize(p->bufs.size());
+        ge->vd.resize(p->bufs.size());
+        for (size_t b = 0; b < p->bufs.size(); ++b) {
+            ge->vh[b] = p->bufs[b].vh;
+            ge->vd[b] = p->bufs[b].vd;
+        }
+        ge->stats = p->stats;
+        ge->ev_used = p->ev_used;
+    } else {
+        cudaGetLastError();  // the run falls back to plain launches; the gene is not captured again
+        ge->failed = true;
+    }
+    if (g) cudaGraphDestroy(g);
+    R.timed_out = false;
+}
+
+extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, double* seconds_out) {
+    if (!p) return fail(GAO_EINVAL, "program is null");
+    const int n = (int)p->loops.size();
+    const int a = gene_length(p);
+    if (a < 64 && (gene >> a) != 0)
+        return fail(GAO_EINVAL, "gene has bits set at or above the gene length (" + std::to_string(a) + ")");
+    const uint64_t gene_mask = loop_mask_of(p, gene);  // bit li: loop li runs on the GPU
+    const bool fuse = gene_fuses(p, gene);
+    for (auto& B : p->bufs)
+        if (B.d.role == GAO_BUF_INPUT && !B.input_set)
+            return fail(GAO_EINVAL, "INPUT buffers must be set with prog_set_input before a run");
+    if (p->dirty_stream) {
+        bool to = false;
+        gao_status s = stream_wait(p->st, 0.0, &to);
+        if (s != GAO_OK) return s;
+        p->dirty_stream = false;
+    }
+    cudaError_t ce = cudaSetDevice(p->device);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
+    RunCtx R{p, 0.0, false, CpuCtx{p->opts.cpu_threads, 0.0, false}, p->st, true};
+    const double t0 = now_s();
+    if (p->opts.timeout_s > 0.0) R.deadline = R.cpu.deadline = t0 + p->opts.timeout_s;
+    const bool uses_gpu = gene_mask != 0;
+    gao_status status = GAO_OK;
+    // a gene that keeps every loop on the GPU is captured as a CUDA graph on its second
+    // run and replayed from then on (one launch per run; the host work of the run is done once)
+    const bool all_gpu = gene_mask == all_genes(n) && gene_length(p) > 0;
+    GraphEntry* ge = nullptr;
+    if (all_gpu && !(flags & GAO_RUN_NO_GRAPH)) {
+        ge = &p->graphs[gene * 4 + (flags & GAO_RUN_KEEP_DEVICE)];
+        ge->runs += 1;
+    }
+    if (ge && !ge->exec && !ge->failed && ge->runs >= 2) capture_run(R, gene_mask, fuse, flags, ge);
+    if (ge && ge->exec) {
+        cudaError_t e = cudaGraphLaunch(ge->exec, p->st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        for (size_t b = 0; b < p->bufs.size(); ++b) {
+            p->bufs[b].vh = ge->vh[b] != 0;
+            p->bufs[b].vd = ge->vd[b] != 0;
+        }
+        p->stats = ge->stats;
+        p->ev_used = ge->ev_used;
+    } else {
+        status = enqueue_run(R, gene_mask, fuse, flags);
+    }
+    if (uses_gpu) {
         gao_status ws = stream_wait(p->st, R.deadline, &R.timed_out);
         if (ws != GAO_OK) {
             p->dirty_stream = true;
@@ -1067,6 +1145,7 @@ extern "C" gao_status prog_stats(gao_prog* p, gao_loop_stat* out, int n) {
 extern "C" gao_status prog_cache_clear(gao_prog* p) {
     if (!p) return fail(GAO_EINVAL, "program is null");
     p->cache.clear();
+    drop_graphs(p);
     return GAO_OK;
 }
 
@@ -1257,6 +1336,7 @@ extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, ga
             autotune_decode(prec, res.best_mask, &kc, &tc);
             p->opts.kchunk = kc;
             p->opts.tile_cfg = tc;
+            drop_graphs(p);
             p->cache.clear();  // times measured under the old configuration
             out->kchunk = kc;
             out->tile_cfg = tc;
