@@ -417,6 +417,42 @@ def our_arm(args, world, rank, local):
                                "measured": ga.evaluations, "served": ga.cache_hits}}
         gao.prog_destroy(q)
 
+    # the twelve-loop program's search: the paper's GA (M = T = 12) over the 12-bit gene with
+    # transfer-aware times (every host <-> device copy a gene implies is in its time; a gene
+    # over 10x the all-GPU time is cut off at that budget), and the FP8 path on the same program
+    if args.search and rank == 0 and args.workload == "twelve_loop":
+        q = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream)
+        t0 = time.perf_counter()
+        ga = gao.ga_run([q], **W.PAPER_GA, seed=11, timeout_s=-1.0)
+        t_search = time.perf_counter() - t0
+        all_gpu = gao.prog_run(q, (1 << 12) - 1)
+        gao.prog_destroy(q)
+        search = {"workload": wname.replace("all_gpu_", "") + "_paper_ga", "wall_s": t_search,
+                  "measured": ga.evaluations, "served": ga.cache_hits,
+                  "best_gene": format(ga.best_mask, "012b"), "best_s": ga.best_s, "all_gpu_s": all_gpu,
+                  "history_best_s": [h["best_s"] for h in ga.history]}
+        if prec != "fp8":
+            q = gao.prog_from_workload(prog, gemm_prec=PREC["fp8"], stream=stream)
+            for _ in range(3):
+                gao.prog_run(q, mask, gao.RUN_KEEP_DEVICE)
+            ks = []
+            for _ in range(20):
+                gao.prog_run(q, mask, gao.RUN_KEEP_DEVICE)
+                ks.append(gao.prog_stats(q)[gemm_loop]["kernel_ms"])
+            gao.prog_run(q, mask)
+            C8 = gao.prog_output(q, prog.index("C"))
+            gm, gk = prog.buffers[prog.index("A")].rows, prog.buffers[prog.index("A")].cols
+            gn = prog.buffers[prog.index("B")].cols
+            rng = np.random.default_rng(1)
+            ii, jj = rng.integers(0, gm, 128), rng.integers(0, gn, 128)
+            import oracle
+            want = oracle.gemm_init_entries(prog.seed, (0, 1, 2), False, gm, gn, gk, 1.5, 0.5, ii, jj)
+            got = C8[ii, jj].astype(np.float64)
+            search["fp8"] = {"gemm_kernel_tflops": flops / (statistics.median(ks) / 1e3) / 1e12,
+                             "gemm_rel_err_sampled": math.sqrt(float(((got - want) ** 2).mean()) /
+                                                               float((want ** 2).mean()))}
+            gao.prog_destroy(q)
+
     if rank != 0:
         return
     pk = peaks()
@@ -675,7 +711,9 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--k", type=int, default=4096)
-    ap.add_argument("--prec", default="bf16x6", choices=list(PREC))
+    ap.add_argument("--prec", default=None, choices=list(PREC),
+                    help="GEMM arithmetic (default: bf16x6 for the six-loop program, bf16x3 for the "
+                         "twelve-loop program and the batch, as their configurations state)")
     ap.add_argument("--no-check", dest="check", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-simt", dest="compare_simt", action="store_false")
@@ -687,6 +725,8 @@ def main():
     ap.add_argument("--ref-target-s", type=float, default=8.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.prec is None:
+        args.prec = "bf16x3" if args.workload in ("twelve_loop", "batch") else "bf16x6"
     world, rank, local = dist_init()
     if args.impl == "reference":
         reference_arm(args, world, rank)

@@ -281,8 +281,9 @@ gao_status ga_run_table(const double *times, int n_genes, const gao_ga_params *p
 
 /* The Simple GA reused as the tensor-core GEMM's autotuner: a 4-bit gene encodes
  * bits 0-1  raster group of 4, 8, 16 or 32 row tiles per CTA group (L2 reuse order),
- * bits 2-3  split precisions: K chunk of 64, 128, 256 or 512 elements (all within the
- *           stated error bound); plain BF16: tile width 128 or 256 columns,
+ * bits 2-3  split precisions: K chunk of 64, 128, 256 or 512 elements (BF16x6) or 128,
+ *           256, 512 or 1024 (BF16x3), all within the stated error bound; plain BF16:
+ *           tile width 128 or 256 columns,
  * and fitness is (measured GEMM time)^(-1/2), the paper's fitness with the kernel time
  * as the benchmark.  The best configuration is written into the program's (or the
  * batch's) options and used from then on. */

@@ -31,8 +31,11 @@ inline void autotune_decode(int prec, uint64_t gene, int* kchunk, int* tile_cfg)
     const int glog = 2 + (int)(gene & 3);
     const int v = (int)((gene >> 2) & 3);
     int bn_sel = 0;
-    if (prec == GAO_GEMM_BF16X3 || prec == GAO_GEMM_BF16X6) {
-        *kchunk = 64 << v;
+    if (prec == GAO_GEMM_BF16X6) {
+        *kchunk = 64 << v;  // 64 .. 512: the six-product error stays under 1e-6
+        bn_sel = 1;
+    } else if (prec == GAO_GEMM_BF16X3) {
+        *kchunk = 128 << v;  // 128 .. 1024: the two-term split, not the chunk, sets the error
         bn_sel = 1;
     } else if (prec == GAO_GEMM_BF16) {
         *kchunk = 0;

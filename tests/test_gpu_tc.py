@@ -172,7 +172,7 @@ def test_full_size_fp8_sampled(gao):
     assert err <= 6e-2, err
 
 
-@pytest.mark.parametrize("prec", ["bf16x6", "bf16"])
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16"])
 def test_prog_autotune_keeps_parity(gao, prec):
     """The GA picks a tile configuration by measured GEMM time; every configuration in its
     search space stays within the precision's error gate, and the program keeps matching
@@ -184,6 +184,8 @@ def test_prog_autotune_keeps_parity(gao, prec):
     assert r["best_ms"] <= 1.25 * r["default_ms"]
     if prec == "bf16x6":
         assert r["kchunk"] in (64, 128, 256, 512)
+    if prec == "bf16x3":
+        assert r["kchunk"] in (128, 256, 512, 1024)
     assert ((r["tile_cfg"] >> 4) & 15) in (2, 3, 4, 5)
     gao.prog_run(p, 0b111111)
     ref = oracle.run_program(prog)
