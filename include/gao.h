@@ -230,6 +230,16 @@ gao_status prog_stats(gao_prog *p, gao_loop_stat *out, int n);
 /* Forget every cached gene time of this program. */
 gao_status prog_cache_clear(gao_prog *p);
 
+/* Checkpoint of the search: the program's measured gene times (the cache of Sec. 4), up
+ * to cap entries into genes[] and seconds[] (a negative time marks a failed gene);
+ * *n_out = the number of entries the cache holds (call with cap = 0 to size the arrays). */
+gao_status prog_cache_export(const gao_prog *p, uint64_t *genes, double *seconds, int cap, int *n_out);
+
+/* Resume: put measured times back into the cache (existing entries are kept).  A ga_run
+ * with the same parameters and seed then replays the generations already searched without
+ * running a program, and measures only genes it has not seen. */
+gao_status prog_cache_import(gao_prog *p, const uint64_t *genes, const double *seconds, int n);
+
 void prog_destroy(gao_prog *p);
 
 /* ---- GA (Sec. 3.3 / Sec. 4 / Sec. 5.1.2) ---------------------------------- */

@@ -102,6 +102,10 @@ SIGNATURES = {
     "prog_run": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]),
     "prog_output": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(gao_buffer)]),
     "prog_gene_length": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "prog_cache_export": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "prog_cache_import": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_int]),
     "prog_loop_offload": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "prog_device_ptr": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "prog_stats": (ctypes.c_int, [_P, ctypes.POINTER(gao_loop_stat), ctypes.c_int]),
@@ -278,6 +282,49 @@ def prog_loop_offload(p: Prog, loop: int):
     v, g = ctypes.c_int(0), ctypes.c_int(0)
     _check(lib().prog_loop_offload(p.handle, loop, ctypes.byref(v), ctypes.byref(g)), "prog_loop_offload")
     return int(v.value), int(g.value)
+
+
+def prog_cache_export(p: Prog):
+    """(genes, seconds) of every measured gene, in gene order."""
+    n = ctypes.c_int(0)
+    _check(lib().prog_cache_export(p.handle, None, None, 0, ctypes.byref(n)), "prog_cache_export")
+    g = (ctypes.c_uint64 * max(1, n.value))()
+    t = (ctypes.c_double * max(1, n.value))()
+    _check(lib().prog_cache_export(p.handle, g, t, n.value, ctypes.byref(n)), "prog_cache_export")
+    return [int(g[i]) for i in range(n.value)], [float(t[i]) for i in range(n.value)]
+
+
+def prog_cache_import(p: Prog, genes, seconds) -> None:
+    k = len(genes)
+    assert len(seconds) == k
+    g = (ctypes.c_uint64 * max(1, k))(*[int(x) for x in genes])
+    t = (ctypes.c_double * max(1, k))(*[float(x) for x in seconds])
+    _check(lib().prog_cache_import(p.handle, g, t, k), "prog_cache_import")
+
+
+def ga_checkpoint(progs: Sequence[Prog], path: str) -> None:
+    """Write every program's measured gene times to a JSON file (a search checkpoint)."""
+    import json
+    data = {"programs": []}
+    for p in progs:
+        g, t = prog_cache_export(p)
+        data["programs"].append({"genes": g, "seconds": t})
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f)
+    os.replace(tmp, path)
+
+
+def ga_resume(progs: Sequence[Prog], path: str) -> None:
+    """Load a checkpoint written by ga_checkpoint into the programs' caches; a ga_run with
+    the same parameters and seed then continues the search where it stopped."""
+    import json
+    with open(path) as f:
+        data = json.load(f)
+    if len(data["programs"]) != len(progs):
+        raise ValueError("checkpoint holds a different number of programs")
+    for p, e in zip(progs, data["programs"]):
+        prog_cache_import(p, e["genes"], e["seconds"])
 
 
 def prog_run(p: Prog, gene_mask: int, flags: int = 0) -> float:

@@ -1149,6 +1149,37 @@ extern "C" gao_status prog_cache_clear(gao_prog* p) {
     return GAO_OK;
 }
 
+extern "C" gao_status prog_cache_export(const gao_prog* p, uint64_t* genes, double* seconds, int cap, int* n_out) {
+    if (!p || !n_out || cap < 0 || (cap > 0 && (!genes || !seconds))) return fail(GAO_EINVAL, "bad argument");
+    // in gene order, so that a checkpoint does not depend on the hash table's layout
+    std::vector<std::pair<uint64_t, double>> v;
+    v.reserve(p->cache.size());
+    for (const auto& kv : p->cache) v.emplace_back(kv.first, kv.second.seconds);
+    std::sort(v.begin(), v.end());
+    *n_out = (int)v.size();
+    for (int i = 0; i < cap && i < (int)v.size(); ++i) {
+        genes[i] = v[(size_t)i].first;
+        seconds[i] = v[(size_t)i].second;
+    }
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_cache_import(gao_prog* p, const uint64_t* genes, const double* seconds, int n) {
+    if (!p || n < 0 || (n > 0 && (!genes || !seconds))) return fail(GAO_EINVAL, "bad argument");
+    const int a = gene_length(p);
+    for (int i = 0; i < n; ++i) {
+        if (a < 64 && (genes[i] >> a) != 0) return fail(GAO_EINVAL, "imported gene longer than the gene length");
+        if (!(seconds[i] == seconds[i])) return fail(GAO_EINVAL, "imported time is not a number");
+    }
+    for (int i = 0; i < n; ++i) {
+        CacheEntry ce;
+        ce.seconds = seconds[i];
+        ce.status = seconds[i] >= 0.0 ? GAO_OK : GAO_EDEVICE;
+        p->cache.emplace(genes[i], ce);
+    }
+    return GAO_OK;
+}
+
 extern "C" void prog_destroy(gao_prog* p) { free_prog(p); }
 
 // ---- C ABI: GA ----------------------------------------------------------------------------

@@ -352,3 +352,29 @@ def test_config1_all_64_genes_n4096(gao):
         assert err <= TOL, (mask, err)
         check_internal_consistency(out)
     gao.prog_destroy(p)
+
+
+def test_ga_checkpoint_and_resume(gao, tmp_path):
+    """The measurement cache is the search's state (Sec. 4): exported after a few
+    generations and imported into fresh program handles, a ga_run with the same seed
+    replays those generations from the cache and continues."""
+    prog = W.six_loop(192, 55, outputs=("C", "r", "f"))
+    p = gao.prog_from_workload(prog, gemm_prec=gao.FP32_SIMT)
+    r1 = gao.ga_run([p], pop=8, generations=3, seed=4)
+    path = str(tmp_path / "search.json")
+    gao.ga_checkpoint([p], path)
+    genes, secs = gao.prog_cache_export(p)
+    assert len(genes) == r1.evaluations and genes == sorted(genes)
+    q = gao.prog_from_workload(prog, gemm_prec=gao.FP32_SIMT)
+    gao.ga_resume([q], path)
+    fit, s2, hits = gao.ga_evaluate([q], genes)
+    assert hits == len(genes) and list(s2) == secs  # served, not measured
+    r2 = gao.ga_run([q], pop=8, generations=6, seed=4)
+    assert [h["best_mask"] for h in r2.history[:3]] == [h["best_mask"] for h in r1.history]
+    assert [h["best_s"] for h in r2.history[:3]] == [h["best_s"] for h in r1.history]
+    g2, _ = gao.prog_cache_export(q)
+    assert set(genes) <= set(g2)
+    with pytest.raises(gao.GaoError):
+        gao.prog_cache_import(q, [1 << 6], [0.1])  # longer than the gene
+    gao.prog_destroy(p)
+    gao.prog_destroy(q)
