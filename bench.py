@@ -292,6 +292,7 @@ def our_arm(args, world, rank, local):
             for i, s_ in enumerate(st):
                 loop_ms[i] += s_["device_ms"]
         launches = sum(s_["launches"] for s_ in st) * args.steps  # the same kernels every step
+        graph_replay = gao.prog_graphs(p)[0] > 0
         time.sleep(0.25)
     barrier(world)
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -492,7 +493,7 @@ def our_arm(args, world, rank, local):
             "data": "synthetic (seeded counter hash, U[-1,1))",
             "config": {"workload": wname, "n": n if args.workload == "six_loop" else None,
                        "gene": format(mask, f"0{prog.n_loops}b"),
-                       "gemm": prec, "fused_chain": bool(args.fuse),
+                       "gemm": prec, "fused_chain": bool(args.fuse), "graph_replay": graph_replay,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "working set larger than the 129 MB L2 (no flush)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -540,6 +541,7 @@ def image_arm(args, world, rank, local):
             for i, s_ in enumerate(st):
                 loop_ms[i] += s_["device_ms"]
         launches = sum(s_["launches"] for s_ in st) * args.steps
+        graph_replay = gao.prog_graphs(p)[0] > 0
         time.sleep(0.25)
     barrier(world)
     ms = allmax(world, ev0.elapsed_time(ev1) / args.steps)
@@ -623,7 +625,7 @@ def image_arm(args, world, rank, local):
     line = {"metric": "image_program_gpixels", "value": value, "unit": "Gpixel/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded counter hash, U[-1,1))",
-            "config": {"workload": f"image_{h}x{w}_all_gpu", "h": h, "w": w,
+            "config": {"workload": f"image_{h}x{w}_all_gpu", "h": h, "w": w, "graph_replay": graph_replay,
                        "gene": format(mask, f"0{prog.n_loops}b"),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "working set larger than the 129 MB L2 (no flush)"},

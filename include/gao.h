@@ -227,6 +227,10 @@ gao_status prog_loop_offload(const gao_prog *p, int loop, int *verdict, int *gen
 /* Per-loop statistics of the last prog_run (n >= loop count). */
 gao_status prog_stats(gao_prog *p, gao_loop_stat *out, int n);
 
+/* Number of genes of this program that replay a captured graph, and of genes whose
+ * capture failed (they keep running with plain launches).  Either output may be NULL. */
+gao_status prog_graphs(const gao_prog *p, int *captured, int *failed);
+
 /* Forget every cached gene time of this program. */
 gao_status prog_cache_clear(gao_prog *p);
 

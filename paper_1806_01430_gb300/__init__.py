@@ -102,6 +102,7 @@ SIGNATURES = {
     "prog_run": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]),
     "prog_output": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(gao_buffer)]),
     "prog_gene_length": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "prog_graphs": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "prog_cache_export": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "prog_cache_import": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
@@ -282,6 +283,13 @@ def prog_loop_offload(p: Prog, loop: int):
     v, g = ctypes.c_int(0), ctypes.c_int(0)
     _check(lib().prog_loop_offload(p.handle, loop, ctypes.byref(v), ctypes.byref(g)), "prog_loop_offload")
     return int(v.value), int(g.value)
+
+
+def prog_graphs(p: Prog):
+    """(genes replayed from a captured graph, genes whose capture failed)."""
+    c, f = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().prog_graphs(p.handle, ctypes.byref(c), ctypes.byref(f)), "prog_graphs")
+    return int(c.value), int(f.value)
 
 
 def prog_cache_export(p: Prog):

@@ -831,9 +831,11 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks) {
                 cudaMemcpyAsync(C0->dev + off_c, (char*)C0->host + off_c, len_c, cudaMemcpyHostToDevice, cs));
             S.h2d_bytes += len_c;
         }
+        // the copy-time stamp goes before the last block's event, so that everything on the
+        // copy stream is joined back into the program's stream (a captured graph needs that)
+        if (r1 == M) GAO_CUDA_TRY(record_timing(ev[1], cs));
         GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + (size_t)nb], cs));
     }
-    GAO_CUDA_TRY(record_timing(ev[1], cs));
     GAO_CUDA_TRY(record_timing(ev[2], st));
     GAO_CUDA_TRY(cudaStreamWaitEvent(st, b_done, 0));
     const float beta = C0 ? (float)L.beta : 0.0f;
@@ -1146,6 +1148,18 @@ extern "C" gao_status prog_cache_clear(gao_prog* p) {
     if (!p) return fail(GAO_EINVAL, "program is null");
     p->cache.clear();
     drop_graphs(p);
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_graphs(const gao_prog* p, int* captured, int* failed) {
+    if (!p) return fail(GAO_EINVAL, "program is null");
+    int c = 0, f = 0;
+    for (const auto& kv : p->graphs) {
+        c += kv.second.exec != nullptr;
+        f += kv.second.failed;
+    }
+    if (captured) *captured = c;
+    if (failed) *failed = f;
     return GAO_OK;
 }
 

@@ -39,6 +39,7 @@ def test_replay_is_bit_identical_and_timed(gao, prec, fuse):
             assert np.array_equal(o[nm], plain[nm]), (it, nm)
         assert all(s["device_ms"] > 0 or s["placement"] == 2 for s in st), st
         assert st[1]["kernel_ms"] > 0 and st[1]["launches"] >= 1
+    assert gao.prog_graphs(p) == (1, 0)  # captured on the second run, replayed since
     gao.prog_destroy(p)
 
 
@@ -52,6 +53,7 @@ def test_replay_with_new_host_inputs_and_overlap(gao):
     gene = (1 << hp.n_loops) - 1
     for _ in range(3):  # plain, capture, replay
         gao.prog_run(p, gene)
+    assert gao.prog_graphs(p) == (1, 0)  # the copy-overlapped GEMM joins back into the capture
     C1 = gao.prog_output(p, hp.index("C")).copy()
     gao.prog_run(p, gene, gao.RUN_NO_GRAPH)
     assert np.array_equal(gao.prog_output(p, hp.index("C")), C1)
@@ -98,4 +100,5 @@ def test_mixed_genes_never_captured(gao):
             ref = C.copy()
         assert np.array_equal(C, ref)
         assert gao.prog_stats(p)[3]["placement"] == 0
+    assert gao.prog_graphs(p) == (0, 0)
     gao.prog_destroy(p)
