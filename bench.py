@@ -514,7 +514,7 @@ def image_arm(args, world, rank, local):
     stream = torch.cuda.Stream()
     h, w = args.h, args.w
     prog = W.image_program(h, w, W.SEED_IMAGE + rank, outputs=("e", "q"))
-    p = gao.prog_from_workload(prog, stream=stream)
+    p = gao.prog_from_workload(prog, stream=stream, fuse_chains=args.fuse)
     mask = (1 << prog.n_loops) - 1
     loop_ms = [0.0] * prog.n_loops
     launches = 0
@@ -556,18 +556,38 @@ def image_arm(args, world, rank, local):
         if v > 0:
             g = algorithmic_bytes(prog, lp) / (v / stat_steps / 1e3) / 1e9
             loop_gbs[key] = {"gbs": round(g, 1), "hbm_frac": round(g / hbm, 3)}
-    # dominant kernel: the three stencil loops, 8 algorithmic bytes per pixel each
-    st_idx = [i for i, lp in enumerate(prog.loops) if lp.kind == W.STENCIL3]
+    # dominant kernel: the stencil passes (the blur, and Sobel x / Sobel y or, fused, the
+    # gradient chain that reads the blurred image once and writes only the magnitude),
+    # 8 algorithmic bytes per pixel each
+    st_idx = [i for i, lp in enumerate(prog.loops) if lp.kind == W.STENCIL3 and loop_ms[i] > 0]
     st_ms = sum(loop_ms[i] for i in st_idx) / (len(st_idx) * stat_steps)
     achieved = 8.0 * pixels / (st_ms / 1e3) / 1e9
     gao.prog_destroy(p)
+
+    # the same frame with every loop a separate kernel
+    unfused = None
+    if args.fuse:
+        q = gao.prog_from_workload(prog, stream=stream, fuse_chains=False)
+        for _ in range(3):
+            gao.prog_run(q, mask, gao.RUN_KEEP_DEVICE)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(3, min(args.steps // 2, 300))
+        e0.record(stream)
+        for _ in range(k):
+            gao.prog_run(q, mask, gao.RUN_KEEP_DEVICE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ums = e0.elapsed_time(e1) / k
+        unfused = {"value": pixels / (ums / 1e3) / 1e9, "unit": "Gpixel/s", "ms_per_step": ums}
+        gao.prog_destroy(q)
 
     # end to end: the image arrives from pinned host memory every step (a camera
     # frame, INPUT buffer), the energy and column maxima are read back
     e2e = None
     if args.e2e:
         hp = W.image_program(h, w, W.SEED_IMAGE + rank, outputs=("e", "q"), host_image=True)
-        q = gao.prog_from_workload(hp, stream=stream)
+        q = gao.prog_from_workload(hp, stream=stream, fuse_chains=args.fuse)
         import oracle  # input generation only (seeded counter hash); not on the timed path
         gao.prog_set_input(q, hp.index("X"), oracle.init_matrix(hp.seed, 0, h, w).astype(np.float32))
         m8 = (1 << hp.n_loops) - 1
@@ -626,15 +646,17 @@ def image_arm(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded counter hash, U[-1,1))",
             "config": {"workload": f"image_{h}x{w}_all_gpu", "h": h, "w": w, "graph_replay": graph_replay,
+                       "fused_chain": bool(args.fuse),
                        "gene": format(mask, f"0{prog.n_loops}b"),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "working set larger than the 129 MB L2 (no flush)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": profile_traffic("kernels_ew.cu", f"stencil3_image_{h}x{w}.md"),
-                         "kernel": "stencil3 (8 algorithmic bytes per pixel)",
+                         "kernel": "stencil3 passes" + (" (blur; fused Sobel x/y, squares, sum)" if args.fuse else "")
+                                   + " (8 algorithmic bytes per pixel)",
                          "peak_source": f"{peaks()['source']} hbm_gbs"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "loop_ms": per_loop, "loop_gbs": loop_gbs, "ga_search": search}
+            "unfused_chain": unfused, "loop_ms": per_loop, "loop_gbs": loop_gbs, "ga_search": search}
     print(json.dumps(line), flush=True)
 
 

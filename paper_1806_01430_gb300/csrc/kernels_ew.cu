@@ -390,10 +390,49 @@ struct StencilRow {
 // same iterations (the strip is per block), so the shuffles always see a full warp.
 constexpr int kStencilAhead = 3;
 
+// Outputs of one pass: a single stencil writes out[0]; the gradient chain (two stencils of
+// the same image g1, g2, their squares s1 = g1*g1, s2 = g2*g2 and m = s_x + alpha s_y with
+// (x, y) = (1, 2), or (2, 1) when `swap`) writes m and whichever of g1, g2, s1, s2 is
+// non-null.  Every value is formed with the operations of the separate loops.
+struct StencilOut {
+    float* g1;
+    float* g2;
+    float* s1;
+    float* s2;
+    float* m;
+    float alpha;
+    int swap;
+};
+
 template <bool VEC>
-__global__ void __launch_bounds__(kStencilThreads, 8) stencil3_kernel(float* __restrict__ out,
-                                                                   const float* __restrict__ in, int64_t rows,
-                                                                   int64_t cols, StencilW w, int strip) {
+__device__ __forceinline__ void store4(float* row, int64_t c0, int64_t cols, const float o[4]) {
+    if (VEC) {
+        if (c0 < cols) *reinterpret_cast<float4*>(row + c0) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (c0 + q < cols) row[c0 + q] = o[q];
+    }
+}
+
+__device__ __forceinline__ float stencil9(const StencilW& w, const float* up, const float* md, const float* dn, int q) {
+    float s = 0.0f;
+    s = __fmaf_rn(w.w[0], up[q], s);
+    s = __fmaf_rn(w.w[1], up[q + 1], s);
+    s = __fmaf_rn(w.w[2], up[q + 2], s);
+    s = __fmaf_rn(w.w[3], md[q], s);
+    s = __fmaf_rn(w.w[4], md[q + 1], s);
+    s = __fmaf_rn(w.w[5], md[q + 2], s);
+    s = __fmaf_rn(w.w[6], dn[q], s);
+    s = __fmaf_rn(w.w[7], dn[q + 1], s);
+    s = __fmaf_rn(w.w[8], dn[q + 2], s);
+    return s;
+}
+
+template <bool VEC, bool CHAIN>
+__global__ void __launch_bounds__(kStencilThreads, CHAIN ? 6 : 8)
+    stencil3_kernel(StencilOut out, const float* __restrict__ in, int64_t rows, int64_t cols, StencilW w,
+                    StencilW w2, int strip) {
     const int lane = threadIdx.x & 31;
     const int64_t c0 = ((int64_t)blockIdx.x * kStencilThreads + threadIdx.x) * 4;
     const int64_t r0 = (int64_t)blockIdx.y * strip;
@@ -417,28 +456,26 @@ __global__ void __launch_bounds__(kStencilThreads, 8) stencil3_kernel(float* __r
             if (row >= r1) break;  // block-uniform
             ring[k].spread(dn, lane);                                            // row + 1
             ring[k].load(in, row + 1 + kStencilAhead, ylim, cols, c0, lane);  // in flight for the next rows
+            const int64_t off = row * cols;
             float o[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float s = 0.0f;
-                s = __fmaf_rn(w.w[0], up[q], s);
-                s = __fmaf_rn(w.w[1], up[q + 1], s);
-                s = __fmaf_rn(w.w[2], up[q + 2], s);
-                s = __fmaf_rn(w.w[3], md[q], s);
-                s = __fmaf_rn(w.w[4], md[q + 1], s);
-                s = __fmaf_rn(w.w[5], md[q + 2], s);
-                s = __fmaf_rn(w.w[6], dn[q], s);
-                s = __fmaf_rn(w.w[7], dn[q + 1], s);
-                s = __fmaf_rn(w.w[8], dn[q + 2], s);
-                o[q] = s;
-            }
-            float* po = out + row * cols;
-            if (VEC) {
-                if (c0 < cols) *reinterpret_cast<float4*>(po + c0) = make_float4(o[0], o[1], o[2], o[3]);
+            for (int q = 0; q < 4; ++q) o[q] = stencil9(w, up, md, dn, q);
+            if constexpr (!CHAIN) {
+                store4<VEC>(out.g1 + off, c0, cols, o);
             } else {
+                float o2[4], a[4], b[4], m[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (c0 + q < cols) po[c0 + q] = o[q];
+                for (int q = 0; q < 4; ++q) {
+                    o2[q] = stencil9(w2, up, md, dn, q);
+                    a[q] = __fmul_rn(o[q], o[q]);
+                    b[q] = __fmul_rn(o2[q], o2[q]);
+                    m[q] = out.swap ? __fmaf_rn(out.alpha, a[q], b[q]) : __fmaf_rn(out.alpha, b[q], a[q]);
+                }
+                if (out.g1) store4<VEC>(out.g1 + off, c0, cols, o);
+                if (out.g2) store4<VEC>(out.g2 + off, c0, cols, o2);
+                if (out.s1) store4<VEC>(out.s1 + off, c0, cols, a);
+                if (out.s2) store4<VEC>(out.s2 + off, c0, cols, b);
+                store4<VEC>(out.m + off, c0, cols, m);
             }
 #pragma unroll
             for (int t = 0; t < 6; ++t) {
@@ -560,27 +597,49 @@ cudaError_t launch_colmax(float* out, const float* in, int64_t rows, int64_t col
     return cudaGetLastError();
 }
 
-cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st) {
-    StencilW w;
-    if (!stencil_weights(preset, w.w)) return cudaErrorInvalidValue;
+namespace {
+cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t rows, int64_t cols, int p1, int p2,
+                                bool chain, cudaStream_t st) {
+    StencilW w, w2;
+    if (!stencil_weights(p1, w.w) || (chain && !stencil_weights(p2, w2.w))) return cudaErrorInvalidValue;
+    if (!chain) w2 = w;
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     const int64_t gx = ((cols + 3) / 4 + kStencilThreads - 1) / kStencilThreads;
     if (gx > 0x7fffffff) return cudaErrorInvalidValue;
-    // strips of rows: about 8 resident 128-thread blocks per SM (<= 64 registers), two
-    // waves, and at least 16 rows per strip so that the two halo rows stay a small share
-    const int64_t want_blocks = (int64_t)sm_count() * 16;
+    // strips of rows: two waves of the resident 128-thread blocks (8 per SM at <= 64
+    // registers, 6 for the chain), and at least 16 rows per strip so that the two halo
+    // rows stay a small share
+    const int64_t want_blocks = (int64_t)sm_count() * (chain ? 12 : 16);
     int64_t strips = (want_blocks + gx - 1) / gx;
     int64_t strip = (rows + strips - 1) / strips;
     if (strip < 16) strip = 16;
     if ((rows + strip - 1) / strip > 65535) strip = (rows + 65534) / 65535;
     if (strip > 0x7fffffff) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)gx, (unsigned)((rows + strip - 1) / strip));
-    const bool vec = (cols % 4 == 0) && (((uintptr_t)in | (uintptr_t)out) & 15u) == 0;
-    if (vec)
-        stencil3_kernel<true><<<grid, kStencilThreads, 0, st>>>(out, in, rows, cols, w, (int)strip);
-    else
-        stencil3_kernel<false><<<grid, kStencilThreads, 0, st>>>(out, in, rows, cols, w, (int)strip);
+    uintptr_t ptrs = (uintptr_t)in | (uintptr_t)o.m | (uintptr_t)o.g1 | (uintptr_t)o.g2 | (uintptr_t)o.s1 |
+                     (uintptr_t)o.s2;
+    const bool vec = (cols % 4 == 0) && (ptrs & 15u) == 0;
+    if (chain) {
+        if (vec) stencil3_kernel<true, true><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, (int)strip);
+        else stencil3_kernel<false, true><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, (int)strip);
+    } else {
+        if (vec) stencil3_kernel<true, false><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, (int)strip);
+        else stencil3_kernel<false, false><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, (int)strip);
+    }
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st) {
+    const StencilOut o{out, nullptr, nullptr, nullptr, nullptr, 0.0f, 0};
+    return launch_stencil_pass(o, in, rows, cols, preset, preset, false, st);
+}
+
+cudaError_t launch_grad_chain(const float* in, int64_t rows, int64_t cols, int p1, int p2, float alpha, bool swap,
+                              float* g1, float* g2, float* s1, float* s2, float* m, cudaStream_t st) {
+    if (!m) return cudaErrorInvalidValue;
+    const StencilOut o{g1, g2, s1, s2, m, alpha, swap ? 1 : 0};
+    return launch_stencil_pass(o, in, rows, cols, p1, p2, true, st);
 }
 
 cudaError_t launch_wait_selftest(int* flag, int* err, double limit_s, cudaStream_t st) {

@@ -1,9 +1,10 @@
 // Loop-program runtime and the C ABI (include/gao.h).
 //
-// A program is a list of buffers and loops (Sec. 4: the parallelisable loops of the
-// application, gene length a = loop count).  prog_run executes the loops in order,
-// loop i on the GPU when gene bit i is 1 and on the host otherwise, and moves a
-// buffer between host and device only when a loop needs it on the other side
+// A program is a list of buffers and loops (Sec. 4: the application's loops; those that
+// pass the parallelisability check are numbered 0..a-1 and make up the gene).
+// prog_run executes the loops in order, offloadable loop k on the GPU when gene bit k
+// is 1 and every other loop on the host, and moves a buffer between host and device
+// only when a loop needs it on the other side
 // (Sec. 3.3: transfers between CPU and GPU memory are what make some loop
 // combinations slower than others).  Residency is tracked per buffer with two bits
 // (valid on host, valid on device).  The time of a run is the wall time from the
@@ -374,6 +375,10 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
         p->verdict.push_back((int8_t)offload_verdict(loops[i]));
         if (p->verdict.back() == GAO_OFFLOAD_OK) p->gene_loop.push_back(i);
     }
+    if (p->opts.fuse_chains == GAO_FUSE_GENE && p->gene_loop.size() >= 64) {
+        delete p;
+        return fail(GAO_EINVAL, "64 offloadable loops leave no gene bit for GAO_FUSE_GENE");
+    }
     p->lay = plan(loops, n_loops, bufs, n_bufs, p->opts);
     auto bail = [&](gao_status st) {
         free_prog(p);
@@ -715,6 +720,65 @@ gao_status run_cpu_loop(RunCtx& R, int li) {
 
 namespace {
 
+// A gradient chain the stencil loop li can run as one pass when the gene puts it all on
+// the GPU: STENCIL3 (X -> g1), STENCIL3 (X -> g2), SQUARE of g1 and of g2 (either order),
+// AXPY of the two squares (either order) in loops li..li+4.  The image is read once; an
+// intermediate that is neither an OUTPUT buffer nor read by a later loop is not written.
+struct GradChain {
+    int x = -1, g1 = -1, g2 = -1, s1 = -1, s2 = -1, m = -1;
+    int p1 = 0, p2 = 0;
+    float alpha = 1.0f;
+    bool swap = false;
+    bool live[4] = {true, true, true, true};  // g1, g2, s1, s2
+};
+
+bool find_grad_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, GradChain* gc) {
+    if (!fuse || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT) return false;
+    const int n = (int)p->loops.size();
+    if (li + 4 >= n) return false;
+    for (int k = li; k <= li + 4; ++k)
+        if (!((mask >> k) & 1)) return false;
+    const gao_loop* L = &p->loops[(size_t)li];
+    if (L[0].kind != GAO_LOOP_STENCIL3 || L[1].kind != GAO_LOOP_STENCIL3 || L[2].kind != GAO_LOOP_SQUARE ||
+        L[3].kind != GAO_LOOP_SQUARE || L[4].kind != GAO_LOOP_AXPY)
+        return false;
+    GradChain c;
+    c.x = L[0].ins[0];
+    if (L[1].ins[0] != c.x) return false;
+    c.g1 = L[0].outs[0];
+    c.g2 = L[1].outs[0];
+    c.p1 = (int)(L[0].flags & ~GAO_LOOP_EXTERNAL_CALL);
+    c.p2 = (int)(L[1].flags & ~GAO_LOOP_EXTERNAL_CALL);
+    if (L[2].ins[0] == c.g1 && L[3].ins[0] == c.g2) {
+        c.s1 = L[2].outs[0];
+        c.s2 = L[3].outs[0];
+    } else if (L[2].ins[0] == c.g2 && L[3].ins[0] == c.g1) {
+        c.s1 = L[3].outs[0];
+        c.s2 = L[2].outs[0];
+    } else {
+        return false;
+    }
+    if (L[4].ins[0] == c.s1 && L[4].ins[1] == c.s2) c.swap = false;
+    else if (L[4].ins[0] == c.s2 && L[4].ins[1] == c.s1) c.swap = true;
+    else return false;
+    c.m = L[4].outs[0];
+    c.alpha = (float)L[4].alpha;
+    const int bufs[6] = {c.x, c.g1, c.g2, c.s1, c.s2, c.m};
+    for (int i = 0; i < 6; ++i)
+        for (int j = i + 1; j < 6; ++j)
+            if (bufs[i] == bufs[j]) return false;
+    const int inter[4] = {c.g1, c.g2, c.s1, c.s2};
+    for (int t = 0; t < 4; ++t) {
+        bool live = p->bufs[(size_t)inter[t]].d.role == GAO_BUF_OUTPUT;
+        for (int j = li + 5; j < n && !live; ++j)
+            for (int b : loop_inputs(p->loops[(size_t)j]))
+                if (b == inter[t]) live = true;
+        c.live[t] = live;
+    }
+    *gc = c;
+    return true;
+}
+
 // A chain the GEMM loop li can run as one pass when the gene puts it all on the GPU:
 // GEMM (C) -> AXPY (D = C + a X) -> TRANSPOSE (E = D^T) [-> FROBENIUS of E, later, with no
 // loop in between writing E].  The buffers must be distinct so that the epilogue's
@@ -898,6 +962,41 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
         }
         cudaEvent_t* ev = &p->ev[(size_t)li * 6];
         Chain chain;
+        GradChain gch;
+        if (gpu && L.kind == GAO_LOOP_STENCIL3 && find_grad_chain(p, li, gene_mask, fuse, &gch)) {
+            BufState& X = p->bufs[(size_t)gch.x];
+            const bool copies = !X.vd;
+            if (copies) GAO_CUDA_TRY(record_timing(ev[0], p->st));
+            if ((status = make_valid(R, gch.x, true, S)) != GAO_OK) break;
+            if (copies) {
+                GAO_CUDA_TRY(record_timing(ev[1], p->st));
+                p->ev_used[(size_t)li] |= 1;
+            }
+            auto dptr = [&](int b, bool live) { return live ? (float*)p->bufs[(size_t)b].dev : nullptr; };
+            GAO_CUDA_TRY(record_timing(ev[2], p->st));
+            const cudaError_t e = launch_grad_chain((const float*)X.dev, X.d.rows, X.d.cols, gch.p1, gch.p2,
+                                                   gch.alpha, gch.swap, dptr(gch.g1, gch.live[0]),
+                                                   dptr(gch.g2, gch.live[1]), dptr(gch.s1, gch.live[2]),
+                                                   dptr(gch.s2, gch.live[3]), (float*)p->bufs[(size_t)gch.m].dev,
+                                                   p->st);
+            if (e != cudaSuccess) {
+                status = cuda_fail(e, "gradient chain launch");
+                break;
+            }
+            GAO_CUDA_TRY(record_timing(ev[3], p->st));
+            p->ev_used[(size_t)li] |= 2;
+            S.launches += X.d.rows * X.d.cols > 0;
+            const int outs[5] = {gch.g1, gch.g2, gch.s1, gch.s2, gch.m};
+            for (int t = 0; t < 5; ++t) {
+                BufState& B = p->bufs[(size_t)outs[t]];
+                B.vh = false;
+                B.vd = t == 4 || gch.live[t];  // an unwritten intermediate holds nothing
+            }
+            for (int j = li + 1; j <= li + 4; ++j) fused |= 1ULL << j;
+            if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
+            if (R.timed_out) break;
+            continue;
+        }
         // a GEMM whose A comes from the host overlaps the copy (row blocks) rather than fusing
         const int64_t blocks = gpu ? pipeline_blocks(p, L) : 0;
         if (gpu && blocks == 0 && L.kind == GAO_LOOP_GEMM && find_chain(p, li, gene_mask, fuse, &chain)) {

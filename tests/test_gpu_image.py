@@ -184,3 +184,39 @@ def test_full_size_8192_sampled(gao):
     M2d = M2.astype(np.float64)
     assert abs(e - M2d.sum()) <= SUM_REL * M2d.sum()
     assert np.array_equal(q.ravel(), M2.max(axis=0))
+
+
+@pytest.mark.parametrize("outputs", [("M2", "e", "q"), ("gx", "sy", "M2", "e", "q")])
+@pytest.mark.parametrize("hw", [(64, 64), (127, 257), (300, 1001)])
+def test_fused_gradient_chain_bit_identical(gao, hw, outputs):
+    """Sobel x, Sobel y, the two squares and their sum in one pass over the blurred image:
+    the same bits as the five separate loops; dead intermediates are not written."""
+    h, w = hw
+    prog = W.image_program(h, w, W.SEED_IMAGE + 3, outputs=outputs)
+    res = {}
+    for fuse in (gao.FUSE_OFF, gao.FUSE_ON):
+        p = gao.prog_from_workload(prog, fuse_chains=fuse)
+        gao.prog_run(p, (1 << prog.n_loops) - 1)
+        res[fuse] = ({nm: gao.prog_output(p, prog.index(nm)) for nm in outputs}, gao.prog_stats(p))
+        gao.prog_destroy(p)
+    (a, _), (b, st) = res[gao.FUSE_OFF], res[gao.FUSE_ON]
+    for nm in outputs:
+        assert np.array_equal(np.asarray(a[nm]).view(np.uint64 if nm == "e" else np.uint32),
+                              np.asarray(b[nm]).view(np.uint64 if nm == "e" else np.uint32)), nm
+    assert [s["placement"] for s in st] == [1, 1, 1, 2, 2, 2, 2, 1, 1]
+    assert st[2]["launches"] == 1
+
+
+def test_gradient_chain_only_when_all_on_gpu(gao):
+    prog = W.image_program(96, 130, 45, outputs=("M2",))
+    ref = oracle.run_program(prog)
+    X = oracle.init_matrix(45, 0, 96, 130)
+    p = gao.prog_from_workload(prog, fuse_chains=gao.FUSE_GENE)
+    assert gao.prog_gene_length(p) == 10
+    for gene, fused in ((0b1111111111, True), (0b0111111111, False), (0b1111101111, False), (0b1000000000, False)):
+        gao.prog_run(p, gene)
+        st = gao.prog_stats(p)
+        assert (st[3]["placement"] == 2) == fused, bin(gene)
+        M2 = gao.prog_output(p, prog.index("M2")).astype(np.float64)
+        assert np.all(np.abs(M2 - ref["M2"]) <= m2_bound(X))
+    gao.prog_destroy(p)
