@@ -65,8 +65,9 @@ typedef enum gao_loop_kind {
     GAO_LOOP_COLMAX = 8,    /* outs[0][j] = max_i ins[0][i,j]   (1 x cols, binary32)             */
     GAO_LOOP_SUM = 9,       /* outs[0] = sum ins[0]             (1 x 1, binary64)                */
     GAO_LOOP_STENCIL3 = 10, /* outs[0][i,j] = sum_{a,b in -1..1} w_ab ins[0][i+a,j+b], ins[0] taken as 0
-                               outside the image; the nine terms are added in row-major (a, b)
-                               order with fused multiply-adds, zero terms included.  flags picks
+                               outside the image; the terms with nonzero weight are added in
+                               row-major (a, b) order with fused multiply-adds, starting from +0
+                               (for finite data the same value as adding all nine).  flags picks
                                w: 0 binomial blur (1 2 1; 2 4 2; 1 2 1)/16, 1 Laplacian
                                (0 1 0; 1 -4 1; 0 1 0), 2 Sobel x (-1 0 1; -2 0 2; -1 0 1),
                                3 Sobel y (-1 -2 -1; 0 0 0; 1 2 1).  The image-analysis loops

@@ -224,9 +224,9 @@ void cpu_colmax(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx&
     }
 }
 
-// 3x3 stencil with zero padding.  Each output adds its nine terms in row-major (a, b)
-// order with fmaf, out-of-image and zero-weight terms included, exactly as the GPU
-// kernel does, so both give the same bits.
+// 3x3 stencil with zero padding.  Each output adds its terms in row-major (a, b) order
+// with fmaf, out-of-image terms included and zero-weight terms skipped, exactly as the
+// GPU kernel does, so both give the same bits.
 void cpu_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, CpuCtx& c) {
     float w[9];
     if (!stencil_weights(preset, w)) return;
@@ -253,17 +253,11 @@ void cpu_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int p
             }
             const float *u = pad[0].data(), *m = pad[1].data(), *d = pad[2].data();
             float* o = out + i * cols;
+            const float* rowp[3] = {u, m, d};
             for (int64_t j = 0; j < cols; ++j) {
                 float s = 0.0f;
-                s = fmaf(w[0], u[j], s);
-                s = fmaf(w[1], u[j + 1], s);
-                s = fmaf(w[2], u[j + 2], s);
-                s = fmaf(w[3], m[j], s);
-                s = fmaf(w[4], m[j + 1], s);
-                s = fmaf(w[5], m[j + 2], s);
-                s = fmaf(w[6], d[j], s);
-                s = fmaf(w[7], d[j + 1], s);
-                s = fmaf(w[8], d[j + 2], s);
+                for (int t = 0; t < 9; ++t)
+                    if (w[t] != 0.0f) s = fmaf(w[t], rowp[t / 3][j + t % 3], s);
                 o[j] = s;
             }
         }

@@ -100,15 +100,22 @@ cudaError_t launch_grad_chain(const float* in, int64_t rows, int64_t cols, int p
 
 // Weights of the 3x3 stencil presets of GAO_LOOP_STENCIL3, row-major over (a, b).
 // Every weight is a small integer or a power-of-two fraction, exact in binary32.
+#ifdef __CUDACC__
+#define GAO_HD __host__ __device__
+#else
+#define GAO_HD
+#endif
+GAO_HD constexpr float stencil_preset(int preset, int t) {
+    // (1 2 1; 2 4 2; 1 2 1) / 16, (0 1 0; 1 -4 1; 0 1 0), (-1 0 1; -2 0 2; -1 0 1),
+    // (-1 -2 -1; 0 0 0; 1 2 1)
+    return preset == 0 ? (t == 4 ? 0.25f : (t & 1) ? 0.125f : 0.0625f)
+         : preset == 1 ? (t == 4 ? -4.0f : (t & 1) ? 1.0f : 0.0f)
+         : preset == 2 ? (float)((t % 3) - 1) * (t / 3 == 1 ? 2.0f : 1.0f)
+                       : (float)((t / 3) - 1) * (t % 3 == 1 ? 2.0f : 1.0f);
+}
 inline bool stencil_weights(int preset, float w[9]) {
-    static const float k[4][9] = {
-        {0.0625f, 0.125f, 0.0625f, 0.125f, 0.25f, 0.125f, 0.0625f, 0.125f, 0.0625f},
-        {0.0f, 1.0f, 0.0f, 1.0f, -4.0f, 1.0f, 0.0f, 1.0f, 0.0f},
-        {-1.0f, 0.0f, 1.0f, -2.0f, 0.0f, 2.0f, -1.0f, 0.0f, 1.0f},
-        {-1.0f, -2.0f, -1.0f, 0.0f, 0.0f, 0.0f, 1.0f, 2.0f, 1.0f},
-    };
     if (preset < 0 || preset > 3) return false;
-    for (int t = 0; t < 9; ++t) w[t] = k[preset][t];
+    for (int t = 0; t < 9; ++t) w[t] = stencil_preset(preset, t);
     return true;
 }
 cudaError_t launch_wait_selftest(int* flag, int* err, double limit_s, cudaStream_t st);

@@ -415,30 +415,37 @@ __device__ __forceinline__ void store4(float* row, int64_t c0, int64_t cols, con
     }
 }
 
+// One output: the terms with nonzero weight in row-major order, fused multiply-adds from
+// +0.  With a preset known at compile time (P >= 0) the zero terms are not even emitted;
+// with run-time weights (P < 0) they are skipped by a warp-uniform test.  Starting from +0
+// the partial sum is never -0, so a zero-weight term would not have changed it for finite
+// data: both forms give the bits of the nine-term sum.
+template <int P>
 __device__ __forceinline__ float stencil9(const StencilW& w, const float* up, const float* md, const float* dn, int q) {
+    const float* rowp[3] = {up, md, dn};
     float s = 0.0f;
-    s = __fmaf_rn(w.w[0], up[q], s);
-    s = __fmaf_rn(w.w[1], up[q + 1], s);
-    s = __fmaf_rn(w.w[2], up[q + 2], s);
-    s = __fmaf_rn(w.w[3], md[q], s);
-    s = __fmaf_rn(w.w[4], md[q + 1], s);
-    s = __fmaf_rn(w.w[5], md[q + 2], s);
-    s = __fmaf_rn(w.w[6], dn[q], s);
-    s = __fmaf_rn(w.w[7], dn[q + 1], s);
-    s = __fmaf_rn(w.w[8], dn[q + 2], s);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        const float wt = P >= 0 ? stencil_preset(P, t) : w.w[t];
+        if (wt != 0.0f) s = __fmaf_rn(wt, rowp[t / 3][q + t % 3], s);
+    }
     return s;
 }
 
-template <bool VEC, bool CHAIN>
-__global__ void __launch_bounds__(kStencilThreads, CHAIN ? 6 : 8)
+constexpr int kChainAhead = 2;   // rows of loads in flight in the chain variant
+constexpr int kChainBlocks = 8;  // resident blocks per SM the chain variant is built for
+
+template <bool VEC, bool CHAIN, int P1, int P2>
+__global__ void __launch_bounds__(kStencilThreads, CHAIN ? kChainBlocks : 8)
     stencil3_kernel(StencilOut out, const float* __restrict__ in, int64_t rows, int64_t cols, StencilW w,
                     StencilW w2, int strip) {
+    constexpr int AHEAD = CHAIN ? kChainAhead : kStencilAhead;
     const int lane = threadIdx.x & 31;
     const int64_t c0 = ((int64_t)blockIdx.x * kStencilThreads + threadIdx.x) * 4;
     const int64_t r0 = (int64_t)blockIdx.y * strip;
     const int64_t r1 = r0 + strip < rows ? r0 + strip : rows;
     const int64_t ylim = r1 + 1 < rows ? r1 + 1 : rows;  // rows >= ylim are never needed
-    StencilRow<VEC> ring[kStencilAhead];
+    StencilRow<VEC> ring[AHEAD];
     float up[6], md[6], dn[6];
     {
         StencilRow<VEC> a;
@@ -448,25 +455,25 @@ __global__ void __launch_bounds__(kStencilThreads, CHAIN ? 6 : 8)
         a.spread(md, lane);
     }
 #pragma unroll
-    for (int k = 0; k < kStencilAhead; ++k) ring[k].load(in, r0 + 1 + k, ylim, cols, c0, lane);
-    for (int64_t i = r0; i < r1; i += kStencilAhead) {
+    for (int k = 0; k < AHEAD; ++k) ring[k].load(in, r0 + 1 + k, ylim, cols, c0, lane);
+    for (int64_t i = r0; i < r1; i += AHEAD) {
 #pragma unroll
-        for (int k = 0; k < kStencilAhead; ++k) {
+        for (int k = 0; k < AHEAD; ++k) {
             const int64_t row = i + k;
             if (row >= r1) break;  // block-uniform
             ring[k].spread(dn, lane);                                            // row + 1
-            ring[k].load(in, row + 1 + kStencilAhead, ylim, cols, c0, lane);  // in flight for the next rows
+            ring[k].load(in, row + 1 + AHEAD, ylim, cols, c0, lane);  // in flight for the next rows
             const int64_t off = row * cols;
             float o[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = stencil9(w, up, md, dn, q);
+            for (int q = 0; q < 4; ++q) o[q] = stencil9<P1>(w, up, md, dn, q);
             if constexpr (!CHAIN) {
                 store4<VEC>(out.g1 + off, c0, cols, o);
             } else {
                 float o2[4], a[4], b[4], m[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    o2[q] = stencil9(w2, up, md, dn, q);
+                    o2[q] = stencil9<P2>(w2, up, md, dn, q);
                     a[q] = __fmul_rn(o[q], o[q]);
                     b[q] = __fmul_rn(o2[q], o2[q]);
                     m[q] = out.swap ? __fmaf_rn(out.alpha, a[q], b[q]) : __fmaf_rn(out.alpha, b[q], a[q]);
@@ -609,7 +616,7 @@ cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t ro
     // strips of rows: two waves of the resident 128-thread blocks (8 per SM at <= 64
     // registers, 6 for the chain), and at least 16 rows per strip so that the two halo
     // rows stay a small share
-    const int64_t want_blocks = (int64_t)sm_count() * (chain ? 12 : 16);
+    const int64_t want_blocks = (int64_t)sm_count() * 2 * (chain ? kChainBlocks : 8);
     int64_t strips = (want_blocks + gx - 1) / gx;
     int64_t strip = (rows + strips - 1) / strips;
     if (strip < 16) strip = 16;
@@ -619,13 +626,31 @@ cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t ro
     uintptr_t ptrs = (uintptr_t)in | (uintptr_t)o.m | (uintptr_t)o.g1 | (uintptr_t)o.g2 | (uintptr_t)o.s1 |
                      (uintptr_t)o.s2;
     const bool vec = (cols % 4 == 0) && (ptrs & 15u) == 0;
+    const int sp = (int)strip;
+#define GAO_STENCIL_LAUNCH(V, C, A, B) \
+    stencil3_kernel<V, C, A, B><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, sp)
     if (chain) {
-        if (vec) stencil3_kernel<true, true><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, (int)strip);
-        else stencil3_kernel<false, true><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, (int)strip);
+        // the image program's pair (Sobel x, Sobel y) with compile-time weights; any
+        // other pair with run-time weights
+        if (p1 == 2 && p2 == 3) {
+            if (vec) GAO_STENCIL_LAUNCH(true, true, 2, 3);
+            else GAO_STENCIL_LAUNCH(false, true, 2, 3);
+        } else if (p1 == 3 && p2 == 2) {
+            if (vec) GAO_STENCIL_LAUNCH(true, true, 3, 2);
+            else GAO_STENCIL_LAUNCH(false, true, 3, 2);
+        } else {
+            if (vec) GAO_STENCIL_LAUNCH(true, true, -1, -1);
+            else GAO_STENCIL_LAUNCH(false, true, -1, -1);
+        }
     } else {
-        if (vec) stencil3_kernel<true, false><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, (int)strip);
-        else stencil3_kernel<false, false><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, (int)strip);
+        switch (p1) {
+            case 0: if (vec) GAO_STENCIL_LAUNCH(true, false, 0, 0); else GAO_STENCIL_LAUNCH(false, false, 0, 0); break;
+            case 1: if (vec) GAO_STENCIL_LAUNCH(true, false, 1, 1); else GAO_STENCIL_LAUNCH(false, false, 1, 1); break;
+            case 2: if (vec) GAO_STENCIL_LAUNCH(true, false, 2, 2); else GAO_STENCIL_LAUNCH(false, false, 2, 2); break;
+            default: if (vec) GAO_STENCIL_LAUNCH(true, false, 3, 3); else GAO_STENCIL_LAUNCH(false, false, 3, 3); break;
+        }
     }
+#undef GAO_STENCIL_LAUNCH
     return cudaGetLastError();
 }
 }  // namespace
