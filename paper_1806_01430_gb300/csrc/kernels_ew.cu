@@ -512,7 +512,7 @@ __global__ void wait_selftest_kernel(volatile int* flag, int* err, unsigned long
 
 }  // namespace
 
-int reduce_blocks() { return sm_count() * 4; }
+int reduce_blocks() { return sm_count() * 8; }  // a full wave of 256-thread blocks
 
 cudaError_t launch_row_exponents(int8_t* e, int64_t rows, uint64_t seed, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
