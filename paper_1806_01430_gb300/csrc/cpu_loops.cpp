@@ -53,19 +53,61 @@ void cpu_init(float* out, int64_t rows, int64_t cols, uint64_t seed, uint32_t bu
     }
 }
 
-// C = alpha*A@B + beta*C0.  Work is split into tasks of (up to 512 rows) x (up to
-// 256 columns); each task walks K in chunks of `kchunk`, keeping a 256 x kchunk
-// panel of B hot in cache while 16-row register/L1 blocks of the chunk sum are
-// formed and then added into the task's binary32 outer sum.
+namespace {
+
+// Register-blocked piece of a K chunk: out[i][j] += sum over k of a[i][k] * b[k][j] for an
+// MR x NR block, the sum formed in k order with fmaf into zero-initialised registers (the
+// chunk sum) and then added to out.  bp is B packed for this block: bp[k * NR + j].
+template <int MR, int NR>
+inline void gemm_micro(const float* a, int64_t lda, const float* bp, int64_t kn, float* out, int64_t ldo) {
+    float acc[MR][NR];
+#pragma GCC unroll 16
+    for (int i = 0; i < MR; ++i)
+#pragma GCC unroll 16
+        for (int j = 0; j < NR; ++j) acc[i][j] = 0.0f;
+    for (int64_t k = 0; k < kn; ++k) {
+        const float* b = bp + k * NR;
+#pragma GCC unroll 16
+        for (int i = 0; i < MR; ++i) {
+            const float av = a[i * lda + k];
+#pragma GCC unroll 16
+            for (int j = 0; j < NR; ++j) acc[i][j] = fmaf(av, b[j], acc[i][j]);
+        }
+    }
+#pragma GCC unroll 16
+    for (int i = 0; i < MR; ++i)
+#pragma GCC unroll 16
+        for (int j = 0; j < NR; ++j) out[i * ldo + j] += acc[i][j];
+}
+
+// The same for a ragged edge block (rn <= MR rows, jn <= NR columns).
+template <int MR, int NR>
+inline void gemm_edge(const float* a, int64_t lda, const float* bp, int64_t kn, float* out, int64_t ldo, int64_t rn,
+                      int64_t jn) {
+    for (int64_t i = 0; i < rn; ++i)
+        for (int64_t j = 0; j < jn; ++j) {
+            float s = 0.0f;
+            for (int64_t k = 0; k < kn; ++k) s = fmaf(a[i * lda + k], bp[k * NR + j], s);
+            out[i * ldo + j] += s;
+        }
+}
+
+}  // namespace
+
+// C = alpha*A@B + beta*C0.  Work is split into tasks of (up to 512 rows) x (up to 256
+// columns); each task walks K in chunks of `kchunk`: the chunk's B panel is packed in
+// 16-column slabs, and 6 x 16 register blocks form the chunk sums (k in order, fmaf),
+// which are added into the task's binary32 outer sums chunk by chunk.
 void cpu_gemm(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K, float alpha,
               float beta, int kchunk, CpuCtx& c) {
-    constexpr int64_t JT = 256, RB = 16, RS = 512;
+    constexpr int64_t JT = 256, RS = 512;
+    constexpr int MR = 6, NR = 16;
     const int64_t kc = kchunk > 0 ? kchunk : 256;
     const int64_t ntj = (N + JT - 1) / JT, nts = (M + RS - 1) / RS;
     std::atomic<bool> stop{false};
 #pragma omp parallel num_threads(nthreads(c))
     {
-        std::vector<float> outer((size_t)RS * JT), acc((size_t)RB * JT);
+        std::vector<float> outer((size_t)RS * JT), pack((size_t)std::min(kc, std::max<int64_t>(K, 1)) * JT);
 #pragma omp for schedule(dynamic, 1)
         for (int64_t task = 0; task < ntj * nts; ++task) {
             if (stop.load(std::memory_order_relaxed)) continue;
@@ -77,22 +119,27 @@ void cpu_gemm(float* C, const float* A, const float* B, const float* C0, int64_t
                     stop = true;
                     break;
                 }
-                const int64_t k1 = std::min(K, k0 + kc);
-                for (int64_t r0 = 0; r0 < in; r0 += RB) {
-                    const int64_t rn = std::min(RB, in - r0);
-                    std::fill(acc.begin(), acc.begin() + rn * JT, 0.0f);
-                    for (int64_t k = k0; k < k1; ++k) {
-                        const float* b = B + k * N + j0;
-                        for (int64_t r = 0; r < rn; ++r) {
-                            const float a = A[(i0 + r0 + r) * K + k];
-                            float* ar = acc.data() + r * JT;
-                            for (int64_t j = 0; j < jn; ++j) ar[j] = fmaf(a, b[j], ar[j]);
-                        }
+                const int64_t kn = std::min(kc, K - k0);
+                // pack B[k0 .. k0+kn) x [j0 .. j0+jn) as slabs [jn / NR][kn][NR] (zero-filled)
+                for (int64_t jb = 0; jb < jn; jb += NR) {
+                    float* slab = pack.data() + jb * kn;
+                    const int64_t w = std::min<int64_t>(NR, jn - jb);
+                    for (int64_t k = 0; k < kn; ++k) {
+                        const float* brow = B + (k0 + k) * N + j0 + jb;
+                        for (int64_t j = 0; j < NR; ++j) slab[k * NR + j] = j < w ? brow[j] : 0.0f;
                     }
-                    for (int64_t r = 0; r < rn; ++r) {
-                        float* orow = outer.data() + (r0 + r) * JT;
-                        const float* ar = acc.data() + r * JT;
-                        for (int64_t j = 0; j < jn; ++j) orow[j] += ar[j];
+                }
+                for (int64_t jb = 0; jb < jn; jb += NR) {
+                    const float* slab = pack.data() + jb * kn;
+                    const int64_t w = std::min<int64_t>(NR, jn - jb);
+                    for (int64_t r0 = 0; r0 < in; r0 += MR) {
+                        const float* a = A + (i0 + r0) * K + k0;
+                        float* out = outer.data() + r0 * JT + jb;
+                        const int64_t rn = std::min<int64_t>(MR, in - r0);
+                        if (rn == MR && w == NR)
+                            gemm_micro<MR, NR>(a, K, slab, kn, out, JT);
+                        else
+                            gemm_edge<MR, NR>(a, K, slab, kn, out, JT, rn, w);
                     }
                 }
             }
