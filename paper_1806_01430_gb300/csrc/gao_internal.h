@@ -142,10 +142,13 @@ size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K);
 struct TcFuse;
 // One row block of a larger GEMM (the split-precision paths): the scratch is laid out for
 // m_layout rows (the whole problem), and b_ready says that B's planes are already in it
-// (split by an earlier row block of the same problem).
+// (split by an earlier row block of the same problem).  With a fused chain the blocks'
+// norm partials go to one array (offset by row_tile0) that the last block reduces.
 struct TcPart {
     int64_t m_layout;
     bool b_ready;
+    int64_t row_tile0;  // fused chain: 128-row tiles of the problem before this block
+    bool last;          // fused chain: the last block (reduces the norm's partials)
 };
 cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M,
                            int64_t N, int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,

@@ -347,7 +347,7 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int64_t col = gcol + 16 * h + 4 * j + q;
-                        if (col < e.N) e.E[col * (int64_t)e.M + grow] = dv[q];
+                        if (col < e.N) e.E[col * e.ldE + grow] = dv[q];
                     }
                 }
             }
@@ -1034,7 +1034,7 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     }
     const int P = planes_of(prec);
     const int64_t Mlay = part ? part->m_layout : M;
-    if (Mlay < M || (part && fuse)) {
+    if (Mlay < M) {
         if (why) *why = "bad row-block arguments";
         return cudaErrorInvalidValue;
     }
@@ -1085,13 +1085,16 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     if (!make_map(&tb, pb, Kp, (int64_t)P * Np, bn, false, why)) return cudaErrorInvalidValue;
     EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
                (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, nullptr, nullptr, 0, 0};
-    double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, M, N, K));
+    double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, Mlay, N, K));
+    const int64_t tiles_n = (N + bn - 1) / bn;
+    ep.ldE = M;
     if (fuse) {
         ep.X = fuse->X;
         ep.D = fuse->D;
         ep.E = fuse->E;
+        ep.ldE = fuse->ldE > 0 ? fuse->ldE : M;
         ep.alpha2 = fuse->alpha2;
-        ep.frob_part = fuse->frob_out ? fpart : nullptr;
+        ep.frob_part = fuse->frob_out ? fpart + (part ? part->row_tile0 : 0) * tiles_n * kEpiWarps : nullptr;
         ep.fuse = 1;
     }
     if (ev.k0) record_timing(ev.k0, st);
@@ -1112,8 +1115,8 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     if (e != cudaSuccess) return e;
     ev.launches += 1;
     if (ev.k1) record_timing(ev.k1, st);
-    if (fuse && fuse->frob_out) {
-        const int64_t tiles = (Mp / BM) * ((N + bn - 1) / bn);
+    if (fuse && fuse->frob_out && (!part || part->last)) {
+        const int64_t tiles = (ru(Mlay, BM) / BM) * tiles_n;  // every block's tiles
         frob_partials_kernel<<<1, 256, 0, st>>>(fpart, tiles * kEpiWarps, fuse->frob_out);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ev.launches += 1;

@@ -27,6 +27,7 @@ struct EpiArgs {
     double* frob_part;
     float alpha2;
     int fuse;
+    int64_t ldE;       // row stride of E (0: M); a row block writes columns of a larger E
 };
 
 // Loops of a chain GEMM -> AXPY (D = C + alpha2 X) -> TRANSPOSE (E = D^T) [-> FROBENIUS of
@@ -37,6 +38,7 @@ struct TcFuse {
     float* E;
     double* frob_out;  // nullptr: no Frobenius loop in the chain
     float alpha2;
+    int64_t ldE;       // row stride of E (0: the launch's M)
 };
 
 // One problem of a grouped launch: its operand planes' TMA descriptors and epilogue.

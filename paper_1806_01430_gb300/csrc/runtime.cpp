@@ -859,7 +859,7 @@ int64_t pipeline_blocks(const gao_prog* p, const gao_loop& L) {
     return blocks >= 2 ? blocks : 0;
 }
 
-gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks) {
+gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain* ch) {
     gao_prog* p = R.p;
     const gao_loop& L = p->loops[(size_t)li];
     gao_loop_stat& S = p->stats[(size_t)li];
@@ -903,19 +903,34 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks) {
     GAO_CUDA_TRY(record_timing(ev[2], st));
     GAO_CUDA_TRY(cudaStreamWaitEvent(st, b_done, 0));
     const float beta = C0 ? (float)L.beta : 0.0f;
+    // a fused chain: each block's epilogue also writes its rows of D = C + alpha2 X, its
+    // columns of E = D^T and its norm partials; X is the GEMM's A (copied in the blocks) or
+    // already on the device
+    const gao_loop* XL = ch ? &p->loops[(size_t)ch->axpy] : nullptr;
+    auto fdev = [&](int b) { return (float*)p->bufs[(size_t)b].dev; };
     int i = 0;
     for (int64_t r0 = 0; r0 < M; r0 += rows, ++i) {
         const int64_t r1 = std::min(M, r0 + rows);
         GAO_CUDA_TRY(cudaStreamWaitEvent(st, p->pipe_ev[2 + (size_t)i], 0));
-        TcPart part{M, i > 0};
+        TcPart part{M, i > 0, r0 / 128, i == nb - 1};
         TcEvents tev{i == 0 ? ev[4] : nullptr, i == nb - 1 ? ev[5] : nullptr, 0};
         std::string why;
         float* c = (float*)C.dev + (size_t)r0 * N;
         const float* c0 = C0 ? (const float*)C0->dev + (size_t)r0 * N : c;
+        TcFuse fz{};
+        if (ch) {
+            const gao_loop& T = p->loops[(size_t)ch->transpose];
+            fz.X = fdev(XL->ins[1]) + (size_t)r0 * N;
+            fz.D = fdev(XL->outs[0]) + (size_t)r0 * N;
+            fz.E = fdev(T.outs[0]) + r0;
+            fz.frob_out = ch->frob >= 0 ? (double*)p->bufs[(size_t)p->loops[(size_t)ch->frob].outs[0]].dev : nullptr;
+            fz.alpha2 = (float)XL->alpha;
+            fz.ldE = M;
+        }
         cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, c, (const float*)A.dev + (size_t)r0 * K,
                                        (const float*)B.dev, c0, r1 - r0, N, K, (float)L.alpha, beta, p->opts.kchunk,
                                        p->opts.tile_cfg, p->arena + p->lay.tc_off, p->lay.tc_bytes,
-                                       (int*)(p->arena + p->lay.err_off), st, tev, &why, nullptr, &part);
+                                       (int*)(p->arena + p->lay.err_off), st, tev, &why, ch ? &fz : nullptr, &part);
         if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "row-block GEMM") : fail(GAO_EINVAL, why);
         S.launches += tev.launches;
     }
@@ -1034,7 +1049,28 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
         if (gpu && per_loop)  // directive offload without a data region: inputs always copied in
             for (int b : ins) p->bufs[(size_t)b].vd = false;
         if (blocks > 0) {
-            if ((status = run_gpu_gemm_pipelined(R, li, blocks)) != GAO_OK) break;
+            // fused too when the chain qualifies and its X is the GEMM's A (copied in the
+            // blocks) or already on the device
+            Chain pch;
+            bool pf = find_chain(p, li, gene_mask, fuse, &pch);
+            if (pf) {
+                const int xb = p->loops[(size_t)pch.axpy].ins[1];
+                pf = xb == L.ins[0] || p->bufs[(size_t)xb].vd;
+            }
+            if ((status = run_gpu_gemm_pipelined(R, li, blocks, pf ? &pch : nullptr)) != GAO_OK) break;
+            if (pf) {
+                for (int j : {li, pch.axpy, pch.transpose, pch.frob}) {
+                    if (j < 0) continue;
+                    for (int b : loop_outputs(p->loops[(size_t)j])) {
+                        p->bufs[(size_t)b].vh = false;
+                        p->bufs[(size_t)b].vd = true;
+                    }
+                    if (j != li) fused |= 1ULL << j;
+                }
+                if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
+                if (R.timed_out) break;
+                continue;
+            }
         } else if (gpu) {
             bool copies = false;
             for (int b : ins) copies |= !p->bufs[(size_t)b].vd;

@@ -124,3 +124,27 @@ def test_fusion_as_a_gene_bit(gao):
     with pytest.raises(gao.GaoError):
         gao.batch_create([p])  # batches run loop by loop
     gao.prog_destroy(p)
+
+
+@pytest.mark.parametrize("n,prec", [(2048, 3), (2500, 2), (2304, 1)])
+def test_fused_chain_in_copy_overlapped_gemm(gao, n, prec):
+    """Host inputs: the GEMM runs in row blocks overlapped with the copy, and with fusion
+    each block's epilogue also writes its rows of D, its columns of E and its norm
+    partials.  Same C, D, E, r as the unfused run; the norm within the reduction bound."""
+    seed = 14
+    hp = W.host_input_program(n, seed, outputs=("C", "D", "E", "r", "f"))
+    ins = {nm: oracle.init_matrix(seed, b, n, n).astype(np.float32) for nm, b in (("A", 0), ("B", 1), ("C0", 2))}
+    res = {}
+    for fuse in (False, True):
+        p = gao.prog_from_workload(hp, gemm_prec=prec, fuse_chains=fuse)
+        for nm, v in ins.items():
+            gao.prog_set_input(p, hp.index(nm), v)
+        gao.prog_run(p, (1 << hp.n_loops) - 1)
+        res[fuse] = (outputs(gao, p, hp), gao.prog_stats(p))
+        gao.prog_destroy(p)
+    (a, _), (b, st) = res[False], res[True]
+    for nm in ("C", "D", "E", "r"):
+        assert np.array_equal(a[nm], b[nm]), nm
+    assert abs(a["f"] - b["f"]) <= 2e-7 * a["f"]
+    assert [s["placement"] for s in st] == [1, 2, 2, 1, 2]
+    assert st[0]["h2d_bytes"] == 3 * n * n * 4
