@@ -132,7 +132,8 @@ typedef enum gao_gemm_prec {
 
 typedef struct gao_opts {
     int32_t gemm_prec;       /* gao_gemm_prec                                               */
-    int32_t kchunk;          /* K elements per binary32 partial sum (0: library default)    */
+    int32_t kchunk;          /* K elements per binary32 partial sum (0: library default; the
+                                FP32 SIMT kernel rounds it up to a multiple of 16)          */
     int32_t tile_cfg;        /* tensor-core tile configuration: bits 0-1 tile width (0 default,
                                 1 = 128, 2 = 256 columns), bits 4-7 log2 of the raster group
                                 (0: default 16); prog_autotune picks one               */
