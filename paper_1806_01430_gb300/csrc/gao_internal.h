@@ -93,6 +93,26 @@ cudaError_t launch_relu(float* out, const float* in, int64_t n, cudaStream_t st)
 cudaError_t launch_square(float* out, const float* in, int64_t n, cudaStream_t st);
 cudaError_t launch_colmax(float* out, const float* in, int64_t rows, int64_t cols, uint32_t* keys, cudaStream_t st);
 cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st);
+
+// A linear chain of element-wise loops in one pass.  Op o computes kind 0 RELU, 1 SQUARE
+// or 2 AXPY (x + alpha y) with x = xa[i] (or the previous op's value when xa is null) and,
+// for AXPY, y = yb[i] (or the previous value); the result is stored to out[i] when out is
+// set.  The first op reads memory for every operand.
+constexpr int kMaxChainOps = 8;
+struct EwChainOp {
+    int kind;
+    float alpha;
+    const float* xa;
+    const float* yb;
+    float* out;
+};
+struct EwChain {
+    int nops;
+    int vec;  // set by launch_ew_chain
+    int64_t n;
+    EwChainOp op[kMaxChainOps];
+};
+cudaError_t launch_ew_chain(const EwChain& c, cudaStream_t st);
 // Gradient chain in one pass: g1, g2 = stencils p1, p2 of `in`; s1 = g1*g1, s2 = g2*g2;
 // m = s1 + alpha s2 (swap: s2 + alpha s1).  Null g1/g2/s1/s2 are not written.
 cudaError_t launch_grad_chain(const float* in, int64_t rows, int64_t cols, int p1, int p2, float alpha, bool swap,

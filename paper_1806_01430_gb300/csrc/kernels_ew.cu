@@ -130,6 +130,54 @@ __global__ void ew_kernel(float* __restrict__ out, const float* __restrict__ x, 
         out[i] = ew_apply<OP>(x[i], OP == Ew::Axpy ? y[i] : 0.0f, alpha);
 }
 
+// ---- element-wise chains ---------------------------------------------------------------
+
+// Consecutive element-wise loops (RELU, SQUARE, AXPY) over the same shape in one pass.
+// The chain is linear: every loop after the first reads the previous loop's value (held
+// in registers) and at most one other buffer from memory; each value is formed with the
+// separate loop's operation, and written only where `out` is set.
+__global__ void ew_chain_kernel(EwChain c) {
+    const int64_t n = c.n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    const bool vec = c.vec != 0;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; i < n; i += stride) {
+        float cur[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const int w = vec ? 4 : (int)(n - i < 4 ? n - i : 4);
+#pragma unroll
+        for (int o = 0; o < kMaxChainOps; ++o) {
+            if (o >= c.nops) break;
+            const EwChainOp& op = c.op[o];
+            float x[4], y[4];
+            auto fetch = [&](const float* src, float* dst) {
+                if (vec) {
+                    const float4 v = *reinterpret_cast<const float4*>(src + i);
+                    dst[0] = v.x, dst[1] = v.y, dst[2] = v.z, dst[3] = v.w;
+                } else {
+                    for (int q = 0; q < 4; ++q) dst[q] = q < w ? src[i + q] : 0.0f;
+                }
+            };
+            if (op.xa) fetch(op.xa, x);
+            else for (int q = 0; q < 4; ++q) x[q] = cur[q];
+            if (op.kind == 2) {  // AXPY: x + alpha y
+                if (op.yb) fetch(op.yb, y);
+                else for (int q = 0; q < 4; ++q) y[q] = cur[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                cur[q] = op.kind == 0 ? ew_apply<Ew::Relu>(x[q], 0.0f, 0.0f)
+                       : op.kind == 1 ? ew_apply<Ew::Square>(x[q], 0.0f, 0.0f)
+                                      : ew_apply<Ew::Axpy>(x[q], y[q], op.alpha);
+            if (op.out) {
+                if (vec) {
+                    *reinterpret_cast<float4*>(op.out + i) = make_float4(cur[0], cur[1], cur[2], cur[3]);
+                } else {
+                    for (int q = 0; q < w; ++q) op.out[i + q] = cur[q];
+                }
+            }
+        }
+    }
+}
+
 // ---- TRANSPOSE -------------------------------------------------------------------------
 
 // 64x64 tile through shared memory; 16-byte loads along input rows and 16-byte
@@ -525,6 +573,18 @@ cudaError_t launch_init(float* out, int64_t rows, int64_t cols, uint64_t seed, u
     const int64_t n = rows * cols;
     if (n <= 0) return cudaSuccess;
     init_kernel<<<grid_for((n + 3) / 4), kThreads, 0, st>>>(out, rows, cols, seed, buf, rowexp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ew_chain(const EwChain& c, cudaStream_t st) {
+    if (c.nops < 1 || c.nops > kMaxChainOps) return cudaErrorInvalidValue;
+    if (c.n <= 0) return cudaSuccess;
+    EwChain k = c;
+    uintptr_t ptrs = 0;
+    for (int o = 0; o < c.nops; ++o)
+        ptrs |= (uintptr_t)c.op[o].xa | (uintptr_t)c.op[o].yb | (uintptr_t)c.op[o].out;
+    k.vec = (c.n % 4 == 0) && (ptrs & 15u) == 0;
+    ew_chain_kernel<<<grid_for((c.n + 3) / 4), kThreads, 0, st>>>(k);
     return cudaGetLastError();
 }
 

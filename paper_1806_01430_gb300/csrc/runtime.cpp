@@ -779,6 +779,49 @@ bool find_grad_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, GradCh
     return true;
 }
 
+// A linear chain of element-wise loops starting at loop li that the gene puts on the GPU:
+// RELU, SQUARE or AXPY loops over one shape, each after the first reading the previous
+// loop's output and at most one buffer the chain did not produce.  Run as one pass, the
+// intermediates stay in registers; an output is written only when it is an OUTPUT buffer
+// or a later loop reads it.
+struct EwPlan {
+    int n = 0;
+    int loops[kMaxChainOps];
+};
+
+bool is_elementwise(int kind) { return kind == GAO_LOOP_RELU || kind == GAO_LOOP_SQUARE || kind == GAO_LOOP_AXPY; }
+
+bool find_ew_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, EwPlan* plan) {
+    if (!fuse || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT) return false;
+    const int n = (int)p->loops.size();
+    const gao_loop& L0 = p->loops[(size_t)li];
+    if (!is_elementwise(L0.kind) || !((mask >> li) & 1)) return false;
+    const gao_buffer& shape = p->bufs[(size_t)L0.outs[0]].d;
+    EwPlan e;
+    e.loops[e.n++] = li;
+    int cur = L0.outs[0];
+    std::vector<int> produced{cur};
+    for (int j = li + 1; j < n && e.n < kMaxChainOps; ++j) {
+        const gao_loop& L = p->loops[(size_t)j];
+        if (!((mask >> j) & 1) || !is_elementwise(L.kind)) break;
+        const gao_buffer& o = p->bufs[(size_t)L.outs[0]].d;
+        if (o.rows != shape.rows || o.cols != shape.cols) break;
+        const std::vector<int> ins = loop_inputs(L);
+        bool uses_cur = false, nonlinear = false;
+        for (int b : ins) {
+            if (b == cur) uses_cur = true;
+            else if (std::find(produced.begin(), produced.end(), b) != produced.end()) nonlinear = true;
+        }
+        if (!uses_cur || nonlinear) break;
+        e.loops[e.n++] = j;
+        cur = L.outs[0];
+        produced.push_back(cur);
+    }
+    if (e.n < 2) return false;
+    *plan = e;
+    return true;
+}
+
 // A chain the GEMM loop li can run as one pass when the gene puts it all on the GPU:
 // GEMM (C) -> AXPY (D = C + a X) -> TRANSPOSE (E = D^T) [-> FROBENIUS of E, later, with no
 // loop in between writing E].  The buffers must be distinct so that the epilogue's
@@ -1008,6 +1051,72 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
                 B.vd = t == 4 || gch.live[t];  // an unwritten intermediate holds nothing
             }
             for (int j = li + 1; j <= li + 4; ++j) fused |= 1ULL << j;
+            if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
+            if (R.timed_out) break;
+            continue;
+        }
+        EwPlan ewp;
+        if (gpu && is_elementwise(L.kind) && find_ew_chain(p, li, gene_mask, fuse, &ewp)) {
+            const int last = ewp.loops[ewp.n - 1];
+            // buffers the chain reads from memory: every input of its first loop, and each
+            // later loop's input other than the previous loop's output
+            std::vector<int> ext;
+            int prev = -1;
+            for (int k = 0; k < ewp.n; ++k) {
+                const gao_loop& Lk = p->loops[(size_t)ewp.loops[k]];
+                for (int b : loop_inputs(Lk))
+                    if ((k == 0 || b != prev) && std::find(ext.begin(), ext.end(), b) == ext.end()) ext.push_back(b);
+                prev = Lk.outs[0];
+            }
+            bool copies = false;
+            for (int b : ext) copies |= !p->bufs[(size_t)b].vd;
+            if (copies) GAO_CUDA_TRY(record_timing(ev[0], p->st));
+            for (int b : ext)
+                if ((status = make_valid(R, b, true, S)) != GAO_OK) break;
+            if (status != GAO_OK) break;
+            if (copies) {
+                GAO_CUDA_TRY(record_timing(ev[1], p->st));
+                p->ev_used[(size_t)li] |= 1;
+            }
+            EwChain c{};
+            c.nops = ewp.n;
+            c.n = (int64_t)p->bufs[(size_t)L.outs[0]].d.rows * p->bufs[(size_t)L.outs[0]].d.cols;
+            std::vector<char> live((size_t)ewp.n, 0);
+            prev = -1;
+            for (int k = 0; k < ewp.n; ++k) {
+                const gao_loop& Lk = p->loops[(size_t)ewp.loops[k]];
+                EwChainOp& op = c.op[k];
+                op.kind = Lk.kind == GAO_LOOP_RELU ? 0 : Lk.kind == GAO_LOOP_SQUARE ? 1 : 2;
+                op.alpha = (float)Lk.alpha;
+                auto src = [&](int b) -> const float* {
+                    return (k > 0 && b == prev) ? nullptr : (const float*)p->bufs[(size_t)b].dev;
+                };
+                op.xa = src(Lk.ins[0]);
+                op.yb = op.kind == 2 ? src(Lk.ins[1]) : nullptr;
+                const int ob = Lk.outs[0];
+                bool lv = p->bufs[(size_t)ob].d.role == GAO_BUF_OUTPUT;
+                for (int j = last + 1; j < n && !lv; ++j)
+                    for (int b : loop_inputs(p->loops[(size_t)j]))
+                        if (b == ob) lv = true;
+                live[(size_t)k] = lv;
+                op.out = lv ? (float*)p->bufs[(size_t)ob].dev : nullptr;
+                prev = ob;
+            }
+            GAO_CUDA_TRY(record_timing(ev[2], p->st));
+            const cudaError_t e = launch_ew_chain(c, p->st);
+            if (e != cudaSuccess) {
+                status = cuda_fail(e, "element-wise chain launch");
+                break;
+            }
+            GAO_CUDA_TRY(record_timing(ev[3], p->st));
+            p->ev_used[(size_t)li] |= 2;
+            S.launches += c.n > 0;
+            for (int k = 0; k < ewp.n; ++k) {  // in loop order: a buffer written twice ends as the last
+                BufState& B = p->bufs[(size_t)p->loops[(size_t)ewp.loops[k]].outs[0]];
+                B.vh = false;
+                B.vd = live[(size_t)k] != 0;  // an unwritten intermediate holds nothing
+            }
+            for (int k = 1; k < ewp.n; ++k) fused |= 1ULL << ewp.loops[k];
             if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
             if (R.timed_out) break;
             continue;

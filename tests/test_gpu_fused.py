@@ -148,3 +148,64 @@ def test_fused_chain_in_copy_overlapped_gemm(gao, n, prec):
     assert abs(a["f"] - b["f"]) <= 2e-7 * a["f"]
     assert [s["placement"] for s in st] == [1, 2, 2, 1, 2]
     assert st[0]["h2d_bytes"] == 3 * n * n * 4
+
+
+def test_twelve_loop_elementwise_chain_bit_identical(gao):
+    """ReLU, E - 0.5F, its square and P = H + 0.25D run as one element-wise pass (F, G, H
+    never written): the same P, column maxima and sum as the separate loops."""
+    prog = W.twelve_loop(300, 96, W.SEED_CONFIG4, outputs=("C", "D", "E", "r", "P", "q", "s"))
+    res = {}
+    for fuse in (False, True):
+        p = gao.prog_from_workload(prog, gemm_prec=2, fuse_chains=fuse)
+        gao.prog_run(p, (1 << 12) - 1)
+        res[fuse] = (outputs(gao, p, prog), gao.prog_stats(p))
+        gao.prog_destroy(p)
+    (a, _), (b, st) = res[False], res[True]
+    for nm in ("C", "D", "E", "r", "P", "q"):
+        assert np.array_equal(a[nm], b[nm]), nm
+    assert a["s"] == b["s"]
+    assert [s_["placement"] for s_ in st] == [1, 1, 2, 2, 1, 2, 1, 2, 2, 2, 1, 1]
+    assert st[6]["launches"] == 1
+
+
+def _ew_program(rng, n_loops, rows, cols):
+    """Random element-wise loops over a few initialised buffers (in place, both operands the
+    same, references to older buffers), all buffers OUTPUT."""
+    nb = 6
+    bufs = [W.Buffer(f"b{i}", rows, cols, W.F32, W.OUTPUT) for i in range(nb)]
+    loops = [W.Loop(W.INIT, [], [0, 1, 2])]
+    defined = [0, 1, 2]
+    for _ in range(n_loops):
+        kind = int(rng.choice([W.RELU, W.SQUARE, W.AXPY]))
+        out = int(rng.integers(0, nb))
+        x = int(rng.choice(defined))
+        if kind == W.AXPY:
+            y = int(rng.choice(defined))
+            loops.append(W.Loop(W.AXPY, [x, y], [out], alpha=float(rng.choice([2.0, -0.5, 0.25, 1.0]))))
+        else:
+            loops.append(W.Loop(kind, [x], [out]))
+        if out not in defined:
+            defined.append(out)
+    for i in range(nb):
+        if i not in defined:
+            bufs[i].role = W.TEMP
+    return W.Program("ew_random", bufs, loops, 61)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_elementwise_chains_bit_identical(gao, seed):
+    rng = np.random.default_rng(seed)
+    rows, cols = [(64, 64), (37, 45), (128, 3)][seed % 3]
+    prog = _ew_program(rng, 10, rows, cols)
+    full = (1 << prog.n_loops) - 1
+    genes = [full, full & ~(1 << int(rng.integers(1, prog.n_loops)))]
+    for gene in genes:
+        res = {}
+        for fuse in (False, True):
+            p = gao.prog_from_workload(prog, fuse_chains=fuse)
+            gao.prog_run(p, gene)
+            res[fuse] = {b.name: gao.prog_output(p, i).copy() for i, b in enumerate(prog.buffers)
+                         if b.role == W.OUTPUT}
+            gao.prog_destroy(p)
+        for nm in res[False]:
+            assert np.array_equal(res[False][nm].view(np.uint32), res[True][nm].view(np.uint32)), (seed, gene, nm)
