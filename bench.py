@@ -234,15 +234,55 @@ def reference_arm(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def algorithmic_bytes(prog, lp) -> float:
-    """Bytes a loop must move at least once: every input read once, every output
-    written once (INIT only writes)."""
-    def nbytes(i):
-        b = prog.buffers[i]
-        return b.rows * b.cols * (8 if b.dtype == W.F64 else 4)
-    ins = [] if lp.kind == W.INIT else [i for i in lp.ins if i >= 0]
-    outs = [o for o in lp.outs if o >= 0]
-    return float(sum(nbytes(i) for i in ins) + sum(nbytes(o) for o in outs))
+def fused_groups(prog, stats):
+    """Loops that ran as one pass: a loop that ran on the GPU (placement 1) and the loops
+    right after it that ran inside its pass (placement 2).  A fused norm belongs to a GEMM
+    chain, which is not a memory-bound pass, and is left out."""
+    groups, head = {}, None
+    for i, s_ in enumerate(stats):
+        if s_["placement"] == 2 and head is not None and prog.loops[i].kind != W.FROBENIUS:
+            groups[head].append(i)
+        else:
+            head = i if s_["placement"] == 1 else None
+            if head is not None:
+                groups[head] = [i]
+    return groups
+
+
+def group_bytes(prog, idx) -> float:
+    """Algorithmic bytes of loops run as one pass: the buffers it reads that it does not
+    produce, read once, and the buffers it produces that are OUTPUTs or read after it,
+    written once."""
+    def nbytes(b):
+        B = prog.buffers[b]
+        return B.rows * B.cols * (8 if B.dtype == W.F64 else 4)
+    produced, reads, writes = set(), set(), []
+    for i in idx:
+        lp = prog.loops[i]
+        for b in ([] if lp.kind == W.INIT else [x for x in lp.ins if x >= 0]):
+            if b not in produced:
+                reads.add(b)
+        for o in (lp.outs if lp.kind == W.INIT else lp.outs[:1]):
+            if o >= 0:
+                produced.add(o)
+                writes.append(o)
+    after = {b for lp in prog.loops[max(idx) + 1:] for b in (lp.ins if lp.kind != W.INIT else []) if b >= 0}
+    live = {o for o in writes if prog.buffers[o].role == W.OUTPUT or o in after}
+    return float(sum(nbytes(b) for b in reads) + sum(nbytes(o) for o in live))
+
+
+def pass_gbs(prog, stats, loop_ms, steps, hbm):
+    """GB/s of every memory-bound pass (a loop, or loops fused into one pass) from the
+    per-loop CUDA-event times; a fused pass is keyed by its first loop and its length."""
+    out = {}
+    for head, idx in fused_groups(prog, stats).items():
+        lp = prog.loops[head]
+        if lp.kind == W.GEMM or loop_ms[head] <= 0:
+            continue
+        g = group_bytes(prog, idx) / (loop_ms[head] / steps / 1e3) / 1e9
+        key = f"L{head}_{W.KIND_NAMES[lp.kind]}" + (f"+{len(idx) - 1}fused" if len(idx) > 1 else "")
+        out[key] = {"gbs": round(g, 1), "hbm_frac": round(g / hbm, 3)}
+    return out
 
 
 # ---- our arm --------------------------------------------------------------------------------------
@@ -300,13 +340,8 @@ def our_arm(args, world, rank, local):
     total_flops = allsum(world, flops)
     value = total_flops / (ms / 1e3) / 1e12
     clocks = clk.summary(t0, t1)
-    loop_bytes = [algorithmic_bytes(prog, lp) for lp in prog.loops]
     hbm = peaks().get("hbm_gbs", FALLBACK["hbm_gbs"])
-    loop_gbs = {}
-    for i, (lp, v, nb) in enumerate(zip(prog.loops, loop_ms, loop_bytes)):
-        if lp.kind != W.GEMM and v > 0:
-            g = nb / (v / stat_steps / 1e3) / 1e9
-            loop_gbs[f"L{i}_{W.KIND_NAMES[lp.kind]}"] = {"gbs": round(g, 1), "hbm_frac": round(g / hbm, 3)}
+    loop_gbs = pass_gbs(prog, st, loop_ms, stat_steps, hbm)
     loop_ms = {f"L{i}_{W.KIND_NAMES[lp.kind]}": round(v / stat_steps, 4) for i, (lp, v) in enumerate(zip(prog.loops, loop_ms))}
 
     # accuracy of this run's GEMM against the oracle on sampled entries (no timing)
@@ -549,13 +584,9 @@ def image_arm(args, world, rank, local):
     value = allsum(world, pixels) / (ms / 1e3) / 1e9
     clocks = clk.summary(t0, t1)
     hbm = peaks().get("hbm_gbs", FALLBACK["hbm_gbs"])
-    loop_gbs, per_loop = {}, {}
-    for i, (lp, v) in enumerate(zip(prog.loops, loop_ms)):
-        key = f"L{i}_{W.KIND_NAMES[lp.kind]}"
-        per_loop[key] = round(v / stat_steps, 4)
-        if v > 0:
-            g = algorithmic_bytes(prog, lp) / (v / stat_steps / 1e3) / 1e9
-            loop_gbs[key] = {"gbs": round(g, 1), "hbm_frac": round(g / hbm, 3)}
+    per_loop = {f"L{i}_{W.KIND_NAMES[lp.kind]}": round(v / stat_steps, 4)
+                for i, (lp, v) in enumerate(zip(prog.loops, loop_ms))}
+    loop_gbs = pass_gbs(prog, st, loop_ms, stat_steps, hbm)
     # dominant kernel: the stencil passes (the blur, and Sobel x / Sobel y or, fused, the
     # gradient chain that reads the blurred image once and writes only the magnitude),
     # 8 algorithmic bytes per pixel each
