@@ -58,6 +58,7 @@ struct gao_prog {
     std::vector<uint8_t> ev_used;  // bit 0 copies, bit 1 loop, bit 2 kernel
     std::unordered_map<uint64_t, gao::CacheEntry> cache;
     bool dirty_stream = false;  // a previous run left work in flight
+    bool stats_pending = false; // the last run's event times are not read yet
     cudaStream_t cst = nullptr;           // copy stream of the copy/compute overlap
     std::vector<cudaEvent_t> pipe_ev;     // its events: fork, B landed, one per row block
     std::vector<int8_t> verdict;  // gao_offload of every loop

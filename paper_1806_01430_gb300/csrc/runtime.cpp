@@ -1296,6 +1296,7 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
     if (p->opts.timeout_s > 0.0) R.deadline = R.cpu.deadline = t0 + p->opts.timeout_s;
     const bool uses_gpu = gene_mask != 0;
     gao_status status = GAO_OK;
+    p->stats_pending = false;
     // a gene that keeps every loop on the GPU is captured as a CUDA graph on its second
     // run and replayed from then on (one launch per run; the host work of the run is done once)
     const bool all_gpu = gene_mask == all_genes(n) && gene_length(p) > 0;
@@ -1334,15 +1335,7 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
         if (seconds_out) *seconds_out = p->opts.timeout_s;
         return fail(GAO_ETIMEOUT, "run exceeded its budget of " + std::to_string(p->opts.timeout_s) + " s");
     }
-    for (int li = 0; li < n; ++li) {
-        gao_loop_stat& S = p->stats[(size_t)li];
-        cudaEvent_t* ev = &p->ev[(size_t)li * 6];
-        const uint8_t u = p->ev_used[(size_t)li];
-        if (u & 1) S.copy_ms = ev_ms(ev[0], ev[1]);
-        if (u & 2) S.device_ms = ev_ms(ev[2], ev[3]);
-        if (u & 4) S.kernel_ms = ev_ms(ev[4], ev[5]);
-        else if (u & 2) S.kernel_ms = S.device_ms;
-    }
+    p->stats_pending = true;  // the event times are read when prog_stats asks for them
     return GAO_OK;
 }
 
@@ -1384,6 +1377,18 @@ extern "C" gao_status prog_loop_offload(const gao_prog* p, int loop, int* verdic
 extern "C" gao_status prog_stats(gao_prog* p, gao_loop_stat* out, int n) {
     if (!p || !out) return fail(GAO_EINVAL, "null argument");
     if (n < (int)p->stats.size()) return fail(GAO_EINVAL, "stats array too short");
+    if (p->stats_pending) {  // the last run's CUDA-event times (its stream has drained)
+        for (size_t li = 0; li < p->stats.size(); ++li) {
+            gao_loop_stat& S = p->stats[li];
+            cudaEvent_t* ev = &p->ev[li * 6];
+            const uint8_t u = p->ev_used[li];
+            if (u & 1) S.copy_ms = ev_ms(ev[0], ev[1]);
+            if (u & 2) S.device_ms = ev_ms(ev[2], ev[3]);
+            if (u & 4) S.kernel_ms = ev_ms(ev[4], ev[5]);
+            else if (u & 2) S.kernel_ms = S.device_ms;
+        }
+        p->stats_pending = false;
+    }
     std::copy(p->stats.begin(), p->stats.end(), out);
     return GAO_OK;
 }
