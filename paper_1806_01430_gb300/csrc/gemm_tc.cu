@@ -56,6 +56,7 @@ constexpr int BM = 128;  // UMMA M (one TMEM lane per output row)
 constexpr int BK = 64;   // 64 bfloat16 = 128 bytes = one swizzle row
 constexpr int BK8 = 128; // 128 e4m3 = 128 bytes = one swizzle row
 constexpr int kEpiWarps = 8;
+constexpr int kMaxSmemProblems = 512;  // grouped launch: problem starts kept in shared memory
 constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 constexpr unsigned long long kDrainLimitNs = 200000000ull;  // 0.2 s
@@ -428,11 +429,12 @@ struct OneProblem {
 struct ProblemTable {
     const TcProblem* probs;
     int nprob, bn;
+    const int* starts;  // shared-memory copy of every problem's tile_start (null: read probs)
     __device__ __forceinline__ void get(int t, TileInfo& ti) const {
         int lo = 0, hi = nprob - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (probs[mid].tile_start <= t) lo = mid;
+            if ((starts ? starts[mid] : probs[mid].tile_start) <= t) lo = mid;
             else hi = mid - 1;
         }
         const TcProblem* P = probs + lo;
@@ -714,7 +716,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     gemm_tc_grouped_kernel(const TcProblem* __restrict__ probs, int nprob, int total_tiles, int* err) {
-    const ProblemTable src{probs, nprob, BN};
+    // every role looks up its tile's problem by binary search over the problems' first
+    // tiles: keep them in shared memory (the persistent body synchronises the block
+    // before any lookup)
+    __shared__ int s_starts[kMaxSmemProblems];
+    const bool in_smem = nprob <= kMaxSmemProblems;
+    if (in_smem)
+        for (int i = threadIdx.x; i < nprob; i += blockDim.x) s_starts[i] = probs[i].tile_start;
+    const ProblemTable src{probs, nprob, BN, in_smem ? s_starts : nullptr};
     gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(src, total_tiles, err);
 }
 
