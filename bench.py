@@ -301,7 +301,14 @@ def our_arm(args, world, rank, local):
         prog = W.six_loop(n, W.SEED_CONFIG1 + rank, outputs=("C", "r", "f"))
         wname = f"six_loop_n{n}_all_gpu_{prec}"
     flops = prog.gemm_flops()
-    p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream, fuse_chains=args.fuse)
+    p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream, fuse_chains=args.fuse,
+                               kchunk=args.kchunk, tile_cfg=args.tile_cfg)
+    # the library's GA autotuner picks the GEMM's tile configuration (raster group, K chunk,
+    # L2 prefetch) by measured kernel time on this GPU, unless one is given
+    tune = None
+    if args.autotune and prec != "fp32_simt" and args.kchunk == 0 and args.tile_cfg == 0:
+        tune = gao.prog_autotune(p, pop=8, generations=6, seed=3)
+    kc, tcfg = (tune["kchunk"], tune["tile_cfg"]) if tune else (args.kchunk, args.tile_cfg)
     mask = (1 << prog.n_loops) - 1
     gemm_loop = 1
     kern_ms, launches = [], 0
@@ -362,7 +369,8 @@ def our_arm(args, world, rank, local):
     # the same program with the chain as separate kernels (GEMM kernel without the fused epilogue)
     unfused = None
     if args.fuse and prec in ("bf16", "bf16x3", "bf16x6"):
-        q = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream, fuse_chains=False)
+        q = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream, fuse_chains=False, kchunk=kc,
+                                   tile_cfg=tcfg)
         for _ in range(3):
             gao.prog_run(q, mask, gao.RUN_KEEP_DEVICE)
         torch.cuda.synchronize()
@@ -409,7 +417,8 @@ def our_arm(args, world, rank, local):
     e2e = None
     if args.e2e and args.workload == "six_loop":
         hp = W.host_input_program(n, prog.seed, outputs=("r", "f"))
-        q = gao.prog_from_workload(hp, gemm_prec=PREC[prec], stream=stream, fuse_chains=args.fuse)
+        q = gao.prog_from_workload(hp, gemm_prec=PREC[prec], stream=stream, fuse_chains=args.fuse, kchunk=kc,
+                                   tile_cfg=tcfg)
         import oracle  # input generation only (seeded counter hash); not on the timed path
         for nm, b in (("A", 0), ("B", 1), ("C0", 2)):
             gao.prog_set_input(q, hp.index(nm), oracle.init_matrix(prog.seed, b, n, n).astype(np.float32))
@@ -501,7 +510,8 @@ def our_arm(args, world, rank, local):
         peak = bf16 * 2.0 if prec == "fp8" else bf16 / PRODUCTS[prec]
         achieved = flops / (gemm_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_{prec}_n{n}{'_fused' if args.fuse else ''}.md"),
+                "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_{prec}_{wname.split('_all_gpu')[0]}"
+                                                         f"{'_fused' if args.fuse else ''}.md"),
                 "kernel": f"gemm_tc ({prec})" + (" with the fused scale-add / transpose / norm epilogue"
                                                   if args.fuse and prec != "fp8" else ""),
                 "products": PRODUCTS[prec],
@@ -529,8 +539,10 @@ def our_arm(args, world, rank, local):
             "config": {"workload": wname, "n": n if args.workload == "six_loop" else None,
                        "gene": format(mask, f"0{prog.n_loops}b"),
                        "gemm": prec, "fused_chain": bool(args.fuse), "graph_replay": graph_replay,
+                       "kchunk": kc, "tile_cfg": tcfg,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "working set larger than the 129 MB L2 (no flush)"},
+            "autotune": tune,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "gemm_rel_err_sampled": err, "unfused_chain": unfused, "fp32_simt": simt,
             "loop_ms": loop_ms,
@@ -764,6 +776,8 @@ def main():
     ap.add_argument("--pop", type=int, default=20)
     ap.add_argument("--generations", type=int, default=20)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--kchunk", type=int, default=0, help="fixed GEMM K chunk (with --tile-cfg: skips the autotuner)")
+    ap.add_argument("--tile-cfg", type=int, default=0, help="fixed GEMM tile configuration id (skips the autotuner)")
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--prec", default=None, choices=list(PREC),

@@ -135,8 +135,10 @@ typedef struct gao_opts {
     int32_t kchunk;          /* K elements per binary32 partial sum (0: library default; the
                                 FP32 SIMT kernel rounds it up to a multiple of 16)          */
     int32_t tile_cfg;        /* tensor-core tile configuration: bits 0-1 tile width (0 default,
-                                1 = 128, 2 = 256 columns), bits 4-7 log2 of the raster group
-                                (0: default 16); prog_autotune picks one               */
+                                1 = 128, 2 = 256 columns), bit 2 L2 prefetch of the operand
+                                tiles 4 K blocks ahead (BF16 variants; changes no value),
+                                bits 4-7 log2 of the raster group (0: default 16);
+                                prog_autotune picks one                                     */
     int32_t cpu_threads;     /* OpenMP threads for CPU loops (0: all)                       */
     uint64_t seed;           /* seed of the INIT loop's counter hash                        */
     double timeout_s;        /* wall-clock budget of one prog_run (0: none)                 */
@@ -295,11 +297,12 @@ gao_status ga_run_table(const double *times, int n_genes, const gao_ga_params *p
 
 /* ---- tile autotuning with the GA ----------------------------------------------- */
 
-/* The Simple GA reused as the tensor-core GEMM's autotuner: a 4-bit gene encodes
+/* The Simple GA reused as the tensor-core GEMM's autotuner: a 5-bit gene encodes
  * bits 0-1  raster group of 4, 8, 16 or 32 row tiles per CTA group (L2 reuse order),
  * bits 2-3  split precisions: K chunk of 64, 128, 256 or 512 elements (BF16x6) or 128,
  *           256, 512 or 1024 (BF16x3), all within the stated error bound; plain BF16:
  *           tile width 128 or 256 columns,
+ * bit 4     L2 prefetch of the operand tiles (tile_cfg bit 2),
  * and fitness is (measured GEMM time)^(-1/2), the paper's fitness with the kernel time
  * as the benchmark.  The best configuration is written into the program's (or the
  * batch's) options and used from then on. */

@@ -522,7 +522,7 @@ def _autotune_out(r) -> Dict:
 
 
 def prog_autotune(p: Prog, pop=8, generations=6, pc=0.9, pm=0.05, seed=0) -> Dict:
-    """GA over the GEMM's tile configuration (4-bit gene); applies and returns the best."""
+    """GA over the GEMM's tile configuration (5-bit gene); applies and returns the best."""
     params = _params(pop, generations, pc, pm, seed)
     r = gao_autotune_result()
     _check(lib().prog_autotune(p.handle, ctypes.byref(params), ctypes.byref(r)), "prog_autotune")

@@ -426,8 +426,10 @@ extern "C" gao_status batch_autotune(gao_batch* b, const gao_ga_params* params, 
     for (auto* p : b->progs) chunked_variant |= p->opts.kchunk > 0;
     std::vector<TcProblem> table = b->h_probs;
     auto apply = [&](int kchunk, int tile_cfg) -> gao_status {
+        table = b->h_probs;  // the configuration in place, then this one's changes
         for (auto& pr : table) {
             pr.group = tc_group_of(tile_cfg);
+            pr.pf_kb = tc_prefetch_of(tile_cfg);
             if (chunked_variant && kchunk > 0) pr.chunk_kb = std::max(1, std::min(pr.num_kb, kchunk / 64));
         }
         GAO_CUDA_TRY(cudaMemcpyAsync(b->d_probs, table.data(), sizeof(TcProblem) * table.size(),
@@ -465,9 +467,14 @@ extern "C" gao_status batch_autotune(gao_batch* b, const gao_ga_params* params, 
         return s2;
     };
     gao_ga_result res{};
-    if ((st = ga_core(4, *params, fn, &res)) != GAO_OK) return st;
-    int kc = 0, tc = 0;
-    autotune_decode(b->prec, res.best_mask, &kc, &tc);
+    if ((st = ga_core(kAutotuneBits, *params, fn, &res)) != GAO_OK) return st;
+    // the configuration in place stays unless the GA found a faster one
+    int kc = kc0, tc = tc0;
+    double best_ms = def_ms;
+    if (res.best_s * 1e3 < def_ms) {
+        autotune_decode(b->prec, res.best_mask, &kc, &tc);
+        best_ms = res.best_s * 1e3;
+    }
     if ((st = apply(kc, tc)) != GAO_OK) return st;
     b->h_probs = table;
     for (auto* p : b->progs) {
@@ -479,7 +486,7 @@ extern "C" gao_status batch_autotune(gao_batch* b, const gao_ga_params* params, 
     GAO_CUDA_TRY(cudaStreamSynchronize(b->st));
     out->kchunk = chunked_variant ? kc : 0;
     out->tile_cfg = tc;
-    out->best_ms = res.best_s * 1e3;
+    out->best_ms = best_ms;
     out->default_ms = def_ms;
     out->evaluations = evals;
     return GAO_OK;

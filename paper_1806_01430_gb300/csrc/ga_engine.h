@@ -24,9 +24,11 @@ using PopFn = std::function<gao_status(const std::vector<uint64_t>& genes, std::
 // ga_core when the times agree.
 gao_status ga_core_pop(int n_genes, const gao_ga_params& p, const PopFn& eval, gao_ga_result* res);
 
-// Tile configuration of a 4-bit autotuning gene for GEMM precision `prec`:
+// Tile configuration of a 5-bit autotuning gene for GEMM precision `prec`:
 // bits 0-1 raster group 4/8/16/32 (log2 2..5, stored in tile_cfg bits 4-7); bits 2-3
-// K chunk 64 << v for split precisions, tile width 128/256 for plain bfloat16.
+// K chunk 64 << v for split precisions, tile width 128/256 for plain bfloat16; bit 4
+// L2 prefetch of the operand tiles (tile_cfg bit 2).
+constexpr int kAutotuneBits = 5;
 inline void autotune_decode(int prec, uint64_t gene, int* kchunk, int* tile_cfg) {
     const int glog = 2 + (int)(gene & 3);
     const int v = (int)((gene >> 2) & 3);
@@ -44,7 +46,7 @@ inline void autotune_decode(int prec, uint64_t gene, int* kchunk, int* tile_cfg)
         *kchunk = 0;
         bn_sel = 1;
     }
-    *tile_cfg = bn_sel | (glog << 4);
+    *tile_cfg = bn_sel | (((gene >> 4) & 1) ? 4 : 0) | (glog << 4);
 }
 
 }  // namespace gao

@@ -125,6 +125,12 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// Pull one tile of a tensor into L2 (no shared memory, no barrier: a hint only).
+__device__ __forceinline__ void tma_prefetch_l2_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x), "r"(y)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
@@ -401,6 +407,7 @@ struct TileInfo {
     const CUtensorMap* tb;
     EpiArgs ep;
     int Mp, Np, num_kb, chunk_kb, m0, n0;
+    int pf_kb;  // operand tiles are pulled into L2 this many K blocks ahead of their loads (0: off)
 };
 
 // Tiles of one problem (kernel arguments).
@@ -408,7 +415,7 @@ struct OneProblem {
     const CUtensorMap* ta;
     const CUtensorMap* tb;
     EpiArgs ep;
-    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, bn;
+    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, bn, pf_kb;
     __device__ __forceinline__ void get(int t, TileInfo& ti) const {
         int tm, tn;
         raster(t, tiles_m, tiles_n, group, tm, tn);
@@ -421,6 +428,7 @@ struct OneProblem {
         ti.chunk_kb = chunk_kb;
         ti.m0 = tm * BM;
         ti.n0 = tn * bn;
+        ti.pf_kb = pf_kb;
     }
 };
 
@@ -449,6 +457,7 @@ struct ProblemTable {
         ti.chunk_kb = P->chunk_kb;
         ti.m0 = tm * BM;
         ti.n0 = tn * bn;
+        ti.pf_kb = P->pf_kb;
     }
 };
 
@@ -515,6 +524,16 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                 for (int kb = 0; kb < ti.num_kb; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (ti.pf_kb > 0) {
+                        // K blocks 0..pf_kb at a tile's start, then block kb + pf_kb
+                        const int k_last = min(kb + ti.pf_kb, ti.num_kb - 1);
+                        for (int k2 = kb == 0 ? 0 : kb + ti.pf_kb; k2 <= k_last; ++k2) {
+#pragma unroll
+                            for (int p = 0; p < PA; ++p) tma_prefetch_l2_2d(ti.ta, k2 * KBE, p * ti.Mp + ti.m0);
+#pragma unroll
+                            for (int p = 0; p < PB; ++p) tma_prefetch_l2_2d(ti.tb, k2 * KBE, p * ti.Np + ti.n0);
+                        }
+                    }
                     if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, err)) {
                         ok = false;
                         break;
@@ -708,8 +727,9 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep,
-                   int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int group, int* err) {
-    const OneProblem src{&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, BN};
+                   int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int group, int pf_kb,
+                   int* err) {
+    const OneProblem src{&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, BN, pf_kb};
     gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(src, tiles_m * tiles_n, err);
 }
 
@@ -941,7 +961,7 @@ bool make_map(CUtensorMap* map, void* base, int64_t inner, int64_t rows, int box
 
 template <int BN, int P, int NPROD, int STAGES, bool CHUNKED, bool FP8 = false>
 cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const EpiArgs& ep, int Mp, int Np, int num_kb,
-                       int chunk_kb, int group, int* err, cudaStream_t st) {
+                       int chunk_kb, int group, int pf_kb, int* err, cudaStream_t st) {
     // Np is the plane stride (a multiple of 256); only ceil(N / BN) column tiles hold data
     using Cfg = TcCfg<BN, P, P, NPROD, STAGES, CHUNKED, FP8>;
     auto kern = gemm_tc_kernel<BN, P, P, NPROD, STAGES, CHUNKED, FP8>;
@@ -956,7 +976,7 @@ cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const EpiAr
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     const int64_t grid = std::min<int64_t>(total, (int64_t)sm_count());  // persistent: one CTA per SM
     kern<<<(unsigned)grid, kThreadsTc, Cfg::SMEM, st>>>(ta, tb, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group,
-                                                        err);
+                                                        pf_kb, err);
     return cudaGetLastError();
 }
 
@@ -1084,9 +1104,11 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     const bool chunked = chunk_kb < num_kb;
     // tile_cfg bits 0-1: 0 = default (128 x 256 for the unchunked single product, else
     // 128 x 128), 1 = 128 x 128, 2 = 128 x 256 (single product, unchunked only);
-    // bits 4-7: raster group = 2^value row tiles (0: default 16)
+    // bit 2: L2 prefetch of the operand tiles; bits 4-7: raster group = 2^value row
+    // tiles (0: default 16)
     const int bn_sel = tile_cfg & 3;
     const int group = tc_group_of(tile_cfg);
+    const int pf_kb = tc_prefetch_of(tile_cfg);
     int bn = 128;
     if (!chunked && P == 1 && (bn_sel == 2 || bn_sel == 0)) bn = 256;
     CUtensorMap ta, tb;
@@ -1110,17 +1132,17 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     cudaError_t e;
     const int mp = (int)Mp, np = (int)Np;
     if (P == 3)
-        e = chunked ? launch_mma<128, 3, 6, 2, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st)
-                    : launch_mma<128, 3, 6, 2, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
+        e = chunked ? launch_mma<128, 3, 6, 2, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st)
+                    : launch_mma<128, 3, 6, 2, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st);
     else if (P == 2)
-        e = chunked ? launch_mma<128, 2, 3, 3, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st)
-                    : launch_mma<128, 2, 3, 3, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
+        e = chunked ? launch_mma<128, 2, 3, 3, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st)
+                    : launch_mma<128, 2, 3, 3, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st);
     else if (chunked)
-        e = launch_mma<128, 1, 1, 6, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
+        e = launch_mma<128, 1, 1, 6, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st);
     else if (bn == 256)
-        e = launch_mma<256, 1, 1, 4, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
+        e = launch_mma<256, 1, 1, 4, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st);
     else
-        e = launch_mma<128, 1, 1, 6, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, err, st);
+        e = launch_mma<128, 1, 1, 6, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st);
     if (e != cudaSuccess) return e;
     ev.launches += 1;
     if (ev.k1) record_timing(ev.k1, st);
@@ -1167,7 +1189,7 @@ cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const floa
                (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, sa, sb, (int)L.kbs,
                (int)L.Np};
     if (ev.k0) record_timing(ev.k0, st);
-    cudaError_t e = launch_mma<128, 1, 1, 6, true, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, (int)L.kbs, 1, group, err, st);
+    cudaError_t e = launch_mma<128, 1, 1, 6, true, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, (int)L.kbs, 1, group, 0, err, st);
     if (e != cudaSuccess) return e;
     ev.launches += 1;
     if (ev.k1) record_timing(ev.k1, st);
@@ -1270,6 +1292,7 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
     prob->tiles_m = prob->Mp / BM;
     prob->tiles_n = (int)((N + 127) / 128);
     prob->group = tc_group_of(tile_cfg);
+    prob->pf_kb = tc_prefetch_of(tile_cfg);
     return cudaSuccess;
 }
 

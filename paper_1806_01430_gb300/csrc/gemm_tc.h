@@ -46,7 +46,7 @@ struct TcFuse {
 struct alignas(128) TcProblem {
     CUtensorMap ta, tb;
     EpiArgs ep;
-    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, tile_start, group;
+    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, tile_start, group, pf_kb;
 };
 
 // Raster group (row tiles per CTA group) encoded in bits 4-7 of a tile configuration
@@ -55,6 +55,13 @@ inline int tc_group_of(int tile_cfg) {
     const int g = (tile_cfg >> 4) & 15;
     return g == 0 ? 16 : (1 << g);
 }
+
+// Bit 2 of a tile configuration id: the producer also pulls each operand tile into L2
+// kL2PrefetchKb K blocks before its load (a hint: it changes no value).  It pays where the
+// operand re-reads of one wave of tiles fit in L2 but miss it (BF16x6 at n = 4096 on
+// GB300: 5% off the GEMM) and costs where they do not, so the autotuner decides it.
+constexpr int kL2PrefetchKb = 4;
+inline int tc_prefetch_of(int tile_cfg) { return (tile_cfg & 4) ? kL2PrefetchKb : 0; }
 
 // Looks up the driver's tensor-map encoder (once); false with a reason if unavailable.
 bool tc_available(std::string* why);

@@ -1624,17 +1624,22 @@ extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, ga
             return s2;
         };
         gao_ga_result res{};
-        st = ga_core(4, *params, fn, &res);
+        st = ga_core(kAutotuneBits, *params, fn, &res);
         if (st == GAO_OK) {
-            int kc = 0, tc = 0;
-            autotune_decode(prec, res.best_mask, &kc, &tc);
+            // the configuration in place stays unless the GA found a faster one
+            int kc = p->opts.kchunk, tc = p->opts.tile_cfg;
+            double best_ms = def_ms;
+            if (res.best_s * 1e3 < def_ms) {
+                autotune_decode(prec, res.best_mask, &kc, &tc);
+                best_ms = res.best_s * 1e3;
+            }
             p->opts.kchunk = kc;
             p->opts.tile_cfg = tc;
             drop_graphs(p);
             p->cache.clear();  // times measured under the old configuration
             out->kchunk = kc;
             out->tile_cfg = tc;
-            out->best_ms = res.best_s * 1e3;
+            out->best_ms = best_ms;
             out->default_ms = def_ms;
             out->evaluations = evals;
         }

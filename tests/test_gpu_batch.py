@@ -95,6 +95,24 @@ def test_batch_rejects_mixed_programs(gao):
         gao.batch_create([a, a])
 
 
+def test_batch_l2_prefetch_changes_no_value(gao):
+    """The grouped launch with tile configuration bit 2 (L2 prefetch of the operand tiles)
+    gives the same bits as without it, for every program of the suite."""
+    sizes = [300, 129, 520, 64]
+    progs = [W.six_loop(n, 3100 + i, outputs=("C", "D", "E", "r", "f")) for i, n in enumerate(sizes)]
+    outs = []
+    for cfg in (0, 4):
+        handles = [gao.prog_from_workload(p, gemm_prec=2, tile_cfg=cfg) for p in progs]
+        b = gao.batch_create(handles)
+        gao.batch_evaluate(b, [0b111111])
+        outs.append([gao.prog_output(h, p.index("C")) for h, p in zip(handles, progs)])
+        gao.batch_destroy(b)
+        for h in handles:
+            gao.prog_destroy(h)
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
+
+
 def test_batch_autotune_keeps_parity(gao):
     sizes = [300, 129, 520, 64]
     progs, handles = suite(gao, sizes, 3)

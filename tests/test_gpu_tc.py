@@ -98,6 +98,34 @@ def test_tc_gemm_bn256_tile(gao):
     assert oracle.rel_err(out["C"], ref["C"]) <= TOL["bf16"]
 
 
+@pytest.mark.parametrize("prec,kchunk,cfg", [("bf16x6", 0, 0), ("bf16x6", 128, 0), ("bf16x3", 0, 0),
+                                            ("bf16", 0, 1), ("bf16", 0, 2)])
+def test_tc_l2_prefetch_changes_no_value(gao, prec, kchunk, cfg):
+    """Tile configuration bit 2 only adds L2 prefetches of the operand tiles ahead of their
+    loads: C is bit-identical with and without it (ragged 300 x 520 x 1000: several tiles,
+    16 K blocks, so the prefetch window is clamped at the end of K)."""
+    prog = gemm_program(300, 520, 1000, 31, inplace=False)
+    a, _ = run_gemm(gao, prog, prec, tile_cfg=cfg, kchunk=kchunk)
+    b, _ = run_gemm(gao, prog, prec, tile_cfg=cfg | 4, kchunk=kchunk)
+    assert np.array_equal(a["C"], b["C"])
+    ref = oracle.run_program(prog)
+    assert oracle.rel_err(b["C"], ref["C"]) <= TOL[prec]
+
+
+def test_tc_l2_prefetch_fused_chain(gao):
+    """The fused GEMM chain (C, D = C + 2A, E = D^T, norm) with the prefetch bit gives the
+    same bits as without it."""
+    prog = W.six_loop(384, 41, outputs=("C", "D", "E", "r", "f"))
+    outs = []
+    for cfg in (0, 4):
+        p = gao.prog_from_workload(prog, gemm_prec=PREC["bf16x6"], tile_cfg=cfg, fuse_chains=gao.FUSE_ON)
+        gao.prog_run(p, 0b111111)
+        outs.append({nm: gao.prog_output(p, prog.index(nm)) for nm in ("C", "D", "E", "r", "f")})
+        gao.prog_destroy(p)
+    for nm in ("C", "D", "E", "r", "f"):
+        assert np.array_equal(outs[0][nm], outs[1][nm]), nm
+
+
 def test_tc_gemm_beta_zero_and_k_zero(gao):
     prog = gemm_program(130, 70, 90, 3, beta=0.0, inplace=False)
     out, _ = run_gemm(gao, prog, "bf16x6")
@@ -186,7 +214,7 @@ def test_prog_autotune_keeps_parity(gao, prec):
         assert r["kchunk"] in (64, 128, 256, 512)
     if prec == "bf16x3":
         assert r["kchunk"] in (128, 256, 512, 1024)
-    assert ((r["tile_cfg"] >> 4) & 15) in (2, 3, 4, 5)
+    assert ((r["tile_cfg"] >> 4) & 15) in (2, 3, 4, 5) and (r["tile_cfg"] & ~0xF7) == 0
     gao.prog_run(p, 0b111111)
     ref = oracle.run_program(prog)
     assert oracle.rel_err(gao.prog_output(p, prog.index("C")), ref["C"]) <= TOL[prec]
