@@ -739,6 +739,16 @@ def batch_arm(args, world, rank, local):
     if rank == 0:
         pk = peaks()
         peak = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        roof = None
+        if gemm_tf and args.prec != "fp32_simt":
+            # the grouped GEMM phase (operand splits included, so a lower bound for the kernel)
+            # against the kernel's own arithmetic peak, as in the single-program line
+            gpk = peak * 2.0 if args.prec == "fp8" else peak / PRODUCTS[args.prec]
+            roof = {"bound": "tensor", "achieved": gemm_tf, "peak": gpk, "unit": "TFLOP/s", "frac": gemm_tf / gpk,
+                    "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_grouped_batch{args.programs}_{args.prec}.md"),
+                    "kernel": "gemm_tc_grouped_kernel (one launch over all programs' tiles; phase time incl. splits)",
+                    "peak_source": f"{pk['source']} bf16 sustained" +
+                                   (" x2 (fp8 nominal ratio)" if args.prec == "fp8" else f" / {PRODUCTS[args.prec]}")}
         line = {"metric": "ga_evals_per_s", "value": evals / wall, "unit": "evals/s", "n_gpus": world,
                 "steps": args.generations, "warmup": 1, "ms_per_step": wall / args.generations * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
@@ -753,7 +763,7 @@ def batch_arm(args, world, rank, local):
                                  "effective_tflops": gemm_tf,
                                  "hw_frac": (gemm_tf * PRODUCTS[args.prec] / peak) if gemm_tf else None},
                 "launches_per_all_gpu_gene": st["launches_per_gene"], "graphs": st["graphs"],
-                "autotune": tune,
+                "autotune": tune, "roofline": roof,
                 "all_gpu_gene_warm_s": st_w["exec_seconds"],
                 "history": [{"best_s": h["best_s"], "evaluated": h["evaluated"], "hits": h["cache_hits"]}
                             for h in res.history],

@@ -120,6 +120,7 @@ def test_batch_autotune_keeps_parity(gao):
     b = gao.batch_create(handles)
     r = gao.batch_autotune(b, pop=6, generations=4, seed=2)
     assert r["evaluations"] >= 1 and r["best_ms"] > 0 and r["kchunk"] in (64, 128, 256, 512)
+    assert r["best_ms"] <= r["default_ms"]  # the configuration in place stays unless beaten
     for mask in (0b111111, 0b111110, 0b101011):
         gao.batch_evaluate(b, [mask])
         check_outputs(gao, progs, handles, refs, mask, 3)

@@ -209,12 +209,13 @@ def test_prog_autotune_keeps_parity(gao, prec):
     p = gao.prog_from_workload(prog, gemm_prec=PREC[prec])
     r = gao.prog_autotune(p, pop=6, generations=4, seed=1)
     assert r["evaluations"] >= 1 and r["best_ms"] > 0 and r["default_ms"] > 0
-    assert r["best_ms"] <= 1.25 * r["default_ms"]
+    assert r["best_ms"] <= r["default_ms"]  # the configuration in place stays unless beaten
     if prec == "bf16x6":
         assert r["kchunk"] in (64, 128, 256, 512)
     if prec == "bf16x3":
         assert r["kchunk"] in (128, 256, 512, 1024)
-    assert ((r["tile_cfg"] >> 4) & 15) in (2, 3, 4, 5) and (r["tile_cfg"] & ~0xF7) == 0
+    # a GA configuration, or the one in place (0: library defaults) when none beat it
+    assert ((r["tile_cfg"] >> 4) & 15) in (0, 2, 3, 4, 5) and (r["tile_cfg"] & ~0xF7) == 0
     gao.prog_run(p, 0b111111)
     ref = oracle.run_program(prog)
     assert oracle.rel_err(gao.prog_output(p, prog.index("C")), ref["C"]) <= TOL[prec]
