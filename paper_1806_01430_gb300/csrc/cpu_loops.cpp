@@ -200,10 +200,24 @@ void cpu_rowsum(float* out, const float* in, int64_t rows, int64_t cols, CpuCtx&
             stop = true;
             continue;
         }
-        float s = 0.0f;
+        // the fixed row-sum order shared with the GPU paths (kRowsumBlock blocks, quadruple
+        // tree per block, four interleaved block accumulators)
         const float* r = in + i * cols;
-        for (int64_t j = 0; j < cols; ++j) s += r[j];
-        out[i] = s;
+        float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const int64_t nblk = (cols + kRowsumBlock - 1) / kRowsumBlock;
+        for (int64_t p = 0; p < nblk; ++p) {
+            const int64_t j0 = p * kRowsumBlock;
+            float x[kRowsumBlock];
+            if (j0 + kRowsumBlock <= cols) {
+                for (int t = 0; t < kRowsumBlock; ++t) x[t] = r[j0 + t];
+            } else {
+                for (int t = 0; t < kRowsumBlock; ++t) x[t] = j0 + t < cols ? r[j0 + t] : 0.0f;
+            }
+            float q[8];
+            for (int m = 0; m < 8; ++m) q[m] = (x[4 * m] + x[4 * m + 1]) + (x[4 * m + 2] + x[4 * m + 3]);
+            u[p & 3] += ((q[0] + q[4]) + (q[2] + q[6])) + ((q[1] + q[5]) + (q[3] + q[7]));
+        }
+        out[i] = (u[0] + u[2]) + (u[1] + u[3]);
     }
 }
 

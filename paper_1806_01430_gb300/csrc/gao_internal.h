@@ -86,6 +86,14 @@ cudaError_t launch_init(float* out, int64_t rows, int64_t cols, uint64_t seed, u
                         cudaStream_t st);
 cudaError_t launch_axpy(float* out, const float* x, float alpha, const float* y, int64_t n, cudaStream_t st);
 cudaError_t launch_transpose(float* out, const float* in, int64_t rows, int64_t cols, cudaStream_t st);
+// Row sums (ROWSUM) follow one fixed order on every path -- the row-sum kernel, the fused
+// GEMM chain's block values and the host loop -- so that equal inputs give equal bits
+// whatever the gene: a row of length L is cut into blocks of kRowsumBlock = 32 elements
+// (elements past L count as +0); a block's value is ((q0 + q4) + (q2 + q6)) + ((q1 + q5) +
+// (q3 + q7)) over its quadruples q_m = (x_4m + x_4m+1) + (x_4m+2 + x_4m+3); block p is
+// added to accumulator p mod 4 (each starts at +0 and takes its blocks in increasing p);
+// the row sum is (u0 + u2) + (u1 + u3).
+constexpr int kRowsumBlock = 32;
 cudaError_t launch_rowsum(float* out, const float* in, int64_t rows, int64_t cols, cudaStream_t st);
 cudaError_t launch_frobenius(double* out, const float* in, int64_t n, ReduceScratch rs, cudaStream_t st);
 cudaError_t launch_sum(double* out, const float* in, int64_t n, ReduceScratch rs, cudaStream_t st);

@@ -345,6 +345,23 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
                     make_float4(dd[it][0], dd[it][1], dd[it][2], dd[it][3]);
             }
             __syncwarp();
+            if (e.rsum_part) {
+                // these 32 rows are block row0 / 32 of the E rows gcol + 16h + 0..15: two lanes
+                // per column form the block's quadruples (rows >= M were staged as +0) and
+                // combine them in the fixed row-sum order
+                const int cc = lane & 15, hb = lane >> 4;
+                float x[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float* col = stg + (4 * (4 * hb + k)) * kStgStride + cc;
+                    x[k] = (col[0] + col[kStgStride]) + (col[2 * kStgStride] + col[3 * kStgStride]);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) x[k] += __shfl_xor_sync(0xffffffffu, x[k], 16);  // q_k + q_k+4
+                const float blk = (x[0] + x[2]) + (x[1] + x[3]);
+                const int64_t col = gcol + 16 * h + cc;
+                if (hb == 0 && col < e.N) e.rsum_part[(row0 / kRowsumBlock) * e.ldR + col] = blk;
+            }
             const int64_t grow = row0 + lane;
             if (grow < e.M) {
 #pragma unroll
@@ -765,6 +782,32 @@ __global__ void __launch_bounds__(256) frob_partials_kernel(const double* __rest
     }
 }
 
+// Row sums of E from a fused chain's block values (column j of D is row j of E): four
+// threads per column, thread b keeping accumulator b of the fixed row-sum order (blocks b,
+// b + 4, ... in increasing order), then (u0 + u2) + (u1 + u3) across the four.
+__global__ void __launch_bounds__(256) rowsum_blocks_kernel(const float* __restrict__ part, int64_t nblk, int64_t ld,
+                                                            int64_t n, float* __restrict__ out) {
+    constexpr int kAhead = 8;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t j = t >> 2;
+    const int b = (int)(t & 3);
+    float u = 0.0f;
+    if (j < n) {
+        int64_t p = b;
+        for (; p + 4 * (kAhead - 1) < nblk; p += 4 * kAhead) {
+            float v[kAhead];
+#pragma unroll
+            for (int k = 0; k < kAhead; ++k) v[k] = part[(p + 4 * k) * ld + j];
+#pragma unroll
+            for (int k = 0; k < kAhead; ++k) u += v[k];
+        }
+        for (; p < nblk; p += 4) u += part[p * ld + j];
+    }
+    u += __shfl_xor_sync(0xffffffffu, u, 2);
+    u += __shfl_xor_sync(0xffffffffu, u, 1);
+    if (j < n && b == 0) out[j] = u;
+}
+
 // ---- split kernels ------------------------------------------------------------------------------
 
 template <int P>
@@ -1007,7 +1050,7 @@ Fp8Layout fp8_layout(int64_t M, int64_t N, int64_t K) {
 }
 
 // Planes (or FP8 arrays) first, then binary64 partials for a fused chain's norm
-// (8 per 128 x 128 tile).
+// (8 per 128 x 128 tile), then its row sums' 32-row block values (binary32, [Mp / 32][N]).
 size_t tc_planes_bytes(int prec, int64_t M, int64_t N, int64_t K) {
     if (prec == GAO_GEMM_FP8) return fp8_layout(M, N, K).total;
     if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_BF16X6) return 0;
@@ -1017,9 +1060,14 @@ size_t tc_planes_bytes(int prec, int64_t M, int64_t N, int64_t K) {
     return (size_t)ru(P * (Mp + Np) * Kp * 2, 1024);
 }
 
-size_t tc_partials_bytes(int64_t M, int64_t N) {
+size_t tc_frob_partials_bytes(int64_t M, int64_t N) {
     const int64_t tiles = (ru(std::max<int64_t>(M, 1), BM) / BM) * ((std::max<int64_t>(N, 1) + 127) / 128);
     return (size_t)ru(tiles * kEpiWarps * (int64_t)sizeof(double), 1024);
+}
+
+size_t tc_partials_bytes(int64_t M, int64_t N) {
+    const int64_t blocks = ru(std::max<int64_t>(M, 1), BM) / kRowsumBlock;
+    return tc_frob_partials_bytes(M, N) + (size_t)ru(blocks * std::max<int64_t>(N, 1) * 4, 1024);
 }
 
 size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K) {
@@ -1117,6 +1165,7 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
                (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, nullptr, nullptr, 0, 0};
     double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, Mlay, N, K));
+    float* rpart = reinterpret_cast<float*>(reinterpret_cast<char*>(fpart) + tc_frob_partials_bytes(Mlay, N));
     const int64_t tiles_n = (N + bn - 1) / bn;
     ep.ldE = M;
     if (fuse) {
@@ -1126,6 +1175,8 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         ep.ldE = fuse->ldE > 0 ? fuse->ldE : M;
         ep.alpha2 = fuse->alpha2;
         ep.frob_part = fuse->frob_out ? fpart + (part ? part->row_tile0 : 0) * tiles_n * kEpiWarps : nullptr;
+        ep.rsum_part = fuse->rowsum_out ? rpart + (part ? part->row_tile0 : 0) * (BM / kRowsumBlock) * N : nullptr;
+        ep.ldR = N;
         ep.fuse = 1;
     }
     if (ev.k0) record_timing(ev.k0, st);
@@ -1149,6 +1200,12 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     if (fuse && fuse->frob_out && (!part || part->last)) {
         const int64_t tiles = (ru(Mlay, BM) / BM) * tiles_n;  // every block's tiles
         frob_partials_kernel<<<1, 256, 0, st>>>(fpart, tiles * kEpiWarps, fuse->frob_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ev.launches += 1;
+    }
+    if (fuse && fuse->rowsum_out && (!part || part->last)) {
+        const int64_t nblk = (Mlay + kRowsumBlock - 1) / kRowsumBlock;  // blocks of the whole E row
+        rowsum_blocks_kernel<<<(unsigned)((4 * N + 255) / 256), 256, 0, st>>>(rpart, nblk, N, N, fuse->rowsum_out);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ev.launches += 1;
     }

@@ -28,10 +28,15 @@ struct EpiArgs {
     float alpha2;
     int fuse;
     int64_t ldE;       // row stride of E (0: M); a row block writes columns of a larger E
+    // Fused row sums of E (= column sums of D): each warp writes, for each of its columns j,
+    // the value of its 32-row block in the fixed row-sum order at
+    // rsum_part[(row0 / 32) * ldR + j]; null when the chain has no row-sum loop.
+    float* rsum_part;
+    int64_t ldR;
 };
 
-// Loops of a chain GEMM -> AXPY (D = C + alpha2 X) -> TRANSPOSE (E = D^T) [-> FROBENIUS of
-// E] done inside the GEMM's epilogue.
+// Loops of a chain GEMM -> AXPY (D = C + alpha2 X) -> TRANSPOSE (E = D^T) [-> ROWSUM of E]
+// [-> FROBENIUS of E] done inside the GEMM's epilogue.
 struct TcFuse {
     const float* X;
     float* D;
@@ -39,6 +44,7 @@ struct TcFuse {
     double* frob_out;  // nullptr: no Frobenius loop in the chain
     float alpha2;
     int64_t ldE;       // row stride of E (0: the launch's M)
+    float* rowsum_out;  // nullptr: no row-sum loop in the chain; else the N row sums of E
 };
 
 // One problem of a grouped launch: its operand planes' TMA descriptors and epilogue.

@@ -233,37 +233,50 @@ __global__ void __launch_bounds__(256) transpose_scalar_kernel(float* __restrict
 
 // ---- ROWSUM ------------------------------------------------------------------------------
 
-// One warp per row.  Lane l adds the 4 entries of float4 l, l+32, ... in order; the
-// 32 lane sums are combined by a fixed butterfly.  Deterministic.
+// Quadruple value of elements [i0, i0 + 4) of a row of length cols (+0 past the end).
+__device__ __forceinline__ float row_quad(const float* row, int64_t i0, int64_t cols, bool vec) {
+    if (vec) {  // cols % 4 == 0: a quadruple is wholly inside or wholly past the row
+        if (i0 >= cols) return 0.0f;
+        const float4 a = *reinterpret_cast<const float4*>(row + i0);
+        return (a.x + a.y) + (a.z + a.w);
+    }
+    float x[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) x[t] = i0 + t < cols ? row[i0 + t] : 0.0f;
+    return (x[0] + x[1]) + (x[2] + x[3]);
+}
+
+// One warp per row, in the fixed row-sum order: a 128-element chunk holds four 32-element
+// blocks; lane l takes quadruple l of the chunk, so lanes 8b..8b+7 hold block b's eight
+// quadruples and a three-step butterfly leaves the block's value in lane 8b, which adds it
+// to its accumulator (lane 8b keeps accumulator b).  Eight chunks' loads are in flight.
 __global__ void rowsum_kernel(float* __restrict__ out, const float* __restrict__ in, int64_t rows, int64_t cols) {
+    constexpr int kAhead = 8;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const bool vec = (cols % 4 == 0) && aligned16(in);
+    const int64_t nblk = (cols + kRowsumBlock - 1) / kRowsumBlock;
+    const int64_t nchunks = (cols + 127) / 128;
     for (int64_t r = warp; r < rows; r += nwarps) {
         const float* row = in + r * cols;
-        float s = 0.0f;
-        if (vec) {
-            const float4* row4 = reinterpret_cast<const float4*>(row);
-            const int64_t n4 = cols / 4;
-            int64_t j = lane;
-            for (; j + 96 < n4; j += 128) {
-                const float4 a = row4[j], b = row4[j + 32], c = row4[j + 64], d = row4[j + 96];
-                s += ((a.x + a.y) + (a.z + a.w));
-                s += ((b.x + b.y) + (b.z + b.w));
-                s += ((c.x + c.y) + (c.z + c.w));
-                s += ((d.x + d.y) + (d.z + d.w));
-            }
-            for (; j < n4; j += 32) {
-                const float4 a = row4[j];
-                s += ((a.x + a.y) + (a.z + a.w));
-            }
-        } else {
-            for (int64_t j = lane; j < cols; j += 32) s += row[j];
-        }
+        float u = 0.0f;
+        for (int64_t c0 = 0; c0 < nchunks; c0 += kAhead) {
+            float q[kAhead];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) out[r] = s;
+            for (int k = 0; k < kAhead; ++k) q[k] = row_quad(row, (c0 + k) * 128 + 4 * lane, cols, vec);
+#pragma unroll
+            for (int k = 0; k < kAhead; ++k) {
+                float s = q[k];
+                s += __shfl_xor_sync(0xffffffffu, s, 4);
+                s += __shfl_xor_sync(0xffffffffu, s, 2);
+                s += __shfl_xor_sync(0xffffffffu, s, 1);
+                if ((c0 + k) * 4 + (lane >> 3) < nblk) u += s;  // blocks past the row are not added
+            }
+        }
+        u += __shfl_xor_sync(0xffffffffu, u, 16);
+        u += __shfl_xor_sync(0xffffffffu, u, 8);
+        if (lane == 0) out[r] = u;
     }
 }
 

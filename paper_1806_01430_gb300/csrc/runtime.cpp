@@ -827,7 +827,7 @@ bool find_ew_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, EwPlan* 
 // loop in between writing E].  The buffers must be distinct so that the epilogue's
 // writes cannot race with its reads.
 struct Chain {
-    int axpy = -1, transpose = -1, frob = -1;
+    int axpy = -1, transpose = -1, rowsum = -1, frob = -1;
 };
 
 bool find_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, Chain* ch) {
@@ -849,16 +849,33 @@ bool find_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, Chain* ch) 
         if (g >= 0 && (g == Db || g == Eb)) return false;
     ch->axpy = li + 1;
     ch->transpose = li + 2;
-    ch->frob = -1;
+    ch->rowsum = ch->frob = -1;
+    // later GPU loops that only reduce E (row sums, norm) join the chain when nothing between
+    // rewrites E or touches their outputs: their results are formed at the GEMM's place
+    const int chain_bufs[] = {gin[0], gin[1], gin[2], Cb, Xb, Db, Eb};
+    auto joins = [&](int j) {
+        const gao_loop& L = p->loops[(size_t)j];
+        const int out = L.outs[0];
+        for (int b : chain_bufs)
+            if (b == out) return false;
+        for (int k = li + 3; k < j; ++k) {
+            const gao_loop& Q = p->loops[(size_t)k];
+            for (int b : loop_inputs(Q))
+                if (b == out) return false;
+            for (int b : loop_outputs(Q))
+                if (b == out) return false;
+        }
+        return true;
+    };
     for (int j = li + 3; j < n; ++j) {
         const gao_loop& L = p->loops[(size_t)j];
-        if (L.kind == GAO_LOOP_FROBENIUS && L.ins[0] == Eb && ((mask >> j) & 1)) {
-            ch->frob = j;
-            break;
+        if (L.ins[0] == Eb && ((mask >> j) & 1)) {
+            if (L.kind == GAO_LOOP_ROWSUM && ch->rowsum < 0 && joins(j)) ch->rowsum = j;
+            if (L.kind == GAO_LOOP_FROBENIUS && ch->frob < 0 && joins(j)) ch->frob = j;
         }
         bool writes_e = false;
         for (int o : loop_outputs(L)) writes_e |= (o == Eb);
-        if (writes_e) break;
+        if (writes_e || (ch->rowsum >= 0 && ch->frob >= 0)) break;
     }
     return true;
 }
@@ -872,6 +889,7 @@ gao_status run_gpu_chain(RunCtx& R, int li, const Chain& ch) {
     TcFuse fz{dptr(X.ins[1]), dptr(X.outs[0]), dptr(T.outs[0]),
               ch.frob >= 0 ? (double*)p->bufs[(size_t)p->loops[(size_t)ch.frob].outs[0]].dev : nullptr,
               (float)X.alpha};
+    fz.rowsum_out = ch.rowsum >= 0 ? dptr(p->loops[(size_t)ch.rowsum].outs[0]) : nullptr;
     TcEvents tev{R.events ? p->ev[(size_t)li * 6 + 4] : nullptr, R.events ? p->ev[(size_t)li * 6 + 5] : nullptr, 0};
     std::string why;
     cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, dptr(G.outs[0]), dptr(G.ins[0]), dptr(G.ins[1]), c0, A.rows,
@@ -969,6 +987,7 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
             fz.frob_out = ch->frob >= 0 ? (double*)p->bufs[(size_t)p->loops[(size_t)ch->frob].outs[0]].dev : nullptr;
             fz.alpha2 = (float)XL->alpha;
             fz.ldE = M;
+            fz.rowsum_out = ch->rowsum >= 0 ? fdev(p->loops[(size_t)ch->rowsum].outs[0]) : nullptr;
         }
         cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, c, (const float*)A.dev + (size_t)r0 * K,
                                        (const float*)B.dev, c0, r1 - r0, N, K, (float)L.alpha, beta, p->opts.kchunk,
@@ -1141,7 +1160,7 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             if ((status = run_gpu_chain(R, li, chain)) != GAO_OK) break;
             GAO_CUDA_TRY(record_timing(ev[3], p->st));
             p->ev_used[(size_t)li] |= 2;
-            for (int j : {li, chain.axpy, chain.transpose, chain.frob}) {
+            for (int j : {li, chain.axpy, chain.transpose, chain.rowsum, chain.frob}) {
                 if (j < 0) continue;
                 for (int b : loop_outputs(p->loops[(size_t)j])) {
                     p->bufs[(size_t)b].vh = false;
@@ -1168,7 +1187,7 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             }
             if ((status = run_gpu_gemm_pipelined(R, li, blocks, pf ? &pch : nullptr)) != GAO_OK) break;
             if (pf) {
-                for (int j : {li, pch.axpy, pch.transpose, pch.frob}) {
+                for (int j : {li, pch.axpy, pch.transpose, pch.rowsum, pch.frob}) {
                     if (j < 0) continue;
                     for (int b : loop_outputs(p->loops[(size_t)j])) {
                         p->bufs[(size_t)b].vh = false;

@@ -121,11 +121,12 @@ def test_all_64_masks_invariance(gao):
         assert np.array_equal(init[0], init0[0]) and np.array_equal(init[1], init0[1])
         key = (mask >> 1) & 1
         if key in by_gemm_side:
-            C0, D0, E0 = by_gemm_side[key]
+            C0, D0, E0, r0 = by_gemm_side[key]
             assert np.array_equal(out["C"], C0)
             assert np.array_equal(out["D"], D0) and np.array_equal(out["E"], E0)
+            assert np.array_equal(out["r"], r0)  # one row-sum order on both sides
         else:
-            by_gemm_side[key] = (out["C"], out["D"], out["E"])
+            by_gemm_side[key] = (out["C"], out["D"], out["E"], out["r"])
         st = gao.prog_stats(p)
         for i, s in enumerate(st):
             assert s["placement"] == ((mask >> i) & 1)
