@@ -210,3 +210,46 @@ def test_random_elementwise_chains_bit_identical(gao, seed):
             gao.prog_destroy(p)
         for nm in res[False]:
             assert np.array_equal(res[False][nm].view(np.uint32), res[True][nm].view(np.uint32)), (seed, gene, nm)
+
+
+def test_full_size_twelve_loop_sampled(gao):
+    """configs[4] size as bench.py runs it: m = 16384, k = 4096, BF16x3, all twelve loops on
+    the GPU with the fused chains.  C on sampled entries against the oracle (entry by entry
+    from the counter hash); D = C + 2S on the samples; E = D^T everywhere; P from E and D
+    with the element-wise operations restated in binary32 on sampled rows; the row sums in
+    their fixed order on sampled rows; column maxima exact; norm and sum within their
+    reduction bounds."""
+    import math
+    from test_gpu_rowsum import rowsum_fixed_order
+    m, k, seed = 16384, 4096, W.SEED_CONFIG4
+    prog = W.twelve_loop(m, k, seed, outputs=("C", "D", "E", "r", "f", "P", "q", "s"))
+    p = gao.prog_from_workload(prog, gemm_prec=2, fuse_chains=gao.FUSE_ON)
+    gao.prog_run(p, (1 << 12) - 1)
+    st = gao.prog_stats(p)
+    assert [s_["placement"] for s_ in st] == [1, 1, 2, 2, 2, 2, 1, 2, 2, 2, 1, 1]
+    out = outputs(gao, p, prog)
+    gao.prog_destroy(p)
+    rng = np.random.default_rng(5)
+    ii, jj = rng.integers(0, m, 512), rng.integers(0, m, 512)
+    want = oracle.gemm_init_entries(seed, (0, 1, 2), False, m, m, k, 1.5, 0.5, ii, jj)
+    C, D, E, P = out["C"], out["D"], out["E"], out["P"]
+    got = C[ii, jj].astype(np.float64)
+    err = math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
+    assert err <= TOL[2], err
+    S = np.array([oracle.init_value(seed, 3, int(i) * m + int(j)) for i, j in zip(ii, jj)])
+    assert np.array_equal(D[ii, jj], (C[ii, jj].astype(np.float64) + 2.0 * S).astype(np.float32))
+    assert np.array_equal(E, D.T)
+    rows = rng.integers(0, m, 16)
+    Er, Dr = E[rows], D[rows]
+    F = np.where(Er > 0, Er, np.float32(0))
+    G = Er + np.float32(-0.5) * F
+    H = G * G
+    assert np.array_equal(P[rows], H + np.float32(0.25) * Dr)
+    assert np.array_equal(out["r"][rows], rowsum_fixed_order(Er))
+    assert np.array_equal(out["q"].ravel(), P.max(axis=0))
+    E64 = E.astype(np.float64)
+    fn = math.sqrt(float(np.einsum("ij,ij->", E64, E64)))
+    assert abs(out["f"] - fn) <= 2e-7 * fn
+    del E64
+    P64 = P.astype(np.float64)
+    assert abs(out["s"] - float(P64.sum())) <= 4 * 2.0 ** -24 * float(np.abs(P64).sum())
