@@ -715,7 +715,8 @@ def batch_arm(args, world, rank, local):
     torch.cuda.set_device(local)
     sizes = W.batch_sizes(args.programs)
     progs = [W.six_loop(n, W.SEED_CONFIG3_BASE + p, outputs=("f",)) for p, n in enumerate(sizes)]
-    handles = [gao.prog_from_workload(pr, gemm_prec=PREC[args.prec]) for pr in progs]
+    handles = [gao.prog_from_workload(pr, gemm_prec=PREC[args.prec],
+                                      fuse_chains=gao.FUSE_ON if args.fuse else gao.FUSE_OFF) for pr in progs]
     b = gao.batch_create(handles)
     # warm-up: the all-GPU gene once (not cached afterwards: fresh batch for the timed GA)
     gao.batch_evaluate(b, [(1 << 6) - 1])
@@ -755,7 +756,7 @@ def batch_arm(args, world, rank, local):
                 "data": "synthetic (seeded counter hash, U[-1,1))",
                 "config": {"workload": f"batch_{args.programs}_programs_n128_2048_pop{args.pop}_gen{args.generations}",
                            "programs": args.programs, "sizes_min_max": [min(sizes), max(sizes)], "pop": args.pop,
-                           "generations": args.generations, "gemm": args.prec},
+                           "generations": args.generations, "gemm": args.prec, "fused_chain": bool(args.fuse)},
                 "executed_genes": st["executed"], "served_genes": st["served"],
                 "executed_program_evals_per_s": st["executed"] * args.programs / max(st["exec_seconds"], 1e-9),
                 "best_gene": format(res.best_mask, "06b"), "best_s": res.best_s,
@@ -763,6 +764,7 @@ def batch_arm(args, world, rank, local):
                                  "effective_tflops": gemm_tf,
                                  "hw_frac": (gemm_tf * PRODUCTS[args.prec] / peak) if gemm_tf else None},
                 "launches_per_all_gpu_gene": st["launches_per_gene"], "graphs": st["graphs"],
+                "fused_gemm_phases": st["fused_phases"],
                 "autotune": tune, "roofline": roof,
                 "all_gpu_gene_warm_s": st_w["exec_seconds"],
                 "history": [{"best_s": h["best_s"], "evaluated": h["evaluated"], "hits": h["cache_hits"]}

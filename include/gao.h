@@ -330,7 +330,13 @@ gao_status prog_autotune(gao_prog *p, const gao_ga_params *params, gao_autotune_
  * gene's time is the wall time of the whole suite, boundary copies included; a gene
  * measured before is served from the batch's cache (Sec. 4).  The programs stay owned
  * by the caller, must outlive the batch, and must not run elsewhere meanwhile; each
- * program's host and device buffers hold its results after a gene runs. */
+ * program's host and device buffers hold its results after a gene runs.  All programs
+ * share one fuse_chains setting (GAO_FUSE_OFF or GAO_FUSE_ON; GAO_FUSE_GENE is refused:
+ * batch genes are loop placements only).  With GAO_FUSE_ON a gene that puts a program's
+ * GEMM -> scale-add -> transpose [-> row sums] [-> norm] chain on the GPU runs the chain
+ * in the grouped launch's epilogue, bit-identical to the separate loops but the norm
+ * (within its reduction's rounding).  The INIT loop (without row scaling) of all programs
+ * is one grouped launch too. */
 typedef struct gao_batch gao_batch;
 
 typedef struct gao_batch_stat {
@@ -342,7 +348,8 @@ typedef struct gao_batch_stat {
     int32_t gemm_tiles;        /* CTAs of the grouped GEMM launch                       */
     int32_t launches_per_gene; /* kernels in the captured graphs (all loops on the GPU) */
     int32_t graphs;            /* phase graphs captured                                 */
-    int32_t _pad;
+    int32_t fused_phases;      /* GEMM phases run with the loop chain in the epilogue
+                                  (programs created with GAO_FUSE_ON; genes measured)     */
 } gao_batch_stat;
 
 gao_status batch_create(gao_prog *const *progs, int n_progs, gao_batch **out);

@@ -42,6 +42,10 @@ struct gao_batch {
     std::vector<cudaGraphExec_t> exec;
     int gemm_loop = -1;
     bool grouped_gemm = false;
+    int init_loop = -1;             // INIT loop run as one grouped launch over all programs
+    InitEntry* d_init = nullptr;    // its table: every program's outputs
+    int n_init = 0;
+    int64_t init_total4 = 0;
     TcProblem* d_probs = nullptr;
     int n_probs = 0, total_tiles = 0;
     std::vector<size_t> gemm_order;  // programs in problem-table order (largest GEMM first)
@@ -52,15 +56,36 @@ struct gao_batch {
     std::unordered_map<uint64_t, double> cache;
     gao_batch_stat stat{};
     double timeout_s = 0.0;
+    // fused chains (programs created with GAO_FUSE_ON): a gene whose chain GEMM -> AXPY ->
+    // TRANSPOSE [-> ROWSUM] [-> FROBENIUS] is on the GPU runs it in the grouped GEMM's
+    // epilogue; one captured GEMM phase per chain shape, made on first use
+    bool fuse = false;
+    struct FusedPhase {
+        bool ok = false;  // every program has this chain
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        TcProblem* d_probs = nullptr;
+    };
+    std::unordered_map<int, FusedPhase> fused;
 };
 
 namespace {
 
 constexpr int kSide = 8;
 
+void drop_fused(gao_batch* b) {
+    for (auto& kv : b->fused) {
+        if (kv.second.x) cudaGraphExecDestroy(kv.second.x);
+        if (kv.second.g) cudaGraphDestroy(kv.second.g);
+        if (kv.second.d_probs) cudaFree(kv.second.d_probs);
+    }
+    b->fused.clear();
+}
+
 void free_batch(gao_batch* b) {
     if (!b) return;
     if (b->st) cudaStreamSynchronize(b->st);
+    drop_fused(b);
     for (auto e : b->exec)
         if (e) cudaGraphExecDestroy(e);
     for (auto g : b->graph)
@@ -73,6 +98,7 @@ void free_batch(gao_batch* b) {
     if (b->g0) cudaEventDestroy(b->g0);
     if (b->g1) cudaEventDestroy(b->g1);
     if (b->d_probs) cudaFree(b->d_probs);
+    if (b->d_init) cudaFree(b->d_init);
     if (b->d_err) cudaFree(b->d_err);
     if (b->h_err) cudaFreeHost(b->h_err);
     if (b->st) cudaStreamDestroy(b->st);
@@ -87,13 +113,14 @@ gao_status capture_phase(gao_batch* b, int li, std::vector<TcProblem>* probs) {
     cudaError_t e = cudaEventRecord(b->fork, st);
     for (int k = 0; k < kSide && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[(size_t)k], b->fork, 0);
     const bool tc_gemm = li == b->gemm_loop && b->grouped_gemm;
+    const bool group_init = li == b->init_loop;  // one launch after the (empty) branches
     std::vector<size_t> order(b->progs.size());
     std::iota(order.begin(), order.end(), 0);
     if (tc_gemm) {
         order = b->gemm_order;
         probs->assign(b->progs.size(), TcProblem{});
     }
-    for (size_t j = 0; j < order.size() && e == cudaSuccess && status == GAO_OK; ++j) {
+    for (size_t j = 0; j < order.size() && e == cudaSuccess && status == GAO_OK && !group_init; ++j) {
         gao_prog* p = b->progs[order[j]];
         cudaStream_t s = b->side[j % kSide];
         if (tc_gemm) {
@@ -120,6 +147,10 @@ gao_status capture_phase(gao_batch* b, int li, std::vector<TcProblem>* probs) {
         e = cudaEventRecord(b->join[(size_t)k], b->side[(size_t)k]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join[(size_t)k], 0);
     }
+    if (group_init && e == cudaSuccess) {
+        e = launch_init_group(b->d_init, b->n_init, b->init_total4, st);
+        b->stat.launches_per_gene += 1;
+    }
     if (tc_gemm && e == cudaSuccess && status == GAO_OK) {
         bool chunked = false;
         for (auto* p : b->progs) chunked |= p->opts.kchunk > 0;
@@ -142,6 +173,117 @@ gao_status capture_phase(gao_batch* b, int li, std::vector<TcProblem>* probs) {
     return GAO_OK;
 }
 
+int chain_key(const Chain& ch) { return (ch.rowsum + 1) * 1024 + (ch.frob + 1); }
+
+// The GEMM phase with chain `ch` fused, for every program: splits on the side streams, one
+// grouped launch whose problems carry the chain's epilogue, then each program's norm and
+// row sums from its partials on the side streams again.
+gao_status capture_fused(gao_batch* b, uint64_t mask, const Chain& ch, gao_batch::FusedPhase* fp) {
+    const size_t n = b->progs.size();
+    fp->ok = true;
+    for (auto* p : b->progs) {  // the same chain in every program, or no fusion for this shape
+        Chain c;
+        if (!find_chain(p, b->gemm_loop, mask, true, &c) || c.axpy != ch.axpy || c.transpose != ch.transpose ||
+            c.rowsum != ch.rowsum || c.frob != ch.frob)
+            fp->ok = false;
+    }
+    if (!fp->ok) return GAO_OK;
+    GAO_CUDA_TRY(cudaMalloc((void**)&fp->d_probs, sizeof(TcProblem) * n));
+    std::vector<TcProblem> probs(n);
+    std::vector<TcFuse> fz(n);
+    auto dev = [](gao_prog* p, int bi) { return (float*)p->bufs[(size_t)bi].dev; };
+    cudaStream_t st = b->st;
+    bool chunked = false;
+    for (auto* p : b->progs) chunked |= p->opts.kchunk > 0;
+    GAO_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    gao_status status = GAO_OK;
+    auto fork = [&]() {
+        cudaError_t e = cudaEventRecord(b->fork, st);
+        for (int k = 0; k < kSide && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[(size_t)k], b->fork, 0);
+        return e;
+    };
+    auto join = [&]() {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kSide && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(b->join[(size_t)k], b->side[(size_t)k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join[(size_t)k], 0);
+        }
+        return e;
+    };
+    cudaError_t e = fork();
+    for (size_t j = 0; j < n && e == cudaSuccess && status == GAO_OK; ++j) {
+        gao_prog* p = b->progs[b->gemm_order[j]];
+        const gao_loop &L = p->loops[(size_t)b->gemm_loop], &X = p->loops[(size_t)ch.axpy],
+                       &T = p->loops[(size_t)ch.transpose];
+        const gao_buffer &A = p->bufs[(size_t)L.ins[0]].d, &B = p->bufs[(size_t)L.ins[1]].d;
+        fz[j] = TcFuse{dev(p, X.ins[1]), dev(p, X.outs[0]), dev(p, T.outs[0]),
+                       ch.frob >= 0 ? (double*)p->bufs[(size_t)p->loops[(size_t)ch.frob].outs[0]].dev : nullptr,
+                       (float)X.alpha, 0, ch.rowsum >= 0 ? dev(p, p->loops[(size_t)ch.rowsum].outs[0]) : nullptr};
+        float* c0 = L.ins[2] >= 0 ? dev(p, L.ins[2]) : dev(p, L.outs[0]);
+        std::string why;
+        int nl = 0;
+        e = tc_prepare(b->prec, dev(p, L.outs[0]), dev(p, L.ins[0]), dev(p, L.ins[1]), c0, A.rows, B.cols, A.cols,
+                       (float)L.alpha, L.ins[2] >= 0 ? (float)L.beta : 0.0f, p->opts.kchunk, p->opts.tile_cfg,
+                       p->arena + p->lay.tc_off, p->lay.tc_bytes, b->side[j % kSide], &probs[j], &nl, &why, &fz[j]);
+        if (e != cudaSuccess && !why.empty()) status = fail(GAO_EINVAL, "batch fused GEMM: " + why);
+    }
+    if (e == cudaSuccess) e = join();
+    if (e == cudaSuccess && status == GAO_OK)
+        e = tc_launch_grouped(b->prec, chunked, fp->d_probs, (int)n, b->total_tiles, b->d_err, st);
+    if (e == cudaSuccess && status == GAO_OK) e = fork();
+    for (size_t j = 0; j < n && e == cudaSuccess && status == GAO_OK; ++j) {
+        gao_prog* p = b->progs[b->gemm_order[j]];
+        const gao_loop& L = p->loops[(size_t)b->gemm_loop];
+        const gao_buffer &A = p->bufs[(size_t)L.ins[0]].d, &B = p->bufs[(size_t)L.ins[1]].d;
+        int nl = 0;
+        e = tc_finalize_chain(b->prec, A.rows, B.cols, A.cols, p->arena + p->lay.tc_off, fz[j], b->side[j % kSide], &nl);
+    }
+    if (e == cudaSuccess && status == GAO_OK) e = join();
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(st, &g);
+    if (status != GAO_OK || e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (status != GAO_OK) return status;
+        return cuda_fail(e != cudaSuccess ? e : e2, "batch fused capture");
+    }
+    fp->g = g;
+    GAO_CUDA_TRY(cudaGraphInstantiate(&fp->x, g, 0));
+    int start = 0;
+    for (auto& pr : probs) {
+        pr.tile_start = start;
+        start += pr.tiles_m * pr.tiles_n;
+    }
+    if (start != b->total_tiles) return fail(GAO_EINVAL, "batch tile count mismatch");
+    GAO_CUDA_TRY(cudaMemcpy(fp->d_probs, probs.data(), sizeof(TcProblem) * n, cudaMemcpyHostToDevice));
+    return GAO_OK;
+}
+
+// Every chain shape a gene can give (the GEMM, scale-add and transpose on the GPU; each
+// later reduction of E on the GPU or not), captured up front so that no gene's time holds
+// a capture.
+gao_status capture_all_fused(gao_batch* b) {
+    if (!b->fuse) return GAO_OK;
+    const gao_prog* p0 = b->progs[0];
+    const uint64_t all = loop_mask_of(p0, all_genes(b->n_genes));
+    Chain full;
+    if (!find_chain(p0, b->gemm_loop, all, true, &full)) return GAO_OK;
+    std::vector<int> opt;
+    for (int j : {full.rowsum, full.frob})
+        if (j >= 0) opt.push_back(j);
+    for (int sub = 0; sub < (1 << opt.size()); ++sub) {
+        uint64_t m = all;
+        for (size_t k = 0; k < opt.size(); ++k)
+            if (!((sub >> k) & 1)) m &= ~(1ULL << opt[k]);
+        Chain c;
+        if (!find_chain(p0, b->gemm_loop, m, true, &c) || b->fused.count(chain_key(c))) continue;
+        gao_batch::FusedPhase& slot = b->fused[chain_key(c)];
+        gao_status s = capture_fused(b, m, c, &slot);
+        if (s != GAO_OK || !slot.x) slot.ok = false;
+        if (s != GAO_OK) return s;
+    }
+    return GAO_OK;
+}
+
 // One gene over the whole suite; *seconds = wall time (budget on timeout, -1 on failure).
 gao_status run_gene(gao_batch* b, uint64_t gene, double* seconds) {
     const int n = b->n_loops;
@@ -158,16 +300,53 @@ gao_status run_gene(gao_batch* b, uint64_t gene, double* seconds) {
         }
         R.push_back(RunCtx{p, deadline, false, CpuCtx{p->opts.cpu_threads, deadline, false}, b->st, false});
     }
+    // the chain in the GEMM's epilogue when this gene puts all of it on the GPU
+    Chain ch;
+    gao_batch::FusedPhase* fp = nullptr;
+    if (b->fuse && ((mask >> b->gemm_loop) & 1) && find_chain(b->progs[0], b->gemm_loop, mask, true, &ch)) {
+        auto it = b->fused.find(chain_key(ch));
+        if (it == b->fused.end()) {
+            gao_batch::FusedPhase& slot = b->fused[chain_key(ch)];
+            gao_status s = capture_fused(b, mask, ch, &slot);
+            if (s != GAO_OK || !slot.x) slot.ok = false;  // never launched half-made
+            if (s != GAO_OK) return s;
+            it = b->fused.find(chain_key(ch));
+        }
+        if (it->second.ok) fp = &it->second;
+    }
+    uint64_t in_epilogue = 0;  // loops that ran in the GEMM's epilogue
     GAO_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->st));
     bool timed_out = false;
     gao_loop_stat scratch{};
     for (int li = 0; li < n && !timed_out; ++li) {
+        if ((in_epilogue >> li) & 1) continue;
         const bool gpu = (mask >> li) & 1;
         for (auto& r : R)
             for (int bi : loop_inputs(r.p->loops[(size_t)li])) {
                 gao_status s = make_valid(r, bi, gpu, scratch);
                 if (s != GAO_OK) return s;
             }
+        if (gpu && fp && li == b->gemm_loop) {
+            for (auto& r : R) {  // the AXPY's second operand is read in the epilogue
+                gao_status s = make_valid(r, r.p->loops[(size_t)ch.axpy].ins[1], true, scratch);
+                if (s != GAO_OK) return s;
+            }
+            GAO_CUDA_TRY(cudaEventRecord(b->g0, b->st));
+            GAO_CUDA_TRY(cudaGraphLaunch(fp->x, b->st));
+            GAO_CUDA_TRY(cudaEventRecord(b->g1, b->st));
+            b->stat.fused_phases += 1;
+            for (int j : {li, ch.axpy, ch.transpose, ch.rowsum, ch.frob}) {
+                if (j < 0) continue;
+                in_epilogue |= 1ULL << j;
+                for (auto& r : R)
+                    for (int bo : loop_outputs(r.p->loops[(size_t)j])) {
+                        r.p->bufs[(size_t)bo].vh = false;
+                        r.p->bufs[(size_t)bo].vd = true;
+                    }
+            }
+            if (deadline > 0.0 && now_s() > deadline) timed_out = true;
+            continue;
+        }
         if (gpu) {
             if (li == b->gemm_loop) GAO_CUDA_TRY(cudaEventRecord(b->g0, b->st));
             GAO_CUDA_TRY(cudaGraphLaunch(b->exec[(size_t)li], b->st));
@@ -253,8 +432,9 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
         if (p->opts.gemm_prec != p0->opts.gemm_prec) return fail(GAO_EINVAL, "batch programs differ in GEMM precision");
         if (p->opts.transfer_mode != GAO_TRANSFER_RESIDENT)
             return fail(GAO_EINVAL, "batches keep buffers resident (transfer_mode RESIDENT only)");
-        if (p->opts.fuse_chains != GAO_FUSE_OFF)
-            return fail(GAO_EINVAL, "batches run loop by loop (fuse_chains must be GAO_FUSE_OFF)");
+        if (p->opts.fuse_chains == GAO_FUSE_GENE)
+            return fail(GAO_EINVAL, "batch genes are loop placements only (fuse_chains GAO_FUSE_GENE is not supported)");
+        if (p->opts.fuse_chains != p0->opts.fuse_chains) return fail(GAO_EINVAL, "batch programs differ in fuse_chains");
         for (auto& B : p->bufs)
             if (B.d.role == GAO_BUF_INPUT && !B.input_set) return fail(GAO_EINVAL, "INPUT buffers must be set first");
         for (int j = 0; j < i; ++j)
@@ -277,6 +457,7 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
             b->gemm_loop = l;
         }
     b->grouped_gemm = b->gemm_loop >= 0 && b->prec != GAO_GEMM_FP32_SIMT;
+    b->fuse = b->grouped_gemm && p0->opts.fuse_chains == GAO_FUSE_ON && b->prec != GAO_GEMM_FP8;
     cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
     b->side.assign(kSide, nullptr);
@@ -344,6 +525,38 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
         if (start > 0x7fffffff) return bail(fail(GAO_EINVAL, "batch GEMM has too many tiles"));
         b->total_tiles = (int)start;
     }
+    // the first INIT loop without row scaling: one grouped launch over every program's
+    // outputs instead of a launch per program (many small launches in a row cost more than
+    // their writes)
+    for (int li = 0; li < b->n_loops && b->init_loop < 0; ++li) {
+        const gao_loop& L0 = p0->loops[(size_t)li];
+        if (L0.kind != GAO_LOOP_INIT || p0->verdict[(size_t)li] != GAO_OFFLOAD_OK) continue;
+        bool plain = true;
+        for (auto* p : b->progs) plain &= (p->loops[(size_t)li].flags & ((1u << GAO_MAX_IO) - 1)) == 0;
+        if (!plain) break;
+        std::vector<InitEntry> tab;
+        int64_t start = 0;
+        for (auto* p : b->progs) {
+            const gao_loop& L = p->loops[(size_t)li];
+            for (int t = 0; t < GAO_MAX_IO; ++t) {
+                const int bi = L.outs[t];
+                if (bi < 0) continue;
+                const gao_buffer& d = p->bufs[(size_t)bi].d;
+                const int64_t n4 = (d.rows * d.cols + 3) / 4;
+                if (n4 <= 0) continue;
+                tab.push_back(InitEntry{(float*)p->bufs[(size_t)bi].dev, d.rows, d.cols, p->opts.seed, (uint32_t)bi, start});
+                start += n4;
+            }
+        }
+        if (tab.empty()) break;
+        if ((e = cudaMalloc((void**)&b->d_init, sizeof(InitEntry) * tab.size())) != cudaSuccess ||
+            (e = cudaMemcpy(b->d_init, tab.data(), sizeof(InitEntry) * tab.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+            return bail(cuda_fail(e, "INIT table"));
+        b->init_loop = li;
+        b->n_init = (int)tab.size();
+        b->init_total4 = start;
+    }
     b->stat.launches_per_gene = 0;
     for (int li = 0; li < b->n_loops; ++li) {
         if (p0->verdict[(size_t)li] != GAO_OFFLOAD_OK) continue;  // host-only loop: no graph
@@ -362,6 +575,7 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
         }
     }
     b->stat.graphs = b->n_genes;
+    if ((s = capture_all_fused(b)) != GAO_OK) return bail(s);
     *out = b;
     return GAO_OK;
 }
@@ -484,6 +698,8 @@ extern "C" gao_status batch_autotune(gao_batch* b, const gao_ga_params* params, 
     }
     b->cache.clear();  // genes measured under the old configuration
     GAO_CUDA_TRY(cudaStreamSynchronize(b->st));
+    drop_fused(b);  // fused GEMM phases are captured again with the new configuration
+    if ((st = capture_all_fused(b)) != GAO_OK) return st;
     out->kchunk = chunked_variant ? kc : 0;
     out->tile_cfg = tc;
     out->best_ms = best_ms;

@@ -82,8 +82,31 @@ struct ReduceScratch {
 int reduce_blocks();
 
 cudaError_t launch_row_exponents(int8_t* e, int64_t rows, uint64_t seed, cudaStream_t st);
-cudaError_t launch_init(float* out, int64_t rows, int64_t cols, uint64_t seed, uint32_t buf, const int8_t* rowexp,
-                        cudaStream_t st);
+// The outputs of one INIT loop: out[i] = init_value(seed, buf, i), times 2^e_row for an
+// output with rowscale (e_row from rowexp, which covers the largest such output's rows).
+struct InitOut {
+    float* out;
+    int64_t rows, cols;
+    uint32_t buf;
+    int rowscale;
+};
+struct InitSet {
+    InitOut o[GAO_MAX_IO];
+    int n;
+    uint64_t seed;
+    const int8_t* rowexp;
+};
+cudaError_t launch_init_set(const InitSet& set, cudaStream_t st);
+// One INIT output of a grouped launch (no row scaling); start4 is the index of its first
+// quadruple in the launch (prefix sum of ceil(rows * cols / 4)), increasing along the table.
+struct InitEntry {
+    float* out;
+    int64_t rows, cols;
+    uint64_t seed;
+    uint32_t buf;
+    int64_t start4;
+};
+cudaError_t launch_init_group(const InitEntry* d_tab, int n_entries, int64_t total4, cudaStream_t st);
 cudaError_t launch_axpy(float* out, const float* x, float alpha, const float* y, int64_t n, cudaStream_t st);
 cudaError_t launch_transpose(float* out, const float* in, int64_t rows, int64_t cols, cudaStream_t st);
 // Row sums (ROWSUM) follow one fixed order on every path -- the row-sum kernel, the fused

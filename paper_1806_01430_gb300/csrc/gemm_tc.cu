@@ -425,6 +425,7 @@ struct TileInfo {
     EpiArgs ep;
     int Mp, Np, num_kb, chunk_kb, m0, n0;
     int pf_kb;  // operand tiles are pulled into L2 this many K blocks ahead of their loads (0: off)
+    int tile0;  // launch index of the problem's first tile (its tiles are t - tile0 = 0, 1, ...)
 };
 
 // Tiles of one problem (kernel arguments).
@@ -446,6 +447,7 @@ struct OneProblem {
         ti.m0 = tm * BM;
         ti.n0 = tn * bn;
         ti.pf_kb = pf_kb;
+        ti.tile0 = 0;
     }
 };
 
@@ -475,6 +477,7 @@ struct ProblemTable {
         ti.m0 = tm * BM;
         ti.n0 = tn * bn;
         ti.pf_kb = P->pf_kb;
+        ti.tile0 = P->tile_start;
     }
 };
 
@@ -728,7 +731,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
             if (ep.fuse && ok) {  // fixed butterfly over the warp's rows, one partial per warp
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
-                if (lane == 0 && ep.frob_part) ep.frob_part[(int64_t)t * kEpiWarps + ew] = sq;
+                if (lane == 0 && ep.frob_part) ep.frob_part[(int64_t)(t - ti.tile0) * kEpiWarps + ew] = sq;
             }
         }
     }
@@ -1281,7 +1284,8 @@ bool tc_available(std::string* why) { return get_encode(why); }
 
 cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
                        int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
-                       size_t scratch_bytes, cudaStream_t st, TcProblem* prob, int* launches, std::string* why) {
+                       size_t scratch_bytes, cudaStream_t st, TcProblem* prob, int* launches, std::string* why,
+                       const TcFuse* fuse) {
     *launches = 0;
     memset(prob, 0, sizeof(*prob));
     if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_FP8 || M <= 0 || N <= 0 || K <= 0 || M > (1 << 30) ||
@@ -1295,6 +1299,10 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
         return cudaErrorInvalidValue;
     }
     const int vec = (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0;
+    if (fuse && prec == GAO_GEMM_FP8) {
+        if (why) *why = "chains are not supported on the FP8 path";
+        return cudaErrorInvalidValue;
+    }
     if (prec == GAO_GEMM_FP8) {
         const Fp8Layout L = fp8_layout(M, N, K);
         uint8_t* base = static_cast<uint8_t*>(scratch);
@@ -1341,6 +1349,19 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
         if (!make_map(&prob->ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;
         if (!make_map(&prob->tb, pb, Kp, (int64_t)P * Np, 128, false, why)) return cudaErrorInvalidValue;
         prob->ep = EpiArgs{C, C0, (int)M, (int)N, alpha, beta, vec, nullptr, nullptr, 0, 0};
+        if (fuse) {  // the chain's epilogue, partials in this problem's scratch (tile-local)
+            double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, M, N, K));
+            float* rpart = reinterpret_cast<float*>(reinterpret_cast<char*>(fpart) + tc_frob_partials_bytes(M, N));
+            prob->ep.X = fuse->X;
+            prob->ep.D = fuse->D;
+            prob->ep.E = fuse->E;
+            prob->ep.ldE = fuse->ldE > 0 ? fuse->ldE : M;
+            prob->ep.alpha2 = fuse->alpha2;
+            prob->ep.frob_part = fuse->frob_out ? fpart : nullptr;
+            prob->ep.rsum_part = fuse->rowsum_out ? rpart : nullptr;
+            prob->ep.ldR = N;
+            prob->ep.fuse = 1;
+        }
         prob->Mp = (int)Mp;
         prob->Np = (int)Np;
         prob->num_kb = (int)(Kp / BK);
@@ -1350,6 +1371,29 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
     prob->tiles_n = (int)((N + 127) / 128);
     prob->group = tc_group_of(tile_cfg);
     prob->pf_kb = tc_prefetch_of(tile_cfg);
+    return cudaSuccess;
+}
+
+cudaError_t tc_finalize_chain(int prec, int64_t M, int64_t N, int64_t K, void* scratch, const TcFuse& fuse,
+                              cudaStream_t st, int* launches) {
+    *launches = 0;
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, M, N, K));
+    float* rpart = reinterpret_cast<float*>(reinterpret_cast<char*>(fpart) + tc_frob_partials_bytes(M, N));
+    if (fuse.frob_out) {
+        const int64_t tiles = (ru(M, BM) / BM) * ((N + 127) / 128);  // 128 x 128 tiles of the grouped launch
+        frob_partials_kernel<<<1, 256, 0, st>>>(fpart, tiles * kEpiWarps, fuse.frob_out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        *launches += 1;
+    }
+    if (fuse.rowsum_out) {
+        rowsum_blocks_kernel<<<(unsigned)((4 * N + 255) / 256), 256, 0, st>>>(rpart, (M + kRowsumBlock - 1) / kRowsumBlock,
+                                                                            N, N, fuse.rowsum_out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        *launches += 1;
+    }
     return cudaSuccess;
 }
 

@@ -74,9 +74,17 @@ bool tc_available(std::string* why);
 
 // Split/quantise the operands of one GEMM into `scratch` (kernels on st) and describe it
 // in *prob for a grouped launch (tile_start left 0).  *launches counts kernels issued.
+// With `fuse`, the problem's epilogue also runs the chain (D, E, norm partials and row-sum
+// block values in the problem's scratch); tc_finalize_chain then reduces the partials.
 cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
                        int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
-                       size_t scratch_bytes, cudaStream_t st, TcProblem* prob, int* launches, std::string* why);
+                       size_t scratch_bytes, cudaStream_t st, TcProblem* prob, int* launches, std::string* why,
+                       const TcFuse* fuse = nullptr);
+
+// After a grouped launch with a fused chain: the norm from the per-warp partials and the
+// row sums from the block values of one problem (kernels on st).
+cudaError_t tc_finalize_chain(int prec, int64_t M, int64_t N, int64_t K, void* scratch, const TcFuse& fuse,
+                              cudaStream_t st, int* launches);
 
 // One launch over nprob problems whose table (tile_start set, in order) is at d_probs
 // in device memory; every problem must come from tc_prepare with the same prec and

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "gao_internal.h"
@@ -37,14 +38,15 @@ __global__ void row_exponents_kernel(int8_t* e, int64_t rows, uint64_t seed) {
 }
 
 // out[i] = init_value(seed, buf, i) (times 2^e_row).  Four consecutive elements per
-// thread and iteration, stored as one float4 when the row length is a multiple of 4.
-__global__ void init_kernel(float* __restrict__ out, int64_t rows, int64_t cols, uint64_t seed, uint32_t buf,
-                            const int8_t* __restrict__ rowexp) {
+// thread and iteration, stored as one float4 (a ragged last quadruple element by element).
+__device__ __forceinline__ void init_body(float* __restrict__ out, int64_t rows, int64_t cols, uint64_t seed,
+                                          uint32_t buf, const int8_t* __restrict__ rowexp) {
     const int64_t n = rows * cols;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-    const bool vec = (cols % 4 == 0) && aligned16(out);
+    // a full quadruple is one float4 store; with row scaling only when no row ends inside it
+    const bool vec = aligned16(out) && (!rowexp || cols % 4 == 0);
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; i < n; i += stride) {
-        if (vec) {
+        if (vec && i + 3 < n) {
             // i is a multiple of 4: two hashes give the four elements
             const uint64_t h0 = sm64_hash(init_key(seed, buf, (uint64_t)i >> 1));
             const uint64_t h1 = sm64_hash(init_key(seed, buf, ((uint64_t)i >> 1) + 1));
@@ -69,6 +71,66 @@ __global__ void init_kernel(float* __restrict__ out, int64_t rows, int64_t cols,
             }
         }
     }
+}
+
+// INIT of many programs in one launch (a batch's INIT phase): the quadruples of all
+// entries form one index space, entry e owning [start4[e], start4[e+1]); a thread finds its
+// first entry by binary search and then moves forward with its index.  Each element is
+// formed exactly as init_body forms it.
+__global__ void init_group_kernel(const InitEntry* __restrict__ tab, int n_entries, int64_t total4) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total4) return;
+    int lo = 0, hi = n_entries - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].start4 <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    // the current entry's fields stay in registers until the index passes its end
+    int e = lo;
+    float* out = nullptr;
+    int64_t cols = 0, n = 0, first = 0, next = 0;
+    uint64_t seed = 0;
+    uint32_t buf = 0;
+    bool vec = false;
+    auto load = [&](int k) {
+        out = tab[k].out;
+        cols = tab[k].cols;
+        n = tab[k].rows * cols;
+        seed = tab[k].seed;
+        buf = tab[k].buf;
+        first = tab[k].start4;
+        next = k + 1 < n_entries ? tab[k + 1].start4 : total4;
+        vec = aligned16(out);  // no row scaling: any full quadruple is one float4
+    };
+    load(e);
+    for (; g < total4; g += stride) {
+        while (g >= next) load(++e);
+        const int64_t i = (g - first) * 4;
+        if (vec && i + 3 < n) {
+            const uint64_t h0 = sm64_hash(init_key(seed, buf, (uint64_t)i >> 1));
+            const uint64_t h1 = sm64_hash(init_key(seed, buf, ((uint64_t)i >> 1) + 1));
+            float4 v;
+            v.x = u24_to_value((uint32_t)(h0 >> 40));
+            v.y = u24_to_value((uint32_t)((h0 >> 16) & 0xFFFFFFu));
+            v.z = u24_to_value((uint32_t)(h1 >> 40));
+            v.w = u24_to_value((uint32_t)((h1 >> 16) & 0xFFFFFFu));
+            *reinterpret_cast<float4*>(out + i) = v;
+        } else {
+            for (int q = 0; q < 4 && i + q < n; ++q) out[i + q] = init_value(seed, buf, (uint64_t)(i + q));
+        }
+    }
+}
+
+// Every output of one INIT loop in one launch, one after the other (the output index is
+// a compile-time constant after unrolling, so the set stays in parameter space).
+__global__ void init_set_kernel(const __grid_constant__ InitSet set) {
+#pragma unroll
+    for (int k = 0; k < GAO_MAX_IO; ++k)
+        if (k < set.n)
+            init_body(set.o[k].out, set.o[k].rows, set.o[k].cols, set.seed, set.o[k].buf,
+                      set.o[k].rowscale ? set.rowexp : nullptr);
 }
 
 // ---- element-wise -------------------------------------------------------------------
@@ -139,9 +201,9 @@ __global__ void ew_kernel(float* __restrict__ out, const float* __restrict__ x, 
 __global__ void ew_chain_kernel(EwChain c) {
     const int64_t n = c.n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-    const bool vec = c.vec != 0;
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; i < n; i += stride) {
         float cur[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const bool vec = c.vec != 0 && i + 4 <= n;  // a ragged last quadruple element by element
         const int w = vec ? 4 : (int)(n - i < 4 ? n - i : 4);
 #pragma unroll
         for (int o = 0; o < kMaxChainOps; ++o) {
@@ -575,17 +637,34 @@ __global__ void wait_selftest_kernel(volatile int* flag, int* err, unsigned long
 
 int reduce_blocks() { return sm_count() * 8; }  // a full wave of 256-thread blocks
 
+// Blocks of a reduction over n elements: the full wave for large arrays, fewer for small
+// ones (at least kReduceMinPerBlock elements a block), so that a small array does not pay
+// for a wave of empty blocks and their partials.  The grid, and with it the summation
+// order, depends on n only.
+constexpr int64_t kReduceMinPerBlock = 4096;
+unsigned reduce_grid(int64_t n) {
+    const int64_t want = (n + kReduceMinPerBlock - 1) / kReduceMinPerBlock;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(reduce_blocks(), want));
+}
+
 cudaError_t launch_row_exponents(int8_t* e, int64_t rows, uint64_t seed, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
     row_exponents_kernel<<<grid_for(rows), kThreads, 0, st>>>(e, rows, seed);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init(float* out, int64_t rows, int64_t cols, uint64_t seed, uint32_t buf, const int8_t* rowexp,
-                        cudaStream_t st) {
-    const int64_t n = rows * cols;
-    if (n <= 0) return cudaSuccess;
-    init_kernel<<<grid_for((n + 3) / 4), kThreads, 0, st>>>(out, rows, cols, seed, buf, rowexp);
+cudaError_t launch_init_group(const InitEntry* d_tab, int n_entries, int64_t total4, cudaStream_t st) {
+    if (n_entries < 1 || total4 <= 0) return cudaSuccess;
+    init_group_kernel<<<grid_for(total4), kThreads, 0, st>>>(d_tab, n_entries, total4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_set(const InitSet& set, cudaStream_t st) {
+    if (set.n < 1 || set.n > GAO_MAX_IO) return cudaErrorInvalidValue;
+    int64_t total = 0;
+    for (int k = 0; k < set.n; ++k) total += set.o[k].rows * set.o[k].cols;
+    if (total <= 0) return cudaSuccess;
+    init_set_kernel<<<grid_for((total + 3) / 4), kThreads, 0, st>>>(set);
     return cudaGetLastError();
 }
 
@@ -596,7 +675,7 @@ cudaError_t launch_ew_chain(const EwChain& c, cudaStream_t st) {
     uintptr_t ptrs = 0;
     for (int o = 0; o < c.nops; ++o)
         ptrs |= (uintptr_t)c.op[o].xa | (uintptr_t)c.op[o].yb | (uintptr_t)c.op[o].out;
-    k.vec = (c.n % 4 == 0) && (ptrs & 15u) == 0;
+    k.vec = (ptrs & 15u) == 0;
     ew_chain_kernel<<<grid_for((c.n + 3) / 4), kThreads, 0, st>>>(k);
     return cudaGetLastError();
 }
@@ -646,12 +725,12 @@ cudaError_t launch_rowsum(float* out, const float* in, int64_t rows, int64_t col
 }
 
 cudaError_t launch_frobenius(double* out, const float* in, int64_t n, ReduceScratch rs, cudaStream_t st) {
-    reduce64_kernel<true><<<reduce_blocks(), 256, 0, st>>>(out, in, n < 0 ? 0 : n, rs.partials, rs.counter);
+    reduce64_kernel<true><<<reduce_grid(n), 256, 0, st>>>(out, in, n < 0 ? 0 : n, rs.partials, rs.counter);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sum(double* out, const float* in, int64_t n, ReduceScratch rs, cudaStream_t st) {
-    reduce64_kernel<false><<<reduce_blocks(), 256, 0, st>>>(out, in, n < 0 ? 0 : n, rs.partials, rs.counter);
+    reduce64_kernel<false><<<reduce_grid(n), 256, 0, st>>>(out, in, n < 0 ? 0 : n, rs.partials, rs.counter);
     return cudaGetLastError();
 }
 

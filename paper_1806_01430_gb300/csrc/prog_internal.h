@@ -102,4 +102,13 @@ inline bool gene_fuses(const gao_prog* p, uint64_t gene) {
 inline uint64_t all_genes(int a) { return a >= 64 ? ~0ULL : ((1ULL << a) - 1); }
 void drop_graphs(gao_prog* p);
 
+// Loops that run in the GEMM's epilogue: GEMM (loop li) -> AXPY -> TRANSPOSE [-> ROWSUM of E]
+// [-> FROBENIUS of E], indices of the later loops (-1: not in the chain).
+struct Chain {
+    int axpy = -1, transpose = -1, rowsum = -1, frob = -1;
+};
+// The chain that starts at GEMM loop li under the loop mask (bit i: loop i on the GPU),
+// false when there is none (fusion off, a loop of it on the host, a precision without it).
+bool find_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, Chain* ch);
+
 }  // namespace gao

@@ -528,21 +528,31 @@ gao_status run_gpu_loop(RunCtx& R, int li) {
     cudaError_t e = cudaSuccess;
     int& nl = p->stats[(size_t)li].launches;
     switch (L.kind) {
-        case GAO_LOOP_INIT:
-            for (int t = 0; t < GAO_MAX_IO && e == cudaSuccess; ++t) {
+        case GAO_LOOP_INIT: {
+            // all outputs in one launch; the row exponents (a function of the row) once, for
+            // the largest row-scaled output
+            InitSet set{};
+            int64_t rx_rows = 0, total = 0;
+            for (int t = 0; t < GAO_MAX_IO; ++t) {
                 const int b = L.outs[t];
                 if (b < 0) continue;
-                const int8_t* rx = nullptr;
-                if ((L.flags >> t) & 1) {
-                    rx = (const int8_t*)(a + p->lay.rowexp_off);
-                    e = launch_row_exponents((int8_t*)rx, shp(b).rows, p->opts.seed, st);
-                    if (e != cudaSuccess) break;
-                    nl += shp(b).rows > 0;
-                }
-                e = launch_init(dptr(b), shp(b).rows, shp(b).cols, p->opts.seed, (uint32_t)b, rx, st);
-                nl += shp(b).rows * shp(b).cols > 0;
+                const int rs = (int)((L.flags >> t) & 1);
+                set.o[set.n++] = InitOut{dptr(b), shp(b).rows, shp(b).cols, (uint32_t)b, rs};
+                if (rs) rx_rows = std::max(rx_rows, shp(b).rows);
+                total += shp(b).rows * shp(b).cols;
+            }
+            set.seed = p->opts.seed;
+            set.rowexp = rx_rows > 0 ? (const int8_t*)(a + p->lay.rowexp_off) : nullptr;
+            if (rx_rows > 0) {
+                e = launch_row_exponents((int8_t*)set.rowexp, rx_rows, p->opts.seed, st);
+                nl += 1;
+            }
+            if (e == cudaSuccess && total > 0) {
+                e = launch_init_set(set, st);
+                nl += 1;
             }
             break;
+        }
         case GAO_LOOP_GEMM: {
             const gao_buffer &A = shp(L.ins[0]), &B = shp(L.ins[1]);
             const float* c0 = L.ins[2] >= 0 ? dptr(L.ins[2]) : nullptr;
@@ -826,11 +836,9 @@ bool find_ew_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, EwPlan* 
 // GEMM (C) -> AXPY (D = C + a X) -> TRANSPOSE (E = D^T) [-> FROBENIUS of E, later, with no
 // loop in between writing E].  The buffers must be distinct so that the epilogue's
 // writes cannot race with its reads.
-struct Chain {
-    int axpy = -1, transpose = -1, rowsum = -1, frob = -1;
-};
+}  // namespace
 
-bool find_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, Chain* ch) {
+bool gao::find_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, Chain* ch) {
     if (!fuse || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT) return false;
     const int prec = p->opts.gemm_prec;
     if (prec != GAO_GEMM_BF16 && prec != GAO_GEMM_BF16X3 && prec != GAO_GEMM_BF16X6) return false;
@@ -879,6 +887,8 @@ bool find_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, Chain* ch) 
     }
     return true;
 }
+
+namespace {
 
 gao_status run_gpu_chain(RunCtx& R, int li, const Chain& ch) {
     gao_prog* p = R.p;

@@ -125,3 +125,49 @@ def test_batch_autotune_keeps_parity(gao):
         gao.batch_evaluate(b, [mask])
         check_outputs(gao, progs, handles, refs, mask, 3)
     gao.batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", [3, 2])
+def test_batch_fused_chain_matches_unfused(gao, prec):
+    """Programs created with GAO_FUSE_ON: a gene that puts the GEMM, scale-add and transpose
+    (and the row sums / norm that follow) on the GPU runs them in the grouped launch's
+    epilogue.  Under every gene: C, D, E and row sums bit-identical to the unfused batch,
+    the norm within its reduction's rounding, and the oracle's tolerance."""
+    sizes = [130, 64, 257, 200, 96, 300]
+    progs = [W.six_loop(n, 3200 + i, outputs=("C", "D", "E", "r", "f")) for i, n in enumerate(sizes)]
+    refs = [oracle.run_program(p) for p in progs]
+    runs = {}
+    for fuse in (gao.FUSE_OFF, gao.FUSE_ON):
+        handles = [gao.prog_from_workload(p, gemm_prec=prec, fuse_chains=fuse) for p in progs]
+        b = gao.batch_create(handles)
+        res = {}
+        for mask in range(64):
+            gao.batch_evaluate(b, [mask])
+            res[mask] = [{nm: gao.prog_output(h, p.index(nm)).copy() for nm in ("C", "D", "E", "r", "f")}
+                         for h, p in zip(handles, progs)]
+            if fuse == gao.FUSE_ON:
+                check_outputs(gao, progs, handles, refs, mask, prec)
+        st = gao.batch_stats(b)
+        runs[fuse] = (res, st)
+        gao.batch_destroy(b)
+        for h in handles:
+            gao.prog_destroy(h)
+    (plain, st0), (fused, st1) = runs[gao.FUSE_OFF], runs[gao.FUSE_ON]
+    assert st0["fused_phases"] == 0
+    # genes with GEMM (bit 1), scale-add (bit 2) and transpose (bit 3) on the GPU fuse
+    assert st1["fused_phases"] == sum(1 for m in range(64) if (m >> 1) & 7 == 7)
+    for mask in range(64):
+        for a, c in zip(plain[mask], fused[mask]):
+            for nm in ("C", "D", "E", "r"):
+                assert np.array_equal(a[nm], c[nm]), (mask, nm)
+            assert abs(float(a["f"][0, 0]) - float(c["f"][0, 0])) <= 2e-7 * abs(float(a["f"][0, 0])), mask
+
+
+def test_batch_rejects_mixed_or_gene_fusion(gao):
+    a = gao.prog_from_workload(W.six_loop(64, 1), gemm_prec=3, fuse_chains=gao.FUSE_ON)
+    c = gao.prog_from_workload(W.six_loop(80, 2), gemm_prec=3)
+    with pytest.raises(gao.GaoError):
+        gao.batch_create([a, c])
+    g = gao.prog_from_workload(W.six_loop(64, 3), gemm_prec=3, fuse_chains=gao.FUSE_GENE)
+    with pytest.raises(gao.GaoError):
+        gao.batch_create([g])
