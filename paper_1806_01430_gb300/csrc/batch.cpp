@@ -9,7 +9,10 @@
 // single CUDA graph launch.  The graphs are captured once, when the batch is created:
 // each phase forks the programs' kernels over several side streams (small kernels of
 // different programs run concurrently) and, for the GEMM loop of a tensor-core
-// precision, joins into one grouped tcgen05 launch over every program's tiles.  A gene
+// precision, joins into one grouped tcgen05 launch over every program's tiles; the INIT
+// loop of all programs is one grouped launch too.  With fused chains, a gene that puts
+// the GEMM -> scale-add -> transpose [-> row sums] [-> norm] chain on the GPU runs it in
+// the grouped launch's epilogue (one captured GEMM phase per chain shape).  A gene
 // then costs its boundary copies, its graph launches and its host loops.  The gene's
 // time is the wall time of the whole suite under that gene; a gene measured before is
 // served from the batch's cache (Sec. 4).
