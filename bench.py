@@ -510,8 +510,9 @@ def our_arm(args, world, rank, local):
         peak = bf16 * 2.0 if prec == "fp8" else bf16 / PRODUCTS[prec]
         achieved = flops / (gemm_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                # DRAM traffic depends on the tile configuration: only a capture of this one counts
                 "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_{prec}_{wname.split('_all_gpu')[0]}"
-                                                         f"{'_fused' if args.fuse else ''}.md"),
+                                                         f"{'_fused' if args.fuse else ''}_k{kc}_t{tcfg}.md"),
                 "kernel": f"gemm_tc ({prec})" + (" with the fused scale-add / transpose / norm epilogue"
                                                   if args.fuse and prec != "fp8" else ""),
                 "products": PRODUCTS[prec],

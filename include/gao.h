@@ -304,7 +304,8 @@ gao_status ga_run_table(const double *times, int n_genes, const gao_ga_params *p
  *           tile width 128 or 256 columns,
  * bit 4     L2 prefetch of the operand tiles (tile_cfg bit 2),
  * and fitness is (measured GEMM time)^(-1/2), the paper's fitness with the kernel time
- * as the benchmark.  The best configuration is written into the program's (or the
+ * as the benchmark (the GEMM with the loop chain in its epilogue when the program fuses
+ * it under the all-GPU gene, since that is the kernel that runs).  The best configuration is written into the program's (or the
  * batch's) options and used from then on. */
 typedef struct gao_autotune_result {
     int32_t kchunk;     /* best K chunk (0: unchunked)                         */

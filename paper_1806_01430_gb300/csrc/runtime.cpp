@@ -1620,6 +1620,19 @@ extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, ga
         return cuda_fail(ce, "cudaEventCreate");
     }
     int* d_err = (int*)(p->arena + p->lay.err_off);
+    // with fused chains the kernel that runs under the all-GPU gene carries the chain in its
+    // epilogue, so that is the one timed (its D, E, row sums and norm are formed again by
+    // the next run)
+    Chain ch;
+    TcFuse fz{};
+    const bool fused = find_chain(p, li, loop_mask_of(p, all), gene_fuses(p, all), &ch);
+    if (fused) {
+        auto dptr = [&](int bi) { return (float*)p->bufs[(size_t)bi].dev; };
+        const gao_loop &X = p->loops[(size_t)ch.axpy], &T = p->loops[(size_t)ch.transpose];
+        fz = TcFuse{dptr(X.ins[1]), dptr(X.outs[0]), dptr(T.outs[0]),
+                    ch.frob >= 0 ? (double*)p->bufs[(size_t)p->loops[(size_t)ch.frob].outs[0]].dev : nullptr,
+                    (float)X.alpha, 0, ch.rowsum >= 0 ? dptr(p->loops[(size_t)ch.rowsum].outs[0]) : nullptr};
+    }
     auto time_cfg = [&](int kchunk, int tile_cfg, double* ms) -> gao_status {
         std::vector<double> v;
         for (int r = 0; r < 6; ++r) {
@@ -1628,7 +1641,7 @@ extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, ga
             cudaError_t e = launch_gemm_tc(prec, C, (const float*)p->bufs[(size_t)L.ins[0]].dev,
                                            (const float*)p->bufs[(size_t)L.ins[1]].dev, C0, A.rows, B.cols, A.cols,
                                            (float)L.alpha, beta, kchunk, tile_cfg, p->arena + p->lay.tc_off,
-                                           p->lay.tc_bytes, d_err, p->st, ev, &why);
+                                           p->lay.tc_bytes, d_err, p->st, ev, &why, fused ? &fz : nullptr);
             if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "autotune launch") : fail(GAO_EINVAL, why);
             if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return cuda_fail(e, "autotune sync");
             float t = 0.0f;

@@ -220,3 +220,23 @@ def test_prog_autotune_keeps_parity(gao, prec):
     ref = oracle.run_program(prog)
     assert oracle.rel_err(gao.prog_output(p, prog.index("C")), ref["C"]) <= TOL[prec]
     gao.prog_destroy(p)
+
+
+def test_prog_autotune_fused_chain(gao):
+    """With fused chains the autotuner times the GEMM that carries the chain; the tuned
+    program still gives the unfused program's C, D, E and row sums bit for bit (same
+    configuration), and the oracle's tolerance."""
+    prog = W.six_loop(1024, 78, outputs=("C", "D", "E", "r", "f"))
+    p = gao.prog_from_workload(prog, gemm_prec=PREC["bf16x6"], fuse_chains=gao.FUSE_ON)
+    r = gao.prog_autotune(p, pop=6, generations=4, seed=1)
+    assert r["evaluations"] >= 1 and 0 < r["best_ms"] <= r["default_ms"]
+    gao.prog_run(p, 0b111111)
+    fused = {nm: gao.prog_output(p, prog.index(nm)) for nm in ("C", "D", "E", "r", "f")}
+    gao.prog_destroy(p)
+    q = gao.prog_from_workload(prog, gemm_prec=PREC["bf16x6"], kchunk=r["kchunk"], tile_cfg=r["tile_cfg"])
+    gao.prog_run(q, 0b111111)
+    for nm in ("C", "D", "E", "r"):
+        assert np.array_equal(fused[nm], gao.prog_output(q, prog.index(nm))), nm
+    ref = oracle.run_program(prog)
+    assert oracle.rel_err(fused["C"], ref["C"]) <= TOL["bf16x6"]
+    gao.prog_destroy(q)
