@@ -123,7 +123,11 @@ cudaError_t launch_sum(double* out, const float* in, int64_t n, ReduceScratch rs
 cudaError_t launch_relu(float* out, const float* in, int64_t n, cudaStream_t st);
 cudaError_t launch_square(float* out, const float* in, int64_t n, cudaStream_t st);
 cudaError_t launch_colmax(float* out, const float* in, int64_t rows, int64_t cols, uint32_t* keys, cudaStream_t st);
-cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st);
+// Output rows [row_begin, row_end) of the rows x cols image (row_end < 0: to the last row);
+// the image is zero outside its own rows, whatever the range, so a frame formed in row
+// ranges gives the same bits as in one launch.
+cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st,
+                            int64_t row_begin = 0, int64_t row_end = -1);
 
 // A linear chain of element-wise loops in one pass.  Op o computes kind 0 RELU, 1 SQUARE
 // or 2 AXPY (x + alpha y) with x = xa[i] (or the previous op's value when xa is null) and,
@@ -147,7 +151,8 @@ cudaError_t launch_ew_chain(const EwChain& c, cudaStream_t st);
 // Gradient chain in one pass: g1, g2 = stencils p1, p2 of `in`; s1 = g1*g1, s2 = g2*g2;
 // m = s1 + alpha s2 (swap: s2 + alpha s1).  Null g1/g2/s1/s2 are not written.
 cudaError_t launch_grad_chain(const float* in, int64_t rows, int64_t cols, int p1, int p2, float alpha, bool swap,
-                              float* g1, float* g2, float* s1, float* s2, float* m, cudaStream_t st);
+                              float* g1, float* g2, float* s1, float* s2, float* m, cudaStream_t st,
+                              int64_t row_begin = 0, int64_t row_end = -1);
 
 // Weights of the 3x3 stencil presets of GAO_LOOP_STENCIL3, row-major over (a, b).
 // Every weight is a small integer or a power-of-two fraction, exact in binary32.

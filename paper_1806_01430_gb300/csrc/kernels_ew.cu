@@ -561,12 +561,13 @@ constexpr int kChainBlocks = 8;  // resident blocks per SM the chain variant is 
 template <bool VEC, bool CHAIN, int P1, int P2>
 __global__ void __launch_bounds__(kStencilThreads, CHAIN ? kChainBlocks : 8)
     stencil3_kernel(StencilOut out, const float* __restrict__ in, int64_t rows, int64_t cols, StencilW w,
-                    StencilW w2, int strip) {
+                    StencilW w2, int strip, int64_t row_begin, int64_t row_end) {
     constexpr int AHEAD = CHAIN ? kChainAhead : kStencilAhead;
     const int lane = threadIdx.x & 31;
     const int64_t c0 = ((int64_t)blockIdx.x * kStencilThreads + threadIdx.x) * 4;
-    const int64_t r0 = (int64_t)blockIdx.y * strip;
-    const int64_t r1 = r0 + strip < rows ? r0 + strip : rows;
+    // output rows [row_begin, row_end) of a rows-high image (zero outside the image only)
+    const int64_t r0 = row_begin + (int64_t)blockIdx.y * strip;
+    const int64_t r1 = r0 + strip < row_end ? r0 + strip : row_end;
     const int64_t ylim = r1 + 1 < rows ? r1 + 1 : rows;  // rows >= ylim are never needed
     StencilRow<VEC> ring[AHEAD];
     float up[6], md[6], dn[6];
@@ -758,11 +759,13 @@ cudaError_t launch_colmax(float* out, const float* in, int64_t rows, int64_t col
 
 namespace {
 cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t rows, int64_t cols, int p1, int p2,
-                                bool chain, cudaStream_t st) {
+                                bool chain, int64_t row_begin, int64_t row_end, cudaStream_t st) {
     StencilW w, w2;
     if (!stencil_weights(p1, w.w) || (chain && !stencil_weights(p2, w2.w))) return cudaErrorInvalidValue;
     if (!chain) w2 = w;
-    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (row_begin < 0 || row_end > rows || row_begin > row_end) return cudaErrorInvalidValue;
+    const int64_t span = row_end - row_begin;  // output rows of this launch
+    if (span <= 0 || cols <= 0) return cudaSuccess;
     const int64_t gx = ((cols + 3) / 4 + kStencilThreads - 1) / kStencilThreads;
     if (gx > 0x7fffffff) return cudaErrorInvalidValue;
     // strips of rows: two waves of the resident 128-thread blocks (8 per SM at <= 64
@@ -770,17 +773,17 @@ cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t ro
     // rows stay a small share
     const int64_t want_blocks = (int64_t)sm_count() * 2 * (chain ? kChainBlocks : 8);
     int64_t strips = (want_blocks + gx - 1) / gx;
-    int64_t strip = (rows + strips - 1) / strips;
+    int64_t strip = (span + strips - 1) / strips;
     if (strip < 16) strip = 16;
-    if ((rows + strip - 1) / strip > 65535) strip = (rows + 65534) / 65535;
+    if ((span + strip - 1) / strip > 65535) strip = (span + 65534) / 65535;
     if (strip > 0x7fffffff) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)gx, (unsigned)((rows + strip - 1) / strip));
+    const dim3 grid((unsigned)gx, (unsigned)((span + strip - 1) / strip));
     uintptr_t ptrs = (uintptr_t)in | (uintptr_t)o.m | (uintptr_t)o.g1 | (uintptr_t)o.g2 | (uintptr_t)o.s1 |
                      (uintptr_t)o.s2;
     const bool vec = (cols % 4 == 0) && (ptrs & 15u) == 0;
     const int sp = (int)strip;
 #define GAO_STENCIL_LAUNCH(V, C, A, B) \
-    stencil3_kernel<V, C, A, B><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, sp)
+    stencil3_kernel<V, C, A, B><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, sp, row_begin, row_end)
     if (chain) {
         // the image program's pair (Sobel x, Sobel y) with compile-time weights; any
         // other pair with run-time weights
@@ -807,16 +810,18 @@ cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t ro
 }
 }  // namespace
 
-cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st) {
+cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st,
+                            int64_t row_begin, int64_t row_end) {
     const StencilOut o{out, nullptr, nullptr, nullptr, nullptr, 0.0f, 0};
-    return launch_stencil_pass(o, in, rows, cols, preset, preset, false, st);
+    return launch_stencil_pass(o, in, rows, cols, preset, preset, false, row_begin, row_end < 0 ? rows : row_end, st);
 }
 
 cudaError_t launch_grad_chain(const float* in, int64_t rows, int64_t cols, int p1, int p2, float alpha, bool swap,
-                              float* g1, float* g2, float* s1, float* s2, float* m, cudaStream_t st) {
+                              float* g1, float* g2, float* s1, float* s2, float* m, cudaStream_t st,
+                              int64_t row_begin, int64_t row_end) {
     if (!m) return cudaErrorInvalidValue;
     const StencilOut o{g1, g2, s1, s2, m, alpha, swap ? 1 : 0};
-    return launch_stencil_pass(o, in, rows, cols, p1, p2, true, st);
+    return launch_stencil_pass(o, in, rows, cols, p1, p2, true, row_begin, row_end < 0 ? rows : row_end, st);
 }
 
 cudaError_t launch_wait_selftest(int* flag, int* err, double limit_s, cudaStream_t st) {

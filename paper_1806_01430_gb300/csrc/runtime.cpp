@@ -1013,6 +1013,75 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
     return GAO_OK;
 }
 
+// Copy/compute overlap for a GPU STENCIL3 loop whose image comes from the host (a camera
+// frame, 30x slower to copy than to read from HBM): the frame is copied in row strips on
+// the copy stream, and as each strip lands the stencil forms the rows whose three input rows
+// are all in -- and the gradient chain on the stencil's output, when the gene fuses one
+// there, the rows whose three blurred rows are done.  A pixel is formed the same way
+// whatever the row ranges, so the bits are those of one launch.
+bool stencil_pipelined(const gao_prog* p, const gao_loop& L) {
+    if (L.kind != GAO_LOOP_STENCIL3 || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT) return false;
+    const BufState& X = p->bufs[(size_t)L.ins[0]];
+    return !X.vd && X.vh && X.bytes >= kPipelineMinBytes && X.d.rows >= 4 * kMaxRowBlocks &&
+           L.ins[0] != L.outs[0];
+}
+
+gao_status run_gpu_stencil_pipelined(RunCtx& R, int li, const GradChain* gch) {
+    gao_prog* p = R.p;
+    const gao_loop& L = p->loops[(size_t)li];
+    gao_loop_stat& S = p->stats[(size_t)li];
+    BufState& X = p->bufs[(size_t)L.ins[0]];
+    float* out = (float*)p->bufs[(size_t)L.outs[0]].dev;
+    const int64_t rows = X.d.rows, cols = X.d.cols;
+    const int nb = kMaxRowBlocks;
+    cudaStream_t st = R.st, cs = p->cst;
+    cudaEvent_t* ev = &p->ev[(size_t)li * 6];
+    GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[0], st));  // the copy overwrites X on the device: after earlier work
+    GAO_CUDA_TRY(cudaStreamWaitEvent(cs, p->pipe_ev[0], 0));
+    GAO_CUDA_TRY(record_timing(ev[0], cs));
+    int64_t at[kMaxRowBlocks + 1];
+    for (int k = 0; k <= nb; ++k) at[k] = rows * k / nb;
+    for (int k = 0; k < nb; ++k) {
+        const size_t off = (size_t)at[k] * cols * 4, len = (size_t)(at[k + 1] - at[k]) * cols * 4;
+        GAO_CUDA_TRY(cudaMemcpyAsync(X.dev + off, (char*)X.host + off, len, cudaMemcpyHostToDevice, cs));
+        S.h2d_bytes += len;
+        // the copy-time stamp goes before the last strip's event, so that everything on the
+        // copy stream is joined back into the program's stream (a captured graph needs that)
+        if (k == nb - 1) GAO_CUDA_TRY(record_timing(ev[1], cs));
+        GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + (size_t)k], cs));
+    }
+    GAO_CUDA_TRY(record_timing(ev[2], st));
+    const int preset = (int)(L.flags & ~GAO_LOOP_EXTERNAL_CALL);
+    auto chain_ptr = [&](int b, bool live) { return live ? (float*)p->bufs[(size_t)b].dev : nullptr; };
+    int64_t formed = 0, chained = 0;  // output rows done by the stencil and by the chain
+    for (int k = 0; k < nb; ++k) {
+        GAO_CUDA_TRY(cudaStreamWaitEvent(st, p->pipe_ev[2 + (size_t)k], 0));
+        const int64_t f1 = k == nb - 1 ? rows : at[k + 1] - 1;  // row r needs input row r + 1
+        if (f1 > formed) {
+            cudaError_t e = launch_stencil3(out, (const float*)X.dev, rows, cols, preset, st, formed, f1);
+            if (e != cudaSuccess) return cuda_fail(e, "stencil strip launch");
+            S.launches += 1;
+            formed = f1;
+        }
+        if (gch) {
+            const int64_t c1 = k == nb - 1 ? rows : formed - 1;  // row r needs stencil row r + 1
+            if (c1 > chained) {
+                cudaError_t e = launch_grad_chain(out, rows, cols, gch->p1, gch->p2, gch->alpha, gch->swap,
+                                                  chain_ptr(gch->g1, gch->live[0]), chain_ptr(gch->g2, gch->live[1]),
+                                                  chain_ptr(gch->s1, gch->live[2]), chain_ptr(gch->s2, gch->live[3]),
+                                                  (float*)p->bufs[(size_t)gch->m].dev, st, chained, c1);
+                if (e != cudaSuccess) return cuda_fail(e, "gradient chain strip launch");
+                S.launches += 1;
+                chained = c1;
+            }
+        }
+    }
+    GAO_CUDA_TRY(record_timing(ev[3], st));
+    X.vd = true;
+    p->ev_used[(size_t)li] |= 1 | 2;
+    return GAO_OK;
+}
+
 double ev_ms(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.0;
@@ -1050,6 +1119,28 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
         cudaEvent_t* ev = &p->ev[(size_t)li * 6];
         Chain chain;
         GradChain gch;
+        if (gpu && stencil_pipelined(p, L)) {
+            // the image comes from the host: strips overlapped with its copy, with the
+            // gradient chain on this stencil's output in the same strips when the gene fuses it
+            const bool chained = li + 1 < n && find_grad_chain(p, li + 1, gene_mask, fuse, &gch) &&
+                                 gch.x == L.outs[0];
+            if ((status = run_gpu_stencil_pipelined(R, li, chained ? &gch : nullptr)) != GAO_OK) break;
+            BufState& Bo = p->bufs[(size_t)L.outs[0]];
+            Bo.vh = false;
+            Bo.vd = true;
+            if (chained) {
+                const int outs[5] = {gch.g1, gch.g2, gch.s1, gch.s2, gch.m};
+                for (int t = 0; t < 5; ++t) {
+                    BufState& B = p->bufs[(size_t)outs[t]];
+                    B.vh = false;
+                    B.vd = t == 4 || gch.live[t];  // an unwritten intermediate holds nothing
+                }
+                for (int j = li + 1; j <= li + 5; ++j) fused |= 1ULL << j;
+            }
+            if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
+            if (R.timed_out) break;
+            continue;
+        }
         if (gpu && L.kind == GAO_LOOP_STENCIL3 && find_grad_chain(p, li, gene_mask, fuse, &gch)) {
             BufState& X = p->bufs[(size_t)gch.x];
             const bool copies = !X.vd;

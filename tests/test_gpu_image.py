@@ -220,3 +220,34 @@ def test_gradient_chain_only_when_all_on_gpu(gao):
         M2 = gao.prog_output(p, prog.index("M2")).astype(np.float64)
         assert np.all(np.abs(M2 - ref["M2"]) <= m2_bound(X))
     gao.prog_destroy(p)
+
+
+@pytest.mark.parametrize("h,w", [(2048, 2048), (2051, 2049)])
+@pytest.mark.parametrize("fuse", [0, 1])
+def test_host_frame_strips_bit_identical(gao, h, w, fuse):
+    """A frame of 16 MiB or more from the host is copied in row strips, and the blur -- and,
+    fused, the gradient chain on its output -- run on each strip's ready rows while the next
+    strips are on the link.  M2, the edge energy and the column maxima equal those of the same
+    frame made on the device (one launch per pass) bit for bit."""
+    seed = 45
+    hp = W.image_program(h, w, seed, outputs=("M2", "e", "q"), host_image=True)
+    dp = W.image_program(h, w, seed, outputs=("M2", "e", "q"))
+    X = oracle.init_matrix(seed, 0, h, w).astype(np.float32)
+    p = gao.prog_from_workload(hp, fuse_chains=fuse)
+    gao.prog_set_input(p, hp.index("X"), X)
+    outs = []
+    for _ in range(2):  # the second run of the all-GPU gene is captured as a graph
+        gao.prog_run(p, (1 << hp.n_loops) - 1)
+        outs.append({nm: gao.prog_output(p, hp.index(nm)).copy() for nm in ("M2", "e", "q")})
+    st = gao.prog_stats(p)
+    gao.prog_destroy(p)
+    q = gao.prog_from_workload(dp, fuse_chains=fuse)
+    gao.prog_run(q, (1 << dp.n_loops) - 1)
+    want = {nm: gao.prog_output(q, dp.index(nm)) for nm in ("M2", "e", "q")}
+    gao.prog_destroy(q)
+    for o in outs:
+        for nm in ("M2", "e", "q"):
+            assert np.array_equal(o[nm], want[nm]), nm
+    assert st[0]["h2d_bytes"] == h * w * 4
+    assert st[0]["launches"] == (8 if fuse else 4)  # a stencil (and a chain) launch per strip
+    assert [s["placement"] for s in st[1:6]] == ([2] * 5 if fuse else [1] * 5)
