@@ -896,10 +896,9 @@ gao_status run_gpu_chain(RunCtx& R, int li, const Chain& ch) {
     auto dptr = [&](int b) { return (float*)p->bufs[(size_t)b].dev; };
     const gao_buffer &A = p->bufs[(size_t)G.ins[0]].d, &B = p->bufs[(size_t)G.ins[1]].d;
     const float* c0 = G.ins[2] >= 0 ? dptr(G.ins[2]) : dptr(G.outs[0]);
-    TcFuse fz{dptr(X.ins[1]), dptr(X.outs[0]), dptr(T.outs[0]),
-              ch.frob >= 0 ? (double*)p->bufs[(size_t)p->loops[(size_t)ch.frob].outs[0]].dev : nullptr,
-              (float)X.alpha};
-    fz.rowsum_out = ch.rowsum >= 0 ? dptr(p->loops[(size_t)ch.rowsum].outs[0]) : nullptr;
+    const TcFuse fz{dptr(X.ins[1]), dptr(X.outs[0]), dptr(T.outs[0]),
+                    ch.frob >= 0 ? (double*)p->bufs[(size_t)p->loops[(size_t)ch.frob].outs[0]].dev : nullptr,
+                    (float)X.alpha, 0, ch.rowsum >= 0 ? dptr(p->loops[(size_t)ch.rowsum].outs[0]) : nullptr};
     TcEvents tev{R.events ? p->ev[(size_t)li * 6 + 4] : nullptr, R.events ? p->ev[(size_t)li * 6 + 5] : nullptr, 0};
     std::string why;
     cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, dptr(G.outs[0]), dptr(G.ins[0]), dptr(G.ins[1]), c0, A.rows,
