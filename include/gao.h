@@ -188,6 +188,9 @@ gao_status prog_set_input(gao_prog *p, int buf, const void *host_src, uint64_t b
 
 #define GAO_RUN_KEEP_DEVICE 1u /* leave OUTPUT buffers on the device (no final copy) */
 #define GAO_RUN_NO_GRAPH 2u    /* plain launches: no CUDA graph is captured or replayed       */
+#define GAO_RUN_NO_LOOP_TIMES 4u /* record no per-loop CUDA events (fewer nodes in a captured
+                                    graph); prog_stats then reports no loop, copy or kernel
+                                    times for the run, the run's own time is unchanged     */
 
 /* Run every loop in program order.  Gene bit k belongs to the k-th offloadable loop in
  * program order (bit i to loop i when every loop is offloadable); that loop runs on the

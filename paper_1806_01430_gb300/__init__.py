@@ -35,6 +35,7 @@ FP32_SIMT, BF16, BF16X3, BF16X6, FP8 = range(5)
 PREC_NAMES = ["fp32_simt", "bf16", "bf16x3", "bf16x6", "fp8"]
 RUN_KEEP_DEVICE = 1
 RUN_NO_GRAPH = 2  # plain launches: no CUDA graph captured or replayed
+RUN_NO_LOOP_TIMES = 4  # no per-loop CUDA events: prog_stats reports no loop times for the run
 TRANSFER_RESIDENT, TRANSFER_PER_LOOP = 0, 1
 FUSE_OFF, FUSE_ON, FUSE_GENE = 0, 1, 2
 MAX_IO = 4

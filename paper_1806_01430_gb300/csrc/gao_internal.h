@@ -186,7 +186,9 @@ cudaError_t launch_gemm_simt(float* C, const float* A, const float* B, const flo
 // Set while a run is being captured as a CUDA graph: timing events are then recorded as
 // graph nodes (external events), so that a replay records them too.
 extern thread_local bool g_capturing;
+extern thread_local bool g_no_times;  // a run without per-loop timing events (GAO_RUN_NO_LOOP_TIMES)
 inline cudaError_t record_timing(cudaEvent_t e, cudaStream_t s) {
+    if (g_no_times) return cudaSuccess;
     return g_capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
 }
 

@@ -63,7 +63,7 @@ struct gao_prog {
     std::vector<cudaEvent_t> pipe_ev;     // its events: fork, B landed, one per row block
     std::vector<int8_t> verdict;  // gao_offload of every loop
     std::vector<int> gene_loop;   // gene bit k -> index of the k-th offloadable loop
-    std::unordered_map<uint64_t, GraphEntry> graphs;  // key: gene * 4 + run flags
+    std::unordered_map<uint64_t, GraphEntry> graphs;  // key: gene * 8 + run flags (KEEP_DEVICE, NO_LOOP_TIMES)
 };
 
 namespace gao {

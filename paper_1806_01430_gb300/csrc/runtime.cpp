@@ -456,6 +456,7 @@ extern "C" gao_status prog_set_input(gao_prog* p, int buf, const void* host_src,
 namespace gao {
 
 thread_local bool g_capturing = false;
+thread_local bool g_no_times = false;
 
 void drop_graphs(gao_prog* p) {
     for (auto& kv : p->graphs)
@@ -1411,6 +1412,11 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
     cudaError_t ce = cudaSetDevice(p->device);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
     RunCtx R{p, 0.0, false, CpuCtx{p->opts.cpu_threads, 0.0, false}, p->st, true};
+    const bool no_times = (flags & GAO_RUN_NO_LOOP_TIMES) != 0;
+    struct TimesOff {  // record_timing is a no-op for this run only
+        explicit TimesOff(bool on) { g_no_times = on; }
+        ~TimesOff() { g_no_times = false; }
+    } times_off(no_times);
     const double t0 = now_s();
     if (p->opts.timeout_s > 0.0) R.deadline = R.cpu.deadline = t0 + p->opts.timeout_s;
     const bool uses_gpu = gene_mask != 0;
@@ -1421,7 +1427,7 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
     const bool all_gpu = gene_mask == all_genes(n) && gene_length(p) > 0;
     GraphEntry* ge = nullptr;
     if (all_gpu && !(flags & GAO_RUN_NO_GRAPH)) {
-        ge = &p->graphs[gene * 4 + (flags & GAO_RUN_KEEP_DEVICE)];
+        ge = &p->graphs[gene * 8 + (flags & (GAO_RUN_KEEP_DEVICE | GAO_RUN_NO_LOOP_TIMES))];
         ge->runs += 1;
     }
     if (ge && !ge->exec && !ge->failed && ge->runs >= 2) capture_run(R, gene_mask, fuse, flags, ge);
@@ -1454,6 +1460,7 @@ extern "C" gao_status prog_run(gao_prog* p, uint64_t gene, uint32_t flags, doubl
         if (seconds_out) *seconds_out = p->opts.timeout_s;
         return fail(GAO_ETIMEOUT, "run exceeded its budget of " + std::to_string(p->opts.timeout_s) + " s");
     }
+    if (no_times) std::fill(p->ev_used.begin(), p->ev_used.end(), 0);  // no event of this run to read
     p->stats_pending = true;  // the event times are read when prog_stats asks for them
     return GAO_OK;
 }

@@ -102,3 +102,30 @@ def test_mixed_genes_never_captured(gao):
         assert gao.prog_stats(p)[3]["placement"] == 0
     assert gao.prog_graphs(p) == (0, 0)
     gao.prog_destroy(p)
+
+
+def test_runs_without_loop_times(gao):
+    """GAO_RUN_NO_LOOP_TIMES records no per-loop events (a captured graph without event
+    nodes, kept apart from the timed one): the same outputs, the run's own time, and no loop
+    times in the statistics; a later timed run reports them again."""
+    prog = W.six_loop(320, 46, outputs=("C", "D", "E", "r", "f"))
+    p = gao.prog_from_workload(prog, gemm_prec=3, fuse_chains=1)
+    gene = (1 << gao.prog_gene_length(p)) - 1
+    gao.prog_run(p, gene)
+    want = outs(gao, p, prog)
+    for it in range(3):  # the second run is captured, the third replayed
+        secs = gao.prog_run(p, gene, gao.RUN_NO_LOOP_TIMES)
+        assert secs > 0
+        o = outs(gao, p, prog)
+        for nm in want:
+            assert np.array_equal(o[nm], want[nm]), (it, nm)
+        st = gao.prog_stats(p)
+        assert all(s["device_ms"] == 0 and s["kernel_ms"] == 0 and s["copy_ms"] == 0 for s in st), st
+        assert [s["placement"] for s in st] == [1, 1, 2, 2, 2, 2]
+    assert gao.prog_graphs(p)[0] == 1
+    for _ in range(3):
+        gao.prog_run(p, gene)
+    st = gao.prog_stats(p)
+    assert st[1]["kernel_ms"] > 0 and st[0]["device_ms"] > 0
+    assert gao.prog_graphs(p)[0] == 2  # the timed variant has its own graph
+    gao.prog_destroy(p)
