@@ -185,6 +185,37 @@ def test_full_size_bf16x6_sampled(gao, n, seed, rowscale):
     assert err <= 1e-6, err
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp32_simt", "fp8"])
+@pytest.mark.parametrize("seed,rowscale", [(W.SEED_CONFIG2, False), (W.SEED_CONFIG2_ROWS, True)])
+def test_full_size_n8192_every_precision(gao, prec, seed, rowscale):
+    """configs[2] at full size, n = 8192, for the other GEMM paths: uniform entries and rows of
+    A scaled by 2^e (e in [-10, 10]); sampled C entries against the oracle, each within its
+    precision's gate (FP8: reported against 6e-2)."""
+    n = 8192
+    if prec == "fp8" and not rowscale:
+        pytest.skip("covered by test_full_size_fp8_sampled")
+    prog = W.six_loop(n, seed, rowscale_a=rowscale, outputs=("C",))
+    p = gao.prog_from_workload(prog, gemm_prec={"fp32_simt": 0, **PREC}[prec])
+    gao.prog_run(p, 0b111111)
+    C = gao.prog_output(p, prog.index("C"))
+    gao.prog_destroy(p)
+    rng = np.random.default_rng(11)
+    ii, jj = rng.integers(0, n, 192), rng.integers(0, n, 192)
+    want = oracle.gemm_init_entries(seed, (0, 1, 2), rowscale, n, n, n, 1.5, 0.5, ii, jj)
+    got = C[ii, jj].astype(np.float64)
+    if rowscale:
+        # every row counts equally: the error and the product term 1.5 (A B)_ij, both in units
+        # of the row's factor 2^e (a raw normwise error over 192 samples measures the one or
+        # two largest rows; the C0 term, not scaled, stays out of the reference)
+        unit = np.array([2.0 ** oracle.row_exponent(seed, int(i)) for i in ii])
+        c0 = np.array([oracle.init_value(seed, 2, int(i) * n + int(j)) for i, j in zip(ii, jj)])
+        err = math.sqrt(float((((got - want) / unit) ** 2).mean()) / float((((want - 0.5 * c0) / unit) ** 2).mean()))
+    else:
+        err = math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
+    print(f"{prec} n={n} rowscale={rowscale} sampled normwise error {err:.3e}")
+    assert err <= {"fp32_simt": 1e-6, **TOL}[prec], err
+
+
 def test_full_size_fp8_sampled(gao):
     """configs[2] size n = 8192: FP8 e4m3 with 128-block scales, error reported against 6e-2."""
     n, seed = 8192, W.SEED_CONFIG2
