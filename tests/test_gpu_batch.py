@@ -171,3 +171,38 @@ def test_batch_rejects_mixed_or_gene_fusion(gao):
     g = gao.prog_from_workload(W.six_loop(64, 3), gemm_prec=3, fuse_chains=gao.FUSE_GENE)
     with pytest.raises(gao.GaoError):
         gao.batch_create([g])
+
+
+def test_batch_full_suite_sampled(gao):
+    """configs[3] at full size: the bench's 64-program suite (n log-uniform in [128, 2048]),
+    BF16x3 with fused chains, the all-GPU gene in one batched evaluation.  Every program: sampled
+    C entries against the oracle (entry by entry from the counter hash), D = C + 2A and E = D^T
+    exactly, row sums in their fixed order exactly, the norm within its rounding bound."""
+    import math
+    from test_gpu_rowsum import rowsum_fixed_order
+    sizes = W.batch_sizes(64)
+    progs = [W.six_loop(n, W.SEED_CONFIG3_BASE + p, outputs=("C", "D", "E", "r", "f"))
+             for p, n in enumerate(sizes)]
+    handles = [gao.prog_from_workload(pr, gemm_prec=2, fuse_chains=gao.FUSE_ON) for pr in progs]
+    b = gao.batch_create(handles)
+    fit, sec, hits = gao.batch_evaluate(b, [0b111111])
+    assert sec[0] > 0 and gao.batch_stats(b)["fused_phases"] == 1
+    rng = np.random.default_rng(17)
+    for prog, h in zip(progs, handles):
+        n, seed = prog.buffers[0].rows, prog.seed
+        C, D, E = (gao.prog_output(h, prog.index(nm)) for nm in ("C", "D", "E"))
+        ii, jj = rng.integers(0, n, 32), rng.integers(0, n, 32)
+        want = oracle.gemm_init_entries(seed, (0, 1, 2), False, n, n, n, 1.5, 0.5, ii, jj)
+        got = C[ii, jj].astype(np.float64)
+        err = math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
+        assert err <= TOL[2], (n, err)
+        A = oracle.init_matrix(seed, 0, n, n).astype(np.float32)
+        assert np.array_equal(D, C + np.float32(2.0) * A), n
+        assert np.array_equal(E, D.T), n
+        assert np.array_equal(gao.prog_output(h, prog.index("r")), rowsum_fixed_order(E)), n
+        E64 = E.astype(np.float64)
+        fn = math.sqrt(float((E64 * E64).sum()))
+        assert abs(float(gao.prog_output(h, prog.index("f"))[0, 0]) - fn) <= 2e-7 * fn, n
+    gao.batch_destroy(b)
+    for h in handles:
+        gao.prog_destroy(h)
