@@ -231,6 +231,62 @@ def test_full_size_fp8_sampled(gao):
     assert err <= 6e-2, err
 
 
+def _freivalds_residual(C, seed, n, rng):
+    """Normwise relative residuals of C x = 1.5 A (B x) + 0.5 C0 x and y^T C = 1.5 (y^T A) B
+    + 0.5 y^T C0 (Freivalds 1977) for random sign vectors, A, B, C0 from the oracle's counter
+    hash in binary64: every entry of C enters, so a wrong tile or row block shows up however
+    few entries it holds."""
+    A, B, C0 = (oracle.init_matrix(seed, b, n, n) for b in (0, 1, 2))
+    x, y = rng.choice([-1.0, 1.0], size=n), rng.choice([-1.0, 1.0], size=n)
+    right = 1.5 * (A @ (B @ x)) + 0.5 * (C0 @ x)
+    left = 1.5 * ((y @ A) @ B) + 0.5 * (y @ C0)
+    C64 = C.astype(np.float64)
+    return max(float(np.linalg.norm(C64 @ x - right) / np.linalg.norm(right)),
+               float(np.linalg.norm(y @ C64 - left) / np.linalg.norm(left)))
+
+
+@pytest.mark.parametrize("kchunk,tile_cfg", [(0, 0), (512, 37), (512, 69)])
+def test_six_loop_n4096_fused_every_entry(gao, kchunk, tile_cfg):
+    """configs[1] in the launch configurations the bench times (BF16X6, the chain GEMM ->
+    scale-add -> transpose -> row sums -> norm in the GEMM epilogue; the library default and
+    the two configurations the autotuner has picked): every entry of C through Freivalds'
+    identities within 1e-6, D = C + 2A and E = D^T exactly, row sums in their fixed order
+    exactly, the norm within its rounding bound of binary64 over the device's own E."""
+    from test_gpu_rowsum import rowsum_fixed_order
+    n, seed = 4096, W.SEED_CONFIG1
+    prog = W.six_loop(n, seed, outputs=("C", "D", "E", "r", "f"))
+    p = gao.prog_from_workload(prog, gemm_prec=PREC["bf16x6"], kchunk=kchunk, tile_cfg=tile_cfg,
+                               fuse_chains=gao.FUSE_ON)
+    gao.prog_run(p, 0b111111)
+    C, D, E, r, f = (gao.prog_output(p, prog.index(nm)) for nm in ("C", "D", "E", "r", "f"))
+    gao.prog_destroy(p)
+    res = _freivalds_residual(C, seed, n, np.random.default_rng(tile_cfg))
+    print(f"n={n} kchunk={kchunk} tile_cfg={tile_cfg} Freivalds residual {res:.3e}")
+    assert res <= 1e-6, res
+    A = oracle.init_matrix(seed, 0, n, n).astype(np.float32)
+    assert np.array_equal(D, C + np.float32(2.0) * A)
+    assert np.array_equal(E, D.T)
+    assert np.array_equal(r, rowsum_fixed_order(E))
+    E64 = E.astype(np.float64)
+    fn = math.sqrt(float((E64 * E64).sum()))
+    assert abs(float(f[0, 0]) - fn) <= 2e-7 * fn
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "fp32_simt"])
+def test_full_size_n8192_every_entry(gao, prec):
+    """configs[2] size n = 8192: every entry of C through Freivalds' identities, within the
+    precision's gate (BF16X3 at its own 2e-5)."""
+    n, seed = 8192, W.SEED_CONFIG2
+    prog = W.six_loop(n, seed, outputs=("C",))
+    p = gao.prog_from_workload(prog, gemm_prec={"fp32_simt": 0, **PREC}[prec])
+    gao.prog_run(p, 0b111111)
+    C = gao.prog_output(p, prog.index("C"))
+    gao.prog_destroy(p)
+    res = _freivalds_residual(C, seed, n, np.random.default_rng(8192))
+    print(f"{prec} n={n} Freivalds residual {res:.3e}")
+    assert res <= {"fp32_simt": 1e-6, **TOL}[prec], res
+
+
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16"])
 def test_prog_autotune_keeps_parity(gao, prec):
     """The GA picks a tile configuration by measured GEMM time; every configuration in its

@@ -132,6 +132,44 @@ def test_gemm_sampled_entries_match_materialised():
     assert np.allclose(col, full[:, 7], rtol=1e-15, atol=0)
 
 
+def _freivalds(C, A, B, C0, alpha, beta, rng):
+    """Relative residuals of Freivalds' identities C x = alpha A (B x) + beta C0 x and
+    y^T C = alpha (y^T A) B + beta y^T C0 for random sign vectors x, y (Freivalds 1977): a
+    wrong entry, a transposed operand or a dropped term leaves a residual of its own size,
+    whatever the loop order that formed C."""
+    x = rng.choice([-1.0, 1.0], size=C.shape[1])
+    y = rng.choice([-1.0, 1.0], size=C.shape[0])
+    right = alpha * (A @ (B @ x)) + beta * (C0 @ x)
+    left = alpha * ((y @ A) @ B) + beta * (y @ C0)
+    return (float(np.linalg.norm(C @ x - right) / np.linalg.norm(right)),
+            float(np.linalg.norm(y @ C - left) / np.linalg.norm(left)))
+
+
+def test_gemm_freivalds_rectangular():
+    """The oracle GEMM on odd rectangular shapes with row-scaled A satisfies both Freivalds
+    identities to binary64 rounding; planted mistakes in its output (one entry off by 1e-9 of
+    the largest, the beta term dropped, the product transposed, the operands swapped) each
+    break them."""
+    rng = np.random.default_rng(5)
+    seed, M, N, K = 21, 517, 263, 389
+    A = oracle.init_matrix(seed, 0, M, K, rowscale=True)
+    B = oracle.init_matrix(seed, 1, K, N)
+    C0 = oracle.init_matrix(seed, 2, M, N)
+    C = oracle.gemm(A, B, C0, 1.5, 0.5)
+    assert max(_freivalds(C, A, B, C0, 1.5, 0.5, rng)) <= 1e-13
+    bad = C.copy()
+    bad[300, 17] += 1e-9 * np.abs(C).max()
+    assert max(_freivalds(bad, A, B, C0, 1.5, 0.5, rng)) > 1e-12
+    assert max(_freivalds(C - 0.5 * C0, A, B, C0, 1.5, 0.5, rng)) > 1e-10
+    # square operands, where a transposed product has the right shape
+    P, Q = oracle.init_matrix(seed, 3, 64, 64), oracle.init_matrix(seed, 4, 64, 64)
+    Z = np.zeros((64, 64))
+    Cpq = oracle.gemm(P, Q, Z, 1.0, 0.0)
+    assert max(_freivalds(Cpq, P, Q, Z, 1.0, 0.0, rng)) <= 1e-13
+    assert max(_freivalds(Cpq.T.copy(), P, Q, Z, 1.0, 0.0, rng)) > 1e-10
+    assert max(_freivalds(oracle.gemm(Q, P, Z, 1.0, 0.0), P, Q, Z, 1.0, 0.0, rng)) > 1e-10
+
+
 # ---- element-wise and reductions -----------------------------------------------
 
 def test_axpy_exact():
