@@ -215,10 +215,10 @@ def test_random_elementwise_chains_bit_identical(gao, seed):
 def test_full_size_twelve_loop_sampled(gao):
     """configs[4] size as bench.py runs it: m = 16384, k = 4096, BF16x3, all twelve loops on
     the GPU with the fused chains.  C on sampled entries against the oracle (entry by entry
-    from the counter hash); D = C + 2S on the samples; E = D^T everywhere; P from E and D
-    with the element-wise operations restated in binary32 on sampled rows; the row sums in
-    their fixed order on sampled rows; column maxima exact; norm and sum within their
-    reduction bounds."""
+    from the counter hash) and on every entry through Freivalds' identities; D = C + 2S,
+    E = D^T and P from E and D (the element-wise operations restated in binary32) exactly
+    everywhere; the row sums in their fixed order on every row; column maxima exact; norm and
+    sum within their reduction bounds."""
     import math
     from test_gpu_rowsum import rowsum_fixed_order
     m, k, seed = 16384, 4096, W.SEED_CONFIG4
@@ -236,16 +236,31 @@ def test_full_size_twelve_loop_sampled(gao):
     got = C[ii, jj].astype(np.float64)
     err = math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
     assert err <= TOL[2], err
-    S = np.array([oracle.init_value(seed, 3, int(i) * m + int(j)) for i, j in zip(ii, jj)])
-    assert np.array_equal(D[ii, jj], (C[ii, jj].astype(np.float64) + 2.0 * S).astype(np.float32))
+    # every entry of C: C x = 1.5 A (B x) + 0.5 C0 x and y^T C = 1.5 (y^T A) B + 0.5 y^T C0
+    # for random sign vectors (Freivalds 1977), operands in binary64 from the hash
+    A, B = oracle.init_matrix(seed, 0, m, k), oracle.init_matrix(seed, 1, k, m)
+    C0 = oracle.init_matrix(seed, 2, m, m)
+    x, y = rng.choice([-1.0, 1.0], size=m), rng.choice([-1.0, 1.0], size=m)
+    right, left = 1.5 * (A @ (B @ x)) + 0.5 * (C0 @ x), 1.5 * ((y @ A) @ B) + 0.5 * (y @ C0)
+    del A, B, C0
+    C64 = C.astype(np.float64)
+    res = max(float(np.linalg.norm(C64 @ x - right) / np.linalg.norm(right)),
+              float(np.linalg.norm(y @ C64 - left) / np.linalg.norm(left)))
+    del C64
+    print(f"twelve-loop m={m} k={k} Freivalds residual {res:.3e}")
+    assert res <= TOL[2], res
+    S = oracle.init_matrix(seed, 3, m, m).astype(np.float32)
+    assert np.array_equal(D, C + np.float32(2.0) * S)
+    del S
     assert np.array_equal(E, D.T)
-    rows = rng.integers(0, m, 16)
-    Er, Dr = E[rows], D[rows]
-    F = np.where(Er > 0, Er, np.float32(0))
-    G = Er + np.float32(-0.5) * F
+    F = np.where(E > 0, E, np.float32(0))
+    G = E + np.float32(-0.5) * F
+    del F
     H = G * G
-    assert np.array_equal(P[rows], H + np.float32(0.25) * Dr)
-    assert np.array_equal(out["r"][rows], rowsum_fixed_order(Er))
+    del G
+    assert np.array_equal(P, H + np.float32(0.25) * D)
+    del H
+    assert np.array_equal(out["r"], rowsum_fixed_order(E))
     assert np.array_equal(out["q"].ravel(), P.max(axis=0))
     E64 = E.astype(np.float64)
     fn = math.sqrt(float(np.einsum("ij,ij->", E64, E64)))
