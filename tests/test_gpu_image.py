@@ -165,7 +165,10 @@ def sample_m2(seed, h, w, i, j):
     return gx * gx + gy * gy, P
 
 
-def test_full_size_8192_sampled(gao):
+def test_full_size_8192(gao):
+    """The bench's frame, 8192 x 8192, every loop on the GPU: M2 on sampled pixels from their
+    5 x 5 neighbourhoods (corners and edges included), then on every pixel against the oracle's
+    binary64 program; the energy within its bound; the column maxima exact on the run's M2."""
     h = w = 8192
     prog = W.image_program(h, w, W.SEED_IMAGE, outputs=("M2", "e", "q"))
     p = gao.prog_from_workload(prog)
@@ -184,6 +187,13 @@ def test_full_size_8192_sampled(gao):
     M2d = M2.astype(np.float64)
     assert abs(e - M2d.sum()) <= SUM_REL * M2d.sum()
     assert np.array_equal(q.ravel(), M2.max(axis=0))
+    # every pixel against the oracle's binary64 program, within the propagated gamma_9 bound
+    ref = oracle.run_program(prog)
+    X = oracle.init_matrix(W.SEED_IMAGE, 0, h, w)
+    bound = m2_bound(X)
+    del X
+    assert np.all(np.abs(M2d - ref["M2"]) <= bound)
+    assert abs(e - ref["e"]) <= float(bound.sum()) + SUM_REL * abs(ref["e"])
 
 
 @pytest.mark.parametrize("outputs", [("M2", "e", "q"), ("gx", "sy", "M2", "e", "q")])
