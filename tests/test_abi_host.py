@@ -1,7 +1,7 @@
 """Host-side checks of the C ABI (no GPU needed): the library builds and loads, every
 entry point declared in include/gao.h is exported, struct layouts agree between the
 header and the binding, argument validation rejects malformed programs, the
-library fails loudly without a GA100-class device, and the C++ Simple GA
+library fails loudly without a CUDA device or without its own shared library, and the C++ Simple GA
 reproduces the oracle GA's trajectory draw for draw."""
 import ctypes
 import os
@@ -112,6 +112,18 @@ def test_valid_program_needs_the_gpu(gao):
     with pytest.raises(gao.GaoError) as ei:
         gao.prog_from_workload(prog)
     assert ei.value.status in (gao.GAO_ENODEV, gao.GAO_ECUDA)
+
+
+def test_missing_library_fails_loudly(gao, monkeypatch, tmp_path):
+    """Without libgao.so the first call raises and names the missing file: the binding has no
+    other implementation to fall back on."""
+    monkeypatch.setattr(gao, "LIB_PATH", str(tmp_path / "libgao.so"))
+    monkeypatch.setattr(gao, "_lib", None)
+    with pytest.raises(RuntimeError) as ei:
+        gao.prog_from_workload(W.six_loop(8, 1))
+    assert "libgao.so is missing" in str(ei.value) and "no fallback" in str(ei.value)
+    with pytest.raises(RuntimeError):
+        gao.lib()
 
 
 def _table_fn(t):
