@@ -214,10 +214,10 @@ def reference_arm(args, world, rank):
     import oracle
     n = args.n
     per_step = max(0.02, min(args.ref_target_s, 120.0 / (args.steps + args.warmup)))
-    r, B = oracle_calibrate(n, W.SEED_CONFIG1, per_step)
+    r, B = oracle_calibrate(n, W.SEED_N4096, per_step)
     secs = []
     for i in range(args.warmup + args.steps):
-        dt = oracle_rows(n, W.SEED_CONFIG1, r, B)
+        dt = oracle_rows(n, W.SEED_N4096, r, B)
         if i >= args.warmup:
             secs.append(dt)
     ms = statistics.median(secs) * 1e3
@@ -300,10 +300,10 @@ def our_arm(args, world, rank, local):
     stream = torch.cuda.Stream()
     n, prec = args.n, args.prec
     if args.workload == "twelve_loop":
-        prog = W.twelve_loop(args.m, args.k, W.SEED_CONFIG4 + rank, outputs=("C", "r", "f", "q", "s"))
+        prog = W.twelve_loop(args.m, args.k, W.SEED_TWELVE_LOOP + rank, outputs=("C", "r", "f", "q", "s"))
         wname = f"twelve_loop_m{args.m}_k{args.k}_all_gpu_{prec}"
     else:
-        prog = W.six_loop(n, W.SEED_CONFIG1 + rank, outputs=("C", "r", "f"))
+        prog = W.six_loop(n, W.SEED_N4096 + rank, outputs=("C", "r", "f"))
         wname = f"six_loop_n{n}_all_gpu_{prec}"
     flops = prog.gemm_flops()
     p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream, fuse_chains=args.fuse,
@@ -448,7 +448,7 @@ def our_arm(args, world, rank, local):
     # all-CPU time over the best gene's time
     search = None
     if args.search and rank == 0 and args.workload == "six_loop":
-        sp = W.six_loop(args.n, W.SEED_CONFIG1, outputs=("C", "r", "f"))
+        sp = W.six_loop(args.n, W.SEED_N4096, outputs=("C", "r", "f"))
         q = gao.prog_from_workload(sp, gemm_prec=PREC["fp32_simt"], stream=stream)
         gao.prog_run(q, 0b111111)
         t0 = time.perf_counter()
@@ -535,7 +535,7 @@ def our_arm(args, world, rank, local):
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
     cpu = None
     if args.cpu_baseline:
-        v, rows, secs, thr = oracle_sample(n, W.SEED_CONFIG1, args.ref_target_s)
+        v, rows, secs, thr = oracle_sample(n, W.SEED_N4096, args.ref_target_s)
         cpu = {"value": v / 1e12, "unit": "TFLOP/s", "cores": thr, "kind": "oracle",
                "sample": f"rows 0..{rows - 1} of the n={n} program in FP64 ({secs:.1f} s)"}
     line = {"metric": "gemm_program_tflops", "value": value, "unit": "TFLOP/s", "n_gpus": world,
@@ -720,7 +720,7 @@ def batch_arm(args, world, rank, local):
     import paper_1806_01430_gb300 as gao
     torch.cuda.set_device(local)
     sizes = W.batch_sizes(args.programs)
-    progs = [W.six_loop(n, W.SEED_CONFIG3_BASE + p, outputs=("f",)) for p, n in enumerate(sizes)]
+    progs = [W.six_loop(n, W.SEED_BATCH_BASE + p, outputs=("f",)) for p, n in enumerate(sizes)]
     handles = [gao.prog_from_workload(pr, gemm_prec=PREC[args.prec],
                                       fuse_chains=gao.FUSE_ON if args.fuse else gao.FUSE_OFF) for pr in progs]
     b = gao.batch_create(handles)

@@ -174,14 +174,14 @@ def test_batch_rejects_mixed_or_gene_fusion(gao):
 
 
 def test_batch_full_suite_sampled(gao):
-    """configs[3] at full size: the bench's 64-program suite (n log-uniform in [128, 2048]),
+    """The batched workload at full size: the bench's 64-program suite (n log-uniform in [128, 2048]),
     BF16x3 with fused chains, the all-GPU gene in one batched evaluation.  Every program: sampled
     C entries against the oracle (entry by entry from the counter hash), D = C + 2A and E = D^T
     exactly, row sums in their fixed order exactly, the norm within its rounding bound."""
     import math
     from test_gpu_rowsum import rowsum_fixed_order
     sizes = W.batch_sizes(64)
-    progs = [W.six_loop(n, W.SEED_CONFIG3_BASE + p, outputs=("C", "D", "E", "r", "f"))
+    progs = [W.six_loop(n, W.SEED_BATCH_BASE + p, outputs=("C", "D", "E", "r", "f"))
              for p, n in enumerate(sizes)]
     handles = [gao.prog_from_workload(pr, gemm_prec=2, fuse_chains=gao.FUSE_ON) for pr in progs]
     b = gao.batch_create(handles)

@@ -71,7 +71,7 @@ def test_fused_chain_only_when_all_on_gpu(gao):
 
 
 def test_fused_twelve_loop(gao):
-    prog = W.twelve_loop(200, 72, W.SEED_CONFIG4, outputs=("C", "D", "E", "r", "f", "P", "q", "s"))
+    prog = W.twelve_loop(200, 72, W.SEED_TWELVE_LOOP, outputs=("C", "D", "E", "r", "f", "P", "q", "s"))
     ref = oracle.run_program(prog)
     p = gao.prog_from_workload(prog, gemm_prec=3, fuse_chains=True)
     gao.prog_run(p, (1 << 12) - 1)
@@ -86,7 +86,7 @@ def test_fused_twelve_loop(gao):
 
 
 def test_fused_full_size_n4096(gao):
-    n, seed = 4096, W.SEED_CONFIG1
+    n, seed = 4096, W.SEED_N4096
     prog = W.six_loop(n, seed, outputs=("C", "D", "E", "r", "f"))
     res = {}
     for fuse in (False, True):
@@ -154,7 +154,7 @@ def test_fused_chain_in_copy_overlapped_gemm(gao, n, prec):
 def test_twelve_loop_elementwise_chain_bit_identical(gao):
     """ReLU, E - 0.5F, its square and P = H + 0.25D run as one element-wise pass (F, G, H
     never written): the same P, column maxima and sum as the separate loops."""
-    prog = W.twelve_loop(300, 96, W.SEED_CONFIG4, outputs=("C", "D", "E", "r", "P", "q", "s"))
+    prog = W.twelve_loop(300, 96, W.SEED_TWELVE_LOOP, outputs=("C", "D", "E", "r", "P", "q", "s"))
     res = {}
     for fuse in (False, True):
         p = gao.prog_from_workload(prog, gemm_prec=2, fuse_chains=fuse)
@@ -213,7 +213,7 @@ def test_random_elementwise_chains_bit_identical(gao, seed):
 
 
 def test_full_size_twelve_loop_sampled(gao):
-    """configs[4] size as bench.py runs it: m = 16384, k = 4096, BF16x3, all twelve loops on
+    """The twelve-loop program at the size bench.py runs it: m = 16384, k = 4096, BF16x3, all twelve loops on
     the GPU with the fused chains.  C on sampled entries against the oracle (entry by entry
     from the counter hash) and on every entry through Freivalds' identities; D = C + 2S,
     E = D^T and P from E and D (the element-wise operations restated in binary32) exactly
@@ -221,7 +221,7 @@ def test_full_size_twelve_loop_sampled(gao):
     sum within their reduction bounds."""
     import math
     from test_gpu_rowsum import rowsum_fixed_order
-    m, k, seed = 16384, 4096, W.SEED_CONFIG4
+    m, k, seed = 16384, 4096, W.SEED_TWELVE_LOOP
     prog = W.twelve_loop(m, k, seed, outputs=("C", "D", "E", "r", "f", "P", "q", "s"))
     p = gao.prog_from_workload(prog, gemm_prec=2, fuse_chains=gao.FUSE_ON)
     gao.prog_run(p, (1 << 12) - 1)

@@ -76,7 +76,7 @@ def check_internal_consistency(out):
 
 
 def test_config0_n256_all_gpu(gao):
-    prog = all_outputs(W.six_loop(256, W.SEED_CONFIG0))
+    prog = all_outputs(W.six_loop(256, W.SEED_N256))
     ref = oracle.run_program(prog)
     out, secs, stats = run_prog(gao, prog, 0b111111)
     check_six(out, ref)
@@ -139,7 +139,7 @@ def test_all_64_masks_invariance(gao):
 
 
 def test_row_scaled_init_bit_exact(gao):
-    prog = all_outputs(W.six_loop(200, W.SEED_CONFIG2_ROWS, rowscale_a=True))
+    prog = all_outputs(W.six_loop(200, W.SEED_N8192_ROWS, rowscale_a=True))
     ref = oracle.run_program(prog)
     for mask in (0b111111, 0b111110):
         out, _, _ = run_prog(gao, prog, mask)
@@ -149,7 +149,7 @@ def test_row_scaled_init_bit_exact(gao):
 
 @pytest.mark.parametrize("m,k", [(200, 72), (129, 33), (64, 256)])
 def test_twelve_loop_program(gao, m, k):
-    prog = all_outputs(W.twelve_loop(m, k, W.SEED_CONFIG4))
+    prog = all_outputs(W.twelve_loop(m, k, W.SEED_TWELVE_LOOP))
     ref = oracle.run_program(prog)
     rng = np.random.default_rng(m + k)
     for mask in [(1 << 12) - 1, 0] + [int(x) for x in rng.integers(0, 1 << 12, size=3)]:
@@ -265,7 +265,7 @@ def test_ga_evaluate_cache_and_ga_run_match_oracle(gao):
     """The GA over measured times: after every gene is measured once (cached), ga_run
     must follow the oracle GA's trajectory on that same time table, and the best gene
     must be the exhaustive optimum of the table."""
-    prog = W.six_loop(256, W.SEED_CONFIG1)
+    prog = W.six_loop(256, W.SEED_N4096)
     p = gao.prog_from_workload(prog)
     masks = list(range(64))
     fit, secs, hits = gao.ga_evaluate([p], masks)
@@ -282,9 +282,9 @@ def test_ga_evaluate_cache_and_ga_run_match_oracle(gao):
 
 
 def test_full_size_n4096_sampled(gao):
-    """configs[1] size: n = 4096, all-GPU gene, FP32 SIMT; sampled C entries against the
+    """The six-loop program at n = 4096, all-GPU gene, FP32 SIMT; sampled C entries against the
     oracle computed entry by entry from the counter hash, plus exact relations."""
-    n, seed = 4096, W.SEED_CONFIG1
+    n, seed = 4096, W.SEED_N4096
     prog = all_outputs(W.six_loop(n, seed))
     out, _, _ = run_prog(gao, prog, 0b111111)
     rng = np.random.default_rng(0)
@@ -324,12 +324,12 @@ def test_per_loop_transfer_mode(gao):
 
 
 def test_config1_all_64_genes_n4096(gao):
-    """configs[1]: the n = 4096 FP32 SIMT program under all 64 genes (CPU loops included).
+    """The n = 4096 FP32 SIMT program under all 64 genes (CPU loops included).
     Every gene is measured once (cache), the fastest gene places the GEMM on the GPU, the
     paper's GA finds the exhaustive optimum of the measured times, and the outputs of
     the all-CPU and of the best gene both match the oracle on sampled GEMM entries and in
     their exact relations."""
-    n, seed = 4096, W.SEED_CONFIG1
+    n, seed = 4096, W.SEED_N4096
     prog = W.six_loop(n, seed, outputs=("A", "C", "D", "E", "r", "f"))
     p = gao.prog_from_workload(prog, gemm_prec=0)
     fit, secs, hits = gao.ga_evaluate([p], list(range(64)))

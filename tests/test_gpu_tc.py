@@ -145,7 +145,7 @@ def test_tc_deterministic(gao):
 
 @pytest.mark.parametrize("prec", ["bf16", "bf16x3", "bf16x6", "fp8"])
 def test_six_loop_program_tc(gao, prec):
-    prog = W.six_loop(256, W.SEED_CONFIG0, outputs=("A", "C", "D", "E", "r", "f"))
+    prog = W.six_loop(256, W.SEED_N256, outputs=("A", "C", "D", "E", "r", "f"))
     ref = oracle.run_program(prog)
     p = gao.prog_from_workload(prog, gemm_prec=PREC[prec])
     for mask in (0b111111, 0b111110, 0b000010, 0b101011):
@@ -166,10 +166,10 @@ def _sampled_err(C, seed, n, rowscale, ii, jj, K=None):
     return math.sqrt(float(((got - want) ** 2).mean()) / float((want ** 2).mean()))
 
 
-@pytest.mark.parametrize("n,seed,rowscale", [(4096, W.SEED_CONFIG1, False), (8192, W.SEED_CONFIG2, False),
-                                             (8192, W.SEED_CONFIG2_ROWS, True)])
+@pytest.mark.parametrize("n,seed,rowscale", [(4096, W.SEED_N4096, False), (8192, W.SEED_N8192, False),
+                                             (8192, W.SEED_N8192_ROWS, True)])
 def test_full_size_bf16x6_sampled(gao, n, seed, rowscale):
-    """configs[1] and configs[2] sizes, all-GPU gene, BF16X6 at the library default
+    """n = 4096 and n = 8192 (uniform and row-scaled A), all-GPU gene, BF16X6 at the library default
     chunking: sampled C entries against the oracle (entry by entry from the hash)."""
     prog = W.six_loop(n, seed, rowscale_a=rowscale, outputs=("C",))
     p = gao.prog_from_workload(prog, gemm_prec=PREC["bf16x6"])
@@ -186,9 +186,9 @@ def test_full_size_bf16x6_sampled(gao, n, seed, rowscale):
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp32_simt", "fp8"])
-@pytest.mark.parametrize("seed,rowscale", [(W.SEED_CONFIG2, False), (W.SEED_CONFIG2_ROWS, True)])
+@pytest.mark.parametrize("seed,rowscale", [(W.SEED_N8192, False), (W.SEED_N8192_ROWS, True)])
 def test_full_size_n8192_every_precision(gao, prec, seed, rowscale):
-    """configs[2] at full size, n = 8192, for the other GEMM paths: uniform entries and rows of
+    """Full size, n = 8192, for the other GEMM paths: uniform entries and rows of
     A scaled by 2^e (e in [-10, 10]); sampled C entries against the oracle, each within its
     precision's gate (FP8: reported against 6e-2)."""
     n = 8192
@@ -217,8 +217,8 @@ def test_full_size_n8192_every_precision(gao, prec, seed, rowscale):
 
 
 def test_full_size_fp8_sampled(gao):
-    """configs[2] size n = 8192: FP8 e4m3 with 128-block scales, error reported against 6e-2."""
-    n, seed = 8192, W.SEED_CONFIG2
+    """n = 8192: FP8 e4m3 with 128-block scales, error reported against 6e-2."""
+    n, seed = 8192, W.SEED_N8192
     prog = W.six_loop(n, seed, outputs=("C",))
     p = gao.prog_from_workload(prog, gemm_prec=PREC["fp8"])
     gao.prog_run(p, 0b111111)
@@ -247,13 +247,13 @@ def _freivalds_residual(C, seed, n, rng):
 
 @pytest.mark.parametrize("kchunk,tile_cfg", [(0, 0), (512, 37), (512, 69)])
 def test_six_loop_n4096_fused_every_entry(gao, kchunk, tile_cfg):
-    """configs[1] in the launch configurations the bench times (BF16X6, the chain GEMM ->
+    """The six-loop program at n = 4096 in the launch configurations the bench times (BF16X6, the chain GEMM ->
     scale-add -> transpose -> row sums -> norm in the GEMM epilogue; the library default and
     the two configurations the autotuner has picked): every entry of C through Freivalds'
     identities within 1e-6, D = C + 2A and E = D^T exactly, row sums in their fixed order
     exactly, the norm within its rounding bound of binary64 over the device's own E."""
     from test_gpu_rowsum import rowsum_fixed_order
-    n, seed = 4096, W.SEED_CONFIG1
+    n, seed = 4096, W.SEED_N4096
     prog = W.six_loop(n, seed, outputs=("C", "D", "E", "r", "f"))
     p = gao.prog_from_workload(prog, gemm_prec=PREC["bf16x6"], kchunk=kchunk, tile_cfg=tile_cfg,
                                fuse_chains=gao.FUSE_ON)
@@ -274,9 +274,9 @@ def test_six_loop_n4096_fused_every_entry(gao, kchunk, tile_cfg):
 
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "fp32_simt"])
 def test_full_size_n8192_every_entry(gao, prec):
-    """configs[2] size n = 8192: every entry of C through Freivalds' identities, within the
+    """n = 8192: every entry of C through Freivalds' identities, within the
     precision's gate (BF16X3 at its own 2e-5)."""
-    n, seed = 8192, W.SEED_CONFIG2
+    n, seed = 8192, W.SEED_N8192
     prog = W.six_loop(n, seed, outputs=("C",))
     p = gao.prog_from_workload(prog, gemm_prec={"fp32_simt": 0, **PREC}[prec])
     gao.prog_run(p, 0b111111)

@@ -212,13 +212,13 @@ def analysis_program(m: int, n: int, seed: int, outputs=("C", "k", "s")) -> Prog
     return Program(f"analysis_{m}x{n}", bufs, loops, seed, {"m": m, "n": n})
 
 
-# ---- seeds of the benchmark configurations ----------------------------------
-SEED_CONFIG0 = 1000      # n = 256, all-GPU gene
-SEED_CONFIG1 = 1001      # n = 4096, all 64 genes
-SEED_CONFIG2 = 1002      # n = 8192 precision, U[-1,1)
-SEED_CONFIG2_ROWS = 1003  # n = 8192 precision, rows of A scaled by 2^e
-SEED_CONFIG3_BASE = 2000  # batch programs use 2000 + p
-SEED_CONFIG4 = 1005      # rectangular 16384 x 16384 x 4096, twelve loops
+# ---- seeds of the benchmark workloads -----------------------------------------
+SEED_N256 = 1000         # six-loop n = 256, all-GPU gene
+SEED_N4096 = 1001        # six-loop n = 4096, all 64 genes
+SEED_N8192 = 1002        # n = 8192 precision study, U[-1,1)
+SEED_N8192_ROWS = 1003   # n = 8192 precision study, rows of A scaled by 2^e
+SEED_BATCH_BASE = 2000   # batch programs use 2000 + p
+SEED_TWELVE_LOOP = 1005  # rectangular 16384 x 16384 x 4096, twelve loops
 SEED_IMAGE = 1006        # edge-detection image program
 SEED_IMAGE = 1006        # edge-detection image program
 
@@ -226,7 +226,7 @@ SEED_IMAGE = 1006        # edge-detection image program
 PAPER_GA = dict(pop=12, generations=12, pc=0.9, pm=0.05, elite=1, mutation=0)
 
 
-def batch_sizes(n_programs: int = 64, lo: int = 128, hi: int = 2048, base_seed: int = SEED_CONFIG3_BASE):
+def batch_sizes(n_programs: int = 64, lo: int = 128, hi: int = 2048, base_seed: int = SEED_BATCH_BASE):
     """Square sizes log-uniform in [lo, hi] for the batched-population workload;
     program p draws from numpy's PCG64 seeded with base_seed + p."""
     out = []
