@@ -135,9 +135,10 @@ typedef struct gao_opts {
     int32_t kchunk;          /* K elements per binary32 partial sum (0: library default; the
                                 FP32 SIMT kernel rounds it up to a multiple of 16)          */
     int32_t tile_cfg;        /* tensor-core tile configuration: bits 0-1 tile width (0 default,
-                                1 = 128, 2 = 256 columns), bit 2 L2 prefetch of the operand
-                                tiles 4 K blocks ahead (BF16 variants; changes no value),
-                                bits 4-7 log2 of the raster group (0: default 16);
+                                1 = 128, 2 = 256 columns; 256 only for plain BF16 without K
+                                chunks, every other variant uses 128), bit 2 L2 prefetch of
+                                the operand tiles 4 K blocks ahead (BF16 variants; changes no
+                                value), bits 4-7 log2 of the raster group (0: default 16);
                                 prog_autotune picks one                                     */
     int32_t cpu_threads;     /* OpenMP threads for CPU loops (0: all)                       */
     uint64_t seed;           /* seed of the INIT loop's counter hash                        */
