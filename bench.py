@@ -722,14 +722,19 @@ def batch_arm(args, world, rank, local):
     sizes = W.batch_sizes(args.programs)
     progs = [W.six_loop(n, W.SEED_BATCH_BASE + p, outputs=("f",)) for p, n in enumerate(sizes)]
     handles = [gao.prog_from_workload(pr, gemm_prec=PREC[args.prec],
-                                      fuse_chains=gao.FUSE_ON if args.fuse else gao.FUSE_OFF) for pr in progs]
+                                      fuse_chains=gao.FUSE_ON if args.fuse else gao.FUSE_OFF,
+                                      kchunk=args.kchunk, tile_cfg=args.tile_cfg) for pr in progs]
     b = gao.batch_create(handles)
     # warm-up: the all-GPU gene once (not cached afterwards: fresh batch for the timed GA)
     gao.batch_evaluate(b, [(1 << 6) - 1])
     st_w = gao.batch_stats(b)
     gao.batch_destroy(b)
     b = gao.batch_create(handles)
-    tune = gao.batch_autotune(b, pop=12, generations=12, seed=3) if args.autotune else None
+    # the GA autotuner picks the grouped GEMM's configuration unless one is given
+    tune = None
+    if args.autotune and args.prec != "fp32_simt" and args.kchunk == 0 and args.tile_cfg == 0:
+        tune = gao.batch_autotune(b, pop=12, generations=12, seed=3)
+    kc, tcfg = (tune["kchunk"], tune["tile_cfg"]) if tune else (args.kchunk, args.tile_cfg)
     torch.cuda.synchronize()
     barrier(world)
     with Clocks(local) as clk:
@@ -752,7 +757,8 @@ def batch_arm(args, world, rank, local):
             # against the kernel's own arithmetic peak, as in the single-program line
             gpk = peak * 2.0 if args.prec == "fp8" else peak / PRODUCTS[args.prec]
             roof = {"bound": "tensor", "achieved": gemm_tf, "peak": gpk, "unit": "TFLOP/s", "frac": gemm_tf / gpk,
-                    "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_grouped_batch{args.programs}_{args.prec}.md"),
+                    "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_grouped_batch{args.programs}_{args.prec}"
+                                                             f"{'_fused' if args.fuse else ''}_k{kc}_t{tcfg}.md"),
                     "kernel": "gemm_tc_grouped_kernel (one launch over all programs' tiles; phase time incl. splits)",
                     "peak_source": f"{pk['source']} bf16 sustained" +
                                    (" x2 (fp8 nominal ratio)" if args.prec == "fp8" else f" / {PRODUCTS[args.prec]}")}
@@ -762,7 +768,8 @@ def batch_arm(args, world, rank, local):
                 "data": "synthetic (seeded counter hash, U[-1,1))",
                 "config": {"workload": f"batch_{args.programs}_programs_n128_2048_pop{args.pop}_gen{args.generations}",
                            "programs": args.programs, "sizes_min_max": [min(sizes), max(sizes)], "pop": args.pop,
-                           "generations": args.generations, "gemm": args.prec, "fused_chain": bool(args.fuse)},
+                           "generations": args.generations, "gemm": args.prec, "fused_chain": bool(args.fuse),
+                           "kchunk": kc, "tile_cfg": tcfg},
                 "executed_genes": st["executed"], "served_genes": st["served"],
                 "executed_program_evals_per_s": st["executed"] * args.programs / max(st["exec_seconds"], 1e-9),
                 "best_gene": format(res.best_mask, "06b"), "best_s": res.best_s,
