@@ -214,10 +214,10 @@ def reference_arm(args, world, rank):
     import oracle
     n = args.n
     per_step = max(0.02, min(args.ref_target_s, 120.0 / (args.steps + args.warmup)))
-    r, B = oracle_calibrate(n, W.SEED_N4096, per_step)
+    r, B = oracle_calibrate(n, W.six_loop_seed(n), per_step)
     secs = []
     for i in range(args.warmup + args.steps):
-        dt = oracle_rows(n, W.SEED_N4096, r, B)
+        dt = oracle_rows(n, W.six_loop_seed(n), r, B)
         if i >= args.warmup:
             secs.append(dt)
     ms = statistics.median(secs) * 1e3
@@ -302,10 +302,15 @@ def our_arm(args, world, rank, local):
     if args.workload == "twelve_loop":
         prog = W.twelve_loop(args.m, args.k, W.SEED_TWELVE_LOOP + rank, outputs=("C", "r", "f", "q", "s"))
         wname = f"twelve_loop_m{args.m}_k{args.k}_all_gpu_{prec}"
+    elif args.workload == "gemm":
+        prog = W.gemm_only(n, W.six_loop_seed(n) + rank)
+        wname = f"gemm_n{n}_all_gpu_{prec}"
     else:
-        prog = W.six_loop(n, W.SEED_N4096 + rank, outputs=("C", "r", "f"))
+        prog = W.six_loop(n, W.six_loop_seed(n) + rank, outputs=("C", "r", "f"))
         wname = f"six_loop_n{n}_all_gpu_{prec}"
     flops = prog.gemm_flops()
+    # whether the GEMM runs with the chain in its epilogue (BF16 variants of programs that have one)
+    chained = bool(args.fuse) and prec in ("bf16", "bf16x3", "bf16x6") and args.workload != "gemm"
     p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream, fuse_chains=args.fuse,
                                kchunk=args.kchunk, tile_cfg=args.tile_cfg)
     # the library's GA autotuner picks the GEMM's tile configuration (raster group, K chunk,
@@ -373,7 +378,7 @@ def our_arm(args, world, rank, local):
 
     # the same program with the chain as separate kernels (GEMM kernel without the fused epilogue)
     unfused = None
-    if args.fuse and prec in ("bf16", "bf16x3", "bf16x6"):
+    if chained:
         q = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream, fuse_chains=False, kchunk=kc,
                                    tile_cfg=tcfg)
         for _ in range(3):
@@ -448,7 +453,7 @@ def our_arm(args, world, rank, local):
     # all-CPU time over the best gene's time
     search = None
     if args.search and rank == 0 and args.workload == "six_loop":
-        sp = W.six_loop(args.n, W.SEED_N4096, outputs=("C", "r", "f"))
+        sp = W.six_loop(args.n, W.six_loop_seed(args.n), outputs=("C", "r", "f"))
         q = gao.prog_from_workload(sp, gemm_prec=PREC["fp32_simt"], stream=stream)
         gao.prog_run(q, 0b111111)
         t0 = time.perf_counter()
@@ -517,9 +522,9 @@ def our_arm(args, world, rank, local):
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 # DRAM traffic depends on the tile configuration: only a capture of this one counts
                 "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_{prec}_{wname.split('_all_gpu')[0]}"
-                                                         f"{'_fused' if args.fuse else ''}_k{kc}_t{tcfg}.md"),
+                                                         f"{'_fused' if chained else ''}_k{kc}_t{tcfg}.md"),
                 "kernel": f"gemm_tc ({prec})" + (" with the fused scale-add / transpose / row-sum / norm epilogue"
-                                                  if args.fuse and prec != "fp8" else ""),
+                                                  if chained else ""),
                 "products": PRODUCTS[prec],
                 "hw_tflops": achieved * PRODUCTS[prec], "hw_frac": achieved * PRODUCTS[prec] / bf16,
                 "peak_source": f"{pk['source']} bf16 sustained" +
@@ -535,16 +540,16 @@ def our_arm(args, world, rank, local):
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
     cpu = None
     if args.cpu_baseline:
-        v, rows, secs, thr = oracle_sample(n, W.SEED_N4096, args.ref_target_s)
+        v, rows, secs, thr = oracle_sample(n, W.six_loop_seed(n), args.ref_target_s)
         cpu = {"value": v / 1e12, "unit": "TFLOP/s", "cores": thr, "kind": "oracle",
                "sample": f"rows 0..{rows - 1} of the n={n} program in FP64 ({secs:.1f} s)"}
     line = {"metric": "gemm_program_tflops", "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x6->f32" if prec == "bf16x6" else prec,
             "data": "synthetic (seeded counter hash, U[-1,1))",
-            "config": {"workload": wname, "n": n if args.workload == "six_loop" else None,
+            "config": {"workload": wname, "n": n if args.workload in ("six_loop", "gemm") else None,
                        "gene": format(mask, f"0{prog.n_loops}b"),
-                       "gemm": prec, "fused_chain": bool(args.fuse), "graph_replay": graph_replay,
+                       "gemm": prec, "fused_chain": chained, "graph_replay": graph_replay,
                        "kchunk": kc, "tile_cfg": tcfg,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "working set larger than the 129 MB L2 (no flush)"},
@@ -794,7 +799,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--workload", default="six_loop", choices=["six_loop", "twelve_loop", "batch", "image"])
+    ap.add_argument("--workload", default="six_loop", choices=["six_loop", "gemm", "twelve_loop", "batch", "image"])
     ap.add_argument("--h", type=int, default=8192)
     ap.add_argument("--w", type=int, default=8192)
     ap.add_argument("--programs", type=int, default=64)

@@ -299,6 +299,15 @@ def test_host_input_program_matches_six_loop():
     assert np.array_equal(out["C"], six["C"]) and np.array_equal(out["r"], six["r"]) and out["f"] == six["f"]
 
 
+
+def test_gemm_only_program_is_the_six_loop_gemm():
+    """The GEMM-only workload computes the six-loop program's C (same buffers and hash
+    streams), with and without row-scaled A."""
+    for n, seed, rows in ((16, 77, False), (33, 78, True)):
+        six = oracle.run_program(W.six_loop(n, seed, rowscale_a=rows, outputs=("C",)))
+        out = oracle.run_program(W.gemm_only(n, seed, rowscale_a=rows))
+        assert np.array_equal(out["C"], six["C"])
+
 # ---- stencil loops (second workload) ------------------------------------------------------
 
 def test_stencil_closed_forms():

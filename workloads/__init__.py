@@ -103,6 +103,15 @@ def six_loop(n: int, seed: int, alpha: float = 1.5, beta: float = 0.5, rowscale_
                                                           "rowscale_a": rowscale_a})
 
 
+def gemm_only(n: int, seed: int, alpha: float = 1.5, beta: float = 0.5, rowscale_a: bool = False) -> Program:
+    """The GEMM on its own, n x n: L0 init A, B, C; L1 C = alpha*A@B + beta*C (the first two
+    loops of the six-loop program, same buffers and hash streams)."""
+    bufs = [Buffer("A", n, n, F32, TEMP), Buffer("B", n, n, F32, TEMP), Buffer("C", n, n, F32, OUTPUT)]
+    loops = [Loop(INIT, [], [0, 1, 2], flags=1 if rowscale_a else 0),
+             Loop(GEMM, [0, 1, 2], [2], alpha=alpha, beta=beta)]
+    return Program(f"gemm_n{n}", bufs, loops, seed, {"n": n, "alpha": alpha, "beta": beta, "rowscale_a": rowscale_a})
+
+
 def host_input_program(n: int, seed: int, alpha: float = 1.5, beta: float = 0.5,
                        outputs=("r", "f")) -> Program:
     """The six-loop program without its INIT loop: A, B, C0 arrive from host memory
@@ -220,7 +229,13 @@ SEED_N8192_ROWS = 1003   # n = 8192 precision study, rows of A scaled by 2^e
 SEED_BATCH_BASE = 2000   # batch programs use 2000 + p
 SEED_TWELVE_LOOP = 1005  # rectangular 16384 x 16384 x 4096, twelve loops
 SEED_IMAGE = 1006        # edge-detection image program
-SEED_IMAGE = 1006        # edge-detection image program
+
+
+def six_loop_seed(n: int) -> int:
+    """Seed of the six-loop program at size n: the precision-study seed at n = 8192, the
+    n = 256 seed there, the n = 4096 seed otherwise."""
+    return {256: SEED_N256, 8192: SEED_N8192}.get(n, SEED_N4096)
+
 
 # GA parameters of the paper's evaluation (Sec. 5.1.2)
 PAPER_GA = dict(pop=12, generations=12, pc=0.9, pm=0.05, elite=1, mutation=0)
