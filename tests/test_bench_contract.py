@@ -23,3 +23,40 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_profile_traffic_only_for_the_current_kernel_source(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu summary only while that summary's
+    source hash matches the kernel file; a stale or incomplete summary gives null."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_1806_01430_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text("__global__ void k() {}\n")
+    sha = hashlib.sha256((csrc / "k.cu").read_bytes()).hexdigest()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    prof = tmp_path / "profiles" / "k.md"
+    prof.write_text(f"# k\n\ntraffic_bytes_per_launch: 123456\nsource_sha256: {sha}\n")
+    assert bench.profile_traffic("k.cu", "k.md") == 123456.0
+    (csrc / "k.cu").write_text("__global__ void k() { }\n")  # the kernel changed since the capture
+    assert bench.profile_traffic("k.cu", "k.md") is None
+    prof.write_text("# k\n\ntraffic_bytes_per_launch: 123456\n")  # no hash line
+    assert bench.profile_traffic("k.cu", "k.md") is None
+    assert bench.profile_traffic("k.cu", "missing.md") is None
+
+
+def test_committed_profiles_name_their_command_and_source():
+    """Every committed ncu summary gives the command that made it; those the bench reads carry
+    a traffic figure and the hash of the kernel source they were taken on."""
+    import re
+    pdir = os.path.join(ROOT, "profiles")
+    names = sorted(os.listdir(pdir))
+    assert names
+    for nm in names:
+        text = open(os.path.join(pdir, nm)).read()
+        assert nm.endswith((".md", ".txt")), nm
+        assert "ncu " in text and "--clock-control none" in text, nm
+        if re.search(r"traffic_bytes_per_launch:", text):
+            assert re.search(r"source_sha256:\s*[0-9a-f]{64}", text), nm
