@@ -469,7 +469,8 @@ def our_arm(args, world, rank, local):
                   "top5": [[format(int(m), "06b"), float(secs[m])] for m in order[:5]],
                   "paper_ga": {"best_gene": format(ga.best_mask, "06b"), "best_s": ga.best_s,
                                "found_exhaustive_best": bool(ga.best_mask == int(order[0])),
-                               "measured": ga.evaluations, "served": ga.cache_hits}}
+                               "measured": ga.evaluations, "served": ga.cache_hits,
+                               "generation_wall_s": [h["wall_s"] for h in ga.history]}}
         gao.prog_destroy(q)
 
     # the twelve-loop program's search: the paper's GA (M = T = 12) over the 12-bit gene with
@@ -485,7 +486,8 @@ def our_arm(args, world, rank, local):
         search = {"workload": wname.replace("all_gpu_", "") + "_paper_ga", "wall_s": t_search,
                   "measured": ga.evaluations, "served": ga.cache_hits,
                   "best_gene": format(ga.best_mask, "012b"), "best_s": ga.best_s, "all_gpu_s": all_gpu,
-                  "history_best_s": [h["best_s"] for h in ga.history]}
+                  "history_best_s": [h["best_s"] for h in ga.history],
+                  "history_wall_s": [h["wall_s"] for h in ga.history]}
         if prec != "fp8":
             q = gao.prog_from_workload(prog, gemm_prec=PREC["fp8"], stream=stream)
             for _ in range(3):
@@ -785,8 +787,8 @@ def batch_arm(args, world, rank, local):
                 "fused_gemm_phases": st["fused_phases"],
                 "autotune": tune, "roofline": roof,
                 "all_gpu_gene_warm_s": st_w["exec_seconds"],
-                "history": [{"best_s": h["best_s"], "evaluated": h["evaluated"], "hits": h["cache_hits"]}
-                            for h in res.history],
+                "history": [{"best_s": h["best_s"], "evaluated": h["evaluated"], "hits": h["cache_hits"],
+                             "wall_s": h["wall_s"]} for h in res.history],
                 "clocks": clk.summary(t0, t1)}
         print(json.dumps(line), flush=True)
     gao.batch_destroy(b)

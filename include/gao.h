@@ -274,6 +274,8 @@ typedef struct gao_ga_gen {
     double mean_s;      /* mean time over the generation's successful individuals       */
     int32_t evaluated;  /* genes measured for the first time in this generation         */
     int32_t cache_hits; /* individuals whose time came from the cache                   */
+    double wall_s;      /* wall-clock seconds of the generation: measuring its new genes
+                           and scoring it (host clock)                                  */
 } gao_ga_gen;
 
 typedef struct gao_ga_result {

@@ -72,7 +72,7 @@ class gao_ga_params(ctypes.Structure):
 
 class gao_ga_gen(ctypes.Structure):
     _fields_ = [("best_mask", ctypes.c_uint64), ("best_s", ctypes.c_double), ("mean_s", ctypes.c_double),
-                ("evaluated", ctypes.c_int32), ("cache_hits", ctypes.c_int32)]
+                ("evaluated", ctypes.c_int32), ("cache_hits", ctypes.c_int32), ("wall_s", ctypes.c_double)]
 
 
 class gao_ga_result(ctypes.Structure):

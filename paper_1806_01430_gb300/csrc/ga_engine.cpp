@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <functional>
 #include <unordered_map>
 #include <vector>
@@ -98,6 +99,7 @@ gao_status ga_core_pop(int n_genes, const gao_ga_params& p, const PopFn& eval, g
     res->cache_hits = 0;
     std::vector<double> times((size_t)M), fit((size_t)M);
     for (int g = 0; g < p.generations; ++g) {
+        const auto g_start = std::chrono::steady_clock::now();
         int ev = 0, hits = 0;
         // distinct genes not measured yet, in population order
         std::vector<uint64_t> fresh;
@@ -151,6 +153,7 @@ gao_status ga_core_pop(int n_genes, const gao_ga_params& p, const PopFn& eval, g
             h.mean_s = okn > 0.0 ? oksum / okn : INFINITY;
             h.evaluated = ev;
             h.cache_hits = hits;
+            h.wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - g_start).count();
         }
         if (g == p.generations - 1) break;
         std::vector<uint64_t> nxt;

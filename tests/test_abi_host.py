@@ -157,6 +157,7 @@ def test_c_ga_matches_oracle_ga(gao, case):
         assert h["best_mask"] == r.best_mask and h["best_s"] == r.best_s
         assert h["evaluated"] == r.evaluated and h["cache_hits"] == r.cache_hits
         assert (h["mean_s"] == r.mean_s) or (np.isinf(h["mean_s"]) and np.isinf(r.mean_s))
+        assert 0.0 <= h["wall_s"] < 60.0
 
 
 def test_c_ga_rejects_bad_params(gao):
