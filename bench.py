@@ -744,6 +744,7 @@ def batch_arm(args, world, rank, local):
     kc, tcfg = (tune["kchunk"], tune["tile_cfg"]) if tune else (args.kchunk, args.tile_cfg)
     torch.cuda.synchronize()
     barrier(world)
+    k_before = gao.batch_stats(b)["kernel_launches"]
     with Clocks(local) as clk:
         time.sleep(0.3)
         t0 = clk.mark()
@@ -752,6 +753,7 @@ def batch_arm(args, world, rank, local):
         t1 = clk.mark()
         time.sleep(0.25)
     st = gao.batch_stats(b)
+    launches = st["kernel_launches"] - k_before  # kernels of the genes the timed GA measured
     wall = allmax(world, t1 - t0)
     evals = allsum(world, args.pop * args.generations)
     gemm_tf = st["gemm_flops"] / (st["gemm_phase_ms"] / 1e3) / 1e12 if st["gemm_phase_ms"] > 0 else None
@@ -784,7 +786,7 @@ def batch_arm(args, world, rank, local):
                                  "effective_tflops": gemm_tf,
                                  "hw_frac": (gemm_tf * PRODUCTS[args.prec] / peak) if gemm_tf else None},
                 "launches_per_all_gpu_gene": st["launches_per_gene"], "graphs": st["graphs"],
-                "fused_gemm_phases": st["fused_phases"],
+                "fused_gemm_phases": st["fused_phases"], "gpu_launches": launches,
                 "autotune": tune, "roofline": roof,
                 "all_gpu_gene_warm_s": st_w["exec_seconds"],
                 "history": [{"best_s": h["best_s"], "evaluated": h["evaluated"], "hits": h["cache_hits"],

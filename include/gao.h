@@ -357,6 +357,8 @@ typedef struct gao_batch_stat {
     int32_t graphs;            /* phase graphs captured                                 */
     int32_t fused_phases;      /* GEMM phases run with the loop chain in the epilogue
                                   (programs created with GAO_FUSE_ON; genes measured)     */
+    int64_t kernel_launches;   /* kernels launched by the genes measured so far (the
+                                  kernels of every phase graph they launched)            */
 } gao_batch_stat;
 
 gao_status batch_create(gao_prog *const *progs, int n_progs, gao_batch **out);

@@ -89,7 +89,8 @@ class gao_autotune_result(ctypes.Structure):
 class gao_batch_stat(ctypes.Structure):
     _fields_ = [("executed", ctypes.c_int64), ("served", ctypes.c_int64), ("exec_seconds", ctypes.c_double),
                 ("gemm_phase_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double), ("gemm_tiles", ctypes.c_int32),
-                ("launches_per_gene", ctypes.c_int32), ("graphs", ctypes.c_int32), ("fused_phases", ctypes.c_int32)]
+                ("launches_per_gene", ctypes.c_int32), ("graphs", ctypes.c_int32), ("fused_phases", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 # every entry point of include/gao.h: name -> (restype, argtypes)

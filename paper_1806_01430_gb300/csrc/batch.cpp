@@ -43,6 +43,7 @@ struct gao_batch {
     cudaEvent_t fork = nullptr, g0 = nullptr, g1 = nullptr;
     std::vector<cudaGraph_t> graph;
     std::vector<cudaGraphExec_t> exec;
+    std::vector<int> phase_kernels;  // kernels in each loop's phase graph
     int gemm_loop = -1;
     bool grouped_gemm = false;
     int init_loop = -1;             // INIT loop run as one grouped launch over all programs
@@ -68,6 +69,7 @@ struct gao_batch {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t x = nullptr;
         TcProblem* d_probs = nullptr;
+        int kernels = 0;  // kernels in the graph
     };
     std::unordered_map<int, FusedPhase> fused;
 };
@@ -119,6 +121,7 @@ gao_status capture_phase(gao_batch* b, int li, std::vector<TcProblem>* probs) {
     const bool group_init = li == b->init_loop;  // one launch after the (empty) branches
     std::vector<size_t> order(b->progs.size());
     std::iota(order.begin(), order.end(), 0);
+    const int32_t kernels0 = b->stat.launches_per_gene;
     if (tc_gemm) {
         order = b->gemm_order;
         probs->assign(b->progs.size(), TcProblem{});
@@ -172,6 +175,7 @@ gao_status capture_phase(gao_batch* b, int li, std::vector<TcProblem>* probs) {
     }
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
     b->graph[(size_t)li] = g;
+    b->phase_kernels[(size_t)li] = b->stat.launches_per_gene - kernels0;
     GAO_CUDA_TRY(cudaGraphInstantiate(&b->exec[(size_t)li], g, 0));
     return GAO_OK;
 }
@@ -229,10 +233,13 @@ gao_status capture_fused(gao_batch* b, uint64_t mask, const Chain& ch, gao_batch
                        (float)L.alpha, L.ins[2] >= 0 ? (float)L.beta : 0.0f, p->opts.kchunk, p->opts.tile_cfg,
                        p->arena + p->lay.tc_off, p->lay.tc_bytes, b->side[j % kSide], &probs[j], &nl, &why, &fz[j]);
         if (e != cudaSuccess && !why.empty()) status = fail(GAO_EINVAL, "batch fused GEMM: " + why);
+        fp->kernels += nl;
     }
     if (e == cudaSuccess) e = join();
-    if (e == cudaSuccess && status == GAO_OK)
+    if (e == cudaSuccess && status == GAO_OK) {
         e = tc_launch_grouped(b->prec, chunked, fp->d_probs, (int)n, b->total_tiles, b->d_err, st);
+        fp->kernels += 1;
+    }
     if (e == cudaSuccess && status == GAO_OK) e = fork();
     for (size_t j = 0; j < n && e == cudaSuccess && status == GAO_OK; ++j) {
         gao_prog* p = b->progs[b->gemm_order[j]];
@@ -240,6 +247,7 @@ gao_status capture_fused(gao_batch* b, uint64_t mask, const Chain& ch, gao_batch
         const gao_buffer &A = p->bufs[(size_t)L.ins[0]].d, &B = p->bufs[(size_t)L.ins[1]].d;
         int nl = 0;
         e = tc_finalize_chain(b->prec, A.rows, B.cols, A.cols, p->arena + p->lay.tc_off, fz[j], b->side[j % kSide], &nl);
+        fp->kernels += nl;
     }
     if (e == cudaSuccess && status == GAO_OK) e = join();
     cudaGraph_t g = nullptr;
@@ -338,6 +346,7 @@ gao_status run_gene(gao_batch* b, uint64_t gene, double* seconds) {
             GAO_CUDA_TRY(cudaGraphLaunch(fp->x, b->st));
             GAO_CUDA_TRY(cudaEventRecord(b->g1, b->st));
             b->stat.fused_phases += 1;
+            b->stat.kernel_launches += fp->kernels;
             for (int j : {li, ch.axpy, ch.transpose, ch.rowsum, ch.frob}) {
                 if (j < 0) continue;
                 in_epilogue |= 1ULL << j;
@@ -353,6 +362,7 @@ gao_status run_gene(gao_batch* b, uint64_t gene, double* seconds) {
         if (gpu) {
             if (li == b->gemm_loop) GAO_CUDA_TRY(cudaEventRecord(b->g0, b->st));
             GAO_CUDA_TRY(cudaGraphLaunch(b->exec[(size_t)li], b->st));
+            b->stat.kernel_launches += b->phase_kernels[(size_t)li];
             if (li == b->gemm_loop) GAO_CUDA_TRY(cudaEventRecord(b->g1, b->st));
         } else {
             gao_status s = stream_wait(b->st, deadline, &timed_out);
@@ -478,6 +488,7 @@ extern "C" gao_status batch_create(gao_prog* const* progs, int n_progs, gao_batc
         return bail(cuda_fail(e, "batch error word"));
     *b->h_err = 0;
     b->graph.assign((size_t)b->n_loops, nullptr);
+    b->phase_kernels.assign((size_t)b->n_loops, 0);
     b->exec.assign((size_t)b->n_loops, nullptr);
     // everything the captures touch that is not a stream operation happens first
     for (auto* p : b->progs) {

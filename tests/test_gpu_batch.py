@@ -186,7 +186,11 @@ def test_batch_full_suite_sampled(gao):
     handles = [gao.prog_from_workload(pr, gemm_prec=2, fuse_chains=gao.FUSE_ON) for pr in progs]
     b = gao.batch_create(handles)
     fit, sec, hits = gao.batch_evaluate(b, [0b111111])
-    assert sec[0] > 0 and gao.batch_stats(b)["fused_phases"] == 1
+    st = gao.batch_stats(b)
+    assert sec[0] > 0 and st["fused_phases"] == 1
+    # one grouped INIT, two operand splits per program, one grouped GEMM, the row sums and the
+    # norm from each program's partials
+    assert st["kernel_launches"] == 1 + 2 * 64 + 1 + 2 * 64
     rng = np.random.default_rng(17)
     for prog, h in zip(progs, handles):
         n, seed = prog.buffers[0].rows, prog.seed
