@@ -60,3 +60,23 @@ def test_committed_profiles_name_their_command_and_source():
         assert "ncu " in text and "--clock-control none" in text, nm
         if re.search(r"traffic_bytes_per_launch:", text):
             assert re.search(r"source_sha256:\s*[0-9a-f]{64}", text), nm
+
+
+def test_clock_summary_of_samples_in_the_timed_window():
+    """The clock record beside a bench number: median SM clock, max clock and the throttle
+    reasons seen during [t0, t1] only, from nvidia-smi's CSV lines (malformed lines skipped)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.Clocks(0)
+    row = "0, {sm}, 2070, 900.5, 0x0, {hw}, Not Active, Not Active, {cap}"
+    c.lines = [(0.5, row.format(sm=1200, hw="Active", cap="Not Active")),   # before the window
+               (1.0, row.format(sm=1980, hw="Not Active", cap="Active")),
+               (1.2, row.format(sm=2010, hw="Not Active", cap="Not Active")),
+               (1.4, "0, [N/A], 2070"),                                      # malformed
+               (1.6, row.format(sm=1950, hw="Not Active", cap="Active")),
+               (3.0, row.format(sm=900, hw="Active", cap="Not Active"))]     # after it
+    s = c.summary(1.0, 2.0)
+    assert s == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    s_all = c.summary()
+    assert s_all["samples"] == 5 and s_all["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.Clocks(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
