@@ -80,3 +80,28 @@ def test_clock_summary_of_samples_in_the_timed_window():
     s_all = c.summary()
     assert s_all["samples"] == 5 and s_all["reasons"] == ["hw_slowdown", "sw_power_cap"]
     assert bench.Clocks(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_pass_bytes_match_the_per_element_figures():
+    """Algorithmic bytes of a memory-bound pass: INIT 4 B per element of each output, scale-add
+    12 B (two reads, one write), transpose 8 B, row sums 4 B per element plus the vector; a
+    fused pass does not count an intermediate that nothing after it reads."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    n = 96
+    six = W.six_loop(n, 1, outputs=("C", "r", "f"))
+    e = n * n
+    assert bench.group_bytes(six, [0]) == 3 * 4 * e            # A, B, C written
+    assert bench.group_bytes(six, [2]) == 12 * e                # D = C + 2A
+    assert bench.group_bytes(six, [3]) == 8 * e                 # E = D^T
+    assert bench.group_bytes(six, [4]) == 4 * e + 4 * n         # r = E 1
+    assert bench.group_bytes(six, [5]) == 4 * e + 8             # f = ||E|| (binary64 out)
+    assert bench.group_bytes(six, [2, 3]) == 12 * e             # D stays inside the pass
+    keep_d = W.six_loop(n, 1, outputs=("D", "r", "f"))
+    assert bench.group_bytes(keep_d, [2, 3]) == 16 * e          # unless D is an output
+    m, k = 64, 32
+    tw = W.twelve_loop(m, k, 2)
+    ew = [i for i, lp in enumerate(tw.loops) if lp.kind in (W.RELU, W.AXPY, W.SQUARE)][1:]  # L6..L9
+    # F = max(E,0), G = E - 0.5F, H = G.G, P = H + 0.25D as one pass: reads E and D, writes P
+    assert bench.group_bytes(tw, ew) == 3 * 4 * m * m
