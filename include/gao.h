@@ -311,8 +311,9 @@ gao_status ga_run_table(const double *times, int n_genes, const gao_ga_params *p
  * bit 4     L2 prefetch of the operand tiles (tile_cfg bit 2),
  * and fitness is (measured GEMM time)^(-1/2), the paper's fitness with the kernel time
  * as the benchmark (the GEMM with the loop chain in its epilogue when the program fuses
- * it under the all-GPU gene, since that is the kernel that runs).  The best configuration is written into the program's (or the
- * batch's) options and used from then on. */
+ * it under the all-GPU gene, since that is the kernel that runs).  The configuration in
+ * place is kept unless the GA's best beats it; the result is written into the program's
+ * (or the batch's) options and used from then on. */
 typedef struct gao_autotune_result {
     int32_t kchunk;     /* best K chunk (0: unchunked)                         */
     int32_t tile_cfg;   /* best tile configuration id (see gao_opts.tile_cfg)  */
