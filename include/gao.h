@@ -187,6 +187,18 @@ gao_status prog_create(const gao_loop *loops, int n_loops, const gao_buffer *buf
 /* Copy `bytes` of host data into INPUT buffer `buf` (its pinned host mirror). */
 gao_status prog_set_input(gao_prog *p, int buf, const void *host_src, uint64_t bytes);
 
+/* Bind caller host memory as buffer `buf`'s host copy (in place of the library's pinned
+ * mirror), so that a run copies an INPUT straight from the caller's array to the device
+ * and an OUTPUT straight back into the caller's array: no staging copy between the caller's
+ * data and the link.  `bytes` must equal the buffer's size.  Memory that is not page-locked
+ * already is registered with cudaHostRegister for as long as it stays bound.  An INPUT
+ * buffer counts as set from then on; the caller may rewrite the array between runs (the
+ * library reads it anew in every run that needs it on the device; the measurement cache
+ * is cleared by this call only).  host = NULL unbinds and returns to the library's mirror
+ * (an INPUT then needs prog_set_input again).  The memory must stay valid while bound;
+ * captured graphs are dropped (they name the old address). */
+gao_status prog_bind_host(gao_prog *p, int buf, void *host, uint64_t bytes);
+
 #define GAO_RUN_KEEP_DEVICE 1u /* leave OUTPUT buffers on the device (no final copy) */
 #define GAO_RUN_NO_GRAPH 2u    /* plain launches: no CUDA graph is captured or replayed       */
 #define GAO_RUN_NO_LOOP_TIMES 4u /* record no per-loop CUDA events (fewer nodes in a captured
@@ -383,6 +395,49 @@ typedef int (*gao_gene_eval_fn)(const uint64_t *genes, int n, double *seconds_ou
  * process per GPU, each measuring a share and exchanging the times. */
 gao_status ga_run_callback(int n_genes, const gao_ga_params *params, gao_gene_eval_fn eval, void *ctx,
                            gao_ga_result *result);
+
+/* ---- residual check of a GEMM on the GPU, in binary64 ------------------------ */
+
+/* Freivalds' check (Freivalds 1977) of C = alpha A B + beta C0, the GEMM loop of the
+ * paper's matrix-product benchmark (Sec. 5.1.1), without forming the product again: for
+ * vectors x (N entries) and y (M entries) the identities
+ *     C x   = alpha A (B x)   + beta C0 x          (right form)
+ *     y^T C = alpha (y^T A) B + beta y^T C0        (left form)
+ * hold exactly for the exact product, and every entry of C enters both.  With the
+ * residual vectors r = C x - beta C0 x - alpha A (B x) (M entries) and s = y^T C -
+ * beta y^T C0 - alpha (y^T A) B (N entries) and the reference sides f = alpha A (B x)
+ * + beta C0 x and g = alpha (y^T A) B + beta y^T C0:
+ *     right = ||r||_2 / ||f||_2,   right_inf = max|r_i| / max|f_i|,
+ *     left  = ||s||_2 / ||g||_2,   left_inf  = max|s_j| / max|g_j|,
+ * and right_argmax / left_argmax the first i (j) where |r_i| (|s_j|) is largest: a single
+ * wrong entry C_ij + d moves r_i by d x_j and s_j by d y_i and nothing else.  Every product
+ * and sum runs in binary64 on the GPU (the binary32 inputs are exact in binary64), in a
+ * fixed order (the same inputs give the same bits).  Random sign vectors x, y make the
+ * check miss an error only with probability <= 1/2 per form (Freivalds 1977). */
+typedef struct gao_residual {
+    double right, left;
+    double right_inf, left_inf;
+    int64_t right_argmax, left_argmax;
+} gao_residual;
+
+/* Device scratch bytes gao_gemm_residual needs for an M x N x K GEMM (M, N >= 1, K >= 0). */
+gao_status gao_gemm_residual_scratch(int64_t M, int64_t N, int64_t K, uint64_t *bytes);
+
+/* The check on caller-owned device data: A (M x K), B (K x N), C0 and C (M x N), row-major
+ * binary32; C0 may be NULL (beta term absent); x (N) and y (M) binary64 device vectors;
+ * scratch: device memory of at least gao_gemm_residual_scratch bytes, 256-byte aligned.
+ * r_out (M doubles) and s_out (N doubles) receive the residual vectors when not NULL
+ * (device memory).  Runs on `stream` (NULL: the legacy default stream) and waits for it;
+ * *out is filled on return.  Allocates nothing. */
+gao_status gao_gemm_residual(const float *A, const float *B, const float *C0, const float *C, int64_t M, int64_t N,
+                             int64_t K, double alpha, double beta, const double *x, const double *y, void *scratch,
+                             uint64_t scratch_bytes, double *r_out, double *s_out, gao_residual *out, void *stream);
+
+/* The same check of GEMM loop `loop` of a program after a run, on the program's own device
+ * buffers and scratch: x (N doubles) and y (M doubles) are host arrays.  The loop's C0
+ * must be a buffer of its own (a GEMM that writes C over C0 leaves nothing to check
+ * against: GAO_EINVAL); a buffer valid only on the host is copied to the device first. */
+gao_status prog_gemm_residual(gao_prog *p, int loop, const double *x, const double *y, gao_residual *out);
 
 /* ---- misc ------------------------------------------------------------------ */
 

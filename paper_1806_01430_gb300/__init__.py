@@ -93,6 +93,11 @@ class gao_batch_stat(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64)]
 
 
+class gao_residual(ctypes.Structure):
+    _fields_ = [("right", ctypes.c_double), ("left", ctypes.c_double), ("right_inf", ctypes.c_double),
+                ("left_inf", ctypes.c_double), ("right_argmax", ctypes.c_int64), ("left_argmax", ctypes.c_int64)]
+
+
 # every entry point of include/gao.h: name -> (restype, argtypes)
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -101,6 +106,7 @@ SIGNATURES = {
     "prog_create": (ctypes.c_int, [ctypes.POINTER(gao_loop), ctypes.c_int, ctypes.POINTER(gao_buffer), ctypes.c_int,
                                    ctypes.POINTER(gao_opts), ctypes.POINTER(_P)]),
     "prog_set_input": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint64]),
+    "prog_bind_host": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint64]),
     "prog_run": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]),
     "prog_output": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(gao_buffer)]),
     "prog_gene_length": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
@@ -125,6 +131,13 @@ SIGNATURES = {
     "gao_version": (ctypes.c_char_p, []),
     "gao_selftest_device_wait": (ctypes.c_int, [ctypes.c_double, _P]),
     "gao_colmax_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "gao_gemm_residual_scratch": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.POINTER(ctypes.c_uint64)]),
+    "gao_gemm_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_double, ctypes.c_double, _P, _P, _P, ctypes.c_uint64, _P, _P,
+                                         ctypes.POINTER(gao_residual), _P]),
+    "prog_gemm_residual": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(gao_residual)]),
     "batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
     "batch_evaluate": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -223,6 +236,7 @@ class Prog:
         self.buffers = list(buffers)
         self.loops = list(loops)
         self._arena = arena  # keeps a caller/torch arena alive
+        self.bound = {}  # host arrays bound with prog_bind_host, kept alive while bound
 
     @property
     def n_loops(self) -> int:
@@ -271,6 +285,24 @@ def prog_from_workload(program, **kw) -> Prog:
 def prog_set_input(p: Prog, buf: int, data: np.ndarray) -> None:
     a = np.ascontiguousarray(data, dtype=np.float64 if p.buffers[buf].dtype == F64 else np.float32)
     _check(lib().prog_set_input(p.handle, buf, a.ctypes.data_as(ctypes.c_void_p), a.nbytes), "prog_set_input")
+
+
+def prog_bind_host(p: Prog, buf: int, arr) -> None:
+    """Bind a caller array (numpy array or pinned torch CPU tensor; None unbinds) as buffer
+    ``buf``'s host copy: runs copy inputs from it and outputs into it directly.  The caller
+    keeps ``arr`` alive while it is bound (the Prog object holds a reference too)."""
+    if arr is None:
+        _check(lib().prog_bind_host(p.handle, buf, None, 0), "prog_bind_host")
+        p.bound.pop(buf, None)
+        return
+    if hasattr(arr, "data_ptr"):  # torch tensor
+        ptr, nbytes = arr.data_ptr(), arr.numel() * arr.element_size()
+    else:
+        if not (isinstance(arr, np.ndarray) and arr.flags["C_CONTIGUOUS"]):
+            raise ValueError("prog_bind_host needs a C-contiguous numpy array or a torch tensor")
+        ptr, nbytes = arr.ctypes.data, arr.nbytes
+    _check(lib().prog_bind_host(p.handle, buf, ctypes.c_void_p(ptr), ctypes.c_uint64(nbytes)), "prog_bind_host")
+    p.bound[buf] = arr
 
 
 def prog_gene_length(p: Prog) -> int:
@@ -366,6 +398,39 @@ def prog_device_ptr(p: Prog, buf: int) -> int:
     ptr = ctypes.c_void_p(None)
     _check(lib().prog_device_ptr(p.handle, buf, ctypes.byref(ptr)), "prog_device_ptr")
     return int(ptr.value or 0)
+
+
+def _residual_dict(r: "gao_residual") -> Dict:
+    return {k: getattr(r, k) for k, _ in gao_residual._fields_}
+
+
+def prog_gemm_residual(p: Prog, loop: int, x: np.ndarray, y: np.ndarray) -> Dict:
+    """Freivalds' residual check of GEMM loop ``loop`` after a run, in binary64 on the GPU;
+    x (N) and y (M) are host vectors.  Returns the gao_residual fields as a dict."""
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    ya = np.ascontiguousarray(y, dtype=np.float64)
+    r = gao_residual()
+    _check(lib().prog_gemm_residual(p.handle, int(loop), xa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    ya.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(r)),
+           "prog_gemm_residual")
+    return _residual_dict(r)
+
+
+def gao_gemm_residual_scratch(M: int, N: int, K: int) -> int:
+    b = ctypes.c_uint64(0)
+    _check(lib().gao_gemm_residual_scratch(int(M), int(N), int(K), ctypes.byref(b)), "gao_gemm_residual_scratch")
+    return int(b.value)
+
+
+def gao_gemm_residual(A: int, B: int, C0: int, C: int, M: int, N: int, K: int, alpha: float, beta: float, x: int,
+                      y: int, scratch: int, scratch_bytes: int, r_out: int = 0, s_out: int = 0, stream=None) -> Dict:
+    """The same check on caller-owned device memory (integer device addresses, 0 for NULL)."""
+    r = gao_residual()
+    vp = lambda a: ctypes.c_void_p(int(a) or None)
+    _check(lib().gao_gemm_residual(vp(A), vp(B), vp(C0), vp(C), int(M), int(N), int(K), float(alpha), float(beta),
+                                   vp(x), vp(y), vp(scratch), ctypes.c_uint64(int(scratch_bytes)), vp(r_out),
+                                   vp(s_out), ctypes.byref(r), _stream_handle(stream)), "gao_gemm_residual")
+    return _residual_dict(r)
 
 
 def prog_stats(p: Prog) -> List[Dict]:

@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libgao.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["kernels_ew.cu", "gemm_simt.cu", "gemm_tc.cu"]
+CU = ["kernels_ew.cu", "gemm_simt.cu", "gemm_tc.cu", "residual.cu"]
 CPP = ["runtime.cpp", "cpu_loops.cpp", "ga_engine.cpp", "batch.cpp"]
 
 

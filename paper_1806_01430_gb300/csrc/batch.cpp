@@ -667,6 +667,8 @@ extern "C" gao_status batch_autotune(gao_batch* b, const gao_ga_params* params, 
     auto time_cfg = [&](int kchunk, int tile_cfg, double* ms) -> gao_status {
         gao_status s = apply(kchunk, tile_cfg);
         if (s != GAO_OK) return s;
+        // a configuration whose launch raised the error word fails the tuning (GAO_EDEVICE)
+        GAO_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->st));
         std::vector<double> v;
         for (int r = 0; r < 4; ++r) {
             GAO_CUDA_TRY(cudaEventRecord(b->g0, b->st));
@@ -677,6 +679,12 @@ extern "C" gao_status batch_autotune(gao_batch* b, const gao_ga_params* params, 
             cudaEventElapsedTime(&t, b->g0, b->g1);
             if (r > 0) v.push_back(t);
         }
+        GAO_CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+        GAO_CUDA_TRY(cudaStreamSynchronize(b->st));
+        if (*b->h_err != 0)
+            return fail(GAO_EDEVICE, "batch autotune: the grouped GEMM raised device error " +
+                                         std::to_string(*b->h_err) + " under tile configuration " +
+                                         std::to_string(tile_cfg));
         std::sort(v.begin(), v.end());
         *ms = v[v.size() / 2];
         return GAO_OK;

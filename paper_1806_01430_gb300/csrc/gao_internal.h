@@ -73,6 +73,8 @@ __host__ __device__ inline uint32_t fmax_unkey(uint32_t key) {
 
 // ---- device info -------------------------------------------------------------
 int sm_count();
+// GAO_OK when the current device is an sm_103 GPU (its index in *dev_out when set).
+gao_status check_device(int* dev_out);
 
 // ---- kernel launchers (all asynchronous on `st`) -------------------------------
 struct ReduceScratch {
@@ -212,6 +214,18 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
                            int64_t N, int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
                            size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why,
                            const TcFuse* fuse = nullptr, const TcPart* part = nullptr);
+
+// Freivalds residual check of C = alpha A B + beta C0 in binary64 (C0 may be null):
+// kernels on st; the residual vectors go to rvec (M) / svec (N) when set; *norms_dev
+// receives the device address of 16 binary64 values (right form at 0..4: ||r||, ||f||,
+// max|r|, max|f|, argmax; left form at 8..12), which residual_from_norms turns into a
+// gao_residual once the stream has drained.
+size_t gemm_residual_scratch_bytes(int64_t M, int64_t N, int64_t K);
+cudaError_t launch_gemm_residual(const float* A, const float* B, const float* C0, const float* C, int64_t M,
+                                 int64_t N, int64_t K, double alpha, double beta, const double* x, const double* y,
+                                 void* scratch, double* rvec, double* svec, cudaStream_t st, int* launches,
+                                 const double** norms_dev);
+void residual_from_norms(const double* norms, gao_residual* out);
 
 // ---- CPU loops (binary32, OpenMP) ------------------------------------------------
 struct CpuCtx {

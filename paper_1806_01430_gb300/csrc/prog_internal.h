@@ -13,7 +13,9 @@ struct BufState {
     gao_buffer d;
     size_t bytes = 0;
     char* dev = nullptr;
-    void* host = nullptr;  // pinned mirror
+    void* host = nullptr;  // pinned host copy: the library's mirror, or caller memory bound to it
+    void* own_host = nullptr;  // the library's mirror (freed with the program)
+    bool registered = false;   // host is caller memory the library page-locked (cudaHostRegister)
     bool vh = false, vd = false;
     bool input_set = false;
 };
@@ -27,6 +29,7 @@ struct Layout {
     std::vector<size_t> buf_off;
     size_t err_off = 0, partial_off = 0, counter_off = 0, keys_off = 0, rowexp_off = 0, tc_off = 0;
     size_t tc_bytes = 0, keys_bytes = 0, rowexp_bytes = 0;
+    size_t resid_off = 0, resid_bytes = 0;  // GEMM residual check: x, y, then its scratch
     size_t total = 0;
 };
 

@@ -274,7 +274,7 @@ Layout plan(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bu
     off += align_up((size_t)reduce_blocks() * sizeof(double));
     L.counter_off = off;
     off += kAlign;
-    size_t keys = 1, rows = 1, tc = 0;
+    size_t keys = 1, rows = 1, tc = 0, resid = 0;
     for (int i = 0; i < n_loops; ++i) {
         const gao_loop& lp = loops[i];
         if (lp.kind == GAO_LOOP_COLMAX) keys = std::max(keys, (size_t)bufs[lp.ins[0]].cols * 4);
@@ -284,6 +284,11 @@ Layout plan(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bu
         if (lp.kind == GAO_LOOP_GEMM && o.gemm_prec != GAO_GEMM_FP32_SIMT) {
             const gao_buffer &A = bufs[lp.ins[0]], &B = bufs[lp.ins[1]];
             tc = std::max(tc, tc_scratch_bytes(o.gemm_prec, A.rows, B.cols, A.cols));
+        }
+        if (lp.kind == GAO_LOOP_GEMM && lp.ins[2] != lp.outs[0]) {  // a GEMM prog_gemm_residual can check
+            const gao_buffer &A = bufs[lp.ins[0]], &B = bufs[lp.ins[1]];
+            resid = std::max(resid, align_up((size_t)B.cols * 8) + align_up((size_t)A.rows * 8) +
+                                        gemm_residual_scratch_bytes(A.rows, B.cols, A.cols));
         }
     }
     L.keys_off = off;
@@ -296,6 +301,9 @@ Layout plan(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bu
     L.tc_off = off;
     L.tc_bytes = tc;
     off += align_up(tc, 1024);
+    L.resid_off = off;
+    L.resid_bytes = resid;
+    off += align_up(resid);
     L.total = off;
     return L;
 }
@@ -327,8 +335,10 @@ namespace {
 void free_prog(gao_prog* p) {
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st);
-    for (auto& b : p->bufs)
-        if (b.host) cudaFreeHost(b.host);
+    for (auto& b : p->bufs) {
+        if (b.registered) cudaHostUnregister(b.host);
+        if (b.own_host) cudaFreeHost(b.own_host);
+    }
     if (p->h_err) cudaFreeHost(p->h_err);
     if (p->cst) cudaStreamSynchronize(p->cst);
     drop_graphs(p);
@@ -408,9 +418,10 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
         B.d = bufs[b];
         B.bytes = (size_t)bufs[b].rows * (size_t)bufs[b].cols * elem_size(bufs[b].dtype);
         B.dev = p->arena + p->lay.buf_off[(size_t)b];
-        cudaError_t e = cudaMallocHost(&B.host, std::max<size_t>(B.bytes, 16));
+        cudaError_t e = cudaMallocHost(&B.own_host, std::max<size_t>(B.bytes, 16));
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost(buffer mirror)"));
-        memset(B.host, 0, std::max<size_t>(B.bytes, 16));
+        memset(B.own_host, 0, std::max<size_t>(B.bytes, 16));
+        B.host = B.own_host;
     }
     cudaError_t e = cudaMallocHost((void**)&p->h_err, 16);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost(err)"));
@@ -450,6 +461,47 @@ extern "C" gao_status prog_set_input(gao_prog* p, int buf, const void* host_src,
     memcpy(B.host, host_src, B.bytes);
     B.input_set = true;
     p->cache.clear();  // new data: earlier times no longer describe this program
+    return GAO_OK;
+}
+
+extern "C" gao_status prog_bind_host(gao_prog* p, int buf, void* host, uint64_t bytes) {
+    if (!p) return fail(GAO_EINVAL, "program is null");
+    if (buf < 0 || buf >= (int)p->bufs.size()) return fail(GAO_EINVAL, "no such buffer");
+    BufState& B = p->bufs[(size_t)buf];
+    if (host && bytes != B.bytes)
+        return fail(GAO_EINVAL, "buffer holds " + std::to_string(B.bytes) + " bytes, got " + std::to_string(bytes));
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    // no queued copy may still use the memory being replaced
+    if ((e = cudaStreamSynchronize(p->st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (p->cst && (e = cudaStreamSynchronize(p->cst)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (B.registered) {
+        cudaHostUnregister(B.host);
+        B.registered = false;
+    }
+    if (!host) {
+        B.host = B.own_host;  // back to the library's mirror (its contents are stale)
+        B.vh = false;
+        if (B.d.role == GAO_BUF_INPUT) B.input_set = false;
+    } else {
+        cudaPointerAttributes a{};
+        e = cudaPointerGetAttributes(&a, host);
+        if (e != cudaSuccess) cudaGetLastError();
+        bool pinned = e == cudaSuccess && a.type == cudaMemoryTypeHost;
+        if (!pinned && B.bytes) {
+            e = cudaHostRegister(host, B.bytes, cudaHostRegisterDefault);
+            if (e != cudaSuccess) {
+                B.host = B.own_host;
+                return cuda_fail(e, "cudaHostRegister(bound buffer)");
+            }
+            B.registered = true;
+        }
+        B.host = host;
+        if (B.d.role == GAO_BUF_INPUT) B.input_set = true;
+        B.vh = B.d.role == GAO_BUF_INPUT;
+    }
+    drop_graphs(p);   // captured copies name the old host address
+    p->cache.clear(); // new input data: earlier times no longer describe this program
     return GAO_OK;
 }
 
@@ -1482,6 +1534,46 @@ extern "C" gao_status prog_device_ptr(gao_prog* p, int buf, void** dev_ptr) {
     return GAO_OK;
 }
 
+extern "C" gao_status prog_gemm_residual(gao_prog* p, int loop, const double* x, const double* y,
+                                         gao_residual* out) {
+    if (!p || !x || !y || !out) return fail(GAO_EINVAL, "null argument");
+    if (loop < 0 || loop >= (int)p->loops.size() || p->loops[(size_t)loop].kind != GAO_LOOP_GEMM)
+        return fail(GAO_EINVAL, "loop " + std::to_string(loop) + " is not a GEMM loop");
+    const gao_loop& L = p->loops[(size_t)loop];
+    if (L.ins[2] == L.outs[0])
+        return fail(GAO_EINVAL, "the GEMM writes C over C0, so C0 is gone: give C0 a buffer of its own to check it");
+    if (p->lay.resid_bytes == 0) return fail(GAO_EINVAL, "program has no residual scratch for this loop");
+    const gao_buffer &A = p->bufs[(size_t)L.ins[0]].d, &B = p->bufs[(size_t)L.ins[1]].d;
+    const int64_t M = A.rows, K = A.cols, N = B.cols;
+    if (M < 1 || N < 1) return fail(GAO_EINVAL, "empty GEMM");
+    cudaError_t ce = cudaSetDevice(p->device);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
+    gao_status s = stream_wait(p->st, 0.0, nullptr);  // nothing of an earlier run still in flight
+    if (s != GAO_OK) return s;
+    p->dirty_stream = false;
+    RunCtx R{p, 0.0, false, CpuCtx{p->opts.cpu_threads, 0.0, false}, p->st, false};
+    gao_loop_stat dummy{};
+    for (int b : {L.ins[0], L.ins[1], L.ins[2], L.outs[0]})
+        if (b >= 0 && (s = make_valid(R, b, true, dummy)) != GAO_OK) return s;
+    char* base = p->arena + p->lay.resid_off;
+    const size_t xo = 0, yo = ((size_t)N * 8 + 255) / 256 * 256, so = yo + ((size_t)M * 8 + 255) / 256 * 256;
+    GAO_CUDA_TRY(cudaMemcpyAsync(base + xo, x, (size_t)N * 8, cudaMemcpyHostToDevice, p->st));
+    GAO_CUDA_TRY(cudaMemcpyAsync(base + yo, y, (size_t)M * 8, cudaMemcpyHostToDevice, p->st));
+    const float* c0 = L.ins[2] >= 0 ? (const float*)p->bufs[(size_t)L.ins[2]].dev : nullptr;
+    const double* nd = nullptr;
+    int launches = 0;
+    GAO_CUDA_TRY(launch_gemm_residual((const float*)p->bufs[(size_t)L.ins[0]].dev,
+                                      (const float*)p->bufs[(size_t)L.ins[1]].dev, c0,
+                                      (const float*)p->bufs[(size_t)L.outs[0]].dev, M, N, K, L.alpha,
+                                      c0 ? L.beta : 0.0, (const double*)(base + xo), (const double*)(base + yo),
+                                      base + so, nullptr, nullptr, p->st, &launches, &nd));
+    double h[16];
+    GAO_CUDA_TRY(cudaMemcpyAsync(h, nd, sizeof(h), cudaMemcpyDeviceToHost, p->st));
+    GAO_CUDA_TRY(cudaStreamSynchronize(p->st));
+    residual_from_norms(h, out);
+    return GAO_OK;
+}
+
 extern "C" gao_status prog_gene_length(const gao_prog* p, int* length) {
     if (!p || !length) return fail(GAO_EINVAL, "null argument");
     *length = gene_length(p);
@@ -1732,6 +1824,10 @@ extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, ga
     }
     auto time_cfg = [&](int kchunk, int tile_cfg, double* ms) -> gao_status {
         std::vector<double> v;
+        // a configuration whose kernel raised the error word (a bounded wait expired) fails
+        // the tuning with GAO_EDEVICE instead of being scored by its cut-off time
+        cudaError_t ze = cudaMemsetAsync(d_err, 0, sizeof(int), p->st);
+        if (ze != cudaSuccess) return cuda_fail(ze, "cudaMemsetAsync(err)");
         for (int r = 0; r < 6; ++r) {
             TcEvents ev{e0, e1, 0};
             std::string why;
@@ -1745,6 +1841,13 @@ extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, ga
             cudaEventElapsedTime(&t, e0, e1);
             if (r > 0) v.push_back(t);  // first launch warms up
         }
+        cudaError_t ce2 = cudaMemcpyAsync(p->h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, p->st);
+        if (ce2 == cudaSuccess) ce2 = cudaStreamSynchronize(p->st);
+        if (ce2 != cudaSuccess) return cuda_fail(ce2, "autotune error word");
+        if (*p->h_err != 0)
+            return fail(GAO_EDEVICE, "autotune: the GEMM raised device error " + std::to_string(*p->h_err) +
+                                         " under K chunk " + std::to_string(kchunk) + ", tile configuration " +
+                                         std::to_string(tile_cfg));
         std::sort(v.begin(), v.end());
         *ms = v[v.size() / 2];
         return GAO_OK;

@@ -50,7 +50,7 @@ def test_every_declared_symbol_is_exported(gao):
 
 def test_struct_layouts_match_header(gao, tmp_path):
     structs = ["gao_buffer", "gao_loop", "gao_opts", "gao_loop_stat", "gao_ga_params", "gao_ga_gen", "gao_ga_result",
-               "gao_batch_stat"]
+               "gao_batch_stat", "gao_residual"]
     src = tmp_path / "sz.c"
     src.write_text('#include "gao.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){\n' +
                    "".join(f'printf("%zu\\n", sizeof({s}));\n' for s in structs) +

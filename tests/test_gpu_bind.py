@@ -1,0 +1,103 @@
+"""Caller host memory bound as a program's host copy (prog_bind_host) through the C ABI.
+
+A run copies a bound INPUT straight from the caller's array and a bound OUTPUT straight
+back into the caller's array.  The results must carry the same bits as the same program
+fed through prog_set_input; rewriting the bound input between runs (also when the all-GPU
+gene replays a captured graph) must show in the next run's output; pageable numpy memory
+(registered by the library) and pinned torch memory both work; unbinding returns the
+buffer to the library's mirror, after which an INPUT needs prog_set_input again.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gao():
+    from paper_1806_01430_gb300 import _build
+    _build.build()
+    import paper_1806_01430_gb300 as g
+    return g
+
+
+def _inputs(n, seed):
+    return {nm: oracle.init_matrix(seed, b, n, n).astype(np.float32) for b, nm in enumerate(("A", "B", "C0"))}
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "fp32_simt"])
+def test_bound_inputs_and_output_match_set_input(gao, prec):
+    n, seed = 1000, 61
+    pr = {"bf16x6": gao.BF16X6, "fp32_simt": gao.FP32_SIMT}[prec]
+    hp = W.host_input_gemm(n)
+    ins = _inputs(n, seed)
+    ref = gao.prog_from_workload(hp, gemm_prec=pr)
+    for nm, v in ins.items():
+        gao.prog_set_input(ref, hp.index(nm), v)
+    gao.prog_run(ref, 1)
+    C_ref = gao.prog_output(ref, hp.index("C"))
+    gao.prog_destroy(ref)
+
+    p = gao.prog_from_workload(hp, gemm_prec=pr)
+    bound = {nm: v.copy() for nm, v in ins.items()}  # pageable numpy: the library registers it
+    C_out = np.zeros((n, n), dtype=np.float32)
+    for nm, v in bound.items():
+        gao.prog_bind_host(p, hp.index(nm), v)
+    gao.prog_bind_host(p, hp.index("C"), C_out)
+    for run in range(4):  # plain runs, then the captured graph's replays
+        C_out[:] = 0.0
+        gao.prog_run(p, 1)
+        assert np.array_equal(C_out.view(np.uint32), C_ref.view(np.uint32)), run
+        assert np.array_equal(gao.prog_output(p, hp.index("C")), C_ref)
+    assert gao.prog_graphs(p)[0] >= 1
+    st = gao.prog_stats(p)
+    assert sum(s["h2d_bytes"] for s in st) == 3 * n * n * 4
+    assert sum(s["d2h_bytes"] for s in st) == n * n * 4
+    # new data in the caller's array: the next run (a graph replay) reads it
+    bound["C0"][:] = np.float32(0.0)
+    gao.prog_run(p, 1)
+    A, B = ins["A"].astype(np.float64), ins["B"].astype(np.float64)
+    rng = np.random.default_rng(0)
+    ii, jj = rng.integers(0, n, 64), rng.integers(0, n, 64)
+    want = np.array([1.5 * (A[i] @ B[:, j]) for i, j in zip(ii, jj)])
+    got = C_out[ii, jj].astype(np.float64)
+    assert np.sqrt(((got - want) ** 2).mean() / (want ** 2).mean()) <= 1e-6
+    # unbinding an INPUT: it needs prog_set_input again
+    gao.prog_bind_host(p, hp.index("C0"), None)
+    with pytest.raises(gao.GaoError):
+        gao.prog_run(p, 1)
+    gao.prog_set_input(p, hp.index("C0"), ins["C0"])
+    gao.prog_run(p, 1)
+    assert np.array_equal(C_out.view(np.uint32), C_ref.view(np.uint32))
+    gao.prog_destroy(p)
+
+
+def test_bound_pinned_torch_tensors(gao):
+    torch = pytest.importorskip("torch")
+    n, seed = 777, 62
+    hp = W.host_input_gemm(n)
+    ins = _inputs(n, seed)
+    ref = oracle.run_program(hp, {k: v.astype(np.float64) for k, v in ins.items()})["C"]
+    p = gao.prog_from_workload(hp, gemm_prec=gao.BF16X6)
+    tens = {}
+    for nm, v in ins.items():
+        tens[nm] = torch.from_numpy(v).pin_memory()
+        gao.prog_bind_host(p, hp.index(nm), tens[nm])
+    tens["C"] = torch.zeros((n, n), dtype=torch.float32).pin_memory()
+    gao.prog_bind_host(p, hp.index("C"), tens["C"])
+    gao.prog_run(p, 1)
+    assert oracle.rel_err(tens["C"].numpy(), ref) <= 1e-6
+    gao.prog_destroy(p)
+
+
+def test_bind_rejects_wrong_size(gao):
+    hp = W.host_input_gemm(64)
+    p = gao.prog_from_workload(hp)
+    with pytest.raises(gao.GaoError):
+        gao.prog_bind_host(p, 0, np.zeros((64, 63), dtype=np.float32))
+    with pytest.raises(gao.GaoError):
+        gao.prog_bind_host(p, 9, np.zeros((64, 64), dtype=np.float32))
+    gao.prog_destroy(p)

@@ -79,9 +79,9 @@ def test_fused_twelve_loop(gao):
     assert [s["placement"] for s in st[:6]] == [1, 1, 2, 2, 2, 2]
     out = outputs(gao, p, prog)
     for nm in ("C", "D", "E", "P", "r", "q"):
-        assert oracle.rel_err(out[nm], ref[nm]) <= 2e-6, nm
+        assert oracle.rel_err(out[nm], ref[nm]) <= 1e-6, nm
     for nm in ("f", "s"):
-        assert abs(out[nm] - ref[nm]) <= 2e-6 * abs(ref[nm])
+        assert abs(out[nm] - ref[nm]) <= 1e-6 * abs(ref[nm])
     gao.prog_destroy(p)
 
 

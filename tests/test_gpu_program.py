@@ -154,11 +154,13 @@ def test_twelve_loop_program(gao, m, k):
     rng = np.random.default_rng(m + k)
     for mask in [(1 << 12) - 1, 0] + [int(x) for x in rng.integers(0, 1 << 12, size=3)]:
         out, _, stats = run_prog(gao, prog, mask)
+        # every output under the 1e-6 gate; H = G (.) G roughly doubles G's relative error
+        # (measured at most 5.5e-7 for H, P and q, against 3e-7 for C, D, E, F, G)
         for nm in ("C", "D", "E", "F", "G", "H", "P", "r", "q"):
             err = oracle.rel_err(out[nm], ref[nm])
-            assert err <= 2 * TOL, f"mask {mask:012b} {nm}: {err:.2e}"
+            assert err <= TOL, f"mask {mask:012b} {nm}: {err:.2e}"
         for nm in ("f", "s"):
-            assert abs(out[nm] - ref[nm]) <= 2 * TOL * abs(ref[nm]), nm
+            assert abs(out[nm] - ref[nm]) <= TOL * abs(ref[nm]), nm
         # exact relations among the run's own outputs
         E, F, G, H, P, D = (out[x] for x in "EFGHPD")
         assert np.array_equal(F, np.maximum(E, 0).astype(np.float32))

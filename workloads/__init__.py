@@ -104,12 +104,23 @@ def six_loop(n: int, seed: int, alpha: float = 1.5, beta: float = 0.5, rowscale_
 
 
 def gemm_only(n: int, seed: int, alpha: float = 1.5, beta: float = 0.5, rowscale_a: bool = False) -> Program:
-    """The GEMM on its own, n x n: L0 init A, B, C; L1 C = alpha*A@B + beta*C (the first two
-    loops of the six-loop program, same buffers and hash streams)."""
-    bufs = [Buffer("A", n, n, F32, TEMP), Buffer("B", n, n, F32, TEMP), Buffer("C", n, n, F32, OUTPUT)]
+    """The GEMM on its own, n x n: L0 init A, B, C0; L1 C = alpha*A@B + beta*C0 (the first
+    two loops of the six-loop program, same hash streams: buffer ids 0, 1, 2).  C is a
+    buffer of its own, so C0 is still there after a run for a residual check."""
+    bufs = [Buffer("A", n, n, F32, TEMP), Buffer("B", n, n, F32, TEMP), Buffer("C0", n, n, F32, TEMP),
+            Buffer("C", n, n, F32, OUTPUT)]
     loops = [Loop(INIT, [], [0, 1, 2], flags=1 if rowscale_a else 0),
-             Loop(GEMM, [0, 1, 2], [2], alpha=alpha, beta=beta)]
+             Loop(GEMM, [0, 1, 2], [3], alpha=alpha, beta=beta)]
     return Program(f"gemm_n{n}", bufs, loops, seed, {"n": n, "alpha": alpha, "beta": beta, "rowscale_a": rowscale_a})
+
+
+def host_input_gemm(n: int, alpha: float = 1.5, beta: float = 0.5) -> Program:
+    """The GEMM with its operands from host memory: A, B, C0 are INPUT buffers (copied to the
+    device inside every run), C the OUTPUT (copied back): L0 C = alpha*A@B + beta*C0."""
+    bufs = [Buffer("A", n, n, F32, INPUT), Buffer("B", n, n, F32, INPUT), Buffer("C0", n, n, F32, INPUT),
+            Buffer("C", n, n, F32, OUTPUT)]
+    return Program(f"host_input_gemm_n{n}", bufs, [Loop(GEMM, [0, 1, 2], [3], alpha=alpha, beta=beta)], 0,
+                   {"n": n, "alpha": alpha, "beta": beta})
 
 
 def host_input_program(n: int, seed: int, alpha: float = 1.5, beta: float = 0.5,
