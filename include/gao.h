@@ -345,44 +345,76 @@ gao_status prog_autotune(gao_prog *p, const gao_ga_params *params, gao_autotune_
  * loop kinds in the same order, same GEMM precision), e.g. six-loop programs of many
  * sizes.  A gene runs on every program at once, loop by loop: on the GPU all programs'
  * loop i is one CUDA graph launch (captured by batch_create; small kernels of different
- * programs run concurrently; a tensor-core GEMM loop is one grouped tcgen05 launch over
- * every program's tiles), on the host the programs' loops run one after another.  The
- * gene's time is the wall time of the whole suite, boundary copies included; a gene
- * measured before is served from the batch's cache (Sec. 4).  The programs stay owned
- * by the caller, must outlive the batch, and must not run elsewhere meanwhile; each
- * program's host and device buffers hold its results after a gene runs.  All programs
- * share one fuse_chains setting (GAO_FUSE_OFF or GAO_FUSE_ON; GAO_FUSE_GENE is refused:
- * batch genes are loop placements only).  With GAO_FUSE_ON a gene that puts a program's
- * GEMM -> scale-add -> transpose [-> row sums] [-> norm] chain on the GPU runs the chain
- * in the grouped launch's epilogue, bit-identical to the separate loops but the norm
- * (within its reduction's rounding).  The INIT loop (without row scaling) of all programs
- * is one grouped launch too. */
+ * programs run concurrently), a tensor-core GEMM loop is the captured operand splits plus
+ * ONE grouped persistent tcgen05 launch over every program's tiles, and on the host the
+ * programs' loops run one after another.  The gene's time is the wall time of the whole
+ * suite, boundary copies included; a gene measured before is served from the batch's
+ * cache (Sec. 4).  The programs stay owned by the caller, must outlive the batch, and must
+ * not run elsewhere meanwhile; each program's host and device buffers hold its results
+ * after a gene runs.  All programs share one fuse_chains setting (GAO_FUSE_OFF or
+ * GAO_FUSE_ON; GAO_FUSE_GENE is refused: batch genes are loop placements only).  With
+ * GAO_FUSE_ON a gene that puts a program's GEMM -> scale-add -> transpose [-> row sums]
+ * [-> norm] chain on the GPU runs the chain in the grouped launch's epilogue,
+ * bit-identical to the separate loops but the norm (within its reduction's rounding).
+ * The INIT loop (without row scaling) of all programs is one grouped launch too.
+ *
+ * Generations (batch_set_replicas with R > 1): the batch makes R - 1 copies of the suite
+ * (same loops, buffers, options and INPUT data; library-owned device memory), and the
+ * new genes of a population or GA generation are measured up to R at a time: gene r runs
+ * on copy r, the copies' phases go one after another on the batch's stream, and the
+ * GEMMs of every one of these genes that offloads the GEMM loop -- genes x programs --
+ * run in ONE grouped persistent launch.  Since genes share that launch, a gene's time is
+ * attributed: the device time of its own phase graphs and boundary copies (CUDA events
+ * around each), the span of its own problems inside the grouped launch (global-timer
+ * stamps taken by the kernel when it starts a tile's loads and when it has stored a tile),
+ * and the host wall time of its CPU loops.  That omits the host's launch overheads, so it
+ * reads a little below the gene's wall time when run alone; gene rankings carry over
+ * (measured, see the tests and the bench).  With a budget, a gene whose attributed time
+ * passes it is cut off at the budget.  Results land in the copy that ran the gene; the
+ * caller's programs hold the results of the first gene of the last group. */
 typedef struct gao_batch gao_batch;
 
 typedef struct gao_batch_stat {
     int64_t executed;          /* genes measured                                        */
     int64_t served;            /* genes answered from the cache                         */
     double exec_seconds;       /* host wall time spent measuring genes                  */
-    double gemm_phase_ms;      /* GPU time of the last GEMM phase (splits + grouped MMA) */
-    double gemm_flops;         /* 2MNK summed over the suite's GEMMs                    */
-    int32_t gemm_tiles;        /* CTAs of the grouped GEMM launch                       */
-    int32_t launches_per_gene; /* kernels in the captured graphs (all loops on the GPU) */
-    int32_t graphs;            /* phase graphs captured                                 */
+    double gemm_phase_ms;      /* GPU time of the last grouped GEMM launch (events around
+                                  it; the operand splits are part of the GEMM loop's
+                                  phase graph before it)                                 */
+    double gemm_flops;         /* 2MNK summed over that launch's GEMMs (over the suite
+                                  before any launch)                                     */
+    int32_t gemm_tiles;        /* CTAs (output tiles) of that launch                    */
+    int32_t launches_per_gene; /* kernels the all-GPU gene launches                     */
+    int32_t graphs;            /* phase graphs captured for the suite                   */
     int32_t fused_phases;      /* GEMM phases run with the loop chain in the epilogue
                                   (programs created with GAO_FUSE_ON; genes measured)     */
     int64_t kernel_launches;   /* kernels launched by the genes measured so far (the
-                                  kernels of every phase graph they launched)            */
+                                  kernels of every phase graph and grouped launch)       */
+    int64_t grouped_launches;  /* grouped GEMM launches made by measured genes          */
+    int64_t grouped_genes;     /* genes those launches served, summed: with generations
+                                  several genes share one launch                         */
+    int32_t replicas;          /* copies of the suite (genes measured together)         */
+    int32_t _pad;
 } gao_batch_stat;
 
 gao_status batch_create(gao_prog *const *progs, int n_progs, gao_batch **out);
+/* Measure up to `replicas` genes together (1: one gene at a time, wall-time measurement;
+ * > 1: generations share one grouped GEMM launch, attributed times, see above).  Makes or
+ * frees copies of the suite and clears the batch's cache.  At most 256. */
+gao_status batch_set_replicas(gao_batch *b, int replicas);
+/* Program `index` of copy `replica` of the suite (copy 0: the caller's own programs), a
+ * borrowed pointer valid until the copy is freed (batch_set_replicas, batch_destroy): the
+ * copy that ran a gene holds that gene's results (prog_output, prog_device_ptr). */
+gao_status batch_replica_prog(gao_batch *b, int replica, int index, gao_prog **out);
 /* Same contract as ga_evaluate, for genes over the whole suite. */
 gao_status batch_evaluate(gao_batch *b, const uint64_t *population, int pop, double *fitness_out,
                           double *seconds_out, int *cache_hits_out);
-/* The Simple GA with batched evaluation (same draws as ga_run). */
+/* The Simple GA with batched evaluation (same draws as ga_run); each generation's new
+ * genes are measured together when the batch has replicas. */
 gao_status batch_ga_run(gao_batch *b, const gao_ga_params *params, gao_ga_result *result);
 gao_status batch_stats(gao_batch *b, gao_batch_stat *out);
 /* Tunes the batch's grouped GEMM launch (same gene as prog_autotune; the time is the
- * GEMM phase of the whole suite). */
+ * GEMM loop's splits and grouped launch over the suite), for every copy of the suite. */
 gao_status batch_autotune(gao_batch *b, const gao_ga_params *params, gao_autotune_result *out);
 void batch_destroy(gao_batch *b);
 

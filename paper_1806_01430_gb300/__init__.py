@@ -90,7 +90,8 @@ class gao_batch_stat(ctypes.Structure):
     _fields_ = [("executed", ctypes.c_int64), ("served", ctypes.c_int64), ("exec_seconds", ctypes.c_double),
                 ("gemm_phase_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double), ("gemm_tiles", ctypes.c_int32),
                 ("launches_per_gene", ctypes.c_int32), ("graphs", ctypes.c_int32), ("fused_phases", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("grouped_launches", ctypes.c_int64),
+                ("grouped_genes", ctypes.c_int64), ("replicas", ctypes.c_int32), ("_pad", ctypes.c_int32)]
 
 
 class gao_residual(ctypes.Structure):
@@ -139,6 +140,8 @@ SIGNATURES = {
     "prog_gemm_residual": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(gao_residual)]),
     "batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "batch_set_replicas": (ctypes.c_int, [_P, ctypes.c_int]),
+    "batch_replica_prog": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
     "batch_evaluate": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int)]),
@@ -237,6 +240,7 @@ class Prog:
         self.loops = list(loops)
         self._arena = arena  # keeps a caller/torch arena alive
         self.bound = {}  # host arrays bound with prog_bind_host, kept alive while bound
+        self.owned = True  # False for a borrowed handle (a batch's copy of a program)
 
     @property
     def n_loops(self) -> int:
@@ -445,7 +449,8 @@ def prog_cache_clear(p: Prog) -> None:
 
 def prog_destroy(p: Prog) -> None:
     if p.handle is not None and p.handle.value:
-        lib().prog_destroy(p.handle)
+        if getattr(p, "owned", True):
+            lib().prog_destroy(p.handle)
         p.handle = ctypes.c_void_p(None)
 
 
@@ -547,10 +552,30 @@ class Batch:
             pass
 
 
-def batch_create(progs: Sequence[Prog]) -> Batch:
+def batch_create(progs: Sequence[Prog], replicas: int = 1) -> Batch:
+    """A batch over the suite `progs`; replicas > 1 measures a generation's new genes that
+    many at a time, their GEMMs in one grouped launch (batch_set_replicas)."""
     h = ctypes.c_void_p(None)
     _check(lib().batch_create(_handles(progs), len(progs), ctypes.byref(h)), "batch_create")
-    return Batch(h, progs)
+    b = Batch(h, progs)
+    if replicas != 1:
+        batch_set_replicas(b, replicas)
+    return b
+
+
+def batch_set_replicas(b: Batch, replicas: int) -> None:
+    _check(lib().batch_set_replicas(b.handle, int(replicas)), "batch_set_replicas")
+
+
+def batch_replica_prog(b: Batch, replica: int, index: int) -> Prog:
+    """Program `index` of copy `replica` of the suite (a borrowed handle: valid while the
+    copy exists; never destroyed through this object)."""
+    h = ctypes.c_void_p(None)
+    _check(lib().batch_replica_prog(b.handle, int(replica), int(index), ctypes.byref(h)), "batch_replica_prog")
+    src = b.progs[index]
+    q = Prog(h, src.buffers, src.loops)
+    q.owned = False
+    return q
 
 
 def batch_evaluate(b: Batch, population: Sequence[int]):

@@ -426,6 +426,7 @@ struct TileInfo {
     int Mp, Np, num_kb, chunk_kb, m0, n0;
     int pf_kb;  // operand tiles are pulled into L2 this many K blocks ahead of their loads (0: off)
     int tile0;  // launch index of the problem's first tile (its tiles are t - tile0 = 0, 1, ...)
+    unsigned long long *span_start, *span_end;  // the problem's time span in the launch (null: none)
 };
 
 // Tiles of one problem (kernel arguments).
@@ -448,6 +449,7 @@ struct OneProblem {
         ti.n0 = tn * bn;
         ti.pf_kb = pf_kb;
         ti.tile0 = 0;
+        ti.span_start = ti.span_end = nullptr;
     }
 };
 
@@ -478,6 +480,8 @@ struct ProblemTable {
         ti.n0 = tn * bn;
         ti.pf_kb = P->pf_kb;
         ti.tile0 = P->tile_start;
+        ti.span_start = P->span_start;
+        ti.span_end = P->span_end;
     }
 };
 
@@ -541,6 +545,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                 src.get(t, ti);
                 tma_prefetch_desc(ti.ta);
                 tma_prefetch_desc(ti.tb);
+                if (ti.span_start) atomicMin(ti.span_start, gtimer());
                 for (int kb = 0; kb < ti.num_kb; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -732,6 +737,10 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
                 if (lane == 0 && ep.frob_part) ep.frob_part[(int64_t)(t - ti.tile0) * kEpiWarps + ew] = sq;
+            }
+            if (ti.span_end && ok && lane == 0) {
+                __threadfence();  // the warp's stores of this tile come first
+                atomicMax(ti.span_end, gtimer());
             }
         }
     }
@@ -1349,19 +1358,7 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
         if (!make_map(&prob->ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;
         if (!make_map(&prob->tb, pb, Kp, (int64_t)P * Np, 128, false, why)) return cudaErrorInvalidValue;
         prob->ep = EpiArgs{C, C0, (int)M, (int)N, alpha, beta, vec, nullptr, nullptr, 0, 0};
-        if (fuse) {  // the chain's epilogue, partials in this problem's scratch (tile-local)
-            double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, M, N, K));
-            float* rpart = reinterpret_cast<float*>(reinterpret_cast<char*>(fpart) + tc_frob_partials_bytes(M, N));
-            prob->ep.X = fuse->X;
-            prob->ep.D = fuse->D;
-            prob->ep.E = fuse->E;
-            prob->ep.ldE = fuse->ldE > 0 ? fuse->ldE : M;
-            prob->ep.alpha2 = fuse->alpha2;
-            prob->ep.frob_part = fuse->frob_out ? fpart : nullptr;
-            prob->ep.rsum_part = fuse->rowsum_out ? rpart : nullptr;
-            prob->ep.ldR = N;
-            prob->ep.fuse = 1;
-        }
+        if (fuse) tc_attach_chain(prec, M, N, K, scratch, *fuse, prob);
         prob->Mp = (int)Mp;
         prob->Np = (int)Np;
         prob->num_kb = (int)(Kp / BK);
@@ -1372,6 +1369,21 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
     prob->group = tc_group_of(tile_cfg);
     prob->pf_kb = tc_prefetch_of(tile_cfg);
     return cudaSuccess;
+}
+
+void tc_attach_chain(int prec, int64_t M, int64_t N, int64_t K, void* scratch, const TcFuse& fuse, TcProblem* prob) {
+    // the chain's epilogue, partials in this problem's scratch (tile-local)
+    double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, M, N, K));
+    float* rpart = reinterpret_cast<float*>(reinterpret_cast<char*>(fpart) + tc_frob_partials_bytes(M, N));
+    prob->ep.X = fuse.X;
+    prob->ep.D = fuse.D;
+    prob->ep.E = fuse.E;
+    prob->ep.ldE = fuse.ldE > 0 ? fuse.ldE : M;
+    prob->ep.alpha2 = fuse.alpha2;
+    prob->ep.frob_part = fuse.frob_out ? fpart : nullptr;
+    prob->ep.rsum_part = fuse.rowsum_out ? rpart : nullptr;
+    prob->ep.ldR = N;
+    prob->ep.fuse = 1;
 }
 
 cudaError_t tc_finalize_chain(int prec, int64_t M, int64_t N, int64_t K, void* scratch, const TcFuse& fuse,

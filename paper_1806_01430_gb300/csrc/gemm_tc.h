@@ -53,6 +53,12 @@ struct alignas(128) TcProblem {
     CUtensorMap ta, tb;
     EpiArgs ep;
     int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, tile_start, group, pf_kb;
+    // Optional time span of the problem inside the launch (global timer, ns): the producer
+    // lowers *span_start to the time it starts loading each of the problem's tiles, every
+    // epilogue warp raises *span_end to the time it has stored its part of a tile.  Null:
+    // not recorded.  The caller sets *span_start = ~0 and *span_end = 0 before the launch.
+    unsigned long long* span_start;
+    unsigned long long* span_end;
 };
 
 // Raster group (row tiles per CTA group) encoded in bits 4-7 of a tile configuration
@@ -80,6 +86,11 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
                        int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
                        size_t scratch_bytes, cudaStream_t st, TcProblem* prob, int* launches, std::string* why,
                        const TcFuse* fuse = nullptr);
+
+// Turns a problem made by tc_prepare (same prec, shapes and scratch, BF16 variants) into
+// one whose epilogue runs the chain `fuse`, on the host: the operand planes are shared, so
+// the same split serves the plain problem and every chain shape.
+void tc_attach_chain(int prec, int64_t M, int64_t N, int64_t K, void* scratch, const TcFuse& fuse, TcProblem* prob);
 
 // After a grouped launch with a fused chain: the norm from the per-warp partials and the
 // row sums from the block values of one problem (kernels on st).

@@ -210,3 +210,118 @@ def test_batch_full_suite_sampled(gao):
     gao.batch_destroy(b)
     for h in handles:
         gao.prog_destroy(h)
+
+
+# ---- generations: several genes measured together, their GEMMs in one grouped launch -----------
+
+def _replica_outputs(gao, b, progs, r):
+    out = []
+    for i, prog in enumerate(progs):
+        h = gao.batch_replica_prog(b, r, i)
+        out.append({nm: gao.prog_output(h, prog.index(nm)).copy() for nm in ("C", "D", "E", "r", "f")})
+    return out
+
+
+@pytest.mark.parametrize("prec,fuse", [(3, False), (2, True), (1, True)])
+def test_generation_results_match_single_gene_runs(gao, prec, fuse):
+    """Four genes measured together (replicas = 4): every copy of the suite ends with its gene's
+    results, bit-identical to the same gene run alone (C, D, E, row sums; the norm within its
+    reduction's rounding when fused), and within the oracle's tolerance; the genes that offload
+    the GEMM share one grouped launch."""
+    sizes = [130, 64, 257, 200, 96, 300]
+    progs = [W.six_loop(n, 3300 + i, outputs=("C", "D", "E", "r", "f")) for i, n in enumerate(sizes)]
+    refs = [oracle.run_program(p) for p in progs]
+    fz = gao.FUSE_ON if fuse else gao.FUSE_OFF
+    genes = [0b111111, 0b000010, 0b111110, 0b001111, 0b110011, 0b011011, 0b111111 ^ 0b000100, 0b000000]
+    alone = {}
+    handles = [gao.prog_from_workload(p, gemm_prec=prec, fuse_chains=fz) for p in progs]
+    b = gao.batch_create(handles)
+    for g in genes:
+        gao.batch_evaluate(b, [g])
+        alone[g] = _replica_outputs(gao, b, progs, 0)
+    gao.batch_destroy(b)
+    for h in handles:
+        gao.prog_destroy(h)
+    handles = [gao.prog_from_workload(p, gemm_prec=prec, fuse_chains=fz) for p in progs]
+    b = gao.batch_create(handles, replicas=4)
+    st0 = gao.batch_stats(b)
+    assert st0["replicas"] == 4
+    for k in range(0, len(genes), 4):
+        group = genes[k:k + 4]
+        before = gao.batch_stats(b)
+        fit, sec, hits = gao.batch_evaluate(b, group)
+        after = gao.batch_stats(b)
+        assert hits == 0 and all(s > 0 for s in sec)
+        n_gemm = sum(1 for g in group if (g >> 1) & 1)
+        assert after["grouped_launches"] - before["grouped_launches"] == (1 if n_gemm else 0)
+        assert after["grouped_genes"] - before["grouped_genes"] == n_gemm
+        for r, g in enumerate(group):
+            got = _replica_outputs(gao, b, progs, r)
+            tol = TOL[prec] if (g >> 1) & 1 else 1e-6
+            for a, c, ref in zip(alone[g], got, refs):
+                for nm in ("C", "D", "E", "r"):
+                    assert np.array_equal(a[nm], c[nm]), (g, nm)
+                    assert oracle.rel_err(c[nm], ref[nm]) <= tol, (g, nm)
+                assert abs(float(a["f"][0, 0]) - float(c["f"][0, 0])) <= 2e-7 * abs(float(a["f"][0, 0]))
+    gao.batch_destroy(b)
+
+
+def test_generation_times_rank_like_single_runs(gao):
+    """All 64 genes timed one at a time (wall time of the suite) and 16 at a time (attributed
+    times in shared launches): the attributed times order the genes like the single runs."""
+    sizes = [256, 384, 192, 512, 128, 320]
+    progs = [W.six_loop(n, 3400 + i, outputs=("f",)) for i, n in enumerate(sizes)]
+    times = {}
+    for reps in (1, 16):
+        handles = [gao.prog_from_workload(p, gemm_prec=2) for p in progs]
+        b = gao.batch_create(handles, replicas=reps)
+        gao.batch_evaluate(b, [0b111111])  # warm
+        gao.batch_set_replicas(b, reps)    # clears the cache
+        st0 = gao.batch_stats(b)
+        _, sec, _ = gao.batch_evaluate(b, list(range(64)))
+        times[reps] = np.array(sec)
+        st = gao.batch_stats(b)
+        if reps == 16:  # four groups, each GEMM-offloading subset of 16 genes in one launch
+            assert st["grouped_launches"] - st0["grouped_launches"] == 4
+            assert st["grouped_genes"] - st0["grouped_genes"] == 32
+        gao.batch_destroy(b)
+        for h in handles:
+            gao.prog_destroy(h)
+    a, c = times[1], times[16]
+    ra, rc = np.argsort(np.argsort(a)), np.argsort(np.argsort(c))
+    rho = 1.0 - 6.0 * float(((ra - rc) ** 2).sum()) / (64 * (64 ** 2 - 1))
+    print(f"Spearman rank correlation, attributed vs single-run gene times: {rho:.3f}")
+    assert rho >= 0.9, rho
+    # the attributed time leaves out host overheads: never far above the wall time
+    assert np.all(c <= 1.5 * a + 1e-3)
+
+
+@pytest.mark.parametrize("reps", [1, 8])
+def test_generation_ga_follows_oracle_ga(gao, reps):
+    """With every gene's time in the batch's cache, the GA (per-generation evaluation) draws
+    exactly the oracle GA's populations, with or without replicas."""
+    sizes = [128, 192, 384, 160]
+    progs, handles = suite(gao, sizes, 2, outputs=("f",))
+    b = gao.batch_create(handles, replicas=reps)
+    _, secs, _ = gao.batch_evaluate(b, list(range(64)))
+    table = np.array(secs)
+    res = gao.batch_ga_run(b, pop=20, generations=20, pc=0.9, pm=0.05, seed=7)
+    ref = oga.run(lambda m: float(table[m]), 6, 20, 20, 0.9, 0.05, 7)
+    assert res.populations == ref.populations
+    assert res.best_mask == ref.best_mask and res.best_s == ref.best_s
+    gao.batch_destroy(b)
+
+
+def test_generation_ga_measures_each_generation_together(gao):
+    """batch_ga_run with replicas: the genes new in a generation are measured together, so the
+    grouped launches serve several genes each."""
+    sizes = W.batch_sizes(16)
+    progs = [W.six_loop(n, W.SEED_BATCH_BASE + p, outputs=("f",)) for p, n in enumerate(sizes)]
+    handles = [gao.prog_from_workload(pr, gemm_prec=2, fuse_chains=gao.FUSE_ON) for pr in progs]
+    b = gao.batch_create(handles, replicas=20)
+    res = gao.batch_ga_run(b, pop=20, generations=6, pc=0.9, pm=0.05, seed=7, timeout_s=-1.0)
+    st = gao.batch_stats(b)
+    assert res.evaluations >= 20 and st["grouped_launches"] >= 1
+    assert st["grouped_genes"] > 2 * st["grouped_launches"]
+    assert np.isfinite(res.best_s) and res.best_s > 0
+    gao.batch_destroy(b)
