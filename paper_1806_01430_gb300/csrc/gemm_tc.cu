@@ -9,10 +9,13 @@
 //   BF16X6  6 products: hi.hi + hi.mid + mid.hi + mid.mid + hi.lo + lo.hi
 //                                                       (three-term split, ~2^-24)
 // Each bfloat16 product is exact in binary32; the tensor core accumulates in binary32.
-//   FP8     e4m3 operands, one binary32 scale per (row of A, 128-element K block) and
-//           per (128-element K block, column of B), each the block's max |x| / 448;
-//           kind::f8f6f4 MMAs sum one K block in tensor memory and the epilogue adds
-//           sa * sb * block_sum into binary32 registers.
+//   FP8     e4m3 operands with one power-of-two scale per (row of A, 128-element K block)
+//           and per (128-element K block, column of B): 2^e with e the smallest exponent
+//           that brings the block's max |x| to <= 448.  The scales travel with the operand
+//           tiles (TMA) into tensor memory (tcgen05.cp), and block-scaled MMAs (kind::
+//           mxf8f6f4, UE8M0 scales, one per 32-element K step, the 128-block's scale
+//           repeated over its four steps) apply them inside the tensor core, so the binary32
+//           accumulator runs over all of K as for the bfloat16 products.
 // An optional K chunk restarts the tensor-memory accumulator every `kchunk`
 // elements and adds the chunk sums in registers, which bounds the growth of the
 // accumulation error with K.
@@ -163,14 +166,30 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
-__device__ __forceinline__ void mma_fp8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
+// Block-scaled e4m3 MMA: A's and B's UE8M0 scale factors are read from tensor memory at
+// sfa / sfb (the byte of each 32-bit word chosen by the instruction descriptor's scale ids).
+__device__ __forceinline__ void mma_mxf8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t sfa,
+                                         uint32_t sfb, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
         : "memory");
+}
+
+// 32 lanes x 128 bits from shared memory into tensor memory, the same rows into each of
+// the four lane quadrants (tcgen05.cp .32x128b.warpx4).
+__device__ __forceinline__ void tmem_cp_32x128b_x4(uint32_t taddr, uint64_t sdesc) {
+    asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
+// Contiguous bytes (16-byte aligned, a multiple of 16) global -> shared, completion on an mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"((uint64_t)src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -206,12 +225,27 @@ __host__ __device__ constexpr uint32_t idesc_bf16() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-// Instruction descriptor for kind::f8f6f4 with e4m3 A and B (format code 0 at bits
-// 7-9 and 10-12), binary32 D, both K-major.
+// Instruction descriptor for kind::mxf8f6f4 with e4m3 A and B (format code 0 at bits 7-9
+// and 10-12), both K-major, UE8M0 scale factors (bit 23), N >> 3 at bits 17-22, M >> 4 at
+// 24-28; the byte of the scale words used by this MMA (its 32-element K step within the
+// 128-element block) is B's scale id at bits 4-5 and A's at bits 29-30.
 template <int N_>
-__host__ __device__ constexpr uint32_t idesc_e4m3() {
-    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_mxf8(int kk) {
+    return ((uint32_t)kk << 4) | (1u << 23) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24) |
+           ((uint32_t)kk << 29);
 }
+
+// Shared-memory descriptor of a 32 x 16-byte block without swizzle (8-row core matrices of
+// 128 contiguous bytes, 128 bytes apart): the scale-factor block of a tcgen05.cp.
+__device__ __forceinline__ uint64_t plain_32x16_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(128 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// Scale factors of one 128-row (or 128-column) tile and one 128-element K block: 512 bytes
+// laid out as tcgen05.cp .32x128b.warpx4 puts them in tensor memory for the block-scaled
+// MMA: row r's scale for the K step kk at byte 16 (r % 32) + 4 (r / 32) + kk.
+constexpr int kSfBlock = 512;
 
 // Products (plane of A, plane of B); planes: 0 = hi, 1 = mid (x6) or lo (x3), 2 = lo.
 //   x1: hi.hi;  x3: hi.hi, hi.lo, lo.hi;  x6: hi.hi, hi.mid, mid.hi, mid.mid, hi.lo, lo.hi
@@ -392,17 +426,23 @@ struct TcCfg {
     // addition per K step instead of NPROD.
     static constexpr bool SPLIT = NPROD > 1;
     static constexpr int BUF_COLS = (SPLIT ? 2 : 1) * BN;  // columns of one accumulator buffer
-    static constexpr int COLS = ACC * BUF_COLS;
+    // FP8: each stage's scale factors in tensor memory after the accumulators, 4 columns
+    // for A's 128 rows and BN / 32 for B's BN columns
+    static constexpr int SF_COLS = FP8 ? 4 + BN / 32 : 0;
+    static constexpr int SF_COL0 = ACC * BUF_COLS;
+    static constexpr int COLS = ACC * BUF_COLS + STAGES * SF_COLS;
     static constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256
                                                                                                               : 512;
     static constexpr uint32_t NBARS = 2 * STAGES + 2 * ACC + 1;
     static constexpr uint32_t STG = kEpiWarps * kStgBytes;  // epilogue staging blocks
-    static constexpr size_t SMEM = 1024 /*align slack*/ + (size_t)STAGES * STAGE + STG + 8 * NBARS + 16;
+    // FP8: scale-factor blocks of every stage (A's, then BN / 128 of B's), after the tiles
+    static constexpr uint32_t SF_STAGE = FP8 ? (uint32_t)kSfBlock * (1 + BN / 128) : 0;
+    static constexpr size_t SMEM = 1024 /*align slack*/ + (size_t)STAGES * (STAGE + SF_STAGE) + STG + 8 * NBARS + 16;
     static_assert(SMEM <= 232448, "shared memory per CTA");
     static_assert(COLS <= 512, "accumulators exceed tensor memory");
     static_assert(BN % 64 == 0 && BN >= 64 && BN <= 256, "BN");
     static_assert(!CHUNKED || BN <= 128, "chunked sums live in registers: BN <= 128");
-    static_assert(!FP8 || (CHUNKED && NPROD == 1 && PA == 1 && PB == 1), "FP8 runs one plane, chunked per K block");
+    static_assert(!FP8 || (!CHUNKED && NPROD == 1 && PA == 1 && PB == 1), "FP8 runs one plane, scaled in the MMA");
 };
 
 // One 128 x BN output tile (row tile tm, column tile tn) of one problem.
@@ -492,15 +532,16 @@ struct ProblemTable {
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8, class Src>
 __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_tiles, int* err) {
     using Cfg = TcCfg<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>;
-    constexpr uint32_t IDESC = FP8 ? idesc_e4m3<BN>() : idesc_bf16<BN>();
+    constexpr uint32_t IDESC = idesc_bf16<BN>();
     constexpr int KBE = FP8 ? BK8 : BK;  // elements per K block
     constexpr int ACC = Cfg::ACC;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const uint32_t tiles = smem_u32(smem);
-    float* stg_all = reinterpret_cast<float*>(smem + (size_t)STAGES * Cfg::STAGE);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)STAGES * Cfg::STAGE + Cfg::STG);
+    const uint32_t sf_smem = tiles + (uint32_t)STAGES * Cfg::STAGE;  // FP8 scale-factor blocks
+    float* stg_all = reinterpret_cast<float*>(smem + (size_t)STAGES * (Cfg::STAGE + Cfg::SF_STAGE));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)STAGES * (Cfg::STAGE + Cfg::SF_STAGE) + Cfg::STG);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + Cfg::NBARS);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const uint32_t bar0 = smem_u32(bars);
@@ -563,8 +604,19 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(full_bar(s), Cfg::STAGE);
+                    mbar_expect_tx(full_bar(s), Cfg::STAGE + Cfg::SF_STAGE);
                     const uint32_t st = tiles + (uint32_t)s * Cfg::STAGE;
+                    if constexpr (FP8) {  // this K block's scale factors of the A and B tiles
+                        const uint8_t* sfa = reinterpret_cast<const uint8_t*>(ti.ep.sa);
+                        const uint8_t* sfb = reinterpret_cast<const uint8_t*>(ti.ep.sb);
+                        const uint32_t sd = sf_smem + (uint32_t)s * Cfg::SF_STAGE;
+                        bulk_load(sd, sfa + ((int64_t)(ti.m0 / BM) * ti.num_kb + kb) * kSfBlock, kSfBlock, full_bar(s));
+#pragma unroll
+                        for (int h = 0; h < BN / 128; ++h)
+                            bulk_load(sd + (uint32_t)(1 + h) * kSfBlock,
+                                      sfb + ((int64_t)(ti.n0 / 128 + h) * ti.num_kb + kb) * kSfBlock, kSfBlock,
+                                      full_bar(s));
+                    }
 #pragma unroll
                     for (int p = 0; p < PA; ++p)
                         tma_load_2d(st + (uint32_t)p * Cfg::A_TILE, ti.ta, kb * KBE, p * ti.Mp + ti.m0, full_bar(s));
@@ -616,6 +668,18 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                         tc_fence_after();
                         const uint32_t a_base = tiles + (uint32_t)s * Cfg::STAGE;
                         const uint32_t b_base = a_base + PA * Cfg::A_TILE;
+                        // FP8: this stage's scale factors into its own tensor-memory columns
+                        // (free again: the MMAs that read them last released the stage)
+                        const uint32_t sfa_t = tmem + (uint32_t)(Cfg::SF_COL0 + s * Cfg::SF_COLS);
+                        const uint32_t sfb_t = sfa_t + 4u;
+                        if constexpr (FP8) {
+                            const uint32_t sd = sf_smem + (uint32_t)s * Cfg::SF_STAGE;
+                            tmem_cp_32x128b_x4(sfa_t, plain_32x16_desc(sd));
+#pragma unroll
+                            for (int h = 0; h < BN / 128; ++h)
+                                tmem_cp_32x128b_x4(sfb_t + 4u * (uint32_t)h,
+                                                   plain_32x16_desc(sd + (uint32_t)(1 + h) * kSfBlock));
+                        }
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {  // 4 MMA K steps of 32 bytes per 128-byte block
 #pragma unroll
@@ -628,7 +692,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                                 const bool first = kb == kb0 && kk == 0 && (pr == 0 || (Cfg::SPLIT && pr == 1));
                                 const uint32_t dd = d + ((Cfg::SPLIT && pr > 0) ? (uint32_t)BN : 0u);
                                 if constexpr (FP8)
-                                    mma_fp8(dd, ad, bd, IDESC, first ? 0u : 1u);
+                                    mma_mxf8(dd, ad, bd, idesc_mxf8<BN>(kk), sfa_t, sfb_t, first ? 0u : 1u);
                                 else
                                     mma_bf16(dd, ad, bd, IDESC, first ? 0u : 1u);
                             }
@@ -702,20 +766,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] += __uint_as_float(r[i]);
                     }
-                    if constexpr (FP8) {
-                        // chunk c is K block c: scale by sa(row, c) * sb(c, column)
-                        const float sa = grow < ep.M ? ep.sa[grow * (int64_t)ep.kbs + c] : 0.0f;
-                        const float4* sb4 =
-                            reinterpret_cast<const float4*>(ep.sb + (int64_t)c * ep.sb_ld + n0 + colbase + g * 32);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const float4 b = sb4[j];
-                            sum[g * 32 + 4 * j + 0] = fmaf(sa * b.x, v[4 * j + 0], sum[g * 32 + 4 * j + 0]);
-                            sum[g * 32 + 4 * j + 1] = fmaf(sa * b.y, v[4 * j + 1], sum[g * 32 + 4 * j + 1]);
-                            sum[g * 32 + 4 * j + 2] = fmaf(sa * b.z, v[4 * j + 2], sum[g * 32 + 4 * j + 2]);
-                            sum[g * 32 + 4 * j + 3] = fmaf(sa * b.w, v[4 * j + 3], sum[g * 32 + 4 * j + 3]);
-                        }
-                    } else if constexpr (CHUNKED) {
+                    if constexpr (CHUNKED) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) sum[g * 32 + i] += v[i];
                     } else {
@@ -902,21 +953,37 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const float* __restrict
 
 // ---- FP8 quantise kernels -----------------------------------------------------------------------
 
-// e4m3 with one scale per 128-element block: s = max|x| / 448 (1 for an all-zero
-// block), q = e4m3(x / s) rounded to nearest, saturating.
-__device__ __forceinline__ float fp8_scale(float amax) { return amax > 0.0f ? amax * (1.0f / 448.0f) : 1.0f; }
+// Exponent e of the power-of-two scale of a block whose largest magnitude is amax: the
+// smallest e with amax / 2^e <= 448 (e4m3's largest finite value, 1.75 * 2^8), clamped to
+// the UE8M0 range; 0 for an all-zero block.
+__device__ __forceinline__ int fp8_block_exp(float amax) {
+    if (!(amax > 0.0f)) return 0;
+    const uint32_t bits = __float_as_uint(amax);
+    int e = ilogbf(amax) - 8;
+    if (((bits >> 23) & 0xFFu) != 0 && (bits & 0x7FFFFFu) > 0x600000u) e += 1;  // significand above 1.75
+    return max(-127, min(127, e));
+}
 
-__device__ __forceinline__ uint32_t fp8_pack4(float a, float b, float c, float d, float inv) {
-    const uint32_t q0 = __nv_cvt_float_to_fp8(a * inv, __NV_SATFINITE, __NV_E4M3);
-    const uint32_t q1 = __nv_cvt_float_to_fp8(b * inv, __NV_SATFINITE, __NV_E4M3);
-    const uint32_t q2 = __nv_cvt_float_to_fp8(c * inv, __NV_SATFINITE, __NV_E4M3);
-    const uint32_t q3 = __nv_cvt_float_to_fp8(d * inv, __NV_SATFINITE, __NV_E4M3);
+// e4m3 of x * 2^-e (the scaling is exact), rounded to nearest, saturating.
+__device__ __forceinline__ uint32_t fp8_pack4(float a, float b, float c, float d, int e) {
+    const uint32_t q0 = __nv_cvt_float_to_fp8(ldexpf(a, -e), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t q1 = __nv_cvt_float_to_fp8(ldexpf(b, -e), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t q2 = __nv_cvt_float_to_fp8(ldexpf(c, -e), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t q3 = __nv_cvt_float_to_fp8(ldexpf(d, -e), __NV_SATFINITE, __NV_E4M3);
     return q0 | (q1 << 8) | (q2 << 16) | (q3 << 24);
 }
 
-// A (M x K) -> q [Mp][Kp] e4m3, sa [Mp][Kp/128]; one warp per (row, K block), lane = 4 k.
+// The 32-bit word of row (or column) r of a 128-row tile in its scale-factor block: the UE8M0
+// code e + 127 in all four bytes (the 128-element block's scale for each of its 32-element
+// K steps).
+__device__ __forceinline__ void put_sf(uint8_t* blk, int r, int e) {
+    *reinterpret_cast<uint32_t*>(blk + 16 * (r & 31) + 4 * (r >> 5)) = (uint32_t)(e + 127) * 0x01010101u;
+}
+
+// A (M x K) -> q [Mp][Kp] e4m3 and scale-factor blocks sfa [Mp / 128][Kp / 128][512 bytes];
+// one warp per (row, K block), lane = 4 k.
 __global__ void quant_rows_fp8_kernel(const float* __restrict__ A, int64_t M, int64_t K, int64_t Mp, int64_t Kp,
-                                      uint8_t* __restrict__ q, float* __restrict__ sa) {
+                                      uint8_t* __restrict__ q, uint8_t* __restrict__ sfa) {
     const int lane = threadIdx.x & 31;
     const int64_t kbs = Kp / 128;
     const int64_t nwork = Mp * kbs;
@@ -929,21 +996,23 @@ __global__ void quant_rows_fp8_kernel(const float* __restrict__ A, int64_t M, in
         float amax = fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fmaxf(fabsf(x[2]), fabsf(x[3])));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-        const float sc = fp8_scale(amax);
-        *reinterpret_cast<uint32_t*>(q + i * Kp + k0) = fp8_pack4(x[0], x[1], x[2], x[3], 1.0f / sc);
-        if (lane == 0) sa[i * kbs + kb] = sc;
+        const int e = fp8_block_exp(amax);
+        *reinterpret_cast<uint32_t*>(q + i * Kp + k0) = fp8_pack4(x[0], x[1], x[2], x[3], e);
+        if (lane == 0) put_sf(sfa + ((i / 128) * kbs + kb) * kSfBlock, (int)(i % 128), e);
     }
 }
 
-// B (K x N) -> q^T [Np][Kp] e4m3, sb [Kp/128][Np]; CTA = (K block, 32 columns).
+// B (K x N) -> q^T [Np][Kp] e4m3 and scale-factor blocks sfb [Np / 128][Kp / 128][512
+// bytes]; CTA = (K block, 32 columns).
 __global__ void __launch_bounds__(256) quant_cols_fp8_kernel(const float* __restrict__ B, int64_t K, int64_t N,
                                                              int64_t Np, int64_t Kp, uint8_t* __restrict__ q,
-                                                             float* __restrict__ sb) {
+                                                             uint8_t* __restrict__ sfb) {
     __shared__ float tile[128][33];
     __shared__ float red[8][32];
-    __shared__ float inv[32];
+    __shared__ int ex[32];
     const int t = threadIdx.x, c = t & 31, g = t >> 5;
     const int64_t kb = blockIdx.y, n0 = (int64_t)blockIdx.x * 32;
+    const int64_t kbs = Kp / 128;
     float m = 0.0f;
     for (int r = g; r < 128; r += 8) {
         const int64_t k = kb * 128 + r, n = n0 + c;
@@ -956,19 +1025,20 @@ __global__ void __launch_bounds__(256) quant_cols_fp8_kernel(const float* __rest
     if (g == 0) {
         float a = red[0][c];
         for (int j = 1; j < 8; ++j) a = fmaxf(a, red[j][c]);
-        const float sc = fp8_scale(a);
-        inv[c] = 1.0f / sc;
-        sb[kb * Np + n0 + c] = sc;
+        const int e = fp8_block_exp(a);
+        ex[c] = e;
+        const int64_t n = n0 + c;
+        put_sf(sfb + ((n / 128) * kbs + kb) * kSfBlock, (int)(n % 128), e);
     }
     __syncthreads();
     // column n = t / 8 of the tile becomes row n0 + n of q^T; 16 k per thread
     const int n = t >> 3, k16 = (t & 7) * 16;
-    const float iv = inv[n];
+    const int e = ex[n];
     uint4 o;
-    o.x = fp8_pack4(tile[k16 + 0][n], tile[k16 + 1][n], tile[k16 + 2][n], tile[k16 + 3][n], iv);
-    o.y = fp8_pack4(tile[k16 + 4][n], tile[k16 + 5][n], tile[k16 + 6][n], tile[k16 + 7][n], iv);
-    o.z = fp8_pack4(tile[k16 + 8][n], tile[k16 + 9][n], tile[k16 + 10][n], tile[k16 + 11][n], iv);
-    o.w = fp8_pack4(tile[k16 + 12][n], tile[k16 + 13][n], tile[k16 + 14][n], tile[k16 + 15][n], iv);
+    o.x = fp8_pack4(tile[k16 + 0][n], tile[k16 + 1][n], tile[k16 + 2][n], tile[k16 + 3][n], e);
+    o.y = fp8_pack4(tile[k16 + 4][n], tile[k16 + 5][n], tile[k16 + 6][n], tile[k16 + 7][n], e);
+    o.z = fp8_pack4(tile[k16 + 8][n], tile[k16 + 9][n], tile[k16 + 10][n], tile[k16 + 11][n], e);
+    o.w = fp8_pack4(tile[k16 + 12][n], tile[k16 + 13][n], tile[k16 + 14][n], tile[k16 + 15][n], e);
     *reinterpret_cast<uint4*>(q + (n0 + n) * Kp + kb * 128 + k16) = o;
 }
 
@@ -1042,7 +1112,8 @@ cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const floa
 
 }  // namespace
 
-// FP8 scratch: q(A) [Mp][Kp], q(B^T) [Np][Kp], sa [Mp][Kp/128], sb [Kp/128][Np]
+// FP8 scratch: q(A) [Mp][Kp], q(B^T) [Np][Kp], then the scale-factor blocks of A
+// [Mp / 128][Kp / 128][512 bytes] and of B [Np / 128][Kp / 128][512 bytes]
 struct Fp8Layout {
     int64_t Mp, Np, Kp, kbs;
     size_t qa, qb, sa, sb, total;
@@ -1056,8 +1127,8 @@ Fp8Layout fp8_layout(int64_t M, int64_t N, int64_t K) {
     L.qa = 0;
     L.qb = ru((int64_t)(L.Mp * L.Kp), 1024);
     L.sa = L.qb + ru(L.Np * L.Kp, 1024);
-    L.sb = L.sa + ru(L.Mp * L.kbs * 4, 1024);
-    L.total = L.sb + ru(L.kbs * L.Np * 4, 1024);
+    L.sb = L.sa + ru((L.Mp / 128) * L.kbs * kSfBlock, 1024);
+    L.total = L.sb + ru((L.Np / 128) * L.kbs * kSfBlock, 1024);
     return L;
 }
 
@@ -1236,7 +1307,7 @@ cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const floa
     }
     uint8_t* base = static_cast<uint8_t*>(scratch);
     uint8_t *qa = base + L.qa, *qb = base + L.qb;
-    float *sa = reinterpret_cast<float*>(base + L.sa), *sb = reinterpret_cast<float*>(base + L.sb);
+    uint8_t *sa = base + L.sa, *sb = base + L.sb;
     {
         const int64_t warps = L.Mp * L.kbs;
         int64_t g = (warps * 32 + 255) / 256;
@@ -1254,11 +1325,13 @@ cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const floa
     CUtensorMap ta, tb;
     if (!make_map(&ta, qa, L.Kp, L.Mp, BM, true, why)) return cudaErrorInvalidValue;
     if (!make_map(&tb, qb, L.Kp, L.Np, 128, true, why)) return cudaErrorInvalidValue;
+    // the epilogue's sa / sb carry the scale-factor blocks (read by the producer's bulk copies)
     EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
-               (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, sa, sb, (int)L.kbs,
-               (int)L.Np};
+               (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0,
+               reinterpret_cast<const float*>(sa), reinterpret_cast<const float*>(sb), (int)L.kbs, (int)L.Np};
     if (ev.k0) record_timing(ev.k0, st);
-    cudaError_t e = launch_mma<128, 1, 1, 6, true, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, (int)L.kbs, 1, group, 0, err, st);
+    const int kbs = (int)L.kbs;
+    cudaError_t e = launch_mma<128, 1, 1, 6, false, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, kbs, kbs, group, 0, err, st);
     if (e != cudaSuccess) return e;
     ev.launches += 1;
     if (ev.k1) record_timing(ev.k1, st);
@@ -1316,7 +1389,7 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
         const Fp8Layout L = fp8_layout(M, N, K);
         uint8_t* base = static_cast<uint8_t*>(scratch);
         uint8_t *qa = base + L.qa, *qb = base + L.qb;
-        float *sa = reinterpret_cast<float*>(base + L.sa), *sb = reinterpret_cast<float*>(base + L.sb);
+        uint8_t *sa = base + L.sa, *sb = base + L.sb;
         const int64_t warps = L.Mp * L.kbs;
         int64_t g = (warps * 32 + 255) / 256;
         if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
@@ -1330,11 +1403,12 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
         *launches = 2;
         if (!make_map(&prob->ta, qa, L.Kp, L.Mp, BM, true, why)) return cudaErrorInvalidValue;
         if (!make_map(&prob->tb, qb, L.Kp, L.Np, 128, true, why)) return cudaErrorInvalidValue;
-        prob->ep = EpiArgs{C, C0, (int)M, (int)N, alpha, beta, vec, sa, sb, (int)L.kbs, (int)L.Np};
+        prob->ep = EpiArgs{C, C0, (int)M, (int)N, alpha, beta, vec, reinterpret_cast<const float*>(sa),
+                           reinterpret_cast<const float*>(sb), (int)L.kbs, (int)L.Np};
         prob->Mp = (int)L.Mp;
         prob->Np = (int)L.Np;
         prob->num_kb = (int)L.kbs;
-        prob->chunk_kb = 1;
+        prob->chunk_kb = prob->num_kb;  // one accumulation over K: the scales act inside the MMA
     } else {
         const int P = planes_of(prec);
         const int64_t Mp = ru(M, BM), Np = ru(N, 256), Kp = ru(K, BK);
@@ -1423,7 +1497,7 @@ cudaError_t tc_launch_grouped(int prec, bool chunked, const TcProblem* d_probs, 
             return chunked ? launch_grouped_t<128, 1, 1, 6, true>(d_probs, nprob, total_tiles, err, st)
                            : launch_grouped_t<128, 1, 1, 6, false>(d_probs, nprob, total_tiles, err, st);
         case GAO_GEMM_FP8:
-            return launch_grouped_t<128, 1, 1, 6, true, true>(d_probs, nprob, total_tiles, err, st);
+            return launch_grouped_t<128, 1, 1, 6, false, true>(d_probs, nprob, total_tiles, err, st);
         default:
             return cudaErrorInvalidValue;
     }

@@ -8,15 +8,15 @@
 
 namespace gao {
 
-// Epilogue of one GEMM: C = alpha * acc + beta * C0 (FP8: acc scaled per K block).
+// Epilogue of one GEMM: C = alpha * acc + beta * C0 (FP8: the MMAs apply the block scales).
 struct EpiArgs {
     float* C;
     const float* C0;
     int M, N;
     float alpha, beta;
     int vec;           // C, C0 16-byte aligned and N % 4 == 0
-    const float* sa;   // FP8: scale of (row, K block), row-major [Mp][kbs]
-    const float* sb;   // FP8: scale of (K block, column), row-major [kbs][sb_ld]
+    const float* sa;   // FP8: A's scale-factor blocks [Mp / 128][kbs][512 bytes] (read as bytes)
+    const float* sb;   // FP8: B's scale-factor blocks [Np / 128][kbs][512 bytes] (read as bytes)
     int kbs, sb_ld;
     // Fused loop chain (fuse != 0): D = C + alpha2 * X written row-major like C, E = D^T
     // written with row stride M, and per-warp binary64 partials of sum(D^2) (8 per tile,

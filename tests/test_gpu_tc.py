@@ -6,9 +6,11 @@ Tolerances (normwise relative error of C = alpha*A@B + beta*C0):
     of each operand, so it sits at a few 1e-6 and does not meet 1e-6; gated here only
     against gross errors, its measured error is reported by the bench;
   * BF16 (one product): 5e-3, the stated bound for plain bfloat16;
-  * FP8 (e4m3, one scale per 128-element K block of each operand): not gated by the
-    stated bounds (its error is ~3e-2, reported by the bench); checked here against
-    6e-2 only to catch gross errors.
+  * FP8 (e4m3, one power-of-two scale per 128-element K block of each operand, applied
+    by block-scaled MMAs): not gated by the stated bounds (its error is ~3e-2, reported by
+    the bench); checked here against 6e-2 only to catch gross errors, and EXACTLY on
+    small-integer operands with power-of-two row factors, which e4m3 with power-of-two
+    block scales represents without rounding (so any misplaced scale shows).
 """
 import math
 
@@ -327,3 +329,28 @@ def test_prog_autotune_fused_chain(gao):
     ref = oracle.run_program(prog)
     assert oracle.rel_err(fused["C"], ref["C"]) <= TOL["bf16x6"]
     gao.prog_destroy(q)
+
+
+@pytest.mark.parametrize("M,N,K", [(200, 136, 300), (128, 128, 128), (257, 384, 1000)])
+def test_fp8_exact_on_small_integers(gao, M, N, K):
+    """Operands whose entries are integers in [-4, 4] (rows of A times 2^(i mod 7 - 3), columns
+    of B times 2^(j mod 5 - 2)) are exact in e4m3 under power-of-two block scales, their
+    products and sums exact in binary32: C = 1.5 A B + 0.5 C0 must come out bit for bit."""
+    rng = np.random.default_rng(M + N + K)
+    ra = 2.0 ** (np.arange(M) % 7 - 3)
+    cb = 2.0 ** (np.arange(N) % 5 - 2)
+    A = (rng.integers(-4, 5, (M, K)) * ra[:, None]).astype(np.float32)
+    B = (rng.integers(-4, 5, (K, N)) * cb[None, :]).astype(np.float32)
+    C0 = rng.integers(-8, 9, (M, N)).astype(np.float32)
+    B_, L_ = W.Buffer, W.Loop
+    bufs = [B_("A", M, K, role=W.INPUT), B_("B", K, N, role=W.INPUT), B_("C0", M, N, role=W.INPUT),
+            B_("C", M, N, role=W.OUTPUT)]
+    prog = W.Program("fp8_int", bufs, [L_(W.GEMM, [0, 1, 2], [3], 1.5, 0.5)], 0)
+    p = gao.prog_from_workload(prog, gemm_prec=PREC["fp8"])
+    for nm, v in (("A", A), ("B", B), ("C0", C0)):
+        gao.prog_set_input(p, prog.index(nm), v)
+    gao.prog_run(p, 1)
+    C = gao.prog_output(p, prog.index("C"))
+    gao.prog_destroy(p)
+    want = (1.5 * (A.astype(np.float64) @ B.astype(np.float64)) + 0.5 * C0).astype(np.float32)
+    assert np.array_equal(C, want)
