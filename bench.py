@@ -46,6 +46,7 @@ PREC = {"fp32_simt": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3, "fp8": 4}
 PRODUCTS = {"fp32_simt": 1, "bf16": 1, "bf16x3": 3, "bf16x6": 6, "fp8": 1}
 GATE = {"fp32_simt": 1e-6, "bf16x6": 1e-6, "bf16x3": 2e-5, "bf16": 5e-3, "fp8": 6e-2}
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+NOMINAL_DENSE_BF16 = 2250.0  # TFLOP/s, GB300 datasheet, dense (no 2:4 sparsity)
 
 
 def peaks():
@@ -593,6 +594,8 @@ def gemm_arm(args, world, rank, local):
                 "kernel": f"gemm_tc ({prec})", "products": PRODUCTS[prec],
                 "hw_tflops": achieved * PRODUCTS[prec], "hw_frac": achieved * PRODUCTS[prec] / bf16,
                 "frac_of_sustained": achieved / sus, "peak_source": how,
+                # the datasheet's dense bf16 figure (2.25 PFLOP/s), for comparison with the measured peaks
+                "frac_of_nominal_dense": achieved * PRODUCTS[prec] / (NOMINAL_DENSE_BF16 * (2.0 if prec == "fp8" else 1.0)),
                 "kernel_ms": gemm_ms, "kernel_ms_source": "library CUDA events around the kernel, every timed step"}
     else:
         mhz = pk.get("sm_max_mhz", 2070.0)
