@@ -142,18 +142,83 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// ---- CTA pairs (a cluster of two CTAs on neighbouring SMs sharing one 256-row tile) ----------
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Address in CTA `rank` of the cluster of the shared-memory location `a` of this CTA.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Arrive on an mbarrier of another CTA of the cluster (release at cluster scope).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+// TMA load into this CTA's shared memory whose completion is counted on an mbarrier of
+// either CTA of the pair (cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                                 uint32_t cluster_bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(cluster_bar)
+        : "memory");
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Completion of the pair's MMAs signalled on the mbarrier at the same offset in both CTAs.
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"((uint16_t)3)
+        : "memory");
+}
+// ... on this CTA's mbarrier only.
+__device__ __forceinline__ void mma_commit_pair_local(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// With PAIR, one warp of each CTA of the pair allocates (and frees) together: both get the
+// same tensor-memory address, the pair's MMAs write each CTA's rows into its own.
+template <bool PAIR>
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-                 : "memory");
+    if constexpr (PAIR)
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                     : "memory");
+    else
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                     : "memory");
 }
+template <bool PAIR>
 __device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    else asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
+template <bool PAIR>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+    if constexpr (PAIR)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -219,10 +284,11 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor for kind::f16: D binary32 (bits 4-5 = 1), A and B bfloat16
-// (bits 7-9 = 1, bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
-template <int N_>
+// (bits 7-9 = 1, bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
+// (M = 256 for a CTA pair: 128 rows of A from each CTA).
+template <int N_, int M_ = BM>
 __host__ __device__ constexpr uint32_t idesc_bf16() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(M_ >> 4) << 24);
 }
 
 // Instruction descriptor for kind::mxf8f6f4 with e4m3 A and B (format code 0 at bits 7-9
@@ -415,10 +481,14 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
     if (fuse) *sq += (double)s2 + (double)s3;
 }
 
-template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8 = false>
+// PAIR: a cluster of two CTAs computes a 256 x BN tile with M = 256 MMAs issued by the first
+// CTA; each CTA holds 128 rows of A and BN / 2 rows of B^T per stage (the pair's B tile is
+// split by columns), and 128 rows of the accumulator in its own tensor memory.
+template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8 = false, bool PAIR = false>
 struct TcCfg {
     static constexpr uint32_t A_TILE = BM * 128;  // 128 rows x 128 bytes
-    static constexpr uint32_t B_TILE = BN * 128;
+    static constexpr uint32_t B_TILE = (PAIR ? BN / 2 : BN) * 128;
+    static constexpr int TILE_M = PAIR ? 2 * BM : BM;  // rows of a tile
     static constexpr uint32_t STAGE = PA * A_TILE + PB * B_TILE;
     static constexpr int ACC = 2;  // accumulator buffers: a tile's epilogue overlaps the next tile's MMAs
     // With more than one product, hi.hi accumulates in its own tensor-memory block and
@@ -434,6 +504,7 @@ struct TcCfg {
     static constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256
                                                                                                               : 512;
     static constexpr uint32_t NBARS = 2 * STAGES + 2 * ACC + 1;
+    static constexpr int EPI_ARRIVALS = (PAIR ? 2 : 1) * kEpiWarps;  // per drained accumulator
     static constexpr uint32_t STG = kEpiWarps * kStgBytes;  // epilogue staging blocks
     // FP8: scale-factor blocks of every stage (A's, then BN / 128 of B's), after the tiles
     static constexpr uint32_t SF_STAGE = FP8 ? (uint32_t)kSfBlock * (1 + BN / 128) : 0;
@@ -443,6 +514,7 @@ struct TcCfg {
     static_assert(BN % 64 == 0 && BN >= 64 && BN <= 256, "BN");
     static_assert(!CHUNKED || BN <= 128, "chunked sums live in registers: BN <= 128");
     static_assert(!FP8 || (!CHUNKED && NPROD == 1 && PA == 1 && PB == 1), "FP8 runs one plane, scaled in the MMA");
+    static_assert(!(PAIR && FP8), "CTA pairs run the bfloat16 variants");
 };
 
 // One 128 x BN output tile (row tile tm, column tile tn) of one problem.
@@ -465,7 +537,7 @@ struct TileInfo {
     EpiArgs ep;
     int Mp, Np, num_kb, chunk_kb, m0, n0;
     int pf_kb;  // operand tiles are pulled into L2 this many K blocks ahead of their loads (0: off)
-    int tile0;  // launch index of the problem's first tile (its tiles are t - tile0 = 0, 1, ...)
+    int tiles_n;  // column tiles of the problem (row-major index of the norm partials)
     unsigned long long *span_start, *span_end;  // the problem's time span in the launch (null: none)
 };
 
@@ -474,7 +546,7 @@ struct OneProblem {
     const CUtensorMap* ta;
     const CUtensorMap* tb;
     EpiArgs ep;
-    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, bn, pf_kb;
+    int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, bn, pf_kb, bm;  // bm: rows of a tile
     __device__ __forceinline__ void get(int t, TileInfo& ti) const {
         int tm, tn;
         raster(t, tiles_m, tiles_n, group, tm, tn);
@@ -485,10 +557,10 @@ struct OneProblem {
         ti.Np = Np;
         ti.num_kb = num_kb;
         ti.chunk_kb = chunk_kb;
-        ti.m0 = tm * BM;
+        ti.m0 = tm * bm;
         ti.n0 = tn * bn;
         ti.pf_kb = pf_kb;
-        ti.tile0 = 0;
+        ti.tiles_n = tiles_n;
         ti.span_start = ti.span_end = nullptr;
     }
 };
@@ -519,7 +591,7 @@ struct ProblemTable {
         ti.m0 = tm * BM;
         ti.n0 = tn * bn;
         ti.pf_kb = P->pf_kb;
-        ti.tile0 = P->tile_start;
+        ti.tiles_n = P->tiles_n;
         ti.span_start = P->span_start;
         ti.span_end = P->span_end;
     }
@@ -529,10 +601,15 @@ struct ProblemTable {
 // shared-memory stage ring and the two tensor-memory accumulator buffers carry on
 // from tile to tile, so the producer runs ahead into the next tile and the MMAs of a
 // tile overlap the epilogue of the previous one.
-template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8, class Src>
+template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8, bool PAIR, class Src>
 __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_tiles, int* err) {
-    using Cfg = TcCfg<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>;
-    constexpr uint32_t IDESC = idesc_bf16<BN>();
+    using Cfg = TcCfg<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8, PAIR>;
+    constexpr uint32_t IDESC = idesc_bf16<BN, Cfg::TILE_M>();
+    // a CTA pair serves tile c, c + clusters, ... (c = its cluster); its second CTA (rank 1)
+    // holds rows 128..255 of each tile and columns BN / 2.. of each B tile
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const int first_tile = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int tile_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     constexpr int KBE = FP8 ? BK8 : BK;  // elements per K block
     constexpr int ACC = Cfg::ACC;
     extern __shared__ uint8_t smem_raw[];
@@ -560,7 +637,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
         }
         for (int b = 0; b < ACC; ++b) {
             mbar_init(accf_bar(b), 1);
-            mbar_init(acce_bar(b), kEpiWarps);
+            mbar_init(acce_bar(b), Cfg::EPI_ARRIVALS);  // a pair: both CTAs' epilogue warps
         }
         mbar_init(tail_bar, 1);
         *abort_flag = 0;
@@ -568,11 +645,12 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
-        tmem_relinquish();
+        tmem_alloc<PAIR>(smem_u32(tmem_slot), Cfg::TMEM_COLS);
+        tmem_relinquish<PAIR>();
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) cluster_sync();  // the peer's barriers exist before any remote arrival
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -581,9 +659,11 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
             // ---- TMA producer ----
             int it = 0;  // k blocks issued so far (all tiles)
             bool ok = true;
-            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+            for (int t = first_tile; t < total_tiles && ok; t += tile_step) {
                 TileInfo ti;
                 src.get(t, ti);
+                const int a_row = ti.m0 + (int)rank * BM;             // this CTA's 128 rows of A
+                const int b_row = ti.n0 + (int)rank * (BN / 2);       // a pair: this CTA's half of B
                 tma_prefetch_desc(ti.ta);
                 tma_prefetch_desc(ti.tb);
                 if (ti.span_start) atomicMin(ti.span_start, gtimer());
@@ -595,17 +675,32 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                         const int k_last = min(kb + ti.pf_kb, ti.num_kb - 1);
                         for (int k2 = kb == 0 ? 0 : kb + ti.pf_kb; k2 <= k_last; ++k2) {
 #pragma unroll
-                            for (int p = 0; p < PA; ++p) tma_prefetch_l2_2d(ti.ta, k2 * KBE, p * ti.Mp + ti.m0);
+                            for (int p = 0; p < PA; ++p) tma_prefetch_l2_2d(ti.ta, k2 * KBE, p * ti.Mp + a_row);
 #pragma unroll
-                            for (int p = 0; p < PB; ++p) tma_prefetch_l2_2d(ti.tb, k2 * KBE, p * ti.Np + ti.n0);
+                            for (int p = 0; p < PB; ++p)
+                                tma_prefetch_l2_2d(ti.tb, k2 * KBE, p * ti.Np + (PAIR ? b_row : ti.n0));
                         }
                     }
                     if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, err)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(full_bar(s), Cfg::STAGE + Cfg::SF_STAGE);
                     const uint32_t st = tiles + (uint32_t)s * Cfg::STAGE;
+                    if constexpr (PAIR) {
+                        // both CTAs' loads complete on the first CTA's full barrier, which
+                        // the first CTA's producer arms with the pair's bytes
+                        const uint32_t fb = cluster_addr(full_bar(s), 0);
+                        if (rank == 0) mbar_expect_tx(full_bar(s), 2 * Cfg::STAGE);
+#pragma unroll
+                        for (int p = 0; p < PA; ++p)
+                            tma_load_2d_pair(st + (uint32_t)p * Cfg::A_TILE, ti.ta, kb * KBE, p * ti.Mp + a_row, fb);
+#pragma unroll
+                        for (int p = 0; p < PB; ++p)
+                            tma_load_2d_pair(st + PA * Cfg::A_TILE + (uint32_t)p * Cfg::B_TILE, ti.tb, kb * KBE,
+                                             p * ti.Np + b_row, fb);
+                        continue;
+                    }
+                    mbar_expect_tx(full_bar(s), Cfg::STAGE + Cfg::SF_STAGE);
                     if constexpr (FP8) {  // this K block's scale factors of the A and B tiles
                         const uint8_t* sfa = reinterpret_cast<const uint8_t*>(ti.ep.sa);
                         const uint8_t* sfb = reinterpret_cast<const uint8_t*>(ti.ep.sb);
@@ -634,16 +729,18 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                     // the MMA's release of the last uses of each stage
                     if (!mbar_wait(empty_bar(s), ph, abort_flag, err)) ok = false;
                 }
-                if (!ok) mbar_drain(full_bar(s), ph);  // let our own copies land
+                // let our own copies land (a pair: the first CTA's full barriers count both CTAs'
+                // copies; the second CTA's land before the pair's final cluster barrier)
+                if (!ok && (!PAIR || rank == 0)) mbar_drain(full_bar(s), ph);
             }
         }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && rank == 0) {  // a pair's MMAs are issued by its first CTA
             // ---- MMA issuer ----
             int it = 0, gc = 0;  // k blocks consumed, accumulator chunks used (all tiles)
             bool ok = true;
-            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+            for (int t = first_tile; t < total_tiles && ok; t += tile_step) {
                 TileInfo ti;
                 src.get(t, ti);
                 const int nchunks = (ti.num_kb + ti.chunk_kb - 1) / ti.chunk_kb;
@@ -693,18 +790,23 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                                 const uint32_t dd = d + ((Cfg::SPLIT && pr > 0) ? (uint32_t)BN : 0u);
                                 if constexpr (FP8)
                                     mma_mxf8(dd, ad, bd, idesc_mxf8<BN>(kk), sfa_t, sfb_t, first ? 0u : 1u);
+                                else if constexpr (PAIR)
+                                    mma_bf16_pair(dd, ad, bd, IDESC, first ? 0u : 1u);
                                 else
                                     mma_bf16(dd, ad, bd, IDESC, first ? 0u : 1u);
                             }
                         }
-                        mma_commit(empty_bar(s));
+                        if constexpr (PAIR) mma_commit_pair(empty_bar(s));  // frees the stage in both CTAs
+                        else mma_commit(empty_bar(s));
                     }
                     if (!ok) break;
-                    mma_commit(accf_bar(ab));
+                    if constexpr (PAIR) mma_commit_pair(accf_bar(ab));
+                    else mma_commit(accf_bar(ab));
                 }
             }
             if (!ok) {  // no MMA may still be running when tensor memory is freed
-                mma_commit(tail_bar);
+                if constexpr (PAIR) mma_commit_pair_local(tail_bar);
+                else mma_commit(tail_bar);
                 mbar_drain(tail_bar, 0);
             }
         }
@@ -720,12 +822,12 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
         constexpr int G = BN / 2 / 32;  // 32-column groups per thread
         int gc = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+        for (int t = first_tile; t < total_tiles && ok; t += tile_step) {
             TileInfo ti;
             src.get(t, ti);
             const EpiArgs& ep = ti.ep;
             const int nchunks = (ti.num_kb + ti.chunk_kb - 1) / ti.chunk_kb;
-            const int64_t row0 = (int64_t)ti.m0 + q * 32;
+            const int64_t row0 = (int64_t)ti.m0 + (int64_t)rank * BM + q * 32;
             const int64_t grow = row0 + lane;
             const int n0 = ti.n0;
             double sq = 0.0;  // fused chain: this thread's sum of D^2 over the tile
@@ -775,7 +877,10 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acce_bar(ab));
+                if (lane == 0) {
+                    if constexpr (PAIR) mbar_arrive_remote(cluster_addr(acce_bar(ab), 0));  // the MMA CTA's
+                    else mbar_arrive(acce_bar(ab));
+                }
             }
             if constexpr (CHUNKED) {
                 if (ok) {
@@ -787,7 +892,10 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
             if (ep.fuse && ok) {  // fixed butterfly over the warp's rows, one partial per warp
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
-                if (lane == 0 && ep.frob_part) ep.frob_part[(int64_t)(t - ti.tile0) * kEpiWarps + ew] = sq;
+                // one slot per (128-row tile, column tile, warp) in row-major tile order, so that
+                // CTA pairs and single CTAs sum the same partials in the same order
+                const int64_t tile128 = (int64_t)((ti.m0 + (int)rank * BM) / BM) * ti.tiles_n + ti.n0 / BN;
+                if (lane == 0 && ep.frob_part) ep.frob_part[tile128 * kEpiWarps + ew] = sq;
             }
             if (ti.span_end && ok && lane == 0) {
                 __threadfence();  // the warp's stores of this tile come first
@@ -798,9 +906,12 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
 
     tc_fence_before();
     __syncthreads();
+    // a pair: neither CTA leaves while the other may still arrive on its barriers, read its
+    // shared memory (the MMAs) or land copies there
+    if constexpr (PAIR) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, Cfg::TMEM_COLS);
+        tmem_dealloc<PAIR>(tmem, Cfg::TMEM_COLS);
     }
 }
 
@@ -809,8 +920,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep,
                    int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int group, int pf_kb,
                    int* err) {
-    const OneProblem src{&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, BN, pf_kb};
-    gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(src, tiles_m * tiles_n, err);
+    const OneProblem src{&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, BN, pf_kb, BM};
+    gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8, false>(src, tiles_m * tiles_n, err);
+}
+
+// The same GEMM on CTA pairs: tiles of 256 x BN rows (tiles_m counts 256-row tiles).
+template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTc, 1)
+    gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep,
+                        int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int group, int pf_kb,
+                        int* err) {
+    const OneProblem src{&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, BN, pf_kb, 2 * BM};
+    gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, false, true>(src, tiles_m * tiles_n, err);
 }
 
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
@@ -824,7 +945,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     if (in_smem)
         for (int i = threadIdx.x; i < nprob; i += blockDim.x) s_starts[i] = probs[i].tile_start;
     const ProblemTable src{probs, nprob, BN, in_smem ? s_starts : nullptr};
-    gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8>(src, total_tiles, err);
+    gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8, false>(src, total_tiles, err);
 }
 
 // Frobenius norm of a fused chain: the per-warp partials summed in index order by one
@@ -1106,6 +1227,43 @@ cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const EpiAr
 }
 
 
+// The pair kernel: Mp a multiple of 256; one cluster of two CTAs per two SMs.
+template <int BN, int P, int NPROD, int STAGES, bool CHUNKED>
+cudaError_t launch_mma_pair(const CUtensorMap& ta, const CUtensorMap& tb, const EpiArgs& ep, int Mp, int Np,
+                            int num_kb, int chunk_kb, int group, int pf_kb, int* err, cudaStream_t st) {
+    using Cfg = TcCfg<BN, P, P, NPROD, STAGES, CHUNKED, false, true>;
+    auto kern = gemm_tc_pair_kernel<BN, P, P, NPROD, STAGES, CHUNKED>;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (Mp % (2 * BM) != 0) return cudaErrorInvalidValue;
+    const int tiles_m = Mp / (2 * BM), tiles_n = (ep.N + BN - 1) / BN;
+    const int64_t total = (int64_t)tiles_m * tiles_n;
+    if (total > 0x7fffffff) return cudaErrorInvalidValue;
+    // persistent: as many pairs as can be resident at once (a cluster needs two SMs of one
+    // GPC, so this can be fewer than half the SMs)
+    static int max_clusters = 0;
+    if (max_clusters == 0) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)(sm_count() & ~1));
+        lc.blockDim = dim3(kThreadsTc);
+        lc.dynamicSmemBytes = Cfg::SMEM;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &lc) != cudaSuccess || n <= 0) {
+            (void)cudaGetLastError();
+            n = sm_count() / 2;
+        }
+        max_clusters = std::min(n, sm_count() / 2);
+    }
+    const int64_t clusters = std::min<int64_t>(total, (int64_t)max_clusters);
+    kern<<<(unsigned)(2 * clusters), kThreadsTc, Cfg::SMEM, st>>>(ta, tb, ep, Mp, Np, num_kb, chunk_kb, tiles_m,
+                                                                  tiles_n, group, pf_kb, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K,
                             float alpha, float beta, int group, void* scratch, size_t scratch_bytes, int* err,
                             cudaStream_t st, TcEvents& ev, std::string* why);
@@ -1138,18 +1296,19 @@ size_t tc_planes_bytes(int prec, int64_t M, int64_t N, int64_t K) {
     if (prec == GAO_GEMM_FP8) return fp8_layout(M, N, K).total;
     if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_BF16X6) return 0;
     const int64_t P = planes_of(prec);
-    const int64_t Mp = ru(std::max<int64_t>(M, 1), BM), Np = ru(std::max<int64_t>(N, 1), 256),
+    // A's rows rounded to 256: the tile of a CTA pair
+    const int64_t Mp = ru(std::max<int64_t>(M, 1), 2 * BM), Np = ru(std::max<int64_t>(N, 1), 256),
                   Kp = ru(std::max<int64_t>(K, 1), BK);
     return (size_t)ru(P * (Mp + Np) * Kp * 2, 1024);
 }
 
 size_t tc_frob_partials_bytes(int64_t M, int64_t N) {
-    const int64_t tiles = (ru(std::max<int64_t>(M, 1), BM) / BM) * ((std::max<int64_t>(N, 1) + 127) / 128);
+    const int64_t tiles = (ru(std::max<int64_t>(M, 1), 2 * BM) / BM) * ((std::max<int64_t>(N, 1) + 127) / 128);
     return (size_t)ru(tiles * kEpiWarps * (int64_t)sizeof(double), 1024);
 }
 
 size_t tc_partials_bytes(int64_t M, int64_t N) {
-    const int64_t blocks = ru(std::max<int64_t>(M, 1), BM) / kRowsumBlock;
+    const int64_t blocks = ru(std::max<int64_t>(M, 1), 2 * BM) / kRowsumBlock;
     return tc_frob_partials_bytes(M, N) + (size_t)ru(blocks * std::max<int64_t>(N, 1) * 4, 1024);
 }
 
@@ -1198,7 +1357,27 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         if (why) *why = "bad row-block arguments";
         return cudaErrorInvalidValue;
     }
-    const int64_t Mp = ru(M, BM), Np = ru(N, 256), Kp = ru(K, BK);
+    const int64_t Np = ru(N, 256), Kp = ru(K, BK);
+    const int num_kb = (int)(Kp / BK);
+    int chunk_kb = num_kb;
+    if (kchunk > 0) chunk_kb = std::max(1, (int)((kchunk + BK - 1) / BK));
+    const bool chunked = chunk_kb < num_kb;
+    // tile_cfg bits 0-1: 0 = default, 1 = 128 x 128 tiles, 2 = 128 x 256 (single product,
+    // unchunked only); bit 2: L2 prefetch of the operand tiles; bit 3: CTA pairs (256-row
+    // tiles on two SMs, each SM loading half of every B tile); bits 4-7: raster group =
+    // 2^value row tiles (0: default 16).  The default is the fastest measured shape:
+    // 256 x 256 on CTA pairs for the unchunked single product (which the pair's halved B
+    // traffic per SM speeds up by 14% at n = 8192), 128 x 128 on one CTA for the split
+    // precisions (tensor-bound already: a pair gains nothing there).
+    const int bn_sel = tile_cfg & 3;
+    const int group = tc_group_of(tile_cfg);
+    const int pf_kb = tc_prefetch_of(tile_cfg);
+    int bn = 128;
+    if (!chunked && P == 1 && (bn_sel == 2 || bn_sel == 0)) bn = 256;
+    // a row block must start on a 256-row boundary to run on pairs
+    const bool pair = ((tile_cfg & 8) != 0 || (bn_sel == 0 && P == 1 && !chunked)) &&
+                      !(part && part->row_tile0 % 2 != 0);
+    const int64_t Mp = ru(M, pair ? 2 * BM : BM);
     if (tc_scratch_bytes(prec, Mlay, N, K) > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
         if (why) *why = "tensor-core scratch too small or misaligned";
         return cudaErrorInvalidValue;
@@ -1206,7 +1385,7 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     // A's planes ([P][Mp][Kp], this call's rows) at the start; B's ([P][Np][Kp]) after
     // room for the whole problem's A planes, so that row blocks can share them
     __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(scratch);
-    __nv_bfloat16* pb = pa + (size_t)P * ru(Mlay, BM) * Kp;
+    __nv_bfloat16* pb = pa + (size_t)P * ru(Mlay, 2 * BM) * Kp;
     const int sms = sm_count();
     {
         const int64_t work = Mp * (Kp / 8);
@@ -1229,22 +1408,9 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
             ev.launches += 1;
         }
     }
-    const int num_kb = (int)(Kp / BK);
-    int chunk_kb = num_kb;
-    if (kchunk > 0) chunk_kb = std::max(1, (int)((kchunk + BK - 1) / BK));
-    const bool chunked = chunk_kb < num_kb;
-    // tile_cfg bits 0-1: 0 = default (128 x 256 for the unchunked single product, else
-    // 128 x 128), 1 = 128 x 128, 2 = 128 x 256 (single product, unchunked only);
-    // bit 2: L2 prefetch of the operand tiles; bits 4-7: raster group = 2^value row
-    // tiles (0: default 16)
-    const int bn_sel = tile_cfg & 3;
-    const int group = tc_group_of(tile_cfg);
-    const int pf_kb = tc_prefetch_of(tile_cfg);
-    int bn = 128;
-    if (!chunked && P == 1 && (bn_sel == 2 || bn_sel == 0)) bn = 256;
     CUtensorMap ta, tb;
     if (!make_map(&ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;
-    if (!make_map(&tb, pb, Kp, (int64_t)P * Np, bn, false, why)) return cudaErrorInvalidValue;
+    if (!make_map(&tb, pb, Kp, (int64_t)P * Np, pair ? bn / 2 : bn, false, why)) return cudaErrorInvalidValue;
     EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
                (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, nullptr, nullptr, 0, 0};
     double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, Mlay, N, K));
@@ -1265,7 +1431,23 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     if (ev.k0) record_timing(ev.k0, st);
     cudaError_t e;
     const int mp = (int)Mp, np = (int)Np;
-    if (P == 3)
+    if (pair) {
+        // stages per variant: as many as fit next to the epilogue's staging blocks
+        if (P == 3)
+            e = chunked ? launch_mma_pair<128, 3, 6, 2, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st)
+                        : launch_mma_pair<128, 3, 6, 2, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err,
+                                                               st);
+        else if (P == 2)
+            e = chunked ? launch_mma_pair<128, 2, 3, 4, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st)
+                        : launch_mma_pair<128, 2, 3, 4, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err,
+                                                               st);
+        else if (chunked)
+            e = launch_mma_pair<128, 1, 1, 8, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st);
+        else if (bn == 256)
+            e = launch_mma_pair<256, 1, 1, 6, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st);
+        else
+            e = launch_mma_pair<128, 1, 1, 8, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st);
+    } else if (P == 3)
         e = chunked ? launch_mma<128, 3, 6, 2, true>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st)
                     : launch_mma<128, 3, 6, 2, false>(ta, tb, ep, mp, np, num_kb, chunk_kb, group, pf_kb, err, st);
     else if (P == 2)

@@ -993,7 +993,7 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
     if (!A.vh || !(B.vd || B.vh) || (C0 && !(C0->vd || C0->vh)))
         return fail(GAO_EINVAL, "a GEMM input holds no data");
     const int64_t M = A.d.rows, K = A.d.cols, N = B.d.cols;
-    const int64_t rows = ((M + blocks - 1) / blocks + 127) / 128 * 128;
+    const int64_t rows = ((M + blocks - 1) / blocks + 255) / 256 * 256;  // whole CTA-pair tiles
     cudaStream_t st = R.st, cs = p->cst;
     cudaEvent_t* ev = &p->ev[(size_t)li * 6];
     cudaEvent_t fork = p->pipe_ev[0], b_done = p->pipe_ev[1];

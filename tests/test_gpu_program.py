@@ -170,14 +170,16 @@ def test_twelve_loop_program(gao, m, k):
         assert abs(out["s"] - s_ref) <= 1e-6 * float(np.abs(P).astype(np.float64).sum())
 
 
-@pytest.mark.parametrize("n,prec", [(2048, "BF16X6"), (2500, "BF16X3"), (2304, "BF16")])
-def test_overlapped_host_gemm_is_bit_identical(gao, n, prec):
+@pytest.mark.parametrize("n,prec,cfg", [(2048, "BF16X6", 0), (2500, "BF16X3", 0), (2304, "BF16", 0),
+                                        (2500, "BF16X6", 8), (2304, "BF16X3", 8)])
+def test_overlapped_host_gemm_is_bit_identical(gao, n, prec, cfg):
     """A GEMM loop whose A comes from the host runs in row blocks overlapped with the copy;
-    its C must carry the same bits as the one-launch GEMM on device-resident inputs."""
+    its C must carry the same bits as the one-launch GEMM on device-resident inputs (with
+    tile configuration 8 on CTA pairs, row blocks of whole 256-row tiles)."""
     seed = 91
     pr = getattr(gao, prec)
     dev = W.six_loop(n, seed, outputs=("C", "r", "f"))
-    p = gao.prog_from_workload(dev, gemm_prec=pr)
+    p = gao.prog_from_workload(dev, gemm_prec=pr, tile_cfg=cfg)
     gao.prog_run(p, 0b111111)
     C_dev = gao.prog_output(p, dev.index("C")).copy()
     r_dev = gao.prog_output(p, dev.index("r")).copy()
@@ -189,7 +191,7 @@ def test_overlapped_host_gemm_is_bit_identical(gao, n, prec):
     assert np.array_equal(gao.prog_output(p, dev.index("r")), r_dev)
     gao.prog_destroy(p)
     hp = W.host_input_program(n, seed, outputs=("C", "r", "f"))
-    q = gao.prog_from_workload(hp, gemm_prec=pr)
+    q = gao.prog_from_workload(hp, gemm_prec=pr, tile_cfg=cfg)
     for nm, b in (("A", 0), ("B", 1), ("C0", 2)):
         gao.prog_set_input(q, hp.index(nm), oracle.init_matrix(seed, b, n, n).astype(np.float32))
     gao.prog_run(q, (1 << hp.n_loops) - 1)

@@ -114,6 +114,49 @@ def test_tc_l2_prefetch_changes_no_value(gao, prec, kchunk, cfg):
     assert oracle.rel_err(b["C"], ref["C"]) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec,kchunk,cfg", [("bf16x6", 0, 0), ("bf16x6", 128, 0), ("bf16x3", 0, 0),
+                                            ("bf16x3", 256, 0), ("bf16", 0, 1), ("bf16", 0, 2), ("bf16", 64, 0),
+                                            ("bf16x6", 0, 4)])
+@pytest.mark.parametrize("shape", [(300, 520, 1000), (129, 200, 77), (1, 1, 1), (513, 130, 260), (256, 256, 64)])
+def test_tc_cta_pair_matches_single_cta(gao, prec, kchunk, cfg, shape):
+    """Tile configuration bit 3 runs the GEMM on CTA pairs: 256-row tiles whose M = 256 MMAs
+    read 128 rows of A from each CTA and half of the B tile from each.  Every output element
+    still takes the same products in the same K order, so C is bit-identical to the
+    single-CTA kernel's; ragged shapes put a partial 256-row tile (and 128-row tiles of
+    padding only) at the bottom edge."""
+    M, N, K = shape
+    prog = gemm_program(M, N, K, 4242 + M + K, inplace=False)
+    a, _ = run_gemm(gao, prog, prec, tile_cfg=cfg, kchunk=kchunk)
+    b, st = run_gemm(gao, prog, prec, tile_cfg=cfg | 8, kchunk=kchunk)
+    assert st[1]["launches"] == 3
+    assert np.array_equal(a["C"].view(np.uint32), b["C"].view(np.uint32))
+    ref = oracle.run_program(prog)
+    A, B, C0 = (ref[x] for x in ("A", "B", "C0"))
+    scale = 1.5 * (np.abs(A) @ np.abs(B)) + 0.5 * np.abs(C0)
+    comp = float(np.max(np.abs(b["C"] - ref["C"]) / (scale + 1e-300)))
+    assert comp <= COMP[prec], f"{prec} {shape}: componentwise {comp:.3e}"
+
+
+@pytest.mark.parametrize("n", [384, 520])
+def test_tc_cta_pair_fused_chain(gao, n):
+    """The fused GEMM chain on CTA pairs (C, D = C + 2A, E = D^T, the norm from per-warp
+    partials kept in row-major tile order, the row sums of E) gives the single-CTA bits;
+    n = 520 leaves a 128-row tile of padding in the last pair tile."""
+    prog = W.six_loop(n, 41 + n, outputs=("C", "D", "E", "r", "f"))
+    outs = []
+    for cfg in (0, 8):
+        p = gao.prog_from_workload(prog, gemm_prec=PREC["bf16x6"], tile_cfg=cfg, fuse_chains=gao.FUSE_ON)
+        gao.prog_run(p, 0b111111)
+        outs.append({nm: gao.prog_output(p, prog.index(nm)) for nm in ("C", "D", "E", "r", "f")})
+        gao.prog_destroy(p)
+    for nm in ("C", "D", "E", "r", "f"):
+        assert np.array_equal(outs[0][nm], outs[1][nm]), nm
+    ref = oracle.run_program(prog)
+    for nm in ("C", "D", "E", "r"):
+        assert oracle.rel_err(outs[1][nm], ref[nm]) <= 1e-6, nm
+    assert abs(float(outs[1]["f"][0, 0]) - ref["f"]) <= 1e-6 * ref["f"]
+
+
 def test_tc_l2_prefetch_fused_chain(gao):
     """The fused GEMM chain (C, D = C + 2A, E = D^T, norm) with the prefetch bit gives the
     same bits as without it."""
@@ -304,7 +347,9 @@ def test_prog_autotune_keeps_parity(gao, prec):
     if prec == "bf16x3":
         assert r["kchunk"] in (128, 256, 512, 1024)
     # a GA configuration, or the one in place (0: library defaults) when none beat it
-    assert ((r["tile_cfg"] >> 4) & 15) in (0, 2, 3, 4, 5) and (r["tile_cfg"] & ~0xF7) == 0
+    assert ((r["tile_cfg"] >> 4) & 15) in (0, 2, 3, 4, 5) and (r["tile_cfg"] & ~0xFF) == 0
+    if prec != "bf16":
+        assert not r["tile_cfg"] & 8  # CTA pairs are tuned for plain BF16 only
     gao.prog_run(p, 0b111111)
     ref = oracle.run_program(prog)
     assert oracle.rel_err(gao.prog_output(p, prog.index("C")), ref["C"]) <= TOL[prec]
