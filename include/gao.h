@@ -136,14 +136,14 @@ typedef struct gao_opts {
                                 FP32 SIMT kernel rounds it up to a multiple of 16)          */
     int32_t tile_cfg;        /* tensor-core tile configuration: bits 0-1 tile width (0 default,
                                 1 = 128, 2 = 256 columns; 256 only for plain BF16 without K
-                                chunks, every other variant uses 128), bit 2 L2 prefetch of
-                                the operand tiles 4 K blocks ahead (BF16 variants; changes no
-                                value), bit 3 CTA pairs: 256-row tiles on two SMs that each
-                                load half of every B tile (BF16 variants; changes no value),
+                                chunks and for FP8, every other variant uses 128), bit 2 L2
+                                prefetch of the operand tiles 4 K blocks ahead (BF16 variants;
+                                changes no value), bit 3 CTA pairs: 256-row tiles on two SMs
+                                that each load half of every B tile (changes no value),
                                 bits 4-7 log2 of the raster group (0: default 16).  The
-                                default (0) runs plain BF16 without K chunks on 256 x 256
-                                pair tiles and every other variant on 128 x 128 tiles of
-                                one CTA; prog_autotune picks one                            */
+                                default (0) runs plain BF16 without K chunks and FP8 on
+                                256 x 256 pair tiles and the split precisions on 128 x 128
+                                tiles of one CTA; prog_autotune picks one                   */
     int32_t cpu_threads;     /* OpenMP threads for CPU loops (0: all)                       */
     uint64_t seed;           /* seed of the INIT loop's counter hash                        */
     double timeout_s;        /* wall-clock budget of one prog_run (0: none)                 */
@@ -322,8 +322,8 @@ gao_status ga_run_table(const double *times, int n_genes, const gao_ga_params *p
 /* The Simple GA reused as the tensor-core GEMM's autotuner: a 5-bit gene encodes
  * bits 0-1  raster group of 4, 8, 16 or 32 row tiles per CTA group (L2 reuse order),
  * bits 2-3  split precisions: K chunk of 64, 128, 256 or 512 elements (BF16x6) or 128,
- *           256, 512 or 1024 (BF16x3), all within the stated error bound; plain BF16:
- *           tile width 128 or 256 columns (bit 2) on one CTA or a CTA pair (bit 3),
+ *           256, 512 or 1024 (BF16x3), all within the stated error bound; plain BF16
+ *           and FP8: tile width 128 or 256 columns (bit 2) on one CTA or a CTA pair (bit 3),
  * bit 4     L2 prefetch of the operand tiles (tile_cfg bit 2),
  * and fitness is (measured GEMM time)^(-1/2), the paper's fitness with the kernel time
  * as the benchmark (the GEMM with the loop chain in its epilogue when the program fuses

@@ -26,9 +26,9 @@ gao_status ga_core_pop(int n_genes, const gao_ga_params& p, const PopFn& eval, g
 
 // Tile configuration of a 5-bit autotuning gene for GEMM precision `prec`:
 // bits 0-1 raster group 4/8/16/32 (log2 2..5, stored in tile_cfg bits 4-7); bits 2-3
-// K chunk 64 << v for split precisions, for plain bfloat16 tile width 128/256 (bit 2)
-// and CTA pairs (bit 3, tile_cfg bit 3); bit 4 L2 prefetch of the operand tiles
-// (tile_cfg bit 2).
+// K chunk 64 << v for split precisions, for plain bfloat16 and FP8 tile width 128/256
+// (bit 2) and CTA pairs (bit 3, tile_cfg bit 3); bit 4 L2 prefetch of the operand tiles
+// (tile_cfg bit 2, BF16 variants).
 constexpr int kAutotuneBits = 5;
 inline void autotune_decode(int prec, uint64_t gene, int* kchunk, int* tile_cfg) {
     const int glog = 2 + (int)(gene & 3);
@@ -40,7 +40,7 @@ inline void autotune_decode(int prec, uint64_t gene, int* kchunk, int* tile_cfg)
     } else if (prec == GAO_GEMM_BF16X3) {
         *kchunk = 128 << v;  // 128 .. 1024: the two-term split, not the chunk, sets the error
         bn_sel = 1;
-    } else if (prec == GAO_GEMM_BF16) {
+    } else if (prec == GAO_GEMM_BF16 || prec == GAO_GEMM_FP8) {
         *kchunk = 0;
         bn_sel = ((v & 1) ? 2 : 1) | ((v & 2) ? 8 : 0);
     } else {

@@ -173,6 +173,33 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(cluster_bar)
         : "memory");
 }
+// 3-D tile (the scale-factor blocks of one K block) into this CTA's shared memory, counted on
+// an mbarrier of either CTA of the pair.
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                                 uint32_t cluster_bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+        "%3, %4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(cluster_bar)
+        : "memory");
+}
+// Issued by the pair's first CTA: each CTA's shared memory at this offset into its own tensor
+// memory at taddr (tcgen05.cp .32x128b.warpx4, cta_group::2).
+__device__ __forceinline__ void tmem_cp_pair_32x128b_x4(uint32_t taddr, uint64_t sdesc) {
+    asm volatile("tcgen05.cp.cta_group::2.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+// Block-scaled e4m3 MMA of a pair: M = 256, each CTA's rows scaled by the A factors in its own
+// tensor memory, and every column by the B factors that each CTA holds for all N columns.
+__device__ __forceinline__ void mma_mxf8_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+        : "memory");
+}
 __device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                               uint32_t accumulate) {
     asm volatile(
@@ -295,9 +322,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16() {
 // and 10-12), both K-major, UE8M0 scale factors (bit 23), N >> 3 at bits 17-22, M >> 4 at
 // 24-28; the byte of the scale words used by this MMA (its 32-element K step within the
 // 128-element block) is B's scale id at bits 4-5 and A's at bits 29-30.
-template <int N_>
+template <int N_, int M_ = BM>
 __host__ __device__ constexpr uint32_t idesc_mxf8(int kk) {
-    return ((uint32_t)kk << 4) | (1u << 23) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24) |
+    return ((uint32_t)kk << 4) | (1u << 23) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(M_ >> 4) << 24) |
            ((uint32_t)kk << 29);
 }
 
@@ -350,9 +377,10 @@ constexpr uint32_t kStgBytes = 32 * kStgStride * 4;  // per epilogue warp
 // half goes through the warp's staging block and is then handled row-major, four
 // consecutive columns per lane, so that C0, X, C and D move in full 64-byte row segments;
 // every element is formed with the same operations as in the separate loops.
+template <bool MAYFUSE = true>  // false: the chain code is left out (FP8 never carries one)
 __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, int64_t gcol, const float* v,
                                                float* stg, int lane, double* sq) {
-    const bool fuse = e.fuse != 0;
+    const bool fuse = MAYFUSE && e.fuse != 0;
     float s2 = 0.0f, s3 = 0.0f;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -490,7 +518,6 @@ struct TcCfg {
     static constexpr uint32_t B_TILE = (PAIR ? BN / 2 : BN) * 128;
     static constexpr int TILE_M = PAIR ? 2 * BM : BM;  // rows of a tile
     static constexpr uint32_t STAGE = PA * A_TILE + PB * B_TILE;
-    static constexpr int ACC = 2;  // accumulator buffers: a tile's epilogue overlaps the next tile's MMAs
     // With more than one product, hi.hi accumulates in its own tensor-memory block and
     // the smaller products in a second one, so the large accumulator takes one rounded
     // addition per K step instead of NPROD.
@@ -499,6 +526,9 @@ struct TcCfg {
     // FP8: each stage's scale factors in tensor memory after the accumulators, 4 columns
     // for A's 128 rows and BN / 32 for B's BN columns
     static constexpr int SF_COLS = FP8 ? 4 + BN / 32 : 0;
+    // accumulator buffers: with two, a tile's epilogue overlaps the next tile's MMAs; one
+    // where two do not fit in tensor memory next to the scale factors (FP8, 256 columns)
+    static constexpr int ACC = 2 * BUF_COLS + STAGES * SF_COLS <= 512 ? 2 : 1;
     static constexpr int SF_COL0 = ACC * BUF_COLS;
     static constexpr int COLS = ACC * BUF_COLS + STAGES * SF_COLS;
     static constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256
@@ -514,7 +544,7 @@ struct TcCfg {
     static_assert(BN % 64 == 0 && BN >= 64 && BN <= 256, "BN");
     static_assert(!CHUNKED || BN <= 128, "chunked sums live in registers: BN <= 128");
     static_assert(!FP8 || (!CHUNKED && NPROD == 1 && PA == 1 && PB == 1), "FP8 runs one plane, scaled in the MMA");
-    static_assert(!(PAIR && FP8), "CTA pairs run the bfloat16 variants");
+    static_assert(!CHUNKED || ACC == 2, "K chunks drain the accumulator while the next chunk runs");
 };
 
 // One 128 x BN output tile (row tile tm, column tile tn) of one problem.
@@ -534,6 +564,8 @@ __device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int gr
 struct TileInfo {
     const CUtensorMap* ta;
     const CUtensorMap* tb;
+    const CUtensorMap* tsa;  // FP8 on CTA pairs: scale-factor blocks of A and B (3-D maps)
+    const CUtensorMap* tsb;
     EpiArgs ep;
     int Mp, Np, num_kb, chunk_kb, m0, n0;
     int pf_kb;  // operand tiles are pulled into L2 this many K blocks ahead of their loads (0: off)
@@ -547,11 +579,15 @@ struct OneProblem {
     const CUtensorMap* tb;
     EpiArgs ep;
     int Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, bn, pf_kb, bm;  // bm: rows of a tile
+    const CUtensorMap* tsa = nullptr;
+    const CUtensorMap* tsb = nullptr;
     __device__ __forceinline__ void get(int t, TileInfo& ti) const {
         int tm, tn;
         raster(t, tiles_m, tiles_n, group, tm, tn);
         ti.ta = ta;
         ti.tb = tb;
+        ti.tsa = tsa;
+        ti.tsb = tsb;
         ti.ep = ep;
         ti.Mp = Mp;
         ti.Np = Np;
@@ -583,6 +619,7 @@ struct ProblemTable {
         raster(t - P->tile_start, P->tiles_m, P->tiles_n, P->group, tm, tn);
         ti.ta = &P->ta;
         ti.tb = &P->tb;
+        ti.tsa = ti.tsb = nullptr;
         ti.ep = P->ep;
         ti.Mp = P->Mp;
         ti.Np = P->Np;
@@ -690,7 +727,14 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                         // both CTAs' loads complete on the first CTA's full barrier, which
                         // the first CTA's producer arms with the pair's bytes
                         const uint32_t fb = cluster_addr(full_bar(s), 0);
-                        if (rank == 0) mbar_expect_tx(full_bar(s), 2 * Cfg::STAGE);
+                        if (rank == 0) mbar_expect_tx(full_bar(s), 2 * (Cfg::STAGE + Cfg::SF_STAGE));
+                        if constexpr (FP8) {
+                            // this CTA's rows' scale block, and the blocks of all BN columns (the
+                            // pair's MMA scales each CTA's rows by the B factors in its own memory)
+                            const uint32_t sd = sf_smem + (uint32_t)s * Cfg::SF_STAGE;
+                            tma_load_3d_pair(sd, ti.tsa, 0, kb, a_row / BM, fb);
+                            tma_load_3d_pair(sd + (uint32_t)kSfBlock, ti.tsb, 0, kb, ti.n0 / 128, fb);
+                        }
 #pragma unroll
                         for (int p = 0; p < PA; ++p)
                             tma_load_2d_pair(st + (uint32_t)p * Cfg::A_TILE, ti.ta, kb * KBE, p * ti.Mp + a_row, fb);
@@ -745,8 +789,8 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                 src.get(t, ti);
                 const int nchunks = (ti.num_kb + ti.chunk_kb - 1) / ti.chunk_kb;
                 for (int c = 0; c < nchunks; ++c, ++gc) {
-                    const int ab = gc & 1;
-                    const uint32_t aph = (uint32_t)(gc >> 1) & 1u;
+                    const int ab = ACC == 1 ? 0 : gc & 1;
+                    const uint32_t aph = (uint32_t)(ACC == 1 ? gc : gc >> 1) & 1u;
                     if (!mbar_wait(acce_bar(ab), aph ^ 1u, abort_flag, err)) {
                         ok = false;
                         break;
@@ -769,7 +813,14 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                         // (free again: the MMAs that read them last released the stage)
                         const uint32_t sfa_t = tmem + (uint32_t)(Cfg::SF_COL0 + s * Cfg::SF_COLS);
                         const uint32_t sfb_t = sfa_t + 4u;
-                        if constexpr (FP8) {
+                        if constexpr (FP8 && PAIR) {  // both CTAs' blocks, each into its own memory
+                            const uint32_t sd = sf_smem + (uint32_t)s * Cfg::SF_STAGE;
+                            tmem_cp_pair_32x128b_x4(sfa_t, plain_32x16_desc(sd));
+#pragma unroll
+                            for (int h = 0; h < BN / 128; ++h)
+                                tmem_cp_pair_32x128b_x4(sfb_t + 4u * (uint32_t)h,
+                                                        plain_32x16_desc(sd + (uint32_t)(1 + h) * kSfBlock));
+                        } else if constexpr (FP8) {
                             const uint32_t sd = sf_smem + (uint32_t)s * Cfg::SF_STAGE;
                             tmem_cp_32x128b_x4(sfa_t, plain_32x16_desc(sd));
 #pragma unroll
@@ -788,7 +839,10 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                                 // first product into each accumulator block of a chunk overwrites it
                                 const bool first = kb == kb0 && kk == 0 && (pr == 0 || (Cfg::SPLIT && pr == 1));
                                 const uint32_t dd = d + ((Cfg::SPLIT && pr > 0) ? (uint32_t)BN : 0u);
-                                if constexpr (FP8)
+                                if constexpr (FP8 && PAIR)
+                                    mma_mxf8_pair(dd, ad, bd, idesc_mxf8<BN, Cfg::TILE_M>(kk), sfa_t, sfb_t,
+                                                  first ? 0u : 1u);
+                                else if constexpr (FP8)
                                     mma_mxf8(dd, ad, bd, idesc_mxf8<BN>(kk), sfa_t, sfb_t, first ? 0u : 1u);
                                 else if constexpr (PAIR)
                                     mma_bf16_pair(dd, ad, bd, IDESC, first ? 0u : 1u);
@@ -831,12 +885,15 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
             const int64_t grow = row0 + lane;
             const int n0 = ti.n0;
             double sq = 0.0;  // fused chain: this thread's sum of D^2 over the tile
-            float sum[CHUNKED ? BN / 2 : 1];
+            // K chunks sum in registers; a single accumulator buffer is copied to registers
+            // and released before the stores, so that the next tile's MMAs start at once
+            constexpr bool HOLD = CHUNKED || ACC == 1;
+            float sum[HOLD ? BN / 2 : 1];
 #pragma unroll
-            for (int i = 0; i < (CHUNKED ? BN / 2 : 1); ++i) sum[i] = 0.0f;
+            for (int i = 0; i < (HOLD ? BN / 2 : 1); ++i) sum[i] = 0.0f;
             for (int c = 0; c < nchunks; ++c, ++gc) {
-                const int ab = gc & 1;
-                const uint32_t aph = (uint32_t)(gc >> 1) & 1u;
+                const int ab = ACC == 1 ? 0 : gc & 1;
+                const uint32_t aph = (uint32_t)(ACC == 1 ? gc : gc >> 1) & 1u;
                 if (c == (nchunks > 2 ? nchunks - 2 : 0) && grow < ep.M) {
                     // the final store reads this thread's C0 (and X) row segment: start
                     // bringing it into L2 a chunk or two ahead
@@ -871,8 +928,11 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                     if constexpr (CHUNKED) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) sum[g * 32 + i] += v[i];
+                    } else if constexpr (HOLD) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) sum[g * 32 + i] = v[i];
                     } else {
-                        store_staged32(ep, row0, (int64_t)n0 + colbase + g * 32, v, stg, lane, &sq);
+                        store_staged32<!FP8>(ep, row0, (int64_t)n0 + colbase + g * 32, v, stg, lane, &sq);
                     }
                 }
                 tc_fence_before();
@@ -882,11 +942,11 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                     else mbar_arrive(acce_bar(ab));
                 }
             }
-            if constexpr (CHUNKED) {
+            if constexpr (HOLD) {
                 if (ok) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        store_staged32(ep, row0, (int64_t)n0 + colbase + g * 32, sum + g * 32, stg, lane, &sq);
+                        store_staged32<!FP8>(ep, row0, (int64_t)n0 + colbase + g * 32, sum + g * 32, stg, lane, &sq);
                 }
             }
             if (ep.fuse && ok) {  // fixed butterfly over the warp's rows, one partial per warp
@@ -925,13 +985,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 }
 
 // The same GEMM on CTA pairs: tiles of 256 x BN rows (tiles_m counts 256-row tiles).
-template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED>
+// FP8: tmSA / tmSB are the scale-factor blocks of A and B (unused otherwise).
+template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTc, 1)
-    gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EpiArgs ep,
+    gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmSA, const __grid_constant__ CUtensorMap tmSB, EpiArgs ep,
                         int Mp, int Np, int num_kb, int chunk_kb, int tiles_m, int tiles_n, int group, int pf_kb,
                         int* err) {
-    const OneProblem src{&tmA, &tmB, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, BN, pf_kb, 2 * BM};
-    gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, false, true>(src, tiles_m * tiles_n, err);
+    const OneProblem src{&tmA,  &tmB, ep, Mp, Np, num_kb, chunk_kb, tiles_m, tiles_n, group, BN, pf_kb, 2 * BM,
+                         &tmSA, &tmSB};
+    gemm_tc_persistent<BN, PA, PB, NPROD, STAGES, CHUNKED, FP8, true>(src, tiles_m * tiles_n, err);
 }
 
 template <int BN, int PA, int PB, int NPROD, int STAGES, bool CHUNKED, bool FP8>
@@ -1188,6 +1251,23 @@ bool get_encode(std::string* why) {
 
 // 2-D map over a row-major plane stack: `inner` elements per row (bf16, or e4m3 as
 // bytes), box = one 128-byte row segment x box_rows rows, 128-byte swizzle.
+// Scale-factor blocks [blocks][kbs][512 bytes] as a 3-D tensor of 32-bit words: a box is one
+// K block's 512-byte block of box_blocks consecutive row (or column) blocks.
+bool make_sf_map(CUtensorMap* map, void* base, int64_t kbs, int64_t blocks, int box_blocks, std::string* why) {
+    cuuint64_t gdim[3] = {(cuuint64_t)(kSfBlock / 4), (cuuint64_t)kbs, (cuuint64_t)blocks};
+    cuuint64_t gstride[2] = {(cuuint64_t)kSfBlock, (cuuint64_t)(kbs * kSfBlock)};
+    cuuint32_t box[3] = {(cuuint32_t)(kSfBlock / 4), 1, (cuuint32_t)box_blocks};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, base, gdim, gstride, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        if (why) *why = "cuTensorMapEncodeTiled (scale factors) failed with code " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+
 bool make_map(CUtensorMap* map, void* base, int64_t inner, int64_t rows, int box_rows, bool fp8, std::string* why) {
     const int esz = fp8 ? 1 : 2;
     cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
@@ -1228,11 +1308,13 @@ cudaError_t launch_mma(const CUtensorMap& ta, const CUtensorMap& tb, const EpiAr
 
 
 // The pair kernel: Mp a multiple of 256; one cluster of two CTAs per two SMs.
-template <int BN, int P, int NPROD, int STAGES, bool CHUNKED>
+template <int BN, int P, int NPROD, int STAGES, bool CHUNKED, bool FP8 = false>
 cudaError_t launch_mma_pair(const CUtensorMap& ta, const CUtensorMap& tb, const EpiArgs& ep, int Mp, int Np,
-                            int num_kb, int chunk_kb, int group, int pf_kb, int* err, cudaStream_t st) {
-    using Cfg = TcCfg<BN, P, P, NPROD, STAGES, CHUNKED, false, true>;
-    auto kern = gemm_tc_pair_kernel<BN, P, P, NPROD, STAGES, CHUNKED>;
+                            int num_kb, int chunk_kb, int group, int pf_kb, int* err, cudaStream_t st,
+                            const CUtensorMap* tsa = nullptr, const CUtensorMap* tsb = nullptr) {
+    using Cfg = TcCfg<BN, P, P, NPROD, STAGES, CHUNKED, FP8, true>;
+    auto kern = gemm_tc_pair_kernel<BN, P, P, NPROD, STAGES, CHUNKED, FP8>;
+    if (FP8 && !(tsa && tsb)) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
@@ -1259,13 +1341,14 @@ cudaError_t launch_mma_pair(const CUtensorMap& ta, const CUtensorMap& tb, const 
         max_clusters = std::min(n, sm_count() / 2);
     }
     const int64_t clusters = std::min<int64_t>(total, (int64_t)max_clusters);
-    kern<<<(unsigned)(2 * clusters), kThreadsTc, Cfg::SMEM, st>>>(ta, tb, ep, Mp, Np, num_kb, chunk_kb, tiles_m,
-                                                                  tiles_n, group, pf_kb, err);
+    kern<<<(unsigned)(2 * clusters), kThreadsTc, Cfg::SMEM, st>>>(ta, tb, FP8 ? *tsa : ta, FP8 ? *tsb : tb, ep, Mp,
+                                                                  Np, num_kb, chunk_kb, tiles_m, tiles_n, group,
+                                                                  pf_kb, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K,
-                            float alpha, float beta, int group, void* scratch, size_t scratch_bytes, int* err,
+                            float alpha, float beta, int tile_cfg, void* scratch, size_t scratch_bytes, int* err,
                             cudaStream_t st, TcEvents& ev, std::string* why);
 
 }  // namespace
@@ -1273,12 +1356,13 @@ cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const floa
 // FP8 scratch: q(A) [Mp][Kp], q(B^T) [Np][Kp], then the scale-factor blocks of A
 // [Mp / 128][Kp / 128][512 bytes] and of B [Np / 128][Kp / 128][512 bytes]
 struct Fp8Layout {
-    int64_t Mp, Np, Kp, kbs;
+    int64_t Mp, Mt, Np, Kp, kbs;  // Mp: stored rows (whole CTA-pair tiles); Mt: rows of 128-row tiles
     size_t qa, qb, sa, sb, total;
 };
 Fp8Layout fp8_layout(int64_t M, int64_t N, int64_t K) {
     Fp8Layout L;
-    L.Mp = ru(std::max<int64_t>(M, 1), BM);
+    L.Mp = ru(std::max<int64_t>(M, 1), 2 * BM);
+    L.Mt = ru(std::max<int64_t>(M, 1), BM);
     L.Np = ru(std::max<int64_t>(N, 1), 256);
     L.Kp = ru(std::max<int64_t>(K, 1), BK8);
     L.kbs = L.Kp / BK8;
@@ -1348,8 +1432,8 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
             if (why) *why = "chains and row blocks are not supported on the FP8 path";
             return cudaErrorInvalidValue;
         }
-        return launch_gemm_fp8(C, A, B, C0, M, N, K, alpha, beta, tc_group_of(tile_cfg), scratch, scratch_bytes, err,
-                               st, ev, why);
+        return launch_gemm_fp8(C, A, B, C0, M, N, K, alpha, beta, tile_cfg, scratch, scratch_bytes, err, st, ev,
+                               why);
     }
     const int P = planes_of(prec);
     const int64_t Mlay = part ? part->m_layout : M;
@@ -1480,8 +1564,14 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
 
 namespace {
 cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N, int64_t K,
-                            float alpha, float beta, int group, void* scratch, size_t scratch_bytes, int* err,
+                            float alpha, float beta, int tile_cfg, void* scratch, size_t scratch_bytes, int* err,
                             cudaStream_t st, TcEvents& ev, std::string* why) {
+    const int group = tc_group_of(tile_cfg);
+    // bits 0-1: 1 = 128, 2 = 256 columns per tile; bit 3: CTA pairs (256 rows); default (0):
+    // 256 x 256 tiles on CTA pairs
+    const int bn_sel = tile_cfg & 3;
+    const bool pair = (tile_cfg & 8) != 0 || bn_sel == 0;
+    const int bn = bn_sel == 1 ? 128 : 256;
     const Fp8Layout L = fp8_layout(M, N, K);
     if (L.total > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
         if (why) *why = "FP8 scratch too small or misaligned";
@@ -1506,14 +1596,29 @@ cudaError_t launch_gemm_fp8(float* C, const float* A, const float* B, const floa
     }
     CUtensorMap ta, tb;
     if (!make_map(&ta, qa, L.Kp, L.Mp, BM, true, why)) return cudaErrorInvalidValue;
-    if (!make_map(&tb, qb, L.Kp, L.Np, 128, true, why)) return cudaErrorInvalidValue;
-    // the epilogue's sa / sb carry the scale-factor blocks (read by the producer's bulk copies)
+    if (!make_map(&tb, qb, L.Kp, L.Np, pair ? bn / 2 : bn, true, why)) return cudaErrorInvalidValue;
+    // the epilogue's sa / sb carry the scale-factor blocks (read by the producer's bulk copies
+    // on one CTA; CTA pairs load them through the 3-D maps)
     EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
                (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0,
                reinterpret_cast<const float*>(sa), reinterpret_cast<const float*>(sb), (int)L.kbs, (int)L.Np};
     if (ev.k0) record_timing(ev.k0, st);
     const int kbs = (int)L.kbs;
-    cudaError_t e = launch_mma<128, 1, 1, 6, false, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, kbs, kbs, group, 0, err, st);
+    cudaError_t e;
+    if (pair) {
+        CUtensorMap tsa, tsb;
+        if (!make_sf_map(&tsa, sa, L.kbs, L.Mp / 128, 1, why)) return cudaErrorInvalidValue;
+        if (!make_sf_map(&tsb, sb, L.kbs, L.Np / 128, bn / 128, why)) return cudaErrorInvalidValue;
+        e = bn == 256 ? launch_mma_pair<256, 1, 1, 6, false, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, kbs, kbs, group, 0,
+                                                                   err, st, &tsa, &tsb)
+                      : launch_mma_pair<128, 1, 1, 8, false, true>(ta, tb, ep, (int)L.Mp, (int)L.Np, kbs, kbs, group, 0,
+                                                                   err, st, &tsa, &tsb);
+    } else {
+        e = bn == 256 ? launch_mma<256, 1, 1, 4, false, true>(ta, tb, ep, (int)L.Mt, (int)L.Np, kbs, kbs, group, 0, err,
+                                                              st)
+                      : launch_mma<128, 1, 1, 6, false, true>(ta, tb, ep, (int)L.Mt, (int)L.Np, kbs, kbs, group, 0, err,
+                                                              st);
+    }
     if (e != cudaSuccess) return e;
     ev.launches += 1;
     if (ev.k1) record_timing(ev.k1, st);
@@ -1587,7 +1692,7 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
         if (!make_map(&prob->tb, qb, L.Kp, L.Np, 128, true, why)) return cudaErrorInvalidValue;
         prob->ep = EpiArgs{C, C0, (int)M, (int)N, alpha, beta, vec, reinterpret_cast<const float*>(sa),
                            reinterpret_cast<const float*>(sb), (int)L.kbs, (int)L.Np};
-        prob->Mp = (int)L.Mp;
+        prob->Mp = (int)L.Mt;  // one plane: Mp only sets the 128-row tiles
         prob->Np = (int)L.Np;
         prob->num_kb = (int)L.kbs;
         prob->chunk_kb = prob->num_kb;  // one accumulation over K: the scales act inside the MMA

@@ -376,11 +376,15 @@ def test_prog_autotune_fused_chain(gao):
     gao.prog_destroy(q)
 
 
-@pytest.mark.parametrize("M,N,K", [(200, 136, 300), (128, 128, 128), (257, 384, 1000)])
-def test_fp8_exact_on_small_integers(gao, M, N, K):
+@pytest.mark.parametrize("cfg", [0, 1, 2, 9])
+@pytest.mark.parametrize("M,N,K", [(200, 136, 300), (128, 128, 128), (257, 384, 1000), (520, 260, 260)])
+def test_fp8_exact_on_small_integers(gao, M, N, K, cfg):
     """Operands whose entries are integers in [-4, 4] (rows of A times 2^(i mod 7 - 3), columns
     of B times 2^(j mod 5 - 2)) are exact in e4m3 under power-of-two block scales, their
-    products and sums exact in binary32: C = 1.5 A B + 0.5 C0 must come out bit for bit."""
+    products and sums exact in binary32: C = 1.5 A B + 0.5 C0 must come out bit for bit, on
+    256 x 256 CTA-pair tiles (tile configuration 0, each CTA's rows scaled from its own tensor
+    memory, one accumulator), 128 x 128 and 128 x 256 tiles of one CTA (1, 2) and 256 x 128
+    pair tiles (9)."""
     rng = np.random.default_rng(M + N + K)
     ra = 2.0 ** (np.arange(M) % 7 - 3)
     cb = 2.0 ** (np.arange(N) % 5 - 2)
@@ -391,7 +395,7 @@ def test_fp8_exact_on_small_integers(gao, M, N, K):
     bufs = [B_("A", M, K, role=W.INPUT), B_("B", K, N, role=W.INPUT), B_("C0", M, N, role=W.INPUT),
             B_("C", M, N, role=W.OUTPUT)]
     prog = W.Program("fp8_int", bufs, [L_(W.GEMM, [0, 1, 2], [3], 1.5, 0.5)], 0)
-    p = gao.prog_from_workload(prog, gemm_prec=PREC["fp8"])
+    p = gao.prog_from_workload(prog, gemm_prec=PREC["fp8"], tile_cfg=cfg)
     for nm, v in (("A", A), ("B", B), ("C0", C0)):
         gao.prog_set_input(p, prog.index(nm), v)
     gao.prog_run(p, 1)
@@ -399,3 +403,25 @@ def test_fp8_exact_on_small_integers(gao, M, N, K):
     gao.prog_destroy(p)
     want = (1.5 * (A.astype(np.float64) @ B.astype(np.float64)) + 0.5 * C0).astype(np.float32)
     assert np.array_equal(C, want)
+
+
+@pytest.mark.parametrize("shape", [(300, 520, 1000), (129, 200, 77), (1, 1, 1), (513, 130, 260), (256, 256, 64)])
+def test_fp8_cta_pair_matches_single_cta(gao, shape):
+    """FP8 on 256 x 256 CTA-pair tiles (default), 256 x 128 pair tiles (9) and 128 x 128 or
+    128 x 256 tiles of one CTA (1, 2): the same e4m3 codes, scales and K order for every
+    element, so the same bits; ragged shapes leave padding rows and columns and a 128-row
+    tile of padding in the last pair tile."""
+    M, N, K = shape
+    prog = gemm_program(M, N, K, 777 + M + N, inplace=False)
+    a, _ = run_gemm(gao, prog, "fp8", tile_cfg=1)
+    for cfg in (2, 9):
+        c, _ = run_gemm(gao, prog, "fp8", tile_cfg=cfg)
+        assert np.array_equal(a["C"].view(np.uint32), c["C"].view(np.uint32)), cfg
+    b, st = run_gemm(gao, prog, "fp8", tile_cfg=0)
+    assert st[1]["launches"] == 3
+    assert np.array_equal(a["C"].view(np.uint32), b["C"].view(np.uint32))
+    ref = oracle.run_program(prog)
+    A, B, C0 = (ref[x] for x in ("A", "B", "C0"))
+    scale = 1.5 * (np.abs(A) @ np.abs(B)) + 0.5 * np.abs(C0)
+    comp = float(np.max(np.abs(b["C"] - ref["C"]) / (scale + 1e-300)))
+    assert comp <= COMP["fp8"], f"{shape}: componentwise {comp:.3e}"
