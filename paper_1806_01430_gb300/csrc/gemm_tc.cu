@@ -200,15 +200,6 @@ __device__ __forceinline__ void mma_mxf8_pair(uint32_t d_tmem, uint64_t adesc, u
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
         : "memory");
 }
-__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                              uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
 // Completion of the pair's MMAs signalled on the mbarrier at the same offset in both CTAs.
 __device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
     asm volatile(
@@ -248,15 +239,33 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+// The same MMA with the A collector buffer (coll as in prod_coll; a constant after unrolling),
+// on one CTA or (PAIR) on a CTA pair.
+#define GAO_MMA_F16(CG, COLL)                                                                               \
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"                                        \
+                 "tcgen05.mma.cta_group::" CG ".kind::f16" COLL " [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem), \
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)                                        \
+                 : "memory")
+template <bool PAIR>
+__device__ __forceinline__ void mma_bf16_coll(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate, int coll) {
+    if constexpr (PAIR) {
+        switch (coll) {
+            case 1: GAO_MMA_F16("2", ".collector::a::fill"); break;
+            case 2: GAO_MMA_F16("2", ".collector::a::use"); break;
+            case 3: GAO_MMA_F16("2", ".collector::a::lastuse"); break;
+            default: GAO_MMA_F16("2", "");
+        }
+    } else {
+        switch (coll) {
+            case 1: GAO_MMA_F16("1", ".collector::a::fill"); break;
+            case 2: GAO_MMA_F16("1", ".collector::a::use"); break;
+            case 3: GAO_MMA_F16("1", ".collector::a::lastuse"); break;
+            default: GAO_MMA_F16("1", "");
+        }
+    }
 }
+#undef GAO_MMA_F16
 
 // Block-scaled e4m3 MMA: A's and B's UE8M0 scale factors are read from tensor memory at
 // sfa / sfb (the byte of each 32-bit word chosen by the instruction descriptor's scale ids).
@@ -341,20 +350,32 @@ __device__ __forceinline__ uint64_t plain_32x16_desc(uint32_t saddr) {
 constexpr int kSfBlock = 512;
 
 // Products (plane of A, plane of B); planes: 0 = hi, 1 = mid (x6) or lo (x3), 2 = lo.
-//   x1: hi.hi;  x3: hi.hi, hi.lo, lo.hi;  x6: hi.hi, hi.mid, mid.hi, mid.mid, hi.lo, lo.hi
+//   x1: hi.hi;  x3: hi.hi, hi.lo, lo.hi;  x6: hi.hi, hi.mid, hi.lo, mid.hi, mid.mid, lo.hi
+// Products that share A's plane follow one another, so that the tensor core's A collector
+// buffer holds the plane across them (read from shared memory once, not once per product).
 __host__ __device__ constexpr int prod_a(int nprod, int i) {
-    return nprod == 6 ? (i == 2 || i == 3 ? 1 : (i == 5 ? 2 : 0)) : (nprod == 3 ? (i == 2 ? 1 : 0) : 0);
+    return nprod == 6 ? (i < 3 ? 0 : (i < 5 ? 1 : 2)) : (nprod == 3 ? (i == 2 ? 1 : 0) : 0);
 }
 __host__ __device__ constexpr int prod_b(int nprod, int i) {
-    return nprod == 6 ? (i == 1 || i == 3 ? 1 : (i == 4 ? 2 : 0)) : (nprod == 3 ? (i == 1 ? 1 : 0) : 0);
+    return nprod == 6 ? (i == 1 || i == 4 ? 1 : (i == 2 ? 2 : 0)) : (nprod == 3 ? (i == 1 ? 1 : 0) : 0);
 }
-static_assert(prod_a(6, 0) == 0 && prod_b(6, 0) == 0 && prod_a(6, 1) == 0 && prod_b(6, 1) == 1 && prod_a(6, 2) == 1 &&
-                  prod_b(6, 2) == 0 && prod_a(6, 3) == 1 && prod_b(6, 3) == 1 && prod_a(6, 4) == 0 &&
-                  prod_b(6, 4) == 2 && prod_a(6, 5) == 2 && prod_b(6, 5) == 0,
+// A collector use of product i: 0 none, 1 fill (read A, keep it), 2 use, 3 last use.
+__host__ __device__ constexpr int prod_coll(int nprod, int i) {
+    return nprod == 6 ? (i == 0 || i == 3 ? 1 : (i == 1 ? 2 : (i == 2 || i == 4 ? 3 : 0)))
+                      : (nprod == 3 ? (i == 0 ? 1 : (i == 1 ? 3 : 0)) : 0);
+}
+static_assert(prod_a(6, 0) == 0 && prod_b(6, 0) == 0 && prod_a(6, 1) == 0 && prod_b(6, 1) == 1 && prod_a(6, 2) == 0 &&
+                  prod_b(6, 2) == 2 && prod_a(6, 3) == 1 && prod_b(6, 3) == 0 && prod_a(6, 4) == 1 &&
+                  prod_b(6, 4) == 1 && prod_a(6, 5) == 2 && prod_b(6, 5) == 0,
               "x6 product table");
 static_assert(prod_a(3, 0) == 0 && prod_b(3, 0) == 0 && prod_a(3, 1) == 0 && prod_b(3, 1) == 1 && prod_a(3, 2) == 1 &&
                   prod_b(3, 2) == 0,
               "x3 product table");
+// every collector run: a fill, then uses of the same A plane, ended by a last use
+static_assert(prod_coll(6, 0) == 1 && prod_coll(6, 1) == 2 && prod_coll(6, 2) == 3 && prod_coll(6, 3) == 1 &&
+                  prod_coll(6, 4) == 3 && prod_coll(6, 5) == 0 && prod_coll(3, 0) == 1 && prod_coll(3, 1) == 3 &&
+                  prod_coll(3, 2) == 0 && prod_coll(1, 0) == 0,
+              "collector table");
 
 
 
@@ -393,17 +414,31 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
         const int cq = lane & 3;
         const int64_t c = gcol + 16 * h + 4 * cq;
         const bool vec = e.vec && c + 3 < e.N;
-        // all of this half's full-width C0 (and X) loads in flight before any is used
+        // all of this half's C0 (and X) loads in flight before any is used: full-width where
+        // the row segment is aligned, else element by element (rows of any length N)
         float4 c0p[4], xp[4];
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const int64_t grow = row0 + it * 8 + (lane >> 2);
             c0p[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             xp[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (vec && grow < e.M) {
+            if (grow < e.M) {
                 const int64_t base = grow * (int64_t)e.N + c;
-                if (e.beta != 0.0f) c0p[it] = __ldg(reinterpret_cast<const float4*>(e.C0 + base));
-                if (fuse) xp[it] = __ldg(reinterpret_cast<const float4*>(e.X + base));
+                if (vec) {
+                    if (e.beta != 0.0f) c0p[it] = __ldg(reinterpret_cast<const float4*>(e.C0 + base));
+                    if (fuse) xp[it] = __ldg(reinterpret_cast<const float4*>(e.X + base));
+                } else {
+                    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f}, u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (c + q < e.N) {
+                            if (e.beta != 0.0f) t[q] = __ldg(e.C0 + base + q);
+                            if (fuse) u[q] = __ldg(e.X + base + q);
+                        }
+                    }
+                    c0p[it] = make_float4(t[0], t[1], t[2], t[3]);
+                    xp[it] = make_float4(u[0], u[1], u[2], u[3]);
+                }
             }
         }
         float dd[4][4];  // fused chain: this lane's D values, staged back for the transposed store
@@ -430,14 +465,16 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
                 }
                 *reinterpret_cast<float4*>(e.C + base) = make_float4(cv[0], cv[1], cv[2], cv[3]);
             } else {
+                const float c0v[4] = {c0p[it].x, c0p[it].y, c0p[it].z, c0p[it].w};
+                const float x4[4] = {xp[it].x, xp[it].y, xp[it].z, xp[it].w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     cv[q] = 0.0f;
                     if (c + q < e.N) {
                         float o = e.alpha * av[q];
-                        if (e.beta != 0.0f) o = fmaf(e.beta, __ldg(e.C0 + base + q), o);
+                        if (e.beta != 0.0f) o = fmaf(e.beta, c0v[q], o);
                         cv[q] = o;
-                        if (fuse) xv[q] = __ldg(e.X + base + q);
+                        if (fuse) xv[q] = x4[q];
                         e.C[base + q] = o;
                     }
                 }
@@ -844,10 +881,8 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                                                   first ? 0u : 1u);
                                 else if constexpr (FP8)
                                     mma_mxf8(dd, ad, bd, idesc_mxf8<BN>(kk), sfa_t, sfb_t, first ? 0u : 1u);
-                                else if constexpr (PAIR)
-                                    mma_bf16_pair(dd, ad, bd, IDESC, first ? 0u : 1u);
                                 else
-                                    mma_bf16(dd, ad, bd, IDESC, first ? 0u : 1u);
+                                    mma_bf16_coll<PAIR>(dd, ad, bd, IDESC, first ? 0u : 1u, prod_coll(NPROD, pr));
                             }
                         }
                         if constexpr (PAIR) mma_commit_pair(empty_bar(s));  // frees the stage in both CTAs
