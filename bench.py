@@ -687,6 +687,10 @@ def sub_results(args, gao, torch, stream):
         out["twelve_loop"] = twelve_result(args, gao, torch, stream)
     except Exception as e:
         out["twelve_loop"] = {"error": str(e)}
+    try:
+        out["six_loop_fused"] = six_fused_result(args, gao, torch, stream)
+    except Exception as e:
+        out["six_loop_fused"] = {"error": str(e)}
     if args.search:
         try:
             out["six_loop_search"] = search_result(args, gao, stream, 4096)
@@ -794,6 +798,27 @@ def twelve_result(args, gao, torch, stream, m=16384, k=4096, prec="bf16x3"):
             "peak_source": how, "rel_err_sampled": err, "loop_gbs": gbs,
             "fp8": {"gemm_kernel_tflops": kern8, "frac_of_peak": kern8 / peak8, "peak_source": how8,
                     "rel_err_sampled": err8}}
+
+
+def six_fused_result(args, gao, torch, stream, n=4096, prec="bf16x6"):
+    """The six-loop program at n = 4096 under the all-GPU gene with its chain (scale-add,
+    transpose, row sums, Frobenius norm) in the BF16x6 GEMM's epilogue, library default
+    tile configuration: program and GEMM-kernel TFLOP/s, the kernel's fraction of the
+    burst peak / 6, and the sampled error of C."""
+    prog = W.six_loop(n, W.six_loop_seed(n), outputs=("C", "D", "E", "r", "f"))
+    flops = prog.gemm_flops()
+    mask = (1 << prog.n_loops) - 1
+    p = gao.prog_from_workload(prog, gemm_prec=PREC[prec], stream=stream, fuse_chains=True)
+    steps = 20
+    T = timed_steps(gao, p, mask, steps, 3, stream, 1, 1, Clocks(0))
+    gao.prog_run(p, mask)
+    err = sampled_gemm_err(gao.prog_output(p, prog.index("C")), prog.seed, False, n, n, n, 1)
+    gao.prog_destroy(p)
+    peak, how, _ = tensor_peak(prec)
+    kern = flops / (statistics.mean(T["kern_ms"]) / 1e3) / 1e12
+    return {"workload": f"six_loop_n{n}_all_gpu_{prec}_fused", "program_tflops": flops / (T["ms"] / 1e3) / 1e12,
+            "ms_per_step": T["ms"], "gemm_kernel_tflops": kern, "gemm_kernel_frac_of_peak": kern / peak,
+            "peak_source": how, "rel_err_sampled": err}
 
 
 # ---- six-loop and twelve-loop lines ------------------------------------------------------------------
