@@ -395,9 +395,10 @@ constexpr uint32_t kStgBytes = 32 * kStgStride * 4;  // per epilogue warp
 // Final values of 32 columns [gcol, gcol + 32) of the warp's 32 rows (row0 + lane holds
 // v[0..31], a row per lane as tensor memory delivers them): alpha v + beta C0 stored to C,
 // and for a fused chain D = C + alpha2 X, E = D^T and the running sum of D^2.  Each 32 x 16
-// half goes through the warp's staging block and is then handled row-major, four
-// consecutive columns per lane, so that C0, X, C and D move in full 64-byte row segments;
-// every element is formed with the same operations as in the separate loops.
+// half goes through the warp's staging block and is then handled row-major -- four
+// consecutive columns per lane in 16-byte accesses where rows are 16-byte aligned, one
+// column per lane (16 lanes per row) elsewhere -- so that C0, X, C and D move in 64-byte
+// row segments; every element is formed with the same operations as in the separate loops.
 template <bool MAYFUSE = true>  // false: the chain code is left out (FP8 never carries one)
 __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, int64_t gcol, const float* v,
                                                float* stg, int lane, double* sq) {
@@ -411,104 +412,114 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
             *reinterpret_cast<float4*>(stg + lane * kStgStride + 4 * j) =
                 make_float4(v[16 * h + 4 * j], v[16 * h + 4 * j + 1], v[16 * h + 4 * j + 2], v[16 * h + 4 * j + 3]);
         __syncwarp();
-        const int cq = lane & 3;
-        const int64_t c = gcol + 16 * h + 4 * cq;
-        const bool vec = e.vec && c + 3 < e.N;
-        // all of this half's C0 (and X) loads in flight before any is used: full-width where
-        // the row segment is aligned, else element by element (rows of any length N)
-        float4 c0p[4], xp[4];
+        if (e.vec) {
+            // rows of a multiple of four floats, 16-byte aligned: lane (row group lane / 4,
+            // quadruple lane % 4) moves four consecutive columns of rows lane / 4 + 8 it in
+            // 16-byte accesses (a quadruple is wholly inside or outside the N columns)
+            const int cq = lane & 3;
+            const int64_t c = gcol + 16 * h + 4 * cq;
+            const bool cin = c < e.N;
+            // all of this half's C0 (and X) loads in flight before any is used
+            float4 c0p[4], xp[4];
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-            const int64_t grow = row0 + it * 8 + (lane >> 2);
-            c0p[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            xp[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (grow < e.M) {
-                const int64_t base = grow * (int64_t)e.N + c;
-                if (vec) {
+            for (int it = 0; it < 4; ++it) {
+                const int64_t grow = row0 + it * 8 + (lane >> 2);
+                c0p[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                xp[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (cin && grow < e.M) {
+                    const int64_t base = grow * (int64_t)e.N + c;
                     if (e.beta != 0.0f) c0p[it] = __ldg(reinterpret_cast<const float4*>(e.C0 + base));
                     if (fuse) xp[it] = __ldg(reinterpret_cast<const float4*>(e.X + base));
-                } else {
-                    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f}, u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (c + q < e.N) {
-                            if (e.beta != 0.0f) t[q] = __ldg(e.C0 + base + q);
-                            if (fuse) u[q] = __ldg(e.X + base + q);
-                        }
-                    }
-                    c0p[it] = make_float4(t[0], t[1], t[2], t[3]);
-                    xp[it] = make_float4(u[0], u[1], u[2], u[3]);
                 }
             }
-        }
-        float dd[4][4];  // fused chain: this lane's D values, staged back for the transposed store
+            float dd[4][4];  // fused chain: this lane's D values, staged back for the transposed store
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-            const int r = it * 8 + (lane >> 2);
-            const int64_t grow = row0 + r;
+            for (int it = 0; it < 4; ++it) {
+                const int r = it * 8 + (lane >> 2);
+                const int64_t grow = row0 + r;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dd[it][q] = 0.0f;
-            if (grow >= e.M) continue;
-            const float4 a = *reinterpret_cast<const float4*>(stg + r * kStgStride + 4 * cq);
-            const float av[4] = {a.x, a.y, a.z, a.w};
-            const int64_t base = grow * (int64_t)e.N + c;
-            const bool full = vec;
-            float cv[4], xv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            if (full) {
-                const float4 c0 = c0p[it];
-                if (fuse) xv[0] = xp[it].x, xv[1] = xp[it].y, xv[2] = xp[it].z, xv[3] = xp[it].w;
-                const float c0v[4] = {c0.x, c0.y, c0.z, c0.w};
+                for (int q = 0; q < 4; ++q) dd[it][q] = 0.0f;
+                if (!cin || grow >= e.M) continue;
+                const float4 a = *reinterpret_cast<const float4*>(stg + r * kStgStride + 4 * cq);
+                const float av[4] = {a.x, a.y, a.z, a.w};
+                const float c0v[4] = {c0p[it].x, c0p[it].y, c0p[it].z, c0p[it].w};
+                const float xv[4] = {xp[it].x, xp[it].y, xp[it].z, xp[it].w};
+                const int64_t base = grow * (int64_t)e.N + c;
+                float cv[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     cv[q] = e.alpha * av[q];
                     if (e.beta != 0.0f) cv[q] = fmaf(e.beta, c0v[q], cv[q]);
                 }
                 *reinterpret_cast<float4*>(e.C + base) = make_float4(cv[0], cv[1], cv[2], cv[3]);
-            } else {
-                const float c0v[4] = {c0p[it].x, c0p[it].y, c0p[it].z, c0p[it].w};
-                const float x4[4] = {xp[it].x, xp[it].y, xp[it].z, xp[it].w};
+                if (fuse) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    cv[q] = 0.0f;
-                    if (c + q < e.N) {
-                        float o = e.alpha * av[q];
-                        if (e.beta != 0.0f) o = fmaf(e.beta, c0v[q], o);
-                        cv[q] = o;
-                        if (fuse) xv[q] = x4[q];
-                        e.C[base + q] = o;
-                    }
-                }
-            }
-            if (fuse) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) dd[it][q] = fmaf(e.alpha2, xv[q], cv[q]);  // D = C + alpha2 X, one rounding
-                if (full) {
+                    for (int q = 0; q < 4; ++q) dd[it][q] = fmaf(e.alpha2, xv[q], cv[q]);  // D = C + alpha2 X, one rounding
                     *reinterpret_cast<float4*>(e.D + base) = make_float4(dd[it][0], dd[it][1], dd[it][2], dd[it][3]);
-                } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (c + q < e.N) e.D[base + q] = dd[it][q];
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (c + q < e.N) {
+                    for (int q = 0; q < 4; ++q) {
                         if (q & 1) s3 = fmaf(dd[it][q], dd[it][q], s3);
                         else s2 = fmaf(dd[it][q], dd[it][q], s2);
                     }
                 }
             }
+            if (fuse) {
+                __syncwarp();
+#pragma unroll
+                for (int it = 0; it < 4; ++it) {
+                    const int r = it * 8 + (lane >> 2);
+                    *reinterpret_cast<float4*>(stg + r * kStgStride + 4 * cq) =
+                        make_float4(dd[it][0], dd[it][1], dd[it][2], dd[it][3]);
+                }
+            }
+        } else {
+            // rows of any length: lane (j = lane % 16, rh = lane / 16) takes column j of this
+            // half in rows rh, rh + 2, ..., rh + 30, so that every access of the warp covers two
+            // 64-byte row segments whatever the rows' alignment; the loads of eight rows go out
+            // before any is used; D goes back into the element's own staging slot (its lane
+            // owns it)
+            const int j = lane & 15, rh = lane >> 4;
+            const int64_t col = gcol + 16 * h + j;
+            const bool cin = col < e.N;
+#pragma unroll 1
+            for (int b8 = 0; b8 < 2; ++b8) {
+                float t[8], u[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int64_t grow = row0 + rh + 2 * (8 * b8 + k);
+                    t[k] = 0.0f;
+                    u[k] = 0.0f;
+                    if (cin && grow < e.M) {
+                        const int64_t base = grow * (int64_t)e.N + col;
+                        if (e.beta != 0.0f) t[k] = __ldg(e.C0 + base);
+                        if (fuse) u[k] = __ldg(e.X + base);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int r = rh + 2 * (8 * b8 + k);
+                    const int64_t grow = row0 + r;
+                    float dv = 0.0f;
+                    if (cin && grow < e.M) {
+                        const int64_t base = grow * (int64_t)e.N + col;
+                        float o = e.alpha * stg[r * kStgStride + j];
+                        if (e.beta != 0.0f) o = fmaf(e.beta, t[k], o);
+                        e.C[base] = o;
+                        if (fuse) {
+                            dv = fmaf(e.alpha2, u[k], o);  // D = C + alpha2 X, one rounding
+                            e.D[base] = dv;
+                            if (k & 1) s3 = fmaf(dv, dv, s3);
+                            else s2 = fmaf(dv, dv, s2);
+                        }
+                    }
+                    if (fuse) stg[r * kStgStride + j] = dv;  // rows >= M and columns >= N staged as +0
+                }
+            }
         }
         if (fuse) {
-            // E = D^T: D goes back through the staging block, then each lane writes its own
-            // row's 16 values down 16 columns of E, so that every store covers 32 rows of
-            // E in one 128-byte segment
-            __syncwarp();
-#pragma unroll
-            for (int it = 0; it < 4; ++it) {
-                const int r = it * 8 + (lane >> 2);
-                *reinterpret_cast<float4*>(stg + r * kStgStride + 4 * cq) =
-                    make_float4(dd[it][0], dd[it][1], dd[it][2], dd[it][3]);
-            }
+            // E = D^T: D is back in the staging block; each lane writes its own row's 16 values
+            // down 16 columns of E, so that every store covers 32 rows of E in one 128-byte
+            // segment
             __syncwarp();
             if (e.rsum_part) {
                 // these 32 rows are block row0 / 32 of the E rows gcol + 16h + 0..15: two lanes
