@@ -64,6 +64,8 @@ struct gao_prog {
     bool stats_pending = false; // the last run's event times are not read yet
     cudaStream_t cst = nullptr;           // copy stream of the copy/compute overlap
     std::vector<cudaEvent_t> pipe_ev;     // its events: fork, B landed, one per row block
+    cudaStream_t ost = nullptr;           // device-to-host stream: a GEMM's C rows as blocks finish
+    std::vector<cudaEvent_t> out_ev;      // one per row block (block done), then the join
     std::vector<int8_t> verdict;  // gao_offload of every loop
     std::vector<int> gene_loop;   // gene bit k -> index of the k-th offloadable loop
     std::unordered_map<uint64_t, GraphEntry> graphs;  // key: gene * 8 + run flags (KEEP_DEVICE, NO_LOOP_TIMES)

@@ -341,12 +341,16 @@ void free_prog(gao_prog* p) {
     }
     if (p->h_err) cudaFreeHost(p->h_err);
     if (p->cst) cudaStreamSynchronize(p->cst);
+    if (p->ost) cudaStreamSynchronize(p->ost);
     drop_graphs(p);
     for (auto e : p->ev)
         if (e) cudaEventDestroy(e);
     for (auto e : p->pipe_ev)
         if (e) cudaEventDestroy(e);
+    for (auto e : p->out_ev)
+        if (e) cudaEventDestroy(e);
     if (p->cst) cudaStreamDestroy(p->cst);
+    if (p->ost) cudaStreamDestroy(p->ost);
     if (p->own_arena && p->arena) cudaFree(p->arena);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
     delete p;
@@ -443,6 +447,13 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
     }
+    e = cudaStreamCreateWithFlags(&p->ost, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate(device-to-host stream)"));
+    p->out_ev.assign(1 + kMaxRowBlocks, nullptr);
+    for (auto& ev : p->out_ev) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    }
     p->ev_used.assign((size_t)n_loops, 0);
     p->stats.assign((size_t)n_loops, gao_loop_stat{});
     *out = p;
@@ -475,6 +486,7 @@ extern "C" gao_status prog_bind_host(gao_prog* p, int buf, void* host, uint64_t 
     // no queued copy may still use the memory being replaced
     if ((e = cudaStreamSynchronize(p->st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     if (p->cst && (e = cudaStreamSynchronize(p->cst)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (p->ost && (e = cudaStreamSynchronize(p->ost)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     if (B.registered) {
         cudaHostUnregister(B.host);
         B.registered = false;
@@ -982,7 +994,12 @@ int64_t pipeline_blocks(const gao_prog* p, const gao_loop& L) {
     return blocks >= 2 ? blocks : 0;
 }
 
-gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain* ch) {
+// With early_out (C an OUTPUT the run copies back at its end), each block's rows of C go back
+// to the host on a third stream as soon as the block's GEMM is done, on the link's other
+// direction while later blocks are still coming in; *c_on_host tells the caller that C's host
+// copy is then valid.
+gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain* ch, bool early_out,
+                                  bool* c_on_host) {
     gao_prog* p = R.p;
     const gao_loop& L = p->loops[(size_t)li];
     gao_loop_stat& S = p->stats[(size_t)li];
@@ -1057,8 +1074,20 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
                                        (int*)(p->arena + p->lay.err_off), st, tev, &why, ch ? &fz : nullptr, &part);
         if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "row-block GEMM") : fail(GAO_EINVAL, why);
         S.launches += tev.launches;
+        if (early_out) {
+            GAO_CUDA_TRY(cudaEventRecord(p->out_ev[(size_t)i], st));
+            GAO_CUDA_TRY(cudaStreamWaitEvent(p->ost, p->out_ev[(size_t)i], 0));
+            const size_t off = (size_t)r0 * N * 4, len = (size_t)(r1 - r0) * N * 4;
+            GAO_CUDA_TRY(cudaMemcpyAsync((char*)C.host + off, C.dev + off, len, cudaMemcpyDeviceToHost, p->ost));
+            S.d2h_bytes += len;
+        }
     }
     GAO_CUDA_TRY(record_timing(ev[3], st));
+    if (early_out) {  // joined back into the program's stream (a captured graph needs that)
+        GAO_CUDA_TRY(cudaEventRecord(p->out_ev[(size_t)kMaxRowBlocks], p->ost));
+        GAO_CUDA_TRY(cudaStreamWaitEvent(st, p->out_ev[(size_t)kMaxRowBlocks], 0));
+    }
+    *c_on_host = early_out;
     A.vd = B.vd = true;
     if (C0) C0->vd = true;
     p->ev_used[(size_t)li] |= 1 | 2 | 4;
@@ -1295,6 +1324,7 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
         }
         // a GEMM whose A comes from the host overlaps the copy (row blocks) rather than fusing
         const int64_t blocks = gpu ? pipeline_blocks(p, L) : 0;
+        bool c_on_host = false;  // the pipelined GEMM copied C back block by block
         if (gpu && blocks == 0 && L.kind == GAO_LOOP_GEMM && find_chain(p, li, gene_mask, fuse, &chain)) {
             // inputs of the whole chain: the GEMM's and the AXPY's second operand
             std::vector<int> cin = loop_inputs(L);
@@ -1338,7 +1368,15 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
                 const int xb = p->loops[(size_t)pch.axpy].ins[1];
                 pf = xb == L.ins[0] || p->bufs[(size_t)xb].vd;
             }
-            if ((status = run_gpu_gemm_pipelined(R, li, blocks, pf ? &pch : nullptr)) != GAO_OK) break;
+            // C's rows go back to the host as their blocks finish when the run copies C back
+            // anyway (an OUTPUT, device buffers not kept, resident transfers)
+            const BufState& Cb = p->bufs[(size_t)L.outs[0]];
+            const bool early_out = !per_loop && !(flags & GAO_RUN_KEEP_DEVICE) && Cb.d.role == GAO_BUF_OUTPUT &&
+                                   Cb.host != nullptr && L.outs[0] != L.ins[0] && L.outs[0] != L.ins[1];
+            c_on_host = false;
+            if ((status = run_gpu_gemm_pipelined(R, li, blocks, pf ? &pch : nullptr, early_out, &c_on_host)) !=
+                GAO_OK)
+                break;
             if (pf) {
                 for (int j : {li, pch.axpy, pch.transpose, pch.rowsum, pch.frob}) {
                     if (j < 0) continue;
@@ -1348,6 +1386,7 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
                     }
                     if (j != li) fused |= 1ULL << j;
                 }
+                if (c_on_host) p->bufs[(size_t)L.outs[0]].vh = true;
                 if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
                 if (R.timed_out) break;
                 continue;
@@ -1387,6 +1426,7 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             p->bufs[(size_t)b].vh = !gpu;
             p->bufs[(size_t)b].vd = gpu;
         }
+        if (blocks > 0 && c_on_host) p->bufs[(size_t)L.outs[0]].vh = true;  // copied back block by block
         if (gpu && per_loop) {  // ... and outputs always copied back out; the device copy is dropped
             for (int b : loop_outputs(L))
                 if ((status = make_valid(R, b, false, S)) != GAO_OK) break;

@@ -101,3 +101,42 @@ def test_bind_rejects_wrong_size(gao):
     with pytest.raises(gao.GaoError):
         gao.prog_bind_host(p, 9, np.zeros((64, 64), dtype=np.float32))
     gao.prog_destroy(p)
+
+
+@pytest.mark.parametrize("prec,n", [("bf16x6", 2304), ("bf16x3", 2500)])
+def test_overlapped_gemm_copies_c_back_by_row_block(gao, prec, n):
+    """A GEMM whose A comes from the host runs in row blocks overlapped with the copy in; with C
+    an OUTPUT bound to the caller's array, each block's rows of C go back as soon as the block is
+    done (the link's other direction).  C must carry the bits of the device-resident run, be
+    copied back exactly once per run (plain runs and graph replays), and a run that keeps the
+    device buffers must not copy it."""
+    pr = {"bf16x6": gao.BF16X6, "bf16x3": gao.BF16X3}[prec]
+    seed = 71
+    hp = W.host_input_gemm(n)
+    ins = _inputs(n, seed)
+    # the same GEMM on operands formed on the device by the INIT loop (same hash streams):
+    # one launch, no row blocks
+    dev = W.gemm_only(n, seed)
+    ref = gao.prog_from_workload(dev, gemm_prec=pr)
+    gao.prog_run(ref, 0b11)
+    assert sum(s["h2d_bytes"] for s in gao.prog_stats(ref)) == 0
+    C_ref = gao.prog_output(ref, dev.index("C")).copy()
+    gao.prog_destroy(ref)
+
+    p = gao.prog_from_workload(hp, gemm_prec=pr)
+    C_out = np.zeros((n, n), dtype=np.float32)
+    for nm, v in ins.items():
+        gao.prog_bind_host(p, hp.index(nm), v.copy())
+    gao.prog_bind_host(p, hp.index("C"), C_out)
+    for run in range(4):
+        C_out[:] = np.float32(-1.0)
+        gao.prog_run(p, 1)
+        assert np.array_equal(C_out.view(np.uint32), C_ref.view(np.uint32)), run
+        st = gao.prog_stats(p)
+        assert sum(s["h2d_bytes"] for s in st) == 3 * n * n * 4
+        assert sum(s["d2h_bytes"] for s in st) == n * n * 4, run
+    C_out[:] = np.float32(-1.0)
+    gao.prog_run(p, 1, gao.RUN_KEEP_DEVICE)
+    assert sum(s["d2h_bytes"] for s in gao.prog_stats(p)) == 0
+    assert np.all(C_out == np.float32(-1.0))
+    gao.prog_destroy(p)
