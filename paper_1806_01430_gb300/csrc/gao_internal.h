@@ -210,10 +210,18 @@ struct TcPart {
     int64_t row_tile0;  // fused chain: 128-row tiles of the problem before this block
     bool last;          // fused chain: the last block (reduces the norm's partials)
 };
+// ready: bit 0, A's bfloat16 planes are already in the scratch (tc_init_planes); bit 1, B's.
 cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M,
                            int64_t N, int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
                            size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why,
-                           const TcFuse* fuse = nullptr, const TcPart* part = nullptr);
+                           const TcFuse* fuse = nullptr, const TcPart* part = nullptr, unsigned ready = 0);
+// The bfloat16 planes of operand `which` (0: A, M x K; 1: B, K x N) of that GEMM (same
+// precision, shapes, K chunk and tile configuration), formed in its scratch straight from the
+// INIT loop's counter hash of buffer `buf` (times 2^e of each row where rowexp is set), with
+// the values, splitting and zero padding of INIT followed by the GEMM's own split.
+cudaError_t tc_init_planes(int prec, int which, int64_t M, int64_t N, int64_t K, int kchunk, int tile_cfg,
+                           uint64_t seed, uint32_t buf, const int8_t* rowexp, void* scratch, size_t scratch_bytes,
+                           cudaStream_t st, int* launches);
 
 // Freivalds residual check of C = alpha A B + beta C0 in binary64 (C0 may be null):
 // kernels on st; the residual vectors go to rvec (M) / svec (N) when set; *norms_dev

@@ -1181,6 +1181,96 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const float* __restrict
     }
 }
 
+// The same planes formed straight from the INIT loop's counter hash (element idx of buffer
+// `buf` is init_value(seed, buf, idx), times 2^e of its row where rowexp is set), for an
+// operand that nothing but this GEMM reads: the binary32 array is never written.  Values,
+// splitting and zero padding are those of INIT followed by split_rows / split_cols.
+// Eight consecutive elements idx0 .. idx0 + 7 from the hashes of idx0 / 2 .. (idx0 + 7) / 2.
+__device__ __forceinline__ void init_gen8(uint64_t seed, uint32_t buf, uint64_t idx0, float (&x)[8]) {
+    const uint64_t h0 = idx0 >> 1;
+    const bool odd = (idx0 & 1) != 0;
+    uint64_t h[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) h[j] = (j < 4 || odd) ? sm64_hash(init_key(seed, buf, h0 + j)) : 0;
+    // element idx takes the high 24 bits of hash idx / 2 when idx is even, bits 16..39 when odd
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint64_t he = h[q >> 1], ho = h[(q + 1) >> 1];
+        x[q] = odd ? ((q & 1) ? u24_to_value((uint32_t)(ho >> 40)) : u24_to_value((uint32_t)((h[q >> 1] >> 16) & 0xFFFFFFu)))
+                   : ((q & 1) ? u24_to_value((uint32_t)((he >> 16) & 0xFFFFFFu)) : u24_to_value((uint32_t)(he >> 40)));
+    }
+}
+
+template <int P>
+__global__ void init_split_rows_kernel(uint64_t seed, uint32_t buf, const int8_t* __restrict__ rowexp, int64_t M,
+                                       int64_t K, int64_t Mp, int64_t Kp, __nv_bfloat16* __restrict__ out) {
+    const int64_t gpr = Kp / 8;
+    const int64_t total = Mp * gpr;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = g / gpr, k0 = (g % gpr) * 8;
+        float x[8];
+        if (i < M && k0 + 8 <= K) {
+            init_gen8(seed, buf, (uint64_t)(i * K + k0), x);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[q] = (i < M && k0 + q < K) ? init_value(seed, buf, (uint64_t)(i * K + k0 + q)) : 0.0f;
+        }
+        if (rowexp && i < M) {
+            const int e = rowexp[i];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[q] = ldexpf(x[q], e);
+        }
+        split8_store<P>(x, out + i * Kp + k0, Mp * Kp);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) init_split_cols_kernel(uint64_t seed, uint32_t buf,
+                                                              const int8_t* __restrict__ rowexp, int64_t K, int64_t N,
+                                                              int64_t Np, int64_t Kp, __nv_bfloat16* __restrict__ out) {
+    __shared__ float tile[64][65];
+    const int t = threadIdx.x;
+    const int c4 = t & 15, r = t >> 4;
+    const int64_t k0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t gk = k0 + r + 16 * j, gn = n0 + 4 * c4;
+        float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (gk < K) {
+            const uint64_t idx = (uint64_t)(gk * N + gn);
+            if (gn + 3 < N && (idx & 1) == 0) {  // two hashes give the four elements
+                const uint64_t h0 = sm64_hash(init_key(seed, buf, idx >> 1));
+                const uint64_t h1 = sm64_hash(init_key(seed, buf, (idx >> 1) + 1));
+                v[0] = u24_to_value((uint32_t)(h0 >> 40));
+                v[1] = u24_to_value((uint32_t)((h0 >> 16) & 0xFFFFFFu));
+                v[2] = u24_to_value((uint32_t)(h1 >> 40));
+                v[3] = u24_to_value((uint32_t)((h1 >> 16) & 0xFFFFFFu));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (gn + q < N) v[q] = init_value(seed, buf, idx + q);
+            }
+            if (rowexp) {
+                const int e = rowexp[gk];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = ldexpf(v[q], e);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tile[r + 16 * j][4 * c4 + q] = v[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int idx = t + 256 * h;
+        const int n = idx >> 3, kc = idx & 7;
+        float x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = tile[kc * 8 + q][n];
+        split8_store<P>(x, out + (n0 + n) * Kp + k0 + kc * 8, Np * Kp);
+    }
+}
+
 // ---- FP8 quantise kernels -----------------------------------------------------------------------
 
 // Exponent e of the power-of-two scale of a block whose largest magnitude is amax: the
@@ -1447,10 +1537,75 @@ size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K) {
     return tc_planes_bytes(prec, M, N, K) + tc_partials_bytes(M, N);
 }
 
+namespace {
+// Tile shape of a split-precision GEMM (see the tile configuration bits in launch_gemm_tc)
+// and where its bfloat16 planes live in the scratch.
+struct TcShape {
+    int P, bn, num_kb, chunk_kb;
+    bool chunked, pair;
+    int64_t Mp, Np, Kp;
+    size_t pb_elems;  // B's planes start this many bfloat16 after A's (room for Mlay rows)
+};
+TcShape tc_shape(int prec, int64_t M, int64_t Mlay, int64_t N, int64_t K, int kchunk, int tile_cfg,
+                 const TcPart* part) {
+    TcShape g{};
+    g.P = planes_of(prec);
+    g.Np = ru(N, 256);
+    g.Kp = ru(K, BK);
+    g.num_kb = (int)(g.Kp / BK);
+    g.chunk_kb = g.num_kb;
+    if (kchunk > 0) g.chunk_kb = std::max(1, (int)((kchunk + BK - 1) / BK));
+    g.chunked = g.chunk_kb < g.num_kb;
+    // tile_cfg bits 0-1: 0 = default, 1 = 128 x 128 tiles, 2 = 128 x 256 (single product,
+    // unchunked only); bit 2: L2 prefetch of the operand tiles; bit 3: CTA pairs (256-row
+    // tiles on two SMs, each SM loading half of every B tile); bits 4-7: raster group =
+    // 2^value row tiles (0: default 16).  The default is the fastest measured shape:
+    // 256 x 256 on CTA pairs for the unchunked single product (which the pair's halved B
+    // traffic per SM speeds up by 14% at n = 8192), 128 x 128 on one CTA for the split
+    // precisions (a pair gains nothing there).
+    const int bn_sel = tile_cfg & 3;
+    g.bn = 128;
+    if (!g.chunked && g.P == 1 && (bn_sel == 2 || bn_sel == 0)) g.bn = 256;
+    // a row block must start on a 256-row boundary to run on pairs
+    g.pair = ((tile_cfg & 8) != 0 || (bn_sel == 0 && g.P == 1 && !g.chunked)) && !(part && part->row_tile0 % 2 != 0);
+    g.Mp = ru(M, g.pair ? 2 * BM : BM);
+    // A's planes ([P][Mp][Kp], this call's rows) at the start; B's ([P][Np][Kp]) after room
+    // for the whole problem's A planes, so that row blocks can share them
+    g.pb_elems = (size_t)g.P * ru(Mlay, 2 * BM) * g.Kp;
+    return g;
+}
+}  // namespace
+
+cudaError_t tc_init_planes(int prec, int which, int64_t M, int64_t N, int64_t K, int kchunk, int tile_cfg,
+                           uint64_t seed, uint32_t buf, const int8_t* rowexp, void* scratch, size_t scratch_bytes,
+                           cudaStream_t st, int* launches) {
+    *launches = 0;
+    if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_BF16X6 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+    if (tc_scratch_bytes(prec, M, N, K) > scratch_bytes || ((uintptr_t)scratch & 1023u)) return cudaErrorInvalidValue;
+    const TcShape g = tc_shape(prec, M, M, N, K, kchunk, tile_cfg, nullptr);
+    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(scratch);
+    if (which == 0) {  // A (M x K) -> [P][Mp][Kp]
+        int64_t blocks = (g.Mp * (g.Kp / 8) + 255) / 256;
+        if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+        if (g.P == 3) init_split_rows_kernel<3><<<(unsigned)blocks, 256, 0, st>>>(seed, buf, rowexp, M, K, g.Mp, g.Kp, pa);
+        else if (g.P == 2) init_split_rows_kernel<2><<<(unsigned)blocks, 256, 0, st>>>(seed, buf, rowexp, M, K, g.Mp, g.Kp, pa);
+        else init_split_rows_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(seed, buf, rowexp, M, K, g.Mp, g.Kp, pa);
+    } else {  // B (K x N) -> B^T planes [P][Np][Kp]
+        dim3 grid((unsigned)(g.Np / 64), (unsigned)(g.Kp / 64));
+        if (grid.y > 65535u) return cudaErrorInvalidValue;
+        __nv_bfloat16* pb = pa + g.pb_elems;
+        if (g.P == 3) init_split_cols_kernel<3><<<grid, 256, 0, st>>>(seed, buf, rowexp, K, N, g.Np, g.Kp, pb);
+        else if (g.P == 2) init_split_cols_kernel<2><<<grid, 256, 0, st>>>(seed, buf, rowexp, K, N, g.Np, g.Kp, pb);
+        else init_split_cols_kernel<1><<<grid, 256, 0, st>>>(seed, buf, rowexp, K, N, g.Np, g.Kp, pb);
+    }
+    *launches = 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M, int64_t N,
                            int64_t K, float alpha, float beta, int kchunk, int tile_cfg, void* scratch,
                            size_t scratch_bytes, int* err, cudaStream_t st, TcEvents& ev, std::string* why,
-                           const TcFuse* fuse, const TcPart* part) {
+                           const TcFuse* fuse, const TcPart* part, unsigned ready) {
     ev.launches = 0;
     if (prec < GAO_GEMM_BF16 || prec > GAO_GEMM_FP8) {
         if (why) *why = "precision not available on the tensor-core path";
@@ -1481,62 +1636,44 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         return launch_gemm_fp8(C, A, B, C0, M, N, K, alpha, beta, tile_cfg, scratch, scratch_bytes, err, st, ev,
                                why);
     }
-    const int P = planes_of(prec);
     const int64_t Mlay = part ? part->m_layout : M;
-    if (Mlay < M) {
+    if (Mlay < M || (part && ready)) {
         if (why) *why = "bad row-block arguments";
         return cudaErrorInvalidValue;
     }
-    const int64_t Np = ru(N, 256), Kp = ru(K, BK);
-    const int num_kb = (int)(Kp / BK);
-    int chunk_kb = num_kb;
-    if (kchunk > 0) chunk_kb = std::max(1, (int)((kchunk + BK - 1) / BK));
-    const bool chunked = chunk_kb < num_kb;
-    // tile_cfg bits 0-1: 0 = default, 1 = 128 x 128 tiles, 2 = 128 x 256 (single product,
-    // unchunked only); bit 2: L2 prefetch of the operand tiles; bit 3: CTA pairs (256-row
-    // tiles on two SMs, each SM loading half of every B tile); bits 4-7: raster group =
-    // 2^value row tiles (0: default 16).  The default is the fastest measured shape:
-    // 256 x 256 on CTA pairs for the unchunked single product (which the pair's halved B
-    // traffic per SM speeds up by 14% at n = 8192), 128 x 128 on one CTA for the split
-    // precisions (tensor-bound already: a pair gains nothing there).
-    const int bn_sel = tile_cfg & 3;
+    const TcShape g = tc_shape(prec, M, Mlay, N, K, kchunk, tile_cfg, part);
+    const int P = g.P, num_kb = g.num_kb, chunk_kb = g.chunk_kb, bn = g.bn;
+    const bool chunked = g.chunked, pair = g.pair;
+    const int64_t Mp = g.Mp, Np = g.Np, Kp = g.Kp;
     const int group = tc_group_of(tile_cfg);
     const int pf_kb = tc_prefetch_of(tile_cfg);
-    int bn = 128;
-    if (!chunked && P == 1 && (bn_sel == 2 || bn_sel == 0)) bn = 256;
-    // a row block must start on a 256-row boundary to run on pairs
-    const bool pair = ((tile_cfg & 8) != 0 || (bn_sel == 0 && P == 1 && !chunked)) &&
-                      !(part && part->row_tile0 % 2 != 0);
-    const int64_t Mp = ru(M, pair ? 2 * BM : BM);
     if (tc_scratch_bytes(prec, Mlay, N, K) > scratch_bytes || ((uintptr_t)scratch & 1023u)) {
         if (why) *why = "tensor-core scratch too small or misaligned";
         return cudaErrorInvalidValue;
     }
-    // A's planes ([P][Mp][Kp], this call's rows) at the start; B's ([P][Np][Kp]) after
-    // room for the whole problem's A planes, so that row blocks can share them
     __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(scratch);
-    __nv_bfloat16* pb = pa + (size_t)P * ru(Mlay, 2 * BM) * Kp;
+    __nv_bfloat16* pb = pa + g.pb_elems;
     const int sms = sm_count();
-    {
+    if (!(ready & 1)) {
         const int64_t work = Mp * (Kp / 8);
-        int64_t g = (work + 255) / 256;
-        if (g > (int64_t)sms * 8) g = (int64_t)sms * 8;
-        if (P == 3) split_rows_kernel<3><<<(unsigned)g, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
-        else if (P == 2) split_rows_kernel<2><<<(unsigned)g, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
-        else split_rows_kernel<1><<<(unsigned)g, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
+        int64_t blocks = (work + 255) / 256;
+        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+        if (P == 3) split_rows_kernel<3><<<(unsigned)blocks, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
+        else if (P == 2) split_rows_kernel<2><<<(unsigned)blocks, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
+        else split_rows_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(A, M, K, Mp, Kp, pa);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         ev.launches += 1;
-        if (!(part && part->b_ready)) {
-            dim3 grid((unsigned)(Np / 64), (unsigned)(Kp / 64));
-            if (grid.y > 65535u) return cudaErrorInvalidValue;
-            if (P == 3) split_cols_kernel<3><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-            else if (P == 2) split_cols_kernel<2><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-            else split_cols_kernel<1><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            ev.launches += 1;
-        }
+    }
+    if (!(part && part->b_ready) && !(ready & 2)) {
+        dim3 grid((unsigned)(Np / 64), (unsigned)(Kp / 64));
+        if (grid.y > 65535u) return cudaErrorInvalidValue;
+        if (P == 3) split_cols_kernel<3><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+        else if (P == 2) split_cols_kernel<2><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+        else split_cols_kernel<1><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        ev.launches += 1;
     }
     CUtensorMap ta, tb;
     if (!make_map(&ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;

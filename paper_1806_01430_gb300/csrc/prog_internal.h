@@ -18,6 +18,10 @@ struct BufState {
     bool registered = false;   // host is caller memory the library page-locked (cudaHostRegister)
     bool vh = false, vd = false;
     bool input_set = false;
+    // Formed by an INIT loop straight into the bfloat16 planes of the one GEMM that reads it
+    // (gen_for): the binary32 array holds nothing (vd and vh false) until something else
+    // needs it, which then runs slot gen_slot of INIT loop gen_loop for it alone.
+    int gen_loop = -1, gen_slot = -1, gen_for = -1;
 };
 
 struct CacheEntry {
@@ -52,7 +56,8 @@ struct gao_prog {
     int device = 0;
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    char* arena = nullptr;
+    char* arena = nullptr;      // 1024-byte aligned (tensor-core scratch, TMA maps)
+    char* arena_raw = nullptr;  // the library's own allocation (freed with the program)
     bool own_arena = false;
     gao::Layout lay;
     int* h_err = nullptr;  // pinned

@@ -351,7 +351,7 @@ void free_prog(gao_prog* p) {
         if (e) cudaEventDestroy(e);
     if (p->cst) cudaStreamDestroy(p->cst);
     if (p->ost) cudaStreamDestroy(p->ost);
-    if (p->own_arena && p->arena) cudaFree(p->arena);
+    if (p->own_arena && p->arena_raw) cudaFree(p->arena_raw);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
     delete p;
 }
@@ -412,9 +412,11 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
         if (((uintptr_t)p->opts.dev_arena) & 1023u) return bail(fail(GAO_EINVAL, "dev_arena must be 1024-byte aligned"));
         p->arena = (char*)p->opts.dev_arena;
     } else {
-        cudaError_t e = cudaMalloc((void**)&p->arena, p->lay.total);
+        // cudaMalloc guarantees 256-byte alignment only; the layout's offsets assume 1024
+        cudaError_t e = cudaMalloc((void**)&p->arena_raw, p->lay.total + 1024);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(arena)"));
         p->own_arena = true;
+        p->arena = p->arena_raw + ((1024u - ((uintptr_t)p->arena_raw & 1023u)) & 1023u);
     }
     p->bufs.resize((size_t)n_bufs);
     for (int b = 0; b < n_bufs; ++b) {
@@ -543,9 +545,32 @@ uint64_t loop_mask_of(const gao_prog* p, uint64_t gene) {
 }
 
 
+// A buffer an INIT loop formed only as a GEMM's bfloat16 planes: its binary32 values, formed
+// now on the device by that INIT slot alone (the same counter hash, the same row exponents).
+gao_status materialize(RunCtx& R, int b) {
+    gao_prog* p = R.p;
+    BufState& B = p->bufs[(size_t)b];
+    const gao_loop& L = p->loops[(size_t)B.gen_loop];
+    const int rs = (int)((L.flags >> B.gen_slot) & 1);
+    InitSet set{};
+    set.o[0] = InitOut{(float*)B.dev, B.d.rows, B.d.cols, (uint32_t)b, rs};
+    set.n = 1;
+    set.seed = p->opts.seed;
+    set.rowexp = rs ? (const int8_t*)(p->arena + p->lay.rowexp_off) : nullptr;
+    if (rs) GAO_CUDA_TRY(launch_row_exponents((int8_t*)set.rowexp, B.d.rows, p->opts.seed, R.st));
+    if (B.d.rows * B.d.cols > 0) GAO_CUDA_TRY(launch_init_set(set, R.st));
+    B.vd = true;
+    B.gen_loop = B.gen_slot = B.gen_for = -1;
+    return GAO_OK;
+}
+
 // Make buffer b valid on the requested side, issuing a copy on the stream if needed.
 gao_status make_valid(RunCtx& R, int b, bool on_gpu, gao_loop_stat& stat) {
     BufState& B = R.p->bufs[(size_t)b];
+    if (!B.vd && !B.vh && B.gen_loop >= 0) {
+        gao_status s = materialize(R, b);
+        if (s != GAO_OK) return s;
+    }
     if (on_gpu) {
         if (B.vd) return GAO_OK;
         if (!B.vh) return fail(GAO_EINVAL, "buffer " + std::to_string(b) + " holds no data");
@@ -634,9 +659,13 @@ gao_status run_gpu_loop(RunCtx& R, int li) {
             } else {
                 std::string why;
                 TcEvents tev{k0, k1, 0};
+                // operands an INIT loop formed straight into this GEMM's planes
+                const unsigned ready = (p->bufs[(size_t)L.ins[0]].gen_for == li ? 1u : 0u) |
+                                       (p->bufs[(size_t)L.ins[1]].gen_for == li ? 2u : 0u);
                 e = launch_gemm_tc(prec, dptr(L.outs[0]), dptr(L.ins[0]), dptr(L.ins[1]), c0 ? c0 : dptr(L.outs[0]),
                                    A.rows, B.cols, A.cols, (float)L.alpha, beta, p->opts.kchunk, p->opts.tile_cfg,
-                                   a + p->lay.tc_off, p->lay.tc_bytes, d_err, st, tev, &why);
+                                   a + p->lay.tc_off, p->lay.tc_bytes, d_err, st, tev, &why, nullptr, nullptr,
+                                   ready);
                 if (e != cudaSuccess && !why.empty()) return fail(GAO_EINVAL, "tensor-core GEMM: " + why);
                 nl += tev.launches;
             }
@@ -989,7 +1018,7 @@ int64_t pipeline_blocks(const gao_prog* p, const gao_loop& L) {
     if (L.ins[0] == L.ins[1] || L.ins[2] == L.ins[0] || L.ins[2] == L.ins[1]) return 0;
     const BufState& A = p->bufs[(size_t)L.ins[0]];
     const gao_buffer& B = p->bufs[(size_t)L.ins[1]].d;
-    if (A.vd || A.bytes < kPipelineMinBytes || A.d.cols <= 0 || B.cols <= 0) return 0;
+    if (A.vd || A.gen_for >= 0 || A.bytes < kPipelineMinBytes || A.d.cols <= 0 || B.cols <= 0) return 0;
     const int64_t blocks = std::min<int64_t>(kMaxRowBlocks, A.d.rows / 256);
     return blocks >= 2 ? blocks : 0;
 }
@@ -1174,12 +1203,91 @@ double ev_ms(cudaEvent_t a, cudaEvent_t b) {
 // host loops run in between: residency reset, the error word, each loop's copies and
 // kernels (or its host loop), the outputs' copies back and the error word's read-back.
 // When every loop is on the GPU this is also what a CUDA graph of the run captures.
+// The GEMM loop that alone reads INIT loop li's output b, as its A (*which = 0) or its B
+// (*which = 1), when that GEMM runs on the GPU in split bfloat16 without a fused chain: b is
+// then formed straight into the GEMM's bfloat16 planes, never as binary32.  -1 otherwise (b
+// is not a TEMP buffer, is read by anything else or written by another loop, the GEMM reads
+// it twice or also as C0, transfers are per loop).
+int planes_consumer(const gao_prog* p, int li, int b, uint64_t gene_mask, bool fuse, int* which) {
+    const BufState& B = p->bufs[(size_t)b];
+    if (B.d.role != GAO_BUF_TEMP || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT || p->lay.tc_bytes == 0) return -1;
+    const int prec = p->opts.gemm_prec;
+    if (prec != GAO_GEMM_BF16 && prec != GAO_GEMM_BF16X3 && prec != GAO_GEMM_BF16X6) return -1;
+    int reader = -1;
+    for (int j = 0; j < (int)p->loops.size(); ++j) {
+        const gao_loop& Lj = p->loops[(size_t)j];
+        if (j != li)
+            for (int o : loop_outputs(Lj))
+                if (o == b) return -1;
+        for (int i : loop_inputs(Lj))
+            if (i == b) {
+                if (reader >= 0 && reader != j) return -1;
+                reader = j;
+            }
+    }
+    if (reader <= li) return -1;
+    const gao_loop& G = p->loops[(size_t)reader];
+    if (G.kind != GAO_LOOP_GEMM || !((gene_mask >> reader) & 1)) return -1;
+    if (G.outs[0] == b || G.ins[2] == b || (G.ins[0] == b) == (G.ins[1] == b)) return -1;
+    Chain c;
+    if (find_chain(p, reader, gene_mask, fuse, &c)) return -1;
+    const gao_buffer &A = p->bufs[(size_t)G.ins[0]].d, &Bm = p->bufs[(size_t)G.ins[1]].d;
+    if (A.rows <= 0 || A.cols <= 0 || Bm.cols <= 0) return -1;
+    *which = G.ins[0] == b ? 0 : 1;
+    return reader;
+}
+
+// INIT loop li on the GPU with the outputs whose cons[t] >= 0 formed as the planes of GEMM
+// loop cons[t] (operand wh[t]) and the others written as binary32, row exponents once.
+gao_status run_gpu_init_planes(RunCtx& R, int li, const int* cons, const int* wh) {
+    gao_prog* p = R.p;
+    const gao_loop& L = p->loops[(size_t)li];
+    cudaStream_t st = R.st;
+    int& nl = p->stats[(size_t)li].launches;
+    char* a = p->arena;
+    InitSet set{};
+    int64_t rx_rows = 0, total = 0;
+    for (int t = 0; t < GAO_MAX_IO; ++t) {
+        const int b = L.outs[t];
+        if (b < 0) continue;
+        const BufState& B = p->bufs[(size_t)b];
+        const int rs = (int)((L.flags >> t) & 1);
+        if (rs) rx_rows = std::max(rx_rows, B.d.rows);
+        if (cons[t] >= 0) continue;
+        set.o[set.n++] = InitOut{(float*)B.dev, B.d.rows, B.d.cols, (uint32_t)b, rs};
+        total += B.d.rows * B.d.cols;
+    }
+    set.seed = p->opts.seed;
+    set.rowexp = rx_rows > 0 ? (const int8_t*)(a + p->lay.rowexp_off) : nullptr;
+    if (rx_rows > 0) {
+        GAO_CUDA_TRY(launch_row_exponents((int8_t*)set.rowexp, rx_rows, p->opts.seed, st));
+        nl += 1;
+    }
+    if (total > 0) {
+        GAO_CUDA_TRY(launch_init_set(set, st));
+        nl += 1;
+    }
+    for (int t = 0; t < GAO_MAX_IO; ++t) {
+        if (L.outs[t] < 0 || cons[t] < 0) continue;
+        const gao_loop& G = p->loops[(size_t)cons[t]];
+        const gao_buffer &A = p->bufs[(size_t)G.ins[0]].d, &Bm = p->bufs[(size_t)G.ins[1]].d;
+        const int rs = (int)((L.flags >> t) & 1);
+        int l = 0;
+        GAO_CUDA_TRY(tc_init_planes(p->opts.gemm_prec, wh[t], A.rows, Bm.cols, A.cols, p->opts.kchunk,
+                                    p->opts.tile_cfg, p->opts.seed, (uint32_t)L.outs[t], rs ? set.rowexp : nullptr,
+                                    a + p->lay.tc_off, p->lay.tc_bytes, st, &l));
+        nl += l;
+    }
+    return GAO_OK;
+}
+
 gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags) {
     gao_prog* p = R.p;
     const int n = (int)p->loops.size();
     for (auto& B : p->bufs) {
         B.vh = (B.d.role == GAO_BUF_INPUT);
         B.vd = false;
+        B.gen_loop = B.gen_slot = B.gen_for = -1;
     }
     std::fill(p->ev_used.begin(), p->ev_used.end(), 0);
     for (auto& s : p->stats) s = gao_loop_stat{};
@@ -1322,6 +1430,34 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             if (R.timed_out) break;
             continue;
         }
+        if (gpu && L.kind == GAO_LOOP_INIT) {
+            // outputs that only a split-precision GEMM reads go straight into its planes
+            int cons[GAO_MAX_IO], wh[GAO_MAX_IO], ndefer = 0;
+            for (int t = 0; t < GAO_MAX_IO; ++t) {
+                cons[t] = L.outs[t] >= 0 ? planes_consumer(p, li, L.outs[t], gene_mask, fuse, &wh[t]) : -1;
+                ndefer += cons[t] >= 0;
+            }
+            if (ndefer > 0) {
+                GAO_CUDA_TRY(record_timing(ev[2], p->st));
+                if ((status = run_gpu_init_planes(R, li, cons, wh)) != GAO_OK) break;
+                GAO_CUDA_TRY(record_timing(ev[3], p->st));
+                p->ev_used[(size_t)li] |= 2;
+                for (int t = 0; t < GAO_MAX_IO; ++t) {
+                    if (L.outs[t] < 0) continue;
+                    BufState& B = p->bufs[(size_t)L.outs[t]];
+                    B.vh = false;
+                    B.vd = cons[t] < 0;
+                    if (cons[t] >= 0) {
+                        B.gen_loop = li;
+                        B.gen_slot = t;
+                        B.gen_for = cons[t];
+                    }
+                }
+                if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
+                if (R.timed_out) break;
+                continue;
+            }
+        }
         // a GEMM whose A comes from the host overlaps the copy (row blocks) rather than fusing
         const int64_t blocks = gpu ? pipeline_blocks(p, L) : 0;
         bool c_on_host = false;  // the pipelined GEMM copied C back block by block
@@ -1393,10 +1529,11 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             }
         } else if (gpu) {
             bool copies = false;
-            for (int b : ins) copies |= !p->bufs[(size_t)b].vd;
+            auto planes_only = [&](int b) { return p->bufs[(size_t)b].gen_for == li; };  // read as planes
+            for (int b : ins) copies |= !p->bufs[(size_t)b].vd && !planes_only(b);
             if (copies) GAO_CUDA_TRY(record_timing(ev[0], p->st));
             for (int b : ins)
-                if ((status = make_valid(R, b, true, S)) != GAO_OK) break;
+                if (!planes_only(b) && (status = make_valid(R, b, true, S)) != GAO_OK) break;
             if (status != GAO_OK) break;
             if (copies) {
                 GAO_CUDA_TRY(record_timing(ev[1], p->st));
@@ -1570,7 +1707,16 @@ extern "C" gao_status prog_output(gao_prog* p, int buf, const void** host_ptr, g
 extern "C" gao_status prog_device_ptr(gao_prog* p, int buf, void** dev_ptr) {
     if (!p || !dev_ptr) return fail(GAO_EINVAL, "null argument");
     if (buf < 0 || buf >= (int)p->bufs.size()) return fail(GAO_EINVAL, "no such buffer");
-    *dev_ptr = p->bufs[(size_t)buf].dev;
+    BufState& B = p->bufs[(size_t)buf];
+    if (!B.vd && !B.vh && B.gen_loop >= 0) {  // formed only as a GEMM's planes: form it now
+        cudaError_t ce = cudaSetDevice(p->device);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
+        RunCtx R{p, 0.0, false, CpuCtx{p->opts.cpu_threads, 0.0, false}, p->st, false};
+        gao_status s = materialize(R, buf);
+        if (s != GAO_OK) return s;
+        if ((ce = cudaStreamSynchronize(p->st)) != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+    }
+    *dev_ptr = B.dev;
     return GAO_OK;
 }
 
@@ -1837,6 +1983,12 @@ extern "C" gao_status prog_autotune(gao_prog* p, const gao_ga_params* params, ga
     gao_status st = prog_run(p, all, GAO_RUN_KEEP_DEVICE, &s0);  // puts the GEMM's inputs on the device
     if (st != GAO_OK) return st;
     const gao_loop& L = p->loops[(size_t)li];
+    {  // ... as binary32 also where the run formed them only as the GEMM's planes
+        RunCtx R{p, 0.0, false, CpuCtx{p->opts.cpu_threads, 0.0, false}, p->st, false};
+        gao_loop_stat dummy{};
+        for (int b : {L.ins[0], L.ins[1]})
+            if ((st = make_valid(R, b, true, dummy)) != GAO_OK) return st;
+    }
     const gao_buffer &A = p->bufs[(size_t)L.ins[0]].d, &B = p->bufs[(size_t)L.ins[1]].d;
     float* C = (float*)p->bufs[(size_t)L.outs[0]].dev;
     const float* C0 = L.ins[2] >= 0 ? (const float*)p->bufs[(size_t)L.ins[2]].dev : C;
