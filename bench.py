@@ -383,12 +383,17 @@ def fused_groups(prog, stats):
     return groups
 
 
-def group_bytes(prog, idx) -> float:
+def group_bytes(prog, idx, planes=None) -> float:
     """Algorithmic bytes of loops run as one pass: the buffers it reads that it does not
     produce, read once, and the buffers it produces that are OUTPUTs or read after it,
-    written once."""
+    written once -- as bfloat16 planes (P x 2 bytes per element) for an INIT output the
+    library formed straight into a GEMM's operand planes (planes: buffer -> P)."""
+    planes = planes or {}
+
     def nbytes(b):
         B = prog.buffers[b]
+        if b in planes:
+            return B.rows * B.cols * 2 * planes[b]
         return B.rows * B.cols * (8 if B.dtype == W.F64 else 4)
     produced, reads, writes = set(), set(), []
     for i in idx:
@@ -405,7 +410,15 @@ def group_bytes(prog, idx) -> float:
     return float(sum(nbytes(b) for b in reads) + sum(nbytes(o) for o in live))
 
 
-def pass_gbs(prog, stats, loop_ms, steps, hbm):
+def planes_of_run(gao, p, prog, prec):
+    """Buffers the last run formed only as a GEMM's bfloat16 planes -> planes per element."""
+    P = {"bf16": 1, "bf16x3": 2, "bf16x6": 3}.get(prec)
+    if P is None:
+        return {}
+    return {b: P for b in range(len(prog.buffers)) if gao.prog_planes_for(p, b) >= 0}
+
+
+def pass_gbs(prog, stats, loop_ms, steps, hbm, planes=None):
     """GB/s of every memory-bound pass (a loop, or loops fused into one pass) from the
     per-loop CUDA-event times; a fused pass is keyed by its first loop and its length."""
     out = {}
@@ -413,7 +426,7 @@ def pass_gbs(prog, stats, loop_ms, steps, hbm):
         lp = prog.loops[head]
         if lp.kind == W.GEMM or loop_ms[head] <= 0:
             continue
-        g = group_bytes(prog, idx) / (loop_ms[head] / steps / 1e3) / 1e9
+        g = group_bytes(prog, idx, planes) / (loop_ms[head] / steps / 1e3) / 1e9
         key = f"L{head}_{W.KIND_NAMES[lp.kind]}" + (f"+{len(idx) - 1}fused" if len(idx) > 1 else "")
         out[key] = {"gbs": round(g, 1), "hbm_frac": round(g / hbm, 3)}
     return out
@@ -530,7 +543,7 @@ def gemm_arm(args, world, rank, local):
     graph_replay = gao.prog_graphs(p)[0] > 0
     pk = peaks()
     hbm = pk.get("hbm_gbs", FALLBACK["hbm_gbs"])
-    loop_gbs = pass_gbs(prog, T["stats"], T["loop_ms"], args.steps, hbm)
+    loop_gbs = pass_gbs(prog, T["stats"], T["loop_ms"], args.steps, hbm, planes_of_run(gao, p, prog, prec))
     loop_ms = {f"L{i}_{W.KIND_NAMES[lp.kind]}": round(v / args.steps, 4)
                for i, (lp, v) in enumerate(zip(prog.loops, T["loop_ms"]))}
 
@@ -589,8 +602,21 @@ def gemm_arm(args, world, rank, local):
     if tc:
         peak, how, sus = tensor_peak(prec, pk)
         bf16 = pk.get("bf16_tflops", FALLBACK["bf16_tflops"])
+        # DRAM bytes per launch from the ncu summary of this configuration, else of the
+        # library's default configuration of the same kernel (named, since the raster group
+        # and prefetch change the traffic)
+        traffic_src = f"gemm_tc_{prec}_gemm_n{n}_k{kc}_t{tcfg}.md"
+        traffic = profile_traffic("gemm_tc.cu", traffic_src)
+        if traffic is None:
+            for alt in (f"gemm_tc_{prec}_gemm_n{n}_k256_t0.md", f"gemm_tc_{prec}_gemm_n{n}.md"):
+                traffic = profile_traffic("gemm_tc.cu", alt)
+                if traffic is not None:
+                    traffic_src = alt
+                    break
+        if traffic is None:
+            traffic_src = None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": profile_traffic("gemm_tc.cu", f"gemm_tc_{prec}_gemm_n{n}_k{kc}_t{tcfg}.md"),
+                "traffic": traffic, "traffic_profile": traffic_src,
                 "kernel": f"gemm_tc ({prec})", "products": PRODUCTS[prec],
                 "hw_tflops": achieved * PRODUCTS[prec], "hw_frac": achieved * PRODUCTS[prec] / bf16,
                 "frac_of_sustained": achieved / sus, "peak_source": how,
@@ -781,7 +807,7 @@ def twelve_result(args, gao, torch, stream, m=16384, k=4096, prec="bf16x3"):
     steps = 10
     T = timed_steps(gao, p, mask, steps, 3, stream, 1, 1, clk)
     hbm = peaks().get("hbm_gbs", FALLBACK["hbm_gbs"])
-    gbs = pass_gbs(prog, T["stats"], T["loop_ms"], steps, hbm)
+    gbs = pass_gbs(prog, T["stats"], T["loop_ms"], steps, hbm, planes_of_run(gao, p, prog, prec))
     gao.prog_run(p, mask)
     err = sampled_gemm_err(gao.prog_output(p, prog.index("C")), prog.seed, False, m, m, k, 1)
     gao.prog_destroy(p)
@@ -858,7 +884,7 @@ def our_arm(args, world, rank, local):
     graph_replay = gao.prog_graphs(p)[0] > 0
     pk = peaks()
     hbm = pk.get("hbm_gbs", FALLBACK["hbm_gbs"])
-    loop_gbs = pass_gbs(prog, T["stats"], T["loop_ms"], args.steps, hbm)
+    loop_gbs = pass_gbs(prog, T["stats"], T["loop_ms"], args.steps, hbm, planes_of_run(gao, p, prog, prec))
     loop_ms = {f"L{i}_{W.KIND_NAMES[lp.kind]}": round(v / args.steps, 4)
                for i, (lp, v) in enumerate(zip(prog.loops, T["loop_ms"]))}
     err = None

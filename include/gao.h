@@ -226,8 +226,20 @@ gao_status prog_run(gao_prog *p, uint64_t gene_mask, uint32_t flags, double *sec
  * run or destroy); *shape_out receives its shape.  GAO_EINVAL if not on the host. */
 gao_status prog_output(gao_prog *p, int buf, const void **host_ptr, gao_buffer *shape_out);
 
-/* Device pointer of buffer `buf` (for callers that keep data on the GPU). */
+/* Device pointer of buffer `buf` (for callers that keep data on the GPU).  A buffer the
+ * last run formed only as a GEMM's bfloat16 planes (prog_planes_for) gets its binary32
+ * values formed first (the INIT slot alone, on the program's stream, waited for). */
 gao_status prog_device_ptr(gao_prog *p, int buf, void **dev_ptr);
+
+/* INIT into GEMM operand planes: a TEMP buffer that an INIT loop writes and that only one
+ * GEMM reads -- as its A or B, on the GPU, in split bfloat16 without a fused chain, with
+ * resident transfers -- is formed by the INIT loop straight into that GEMM's bfloat16
+ * planes (the counter hash's values split as the GEMM's split kernels would; the GEMM then
+ * skips them), and its binary32 array is not written.  *gemm_loop = that GEMM loop if the
+ * last run formed buffer `buf` this way and nothing has formed its binary32 values since,
+ * else -1.  Anything that reads the buffer afterwards (prog_gemm_residual, prog_device_ptr,
+ * prog_autotune) forms it from the INIT slot first. */
+gao_status prog_planes_for(const gao_prog *p, int buf, int *gemm_loop);
 
 typedef struct gao_loop_stat {
     int32_t placement;  /* 1: ran on the GPU, 0: on the CPU, 2: on the GPU inside the

@@ -118,6 +118,7 @@ SIGNATURES = {
                                          ctypes.c_int]),
     "prog_loop_offload": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "prog_device_ptr": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "prog_planes_for": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "prog_stats": (ctypes.c_int, [_P, ctypes.POINTER(gao_loop_stat), ctypes.c_int]),
     "prog_cache_clear": (ctypes.c_int, [_P]),
     "prog_destroy": (None, [_P]),
@@ -402,6 +403,14 @@ def prog_device_ptr(p: Prog, buf: int) -> int:
     ptr = ctypes.c_void_p(None)
     _check(lib().prog_device_ptr(p.handle, buf, ctypes.byref(ptr)), "prog_device_ptr")
     return int(ptr.value or 0)
+
+
+def prog_planes_for(p: Prog, buf: int) -> int:
+    """The GEMM loop whose bfloat16 planes the last run formed buffer `buf` into (the INIT
+    loop skipped its binary32 array), or -1."""
+    g = ctypes.c_int(-1)
+    _check(lib().prog_planes_for(p.handle, buf, ctypes.byref(g)), "prog_planes_for")
+    return g.value
 
 
 def _residual_dict(r: "gao_residual") -> Dict:

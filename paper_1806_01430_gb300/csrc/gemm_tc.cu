@@ -1206,8 +1206,18 @@ __global__ void init_split_rows_kernel(uint64_t seed, uint32_t buf, const int8_t
                                        int64_t K, int64_t Mp, int64_t Kp, __nv_bfloat16* __restrict__ out) {
     const int64_t gpr = Kp / 8;
     const int64_t total = Mp * gpr;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = g / gpr, k0 = (g % gpr) * 8;
+    // (row, group) of the grid-stride index advanced by the stride's quotient and remainder
+    // (no 64-bit division in the loop)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t di = stride / gpr, dq = stride % gpr;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t i = g / gpr, q8 = g % gpr;
+    for (; g < total; g += stride, i += di, q8 += dq) {
+        if (q8 >= gpr) {
+            q8 -= gpr;
+            ++i;
+        }
+        const int64_t k0 = q8 * 8;
         float x[8];
         if (i < M && k0 + 8 <= K) {
             init_gen8(seed, buf, (uint64_t)(i * K + k0), x);

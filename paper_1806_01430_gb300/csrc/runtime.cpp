@@ -1720,6 +1720,13 @@ extern "C" gao_status prog_device_ptr(gao_prog* p, int buf, void** dev_ptr) {
     return GAO_OK;
 }
 
+extern "C" gao_status prog_planes_for(const gao_prog* p, int buf, int* gemm_loop) {
+    if (!p || !gemm_loop) return fail(GAO_EINVAL, "null argument");
+    if (buf < 0 || buf >= (int)p->bufs.size()) return fail(GAO_EINVAL, "no such buffer");
+    *gemm_loop = p->bufs[(size_t)buf].gen_for;
+    return GAO_OK;
+}
+
 extern "C" gao_status prog_gemm_residual(gao_prog* p, int loop, const double* x, const double* y,
                                          gao_residual* out) {
     if (!p || !x || !y || !out) return fail(GAO_EINVAL, "null argument");

@@ -56,6 +56,8 @@ def test_init_planes_match_split_path(gao, prec, kchunk, cfg, shape):
     # INIT: C0 as binary32, A and B as planes (3 launches); GEMM: the MMA alone
     assert st[0]["launches"] == 3 and st[1]["launches"] == 1
     assert st_ref[0]["launches"] == 1 and st_ref[1]["launches"] == 3
+    assert [gao.prog_planes_for(p, b) for b in range(4)] == [1, 1, -1, -1]
+    assert [gao.prog_planes_for(q, b) for b in range(4)] == [-1, -1, -1, -1]
     # a second run (graph replay) gives the same bits
     gao.prog_run(p, 0b11)
     assert np.array_equal(gao.prog_output(p, 3).view(np.uint32), C_ref.view(np.uint32))
@@ -84,7 +86,9 @@ def test_init_planes_residual_forms_operands_on_demand(gao):
     assert st[1]["launches"] == 1
     rng = np.random.default_rng(3)
     x, y = rng.choice([-1.0, 1.0], n), rng.choice([-1.0, 1.0], n)
+    assert gao.prog_planes_for(p, 0) == 1
     r = gao.prog_gemm_residual(p, 1, x, y)
+    assert gao.prog_planes_for(p, 0) == -1  # formed as binary32 for the check
     r_ref = gao.prog_gemm_residual(q, 1, x, y)
     assert r["right"] == r_ref["right"] and r["left"] == r_ref["left"]
     assert max(r["right"], r["left"]) <= 1e-6
