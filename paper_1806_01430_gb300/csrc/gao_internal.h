@@ -150,11 +150,26 @@ struct EwChain {
     EwChainOp op[kMaxChainOps];
 };
 cudaError_t launch_ew_chain(const EwChain& c, cudaStream_t st);
+// Reductions of the gradient chain's m formed in the same pass (whole image only): the sum
+// (binary64, from one partial per block of the pass in `part`, at least grad_chain_blocks
+// entries, added in index order) and the column maxima (order-preserving keys in `keys`,
+// one per column, decoded into colmax_out).  Either output may be null.
+struct GradReduce {
+    double* sum_out;
+    double* part;
+    int64_t part_cap;
+    float* colmax_out;
+    uint32_t* keys;
+};
+int64_t grad_chain_blocks(int64_t rows, int64_t cols);
 // Gradient chain in one pass: g1, g2 = stencils p1, p2 of `in`; s1 = g1*g1, s2 = g2*g2;
-// m = s1 + alpha s2 (swap: s2 + alpha s1).  Null g1/g2/s1/s2 are not written.
+// m = s1 + alpha s2 (swap: s2 + alpha s1).  Null g1/g2/s1/s2 are not written.  With `red`,
+// also the sum and / or column maxima of m, and m may then be null (formed for the
+// reductions only); *launches counts the kernels issued.
 cudaError_t launch_grad_chain(const float* in, int64_t rows, int64_t cols, int p1, int p2, float alpha, bool swap,
                               float* g1, float* g2, float* s1, float* s2, float* m, cudaStream_t st,
-                              int64_t row_begin = 0, int64_t row_end = -1);
+                              int64_t row_begin = 0, int64_t row_end = -1, const GradReduce* red = nullptr,
+                              int* launches = nullptr);
 
 // Weights of the 3x3 stencil presets of GAO_LOOP_STENCIL3, row-major over (a, b).
 // Every weight is a small integer or a power-of-two fraction, exact in binary32.

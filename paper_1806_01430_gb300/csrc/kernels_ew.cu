@@ -525,6 +525,11 @@ struct StencilOut {
     float* m;
     float alpha;
     int swap;
+    // the sum and the column maxima of m in the same pass (either may be null): one binary64
+    // partial per block (a compensated binary32 sum of each thread's four-column partials,
+    // threads combined in binary64 by a fixed tree), and order-preserving keys per column
+    double* part;
+    uint32_t* keys;
 };
 
 template <bool VEC>
@@ -558,10 +563,12 @@ __device__ __forceinline__ float stencil9(const StencilW& w, const float* up, co
 constexpr int kChainAhead = 2;   // rows of loads in flight in the chain variant
 constexpr int kChainBlocks = 8;  // resident blocks per SM the chain variant is built for
 
-template <bool VEC, bool CHAIN, int P1, int P2>
+template <bool VEC, bool CHAIN, int P1, int P2, bool RED = false>
 __global__ void __launch_bounds__(kStencilThreads, CHAIN ? kChainBlocks : 8)
     stencil3_kernel(StencilOut out, const float* __restrict__ in, int64_t rows, int64_t cols, StencilW w,
                     StencilW w2, int strip, int64_t row_begin, int64_t row_end) {
+    float rs = 0.0f, rc = 0.0f;                   // RED: this thread's compensated sum of m
+    uint32_t mk[4] = {0u, 0u, 0u, 0u};            // RED: its columns' maxima (keys)
     constexpr int AHEAD = CHAIN ? kChainAhead : kStencilAhead;
     const int lane = threadIdx.x & 31;
     const int64_t c0 = ((int64_t)blockIdx.x * kStencilThreads + threadIdx.x) * 4;
@@ -606,7 +613,16 @@ __global__ void __launch_bounds__(kStencilThreads, CHAIN ? kChainBlocks : 8)
                 if (out.g2) store4<VEC>(out.g2 + off, c0, cols, o2);
                 if (out.s1) store4<VEC>(out.s1 + off, c0, cols, a);
                 if (out.s2) store4<VEC>(out.s2 + off, c0, cols, b);
-                store4<VEC>(out.m + off, c0, cols, m);
+                if (!RED || out.m) store4<VEC>(out.m + off, c0, cols, m);  // m consumed in the pass only: not written
+                if constexpr (RED) {
+                    float v[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        v[q] = c0 + q < cols ? m[q] : 0.0f;
+                        if (c0 + q < cols) mk[q] = max(mk[q], fmax_key(__float_as_uint(m[q])));
+                    }
+                    if (out.part) comp_add(rs, rc, (v[0] + v[1]) + (v[2] + v[3]));
+                }
             }
 #pragma unroll
             for (int t = 0; t < 6; ++t) {
@@ -614,6 +630,45 @@ __global__ void __launch_bounds__(kStencilThreads, CHAIN ? kChainBlocks : 8)
                 md[t] = dn[t];
             }
         }
+    }
+    if constexpr (RED) {
+        if (out.keys && r1 > r0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c0 + q < cols) atomicMax(out.keys + c0 + q, mk[q]);  // max: exact and order-free
+        }
+        if (out.part) {
+            __shared__ double wsum[kStencilThreads / 32];
+            double acc = (double)rs + (double)rc;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) wsum[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double b = 0.0;
+#pragma unroll
+                for (int k = 0; k < kStencilThreads / 32; ++k) b += wsum[k];
+                out.part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = b;
+            }
+        }
+    }
+}
+
+// The block partials of a fused sum, added in index order by one block (fixed partition and
+// tree).
+__global__ void __launch_bounds__(256) sum_partials_kernel(const double* __restrict__ part, int64_t n,
+                                                           double* __restrict__ out) {
+    __shared__ double w[8];
+    double t = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) t += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < 8; ++k) u += w[k];
+        *out = u;
     }
 }
 
@@ -758,6 +813,20 @@ cudaError_t launch_colmax(float* out, const float* in, int64_t rows, int64_t col
 }
 
 namespace {
+// Grid of a stencil pass over `span` output rows: column blocks of 512 columns, and strips of
+// rows for two waves of the resident 128-thread blocks (8 per SM), at least 16 rows per
+// strip so that the two halo rows stay a small share.
+void stencil_grid(int64_t span, int64_t cols, bool chain, int64_t* gx, int64_t* strip, int64_t* gy) {
+    *gx = ((cols + 3) / 4 + kStencilThreads - 1) / kStencilThreads;
+    const int64_t want_blocks = (int64_t)sm_count() * 2 * (chain ? kChainBlocks : 8);
+    const int64_t strips = (want_blocks + *gx - 1) / *gx;
+    int64_t s = (span + strips - 1) / strips;
+    if (s < 16) s = 16;
+    if ((span + s - 1) / s > 65535) s = (span + 65534) / 65535;
+    *strip = s;
+    *gy = (span + s - 1) / s;
+}
+
 cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t rows, int64_t cols, int p1, int p2,
                                 bool chain, int64_t row_begin, int64_t row_end, cudaStream_t st) {
     StencilW w, w2;
@@ -766,25 +835,32 @@ cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t ro
     if (row_begin < 0 || row_end > rows || row_begin > row_end) return cudaErrorInvalidValue;
     const int64_t span = row_end - row_begin;  // output rows of this launch
     if (span <= 0 || cols <= 0) return cudaSuccess;
-    const int64_t gx = ((cols + 3) / 4 + kStencilThreads - 1) / kStencilThreads;
-    if (gx > 0x7fffffff) return cudaErrorInvalidValue;
-    // strips of rows: two waves of the resident 128-thread blocks (8 per SM at <= 64
-    // registers, 6 for the chain), and at least 16 rows per strip so that the two halo
-    // rows stay a small share
-    const int64_t want_blocks = (int64_t)sm_count() * 2 * (chain ? kChainBlocks : 8);
-    int64_t strips = (want_blocks + gx - 1) / gx;
-    int64_t strip = (span + strips - 1) / strips;
-    if (strip < 16) strip = 16;
-    if ((span + strip - 1) / strip > 65535) strip = (span + 65534) / 65535;
-    if (strip > 0x7fffffff) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)gx, (unsigned)((span + strip - 1) / strip));
+    int64_t gx, strip, gy;
+    stencil_grid(span, cols, chain, &gx, &strip, &gy);
+    if (gx > 0x7fffffff || strip > 0x7fffffff) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)gx, (unsigned)gy);
     uintptr_t ptrs = (uintptr_t)in | (uintptr_t)o.m | (uintptr_t)o.g1 | (uintptr_t)o.g2 | (uintptr_t)o.s1 |
                      (uintptr_t)o.s2;
     const bool vec = (cols % 4 == 0) && (ptrs & 15u) == 0;
     const int sp = (int)strip;
 #define GAO_STENCIL_LAUNCH(V, C, A, B) \
     stencil3_kernel<V, C, A, B><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, sp, row_begin, row_end)
-    if (chain) {
+#define GAO_STENCIL_LAUNCH_RED(V, A, B)                                                                     \
+    stencil3_kernel<V, true, A, B, true><<<grid, kStencilThreads, 0, st>>>(o, in, rows, cols, w, w2, sp, row_begin, \
+                                                                          row_end)
+    if (chain && (o.part || o.keys)) {
+        // the sum and column maxima of m in the same pass (the image program's pair only)
+        if (p1 == 2 && p2 == 3) {
+            if (vec) GAO_STENCIL_LAUNCH_RED(true, 2, 3);
+            else GAO_STENCIL_LAUNCH_RED(false, 2, 3);
+        } else if (p1 == 3 && p2 == 2) {
+            if (vec) GAO_STENCIL_LAUNCH_RED(true, 3, 2);
+            else GAO_STENCIL_LAUNCH_RED(false, 3, 2);
+        } else {
+            if (vec) GAO_STENCIL_LAUNCH_RED(true, -1, -1);
+            else GAO_STENCIL_LAUNCH_RED(false, -1, -1);
+        }
+    } else if (chain) {
         // the image program's pair (Sobel x, Sobel y) with compile-time weights; any
         // other pair with run-time weights
         if (p1 == 2 && p2 == 3) {
@@ -806,22 +882,55 @@ cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t ro
         }
     }
 #undef GAO_STENCIL_LAUNCH
+#undef GAO_STENCIL_LAUNCH_RED
     return cudaGetLastError();
 }
 }  // namespace
 
+int64_t grad_chain_blocks(int64_t rows, int64_t cols) {
+    if (rows <= 0 || cols <= 0) return 0;
+    int64_t gx, strip, gy;
+    stencil_grid(rows, cols, true, &gx, &strip, &gy);
+    return gx * gy;
+}
+
 cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st,
                             int64_t row_begin, int64_t row_end) {
-    const StencilOut o{out, nullptr, nullptr, nullptr, nullptr, 0.0f, 0};
+    const StencilOut o{out, nullptr, nullptr, nullptr, nullptr, 0.0f, 0, nullptr, nullptr};
     return launch_stencil_pass(o, in, rows, cols, preset, preset, false, row_begin, row_end < 0 ? rows : row_end, st);
 }
 
 cudaError_t launch_grad_chain(const float* in, int64_t rows, int64_t cols, int p1, int p2, float alpha, bool swap,
                               float* g1, float* g2, float* s1, float* s2, float* m, cudaStream_t st,
-                              int64_t row_begin, int64_t row_end) {
-    if (!m) return cudaErrorInvalidValue;
-    const StencilOut o{g1, g2, s1, s2, m, alpha, swap ? 1 : 0};
-    return launch_stencil_pass(o, in, rows, cols, p1, p2, true, row_begin, row_end < 0 ? rows : row_end, st);
+                              int64_t row_begin, int64_t row_end, const GradReduce* red, int* launches) {
+    if (!m && !(red && (red->sum_out || red->colmax_out))) return cudaErrorInvalidValue;
+    if (launches) *launches = 0;
+    const bool full = row_begin == 0 && (row_end < 0 || row_end == rows);
+    if (red && (!full || (red->sum_out && (!red->part || red->part_cap < grad_chain_blocks(rows, cols))) ||
+                (red->colmax_out && !red->keys)))
+        return cudaErrorInvalidValue;
+    const bool want_sum = red && red->sum_out, want_max = red && red->colmax_out;
+    const StencilOut o{g1, g2, s1, s2, m, alpha, swap ? 1 : 0, want_sum ? red->part : nullptr,
+                       want_max ? red->keys : nullptr};
+    cudaError_t e;
+    if (want_max && cols > 0) {
+        if ((e = cudaMemsetAsync(red->keys, 0, (size_t)cols * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    }
+    if ((e = launch_stencil_pass(o, in, rows, cols, p1, p2, true, row_begin, row_end < 0 ? rows : row_end, st)) !=
+        cudaSuccess)
+        return e;
+    if (launches) *launches += rows > 0 && cols > 0;
+    if (want_sum) {
+        sum_partials_kernel<<<1, 256, 0, st>>>(red->part, grad_chain_blocks(rows, cols), red->sum_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (launches) *launches += 1;
+    }
+    if (want_max && cols > 0) {
+        colmax_decode_kernel<<<grid_for(cols), kThreads, 0, st>>>(red->colmax_out, red->keys, cols, rows);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (launches) *launches += 1;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_wait_selftest(int* flag, int* err, double limit_s, cudaStream_t st) {

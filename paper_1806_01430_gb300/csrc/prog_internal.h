@@ -34,6 +34,7 @@ struct Layout {
     size_t err_off = 0, partial_off = 0, counter_off = 0, keys_off = 0, rowexp_off = 0, tc_off = 0;
     size_t tc_bytes = 0, keys_bytes = 0, rowexp_bytes = 0;
     size_t resid_off = 0, resid_bytes = 0;  // GEMM residual check: x, y, then its scratch
+    size_t chainpart_off = 0, chainpart_bytes = 0;  // gradient chain's fused sum: block partials
     size_t total = 0;
 };
 

@@ -274,10 +274,12 @@ Layout plan(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bu
     off += align_up((size_t)reduce_blocks() * sizeof(double));
     L.counter_off = off;
     off += kAlign;
-    size_t keys = 1, rows = 1, tc = 0, resid = 0;
+    size_t keys = 1, rows = 1, tc = 0, resid = 0, chainpart = 0;
     for (int i = 0; i < n_loops; ++i) {
         const gao_loop& lp = loops[i];
         if (lp.kind == GAO_LOOP_COLMAX) keys = std::max(keys, (size_t)bufs[lp.ins[0]].cols * 4);
+        if (lp.kind == GAO_LOOP_STENCIL3)  // a gradient chain's fused sum: one partial per block
+            chainpart = std::max(chainpart, (size_t)grad_chain_blocks(bufs[lp.ins[0]].rows, bufs[lp.ins[0]].cols) * 8);
         if (lp.kind == GAO_LOOP_INIT)
             for (int t = 0; t < GAO_MAX_IO; ++t)
                 if (lp.outs[t] >= 0 && ((lp.flags >> t) & 1)) rows = std::max(rows, (size_t)bufs[lp.outs[t]].rows);
@@ -304,6 +306,9 @@ Layout plan(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bu
     L.resid_off = off;
     L.resid_bytes = resid;
     off += align_up(resid);
+    L.chainpart_off = off;
+    L.chainpart_bytes = chainpart;
+    off += align_up(chainpart);
     L.total = off;
     return L;
 }
@@ -834,9 +839,13 @@ struct GradChain {
     float alpha = 1.0f;
     bool swap = false;
     bool live[4] = {true, true, true, true};  // g1, g2, s1, s2
+    // with `reductions`: a SUM and / or a COLMAX loop of m right after the chain (li + 5 ..
+    // li + 6, on the GPU), formed in the same pass
+    int sum_loop = -1, colmax_loop = -1;
+    bool m_live = true;  // m itself is written: an OUTPUT, or read after the pass
 };
 
-bool find_grad_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, GradChain* gc) {
+bool find_grad_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, GradChain* gc, bool reductions = false) {
     if (!fuse || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT) return false;
     const int n = (int)p->loops.size();
     if (li + 4 >= n) return false;
@@ -879,6 +888,22 @@ bool find_grad_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, GradCh
                 if (b == inter[t]) live = true;
         c.live[t] = live;
     }
+    if (reductions) {
+        for (int j = li + 5; j <= li + 6 && j < n && ((mask >> j) & 1); ++j) {
+            const gao_loop& R = p->loops[(size_t)j];
+            if (R.ins[0] != c.m || R.outs[0] < 0 || R.outs[0] == c.m) break;
+            if (R.kind == GAO_LOOP_SUM && c.sum_loop < 0) c.sum_loop = j;
+            else if (R.kind == GAO_LOOP_COLMAX && c.colmax_loop < 0) c.colmax_loop = j;
+            else break;
+        }
+    }
+    // m is written only if it is an OUTPUT or a loop after the pass (its fused reductions
+    // included in the pass) reads it
+    const int last = std::max(li + 4, std::max(c.sum_loop, c.colmax_loop));
+    c.m_live = p->bufs[(size_t)c.m].d.role == GAO_BUF_OUTPUT;
+    for (int j = last + 1; j < n && !c.m_live; ++j)
+        for (int b : loop_inputs(p->loops[(size_t)j]))
+            if (b == c.m) c.m_live = true;
     *gc = c;
     return true;
 }
@@ -1330,7 +1355,7 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             if (R.timed_out) break;
             continue;
         }
-        if (gpu && L.kind == GAO_LOOP_STENCIL3 && find_grad_chain(p, li, gene_mask, fuse, &gch)) {
+        if (gpu && L.kind == GAO_LOOP_STENCIL3 && find_grad_chain(p, li, gene_mask, fuse, &gch, true)) {
             BufState& X = p->bufs[(size_t)gch.x];
             const bool copies = !X.vd;
             if (copies) GAO_CUDA_TRY(record_timing(ev[0], p->st));
@@ -1341,25 +1366,45 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             }
             auto dptr = [&](int b, bool live) { return live ? (float*)p->bufs[(size_t)b].dev : nullptr; };
             GAO_CUDA_TRY(record_timing(ev[2], p->st));
+            // the sum and the column maxima of m that follow the chain, in the same pass
+            GradReduce red{};
+            if (gch.sum_loop >= 0) {
+                red.sum_out = (double*)p->bufs[(size_t)p->loops[(size_t)gch.sum_loop].outs[0]].dev;
+                red.part = (double*)(p->arena + p->lay.chainpart_off);
+                red.part_cap = (int64_t)(p->lay.chainpart_bytes / 8);
+            }
+            if (gch.colmax_loop >= 0) {
+                red.colmax_out = (float*)p->bufs[(size_t)p->loops[(size_t)gch.colmax_loop].outs[0]].dev;
+                red.keys = (uint32_t*)(p->arena + p->lay.keys_off);
+            }
+            const bool reduce = gch.sum_loop >= 0 || gch.colmax_loop >= 0;
+            int nl = 0;
             const cudaError_t e = launch_grad_chain((const float*)X.dev, X.d.rows, X.d.cols, gch.p1, gch.p2,
                                                    gch.alpha, gch.swap, dptr(gch.g1, gch.live[0]),
                                                    dptr(gch.g2, gch.live[1]), dptr(gch.s1, gch.live[2]),
-                                                   dptr(gch.s2, gch.live[3]), (float*)p->bufs[(size_t)gch.m].dev,
-                                                   p->st);
+                                                   dptr(gch.s2, gch.live[3]), dptr(gch.m, gch.m_live),
+                                                   p->st, 0, -1, reduce ? &red : nullptr, &nl);
             if (e != cudaSuccess) {
                 status = cuda_fail(e, "gradient chain launch");
                 break;
             }
             GAO_CUDA_TRY(record_timing(ev[3], p->st));
             p->ev_used[(size_t)li] |= 2;
-            S.launches += X.d.rows * X.d.cols > 0;
+            S.launches += nl;
             const int outs[5] = {gch.g1, gch.g2, gch.s1, gch.s2, gch.m};
             for (int t = 0; t < 5; ++t) {
                 BufState& B = p->bufs[(size_t)outs[t]];
                 B.vh = false;
-                B.vd = t == 4 || gch.live[t];  // an unwritten intermediate holds nothing
+                B.vd = t == 4 ? gch.m_live : gch.live[t];  // an unwritten intermediate holds nothing
             }
             for (int j = li + 1; j <= li + 4; ++j) fused |= 1ULL << j;
+            for (int j : {gch.sum_loop, gch.colmax_loop}) {
+                if (j < 0) continue;
+                fused |= 1ULL << j;
+                BufState& B = p->bufs[(size_t)p->loops[(size_t)j].outs[0]];
+                B.vh = false;
+                B.vd = true;
+            }
             if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
             if (R.timed_out) break;
             continue;
