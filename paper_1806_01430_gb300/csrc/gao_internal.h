@@ -150,18 +150,27 @@ struct EwChain {
     EwChainOp op[kMaxChainOps];
 };
 cudaError_t launch_ew_chain(const EwChain& c, cudaStream_t st);
-// Reductions of the gradient chain's m formed in the same pass (whole image only): the sum
-// (binary64, from one partial per block of the pass in `part`, at least grad_chain_blocks
-// entries, added in index order) and the column maxima (order-preserving keys in `keys`,
-// one per column, decoded into colmax_out).  Either output may be null.
+// Reductions of the gradient chain's m formed in the same pass: the sum (binary64, from one
+// partial per block of the pass in `part`, added in index order) and the column maxima
+// (order-preserving keys in `keys`, one per column, decoded into colmax_out).  Either output
+// may be null.  An image may be covered by several row-range launches in row order (the
+// strips of a frame that arrives from the host): the first (`first`) clears the keys, each
+// writes its partials from part[part_at] on (grad_chain_blocks(its rows, cols) of them), and
+// the last (`last`) adds part[0 .. part_at + its own) and decodes the keys.  A single
+// launch over the whole image is first and last with part_at = 0, as the defaults say.
 struct GradReduce {
     double* sum_out;
     double* part;
     int64_t part_cap;
     float* colmax_out;
     uint32_t* keys;
+    int64_t part_at = 0;
+    bool first = true, last = true;
 };
+// Blocks of a gradient-chain pass over `rows` output rows (a launch's row range) of width cols.
 int64_t grad_chain_blocks(int64_t rows, int64_t cols);
+// The most blocks any gradient-chain launch of width cols has, whatever its row range.
+int64_t grad_chain_blocks_max(int64_t cols);
 // Gradient chain in one pass: g1, g2 = stencils p1, p2 of `in`; s1 = g1*g1, s2 = g2*g2;
 // m = s1 + alpha s2 (swap: s2 + alpha s1).  Null g1/g2/s1/s2 are not written.  With `red`,
 // also the sum and / or column maxima of m, and m may then be null (formed for the

@@ -894,6 +894,16 @@ int64_t grad_chain_blocks(int64_t rows, int64_t cols) {
     return gx * gy;
 }
 
+// At most this many blocks in any gradient-chain launch of width cols: stencil_grid makes
+// strips of at least ceil(span / strips) rows, so a launch has at most `strips` of them.
+int64_t grad_chain_blocks_max(int64_t cols) {
+    if (cols <= 0) return 0;
+    int64_t gx, strip, gy;
+    stencil_grid(1, cols, true, &gx, &strip, &gy);
+    const int64_t want_blocks = (int64_t)sm_count() * 2 * kChainBlocks;
+    return gx * ((want_blocks + gx - 1) / gx);
+}
+
 cudaError_t launch_stencil3(float* out, const float* in, int64_t rows, int64_t cols, int preset, cudaStream_t st,
                             int64_t row_begin, int64_t row_end) {
     const StencilOut o{out, nullptr, nullptr, nullptr, nullptr, 0.0f, 0, nullptr, nullptr};
@@ -905,27 +915,26 @@ cudaError_t launch_grad_chain(const float* in, int64_t rows, int64_t cols, int p
                               int64_t row_begin, int64_t row_end, const GradReduce* red, int* launches) {
     if (!m && !(red && (red->sum_out || red->colmax_out))) return cudaErrorInvalidValue;
     if (launches) *launches = 0;
-    const bool full = row_begin == 0 && (row_end < 0 || row_end == rows);
-    if (red && (!full || (red->sum_out && (!red->part || red->part_cap < grad_chain_blocks(rows, cols))) ||
-                (red->colmax_out && !red->keys)))
-        return cudaErrorInvalidValue;
+    if (row_end < 0) row_end = rows;
+    if (row_begin < 0 || row_end > rows || row_begin > row_end) return cudaErrorInvalidValue;
     const bool want_sum = red && red->sum_out, want_max = red && red->colmax_out;
-    const StencilOut o{g1, g2, s1, s2, m, alpha, swap ? 1 : 0, want_sum ? red->part : nullptr,
+    const int64_t nblk = grad_chain_blocks(row_end - row_begin, cols);  // this launch's partials
+    if (want_sum && (!red->part || red->part_at < 0 || red->part_cap < red->part_at + nblk)) return cudaErrorInvalidValue;
+    if (want_max && !red->keys) return cudaErrorInvalidValue;
+    const StencilOut o{g1, g2, s1, s2, m, alpha, swap ? 1 : 0, want_sum ? red->part + red->part_at : nullptr,
                        want_max ? red->keys : nullptr};
     cudaError_t e;
-    if (want_max && cols > 0) {
+    if (want_max && red->first && cols > 0) {
         if ((e = cudaMemsetAsync(red->keys, 0, (size_t)cols * sizeof(uint32_t), st)) != cudaSuccess) return e;
     }
-    if ((e = launch_stencil_pass(o, in, rows, cols, p1, p2, true, row_begin, row_end < 0 ? rows : row_end, st)) !=
-        cudaSuccess)
-        return e;
-    if (launches) *launches += rows > 0 && cols > 0;
-    if (want_sum) {
-        sum_partials_kernel<<<1, 256, 0, st>>>(red->part, grad_chain_blocks(rows, cols), red->sum_out);
+    if ((e = launch_stencil_pass(o, in, rows, cols, p1, p2, true, row_begin, row_end, st)) != cudaSuccess) return e;
+    if (launches) *launches += nblk > 0;
+    if (want_sum && red->last) {
+        sum_partials_kernel<<<1, 256, 0, st>>>(red->part, red->part_at + nblk, red->sum_out);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (launches) *launches += 1;
     }
-    if (want_max && cols > 0) {
+    if (want_max && red->last && cols > 0) {
         colmax_decode_kernel<<<grid_for(cols), kThreads, 0, st>>>(red->colmax_out, red->keys, cols, rows);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (launches) *launches += 1;

@@ -278,8 +278,11 @@ Layout plan(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bu
     for (int i = 0; i < n_loops; ++i) {
         const gao_loop& lp = loops[i];
         if (lp.kind == GAO_LOOP_COLMAX) keys = std::max(keys, (size_t)bufs[lp.ins[0]].cols * 4);
-        if (lp.kind == GAO_LOOP_STENCIL3)  // a gradient chain's fused sum: one partial per block
-            chainpart = std::max(chainpart, (size_t)grad_chain_blocks(bufs[lp.ins[0]].rows, bufs[lp.ins[0]].cols) * 8);
+        if (lp.kind == GAO_LOOP_STENCIL3)  // a gradient chain's fused sum: one partial per block,
+            // over one launch or over the row strips of a frame copied in from the host
+            chainpart = std::max(chainpart, (size_t)(std::max(grad_chain_blocks(bufs[lp.ins[0]].rows, bufs[lp.ins[0]].cols),
+                                                              kMaxRowBlocks * grad_chain_blocks_max(bufs[lp.ins[0]].cols)) *
+                                                     8));
         if (lp.kind == GAO_LOOP_INIT)
             for (int t = 0; t < GAO_MAX_IO; ++t)
                 if (lp.outs[t] >= 0 && ((lp.flags >> t) & 1)) rows = std::max(rows, (size_t)bufs[lp.outs[t]].rows);
@@ -904,8 +907,45 @@ bool find_grad_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, GradCh
     for (int j = last + 1; j < n && !c.m_live; ++j)
         for (int b : loop_inputs(p->loops[(size_t)j]))
             if (b == c.m) c.m_live = true;
+    if (c.sum_loop < 0 && c.colmax_loop < 0) c.m_live = true;  // the pass writes at least m
     *gc = c;
     return true;
+}
+
+// Where the chain's fused sum and column maxima go: the SUM loop's and COLMAX loop's outputs,
+// the block partials and the column keys in the arena.
+GradReduce grad_reduce_for(const gao_prog* p, const GradChain& gch) {
+    GradReduce red{};
+    if (gch.sum_loop >= 0) {
+        red.sum_out = (double*)p->bufs[(size_t)p->loops[(size_t)gch.sum_loop].outs[0]].dev;
+        red.part = (double*)(p->arena + p->lay.chainpart_off);
+        red.part_cap = (int64_t)(p->lay.chainpart_bytes / 8);
+    }
+    if (gch.colmax_loop >= 0) {
+        red.colmax_out = (float*)p->bufs[(size_t)p->loops[(size_t)gch.colmax_loop].outs[0]].dev;
+        red.keys = (uint32_t*)(p->arena + p->lay.keys_off);
+    }
+    return red;
+}
+
+// Residency after the chain starting at loop first ran as one pass (with its reductions):
+// what it wrote is valid on the device only, an unwritten intermediate holds nothing, and its
+// loops are marked as run.
+void grad_chain_done(gao_prog* p, const GradChain& gch, int first, uint64_t* fused) {
+    const int outs[5] = {gch.g1, gch.g2, gch.s1, gch.s2, gch.m};
+    for (int t = 0; t < 5; ++t) {
+        BufState& B = p->bufs[(size_t)outs[t]];
+        B.vh = false;
+        B.vd = t == 4 ? gch.m_live : gch.live[t];
+    }
+    for (int j = first + 1; j <= first + 4; ++j) *fused |= 1ULL << j;
+    for (int j : {gch.sum_loop, gch.colmax_loop}) {
+        if (j < 0) continue;
+        *fused |= 1ULL << j;
+        BufState& B = p->bufs[(size_t)p->loops[(size_t)j].outs[0]];
+        B.vh = false;
+        B.vd = true;
+    }
 }
 
 // A linear chain of element-wise loops starting at loop li that the gene puts on the GPU:
@@ -1188,6 +1228,11 @@ gao_status run_gpu_stencil_pipelined(RunCtx& R, int li, const GradChain* gch) {
     GAO_CUDA_TRY(record_timing(ev[2], st));
     const int preset = (int)(L.flags & ~GAO_LOOP_EXTERNAL_CALL);
     auto chain_ptr = [&](int b, bool live) { return live ? (float*)p->bufs[(size_t)b].dev : nullptr; };
+    // the chain's sum and column maxima across the strips: keys cleared by the first strip,
+    // partials laid out strip after strip, added and decoded after the last
+    GradReduce red{};
+    if (gch) red = grad_reduce_for(p, *gch);
+    const bool reduce = gch && (gch->sum_loop >= 0 || gch->colmax_loop >= 0);
     int64_t formed = 0, chained = 0;  // output rows done by the stencil and by the chain
     for (int k = 0; k < nb; ++k) {
         GAO_CUDA_TRY(cudaStreamWaitEvent(st, p->pipe_ev[2 + (size_t)k], 0));
@@ -1201,12 +1246,17 @@ gao_status run_gpu_stencil_pipelined(RunCtx& R, int li, const GradChain* gch) {
         if (gch) {
             const int64_t c1 = k == nb - 1 ? rows : formed - 1;  // row r needs stencil row r + 1
             if (c1 > chained) {
+                red.first = chained == 0;
+                red.last = c1 == rows;
+                int nl = 0;
                 cudaError_t e = launch_grad_chain(out, rows, cols, gch->p1, gch->p2, gch->alpha, gch->swap,
                                                   chain_ptr(gch->g1, gch->live[0]), chain_ptr(gch->g2, gch->live[1]),
                                                   chain_ptr(gch->s1, gch->live[2]), chain_ptr(gch->s2, gch->live[3]),
-                                                  (float*)p->bufs[(size_t)gch->m].dev, st, chained, c1);
+                                                  chain_ptr(gch->m, gch->m_live), st, chained, c1,
+                                                  reduce ? &red : nullptr, &nl);
                 if (e != cudaSuccess) return cuda_fail(e, "gradient chain strip launch");
-                S.launches += 1;
+                S.launches += nl;
+                red.part_at += grad_chain_blocks(c1 - chained, cols);
                 chained = c1;
             }
         }
@@ -1336,20 +1386,15 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
         if (gpu && stencil_pipelined(p, L)) {
             // the image comes from the host: strips overlapped with its copy, with the
             // gradient chain on this stencil's output in the same strips when the gene fuses it
-            const bool chained = li + 1 < n && find_grad_chain(p, li + 1, gene_mask, fuse, &gch) &&
+            const bool chained = li + 1 < n && find_grad_chain(p, li + 1, gene_mask, fuse, &gch, true) &&
                                  gch.x == L.outs[0];
             if ((status = run_gpu_stencil_pipelined(R, li, chained ? &gch : nullptr)) != GAO_OK) break;
             BufState& Bo = p->bufs[(size_t)L.outs[0]];
             Bo.vh = false;
             Bo.vd = true;
             if (chained) {
-                const int outs[5] = {gch.g1, gch.g2, gch.s1, gch.s2, gch.m};
-                for (int t = 0; t < 5; ++t) {
-                    BufState& B = p->bufs[(size_t)outs[t]];
-                    B.vh = false;
-                    B.vd = t == 4 || gch.live[t];  // an unwritten intermediate holds nothing
-                }
-                for (int j = li + 1; j <= li + 5; ++j) fused |= 1ULL << j;
+                grad_chain_done(p, gch, li + 1, &fused);
+                fused |= 1ULL << (li + 1);
             }
             if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
             if (R.timed_out) break;
@@ -1367,16 +1412,7 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             auto dptr = [&](int b, bool live) { return live ? (float*)p->bufs[(size_t)b].dev : nullptr; };
             GAO_CUDA_TRY(record_timing(ev[2], p->st));
             // the sum and the column maxima of m that follow the chain, in the same pass
-            GradReduce red{};
-            if (gch.sum_loop >= 0) {
-                red.sum_out = (double*)p->bufs[(size_t)p->loops[(size_t)gch.sum_loop].outs[0]].dev;
-                red.part = (double*)(p->arena + p->lay.chainpart_off);
-                red.part_cap = (int64_t)(p->lay.chainpart_bytes / 8);
-            }
-            if (gch.colmax_loop >= 0) {
-                red.colmax_out = (float*)p->bufs[(size_t)p->loops[(size_t)gch.colmax_loop].outs[0]].dev;
-                red.keys = (uint32_t*)(p->arena + p->lay.keys_off);
-            }
+            const GradReduce red = grad_reduce_for(p, gch);
             const bool reduce = gch.sum_loop >= 0 || gch.colmax_loop >= 0;
             int nl = 0;
             const cudaError_t e = launch_grad_chain((const float*)X.dev, X.d.rows, X.d.cols, gch.p1, gch.p2,
@@ -1391,20 +1427,7 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             GAO_CUDA_TRY(record_timing(ev[3], p->st));
             p->ev_used[(size_t)li] |= 2;
             S.launches += nl;
-            const int outs[5] = {gch.g1, gch.g2, gch.s1, gch.s2, gch.m};
-            for (int t = 0; t < 5; ++t) {
-                BufState& B = p->bufs[(size_t)outs[t]];
-                B.vh = false;
-                B.vd = t == 4 ? gch.m_live : gch.live[t];  // an unwritten intermediate holds nothing
-            }
-            for (int j = li + 1; j <= li + 4; ++j) fused |= 1ULL << j;
-            for (int j : {gch.sum_loop, gch.colmax_loop}) {
-                if (j < 0) continue;
-                fused |= 1ULL << j;
-                BufState& B = p->bufs[(size_t)p->loops[(size_t)j].outs[0]];
-                B.vh = false;
-                B.vd = true;
-            }
+            grad_chain_done(p, gch, li, &fused);
             if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
             if (R.timed_out) break;
             continue;
