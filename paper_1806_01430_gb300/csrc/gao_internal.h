@@ -180,6 +180,17 @@ cudaError_t launch_grad_chain(const float* in, int64_t rows, int64_t cols, int p
                               int64_t row_begin = 0, int64_t row_end = -1, const GradReduce* red = nullptr,
                               int* launches = nullptr);
 
+// The image program's first stencil and the gradient chain on its output in one pass over
+// the raw image `in`: B = p0(in), written to bout only if bout is non-null; g1, g2 = stencils
+// p1, p2 of B; s1, s2, m and the reductions as launch_grad_chain.  Row ranges, `red` and
+// *launches as there, with edge_chain_blocks partials per launch.
+cudaError_t launch_edge_chain(const float* in, float* bout, int64_t rows, int64_t cols, int p0, int p1, int p2,
+                              float alpha, bool swap, float* g1, float* g2, float* s1, float* s2, float* m,
+                              cudaStream_t st, int64_t row_begin = 0, int64_t row_end = -1,
+                              const GradReduce* red = nullptr, int* launches = nullptr);
+int64_t edge_chain_blocks(int64_t rows, int64_t cols);
+int64_t edge_chain_blocks_max(int64_t cols);
+
 // Weights of the 3x3 stencil presets of GAO_LOOP_STENCIL3, row-major over (a, b).
 // Every weight is a small integer or a power-of-two fraction, exact in binary32.
 #ifdef __CUDACC__

@@ -654,6 +654,229 @@ __global__ void __launch_bounds__(kStencilThreads, CHAIN ? kChainBlocks : 8)
     }
 }
 
+// ---- the blur and the gradient chain in one pass ----------------------------------------
+//
+// The image program's first stencil P0 (the blur, B = P0(X)) and the gradient chain on its
+// output (g1 = P1(B), g2 = P2(B), their squares, m = s1 + alpha s2, and with RED the sum and
+// column maxima of m), formed in one pass over the raw image X.  Each thread walks down a
+// strip of rows holding two raw rows and three rows of B in registers: at output row r it
+// forms B's row r + 1 from raw rows r .. r + 2 and the chain's row r from B's rows r - 1 ..
+// r + 1, so neither B nor the chain's intermediates go through memory (B is written only when
+// something else reads it).  B is zero outside the image, as the separate loops pad it, and
+// every value is formed with the separate loops' operations, so the bits are theirs.
+// Lanes hold four columns each; lanes 1 .. 30 of a warp produce its 120 output columns, and
+// lanes 0 and 31 hold the four columns either side, whose raw values and B values their
+// neighbours take by shuffle, so no lane loads an edge column of its own.
+constexpr int kEdgeNC = 8;          // columns a lane holds (a multiple of 4)
+constexpr int kEdgeCols = 30 * kEdgeNC;  // output columns of a warp (lanes 1 .. 30)
+constexpr int kEdgeBlocks = 5;      // resident 128-thread blocks per SM the kernel is built for
+constexpr int kEdgeAhead = 1;       // raw rows of loads in flight
+constexpr int kEdgeBlockCols = kEdgeCols * (kStencilThreads / 32);  // output columns of a block
+
+// A lane's columns c0 .. c0 + kEdgeNC - 1 of one raw row (zero outside the image): with 16-byte
+// rows, groups of four that are each wholly inside or outside the image.
+struct EdgeRow {
+    float4 g[kEdgeNC / 4];
+};
+
+template <bool VEC>
+__device__ __forceinline__ void edge_load(EdgeRow& r, const float* __restrict__ in, int64_t y, int64_t ylim,
+                                          int64_t cols, int64_t c0, const bool inc[kEdgeNC]) {
+#pragma unroll
+    for (int k = 0; k < kEdgeNC / 4; ++k) r.g[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (y < 0 || y >= ylim) return;
+    const float* p = in + y * cols + c0;
+#pragma unroll
+    for (int k = 0; k < kEdgeNC / 4; ++k) {
+        if (VEC) {
+            if (inc[4 * k]) r.g[k] = __ldg(reinterpret_cast<const float4*>(p + 4 * k));
+        } else {
+            if (inc[4 * k]) r.g[k].x = __ldg(p + 4 * k);
+            if (inc[4 * k + 1]) r.g[k].y = __ldg(p + 4 * k + 1);
+            if (inc[4 * k + 2]) r.g[k].z = __ldg(p + 4 * k + 2);
+            if (inc[4 * k + 3]) r.g[k].w = __ldg(p + 4 * k + 3);
+        }
+    }
+}
+
+// The values c0 - 1 .. c0 + kEdgeNC of a row whose columns c0 .. c0 + kEdgeNC - 1 this lane
+// holds in b (the first and last lane's outer values are not used).
+__device__ __forceinline__ void edge_spread(float v[kEdgeNC + 2], const float b[kEdgeNC]) {
+    v[0] = __shfl_up_sync(0xffffffffu, b[kEdgeNC - 1], 1);
+#pragma unroll
+    for (int q = 0; q < kEdgeNC; ++q) v[q + 1] = b[q];
+    v[kEdgeNC + 1] = __shfl_down_sync(0xffffffffu, b[0], 1);
+}
+
+__device__ __forceinline__ void edge_flat(float b[kEdgeNC], const EdgeRow& r) {
+#pragma unroll
+    for (int k = 0; k < kEdgeNC / 4; ++k) {
+        b[4 * k] = r.g[k].x;
+        b[4 * k + 1] = r.g[k].y;
+        b[4 * k + 2] = r.g[k].z;
+        b[4 * k + 3] = r.g[k].w;
+    }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void edge_store(float* row, int64_t c0, const bool outc[kEdgeNC], const float v[kEdgeNC]) {
+#pragma unroll
+    for (int k = 0; k < kEdgeNC / 4; ++k) {
+        if (VEC) {
+            if (outc[4 * k])
+                *reinterpret_cast<float4*>(row + c0 + 4 * k) = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int q = 4 * k; q < 4 * k + 4; ++q)
+                if (outc[q]) row[c0 + q] = v[q];
+        }
+    }
+}
+
+template <bool VEC, int P0, int P1, int P2, bool RED, bool STORE>
+__global__ void __launch_bounds__(kStencilThreads, kEdgeBlocks)
+    edge_chain_kernel(StencilOut out, float* __restrict__ bout, const float* __restrict__ in, int64_t rows,
+                      int64_t cols, StencilW w0, StencilW w1, StencilW w2, int strip, int64_t row_begin,
+                      int64_t row_end) {
+    constexpr int NC = kEdgeNC;
+    float rs = 0.0f, rc = 0.0f;  // RED: this thread's compensated sum of m
+    uint32_t mk[NC];             // RED: its columns' maxima (keys)
+#pragma unroll
+    for (int q = 0; q < NC; ++q) mk[q] = 0u;
+    const int lane = threadIdx.x & 31;
+    const int64_t c0 = ((int64_t)blockIdx.x * (kStencilThreads / 32) + (threadIdx.x >> 5)) * kEdgeCols - NC + NC * lane;
+    bool inc[NC], outc[NC];  // column c0 + q inside the image; and produced by this lane
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        const int64_t c = VEC ? c0 + (q & ~3) : c0 + q;  // with 16-byte rows, by groups of four
+        inc[q] = c >= 0 && c < cols;
+        outc[q] = inc[q] && lane >= 1 && lane <= 30;
+    }
+    // output rows [r0, r1) of this block's strip; raw rows r0 - 2 .. r1 + 1 are read
+    const int64_t r0 = row_begin + (int64_t)blockIdx.y * strip;
+    const int64_t r1 = r0 + strip < row_end ? r0 + strip : row_end;
+    const int64_t ylim = r1 + 2 < rows ? r1 + 2 : rows;
+    // B's row from the raw rows above, at and below it (zero outside the image)
+    auto blur = [&](float b[NC], const float* xu, const float* xm, const float* xd, bool row_in) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) b[q] = (row_in && inc[q]) ? stencil9<P0>(w0, xu, xm, xd, q) : 0.0f;
+    };
+    auto store_b = [&](int64_t y, const float b[NC]) {
+        if (STORE && bout && y >= r0 && y < r1) edge_store<VEC>(bout + y * cols, c0, outc, b);
+    };
+    float xa[NC + 2], xb[NC + 2];  // raw rows r, r + 1
+    float ba[NC + 2], bb[NC + 2];  // B's rows r - 1, r
+    {
+        EdgeRow v;
+        float x0[NC + 2], f[NC], t[NC];
+        edge_load<VEC>(v, in, r0 - 2, ylim, cols, c0, inc);
+        edge_flat(f, v);
+        edge_spread(x0, f);
+        edge_load<VEC>(v, in, r0 - 1, ylim, cols, c0, inc);
+        edge_flat(f, v);
+        edge_spread(xa, f);
+        edge_load<VEC>(v, in, r0, ylim, cols, c0, inc);
+        edge_flat(f, v);
+        edge_spread(xb, f);
+        blur(t, x0, xa, xb, r0 >= 1);  // B's row r0 - 1
+        edge_spread(ba, t);
+        edge_load<VEC>(v, in, r0 + 1, ylim, cols, c0, inc);
+        edge_flat(f, v);
+        edge_spread(x0, f);
+        blur(t, xa, xb, x0, r0 < rows);  // B's row r0
+        store_b(r0, t);
+        edge_spread(bb, t);
+#pragma unroll
+        for (int k = 0; k < NC + 2; ++k) {
+            xa[k] = xb[k];
+            xb[k] = x0[k];
+        }
+    }
+    EdgeRow ring[kEdgeAhead];  // raw rows r + 2 .. r + 1 + kEdgeAhead, in flight
+#pragma unroll
+    for (int k = 0; k < kEdgeAhead; ++k) edge_load<VEC>(ring[k], in, r0 + 2 + k, ylim, cols, c0, inc);
+    for (int64_t i = r0; i < r1; i += kEdgeAhead) {
+#pragma unroll
+        for (int k = 0; k < kEdgeAhead; ++k) {
+            const int64_t row = i + k;
+            if (row >= r1) break;  // block-uniform
+            float xn[NC + 2], bn[NC], bc[NC + 2], f[NC];
+            edge_flat(f, ring[k]);
+            edge_spread(xn, f);  // raw row + 2
+            edge_load<VEC>(ring[k], in, row + 2 + kEdgeAhead, ylim, cols, c0, inc);
+            blur(bn, xa, xb, xn, row + 1 < rows);  // B's row + 1
+            store_b(row + 1, bn);
+            edge_spread(bc, bn);
+            float o[NC], o2[NC], a[NC], b[NC], m[NC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                o[q] = stencil9<P1>(w1, ba, bb, bc, q);
+                o2[q] = stencil9<P2>(w2, ba, bb, bc, q);
+                a[q] = __fmul_rn(o[q], o[q]);
+                b[q] = __fmul_rn(o2[q], o2[q]);
+                m[q] = out.swap ? __fmaf_rn(out.alpha, a[q], b[q]) : __fmaf_rn(out.alpha, b[q], a[q]);
+            }
+            if constexpr (STORE) {
+                const int64_t off = row * cols;
+                if (out.g1) edge_store<VEC>(out.g1 + off, c0, outc, o);
+                if (out.g2) edge_store<VEC>(out.g2 + off, c0, outc, o2);
+                if (out.s1) edge_store<VEC>(out.s1 + off, c0, outc, a);
+                if (out.s2) edge_store<VEC>(out.s2 + off, c0, outc, b);
+                if (out.m) edge_store<VEC>(out.m + off, c0, outc, m);  // null when only the reductions read m
+            }
+            if constexpr (RED) {
+                // the keys of every column are kept and only those of produced columns are
+                // raised at the end; the sum takes produced values only: with 16-byte rows a
+                // lane that produces none (the warp's outer lanes, lanes right of the image)
+                // sums values that are dropped at the end, and only the groups of four right
+                // of the image in a lane that produces some are zeroed here
+#pragma unroll
+                for (int q = 0; q < NC; ++q) mk[q] = max(mk[q], fmax_key(__float_as_uint(m[q])));
+                if (out.part) {
+                    float v[NC];
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) v[q] = (VEC ? (q < 4 || inc[q]) : outc[q]) ? m[q] : 0.0f;
+                    float t = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < NC / 4; ++k) {
+                        const float g = (v[4 * k] + v[4 * k + 1]) + (v[4 * k + 2] + v[4 * k + 3]);
+                        t = k == 0 ? g : t + g;
+                    }
+                    comp_add(rs, rc, t);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < NC + 2; ++t) {
+                xa[t] = xb[t];
+                xb[t] = xn[t];
+                ba[t] = bb[t];
+                bb[t] = bc[t];
+            }
+        }
+    }
+    if constexpr (RED) {
+        if (out.keys && r1 > r0) {
+#pragma unroll
+            for (int q = 0; q < NC; ++q)
+                if (outc[q]) atomicMax(out.keys + c0 + q, mk[q]);  // max: exact and order-free
+        }
+        if (out.part) {
+            __shared__ double wsum[kStencilThreads / 32];
+            double acc = (!VEC || outc[0]) ? (double)rs + (double)rc : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) wsum[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double b = 0.0;
+#pragma unroll
+                for (int k = 0; k < kStencilThreads / 32; ++k) b += wsum[k];
+                out.part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = b;
+            }
+        }
+    }
+}
+
 // The block partials of a fused sum, added in index order by one block (fixed partition and
 // tree).
 __global__ void __launch_bounds__(256) sum_partials_kernel(const double* __restrict__ part, int64_t n,
@@ -886,6 +1109,110 @@ cudaError_t launch_stencil_pass(const StencilOut& o, const float* in, int64_t ro
     return cudaGetLastError();
 }
 }  // namespace
+
+namespace {
+// Grid of a blur + gradient-chain pass over `span` output rows: blocks of 480 output columns,
+// and strips of rows for two waves of the resident blocks, at least 16 rows per strip (each
+// strip reads four raw rows beyond its own).
+void edge_grid(int64_t span, int64_t cols, int64_t* gx, int64_t* strip, int64_t* gy) {
+    *gx = (cols + kEdgeBlockCols - 1) / kEdgeBlockCols;
+    const int64_t want_blocks = (int64_t)sm_count() * 2 * kEdgeBlocks;
+    const int64_t strips = (want_blocks + *gx - 1) / *gx;
+    int64_t s = (span + strips - 1) / strips;
+    if (s < 16) s = 16;
+    if ((span + s - 1) / s > 65535) s = (span + 65534) / 65535;
+    *strip = s;
+    *gy = (span + s - 1) / s;
+}
+}  // namespace
+
+int64_t edge_chain_blocks(int64_t rows, int64_t cols) {
+    if (rows <= 0 || cols <= 0) return 0;
+    int64_t gx, strip, gy;
+    edge_grid(rows, cols, &gx, &strip, &gy);
+    return gx * gy;
+}
+
+// At most this many blocks in any blur + gradient-chain launch of width cols (as for the
+// chain alone: a launch has at most `strips` strips).
+int64_t edge_chain_blocks_max(int64_t cols) {
+    if (cols <= 0) return 0;
+    const int64_t gx = (cols + kEdgeBlockCols - 1) / kEdgeBlockCols;
+    const int64_t want_blocks = (int64_t)sm_count() * 2 * kEdgeBlocks;
+    return gx * ((want_blocks + gx - 1) / gx);
+}
+
+cudaError_t launch_edge_chain(const float* in, float* bout, int64_t rows, int64_t cols, int p0, int p1, int p2,
+                              float alpha, bool swap, float* g1, float* g2, float* s1, float* s2, float* m,
+                              cudaStream_t st, int64_t row_begin, int64_t row_end, const GradReduce* red,
+                              int* launches) {
+    if (!m && !(red && (red->sum_out || red->colmax_out))) return cudaErrorInvalidValue;
+    if (launches) *launches = 0;
+    if (row_end < 0) row_end = rows;
+    if (row_begin < 0 || row_end > rows || row_begin > row_end) return cudaErrorInvalidValue;
+    StencilW w0, w1, w2;
+    if (!stencil_weights(p0, w0.w) || !stencil_weights(p1, w1.w) || !stencil_weights(p2, w2.w))
+        return cudaErrorInvalidValue;
+    const bool want_sum = red && red->sum_out, want_max = red && red->colmax_out;
+    const int64_t span = row_end - row_begin;
+    const int64_t nblk = edge_chain_blocks(span, cols);  // this launch's partials
+    if (want_sum && (!red->part || red->part_at < 0 || red->part_cap < red->part_at + nblk)) return cudaErrorInvalidValue;
+    if (want_max && !red->keys) return cudaErrorInvalidValue;
+    const StencilOut o{g1, g2, s1, s2, m, alpha, swap ? 1 : 0, want_sum ? red->part + red->part_at : nullptr,
+                       want_max ? red->keys : nullptr};
+    cudaError_t e;
+    if (want_max && red->first && cols > 0) {
+        if ((e = cudaMemsetAsync(red->keys, 0, (size_t)cols * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    }
+    if (span > 0 && cols > 0) {
+        int64_t gx, strip, gy;
+        edge_grid(span, cols, &gx, &strip, &gy);
+        if (gx > 0x7fffffff || strip > 0x7fffffff) return cudaErrorInvalidValue;
+        const dim3 grid((unsigned)gx, (unsigned)gy);
+        const uintptr_t ptrs = (uintptr_t)in | (uintptr_t)bout | (uintptr_t)m | (uintptr_t)g1 | (uintptr_t)g2 |
+                               (uintptr_t)s1 | (uintptr_t)s2;
+        const bool vec = (cols % 4 == 0) && (ptrs & 15u) == 0;
+        const bool reduce = want_sum || want_max;
+        const bool stores = bout || m || g1 || g2 || s1 || s2;  // per-pixel outputs (else reductions only)
+        const int sp = (int)strip;
+#define GAO_EDGE_LAUNCH(V, A, B, C, R, S)                                                                \
+    edge_chain_kernel<V, A, B, C, R, S><<<grid, kStencilThreads, 0, st>>>(o, bout, in, rows, cols, w0, w1, w2, \
+                                                                         sp, row_begin, row_end)
+#define GAO_EDGE_PAIR(A, B, C)                                          \
+    do {                                                                \
+        if (reduce && !stores) {                                        \
+            if (vec) GAO_EDGE_LAUNCH(true, A, B, C, true, false);       \
+            else GAO_EDGE_LAUNCH(false, A, B, C, true, false);          \
+        } else if (reduce) {                                            \
+            if (vec) GAO_EDGE_LAUNCH(true, A, B, C, true, true);        \
+            else GAO_EDGE_LAUNCH(false, A, B, C, true, true);           \
+        } else {                                                        \
+            if (vec) GAO_EDGE_LAUNCH(true, A, B, C, false, true);       \
+            else GAO_EDGE_LAUNCH(false, A, B, C, false, true);          \
+        }                                                               \
+    } while (0)
+        // the image program's stencils (binomial blur, then Sobel x and Sobel y) with
+        // compile-time weights; any other triple with run-time weights
+        if (p0 == 0 && p1 == 2 && p2 == 3) GAO_EDGE_PAIR(0, 2, 3);
+        else if (p0 == 0 && p1 == 3 && p2 == 2) GAO_EDGE_PAIR(0, 3, 2);
+        else GAO_EDGE_PAIR(-1, -1, -1);
+#undef GAO_EDGE_PAIR
+#undef GAO_EDGE_LAUNCH
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (launches) *launches += 1;
+    }
+    if (want_sum && red->last) {
+        sum_partials_kernel<<<1, 256, 0, st>>>(red->part, red->part_at + nblk, red->sum_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (launches) *launches += 1;
+    }
+    if (want_max && red->last && cols > 0) {
+        colmax_decode_kernel<<<grid_for(cols), kThreads, 0, st>>>(red->colmax_out, red->keys, cols, rows);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (launches) *launches += 1;
+    }
+    return cudaSuccess;
+}
 
 int64_t grad_chain_blocks(int64_t rows, int64_t cols) {
     if (rows <= 0 || cols <= 0) return 0;

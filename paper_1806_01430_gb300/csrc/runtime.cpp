@@ -278,11 +278,14 @@ Layout plan(const gao_loop* loops, int n_loops, const gao_buffer* bufs, int n_bu
     for (int i = 0; i < n_loops; ++i) {
         const gao_loop& lp = loops[i];
         if (lp.kind == GAO_LOOP_COLMAX) keys = std::max(keys, (size_t)bufs[lp.ins[0]].cols * 4);
-        if (lp.kind == GAO_LOOP_STENCIL3)  // a gradient chain's fused sum: one partial per block,
-            // over one launch or over the row strips of a frame copied in from the host
-            chainpart = std::max(chainpart, (size_t)(std::max(grad_chain_blocks(bufs[lp.ins[0]].rows, bufs[lp.ins[0]].cols),
-                                                              kMaxRowBlocks * grad_chain_blocks_max(bufs[lp.ins[0]].cols)) *
-                                                     8));
+        if (lp.kind == GAO_LOOP_STENCIL3) {  // a gradient chain's fused sum: one partial per block,
+            // over one launch or over the row strips of a frame copied in from the host, of the
+            // chain alone or with the blur before it
+            const int64_t r = bufs[lp.ins[0]].rows, c = bufs[lp.ins[0]].cols;
+            const int64_t blocks = std::max({grad_chain_blocks(r, c), kMaxRowBlocks * grad_chain_blocks_max(c),
+                                             edge_chain_blocks(r, c), kMaxRowBlocks * edge_chain_blocks_max(c)});
+            chainpart = std::max(chainpart, (size_t)blocks * 8);
+        }
         if (lp.kind == GAO_LOOP_INIT)
             for (int t = 0; t < GAO_MAX_IO; ++t)
                 if (lp.outs[t] >= 0 && ((lp.flags >> t) & 1)) rows = std::max(rows, (size_t)bufs[lp.outs[t]].rows);
@@ -846,6 +849,10 @@ struct GradChain {
     // li + 6, on the GPU), formed in the same pass
     int sum_loop = -1, colmax_loop = -1;
     bool m_live = true;  // m itself is written: an OUTPUT, or read after the pass
+    // a stencil loop `pre` (preset p0) that forms x from the raw image `raw`, in the same pass
+    // (find_edge_chain); x is then written only when x_live
+    int pre = -1, raw = -1, p0 = 0;
+    bool x_live = true;
 };
 
 bool find_grad_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, GradChain* gc, bool reductions = false) {
@@ -912,6 +919,33 @@ bool find_grad_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, GradCh
     return true;
 }
 
+// A GPU STENCIL3 loop li (the blur) whose output x starts a gradient chain (with its
+// reductions): the blur joins the chain's pass, which then reads the raw image instead of x.
+// x is written only when it is an OUTPUT or a loop after the chain's two stencils reads it.
+bool find_edge_chain(const gao_prog* p, int li, uint64_t mask, bool fuse, GradChain* gc) {
+    const int n = (int)p->loops.size();
+    if (li + 1 >= n || !((mask >> li) & 1)) return false;
+    const gao_loop& L = p->loops[(size_t)li];
+    if (L.kind != GAO_LOOP_STENCIL3 || L.ins[0] == L.outs[0]) return false;
+    GradChain c;
+    if (!find_grad_chain(p, li + 1, mask, fuse, &c, true) || c.x != L.outs[0]) return false;
+    const int raw = L.ins[0];
+    const int made[6] = {c.x, c.g1, c.g2, c.s1, c.s2, c.m};
+    for (int b : made)
+        if (b == raw) return false;
+    for (int j : {c.sum_loop, c.colmax_loop})
+        if (j >= 0 && p->loops[(size_t)j].outs[0] == raw) return false;
+    c.pre = li;
+    c.raw = raw;
+    c.p0 = (int)(L.flags & ~GAO_LOOP_EXTERNAL_CALL);
+    c.x_live = p->bufs[(size_t)c.x].d.role == GAO_BUF_OUTPUT;
+    for (int j = li + 3; j < n && !c.x_live; ++j)
+        for (int b : loop_inputs(p->loops[(size_t)j]))
+            if (b == c.x) c.x_live = true;
+    *gc = c;
+    return true;
+}
+
 // Where the chain's fused sum and column maxima go: the SUM loop's and COLMAX loop's outputs,
 // the block partials and the column keys in the arena.
 GradReduce grad_reduce_for(const gao_prog* p, const GradChain& gch) {
@@ -928,9 +962,9 @@ GradReduce grad_reduce_for(const gao_prog* p, const GradChain& gch) {
     return red;
 }
 
-// Residency after the chain starting at loop first ran as one pass (with its reductions):
-// what it wrote is valid on the device only, an unwritten intermediate holds nothing, and its
-// loops are marked as run.
+// Residency after the chain starting at loop first ran as one pass (with its reductions, and
+// with the blur before it when gch.pre >= 0): what it wrote is valid on the device only, an
+// unwritten intermediate holds nothing, and its loops are marked as run.
 void grad_chain_done(gao_prog* p, const GradChain& gch, int first, uint64_t* fused) {
     const int outs[5] = {gch.g1, gch.g2, gch.s1, gch.s2, gch.m};
     for (int t = 0; t < 5; ++t) {
@@ -939,6 +973,12 @@ void grad_chain_done(gao_prog* p, const GradChain& gch, int first, uint64_t* fus
         B.vd = t == 4 ? gch.m_live : gch.live[t];
     }
     for (int j = first + 1; j <= first + 4; ++j) *fused |= 1ULL << j;
+    if (gch.pre >= 0) {  // the blur ran in the pass too: the chain's first loop with it
+        *fused |= 1ULL << first;
+        BufState& X = p->bufs[(size_t)gch.x];
+        X.vh = false;
+        X.vd = gch.x_live;
+    }
     for (int j : {gch.sum_loop, gch.colmax_loop}) {
         if (j < 0) continue;
         *fused |= 1ULL << j;
@@ -1191,9 +1231,10 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
 // Copy/compute overlap for a GPU STENCIL3 loop whose image comes from the host (a camera
 // frame, 30x slower to copy than to read from HBM): the frame is copied in row strips on
 // the copy stream, and as each strip lands the stencil forms the rows whose three input rows
-// are all in -- and the gradient chain on the stencil's output, when the gene fuses one
-// there, the rows whose three blurred rows are done.  A pixel is formed the same way
-// whatever the row ranges, so the bits are those of one launch.
+// are all in -- or, when the gene fuses the gradient chain on the stencil's output (gch,
+// from find_edge_chain), the blur and the chain in one pass form the rows whose five raw rows
+// are in.  A pixel is formed the same way whatever the row ranges, so the bits are those of
+// one launch.
 bool stencil_pipelined(const gao_prog* p, const gao_loop& L) {
     if (L.kind != GAO_LOOP_STENCIL3 || p->opts.transfer_mode != GAO_TRANSFER_RESIDENT) return false;
     const BufState& X = p->bufs[(size_t)L.ins[0]];
@@ -1233,32 +1274,35 @@ gao_status run_gpu_stencil_pipelined(RunCtx& R, int li, const GradChain* gch) {
     GradReduce red{};
     if (gch) red = grad_reduce_for(p, *gch);
     const bool reduce = gch && (gch->sum_loop >= 0 || gch->colmax_loop >= 0);
-    int64_t formed = 0, chained = 0;  // output rows done by the stencil and by the chain
+    int64_t formed = 0;  // output rows done
     for (int k = 0; k < nb; ++k) {
         GAO_CUDA_TRY(cudaStreamWaitEvent(st, p->pipe_ev[2 + (size_t)k], 0));
-        const int64_t f1 = k == nb - 1 ? rows : at[k + 1] - 1;  // row r needs input row r + 1
-        if (f1 > formed) {
-            cudaError_t e = launch_stencil3(out, (const float*)X.dev, rows, cols, preset, st, formed, f1);
-            if (e != cudaSuccess) return cuda_fail(e, "stencil strip launch");
-            S.launches += 1;
-            formed = f1;
-        }
-        if (gch) {
-            const int64_t c1 = k == nb - 1 ? rows : formed - 1;  // row r needs stencil row r + 1
-            if (c1 > chained) {
-                red.first = chained == 0;
-                red.last = c1 == rows;
-                int nl = 0;
-                cudaError_t e = launch_grad_chain(out, rows, cols, gch->p1, gch->p2, gch->alpha, gch->swap,
-                                                  chain_ptr(gch->g1, gch->live[0]), chain_ptr(gch->g2, gch->live[1]),
-                                                  chain_ptr(gch->s1, gch->live[2]), chain_ptr(gch->s2, gch->live[3]),
-                                                  chain_ptr(gch->m, gch->m_live), st, chained, c1,
-                                                  reduce ? &red : nullptr, &nl);
-                if (e != cudaSuccess) return cuda_fail(e, "gradient chain strip launch");
-                S.launches += nl;
-                red.part_at += grad_chain_blocks(c1 - chained, cols);
-                chained = c1;
+        if (!gch) {
+            const int64_t f1 = k == nb - 1 ? rows : at[k + 1] - 1;  // row r needs input row r + 1
+            if (f1 > formed) {
+                cudaError_t e = launch_stencil3(out, (const float*)X.dev, rows, cols, preset, st, formed, f1);
+                if (e != cudaSuccess) return cuda_fail(e, "stencil strip launch");
+                S.launches += 1;
+                formed = f1;
             }
+            continue;
+        }
+        // the blur and the chain in one pass: output row r needs raw rows up to r + 2
+        const int64_t f1 = k == nb - 1 ? rows : at[k + 1] - 2;
+        if (f1 > formed) {
+            red.first = formed == 0;
+            red.last = f1 == rows;
+            int nl = 0;
+            cudaError_t e = launch_edge_chain((const float*)X.dev, chain_ptr(gch->x, gch->x_live), rows, cols, gch->p0,
+                                              gch->p1, gch->p2, gch->alpha, gch->swap,
+                                              chain_ptr(gch->g1, gch->live[0]), chain_ptr(gch->g2, gch->live[1]),
+                                              chain_ptr(gch->s1, gch->live[2]), chain_ptr(gch->s2, gch->live[3]),
+                                              chain_ptr(gch->m, gch->m_live), st, formed, f1,
+                                              reduce ? &red : nullptr, &nl);
+            if (e != cudaSuccess) return cuda_fail(e, "blur and gradient chain strip launch");
+            S.launches += nl;
+            red.part_at += edge_chain_blocks(f1 - formed, cols);
+            formed = f1;
         }
     }
     GAO_CUDA_TRY(record_timing(ev[3], st));
@@ -1386,25 +1430,25 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
         if (gpu && stencil_pipelined(p, L)) {
             // the image comes from the host: strips overlapped with its copy, with the
             // gradient chain on this stencil's output in the same strips when the gene fuses it
-            const bool chained = li + 1 < n && find_grad_chain(p, li + 1, gene_mask, fuse, &gch, true) &&
-                                 gch.x == L.outs[0];
+            const bool chained = find_edge_chain(p, li, gene_mask, fuse, &gch);
             if ((status = run_gpu_stencil_pipelined(R, li, chained ? &gch : nullptr)) != GAO_OK) break;
             BufState& Bo = p->bufs[(size_t)L.outs[0]];
             Bo.vh = false;
             Bo.vd = true;
-            if (chained) {
-                grad_chain_done(p, gch, li + 1, &fused);
-                fused |= 1ULL << (li + 1);
-            }
+            if (chained) grad_chain_done(p, gch, li + 1, &fused);
             if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
             if (R.timed_out) break;
             continue;
         }
-        if (gpu && L.kind == GAO_LOOP_STENCIL3 && find_grad_chain(p, li, gene_mask, fuse, &gch, true)) {
-            BufState& X = p->bufs[(size_t)gch.x];
+        // a blur whose output starts a gradient chain: both in one pass over the raw image
+        // (edge); else a gradient chain starting here, in one pass over the blurred image
+        const bool edge = gpu && L.kind == GAO_LOOP_STENCIL3 && find_edge_chain(p, li, gene_mask, fuse, &gch);
+        if (edge || (gpu && L.kind == GAO_LOOP_STENCIL3 && find_grad_chain(p, li, gene_mask, fuse, &gch, true))) {
+            const int src = edge ? gch.raw : gch.x;  // the image the pass reads
+            BufState& X = p->bufs[(size_t)src];
             const bool copies = !X.vd;
             if (copies) GAO_CUDA_TRY(record_timing(ev[0], p->st));
-            if ((status = make_valid(R, gch.x, true, S)) != GAO_OK) break;
+            if ((status = make_valid(R, src, true, S)) != GAO_OK) break;
             if (copies) {
                 GAO_CUDA_TRY(record_timing(ev[1], p->st));
                 p->ev_used[(size_t)li] |= 1;
@@ -1415,19 +1459,24 @@ gao_status enqueue_run(RunCtx& R, uint64_t gene_mask, bool fuse, uint32_t flags)
             const GradReduce red = grad_reduce_for(p, gch);
             const bool reduce = gch.sum_loop >= 0 || gch.colmax_loop >= 0;
             int nl = 0;
-            const cudaError_t e = launch_grad_chain((const float*)X.dev, X.d.rows, X.d.cols, gch.p1, gch.p2,
-                                                   gch.alpha, gch.swap, dptr(gch.g1, gch.live[0]),
-                                                   dptr(gch.g2, gch.live[1]), dptr(gch.s1, gch.live[2]),
-                                                   dptr(gch.s2, gch.live[3]), dptr(gch.m, gch.m_live),
-                                                   p->st, 0, -1, reduce ? &red : nullptr, &nl);
+            const cudaError_t e =
+                edge ? launch_edge_chain((const float*)X.dev, dptr(gch.x, gch.x_live), X.d.rows, X.d.cols, gch.p0,
+                                         gch.p1, gch.p2, gch.alpha, gch.swap, dptr(gch.g1, gch.live[0]),
+                                         dptr(gch.g2, gch.live[1]), dptr(gch.s1, gch.live[2]),
+                                         dptr(gch.s2, gch.live[3]), dptr(gch.m, gch.m_live), p->st, 0, -1,
+                                         reduce ? &red : nullptr, &nl)
+                     : launch_grad_chain((const float*)X.dev, X.d.rows, X.d.cols, gch.p1, gch.p2, gch.alpha,
+                                         gch.swap, dptr(gch.g1, gch.live[0]), dptr(gch.g2, gch.live[1]),
+                                         dptr(gch.s1, gch.live[2]), dptr(gch.s2, gch.live[3]),
+                                         dptr(gch.m, gch.m_live), p->st, 0, -1, reduce ? &red : nullptr, &nl);
             if (e != cudaSuccess) {
-                status = cuda_fail(e, "gradient chain launch");
+                status = cuda_fail(e, edge ? "blur and gradient chain launch" : "gradient chain launch");
                 break;
             }
             GAO_CUDA_TRY(record_timing(ev[3], p->st));
             p->ev_used[(size_t)li] |= 2;
             S.launches += nl;
-            grad_chain_done(p, gch, li, &fused);
+            grad_chain_done(p, gch, edge ? li + 1 : li, &fused);
             if (R.deadline > 0.0 && now_s() > R.deadline) R.timed_out = true;
             if (R.timed_out) break;
             continue;

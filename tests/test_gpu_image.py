@@ -197,14 +197,15 @@ def test_full_size_8192(gao):
     assert abs(e - ref["e"]) <= float(bound.sum()) + SUM_REL * abs(ref["e"])
 
 
-@pytest.mark.parametrize("outputs", [("M2", "e", "q"), ("gx", "sy", "M2", "e", "q"), ("e", "q")])
-@pytest.mark.parametrize("hw", [(64, 64), (127, 257), (300, 1001)])
+@pytest.mark.parametrize("outputs", [("M2", "e", "q"), ("gx", "sy", "M2", "e", "q"), ("e", "q"), ("B", "e", "q")])
+@pytest.mark.parametrize("hw", [(64, 64), (127, 257), (300, 1001), (5, 481)])
 def test_fused_gradient_chain_bit_identical(gao, hw, outputs):
-    """Sobel x, Sobel y, the two squares and their sum in one pass over the blurred image,
-    with the edge energy (SUM) and the column maxima (COLMAX) of M2 formed in the same pass:
-    the same bits as the seven separate loops (the edge energy within its rounding bound: the
-    pass partitions the sum differently); dead intermediates are not written (M2 too, when
-    only the reductions read it)."""
+    """The blur, Sobel x, Sobel y, the two squares and their sum in one pass over the raw
+    image, with the edge energy (SUM) and the column maxima (COLMAX) of M2 formed in the same
+    pass: the same bits as the eight separate loops (the edge energy within its rounding
+    bound: the pass partitions the sum differently); the blurred image and the dead
+    intermediates are not written (M2 too, when only the reductions read it) unless they are
+    outputs.  Widths around a warp's 120 output columns and a block's 480 included."""
     h, w = hw
     prog = W.image_program(h, w, W.SEED_IMAGE + 3, outputs=outputs)
     res = {}
@@ -220,8 +221,29 @@ def test_fused_gradient_chain_bit_identical(gao, hw, outputs):
             assert abs(ea - eb) <= 2 * SUM_REL * abs(ea), (ea, eb)
         else:
             assert np.array_equal(np.asarray(a[nm]).view(np.uint32), np.asarray(b[nm]).view(np.uint32)), nm
-    assert [s["placement"] for s in st] == [1, 1, 1, 2, 2, 2, 2, 2, 2]
-    assert st[2]["launches"] == 3  # the pass, the sum of its block partials, the column maxima's decode
+    assert [s["placement"] for s in st] == [1, 1, 2, 2, 2, 2, 2, 2, 2]
+    assert st[1]["launches"] == 3  # the pass, the sum of its block partials, the column maxima's decode
+
+
+@pytest.mark.parametrize("hw", [(64, 64), (300, 1001)])
+def test_gradient_chain_alone_when_blur_on_cpu(gao, hw):
+    """With the blur on the CPU the gradient chain and its reductions still run as one pass,
+    over the blurred image copied in: the same bits as the separate loops."""
+    h, w = hw
+    prog = W.image_program(h, w, W.SEED_IMAGE + 4, outputs=("M2", "e", "q"))
+    gene = ((1 << prog.n_loops) - 1) & ~0b10
+    res = {}
+    for fuse in (gao.FUSE_OFF, gao.FUSE_ON):
+        p = gao.prog_from_workload(prog, fuse_chains=fuse)
+        gao.prog_run(p, gene)
+        res[fuse] = ({nm: gao.prog_output(p, prog.index(nm)) for nm in ("M2", "e", "q")}, gao.prog_stats(p))
+        gao.prog_destroy(p)
+    (a, _), (b, st) = res[gao.FUSE_OFF], res[gao.FUSE_ON]
+    assert np.array_equal(a["M2"].view(np.uint32), b["M2"].view(np.uint32))
+    assert np.array_equal(a["q"].view(np.uint32), b["q"].view(np.uint32))
+    assert abs(float(a["e"][0, 0]) - float(b["e"][0, 0])) <= 2 * SUM_REL * abs(float(a["e"][0, 0]))
+    assert [s["placement"] for s in st] == [1, 0, 1, 2, 2, 2, 2, 2, 2]
+    assert st[2]["launches"] == 3
 
 
 def test_gradient_chain_only_when_all_on_gpu(gao):
@@ -230,7 +252,8 @@ def test_gradient_chain_only_when_all_on_gpu(gao):
     X = oracle.init_matrix(45, 0, 96, 130)
     p = gao.prog_from_workload(prog, fuse_chains=gao.FUSE_GENE)
     assert gao.prog_gene_length(p) == 10
-    for gene, fused in ((0b1111111111, True), (0b0111111111, False), (0b1111101111, False), (0b1000000000, False)):
+    for gene, fused in ((0b1111111111, True), (0b1111111101, True), (0b0111111111, False), (0b1111101111, False),
+                        (0b1000000000, False)):
         gao.prog_run(p, gene)
         st = gao.prog_stats(p)
         assert (st[3]["placement"] == 2) == fused, bin(gene)
@@ -242,9 +265,9 @@ def test_gradient_chain_only_when_all_on_gpu(gao):
 @pytest.mark.parametrize("h,w", [(2048, 2048), (2051, 2049)])
 @pytest.mark.parametrize("fuse,outputs", [(0, ("M2", "e", "q")), (1, ("M2", "e", "q")), (1, ("e", "q"))])
 def test_host_frame_strips_bit_identical(gao, h, w, fuse, outputs):
-    """A frame of 16 MiB or more from the host is copied in row strips, and the blur -- and,
-    fused, the gradient chain on its output with the edge energy and the column maxima of M2
-    -- run on each strip's ready rows while the next strips are on the link.  M2 and the
+    """A frame of 16 MiB or more from the host is copied in row strips, and the blur -- fused,
+    in one pass with the gradient chain on its output and the edge energy and the column
+    maxima of M2 -- runs on each strip's ready rows while the next strips are on the link.  M2 and the
     column maxima equal those of the same frame made on the device (one launch per pass) bit
     for bit, and so does the edge energy unfused; fused, the strips partition its sum
     differently from one launch (within the rounding bound), and the same in every run."""
@@ -272,6 +295,7 @@ def test_host_frame_strips_bit_identical(gao, h, w, fuse, outputs):
                 assert np.array_equal(o[nm], want[nm]), nm
     assert np.array_equal(outs[0]["e"].view(np.uint64), outs[1]["e"].view(np.uint64))
     assert st[0]["h2d_bytes"] == h * w * 4
-    # a stencil (and a chain) launch per strip; fused, the partials' sum and the keys' decode
-    assert st[0]["launches"] == (10 if fuse else 4)
+    # a stencil launch per strip (fused: the blur and the chain in one), then, fused, the
+    # partials' sum and the keys' decode
+    assert st[0]["launches"] == (6 if fuse else 4)
     assert [s["placement"] for s in st[1:8]] == ([2] * 7 if fuse else [1] * 7)
