@@ -1010,16 +1010,24 @@ def image_arm(args, world, rank, local):
     per_loop = {f"L{i}_{W.KIND_NAMES[lp.kind]}": round(v / args.steps, 4)
                 for i, (lp, v) in enumerate(zip(prog.loops, loop_ms))}
     loop_gbs = pass_gbs(prog, st, loop_ms, args.steps, hbm)
-    # dominant kernels: the stencil passes -- the blur, and Sobel x / Sobel y or, fused, the
-    # gradient chain that reads the blurred image once and forms the magnitude's sum and
-    # column maxima in the same pass (writing the magnitude only if something reads it) --
-    # with each pass's algorithmic bytes (the same accounting as loop_gbs)
+    # dominant kernels: the stencil passes -- the blur, Sobel x and Sobel y, or, fused, one
+    # pass that reads the raw frame once and forms the blur, both gradients, the squares, the
+    # magnitude and its sum and column maxima (writing none of the intermediates) -- with each
+    # pass's algorithmic bytes (the same accounting as loop_gbs)
     groups = fused_groups(prog, st)
     st_idx = [i for i in groups if prog.loops[i].kind == W.STENCIL3 and loop_ms[i] > 0]
     st_bytes = sum(group_bytes(prog, groups[i]) for i in st_idx)
     st_ms = sum(loop_ms[i] for i in st_idx) / args.steps
     achieved = st_bytes / (st_ms / 1e3) / 1e9
     st_bpp = st_bytes / pixels
+    # the same passes against the FP32 lanes: one operation per nonzero stencil weight
+    # (a multiply-add), square, magnitude multiply-add and sum addition per pixel
+    nonzero = {W.BLUR: 9, W.LAPLACIAN: 5, W.SOBEL_X: 6, W.SOBEL_Y: 6}
+    kind_ops = {W.SQUARE: 1, W.AXPY: 1, W.SUM: 1}
+    ops_px = sum(nonzero[prog.loops[j].flags] if prog.loops[j].kind == W.STENCIL3 else kind_ops.get(prog.loops[j].kind, 0)
+                 for i in st_idx for j in groups[i])
+    fp32_peak = 152 * 128 * 2.07e9 / 1e12  # lane operations per second: SMs x FP32 lanes x maximum SM clock
+    alu_achieved = ops_px * pixels / (st_ms / 1e3) / 1e12
     gao.prog_destroy(p)
 
     unfused = None
@@ -1109,11 +1117,15 @@ def image_arm(args, world, rank, local):
             "launch_config": {"graph_replay": graph_replay, "fused_chain": bool(args.fuse),
                               "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": profile_traffic("kernels_ew.cu", f"stencil3_image_{h}x{w}.md"),
-                         "kernel": "stencil3 passes" + (" (blur; fused Sobel x/y, squares, magnitude, its sum and"
-                                                        " column maxima)" if args.fuse else "")
+                         "traffic": profile_traffic("kernels_ew.cu", f"edge_chain_image_{h}x{w}.md" if args.fuse
+                                                    else f"stencil3_image_{h}x{w}.md"),
+                         "kernel": ("edge_chain_kernel (the blur, Sobel x/y, squares, magnitude, its sum and column"
+                                    " maxima in one pass over the raw frame)" if args.fuse else "stencil3 passes")
                                    + f" ({st_bpp:.1f} algorithmic bytes per pixel over the passes)",
-                         "peak_source": f"{peaks()['source']} hbm_gbs"},
+                         "peak_source": f"{peaks()['source']} hbm_gbs",
+                         "alu": {"ops_per_pixel": ops_px, "achieved": alu_achieved, "peak": fp32_peak,
+                                 "unit": "T lane-op/s", "frac": alu_achieved / fp32_peak,
+                                 "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz"}},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": T["launches"], "clocks": clocks,
             "unfused_chain": unfused, "loop_ms": per_loop, "loop_gbs": loop_gbs, "ga_search": search}
     print(json.dumps(line), flush=True)
