@@ -455,7 +455,7 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
     }
     e = cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate(copy stream)"));
-    p->pipe_ev.assign(2 + kMaxRowBlocks, nullptr);
+    p->pipe_ev.assign(2 + 2 * kMaxRowBlocks, nullptr);
     for (auto& ev : p->pipe_ev) {
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
@@ -1157,22 +1157,44 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
     }
     GAO_CUDA_TRY(cudaEventRecord(b_done, cs));
     const bool copy_c0 = C0 && !C0->vd;
+    // Without a fused chain, beta C0 joins each block's rows after its GEMM: the GEMM forms
+    // alpha AB as its epilogue rounds it and a pass adds fma(beta, C0, .), the epilogue's own
+    // last step, so the bits are the same; C0's rows then travel after the next block's A rows
+    // and no GEMM waits for them (C0's block k lands on pipe_ev[2 + kMaxRowBlocks + k]).  Not
+    // when C0 is C itself (the GEMM would overwrite C0 before the pass reads it).
+    const int nblocks = (int)((M + rows - 1) / rows);
+    const bool late_c0 = C0 && !ch && (float)L.beta != 0.0f && nblocks >= 2 && L.ins[2] != L.outs[0];
+    auto copy_c0_block = [&](int k) -> gao_status {
+        const int64_t r0 = k * rows, r1 = std::min(M, r0 + rows);
+        const size_t off_c = (size_t)r0 * N * 4, len_c = (size_t)(r1 - r0) * N * 4;
+        GAO_CUDA_TRY(cudaMemcpyAsync(C0->dev + off_c, (char*)C0->host + off_c, len_c, cudaMemcpyHostToDevice, cs));
+        S.h2d_bytes += len_c;
+        return GAO_OK;
+    };
     int nb = 0;
+    gao_status cst = GAO_OK;
     for (int64_t r0 = 0; r0 < M; r0 += rows, ++nb) {
         const int64_t r1 = std::min(M, r0 + rows);
         const size_t off_a = (size_t)r0 * K * 4, len_a = (size_t)(r1 - r0) * K * 4;
         GAO_CUDA_TRY(cudaMemcpyAsync(A.dev + off_a, (char*)A.host + off_a, len_a, cudaMemcpyHostToDevice, cs));
         S.h2d_bytes += len_a;
-        if (copy_c0) {
-            const size_t off_c = (size_t)r0 * N * 4, len_c = (size_t)(r1 - r0) * N * 4;
-            GAO_CUDA_TRY(
-                cudaMemcpyAsync(C0->dev + off_c, (char*)C0->host + off_c, len_c, cudaMemcpyHostToDevice, cs));
-            S.h2d_bytes += len_c;
-        }
-        // the copy-time stamp goes before the last block's event, so that everything on the
-        // copy stream is joined back into the program's stream (a captured graph needs that)
-        if (r1 == M) GAO_CUDA_TRY(record_timing(ev[1], cs));
+        if (copy_c0 && !late_c0 && (cst = copy_c0_block(nb)) != GAO_OK) return cst;
+        // the copy-time stamp goes before the copy stream's last event, so that everything on
+        // it is joined back into the program's stream (a captured graph needs that)
+        const bool last_copy = r1 == M && !(copy_c0 && late_c0);
+        if (last_copy) GAO_CUDA_TRY(record_timing(ev[1], cs));
         GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + (size_t)nb], cs));
+        if (copy_c0 && late_c0 && nb >= 1) {  // the previous block's C0 rows, behind this block's A rows
+            if ((cst = copy_c0_block(nb - 1)) != GAO_OK) return cst;
+            if (nb == nblocks - 1) {
+                if ((cst = copy_c0_block(nb)) != GAO_OK) return cst;
+                GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + kMaxRowBlocks + (size_t)nb - 1], cs));
+                GAO_CUDA_TRY(record_timing(ev[1], cs));
+                GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + kMaxRowBlocks + (size_t)nb], cs));
+            } else {
+                GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + kMaxRowBlocks + (size_t)nb - 1], cs));
+            }
+        }
     }
     GAO_CUDA_TRY(record_timing(ev[2], st));
     GAO_CUDA_TRY(cudaStreamWaitEvent(st, b_done, 0));
@@ -1190,7 +1212,7 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
         TcEvents tev{i == 0 ? ev[4] : nullptr, i == nb - 1 ? ev[5] : nullptr, 0};
         std::string why;
         float* c = (float*)C.dev + (size_t)r0 * N;
-        const float* c0 = C0 ? (const float*)C0->dev + (size_t)r0 * N : c;
+        const float* c0 = C0 && !late_c0 ? (const float*)C0->dev + (size_t)r0 * N : c;
         TcFuse fz{};
         if (ch) {
             const gao_loop& T = p->loops[(size_t)ch->transpose];
@@ -1203,11 +1225,17 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
             fz.rowsum_out = ch->rowsum >= 0 ? fdev(p->loops[(size_t)ch->rowsum].outs[0]) : nullptr;
         }
         cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, c, (const float*)A.dev + (size_t)r0 * K,
-                                       (const float*)B.dev, c0, r1 - r0, N, K, (float)L.alpha, beta, p->opts.kchunk,
-                                       p->opts.tile_cfg, p->arena + p->lay.tc_off, p->lay.tc_bytes,
+                                       (const float*)B.dev, c0, r1 - r0, N, K, (float)L.alpha, late_c0 ? 0.0f : beta,
+                                       p->opts.kchunk, p->opts.tile_cfg, p->arena + p->lay.tc_off, p->lay.tc_bytes,
                                        (int*)(p->arena + p->lay.err_off), st, tev, &why, ch ? &fz : nullptr, &part);
         if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "row-block GEMM") : fail(GAO_EINVAL, why);
         S.launches += tev.launches;
+        if (late_c0) {  // C = fma(beta, C0, alpha AB) over the block's rows
+            if (copy_c0) GAO_CUDA_TRY(cudaStreamWaitEvent(st, p->pipe_ev[2 + kMaxRowBlocks + (size_t)i], 0));
+            e = launch_axpy(c, c, beta, (const float*)C0->dev + (size_t)r0 * N, (r1 - r0) * N, st);
+            if (e != cudaSuccess) return cuda_fail(e, "row-block beta C0");
+            S.launches += 1;
+        }
         if (early_out) {
             GAO_CUDA_TRY(cudaEventRecord(p->out_ev[(size_t)i], st));
             GAO_CUDA_TRY(cudaStreamWaitEvent(p->ost, p->out_ev[(size_t)i], 0));
