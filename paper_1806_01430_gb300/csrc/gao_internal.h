@@ -244,6 +244,10 @@ struct TcPart {
     bool b_ready;
     int64_t row_tile0;  // fused chain: 128-row tiles of the problem before this block
     bool last;          // fused chain: the last block (reduces the norm's partials)
+    // columns [n_begin, n_end) of C only (n_end < 0: to N; n_begin a multiple of 256; no
+    // fused chain): B's planes of those columns are formed unless b_ready
+    int64_t n_begin = 0, n_end = -1;
+    bool a_ready = false;  // this block's A planes are already formed (an earlier column range)
 };
 // ready: bit 0, A's bfloat16 planes are already in the scratch (tc_init_planes); bit 1, B's.
 cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, const float* C0, int64_t M,

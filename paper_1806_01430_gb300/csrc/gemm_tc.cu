@@ -427,7 +427,7 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
                 c0p[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 xp[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (cin && grow < e.M) {
-                    const int64_t base = grow * (int64_t)e.N + c;
+                    const int64_t base = grow * (e.ldc > 0 ? e.ldc : (int64_t)e.N) + c;
                     if (e.beta != 0.0f) c0p[it] = __ldg(reinterpret_cast<const float4*>(e.C0 + base));
                     if (fuse) xp[it] = __ldg(reinterpret_cast<const float4*>(e.X + base));
                 }
@@ -444,7 +444,7 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
                 const float av[4] = {a.x, a.y, a.z, a.w};
                 const float c0v[4] = {c0p[it].x, c0p[it].y, c0p[it].z, c0p[it].w};
                 const float xv[4] = {xp[it].x, xp[it].y, xp[it].z, xp[it].w};
-                const int64_t base = grow * (int64_t)e.N + c;
+                const int64_t base = grow * (e.ldc > 0 ? e.ldc : (int64_t)e.N) + c;
                 float cv[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -490,7 +490,7 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
                     t[k] = 0.0f;
                     u[k] = 0.0f;
                     if (cin && grow < e.M) {
-                        const int64_t base = grow * (int64_t)e.N + col;
+                        const int64_t base = grow * (e.ldc > 0 ? e.ldc : (int64_t)e.N) + col;
                         if (e.beta != 0.0f) t[k] = __ldg(e.C0 + base);
                         if (fuse) u[k] = __ldg(e.X + base);
                     }
@@ -501,7 +501,7 @@ __device__ __forceinline__ void store_staged32(const EpiArgs& e, int64_t row0, i
                     const int64_t grow = row0 + r;
                     float dv = 0.0f;
                     if (cin && grow < e.M) {
-                        const int64_t base = grow * (int64_t)e.N + col;
+                        const int64_t base = grow * (e.ldc > 0 ? e.ldc : (int64_t)e.N) + col;
                         float o = e.alpha * stg[r * kStgStride + j];
                         if (e.beta != 0.0f) o = fmaf(e.beta, t[k], o);
                         e.C[base] = o;
@@ -943,7 +943,7 @@ __device__ __forceinline__ void gemm_tc_persistent(const Src& src, int total_til
                 if (c == (nchunks > 2 ? nchunks - 2 : 0) && grow < ep.M) {
                     // the final store reads this thread's C0 (and X) row segment: start
                     // bringing it into L2 a chunk or two ahead
-                    const int64_t off = grow * (int64_t)ep.N + n0 + colbase;
+                    const int64_t off = grow * (ep.ldc > 0 ? ep.ldc : (int64_t)ep.N) + n0 + colbase;
 #pragma unroll
                     for (int k = 0; k < BN / 2; k += 32) {
                         if (ep.beta != 0.0f) prefetch_l2(ep.C0 + off + k);
@@ -1147,11 +1147,12 @@ __global__ void split_rows_kernel(const float* __restrict__ A, int64_t M, int64_
 // through shared memory (coalesced reads along N, 16-byte writes along K).
 template <int P>
 __global__ void __launch_bounds__(256) split_cols_kernel(const float* __restrict__ B, int64_t K, int64_t N,
-                                                         int64_t Np, int64_t Kp, __nv_bfloat16* __restrict__ out) {
+                                                         int64_t Np, int64_t Kp, __nv_bfloat16* __restrict__ out,
+                                                         int64_t cb0) {
     __shared__ float tile[64][65];
     const int t = threadIdx.x;
     const int c4 = t & 15, r = t >> 4;
-    const int64_t k0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+    const int64_t k0 = (int64_t)blockIdx.y * 64, n0 = ((int64_t)blockIdx.x + cb0) * 64;  // columns from 64 cb0 on
     const bool vec = (N % 4 == 0) && (((uintptr_t)B & 15u) == 0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1651,6 +1652,12 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         if (why) *why = "bad row-block arguments";
         return cudaErrorInvalidValue;
     }
+    // columns [ncol0, ncol1) of C (all of them unless a row block names a range)
+    const int64_t ncol0 = part ? part->n_begin : 0, ncol1 = part && part->n_end >= 0 ? part->n_end : N;
+    if (ncol0 < 0 || ncol0 % 256 != 0 || ncol1 > N || ncol1 <= ncol0 || (fuse && (ncol0 != 0 || ncol1 != N))) {
+        if (why) *why = "bad column range";
+        return cudaErrorInvalidValue;
+    }
     const TcShape g = tc_shape(prec, M, Mlay, N, K, kchunk, tile_cfg, part);
     const int P = g.P, num_kb = g.num_kb, chunk_kb = g.chunk_kb, bn = g.bn;
     const bool chunked = g.chunked, pair = g.pair;
@@ -1664,7 +1671,7 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
     __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(scratch);
     __nv_bfloat16* pb = pa + g.pb_elems;
     const int sms = sm_count();
-    if (!(ready & 1)) {
+    if (!(ready & 1) && !(part && part->a_ready)) {
         const int64_t work = Mp * (Kp / 8);
         int64_t blocks = (work + 255) / 256;
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
@@ -1676,20 +1683,31 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         ev.launches += 1;
     }
     if (!(part && part->b_ready) && !(ready & 2)) {
-        dim3 grid((unsigned)(Np / 64), (unsigned)(Kp / 64));
+        // B's columns [nb0, nb1) (the column range; to the padded width at the right end)
+        const int64_t nb0 = ncol0, nb1 = ncol1 == N ? Np : ncol1;
+        dim3 grid((unsigned)((nb1 - nb0 + 63) / 64), (unsigned)(Kp / 64));
         if (grid.y > 65535u) return cudaErrorInvalidValue;
-        if (P == 3) split_cols_kernel<3><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-        else if (P == 2) split_cols_kernel<2><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-        else split_cols_kernel<1><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+        const int64_t cb0 = nb0 / 64;
+        if (P == 3) split_cols_kernel<3><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb, cb0);
+        else if (P == 2) split_cols_kernel<2><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb, cb0);
+        else split_cols_kernel<1><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb, cb0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         ev.launches += 1;
     }
     CUtensorMap ta, tb;
     if (!make_map(&ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;
-    if (!make_map(&tb, pb, Kp, (int64_t)P * Np, pair ? bn / 2 : bn, false, why)) return cudaErrorInvalidValue;
-    EpiArgs ep{C, C0, (int)M, (int)N, alpha, beta,
-               (N % 4 == 0) && ((((uintptr_t)C) | ((uintptr_t)C0)) & 15u) == 0 ? 1 : 0, nullptr, nullptr, 0, 0};
+    // a column range reads B's planes from row ncol0 of each plane on: the map starts there and
+    // the kernel's plane offsets (multiples of Np) are unchanged
+    if (!make_map(&tb, pb + (size_t)ncol0 * Kp, Kp, (int64_t)P * Np - ncol0, pair ? bn / 2 : bn, false, why))
+        return cudaErrorInvalidValue;
+    float* Cr = C + ncol0;
+    const float* C0r = C0 + ncol0;
+    const int64_t ncols = ncol1 - ncol0;
+    EpiArgs ep{Cr, C0r, (int)M, (int)ncols, alpha, beta,
+               (ncols % 4 == 0) && (N % 4 == 0) && ((((uintptr_t)Cr) | ((uintptr_t)C0r)) & 15u) == 0 ? 1 : 0,
+               nullptr, nullptr, 0, 0};
+    ep.ldc = N;
     double* fpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + tc_planes_bytes(prec, Mlay, N, K));
     float* rpart = reinterpret_cast<float*>(reinterpret_cast<char*>(fpart) + tc_frob_partials_bytes(Mlay, N));
     const int64_t tiles_n = (N + bn - 1) / bn;
@@ -1904,9 +1922,9 @@ cudaError_t tc_prepare(int prec, float* C, const float* A, const float* B, const
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)(Np / 64), (unsigned)(Kp / 64));
         if (grid.y > 65535u) return cudaErrorInvalidValue;
-        if (P == 3) split_cols_kernel<3><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-        else if (P == 2) split_cols_kernel<2><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
-        else split_cols_kernel<1><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb);
+        if (P == 3) split_cols_kernel<3><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb, 0);
+        else if (P == 2) split_cols_kernel<2><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb, 0);
+        else split_cols_kernel<1><<<grid, 256, 0, st>>>(B, K, N, Np, Kp, pb, 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches = 2;
         if (!make_map(&prob->ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;

@@ -33,6 +33,7 @@ struct EpiArgs {
     // rsum_part[(row0 / 32) * ldR + j]; null when the chain has no row-sum loop.
     float* rsum_part;
     int64_t ldR;
+    int64_t ldc;  // row stride of C, C0, X and D (0: N); a column range of a wider C
 };
 
 // Loops of a chain GEMM -> AXPY (D = C + alpha2 X) -> TRANSPOSE (E = D^T) [-> ROWSUM of E]

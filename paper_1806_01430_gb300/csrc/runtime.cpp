@@ -455,7 +455,7 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
     }
     e = cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate(copy stream)"));
-    p->pipe_ev.assign(2 + 2 * kMaxRowBlocks, nullptr);
+    p->pipe_ev.assign(3 + 2 * kMaxRowBlocks, nullptr);
     for (auto& ev : p->pipe_ev) {
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
@@ -1151,7 +1151,22 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
     GAO_CUDA_TRY(cudaEventRecord(fork, st));  // the copies overwrite device buffers: after earlier work
     GAO_CUDA_TRY(cudaStreamWaitEvent(cs, fork, 0));
     GAO_CUDA_TRY(record_timing(ev[0], cs));
-    if (!B.vd) {
+    // Without a fused chain, the first row block runs as two column ranges: the first starts
+    // once B's left columns [0, nh) and A's first rows have landed, while B's other columns are
+    // still on the link (they land on pipe_ev[2 + 2 kMaxRowBlocks]).  Each output is formed as
+    // in one launch, so the bits are the same.
+    const int64_t nh = (!ch && !B.vd && N >= 512) ? (N / 2 + 255) / 256 * 256 : 0;
+    cudaEvent_t b_right = p->pipe_ev[2 + 2 * (size_t)kMaxRowBlocks];
+    auto copy_b_cols = [&](int64_t c0, int64_t c1) -> gao_status {  // B's columns [c0, c1), every row
+        GAO_CUDA_TRY(cudaMemcpy2DAsync(B.dev + (size_t)c0 * 4, (size_t)N * 4, (const char*)B.host + (size_t)c0 * 4,
+                                       (size_t)N * 4, (size_t)(c1 - c0) * 4, (size_t)K, cudaMemcpyHostToDevice, cs));
+        S.h2d_bytes += (uint64_t)(c1 - c0) * K * 4;
+        return GAO_OK;
+    };
+    gao_status cst = GAO_OK;
+    if (nh > 0) {
+        if ((cst = copy_b_cols(0, nh)) != GAO_OK) return cst;
+    } else if (!B.vd) {
         GAO_CUDA_TRY(cudaMemcpyAsync(B.dev, B.host, B.bytes, cudaMemcpyHostToDevice, cs));
         S.h2d_bytes += B.bytes;
     }
@@ -1172,7 +1187,6 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
         return GAO_OK;
     };
     int nb = 0;
-    gao_status cst = GAO_OK;
     for (int64_t r0 = 0; r0 < M; r0 += rows, ++nb) {
         const int64_t r1 = std::min(M, r0 + rows);
         const size_t off_a = (size_t)r0 * K * 4, len_a = (size_t)(r1 - r0) * K * 4;
@@ -1181,9 +1195,14 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
         if (copy_c0 && !late_c0 && (cst = copy_c0_block(nb)) != GAO_OK) return cst;
         // the copy-time stamp goes before the copy stream's last event, so that everything on
         // it is joined back into the program's stream (a captured graph needs that)
-        const bool last_copy = r1 == M && !(copy_c0 && late_c0);
+        const bool last_copy = r1 == M && !(copy_c0 && late_c0) && !(nh > 0 && nb == 0);
         if (last_copy) GAO_CUDA_TRY(record_timing(ev[1], cs));
         GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + (size_t)nb], cs));
+        if (nh > 0 && nb == 0) {  // B's other columns, right behind A's first rows
+            if ((cst = copy_b_cols(nh, N)) != GAO_OK) return cst;
+            if (r1 == M && !(copy_c0 && late_c0)) GAO_CUDA_TRY(record_timing(ev[1], cs));
+            GAO_CUDA_TRY(cudaEventRecord(b_right, cs));
+        }
         if (copy_c0 && late_c0 && nb >= 1) {  // the previous block's C0 rows, behind this block's A rows
             if ((cst = copy_c0_block(nb - 1)) != GAO_OK) return cst;
             if (nb == nblocks - 1) {
@@ -1211,6 +1230,23 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
         TcPart part{M, i > 0, r0 / 128, i == nb - 1};
         TcEvents tev{i == 0 ? ev[4] : nullptr, i == nb - 1 ? ev[5] : nullptr, 0};
         std::string why;
+        if (i == 0 && nh > 0) {  // the first block's left columns, before B's others land
+            TcPart left = part;
+            left.n_end = nh;
+            TcEvents lev{ev[4], nullptr, 0};
+            const float* c0l = C0 && !late_c0 ? (const float*)C0->dev : (const float*)C.dev;
+            cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, (float*)C.dev, (const float*)A.dev,
+                                           (const float*)B.dev, c0l, r1 - r0, N, K, (float)L.alpha,
+                                           late_c0 ? 0.0f : beta, p->opts.kchunk, p->opts.tile_cfg,
+                                           p->arena + p->lay.tc_off, p->lay.tc_bytes, (int*)(p->arena + p->lay.err_off),
+                                           st, lev, &why, nullptr, &left);
+            if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "row-block GEMM") : fail(GAO_EINVAL, why);
+            S.launches += lev.launches;
+            GAO_CUDA_TRY(cudaStreamWaitEvent(st, b_right, 0));
+            part.n_begin = nh;
+            part.a_ready = true;
+            tev.k0 = nullptr;
+        }
         float* c = (float*)C.dev + (size_t)r0 * N;
         const float* c0 = C0 && !late_c0 ? (const float*)C0->dev + (size_t)r0 * N : c;
         TcFuse fz{};
