@@ -232,6 +232,7 @@ inline cudaError_t record_timing(cudaEvent_t e, cudaStream_t s) {
 struct TcEvents {
     cudaEvent_t k0 = nullptr, k1 = nullptr;  // recorded around the MMA kernel if non-null
     int launches = 0;                         // out: kernels launched
+    cudaEvent_t planes = nullptr;             // recorded once the operand planes are formed, if non-null
 };
 size_t tc_scratch_bytes(int prec, int64_t M, int64_t N, int64_t K);
 struct TcFuse;

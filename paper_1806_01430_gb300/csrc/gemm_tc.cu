@@ -1668,8 +1668,10 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         if (why) *why = "tensor-core scratch too small or misaligned";
         return cudaErrorInvalidValue;
     }
-    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(scratch);
-    __nv_bfloat16* pb = pa + g.pb_elems;
+    // A's planes: a row block's own region of the room kept for the whole problem's (so that
+    // blocks in flight at the same time do not share one), B's after that room
+    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(scratch) + (part ? (size_t)P * part->row_tile0 * BM * Kp : 0);
+    __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(scratch) + g.pb_elems;
     const int sms = sm_count();
     if (!(ready & 1) && !(part && part->a_ready)) {
         const int64_t work = Mp * (Kp / 8);
@@ -1694,6 +1696,10 @@ cudaError_t launch_gemm_tc(int prec, float* C, const float* A, const float* B, c
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         ev.launches += 1;
+    }
+    if (ev.planes) {
+        cudaError_t e = cudaEventRecord(ev.planes, st);
+        if (e != cudaSuccess) return e;
     }
     CUtensorMap ta, tb;
     if (!make_map(&ta, pa, Kp, (int64_t)P * Mp, BM, false, why)) return cudaErrorInvalidValue;

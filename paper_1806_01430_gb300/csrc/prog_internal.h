@@ -72,6 +72,8 @@ struct gao_prog {
     std::vector<cudaEvent_t> pipe_ev;     // its events: fork, B landed, one per row block
     cudaStream_t ost = nullptr;           // device-to-host stream: a GEMM's C rows as blocks finish
     std::vector<cudaEvent_t> out_ev;      // one per row block (block done), then the join
+    cudaStream_t st2 = nullptr;           // second compute stream: every other row block's GEMM
+    std::vector<cudaEvent_t> cmp_ev;      // its fork, B's planes formed, its join
     std::vector<int8_t> verdict;  // gao_offload of every loop
     std::vector<int> gene_loop;   // gene bit k -> index of the k-th offloadable loop
     std::unordered_map<uint64_t, GraphEntry> graphs;  // key: gene * 8 + run flags (KEEP_DEVICE, NO_LOOP_TIMES)

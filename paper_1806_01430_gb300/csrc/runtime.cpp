@@ -353,6 +353,7 @@ void free_prog(gao_prog* p) {
     if (p->h_err) cudaFreeHost(p->h_err);
     if (p->cst) cudaStreamSynchronize(p->cst);
     if (p->ost) cudaStreamSynchronize(p->ost);
+    if (p->st2) cudaStreamSynchronize(p->st2);
     drop_graphs(p);
     for (auto e : p->ev)
         if (e) cudaEventDestroy(e);
@@ -360,8 +361,11 @@ void free_prog(gao_prog* p) {
         if (e) cudaEventDestroy(e);
     for (auto e : p->out_ev)
         if (e) cudaEventDestroy(e);
+    for (auto e : p->cmp_ev)
+        if (e) cudaEventDestroy(e);
     if (p->cst) cudaStreamDestroy(p->cst);
     if (p->ost) cudaStreamDestroy(p->ost);
+    if (p->st2) cudaStreamDestroy(p->st2);
     if (p->own_arena && p->arena_raw) cudaFree(p->arena_raw);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
     delete p;
@@ -464,6 +468,13 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate(device-to-host stream)"));
     p->out_ev.assign(1 + kMaxRowBlocks, nullptr);
     for (auto& ev : p->out_ev) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    }
+    e = cudaStreamCreateWithFlags(&p->st2, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate(second compute stream)"));
+    p->cmp_ev.assign(3, nullptr);
+    for (auto& ev : p->cmp_ev) {
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
     }
@@ -1223,12 +1234,26 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
     // already on the device
     const gao_loop* XL = ch ? &p->loops[(size_t)ch->axpy] : nullptr;
     auto fdev = [&](int b) { return (float*)p->bufs[(size_t)b].dev; };
+    // Without a fused chain the blocks are independent once B's planes are formed: odd blocks
+    // run on a second stream, so that a block's GEMM takes up the SMs its predecessor's last
+    // tiles leave idle and its A split runs beside that GEMM (each block's A planes have a
+    // region of their own).  A fused chain's blocks share the norm's and row sums' partials
+    // and stay on one stream.
+    const bool alt = !ch && nb >= 2;
+    cudaEvent_t fork2 = p->cmp_ev[0], planes = p->cmp_ev[1], join2 = p->cmp_ev[2];
+    if (alt) {
+        GAO_CUDA_TRY(cudaEventRecord(fork2, st));
+        GAO_CUDA_TRY(cudaStreamWaitEvent(p->st2, fork2, 0));
+    }
     int i = 0;
     for (int64_t r0 = 0; r0 < M; r0 += rows, ++i) {
         const int64_t r1 = std::min(M, r0 + rows);
-        GAO_CUDA_TRY(cudaStreamWaitEvent(st, p->pipe_ev[2 + (size_t)i], 0));
+        cudaStream_t sx = alt && (i & 1) ? p->st2 : st;
+        GAO_CUDA_TRY(cudaStreamWaitEvent(sx, p->pipe_ev[2 + (size_t)i], 0));
+        if (alt && i > 0) GAO_CUDA_TRY(cudaStreamWaitEvent(sx, planes, 0));
         TcPart part{M, i > 0, r0 / 128, i == nb - 1};
         TcEvents tev{i == 0 ? ev[4] : nullptr, i == nb - 1 ? ev[5] : nullptr, 0};
+        if (alt && i == 0) tev.planes = planes;
         std::string why;
         if (i == 0 && nh > 0) {  // the first block's left columns, before B's others land
             TcPart left = part;
@@ -1263,22 +1288,26 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
         cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, c, (const float*)A.dev + (size_t)r0 * K,
                                        (const float*)B.dev, c0, r1 - r0, N, K, (float)L.alpha, late_c0 ? 0.0f : beta,
                                        p->opts.kchunk, p->opts.tile_cfg, p->arena + p->lay.tc_off, p->lay.tc_bytes,
-                                       (int*)(p->arena + p->lay.err_off), st, tev, &why, ch ? &fz : nullptr, &part);
+                                       (int*)(p->arena + p->lay.err_off), sx, tev, &why, ch ? &fz : nullptr, &part);
         if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "row-block GEMM") : fail(GAO_EINVAL, why);
         S.launches += tev.launches;
         if (late_c0) {  // C = fma(beta, C0, alpha AB) over the block's rows
-            if (copy_c0) GAO_CUDA_TRY(cudaStreamWaitEvent(st, p->pipe_ev[2 + kMaxRowBlocks + (size_t)i], 0));
-            e = launch_axpy(c, c, beta, (const float*)C0->dev + (size_t)r0 * N, (r1 - r0) * N, st);
+            if (copy_c0) GAO_CUDA_TRY(cudaStreamWaitEvent(sx, p->pipe_ev[2 + kMaxRowBlocks + (size_t)i], 0));
+            e = launch_axpy(c, c, beta, (const float*)C0->dev + (size_t)r0 * N, (r1 - r0) * N, sx);
             if (e != cudaSuccess) return cuda_fail(e, "row-block beta C0");
             S.launches += 1;
         }
         if (early_out) {
-            GAO_CUDA_TRY(cudaEventRecord(p->out_ev[(size_t)i], st));
+            GAO_CUDA_TRY(cudaEventRecord(p->out_ev[(size_t)i], sx));
             GAO_CUDA_TRY(cudaStreamWaitEvent(p->ost, p->out_ev[(size_t)i], 0));
             const size_t off = (size_t)r0 * N * 4, len = (size_t)(r1 - r0) * N * 4;
             GAO_CUDA_TRY(cudaMemcpyAsync((char*)C.host + off, C.dev + off, len, cudaMemcpyDeviceToHost, p->ost));
             S.d2h_bytes += len;
         }
+    }
+    if (alt) {  // the second stream joined back into the program's stream (a captured graph needs that)
+        GAO_CUDA_TRY(cudaEventRecord(join2, p->st2));
+        GAO_CUDA_TRY(cudaStreamWaitEvent(st, join2, 0));
     }
     GAO_CUDA_TRY(record_timing(ev[3], st));
     if (early_out) {  // joined back into the program's stream (a captured graph needs that)
