@@ -37,11 +37,41 @@ __global__ void row_exponents_kernel(int8_t* e, int64_t rows, uint64_t seed) {
         e[r] = (int8_t)row_exponent(seed, r);
 }
 
+constexpr int kInitQuads = 4;  // quadruples per thread and trip in the plain INIT loop
+
+// Elements 4q .. 4q + 3 of an INIT buffer whose element keys are khi ^ index (the hashes of
+// keys 2q and 2q + 1 give them).
+__device__ __forceinline__ float4 init_quad(uint64_t khi, uint64_t q) {
+    const uint64_t h0 = sm64_hash(khi ^ (2 * q));
+    const uint64_t h1 = sm64_hash(khi ^ (2 * q + 1));
+    return make_float4(u24_to_value((uint32_t)(h0 >> 40)), u24_to_value((uint32_t)((h0 >> 16) & 0xFFFFFFu)),
+                       u24_to_value((uint32_t)(h1 >> 40)), u24_to_value((uint32_t)((h1 >> 16) & 0xFFFFFFu)));
+}
+
 // out[i] = init_value(seed, buf, i) (times 2^e_row).  Four consecutive elements per
 // thread and iteration, stored as one float4 (a ragged last quadruple element by element).
 __device__ __forceinline__ void init_body(float* __restrict__ out, int64_t rows, int64_t cols, uint64_t seed,
                                           uint32_t buf, const int8_t* __restrict__ rowexp) {
     const int64_t n = rows * cols;
+    if (!rowexp && aligned16(out)) {
+        // no row factors: kInitQuads independent quadruples per trip (their hashes in flight
+        // together), then the ragged tail element by element
+        const uint64_t khi = init_key(seed, buf, 0);
+        const int64_t nq = n / 4, nth = (int64_t)gridDim.x * blockDim.x;
+        float4* o4 = reinterpret_cast<float4*>(out);
+        int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        for (; q + (kInitQuads - 1) * nth < nq; q += kInitQuads * nth) {
+            float4 v[kInitQuads];
+#pragma unroll
+            for (int u = 0; u < kInitQuads; ++u) v[u] = init_quad(khi, (uint64_t)(q + u * nth));
+#pragma unroll
+            for (int u = 0; u < kInitQuads; ++u) o4[q + u * nth] = v[u];
+        }
+        for (; q < nq; q += nth) o4[q] = init_quad(khi, (uint64_t)q);
+        const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (t < n - 4 * nq) out[4 * nq + t] = init_value(seed, buf, (uint64_t)(4 * nq + t));
+        return;
+    }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
     // a full quadruple is one float4 store; with row scaling only when no row ends inside it
     const bool vec = aligned16(out) && (!rowexp || cols % 4 == 0);

@@ -138,6 +138,19 @@ def test_all_64_masks_invariance(gao):
     gao.prog_destroy(p)
 
 
+@pytest.mark.parametrize("shapes", [[(7, 13), (1, 3), (1000, 1001)], [(4096, 4096)], [(1, 1), (3, 5), (2, 2)]])
+def test_init_outputs_bit_exact(gao, shapes):
+    """One INIT loop with several outputs of ragged sizes (a tail of 1-3 elements after the
+    whole quadruples, grids that cover a buffer in several trips): every element is the
+    counter hash's value, bit for bit against the oracle's."""
+    seed = 4242
+    bufs = [W.Buffer(f"X{k}", r, c, W.F32, W.OUTPUT) for k, (r, c) in enumerate(shapes)]
+    prog = W.Program("init_only", bufs, [W.Loop(W.INIT, [], list(range(len(shapes))))], seed)
+    out, _, _ = run_prog(gao, prog, 0b1)
+    for k, (r, c) in enumerate(shapes):
+        assert np.array_equal(out[f"X{k}"], oracle.init_matrix(seed, k, r, c).astype(np.float32)), (k, r, c)
+
+
 def test_row_scaled_init_bit_exact(gao):
     prog = all_outputs(W.six_loop(200, W.SEED_N8192_ROWS, rowscale_a=True))
     ref = oracle.run_program(prog)
