@@ -82,6 +82,7 @@ struct gao_prog {
 namespace gao {
 
 constexpr int kMaxRowBlocks = 4;                 // row blocks of an overlapped GEMM loop
+constexpr int kMaxColParts = 2;                  // column ranges of its first row block
 constexpr size_t kPipelineMinBytes = 16u << 20;  // smallest A worth overlapping
 
 // One execution of a program (or of a batch of programs sharing a stream).

@@ -459,7 +459,7 @@ extern "C" gao_status prog_create(const gao_loop* loops, int n_loops, const gao_
     }
     e = cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate(copy stream)"));
-    p->pipe_ev.assign(3 + 2 * kMaxRowBlocks, nullptr);
+    p->pipe_ev.assign(1 + 2 * kMaxRowBlocks + kMaxColParts, nullptr);
     for (auto& ev : p->pipe_ev) {
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
@@ -1162,12 +1162,20 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
     GAO_CUDA_TRY(cudaEventRecord(fork, st));  // the copies overwrite device buffers: after earlier work
     GAO_CUDA_TRY(cudaStreamWaitEvent(cs, fork, 0));
     GAO_CUDA_TRY(record_timing(ev[0], cs));
-    // Without a fused chain, the first row block runs as two column ranges: the first starts
-    // once B's left columns [0, nh) and A's first rows have landed, while B's other columns are
-    // still on the link (they land on pipe_ev[2 + 2 kMaxRowBlocks]).  Each output is formed as
-    // in one launch, so the bits are the same.
-    const int64_t nh = (!ch && !B.vd && N >= 512) ? (N / 2 + 255) / 256 * 256 : 0;
-    cudaEvent_t b_right = p->pipe_ev[2 + 2 * (size_t)kMaxRowBlocks];
+    // Without a fused chain, the first row block runs as column ranges [cut[j], cut[j + 1]) of
+    // whole 256-column tiles: the first starts once B's first columns and A's first rows have
+    // landed, and each next one as its columns of B land behind them (range j > 0 on
+    // pipe_ev[1 + 2 kMaxRowBlocks + j]).  Each output is formed as in one launch, so the bits
+    // are the same.
+    int nparts = 1;
+    int64_t cut[kMaxColParts + 1] = {0, N};
+    if (!ch && !B.vd && N >= 512) {
+        nparts = 2;  // four ranges at n = 8192 measured no faster (5.75 against 5.64-5.72 ms per step)
+        for (int j = 0; j <= nparts; ++j) cut[j] = j == nparts ? N : (j * N / nparts + 255) / 256 * 256;
+        for (int j = 1; j <= nparts; ++j)
+            if (cut[j] <= cut[j - 1]) return fail(GAO_EINVAL, "column ranges of the first row block");
+    }
+    auto part_ev = [&](int j) { return j == 0 ? b_done : p->pipe_ev[1 + 2 * (size_t)kMaxRowBlocks + (size_t)j]; };
     auto copy_b_cols = [&](int64_t c0, int64_t c1) -> gao_status {  // B's columns [c0, c1), every row
         GAO_CUDA_TRY(cudaMemcpy2DAsync(B.dev + (size_t)c0 * 4, (size_t)N * 4, (const char*)B.host + (size_t)c0 * 4,
                                        (size_t)N * 4, (size_t)(c1 - c0) * 4, (size_t)K, cudaMemcpyHostToDevice, cs));
@@ -1175,8 +1183,8 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
         return GAO_OK;
     };
     gao_status cst = GAO_OK;
-    if (nh > 0) {
-        if ((cst = copy_b_cols(0, nh)) != GAO_OK) return cst;
+    if (nparts > 1) {
+        if ((cst = copy_b_cols(0, cut[1])) != GAO_OK) return cst;
     } else if (!B.vd) {
         GAO_CUDA_TRY(cudaMemcpyAsync(B.dev, B.host, B.bytes, cudaMemcpyHostToDevice, cs));
         S.h2d_bytes += B.bytes;
@@ -1206,13 +1214,15 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
         if (copy_c0 && !late_c0 && (cst = copy_c0_block(nb)) != GAO_OK) return cst;
         // the copy-time stamp goes before the copy stream's last event, so that everything on
         // it is joined back into the program's stream (a captured graph needs that)
-        const bool last_copy = r1 == M && !(copy_c0 && late_c0) && !(nh > 0 && nb == 0);
+        const bool last_copy = r1 == M && !(copy_c0 && late_c0) && !(nparts > 1 && nb == 0);
         if (last_copy) GAO_CUDA_TRY(record_timing(ev[1], cs));
         GAO_CUDA_TRY(cudaEventRecord(p->pipe_ev[2 + (size_t)nb], cs));
-        if (nh > 0 && nb == 0) {  // B's other columns, right behind A's first rows
-            if ((cst = copy_b_cols(nh, N)) != GAO_OK) return cst;
-            if (r1 == M && !(copy_c0 && late_c0)) GAO_CUDA_TRY(record_timing(ev[1], cs));
-            GAO_CUDA_TRY(cudaEventRecord(b_right, cs));
+        if (nparts > 1 && nb == 0) {  // B's other columns, range by range, right behind A's first rows
+            for (int j = 1; j < nparts; ++j) {
+                if ((cst = copy_b_cols(cut[j], cut[j + 1])) != GAO_OK) return cst;
+                if (j == nparts - 1 && r1 == M && !(copy_c0 && late_c0)) GAO_CUDA_TRY(record_timing(ev[1], cs));
+                GAO_CUDA_TRY(cudaEventRecord(part_ev(j), cs));
+            }
         }
         if (copy_c0 && late_c0 && nb >= 1) {  // the previous block's C0 rows, behind this block's A rows
             if ((cst = copy_c0_block(nb - 1)) != GAO_OK) return cst;
@@ -1255,20 +1265,25 @@ gao_status run_gpu_gemm_pipelined(RunCtx& R, int li, int64_t blocks, const Chain
         TcEvents tev{i == 0 ? ev[4] : nullptr, i == nb - 1 ? ev[5] : nullptr, 0};
         if (alt && i == 0) tev.planes = planes;
         std::string why;
-        if (i == 0 && nh > 0) {  // the first block's left columns, before B's others land
-            TcPart left = part;
-            left.n_end = nh;
-            TcEvents lev{ev[4], nullptr, 0};
-            const float* c0l = C0 && !late_c0 ? (const float*)C0->dev : (const float*)C.dev;
-            cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, (float*)C.dev, (const float*)A.dev,
-                                           (const float*)B.dev, c0l, r1 - r0, N, K, (float)L.alpha,
-                                           late_c0 ? 0.0f : beta, p->opts.kchunk, p->opts.tile_cfg,
-                                           p->arena + p->lay.tc_off, p->lay.tc_bytes, (int*)(p->arena + p->lay.err_off),
-                                           st, lev, &why, nullptr, &left);
-            if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "row-block GEMM") : fail(GAO_EINVAL, why);
-            S.launches += lev.launches;
-            GAO_CUDA_TRY(cudaStreamWaitEvent(st, b_right, 0));
-            part.n_begin = nh;
+        if (i == 0 && nparts > 1) {  // the first block's column ranges but the last, as B's columns land
+            for (int j = 0; j + 1 < nparts; ++j) {
+                TcPart pj = part;
+                pj.n_begin = cut[j];
+                pj.n_end = cut[j + 1];
+                pj.a_ready = j > 0;  // A's planes formed by the first range
+                TcEvents lev{j == 0 ? ev[4] : nullptr, nullptr, 0};
+                if (j > 0) GAO_CUDA_TRY(cudaStreamWaitEvent(st, part_ev(j), 0));
+                const float* c0l = C0 && !late_c0 ? (const float*)C0->dev : (const float*)C.dev;
+                cudaError_t e = launch_gemm_tc(p->opts.gemm_prec, (float*)C.dev, (const float*)A.dev,
+                                               (const float*)B.dev, c0l, r1 - r0, N, K, (float)L.alpha,
+                                               late_c0 ? 0.0f : beta, p->opts.kchunk, p->opts.tile_cfg,
+                                               p->arena + p->lay.tc_off, p->lay.tc_bytes,
+                                               (int*)(p->arena + p->lay.err_off), st, lev, &why, nullptr, &pj);
+                if (e != cudaSuccess) return why.empty() ? cuda_fail(e, "row-block GEMM") : fail(GAO_EINVAL, why);
+                S.launches += lev.launches;
+            }
+            GAO_CUDA_TRY(cudaStreamWaitEvent(st, part_ev(nparts - 1), 0));
+            part.n_begin = cut[nparts - 1];
             part.a_ready = true;
             tev.k0 = nullptr;
         }

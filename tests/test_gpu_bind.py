@@ -103,14 +103,14 @@ def test_bind_rejects_wrong_size(gao):
     gao.prog_destroy(p)
 
 
-@pytest.mark.parametrize("prec,n", [("bf16x6", 2304), ("bf16x3", 2500)])
+@pytest.mark.parametrize("prec,n", [("bf16x6", 2304), ("bf16x3", 2500), ("bf16x6", 4096), ("bf16", 4352)])
 def test_overlapped_gemm_copies_c_back_by_row_block(gao, prec, n):
     """A GEMM whose A comes from the host runs in row blocks overlapped with the copy in; with C
     an OUTPUT bound to the caller's array, each block's rows of C go back as soon as the block is
     done (the link's other direction).  C must carry the bits of the device-resident run, be
     copied back exactly once per run (plain runs and graph replays), and a run that keeps the
     device buffers must not copy it."""
-    pr = {"bf16x6": gao.BF16X6, "bf16x3": gao.BF16X3}[prec]
+    pr = {"bf16x6": gao.BF16X6, "bf16x3": gao.BF16X3, "bf16": gao.BF16}[prec]
     seed = 71
     hp = W.host_input_gemm(n)
     ins = _inputs(n, seed)
