@@ -152,11 +152,18 @@ typedef struct gao_opts {
                                 (NULL: the library allocates it); must outlive the program */
     uint64_t dev_arena_bytes;
     int32_t transfer_mode;   /* GAO_TRANSFER_RESIDENT or GAO_TRANSFER_PER_LOOP               */
-    int32_t fuse_chains;     /* GAO_FUSE_*: whether a chain GEMM -> AXPY(C + a X) -> TRANSPOSE
-                                [-> FROBENIUS of the transpose] that a gene puts on the GPU
-                                (tensor-core BF16 precisions, resident transfers) runs as one
-                                pass: the GEMM's epilogue writes C, D and E and the norm's
-                                partial sums                                                */
+    int32_t fuse_chains;     /* GAO_FUSE_*: whether loop chains that a gene puts on the GPU
+                                (resident transfers) run as one pass each:
+                                GEMM -> AXPY(C + a X) -> TRANSPOSE [-> ROWSUM] [-> FROBENIUS]
+                                of the transpose (tensor-core BF16 precisions: the GEMM's
+                                epilogue writes C, D, E, the row sums' block values and the
+                                norm's partial sums); linear RELU / SQUARE / AXPY chains;
+                                STENCIL3 x2 -> SQUARE x2 -> AXPY [-> SUM] [-> COLMAX] of the
+                                magnitude (the gradient chain), with the STENCIL3 that forms
+                                its input joining the pass when it is on the GPU too (one pass
+                                over the raw image); intermediates no later loop reads are not
+                                written.  Results keep the separate loops' bits but for the
+                                norm and SUM, which partition their sums differently          */
 } gao_opts;
 
 /* Data movement between host and device under a gene (Sec. 2 and Sec. 3.3: CPU-GPU
