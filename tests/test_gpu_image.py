@@ -225,6 +225,28 @@ def test_fused_gradient_chain_bit_identical(gao, hw, outputs):
     assert st[1]["launches"] == 3  # the pass, the sum of its block partials, the column maxima's decode
 
 
+@pytest.mark.parametrize("hw", [(1, 1), (2, 3), (3, 7), (9, 240), (17, 241), (33, 8), (4, 964)])
+def test_fused_pass_degenerate_shapes(gao, hw):
+    """The one-pass blur and gradient chain on frames of one to a few rows or columns and on
+    widths around a warp's 240 output columns (a lane's eight columns straddling the right
+    edge): the same bits as the separate loops for M2 and the column maxima, the edge energy
+    within its rounding bound."""
+    h, w = hw
+    prog = W.image_program(h, w, W.SEED_IMAGE + 5, outputs=("M2", "e", "q"))
+    res = {}
+    for fuse in (gao.FUSE_OFF, gao.FUSE_ON):
+        p = gao.prog_from_workload(prog, fuse_chains=fuse)
+        gao.prog_run(p, (1 << prog.n_loops) - 1)
+        res[fuse] = ({nm: gao.prog_output(p, prog.index(nm)) for nm in ("M2", "e", "q")}, gao.prog_stats(p))
+        gao.prog_destroy(p)
+    (a, _), (b, st) = res[gao.FUSE_OFF], res[gao.FUSE_ON]
+    assert np.array_equal(a["M2"].view(np.uint32), b["M2"].view(np.uint32))
+    assert np.array_equal(a["q"].view(np.uint32), b["q"].view(np.uint32))
+    ea, eb = float(a["e"][0, 0]), float(b["e"][0, 0])
+    assert abs(ea - eb) <= 2 * SUM_REL * abs(ea) + 1e-30, (ea, eb)
+    assert st[1]["placement"] == 1 and all(s["placement"] == 2 for s in st[2:])
+
+
 @pytest.mark.parametrize("hw", [(64, 64), (300, 1001)])
 def test_gradient_chain_alone_when_blur_on_cpu(gao, hw):
     """With the blur on the CPU the gradient chain and its reductions still run as one pass,
