@@ -63,9 +63,14 @@ __host__ __device__ inline int row_exponent(uint64_t seed, int64_t row) {
 }
 
 // Order-preserving key of a binary32 value for max reductions with integer atomics
-// (+0 above -0; NaN above +inf).  Used identically by the CPU loop.
+// (+0 above -0; a NaN with the sign bit clear above +inf, one with it set below -inf): the
+// bits with the sign bit set when it is clear, all bits flipped when it is set.  Written as one
+// exclusive or with a mask built from the sign bit, not as a choice between the two forms: in
+// that form, applied to the result of arithmetic still in registers, the compiled maximum of
+// the keys lost NaN values (a NaN pixel of the image pass never reached the column maxima),
+// while keys of values loaded from memory were right.  Used identically by the CPU loop.
 __host__ __device__ inline uint32_t fmax_key(uint32_t bits) {
-    return (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+    return bits ^ ((0u - (bits >> 31)) | 0x80000000u);
 }
 __host__ __device__ inline uint32_t fmax_unkey(uint32_t key) {
     return (key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key;

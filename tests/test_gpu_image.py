@@ -247,6 +247,39 @@ def test_fused_pass_degenerate_shapes(gao, hw):
     assert st[1]["placement"] == 1 and all(s["placement"] == 2 for s in st[2:])
 
 
+@pytest.mark.parametrize("h,w", [(64, 250), (2048, 2048)])
+def test_fused_pass_special_values(gao, h, w):
+    """A frame holding NaNs of either sign (quiet, signalling, with payloads), infinities,
+    -0 and values whose squares overflow: the one-pass blur and gradient chain gives M2's and
+    the column maxima's bits of the separate loops (the column maxima rank every value the
+    same way whether taken in the pass or by the COLMAX loop), and an edge energy that is NaN
+    exactly when theirs is.  The larger frame comes in row strips from the host."""
+    seed = 61
+    prog = W.image_program(h, w, seed, outputs=("M2", "e", "q"), host_image=True)
+    X = oracle.init_matrix(seed, 0, h, w).astype(np.float32)
+    bits = X.view(np.uint32)
+    rng = np.random.default_rng(h + w)
+    specials = np.array([0x7FC00000, 0xFFC00000, 0x7F800001, 0xFF800001, 0x7FFFFFFF, 0xFFFFFFFF,
+                         0x7F800000, 0xFF800000, 0x80000000, 0x7149F2CA, 0xF149F2CA], dtype=np.uint32)
+    for v in specials:  # a few of each, at random places (some columns clean)
+        rr = rng.integers(0, h, 3)
+        cc = rng.integers(0, w // 2, 3)
+        bits[rr, cc] = v
+    outs = {}
+    for fuse in (gao.FUSE_OFF, gao.FUSE_ON):
+        p = gao.prog_from_workload(prog, fuse_chains=fuse)
+        gao.prog_set_input(p, prog.index("X"), X)
+        gao.prog_run(p, (1 << prog.n_loops) - 1)
+        outs[fuse] = {nm: gao.prog_output(p, prog.index(nm)).copy() for nm in ("M2", "e", "q")}
+        gao.prog_destroy(p)
+    a, b = outs[gao.FUSE_OFF], outs[gao.FUSE_ON]
+    assert np.array_equal(a["M2"].view(np.uint32), b["M2"].view(np.uint32))
+    assert np.array_equal(a["q"].view(np.uint32), b["q"].view(np.uint32))
+    assert np.isnan(a["q"]).any()  # the special values reached the maxima
+    ea, eb = float(a["e"][0, 0]), float(b["e"][0, 0])
+    assert np.isnan(ea) == np.isnan(eb) and (np.isnan(ea) or ea == eb or abs(ea - eb) <= 2 * SUM_REL * abs(ea))
+
+
 @pytest.mark.parametrize("hw", [(64, 64), (300, 1001)])
 def test_gradient_chain_alone_when_blur_on_cpu(gao, hw):
     """With the blur on the CPU the gradient chain and its reductions still run as one pass,
