@@ -151,6 +151,37 @@ def test_fused_chain_in_copy_overlapped_gemm(gao, n, prec):
     assert st[0]["h2d_bytes"] == 3 * n * n * 4
 
 
+@pytest.mark.parametrize("n,prec", [(640, 3), (2048, 3), (2304, 1)])
+def test_special_values_fused_and_overlapped(gao, n, prec):
+    """Host inputs with NaNs of either sign, infinities, -0 and huge values in A, B and C0
+    (n = 640: one launch; n >= 2048: copy-overlapped row blocks, the first in column ranges):
+    the chain in the GEMM's epilogue gives the same bits of C, D, E and r as the separate
+    loops, and a norm that is NaN exactly when theirs is."""
+    seed = 15
+    hp = W.host_input_program(n, seed, outputs=("C", "D", "E", "r", "f"))
+    ins = {nm: oracle.init_matrix(seed, b, n, n).astype(np.float32) for nm, b in (("A", 0), ("B", 1), ("C0", 2))}
+    rng = np.random.default_rng(n)
+    specials = np.array([0x7FC00000, 0xFFC00000, 0x7F800001, 0x7F800000, 0xFF800000, 0x80000000, 0x7E967699],
+                        dtype=np.uint32)
+    for nm in ("A", "B", "C0"):
+        bits = ins[nm].view(np.uint32)
+        for v in specials:
+            bits[rng.integers(0, n // 2, 2), rng.integers(0, n // 2, 2)] = v
+    res = {}
+    for fuse in (False, True):
+        p = gao.prog_from_workload(hp, gemm_prec=prec, fuse_chains=fuse)
+        for nm, v in ins.items():
+            gao.prog_set_input(p, hp.index(nm), v)
+        gao.prog_run(p, (1 << hp.n_loops) - 1)
+        res[fuse] = outputs(gao, p, hp)
+        gao.prog_destroy(p)
+    a, b = res[False], res[True]
+    for nm in ("C", "D", "E", "r"):
+        assert np.array_equal(a[nm].view(np.uint32), b[nm].view(np.uint32)), nm
+    assert np.isnan(a["C"]).any() and np.isfinite(a["C"]).any()
+    assert np.isnan(a["f"]) == np.isnan(b["f"])
+
+
 def test_twelve_loop_elementwise_chain_bit_identical(gao):
     """ReLU, E - 0.5F, its square and P = H + 0.25D run as one element-wise pass (F, G, H
     never written): the same P, column maxima and sum as the separate loops."""
