@@ -268,7 +268,9 @@ def test_generation_results_match_single_gene_runs(gao, prec, fuse):
 
 def test_generation_times_rank_like_single_runs(gao):
     """All 64 genes timed one at a time (wall time of the suite) and 16 at a time (attributed
-    times in shared launches): the attributed times order the genes like the single runs."""
+    times in shared launches): the attributed times order the genes like the single runs.
+    Each mode measures every gene twice and keeps the shorter time (a shared machine's noise
+    only ever adds time)."""
     sizes = [256, 384, 192, 512, 128, 320]
     progs = [W.six_loop(n, 3400 + i, outputs=("f",)) for i, n in enumerate(sizes)]
     times = {}
@@ -276,14 +278,17 @@ def test_generation_times_rank_like_single_runs(gao):
         handles = [gao.prog_from_workload(p, gemm_prec=2) for p in progs]
         b = gao.batch_create(handles, replicas=reps)
         gao.batch_evaluate(b, [0b111111])  # warm
-        gao.batch_set_replicas(b, reps)    # clears the cache
-        st0 = gao.batch_stats(b)
-        _, sec, _ = gao.batch_evaluate(b, list(range(64)))
-        times[reps] = np.array(sec)
-        st = gao.batch_stats(b)
-        if reps == 16:  # four groups, each GEMM-offloading subset of 16 genes in one launch
-            assert st["grouped_launches"] - st0["grouped_launches"] == 4
-            assert st["grouped_genes"] - st0["grouped_genes"] == 32
+        runs = []
+        for rep in range(2):
+            gao.batch_set_replicas(b, reps)  # clears the cache
+            st0 = gao.batch_stats(b)
+            _, sec, _ = gao.batch_evaluate(b, list(range(64)))
+            runs.append(np.array(sec))
+            st = gao.batch_stats(b)
+            if reps == 16:  # four groups, each GEMM-offloading subset of 16 genes in one launch
+                assert st["grouped_launches"] - st0["grouped_launches"] == 4
+                assert st["grouped_genes"] - st0["grouped_genes"] == 32
+        times[reps] = np.minimum(runs[0], runs[1])
         gao.batch_destroy(b)
         for h in handles:
             gao.prog_destroy(h)
