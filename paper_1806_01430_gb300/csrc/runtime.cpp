@@ -1122,10 +1122,11 @@ gao_status run_gpu_chain(RunCtx& R, int li, const Chain& ch) {
 }
 
 // Copy/compute overlap for a GPU GEMM loop whose A has to come from the host (the
-// host-to-device link, ~210 GB/s on this machine, is 30x slower than HBM): B is copied
-// first, then A and C0 in row blocks on a copy stream, and each row block's split and
-// tensor-core GEMM start as soon as its rows have landed, while the next block is still
-// on the link.  Row blocks give the same bits as one launch (every output is formed the
+// host-to-device link, measured at ~210 GB/s, is 30x slower than HBM): B (without a fused
+// chain: its first column range, then A's first rows, then its other columns), then A and
+// C0 in row blocks travel on a copy stream, and each row block's split and tensor-core GEMM
+// start as soon as its rows have landed, while the next block is still on the link.  Row
+// blocks and column ranges give the same bits as one launch (every output is formed the
 // same way); only the split precisions take this path.
 int64_t pipeline_blocks(const gao_prog* p, const gao_loop& L) {
     const int prec = p->opts.gemm_prec;
