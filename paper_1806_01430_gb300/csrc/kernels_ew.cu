@@ -787,9 +787,18 @@ __global__ void __launch_bounds__(kStencilThreads, kEdgeBlocks)
     const int64_t r1 = r0 + strip < row_end ? r0 + strip : row_end;
     const int64_t ylim = r1 + 2 < rows ? r1 + 2 : rows;
     // B's row from the raw rows above, at and below it (zero outside the image)
+    // a lane whose columns are all inside the image zeroes none of its B values but in the
+    // rows above and below it, so it skips the per-value choice elsewhere
+    bool all_in = true;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) all_in = all_in && inc[q];
     auto blur = [&](float b[NC], const float* xu, const float* xm, const float* xd, bool row_in) {
 #pragma unroll
-        for (int q = 0; q < NC; ++q) b[q] = (row_in && inc[q]) ? stencil9<P0>(w0, xu, xm, xd, q) : 0.0f;
+        for (int q = 0; q < NC; ++q) b[q] = stencil9<P0>(w0, xu, xm, xd, q);
+        if (!(row_in && all_in)) {
+#pragma unroll
+            for (int q = 0; q < NC; ++q) b[q] = (row_in && inc[q]) ? b[q] : 0.0f;
+        }
     };
     auto store_b = [&](int64_t y, const float b[NC]) {
         if (STORE && bout && y >= r0 && y < r1) edge_store<VEC>(bout + y * cols, c0, outc, b);
