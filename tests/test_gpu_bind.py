@@ -140,3 +140,32 @@ def test_overlapped_gemm_copies_c_back_by_row_block(gao, prec, n):
     assert sum(s["d2h_bytes"] for s in gao.prog_stats(p)) == 0
     assert np.all(C_out == np.float32(-1.0))
     gao.prog_destroy(p)
+
+
+@pytest.mark.parametrize("prec,m,k,n", [("bf16x6", 4100, 1100, 1800), ("bf16", 4352, 1024, 2700),
+                                         ("bf16x3", 5000, 900, 513)])
+def test_overlapped_rectangular_gemm_bit_identical(gao, prec, m, k, n):
+    """A rectangular GEMM whose operands come from the host (A's rows in blocks, the first
+    block's columns of C in two ranges, beta C0 after each block): the bits of the same GEMM
+    on operands the INIT loop formed on the device, one launch."""
+    pr = {"bf16x6": gao.BF16X6, "bf16x3": gao.BF16X3, "bf16": gao.BF16}[prec]
+    seed = 73
+    shapes = {"A": (m, k), "B": (k, n), "C0": (m, n), "C": (m, n)}
+    dev = W.Program("rect_dev", [W.Buffer(nm, *shapes[nm], W.F32, W.OUTPUT if nm == "C" else W.TEMP)
+                                 for nm in ("A", "B", "C0", "C")],
+                    [W.Loop(W.INIT, [], [0, 1, 2]), W.Loop(W.GEMM, [0, 1, 2], [3], alpha=1.5, beta=0.5)], seed)
+    host = W.Program("rect_host", [W.Buffer(nm, *shapes[nm], W.F32, W.OUTPUT if nm == "C" else W.INPUT)
+                                   for nm in ("A", "B", "C0", "C")],
+                     [W.Loop(W.GEMM, [0, 1, 2], [3], alpha=1.5, beta=0.5)], seed)
+    p = gao.prog_from_workload(dev, gemm_prec=pr)
+    gao.prog_run(p, 0b11)
+    C_ref = gao.prog_output(p, 3).copy()
+    gao.prog_destroy(p)
+    q = gao.prog_from_workload(host, gemm_prec=pr)
+    for b, nm in enumerate(("A", "B", "C0")):
+        gao.prog_set_input(q, b, oracle.init_matrix(seed, b, *shapes[nm]).astype(np.float32))
+    for _ in range(2):  # a plain run, then the captured graph
+        gao.prog_run(q, 0b1)
+        assert np.array_equal(gao.prog_output(q, 3).view(np.uint32), C_ref.view(np.uint32))
+    assert gao.prog_stats(q)[0]["launches"] > 3  # row blocks (and column ranges) ran
+    gao.prog_destroy(q)
