@@ -247,6 +247,24 @@ def test_fused_pass_degenerate_shapes(gao, hw):
     assert st[1]["placement"] == 1 and all(s["placement"] == 2 for s in st[2:])
 
 
+@pytest.mark.parametrize("hw", [(0, 64), (64, 0), (0, 0)])
+def test_empty_frames(gao, hw):
+    """Frames with no rows or no columns, separate loops and one fused pass: nothing is
+    launched over the empty image, the edge energy is 0 and each column maximum of no rows is
+    -inf, as in the oracle."""
+    h, w = hw
+    prog = W.image_program(h, w, W.SEED_IMAGE, outputs=("M2", "e", "q"))
+    ref = oracle.run_program(prog)
+    for fuse in (gao.FUSE_OFF, gao.FUSE_ON):
+        p = gao.prog_from_workload(prog, fuse_chains=fuse)
+        gao.prog_run(p, (1 << prog.n_loops) - 1)
+        assert gao.prog_output(p, prog.index("M2")).shape == (h, w)
+        assert float(gao.prog_output(p, prog.index("e"))[0, 0]) == 0.0 == float(ref["e"])
+        q = gao.prog_output(p, prog.index("q"))
+        assert q.shape == (1, w) and np.all(q == -np.inf) and np.all(np.asarray(ref["q"]) == -np.inf)
+        gao.prog_destroy(p)
+
+
 @pytest.mark.parametrize("h,w", [(64, 250), (2048, 2048)])
 def test_fused_pass_special_values(gao, h, w):
     """A frame holding NaNs of either sign (quiet, signalling, with payloads), infinities,

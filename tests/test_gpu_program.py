@@ -151,6 +151,22 @@ def test_init_outputs_bit_exact(gao, shapes):
         assert np.array_equal(out[f"X{k}"], oracle.init_matrix(seed, k, r, c).astype(np.float32)), (k, r, c)
 
 
+@pytest.mark.parametrize("prec", ["FP32_SIMT", "BF16X6", "BF16", "FP8"])
+@pytest.mark.parametrize("fuse", [0, 1])
+def test_empty_six_loop_program(gao, prec, fuse):
+    """n = 0: every buffer empty, every gene runs, nothing is launched over an empty shape and
+    the norm is 0, as in the oracle."""
+    prog = W.six_loop(0, 5, outputs=("C", "D", "E", "r", "f"))
+    p = gao.prog_from_workload(prog, gemm_prec=getattr(gao, prec), fuse_chains=fuse)
+    for mask in (0b111111, 0b000000, 0b101010):
+        gao.prog_run(p, mask)
+        for nm in ("C", "D", "E"):
+            assert gao.prog_output(p, prog.index(nm)).shape == (0, 0)
+        assert gao.prog_output(p, prog.index("r")).shape == (0, 1)
+        assert float(gao.prog_output(p, prog.index("f"))[0, 0]) == 0.0
+    gao.prog_destroy(p)
+
+
 def test_row_scaled_init_bit_exact(gao):
     prog = all_outputs(W.six_loop(200, W.SEED_N8192_ROWS, rowscale_a=True))
     ref = oracle.run_program(prog)
