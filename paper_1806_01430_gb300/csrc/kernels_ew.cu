@@ -694,9 +694,9 @@ __global__ void __launch_bounds__(kStencilThreads, CHAIN ? kChainBlocks : 8)
 // r + 1, so neither B nor the chain's intermediates go through memory (B is written only when
 // something else reads it).  B is zero outside the image, as the separate loops pad it, and
 // every value is formed with the separate loops' operations, so the bits are theirs.
-// Lanes hold four columns each; lanes 1 .. 30 of a warp produce its 120 output columns, and
-// lanes 0 and 31 hold the four columns either side, whose raw values and B values their
-// neighbours take by shuffle, so no lane loads an edge column of its own.
+// Lanes hold kEdgeNC (eight) columns each; lanes 1 .. 30 of a warp produce its 240 output
+// columns, and lanes 0 and 31 hold the eight columns either side, whose raw values and B
+// values their neighbours take by shuffle, so no lane loads an edge column of its own.
 constexpr int kEdgeNC = 8;          // columns a lane holds (a multiple of 4)
 constexpr int kEdgeCols = 30 * kEdgeNC;  // output columns of a warp (lanes 1 .. 30)
 constexpr int kEdgeBlocks = 5;      // resident 128-thread blocks per SM the kernel is built for
